@@ -1,0 +1,345 @@
+"""ctypes wrapper of the CPU oracle (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline and
+reference legs may import this package.  The oracle is plain C in double
+precision (binary32 only where a float decides an integer), brute force over
+every triangle, and shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        _declare(_lib)
+    return _lib
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("fwd", C.c_float * 3), ("right", C.c_float * 3),
+                ("up", C.c_float * 3), ("tan_half_fov_y", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class OrcTraceParams(C.Structure):
+    _fields_ = [("n_lights", C.c_int32), ("light_dir", (C.c_float * 3) * 8),
+                ("cone_half_angle", C.c_float * 8), ("ao_radius", C.c_float),
+                ("ao_spp", C.c_int32), ("frame", C.c_uint32), ("seed", C.c_uint32)]
+
+
+class OrcMargin(C.Structure):
+    _fields_ = [("eps_abs", C.c_double), ("eps_rel", C.c_double)]
+
+
+class OrcSvgfParams(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("sigma_z", C.c_double), ("sigma_n", C.c_double),
+                ("sigma_l", C.c_double), ("eps_z", C.c_double), ("eps_l", C.c_double),
+                ("ao_spp", C.c_int32), ("levels", C.c_int32), ("fixed_alpha", C.c_int32),
+                ("wl_in_atrous", C.c_int32)]
+
+
+P = C.c_void_p
+
+
+def _declare(L):
+    L.orc_pcg4d.argtypes = [P]
+    L.orc_u24.argtypes = [C.c_uint32]
+    L.orc_u24.restype = C.c_float
+    L.orc_disk_point.argtypes = [C.c_uint32] * 6 + [P]
+    L.orc_disk_point.restype = C.c_int
+    L.orc_onb_f32.argtypes = [P, P, P]
+    L.orc_ao_dir_f32.argtypes = [P, C.c_float, C.c_float, P]
+    L.orc_cone_dir_f32.argtypes = [P, C.c_float, C.c_float, C.c_float, P]
+    L.orc_sample_batch_f32.argtypes = [C.c_int64, P, P, C.c_uint32, C.c_uint32, C.c_uint32,
+                                       P, P, C.c_float, P, P, P, P]
+    L.orc_scene_create.argtypes = [P, P, P, C.c_int64, C.c_int64]
+    L.orc_scene_create.restype = P
+    L.orc_scene_destroy.argtypes = [P]
+    L.orc_cast.argtypes = [P, P, P, C.c_double, C.c_double, C.c_int, P, P, P, P, P, P]
+    L.orc_trace.argtypes = [P, P, P, P, P, C.c_int64] + [P] * 10
+    L.orc_num_threads.restype = C.c_int
+    L.orc_svgf_temporal.argtypes = [C.c_int, C.c_int] + [P] * 15
+    L.orc_svgf_atrous.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P]
+    L.orc_svgf_frame.argtypes = [C.c_int, C.c_int] + [P] * 16
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------
+# sampling
+# --------------------------------------------------------------------------
+def pcg4d(v):
+    a = _c(v, np.uint32).copy()
+    lib().orc_pcg4d(_p(a))
+    return a
+
+
+def u24(h: int) -> float:
+    return lib().orc_u24(int(h))
+
+
+def disk_point(px, py, frame, seed, ray_type, sample):
+    xy = np.zeros(2, np.float32)
+    k = lib().orc_disk_point(px, py, frame, seed, ray_type, sample, _p(xy))
+    return float(xy[0]), float(xy[1]), k
+
+
+def onb_f32(n):
+    n = _c(n, np.float32)
+    T = np.zeros(3, np.float32)
+    B = np.zeros(3, np.float32)
+    lib().orc_onb_f32(_p(n), _p(T), _p(B))
+    return T, B
+
+
+def ao_dir_f32(n, x, y):
+    n = _c(n, np.float32)
+    d = np.zeros(3, np.float32)
+    lib().orc_ao_dir_f32(_p(n), x, y, _p(d))
+    return d
+
+
+def cone_dir_f32(l, tan_theta, x, y):
+    l = _c(l, np.float32)
+    d = np.zeros(3, np.float32)
+    lib().orc_cone_dir_f32(_p(l), tan_theta, x, y, _p(d))
+    return d
+
+
+def sample_batch(px, py, frame, seed, sample, normals, light, tan_theta):
+    px = _c(px, np.uint32)
+    py = _c(py, np.uint32)
+    n = len(px)
+    normals = _c(normals, np.float32).reshape(n, 3)
+    light = _c(light, np.float32)
+    out = [np.zeros((n, 2), np.float32), np.zeros((n, 3), np.float32),
+           np.zeros((n, 2), np.float32), np.zeros((n, 3), np.float32)]
+    lib().orc_sample_batch_f32(n, _p(px), _p(py), frame, seed, sample, _p(normals), _p(light),
+                               float(np.float32(tan_theta)), *[_p(o) for o in out])
+    return dict(disk_ao=out[0], dir_ao=out[1], disk_sh=out[2], dir_sh=out[3])
+
+
+def tan_f32(angle_rad: float) -> float:
+    """tan of the cone half angle, computed in double and rounded once."""
+    return float(np.float32(math.tan(float(np.float32(angle_rad)))))
+
+
+# --------------------------------------------------------------------------
+# geometry
+# --------------------------------------------------------------------------
+DEFAULT_MARGIN = (3e-5, 6e-5)
+
+
+class Scene:
+    def __init__(self, scene: dict):
+        self.v = _c(scene["vertices"], np.float32)
+        self.i = _c(scene["indices"], np.uint32)
+        self.m = _c(scene["mesh_ids"], np.uint32)
+        self.n = len(self.i)
+        self.h = lib().orc_scene_create(_p(self.v), _p(self.i), _p(self.m), len(self.v), self.n)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.orc_scene_destroy(self.h)
+            self.h = None
+
+
+def cast(scene: Scene, o, d, tmin=0.0, tmax=math.inf, any_hit=False, margin=DEFAULT_MARGIN):
+    o = _c(o, np.float64)
+    d = _c(d, np.float64)
+    mg = OrcMargin(*margin)
+    hit, amb = C.c_int32(), C.c_int32()
+    t, tri = C.c_double(), C.c_int64()
+    uv = np.zeros(2)
+    lib().orc_cast(scene.h, _p(o), _p(d), tmin, tmax, int(any_hit), C.byref(mg), C.byref(hit),
+                   C.byref(amb), C.byref(t), C.byref(tri), _p(uv))
+    return dict(hit=bool(hit.value), ambiguous=bool(amb.value), t=t.value, tri=tri.value, uv=uv)
+
+
+def make_camera(cam) -> OrcCamera:
+    c = OrcCamera()
+    c.pos[:] = [float(x) for x in cam.pos]
+    c.fwd[:] = [float(x) for x in cam.forward]
+    c.right[:] = [float(x) for x in cam.right]
+    c.up[:] = [float(x) for x in cam.up]
+    c.tan_half_fov_y = cam.tan_half_fov_y
+    c.width = cam.width
+    c.height = cam.height
+    return c
+
+
+@dataclass
+class TraceParams:
+    light_dirs: list = field(default_factory=lambda: [(0.3, 1.0, 0.2)])
+    cone_half_angle_deg: list = field(default_factory=lambda: [0.5])
+    ao_radius: float = 1.0
+    ao_spp: int = 1
+    frame: int = 0
+    seed: int = 0
+
+    def unit_lights(self):
+        out = []
+        for l in self.light_dirs:
+            l = np.asarray(l, np.float64)
+            out.append((l / np.linalg.norm(l)).astype(np.float32))
+        return out
+
+    def to_c(self) -> OrcTraceParams:
+        p = OrcTraceParams()
+        ls = self.unit_lights()
+        p.n_lights = len(ls)
+        for k, l in enumerate(ls):
+            p.light_dir[k][:] = [float(x) for x in l]
+            p.cone_half_angle[k] = math.radians(self.cone_half_angle_deg[k])
+        p.ao_radius = self.ao_radius
+        p.ao_spp = self.ao_spp
+        p.frame = self.frame
+        p.seed = self.seed
+        return p
+
+
+def trace(scene: Scene, cam, params: TraceParams, pixels=None, margin=DEFAULT_MARGIN):
+    """Brute-force trace of the given pixels ([n, 2] int (x, y); None = all)."""
+    if pixels is None:
+        ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+        pixels = np.stack([xs.ravel(), ys.ravel()], -1)
+    pixels = _c(pixels, np.int32).reshape(-1, 2)
+    n = len(pixels)
+    out = dict(depth=np.zeros(n), normal=np.zeros((n, 3)), pos=np.zeros((n, 3)),
+               tri=np.zeros(n, np.int64), mesh=np.zeros(n, np.uint32),
+               shadow_mask=np.zeros(n, np.uint8), ao_count=np.zeros(n, np.uint8),
+               amb_primary=np.zeros(n, np.uint8), amb_shadow=np.zeros(n, np.uint8),
+               amb_ao=np.zeros(n, np.uint8))
+    c = make_camera(cam)
+    tp = params.to_c()
+    mg = OrcMargin(*margin)
+    lib().orc_trace(scene.h, C.byref(c), C.byref(tp), C.byref(mg), _p(pixels), n,
+                    *[_p(out[k]) for k in ("depth", "normal", "pos", "tri", "mesh", "shadow_mask",
+                                           "ao_count", "amb_primary", "amb_shadow", "amb_ao")])
+    out["pixels"] = pixels
+    return out
+
+
+def gbuffer_f32(tr, width, height):
+    """Full-frame trace result -> binary32 G-buffer (zn [H, W, 4], mesh [H, W])."""
+    zn = np.zeros((height, width, 4), np.float32)
+    zn[..., 0] = tr["depth"].reshape(height, width)
+    zn[..., 1:] = tr["normal"].reshape(height, width, 3)
+    mesh = tr["mesh"].reshape(height, width).astype(np.uint32)
+    return zn, mesh
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+# --------------------------------------------------------------------------
+# modified SVGF
+# --------------------------------------------------------------------------
+@dataclass
+class SvgfParams:
+    alpha: float = 0.2
+    sigma_z: float = 1.0
+    sigma_n: float = 128.0
+    sigma_l: float = 4.0
+    eps_z: float = 1e-6
+    eps_l: float = 1e-10
+    ao_spp: int = 1
+    levels: int = 5
+    fixed_alpha: bool = False
+    wl_in_atrous: bool = True
+
+    def to_c(self) -> OrcSvgfParams:
+        return OrcSvgfParams(self.alpha, self.sigma_z, self.sigma_n, self.sigma_l, self.eps_z,
+                             self.eps_l, self.ao_spp, self.levels, int(self.fixed_alpha),
+                             int(self.wl_in_atrous))
+
+
+class SvgfState:
+    """History of the oracle's SVGF: colour, moments, history length."""
+
+    def __init__(self, width, height):
+        self.w, self.h = width, height
+        self.col = np.zeros((height, width, 2))
+        self.mom = np.zeros((height, width, 4))
+        self.hist = np.zeros((height, width), np.int32)
+        self.prev = None          # (zn, mesh, camera) of the previous frame
+
+    def frame(self, zn, mesh, cam, mask, ao, params: SvgfParams, keep_levels=False):
+        W, H = self.w, self.h
+        zn = _c(zn, np.float32)
+        mesh = _c(mesh, np.uint32)
+        mask = _c(mask, np.uint8)
+        ao = _c(ao, np.uint8)
+        illum = np.zeros((H, W, 4))
+        levels = np.zeros((max(params.levels, 1), H, W, 4)) if keep_levels else None
+        ao_out = np.zeros((H, W))
+        sh_out = np.zeros((H, W))
+        c = make_camera(cam)
+        if self.prev is not None:
+            znp, meshp, camp = self.prev
+            cp = make_camera(camp)
+        else:
+            znp = meshp = None
+            cp = c
+        pp = params.to_c()
+        lib().orc_svgf_frame(W, H, _p(zn), _p(mesh), _p(znp), _p(meshp), C.byref(c), C.byref(cp),
+                             _p(mask), _p(ao), C.byref(pp), _p(self.col), _p(self.mom),
+                             _p(self.hist), _p(illum), _p(levels), _p(ao_out), _p(sh_out))
+        self.prev = (zn, mesh, cam)
+        return dict(ao=ao_out, shadow=sh_out, illum=illum, levels=levels)
+
+
+def svgf_temporal(zn, mesh, cam, mask, ao, params: SvgfParams, prev=None, col_hist=None,
+                  mom=None, hist=None):
+    """Temporal accumulation + variance only.  prev = (zn, mesh, camera) or None."""
+    H, W = zn.shape[:2]
+    zn = _c(zn, np.float32)
+    mesh = _c(mesh, np.uint32)
+    col_hist = _c(col_hist if col_hist is not None else np.zeros((H, W, 2)), np.float64)
+    mom = _c(mom if mom is not None else np.zeros((H, W, 4)), np.float64)
+    hist = _c(hist if hist is not None else np.zeros((H, W)), np.int32)
+    mom_out = np.zeros((H, W, 4))
+    hist_out = np.zeros((H, W), np.int32)
+    illum = np.zeros((H, W, 4))
+    valid = np.zeros((H, W), np.int32)
+    c = make_camera(cam)
+    if prev is not None:
+        znp, meshp = _c(prev[0], np.float32), _c(prev[1], np.uint32)
+        cp = make_camera(prev[2])
+    else:
+        znp = meshp = None
+        cp = c
+    pp = params.to_c()
+    lib().orc_svgf_temporal(W, H, _p(zn), _p(mesh), _p(znp), _p(meshp), C.byref(c), C.byref(cp),
+                            _p(_c(mask, np.uint8)), _p(_c(ao, np.uint8)), C.byref(pp),
+                            _p(col_hist), _p(mom), _p(hist), _p(mom_out), _p(hist_out), _p(illum),
+                            _p(valid))
+    return dict(illum=illum, mom=mom_out, hist=hist_out, valid=valid)
+
+
+def svgf_atrous(zn, illum, step, params: SvgfParams):
+    H, W = zn.shape[:2]
+    zn = _c(zn, np.float32)
+    illum = _c(illum, np.float64)
+    out = np.zeros((H, W, 4))
+    pp = params.to_c()
+    lib().orc_svgf_atrous(W, H, _p(zn), _p(illum), int(step), C.byref(pp), _p(out))
+    return out

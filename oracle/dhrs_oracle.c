@@ -1,0 +1,919 @@
+/*
+ * dhrs_oracle.c -- CPU oracle for the DHR+S server hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant generator with the CUDA library; the two
+ * meet only through the seeded inputs of the `workloads` package and through
+ * the written specification of the sampling formulas.
+ *
+ * What it computes, and where each part comes from:
+ *   - primary visibility (G-buffer from pixel-centre rays): stands in for the
+ *     client rasteriser of Section 1 / Section 3.3 (depth, normal, mesh id);
+ *   - soft shadow: one shadow ray per light whose direction is jittered
+ *     uniformly over the light's cone (Section 3.1, Fig. 1);
+ *   - ambient occlusion: cosine-weighted hemisphere rays bounded by radius r,
+ *     O = N_unoccluded / N (Section 3.2, Eqs. 1-3);
+ *   - modified SVGF: temporal reprojection + exponential moving average,
+ *     moment variance with a 7x7 depth/normal-weighted spatial fallback, and
+ *     edge-stopping a-trous iterations (Section 3.3).
+ *
+ * Precision: geometry, intersection and filtering run in double.  Where a
+ * floating-point value decides an integer (disk-sample rejection, validity
+ * of reprojected history taps) the decision is taken in binary32 with every
+ * operation written out and correctly rounded, so that a binary32 GPU kernel
+ * can take the same decision.  Compile with -ffp-contract=off and without
+ * -ffast-math.
+ *
+ * Intersection is brute force over every triangle (Moller-Trumbore in double);
+ * there is no acceleration structure here.
+ *
+ * Parity pins: see tests/test_oracle_*.py.  Every exported function below is
+ * pinned by at least one closed form, invariant or independent library
+ * routine there.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_MAX_LIGHTS 8
+#define ORC_BACKGROUND 0xFFFFFFFFu
+
+/* ------------------------------------------------------------------------ */
+/* Structures (ctypes mirrors live in oracle/__init__.py)                   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    float pos[3], fwd[3], right[3], up[3];
+    float tan_half_fov_y;
+    int32_t width, height;
+} orc_camera;
+
+typedef struct {
+    int32_t n_lights;
+    float light_dir[ORC_MAX_LIGHTS][3];   /* unit, pointing toward the light */
+    float cone_half_angle[ORC_MAX_LIGHTS];/* radians */
+    float ao_radius;
+    int32_t ao_spp;
+    uint32_t frame;
+    uint32_t seed;
+} orc_trace_params;
+
+typedef struct {
+    double eps_abs;   /* world-space tolerance for the grazing classification */
+    double eps_rel;   /* ... plus eps_rel * (|origin|_inf + distance along the ray) */
+} orc_margin;
+
+typedef struct {
+    int64_t n;
+    double *v0, *e1, *e2;    /* [n][3] */
+    double *inv_h;           /* [n][3]: 1 / (distance of vertex k to the opposite edge) */
+    double *nrm;             /* [n][3] unit geometric normal (e1 x e2) */
+    uint32_t *mesh;
+    double extent;           /* largest |coordinate| of any vertex */
+} orc_scene;
+
+typedef struct {
+    double alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
+    int32_t ao_spp, levels, fixed_alpha, wl_in_atrous;
+} orc_svgf_params;
+
+/* ======================================================================== */
+/* 1. Random numbers: pcg4d of Jarzynski & Olano, "Hash Functions for GPU   */
+/*    Rendering", JCGT 9(3), 2020.  The paper only says the jitter is       */
+/*    random (Section 3.1) and that AO rays are shot at random (Section     */
+/*    3.3); this counter-based hash is the chosen generator.                */
+/* ======================================================================== */
+void orc_pcg4d(uint32_t v[4])
+{
+    /* linear congruential step on each lane */
+    for (int k = 0; k < 4; ++k) v[k] = v[k] * 1664525u + 1013904223u;
+    /* cross-lane mixing, shift, mixing again */
+    v[0] += v[1] * v[3];
+    v[1] += v[2] * v[0];
+    v[2] += v[0] * v[1];
+    v[3] += v[1] * v[2];
+    for (int k = 0; k < 4; ++k) v[k] ^= v[k] >> 16;
+    v[0] += v[1] * v[3];
+    v[1] += v[2] * v[0];
+    v[2] += v[0] * v[1];
+    v[3] += v[1] * v[2];
+}
+
+/* top 24 bits of a hash word -> exact float in [0, 1) */
+float orc_u24(uint32_t h) { return (float)(h >> 8) * (1.0f / 16777216.0f); }
+
+/* Hash input for one sample: (px, py, frame ^ seed, stream) with
+ * stream = ray_type << 24 | (sample & 0xFFFF) << 8 | call. */
+static void hash_call(uint32_t px, uint32_t py, uint32_t frame, uint32_t seed,
+                      uint32_t ray_type, uint32_t sample, uint32_t call, uint32_t out[4])
+{
+    out[0] = px;
+    out[1] = py;
+    out[2] = frame ^ seed;
+    out[3] = (ray_type << 24) | ((sample & 0xFFFFu) << 8) | (call & 0xFFu);
+    orc_pcg4d(out);
+}
+
+/* Uniform point on the unit disk by rejection: up to 8 candidates, two per
+ * hash call (u0,u1) then (u2,u3); the test x*x + y*y < 1 is taken in
+ * binary32.  Returns the index of the accepted candidate, 8 if all were
+ * rejected (then the point is the centre). */
+int orc_disk_point(uint32_t px, uint32_t py, uint32_t frame, uint32_t seed,
+                   uint32_t ray_type, uint32_t sample, float xy[2])
+{
+    for (uint32_t call = 0; call < 4; ++call) {
+        uint32_t h[4];
+        hash_call(px, py, frame, seed, ray_type, sample, call, h);
+        for (int half = 0; half < 2; ++half) {
+            volatile float x = 2.0f * orc_u24(h[2 * half]) - 1.0f;
+            volatile float y = 2.0f * orc_u24(h[2 * half + 1]) - 1.0f;
+            volatile float xx = x * x;
+            volatile float yy = y * y;
+            volatile float s = xx + yy;
+            if (s < 1.0f) {
+                xy[0] = x;
+                xy[1] = y;
+                return (int)(2 * call + half);
+            }
+        }
+    }
+    xy[0] = 0.0f;
+    xy[1] = 0.0f;
+    return 8;
+}
+
+/* Orthonormal basis (T, B) around unit n: the branch-free construction of
+ * Duff et al., "Building an Orthonormal Basis, Revisited", JCGT 6(1), 2017.
+ * binary32 version, one rounding per written operation. */
+void orc_onb_f32(const float n[3], float T[3], float B[3])
+{
+    volatile float sgn = copysignf(1.0f, n[2]);
+    volatile float den = sgn + n[2];
+    volatile float a = -1.0f / den;
+    volatile float nxny = n[0] * n[1];
+    volatile float b = nxny * a;
+    volatile float snx = sgn * n[0];
+    volatile float snxnx = snx * n[0];
+    volatile float t0 = snxnx * a;
+    T[0] = 1.0f + t0;
+    T[1] = sgn * b;
+    T[2] = -(sgn * n[0]);
+    volatile float nyny = n[1] * n[1];
+    volatile float b1 = nyny * a;
+    B[0] = b;
+    B[1] = sgn + b1;
+    B[2] = -n[1];
+}
+
+static void onb_f64(const double n[3], double T[3], double B[3])
+{
+    double sgn = copysign(1.0, n[2]);
+    double a = -1.0 / (sgn + n[2]);
+    double b = n[0] * n[1] * a;
+    T[0] = 1.0 + sgn * n[0] * n[0] * a;
+    T[1] = sgn * b;
+    T[2] = -sgn * n[0];
+    B[0] = b;
+    B[1] = sgn + n[1] * n[1] * a;
+    B[2] = -n[1];
+}
+
+/* Cosine-weighted direction about n (Malley's method: a uniform disk point
+ * lifted to the hemisphere); Section 3.2 samples AO directions with a
+ * cosine-weighted pdf.  binary32: d = (x T + y B) + z n. */
+void orc_ao_dir_f32(const float n[3], float x, float y, float d[3])
+{
+    float T[3], B[3];
+    orc_onb_f32(n, T, B);
+    volatile float xx = x * x, yy = y * y;
+    volatile float s = xx + yy;
+    volatile float om = 1.0f - s;
+    volatile float z = sqrtf(om > 0.0f ? om : 0.0f);
+    for (int k = 0; k < 3; ++k) {
+        volatile float a = x * T[k];
+        volatile float b = y * B[k];
+        volatile float c = z * n[k];
+        volatile float ab = a + b;
+        d[k] = ab + c;
+    }
+}
+
+/* Soft-shadow direction, Section 3.1 / Fig. 1b: the direction toward the
+ * light is offset by a bounded random amount inside the cone of half angle
+ * theta and renormalised to unit length (its length does not change).
+ * Disk form: q = l + tan(theta) (x T_l + y B_l), d = q / |q|.  binary32. */
+void orc_cone_dir_f32(const float l[3], float tan_theta, float x, float y, float d[3])
+{
+    float T[3], B[3];
+    orc_onb_f32(l, T, B);
+    float q[3];
+    for (int k = 0; k < 3; ++k) {
+        volatile float a = x * T[k];
+        volatile float b = y * B[k];
+        volatile float ab = a + b;
+        volatile float o = tan_theta * ab;
+        q[k] = l[k] + o;
+    }
+    volatile float q0 = q[0] * q[0], q1 = q[1] * q[1], q2 = q[2] * q[2];
+    volatile float s01 = q0 + q1;
+    volatile float s = s01 + q2;
+    volatile float len = sqrtf(s);
+    for (int k = 0; k < 3; ++k) d[k] = q[k] / len;
+}
+
+static void ao_dir_f64(const double n[3], double x, double y, double d[3])
+{
+    double T[3], B[3];
+    onb_f64(n, T, B);
+    double z = sqrt(fmax(0.0, 1.0 - x * x - y * y));
+    for (int k = 0; k < 3; ++k) d[k] = x * T[k] + y * B[k] + z * n[k];
+}
+
+static void cone_dir_f64(const double l[3], double tan_theta, double x, double y, double d[3])
+{
+    double T[3], B[3];
+    onb_f64(l, T, B);
+    double q[3], s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        q[k] = l[k] + tan_theta * (x * T[k] + y * B[k]);
+        s += q[k] * q[k];
+    }
+    s = sqrt(s);
+    for (int k = 0; k < 3; ++k) d[k] = q[k] / s;
+}
+
+/* Batch form used by the bit-exactness test: for each (pixel, sample) the
+ * accepted disk point and both binary32 directions. */
+void orc_sample_batch_f32(int64_t n, const uint32_t* px, const uint32_t* py, uint32_t frame,
+                          uint32_t seed, uint32_t sample, const float* normals /*[n][3]*/,
+                          const float* light /*[3]*/, float tan_theta,
+                          float* disk_ao /*[n][2]*/, float* dir_ao /*[n][3]*/,
+                          float* disk_sh /*[n][2]*/, float* dir_sh /*[n][3]*/)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        orc_disk_point(px[i], py[i], frame, seed, 1u, sample, disk_ao + 2 * i);
+        orc_ao_dir_f32(normals + 3 * i, disk_ao[2 * i], disk_ao[2 * i + 1], dir_ao + 3 * i);
+        orc_disk_point(px[i], py[i], frame, seed, 0u, sample, disk_sh + 2 * i);
+        orc_cone_dir_f32(light, tan_theta, disk_sh[2 * i], disk_sh[2 * i + 1], dir_sh + 3 * i);
+    }
+}
+
+/* ======================================================================== */
+/* 2. Scene and brute-force ray casting (double)                            */
+/* ======================================================================== */
+static inline void sub3(const double* a, const double* b, double* o)
+{ o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static inline void cross3(const double* a, const double* b, double* o)
+{ o[0] = a[1] * b[2] - a[2] * b[1]; o[1] = a[2] * b[0] - a[0] * b[2]; o[2] = a[0] * b[1] - a[1] * b[0]; }
+static inline double dot3(const double* a, const double* b)
+{ return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static inline double norm3(const double* a) { return sqrt(dot3(a, a)); }
+
+orc_scene* orc_scene_create(const float* verts, const uint32_t* idx, const uint32_t* mesh,
+                            int64_t n_vertices, int64_t n_tris)
+{
+    orc_scene* s = (orc_scene*)calloc(1, sizeof(orc_scene));
+    s->n = n_tris;
+    s->v0 = (double*)malloc(sizeof(double) * 3 * (size_t)n_tris);
+    s->e1 = (double*)malloc(sizeof(double) * 3 * (size_t)n_tris);
+    s->e2 = (double*)malloc(sizeof(double) * 3 * (size_t)n_tris);
+    s->inv_h = (double*)malloc(sizeof(double) * 3 * (size_t)n_tris);
+    s->nrm = (double*)malloc(sizeof(double) * 3 * (size_t)n_tris);
+    s->mesh = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)n_tris);
+    double ext = 0.0;
+    for (int64_t v = 0; v < n_vertices * 3; ++v) ext = fmax(ext, fabs((double)verts[v]));
+    s->extent = ext;
+    for (int64_t i = 0; i < n_tris; ++i) {
+        double p[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int c = 0; c < 3; ++c) p[k][c] = (double)verts[3 * (int64_t)idx[3 * i + k] + c];
+        double *v0 = s->v0 + 3 * i, *e1 = s->e1 + 3 * i, *e2 = s->e2 + 3 * i;
+        memcpy(v0, p[0], sizeof(double) * 3);
+        sub3(p[1], p[0], e1);
+        sub3(p[2], p[0], e2);
+        double c[3];
+        cross3(e1, e2, c);
+        double a2 = norm3(c);                      /* twice the area */
+        double e12[3];
+        sub3(p[2], p[1], e12);
+        double len_opp[3] = {norm3(e12), norm3(e2), norm3(e1)};  /* edges opposite v0, v1, v2 */
+        for (int k = 0; k < 3; ++k) {
+            double h = (a2 > 0.0 && len_opp[k] > 0.0) ? a2 / len_opp[k] : 0.0;
+            s->inv_h[3 * i + k] = h > 0.0 ? 1.0 / h : 0.0;
+            s->nrm[3 * i + k] = a2 > 0.0 ? c[k] / a2 : 0.0;
+        }
+        s->mesh[i] = mesh ? mesh[i] : 0u;
+    }
+    return s;
+}
+
+void orc_scene_destroy(orc_scene* s)
+{
+    if (!s) return;
+    free(s->v0); free(s->e1); free(s->e2); free(s->inv_h); free(s->nrm); free(s->mesh);
+    free(s);
+}
+
+/* Moller & Trumbore, "Fast, Minimum Storage Ray/Triangle Intersection"
+ * (JGT 1997), double precision.  Returns 0 when the ray is parallel to the
+ * plane; otherwise the ray parameter t of the plane crossing and its
+ * barycentrics (u on v1, v on v2; 1-u-v on v0). */
+static inline int mt_plane(const orc_scene* s, int64_t i, const double* o, const double* d,
+                           double* t, double* u, double* v)
+{
+    const double *v0 = s->v0 + 3 * i, *e1 = s->e1 + 3 * i, *e2 = s->e2 + 3 * i;
+    double pv[3], tv[3], qv[3];
+    cross3(d, e2, pv);
+    double det = dot3(e1, pv);
+    if (det == 0.0) return 0;
+    double inv = 1.0 / det;
+    sub3(o, v0, tv);
+    *u = dot3(tv, pv) * inv;
+    cross3(tv, e1, qv);
+    *v = dot3(d, qv) * inv;
+    *t = dot3(e2, qv) * inv;
+    return 1;
+}
+
+/* signed world distance from the plane crossing to the triangle boundary
+ * (positive inside) */
+static inline double edge_margin(const orc_scene* s, int64_t i, double u, double v)
+{
+    const double* ih = s->inv_h + 3 * i;
+    double w = 1.0 - u - v;
+    double m0 = ih[0] > 0.0 ? w / ih[0] : -INFINITY;
+    double m1 = ih[1] > 0.0 ? u / ih[1] : -INFINITY;
+    double m2 = ih[2] > 0.0 ? v / ih[2] : -INFINITY;
+    return fmin(m0, fmin(m1, m2));
+}
+
+static inline double inf_norm3(const double* a)
+{ return fmax(fabs(a[0]), fmax(fabs(a[1]), fabs(a[2]))); }
+
+typedef struct {
+    int hit;              /* exact outcome */
+    int ambiguous;        /* outcome may flip under a perturbation within the margin */
+    double t;             /* closest: hit distance (ray parameter) */
+    int64_t tri;          /* closest: triangle index (ties: smaller index) */
+    double u, v;
+} cast_result;
+
+/* Closest hit with t in (tmin, tmax).  Ambiguity flags a silhouette, an
+ * edge crossing or a near-tie between surfaces within the margin. */
+static cast_result cast_closest(const orc_scene* s, const double* o, const double* d,
+                                double tmin, double tmax, const orc_margin* mg)
+{
+    cast_result r = {0, 0, INFINITY, -1, 0, 0};
+    double dl = norm3(d);
+    double oinf = inf_norm3(o);
+    for (int64_t i = 0; i < s->n; ++i) {
+        double t, u, v;
+        if (!mt_plane(s, i, o, d, &t, &u, &v)) continue;
+        if (!(t > tmin && t < tmax)) continue;
+        if (u >= 0.0 && v >= 0.0 && u + v <= 1.0) {
+            if (t < r.t || (t == r.t && i < r.tri)) {
+                r.t = t; r.tri = i; r.u = u; r.v = v; r.hit = 1;
+            }
+        }
+    }
+    /* ambiguity pass */
+    double t_ref = r.hit ? r.t : tmax;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double t, u, v;
+        if (!mt_plane(s, i, o, d, &t, &u, &v)) continue;
+        if (!(t > tmin)) continue;
+        double tw = t * dl;
+        double eps = mg->eps_abs + mg->eps_rel * (oinf + tw);
+        double cosang = fabs(dot3(d, s->nrm + 3 * i)) / dl;
+        double eps_t = eps / fmax(cosang, 1e-3);
+        double m = edge_margin(s, i, u, v);
+        if (i == r.tri) {
+            if (m < eps) r.ambiguous = 1;          /* hit close to an edge */
+            continue;
+        }
+        if (m >= -eps && tw < t_ref * dl + eps_t && t < tmax) {
+            r.ambiguous = 1;                       /* another surface within the margin in front */
+            break;
+        }
+    }
+    return r;
+}
+
+/* Any hit with t in (tmin, tmax) (occlusion test). */
+static cast_result cast_any(const orc_scene* s, const double* o, const double* d,
+                            double tmin, double tmax, const orc_margin* mg)
+{
+    cast_result r = {0, 0, INFINITY, -1, 0, 0};
+    double dl = norm3(d);
+    double oinf = inf_norm3(o);
+    int loose = 0, strict = 0;
+    double tmax_w = tmax * dl;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double t, u, v;
+        if (!mt_plane(s, i, o, d, &t, &u, &v)) continue;
+        if (!(t > tmin)) continue;
+        double tw = t * dl;
+        double eps = mg->eps_abs + mg->eps_rel * (oinf + fmin(tw, 4.0 * s->extent));
+        double cosang = fabs(dot3(d, s->nrm + 3 * i)) / dl;
+        double eps_t = eps / fmax(cosang, 1e-3);
+        double m = edge_margin(s, i, u, v);
+        if (m >= 0.0 && t < tmax) {
+            r.hit = 1;
+            if (r.tri < 0) { r.tri = i; r.t = t; }
+        }
+        if (m >= -eps && tw < tmax_w + eps_t) loose = 1;
+        if (m >= eps && tw > eps_t && tw < tmax_w - eps_t) strict = 1;
+        if (r.hit && strict) break;                /* certain occlusion */
+    }
+    r.ambiguous = (loose != strict);
+    return r;
+}
+
+/* Public single-ray entry points (unit tests) */
+void orc_cast(const orc_scene* s, const double* o, const double* d, double tmin, double tmax,
+              int any_hit, const orc_margin* mg, int32_t* hit, int32_t* ambiguous,
+              double* t, int64_t* tri, double* uv)
+{
+    cast_result r = any_hit ? cast_any(s, o, d, tmin, tmax, mg) : cast_closest(s, o, d, tmin, tmax, mg);
+    *hit = r.hit; *ambiguous = r.ambiguous; *t = r.t; *tri = r.tri;
+    if (uv) { uv[0] = r.u; uv[1] = r.v; }
+}
+
+/* Pixel-centre camera ray, unnormalised: D = f + sx r + sy u, so that the
+ * ray parameter of a hit equals its linear view depth (dot(D, f) = 1 for an
+ * orthonormal basis).  Image row 0 is the top row. */
+static void camera_ray(const orc_camera* c, int x, int y, double o[3], double D[3])
+{
+    double W = c->width, H = c->height;
+    double sx = (2.0 * (x + 0.5) / W - 1.0) * c->tan_half_fov_y * (W / H);
+    double sy = (1.0 - 2.0 * (y + 0.5) / H) * c->tan_half_fov_y;
+    for (int k = 0; k < 3; ++k) {
+        o[k] = c->pos[k];
+        D[k] = (double)c->fwd[k] + sx * c->right[k] + sy * c->up[k];
+    }
+}
+
+/*
+ * Trace pixels: G-buffer (closest hit of the pixel-centre ray), one
+ * cone-jittered shadow ray per light, ao_spp cosine-weighted AO rays of
+ * length r (Section 3.1, Section 3.2 Eqs. 1-3).
+ *
+ * Per pixel outputs: depth = dot(X - eye, forward) (+inf on a miss),
+ * normal = unit geometric normal facing the eye, pos = X, tri and mesh id
+ * (0xFFFFFFFF on a miss), shadow_mask bit k = light k unoccluded (all bits
+ * set on a miss; 0 when the jittered direction points below the surface,
+ * n . d <= 0, which the surface itself blocks), ao_count = N_unoccluded
+ * (ao_spp on a miss).  Ambiguity
+ * outputs: amb_primary, amb_shadow (bit per light), amb_ao (count of AO
+ * rays whose outcome is within the margin).
+ * Secondary rays start at X and accept hits with t > 1e-9 (1 + |X|_inf).
+ */
+void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params* tp,
+               const orc_margin* mg, const int32_t* pixels /*[np][2] (x, y)*/, int64_t np,
+               double* depth, double* normal, double* pos, int64_t* tri, uint32_t* mesh,
+               uint8_t* shadow_mask, uint8_t* ao_count,
+               uint8_t* amb_primary, uint8_t* amb_shadow, uint8_t* amb_ao)
+{
+    double tan_t[ORC_MAX_LIGHTS];
+    for (int k = 0; k < tp->n_lights; ++k) tan_t[k] = tan((double)tp->cone_half_angle[k]);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < np; ++i) {
+        int x = pixels[2 * i], y = pixels[2 * i + 1];
+        double o[3], D[3];
+        camera_ray(cam, x, y, o, D);
+        cast_result pr = cast_closest(s, o, D, 0.0, INFINITY, mg);
+        amb_primary[i] = (uint8_t)pr.ambiguous;
+        amb_shadow[i] = 0;
+        amb_ao[i] = 0;
+        if (!pr.hit) {
+            depth[i] = INFINITY;
+            for (int k = 0; k < 3; ++k) { normal[3 * i + k] = 0.0; pos[3 * i + k] = 0.0; }
+            tri[i] = -1;
+            mesh[i] = ORC_BACKGROUND;
+            shadow_mask[i] = (uint8_t)((1u << tp->n_lights) - 1u);
+            ao_count[i] = (uint8_t)tp->ao_spp;
+            continue;
+        }
+        double X[3], n[3];
+        for (int k = 0; k < 3; ++k) X[k] = o[k] + pr.t * D[k];
+        const double* gn = s->nrm + 3 * pr.tri;
+        double side = dot3(gn, D) > 0.0 ? -1.0 : 1.0;
+        for (int k = 0; k < 3; ++k) n[k] = side * gn[k];
+        double f[3] = {cam->fwd[0], cam->fwd[1], cam->fwd[2]};
+        double rel[3];
+        sub3(X, o, rel);
+        depth[i] = dot3(rel, f);
+        for (int k = 0; k < 3; ++k) { normal[3 * i + k] = n[k]; pos[3 * i + k] = X[k]; }
+        tri[i] = pr.tri;
+        mesh[i] = s->mesh[pr.tri];
+        double tmin = 1e-9 * (1.0 + inf_norm3(X));
+        /* shadow rays, one per light */
+        uint8_t m = 0, am = 0;
+        for (int k = 0; k < tp->n_lights; ++k) {
+            float xy[2];
+            orc_disk_point((uint32_t)x, (uint32_t)y, tp->frame, tp->seed, 0u, (uint32_t)k, xy);
+            double l[3] = {tp->light_dir[k][0], tp->light_dir[k][1], tp->light_dir[k][2]};
+            double d[3];
+            cone_dir_f64(l, tan_t[k], xy[0], xy[1], d);
+            /* a direction below the surface is blocked by the surface itself */
+            double facing = dot3(d, n);
+            if (fabs(facing) < 1e-6) am |= (uint8_t)(1u << k);
+            if (facing <= 0.0) continue;
+            cast_result sr = cast_any(s, X, d, tmin, INFINITY, mg);
+            if (!sr.hit) m |= (uint8_t)(1u << k);
+            if (sr.ambiguous) am |= (uint8_t)(1u << k);
+        }
+        shadow_mask[i] = m;
+        amb_shadow[i] = am;
+        /* ambient occlusion rays, Eq. 3: count unoccluded rays of length r */
+        int cnt = 0, amb = 0;
+        for (int j = 0; j < tp->ao_spp; ++j) {
+            float xy[2];
+            orc_disk_point((uint32_t)x, (uint32_t)y, tp->frame, tp->seed, 1u, (uint32_t)j, xy);
+            double d[3];
+            ao_dir_f64(n, xy[0], xy[1], d);
+            cast_result ar = cast_any(s, X, d, tmin, (double)tp->ao_radius, mg);
+            if (!ar.hit) ++cnt;
+            if (ar.ambiguous) ++amb;
+        }
+        ao_count[i] = (uint8_t)cnt;
+        amb_ao[i] = (uint8_t)amb;
+    }
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ======================================================================== */
+/* 3. Modified SVGF (Section 3.3), double precision                         */
+/* ======================================================================== */
+/* Buffers: zn = [H][W][4] binary32 (linear depth, unit normal), mesh =
+ * [H][W]; background pixels have depth +inf and mesh id 0xFFFFFFFF.
+ * illum = [H][W][4] double (colour AO, colour shadow, variance AO,
+ * variance shadow). */
+
+static inline int is_fg(const float* zn, int64_t p) { return isfinite(zn[4 * p]); }
+
+/* Temporal reprojection decision in binary32 (Section 3.3: back-project the
+ * pixel's world position into the previous frame; discard history samples
+ * inconsistent in projected depth, normal or mesh id).  The written order of
+ * operations is the specification shared with the GPU kernel; each
+ * intermediate is rounded to binary32.
+ * Returns 1 with the four bilinear taps (valid flags and weights, history
+ * length of the valid taps) or 0 when no valid history exists. */
+typedef struct {
+    int valid;
+    int tx[4], ty[4], ok[4];
+    float w[4];
+    float sumw;
+    int histlen_min;
+} reproj_t;
+
+static reproj_t reproject_f32(int W, int H, int x, int y, const float* znp, uint32_t mp,
+                              const orc_camera* cc, const orc_camera* cp,
+                              const float* zn_prev, const uint32_t* mesh_prev, const int32_t* hist)
+{
+    reproj_t r;
+    memset(&r, 0, sizeof(r));
+    volatile float Wf = (float)W, Hf = (float)H;
+    volatile float aspect = Wf / Hf;
+    volatile float fx = (float)x + 0.5f, fy = (float)y + 0.5f;
+    volatile float t2x = 2.0f * fx, t2y = 2.0f * fy;
+    volatile float qx = t2x / Wf, qy = t2y / Hf;
+    volatile float ndx = qx - 1.0f, ndy = 1.0f - qy;
+    volatile float sxa = ndx * cc->tan_half_fov_y;
+    volatile float sx = sxa * aspect;
+    volatile float sy = ndy * cc->tan_half_fov_y;
+    float z = znp[0];
+    float X[3];
+    for (int k = 0; k < 3; ++k) {
+        volatile float a = sx * cc->right[k];
+        volatile float b = sy * cc->up[k];
+        volatile float fa = cc->fwd[k] + a;
+        volatile float D = fa + b;
+        volatile float zd = z * D;
+        X[k] = cc->pos[k] + zd;
+    }
+    float rr[3];
+    for (int k = 0; k < 3; ++k) rr[k] = X[k] - cp->pos[k];
+    volatile float f0 = rr[0] * cp->fwd[0], f1 = rr[1] * cp->fwd[1], f2 = rr[2] * cp->fwd[2];
+    volatile float f01 = f0 + f1;
+    volatile float zp = f01 + f2;
+    volatile float r0 = rr[0] * cp->right[0], r1 = rr[1] * cp->right[1], r2 = rr[2] * cp->right[2];
+    volatile float r01 = r0 + r1;
+    volatile float rx = r01 + r2;
+    volatile float u0 = rr[0] * cp->up[0], u1 = rr[1] * cp->up[1], u2 = rr[2] * cp->up[2];
+    volatile float u01 = u0 + u1;
+    volatile float ry = u01 + u2;
+    if (!(zp > 0.0f)) return r;
+    volatile float zt = zp * cp->tan_half_fov_y;
+    volatile float zta = zt * aspect;
+    volatile float su = rx / zta;
+    volatile float sv = ry / zt;
+    volatile float pu = su + 1.0f, pv = 1.0f - sv;
+    volatile float hu = pu * 0.5f, hv = pv * 0.5f;
+    volatile float pxc = hu * Wf, pyc = hv * Hf;
+    volatile float gx = pxc - 0.5f, gy = pyc - 0.5f;
+    if (!(gx > -1.0f && gx < Wf && gy > -1.0f && gy < Hf)) return r;
+    float x0f = floorf(gx), y0f = floorf(gy);
+    volatile float ax = gx - x0f, ay = gy - y0f;
+    volatile float bx = 1.0f - ax, by = 1.0f - ay;
+    volatile float w00 = bx * by, w10 = ax * by, w01 = bx * ay, w11 = ax * ay;
+    float wt[4] = {w00, w10, w01, w11};
+    int x0 = (int)x0f, y0 = (int)y0f;
+    int dxs[4] = {0, 1, 0, 1}, dys[4] = {0, 0, 1, 1};
+    volatile float sumw = 0.0f;
+    int hmin = 1 << 30;
+    volatile float zlim = 0.01f * zp;
+    for (int k = 0; k < 4; ++k) {
+        int qx2 = x0 + dxs[k], qy2 = y0 + dys[k];
+        r.tx[k] = qx2; r.ty[k] = qy2; r.w[k] = wt[k]; r.ok[k] = 0;
+        if (qx2 < 0 || qy2 < 0 || qx2 >= W || qy2 >= H) continue;
+        int64_t q = (int64_t)qy2 * W + qx2;
+        if (mesh_prev[q] != mp) continue;
+        volatile float dz = zn_prev[4 * q] - zp;
+        if (!(fabsf(dz) <= zlim)) continue;
+        volatile float n0 = znp[1] * zn_prev[4 * q + 1];
+        volatile float n1 = znp[2] * zn_prev[4 * q + 2];
+        volatile float n2 = znp[3] * zn_prev[4 * q + 3];
+        volatile float n01 = n0 + n1;
+        volatile float nd = n01 + n2;
+        if (!(nd >= 0.9f)) continue;
+        r.ok[k] = 1;
+        sumw = sumw + wt[k];
+        if (hist[q] < hmin) hmin = hist[q];
+    }
+    r.sumw = sumw;
+    r.valid = (sumw >= 1e-4f);
+    r.histlen_min = r.valid ? hmin : 0;
+    return r;
+}
+
+/* depth gradient at p: per axis the one-sided difference of smaller
+ * magnitude among the foreground neighbours (0 if none) */
+static void depth_grad(int W, int H, const float* zn, int x, int y, double g[2])
+{
+    int64_t p = (int64_t)y * W + x;
+    double zp = zn[4 * p];
+    for (int ax = 0; ax < 2; ++ax) {
+        int has_p = 0, has_m = 0;
+        double dp = 0.0, dm = 0.0;
+        int xp = x + (ax == 0), yp = y + (ax == 1);
+        int xm = x - (ax == 0), ym = y - (ax == 1);
+        if (xp < W && yp < H) {
+            int64_t q = (int64_t)yp * W + xp;
+            if (is_fg(zn, q)) { dp = (double)zn[4 * q] - zp; has_p = 1; }
+        }
+        if (xm >= 0 && ym >= 0) {
+            int64_t q = (int64_t)ym * W + xm;
+            if (is_fg(zn, q)) { dm = zp - (double)zn[4 * q]; has_m = 1; }
+        }
+        if (has_p && has_m) g[ax] = (fabs(dm) < fabs(dp)) ? dm : dp;
+        else if (has_p) g[ax] = dp;
+        else if (has_m) g[ax] = dm;
+        else g[ax] = 0.0;
+    }
+}
+
+/* depth edge-stopping weight for offset (ox, oy) = p - q in pixels */
+static inline double w_depth(double zp, double zq, const double g[2], double ox, double oy,
+                             const orc_svgf_params* P)
+{
+    double den = P->sigma_z * fabs(g[0] * ox + g[1] * oy) + P->eps_z;
+    return exp(-fabs(zp - zq) / den);
+}
+
+/* normal edge-stopping weight max(0, n_p . n_q)^sigma_n */
+static inline double w_normal(const float* a, const float* b, double sigma_n)
+{
+    double d = (double)a[0] * b[0] + (double)a[1] * b[1] + (double)a[2] * b[2];
+    d = fmax(0.0, d);
+    return pow(d, sigma_n);
+}
+
+/* noisy signals of the current frame: AO = N_unoccluded / N (Eq. 3),
+ * shadow = visibility bit of light 0 */
+static inline void noisy(const uint8_t* mask, const uint8_t* ao, int64_t p, int spp, double s[2])
+{
+    s[0] = (double)ao[p] / (double)spp;
+    s[1] = (mask[p] & 1u) ? 1.0 : 0.0;
+}
+
+/*
+ * Temporal accumulation + variance estimation (Section 3.3).
+ * In:  current G-buffer, previous G-buffer (NULL: no history), cameras,
+ *      noisy inputs, history (col_hist [H][W][2], mom [H][W][4] = mu1 AO,
+ *      mu1 shadow, mu2 AO, mu2 shadow, histlen [H][W]).
+ * Out: illum [H][W][4]; new moments mom_out and histlen_out.
+ * Exponential moving average with alpha_eff = max(alpha, 1/n) (or alpha
+ * when fixed_alpha; 1 without history); n = min(histlen + 1, 255).
+ * Variance = max(0, mu2 - mu1^2) when n >= 4, else a 7x7 spatial estimate
+ * of the current frame's signal weighted by depth and normal only (the
+ * paper's modification: no luminance term), whose mean is also the colour.
+ */
+void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
+                       const float* zn_prev, const uint32_t* mesh_prev,
+                       const orc_camera* cam, const orc_camera* cam_prev,
+                       const uint8_t* mask, const uint8_t* ao, const orc_svgf_params* P,
+                       const double* col_hist, const double* mom_in, const int32_t* hist_in,
+                       double* mom_out, int32_t* hist_out, double* illum,
+                       int32_t* valid_out /* optional [H][W] */)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t p = (int64_t)y * W + x;
+            if (!is_fg(zn, p)) {
+                illum[4 * p + 0] = 1.0; illum[4 * p + 1] = 1.0;
+                illum[4 * p + 2] = 0.0; illum[4 * p + 3] = 0.0;
+                for (int k = 0; k < 4; ++k) mom_out[4 * p + k] = 1.0;
+                hist_out[p] = 0;
+                if (valid_out) valid_out[p] = 0;
+                continue;
+            }
+            double s[2];
+            noisy(mask, ao, p, P->ao_spp, s);
+            double ch[2] = {0, 0}, mh[4] = {0, 0, 0, 0};
+            int n = 1, valid = 0;
+            if (zn_prev) {
+                reproj_t r = reproject_f32(W, H, x, y, zn + 4 * p, mesh[p], cam, cam_prev,
+                                           zn_prev, mesh_prev, hist_in);
+                if (r.valid) {
+                    valid = 1;
+                    double sw = 0.0;
+                    for (int k = 0; k < 4; ++k) if (r.ok[k]) sw += (double)r.w[k];
+                    for (int k = 0; k < 4; ++k) {
+                        if (!r.ok[k]) continue;
+                        int64_t q = (int64_t)r.ty[k] * W + r.tx[k];
+                        double w = (double)r.w[k] / sw;
+                        ch[0] += w * col_hist[2 * q]; ch[1] += w * col_hist[2 * q + 1];
+                        for (int c = 0; c < 4; ++c) mh[c] += w * mom_in[4 * q + c];
+                    }
+                    n = r.histlen_min + 1;
+                    if (n > 255) n = 255;
+                }
+            }
+            if (valid_out) valid_out[p] = valid;
+            double a = valid ? (P->fixed_alpha ? P->alpha : fmax(P->alpha, 1.0 / n)) : 1.0;
+            double c[2], m[4];
+            for (int k = 0; k < 2; ++k) {
+                c[k] = (1.0 - a) * ch[k] + a * s[k];
+                m[k] = (1.0 - a) * mh[k] + a * s[k];
+                m[2 + k] = (1.0 - a) * mh[2 + k] + a * s[k] * s[k];
+            }
+            for (int k = 0; k < 4; ++k) mom_out[4 * p + k] = m[k];
+            hist_out[p] = n;
+            if (n >= 4) {
+                illum[4 * p + 0] = c[0];
+                illum[4 * p + 1] = c[1];
+                illum[4 * p + 2] = fmax(0.0, m[2] - m[0] * m[0]);
+                illum[4 * p + 3] = fmax(0.0, m[3] - m[1] * m[1]);
+            } else {
+                double g[2];
+                depth_grad(W, H, zn, x, y, g);
+                double sw = 0.0, s1[2] = {0, 0}, s2[2] = {0, 0};
+                for (int dy = -3; dy <= 3; ++dy) {
+                    for (int dx = -3; dx <= 3; ++dx) {
+                        int qx = x + dx, qy = y + dy;
+                        if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                        int64_t q = (int64_t)qy * W + qx;
+                        if (!is_fg(zn, q)) continue;
+                        double w = 1.0;
+                        if (dx || dy)
+                            w = w_depth(zn[4 * p], zn[4 * q], g, -dx, -dy, P)
+                                * w_normal(zn + 4 * p + 1, zn + 4 * q + 1, P->sigma_n);
+                        double sq[2];
+                        noisy(mask, ao, q, P->ao_spp, sq);
+                        sw += w;
+                        for (int k = 0; k < 2; ++k) { s1[k] += w * sq[k]; s2[k] += w * sq[k] * sq[k]; }
+                    }
+                }
+                for (int k = 0; k < 2; ++k) {
+                    double m1 = s1[k] / sw, m2 = s2[k] / sw;
+                    illum[4 * p + k] = m1;
+                    illum[4 * p + 2 + k] = fmax(0.0, m2 - m1 * m1);
+                }
+            }
+        }
+    }
+}
+
+/*
+ * One edge-stopping a-trous iteration with step h (Section 3.3: the filter
+ * is repeated several times, each pass working on the previous pass's
+ * output): 5x5 B3-spline taps (1/16, 1/4, 3/8, 1/4, 1/16) at offsets
+ * h*{-2..2}, weights k * w_z * w_n * w_l; w_l uses a 3x3 Gaussian of the
+ * variance at p.  colour' = sum w c / sum w, variance' = sum w^2 var / (sum w)^2.
+ */
+void orc_svgf_atrous(int W, int H, const float* zn, const double* in, int step,
+                     const orc_svgf_params* P, double* out)
+{
+    static const double k5[5] = {1.0 / 16, 1.0 / 4, 3.0 / 8, 1.0 / 4, 1.0 / 16};
+    static const double k3[3] = {1.0 / 4, 1.0 / 2, 1.0 / 4};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t p = (int64_t)y * W + x;
+            if (!is_fg(zn, p)) {
+                out[4 * p + 0] = 1.0; out[4 * p + 1] = 1.0;
+                out[4 * p + 2] = 0.0; out[4 * p + 3] = 0.0;
+                continue;
+            }
+            /* 3x3 Gaussian of the variance, renormalised over foreground taps */
+            double gv[2] = {0, 0}, gw = 0.0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                    int64_t q = (int64_t)qy * W + qx;
+                    if (!is_fg(zn, q)) continue;
+                    double k = k3[dx + 1] * k3[dy + 1];
+                    gw += k;
+                    gv[0] += k * in[4 * q + 2];
+                    gv[1] += k * in[4 * q + 3];
+                }
+            gv[0] /= gw; gv[1] /= gw;
+            double g[2];
+            depth_grad(W, H, zn, x, y, g);
+            double sw[2] = {0, 0}, sc[2] = {0, 0}, sv[2] = {0, 0};
+            for (int j = -2; j <= 2; ++j) {
+                for (int i = -2; i <= 2; ++i) {
+                    int qx = x + i * step, qy = y + j * step;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                    int64_t q = (int64_t)qy * W + qx;
+                    if (!is_fg(zn, q)) continue;
+                    double k = k5[i + 2] * k5[j + 2];
+                    for (int ch = 0; ch < 2; ++ch) {
+                        double w = k;
+                        if (i || j) {
+                            double wz = w_depth(zn[4 * p], zn[4 * q], g, -(double)i * step,
+                                                -(double)j * step, P);
+                            double wn = w_normal(zn + 4 * p + 1, zn + 4 * q + 1, P->sigma_n);
+                            double wl = 1.0;
+                            if (P->wl_in_atrous)
+                                wl = exp(-fabs(in[4 * p + ch] - in[4 * q + ch])
+                                         / (P->sigma_l * sqrt(fmax(0.0, gv[ch])) + P->eps_l));
+                            w = k * wz * wn * wl;
+                        }
+                        sw[ch] += w;
+                        sc[ch] += w * in[4 * q + ch];
+                        sv[ch] += w * w * in[4 * q + 2 + ch];
+                    }
+                }
+            }
+            for (int ch = 0; ch < 2; ++ch) {
+                out[4 * p + ch] = sc[ch] / sw[ch];
+                out[4 * p + 2 + ch] = sv[ch] / (sw[ch] * sw[ch]);
+            }
+        }
+    }
+}
+
+/*
+ * One full frame of the modified SVGF: temporal + variance, then `levels`
+ * a-trous iterations with steps 1, 2, 4, ...; the first iteration's colour
+ * becomes next frame's colour history (the SVGF design the paper adopts);
+ * the last iteration's colour is the output.
+ * State (in/out): col_hist [H][W][2], mom [H][W][4], hist [H][W].
+ * levels_out (optional): [levels][H][W][4]; illum_out (optional): [H][W][4].
+ */
+void orc_svgf_frame(int W, int H, const float* zn, const uint32_t* mesh,
+                    const float* zn_prev, const uint32_t* mesh_prev,
+                    const orc_camera* cam, const orc_camera* cam_prev,
+                    const uint8_t* mask, const uint8_t* ao, const orc_svgf_params* P,
+                    double* col_hist, double* mom, int32_t* hist,
+                    double* illum_out, double* levels_out, double* ao_out, double* sh_out)
+{
+    int64_t n = (int64_t)W * H;
+    double* a = (double*)malloc(sizeof(double) * 4 * (size_t)n);
+    double* b = (double*)malloc(sizeof(double) * 4 * (size_t)n);
+    double* mom2 = (double*)malloc(sizeof(double) * 4 * (size_t)n);
+    int32_t* hist2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    orc_svgf_temporal(W, H, zn, mesh, zn_prev, mesh_prev, cam, cam_prev, mask, ao, P,
+                      col_hist, mom, hist, mom2, hist2, a, NULL);
+    memcpy(mom, mom2, sizeof(double) * 4 * (size_t)n);
+    memcpy(hist, hist2, sizeof(int32_t) * (size_t)n);
+    if (illum_out) memcpy(illum_out, a, sizeof(double) * 4 * (size_t)n);
+    if (P->levels == 0)
+        for (int64_t p = 0; p < n; ++p) { col_hist[2 * p] = a[4 * p]; col_hist[2 * p + 1] = a[4 * p + 1]; }
+    for (int l = 0; l < P->levels; ++l) {
+        orc_svgf_atrous(W, H, zn, a, 1 << l, P, b);
+        if (l == 0)
+            for (int64_t p = 0; p < n; ++p) { col_hist[2 * p] = b[4 * p]; col_hist[2 * p + 1] = b[4 * p + 1]; }
+        if (levels_out) memcpy(levels_out + 4 * n * l, b, sizeof(double) * 4 * (size_t)n);
+        double* t = a; a = b; b = t;
+    }
+    for (int64_t p = 0; p < n; ++p) { ao_out[p] = a[4 * p]; sh_out[p] = a[4 * p + 1]; }
+    free(a); free(b); free(mom2); free(hist2);
+}
