@@ -1,0 +1,362 @@
+"""Benchmark of the DHR+S server hot path on one B300 (or N replicas).
+
+One step = one frame of the hot path through dhr_step_frame: LBVH traversal
+of the primary G-buffer rays, one cone-jittered shadow ray and one
+cosine-weighted AO ray per foreground pixel, then the modified SVGF
+(temporal accumulation + variance + 5 a-trous levels) at 1920x1080 on the
+776,050-triangle terrain scene, frames taken from the 60-frame seeded camera
+spline.  The scene and BVH are built once before timing (static scene).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (brute
+force, fp64) on a bounded pixel sample per step on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s; ms/frame (trace+SVGF) at 1080p; p99 frame latency at 32 clients"
+W, H = 1920, 1080
+N_FRAMES = 60
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = "terrain776k_1080p_spline60"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _csrc_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2406_06963_b300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("csrc_sha") != _csrc_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2406_06963_b300 as dhrs
+    import workloads as wl
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    scene_d = wl.scene_terrain()
+    cams = wl.spline_path(scene_d["terrain"], N_FRAMES, W, H)
+    stream = torch.cuda.current_stream()
+    sc = dhrs.Scene(scene_d)
+    info = sc.info()
+    tp = dhrs.TraceParams(ao_spp=1)
+    sp = dhrs.SvgfParams(ao_spp=1, levels=5, alpha=0.2)
+    sess = dhrs.Session(sc, W, H, dhrs.DHR_FP32, tp, sp)
+    ao_out = torch.empty((H, W), device="cuda")
+    sh_out = torch.empty((H, W), device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    K, Wm = args.steps, args.warmup
+    for i in range(Wm):
+        sess.step(cams[i % N_FRAMES], i, ao_out, sh_out)
+    torch.cuda.synchronize()
+
+    # timed region: K frames; L2 flushed before each frame (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(K):
+        f = (Wm + i) % N_FRAMES
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        sess.step(cams[f], Wm + i, ao_out, sh_out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t_wall = time.perf_counter() - t_wall
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = _max_over_ranks(ws, sum(ms))
+
+    # stage split: the same frames through the two component calls
+    g = dhrs.GBuffer(W, H)
+    gp = dhrs.GBuffer(W, H)
+    mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    aoc = torch.empty_like(mask)
+    st = dhrs.SvgfState(W, H)
+    tr_ms, sv_ms = [], []
+    prev_cam = None
+    for i in range(K):
+        f = (Wm + i) % N_FRAMES
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        flush.fill_(float(i))
+        e0.record(stream)
+        dhrs.trace_visibility(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=Wm + i), g, mask, aoc)
+        e1.record(stream)
+        st.reconstruct(g, gp if prev_cam is not None else None, cams[f], prev_cam, mask, aoc, sp, ao_out, sh_out)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        tr_ms.append(e0.elapsed_time(e1))
+        sv_ms.append(e1.elapsed_time(e2))
+        g, gp = gp, g
+        prev_cam = cams[f]
+    clk = clocks.stop()
+
+    # end to end through the host-output entry point (camera in, filtered AO and
+    # shadow out to pinned host memory every step)
+    ah = torch.empty((H, W), pin_memory=True)
+    shh = torch.empty((H, W), pin_memory=True)
+    sess2 = dhrs.Session(sc, W, H, dhrs.DHR_FP32, tp, sp)
+    for i in range(Wm):
+        sess2.step_host(cams[i % N_FRAMES], i, ah, shh)
+    _barrier(ws)
+    t0 = time.perf_counter()
+    for i in range(K):
+        sess2.step_host(cams[(Wm + i) % N_FRAMES], Wm + i, ah, shh)
+    e2e_s = _max_over_ranks(ws, time.perf_counter() - t0)
+
+    # rays and traversal work of every frame of the path (counting variant of
+    # the trace kernel, run after the timed regions)
+    stats = [dhrs.trace_stats(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=f)) for f in range(N_FRAMES)]
+    rays = [sum(s["rays"]) for s in stats]
+    sec_rays = [s["rays"][1] + s["rays"][2] for s in stats]
+    step_rays = sum(rays[(Wm + i) % N_FRAMES] for i in range(K))
+    step_sec = sum(sec_rays[(Wm + i) % N_FRAMES] for i in range(K))
+    value = ws * step_rays / (total_ms * 1e-3) / 1e6
+    e2e_value = ws * step_rays / e2e_s / 1e6
+
+    peaks, peak_src = _peaks()
+    trace_ms = statistics.mean(tr_ms)
+    svgf_ms = statistics.mean(sv_ms)
+    # dominant kernel: trace.  Algorithmic ALU work per frame from the
+    # counters: 2 slab tests (12 FMA + 12 min/max) per node visit and one
+    # watertight test (~24 FMA/FMUL + 12 other) per triangle test.
+    sub = [(Wm + i) % N_FRAMES for i in range(K)]
+    visits = statistics.mean(sum(stats[f]["visits"]) for f in sub)
+    tests = statistics.mean(sum(stats[f]["tests"]) for f in sub)
+    ops = visits * 36 + tests * 48
+    alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # lane-ops/s, Tops
+    achieved = ops / (trace_ms * 1e-3) / 1e12
+    svgf_bytes = W * H * 340
+    svgf_gbs = svgf_bytes / (svgf_ms * 1e-3) / 1e9
+    res = {
+        "metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": ws, "steps": K,
+        "warmup": Wm, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "resolution": [W, H], "triangles": info["n_triangles"],
+                   "frames_in_path": N_FRAMES, "spp": {"shadow": 1, "ao": 1}, "svgf_levels": 5,
+                   "alpha": 0.2, "parallelism": f"replicas{ws}",
+                   "l2": "flushed (256 MB write) before every timed frame, outside the events"},
+        "ms_per_frame": {"trace_svgf": round(total_ms / K, 4), "trace": round(trace_ms, 4),
+                         "svgf": round(svgf_ms, 4)},
+        "secondary_mrays_s": round(ws * step_sec / (total_ms * 1e-3) / 1e6, 2),
+        "rays_per_frame": round(step_rays / K),
+        "bvh": {"height": info["height"], "build_ms": round(info["build_ms"], 3),
+                "visits_per_ray": round(visits / (step_rays / K), 2),
+                "tests_per_ray": round(tests / (step_rays / K), 2)},
+        "roofline": {"kernel": "trace_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(alu_peak, 2), "unit": "Tops/s (fp32 lane ops)",
+                     "frac": round(achieved / alu_peak, 4), "traffic": _traffic("trace_kernel"),
+                     "peak_source": "148 SMs x 128 fp32 lanes x max SM clock (%s)" % peak_src},
+        "roofline_svgf": {"bound": "hbm", "achieved": round(svgf_gbs, 1), "peak": peaks["hbm_gbs"],
+                          "unit": "GB/s", "frac": round(svgf_gbs / peaks["hbm_gbs"], 4),
+                          "algorithmic_bytes_per_px": 340, "peak_source": peak_src},
+        "e2e": {"value": round(e2e_value, 2), "unit": "Mrays/s", "h2d_bytes_per_step": 60,
+                "d2h_bytes_per_step": 2 * 4 * W * H,
+                "ms_per_step": round(e2e_s * 1e3 / K, 4)},
+        "gpu_launches": 7 * K,
+        "clocks": clk,
+        "wall_s_timed_region": round(t_wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(scene_d, cams, sample_px=args.cpu_pixels)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return res if rank == 0 else None
+
+
+def cpu_baseline(scene_d, cams, sample_px=1024, seed=7):
+    """The oracle as it stands (brute force over all triangles, fp64, OpenMP
+    on every host core) on a bounded sample of the same workload."""
+    import numpy as np
+
+    import oracle as orc
+    S = orc.Scene(scene_d)
+    r = np.random.default_rng(seed)
+    pix = np.stack([r.integers(0, W, sample_px), r.integers(0, H, sample_px)], -1)
+    t0 = time.perf_counter()
+    tr = orc.trace(S, cams[0], orc.TraceParams(frame=0), pixels=pix)
+    dt = time.perf_counter() - t0
+    fg = int((tr["mesh"] != 0xFFFFFFFF).sum())
+    n_rays = sample_px + 2 * fg
+    return {"value": round(n_rays / dt / 1e6, 6), "unit": "Mrays/s", "cores": orc.num_threads(),
+            "kind": "oracle",
+            "sample": f"{sample_px} seeded pixels of frame 0 (primary + shadow + AO rays, "
+                      f"{n_rays} rays, {dt:.1f} s) of the 1920x1080 776,050-triangle workload"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed per step on a bounded pixel sample
+    (the same metric and workload as ours)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle as orc
+    import workloads as wl
+    scene_d = wl.scene_terrain()
+    cams = wl.spline_path(scene_d["terrain"], N_FRAMES, W, H)
+    S = orc.Scene(scene_d)
+    r = np.random.default_rng(11)
+    per_step = args.ref_pixels
+
+    def step(i):
+        pix = np.stack([r.integers(0, W, per_step), r.integers(0, H, per_step)], -1)
+        tr = orc.trace(S, cams[i % N_FRAMES], orc.TraceParams(frame=i), pixels=pix)
+        return per_step + 2 * int((tr["mesh"] != 0xFFFFFFFF).sum())
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    n = sum(step(args.warmup + i) for i in range(args.steps))
+    dt = time.perf_counter() - t0
+    v = n / dt / 1e6
+    sample = f"{per_step} seeded pixels per step (primary + shadow + AO rays) of the 1920x1080 " \
+             f"776,050-triangle workload"
+    return {"metric": METRIC, "value": round(v, 6), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "resolution": [W, H], "triangles": 776050},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(v, 6), "unit": "Mrays/s", "cores": orc.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-pixels", type=int, default=1024)
+    ap.add_argument("--ref-pixels", type=int, default=24)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    res = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * dhrs.h -- C ABI of libdhrs: the server-side hot path of DHR+S (distributed
+ * hybrid rendering with soft shadows and ambient occlusion) on one NVIDIA
+ * B300 (sm_103a).
+ *
+ * Per frame the server receives a camera (Section 4.1: the client sends its
+ * camera data), traces per-pixel visibility -- one cone-jittered shadow ray
+ * per light (Section 3.1, Fig. 1) and N cosine-weighted ambient-occlusion
+ * rays of length r (Section 3.2, Eqs. 1-3) -- from a G-buffer produced by
+ * primary rays (standing in for the client rasteriser of Section 1), and
+ * reconstructs the noisy result with the modified SVGF of Section 3.3.
+ * Outputs per pixel: a visibility bitmask with one bit per light (Fig. 1)
+ * and the 8-bit count N_unoccluded (Section 3.2), or their filtered form.
+ *
+ * Conventions
+ *  - Every call returns dhr_status; nothing throws across the ABI.  On
+ *    failure dhr_last_error() returns a thread-local message.
+ *  - "device" pointers are CUDA global-memory pointers of the current
+ *    device; "host" pointers are CPU memory.  Per-frame inputs and outputs
+ *    are owned by the caller; scenes, SVGF history and sessions are owned by
+ *    the library and freed by their destroy call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Kernels
+ *    are enqueued asynchronously on it; a launch error is reported by the
+ *    call that enqueued it, an execution error by the next synchronising
+ *    call (DHR_ERR_CUDA).
+ *  - Images are row-major, row 0 at the top, W*H pixels.  A pixel is
+ *    background when its primary ray misses: depth +inf, mesh id
+ *    DHR_BACKGROUND.
+ */
+#ifndef DHRS_H
+#define DHRS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DHR_OK = 0,
+    DHR_ERR_INVALID = 1,    /* bad argument (size, range, null pointer)      */
+    DHR_ERR_OOM = 2,        /* device or host allocation failed             */
+    DHR_ERR_CUDA = 3,       /* a CUDA runtime call or kernel failed         */
+    DHR_ERR_TIMEOUT = 4,    /* a bounded wait gave up                       */
+    DHR_ERR_ADMISSION = 5,  /* serving: session refused (memory budget)     */
+    DHR_ERR_STATE = 6       /* call not valid in the object's current state */
+} dhr_status;
+
+typedef enum { DHR_FP32 = 0, DHR_FP16 = 1 } dhr_precision;
+
+#define DHR_MAX_LIGHTS 8
+#define DHR_BACKGROUND 0xFFFFFFFFu
+
+/* Pinhole camera with an orthonormal basis.  The ray of pixel (x, y) has
+ * direction forward + sx right + sy up with
+ *   sx = (2 (x + 0.5) / W - 1) tan_half_fov_y W / H,
+ *   sy = (1 - 2 (y + 0.5) / H) tan_half_fov_y. */
+typedef struct {
+    float pos[3];
+    float forward[3];
+    float right[3];
+    float up[3];
+    float tan_half_fov_y;
+    int32_t width;
+    int32_t height;
+} dhr_camera;
+
+/* Triangle soup, host memory; read during dhr_create_scene only. */
+typedef struct {
+    const float* vertices;     /* [n_vertices][3] */
+    const uint32_t* indices;   /* [n_triangles][3], each < n_vertices */
+    const uint32_t* mesh_ids;  /* [n_triangles]; NULL = all 0 */
+    uint32_t n_vertices;
+    uint32_t n_triangles;
+} dhr_scene_desc;
+
+typedef struct dhr_scene dhr_scene;
+
+typedef struct {
+    uint32_t n_triangles;
+    uint32_t n_nodes;          /* internal BVH nodes */
+    uint32_t height;           /* longest root-to-leaf path (edges) */
+    uint64_t device_bytes;     /* scene + BVH memory held on the device */
+    float build_ms;            /* device time of the LBVH build */
+} dhr_scene_info;
+
+/* Visibility tracing parameters (Sections 3.1, 3.2). */
+typedef struct {
+    uint32_t n_lights;                      /* 1..DHR_MAX_LIGHTS directional lights */
+    float light_dir[DHR_MAX_LIGHTS][3];     /* unit vector toward light k */
+    float cone_half_angle[DHR_MAX_LIGHTS];  /* radians in [0, pi/2); 0 = hard shadow */
+    float ao_radius;                        /* r > 0: a hit at t < r occludes */
+    uint32_t ao_spp;                        /* N in 1..255 (8-bit count, Section 3.2) */
+    uint32_t frame;                         /* hash input: frame index */
+    uint32_t seed;                          /* hash input: xored into the frame */
+} dhr_trace_params;
+
+/* G-buffer (caller-owned device memory, W*H pixels).
+ *  FP32: depth_normal = float4 per pixel (linear view depth, unit normal x,
+ *        y, z facing the camera);
+ *  FP16: depth_normal = 4 x binary16 per pixel, same fields.
+ *  mesh_id = uint32 per pixel (DHR_BACKGROUND on a miss).
+ *  Both pointers must be 16-byte aligned. */
+typedef struct {
+    dhr_precision precision;
+    int32_t width;
+    int32_t height;
+    void* depth_normal;
+    uint32_t* mesh_id;
+} dhr_gbuffer;
+
+/* Modified SVGF parameters (Section 3.3). */
+typedef struct {
+    float alpha;          /* temporal blend (0, 1]; effective max(alpha, 1/n) */
+    float sigma_z;        /* depth edge stopping */
+    float sigma_n;        /* normal edge stopping exponent (>= 0) */
+    float sigma_l;        /* luminance edge stopping */
+    float eps_z;
+    float eps_l;
+    uint32_t ao_spp;      /* N used to turn the AO count into [0, 1] */
+    uint32_t levels;      /* a-trous iterations, 0..8 (step 2^i) */
+    uint32_t fixed_alpha; /* 1: effective alpha = alpha once history exists */
+    uint32_t wl_in_atrous;/* 1: luminance term in the a-trous weights */
+} dhr_svgf_params;
+
+typedef struct dhr_svgf_state dhr_svgf_state;
+
+/* Device views of an SVGF state's buffers (owned by the state). */
+typedef struct {
+    void* illum;        /* FP32: float4 [W*H] temporal colour AO, shadow, variance AO, shadow */
+    void* moments;      /* FP32: float4 [W*H] mu1 AO, mu1 shadow, mu2 AO, mu2 shadow (current) */
+    void* color_hist;   /* FP32: float2 [W*H] colour history for the next frame */
+    uint8_t* histlen;   /* [W*H] history length n (current) */
+} dhr_svgf_buffers;
+
+typedef struct dhr_session dhr_session;
+
+/* ---------------------------------------------------------------------- */
+/* Errors                                                                  */
+/* ---------------------------------------------------------------------- */
+/* Message of the last failing call on this thread ("" if none). */
+const char* dhr_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Scene and BVH (Section 3.2: scene objects grouped hierarchically into   */
+/* bounding volumes).  Builds an LBVH over 63-bit Morton codes of the      */
+/* triangle centroids on the device.                                        */
+/* ---------------------------------------------------------------------- */
+/* Copies the soup to the device, builds the BVH on `stream`, synchronises.
+ * Errors: DHR_ERR_INVALID (null desc, index out of range, more than 2^31
+ * triangles), DHR_ERR_OOM, DHR_ERR_CUDA. */
+dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream, dhr_scene** out);
+void dhr_destroy_scene(dhr_scene* scene);
+dhr_status dhr_scene_get_info(const dhr_scene* scene, dhr_scene_info* out);
+
+/* ---------------------------------------------------------------------- */
+/* Visibility tracing                                                      */
+/* ---------------------------------------------------------------------- */
+/* Primary G-buffer + shadow bitmask + AO count for every pixel of `cam`.
+ *  gbuf_out: caller device buffers sized cam->width x cam->height (its
+ *            width/height must match the camera; FP32 or FP16).
+ *  shadow_mask_out (device, W*H bytes): bit k = light k unoccluded;
+ *            0 where the jittered direction points below the surface;
+ *            all light bits set on background.
+ *  ao_count_out (device, W*H bytes): N_unoccluded in 0..ao_spp (Eq. 3);
+ *            ao_spp on background.
+ * Errors: DHR_ERR_INVALID (sizes, ao_spp outside 1..255, n_lights outside
+ * 1..8, cone angle outside [0, pi/2), ao_radius <= 0, null pointers),
+ * DHR_ERR_CUDA. */
+dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_camera* cam,
+                                const dhr_trace_params* params, dhr_gbuffer* gbuf_out,
+                                uint8_t* shadow_mask_out, uint8_t* ao_count_out, void* stream);
+
+/* Generic ray casting through the scene's BVH (device arrays of n rays).
+ *  origins, dirs: float [n][3]; tmin, tmax: float [n]; a hit needs
+ *  tmin < t < tmax.  any_hit = 1: occlusion query (t_out = some hit
+ *  distance).  t_out: float [n] (+inf on miss); tri_out: int32 [n]
+ *  (scene triangle index or -1). */
+dhr_status dhr_cast_rays(const dhr_scene* scene, const float* origins, const float* dirs,
+                         const float* tmin, const float* tmax, int32_t any_hit, int64_t n,
+                         float* t_out, int32_t* tri_out, void* stream);
+
+/* Traversal work counters of one dhr_trace_visibility frame (runs a
+ * counting variant of the trace kernel into scratch buffers it allocates;
+ * synchronises `stream`).  counters (host, 9 values): rays traced
+ * {primary, shadow, AO}, internal BVH nodes visited {primary, shadow, AO},
+ * triangles tested {primary, shadow, AO}.  Errors as dhr_trace_visibility. */
+dhr_status dhr_trace_stats(const dhr_scene* scene, const dhr_camera* cam,
+                           const dhr_trace_params* params, uint64_t* counters, void* stream);
+
+/* Sampling check entry: for each of n (px, py) and the given frame, seed
+ * and sample index, the accepted disk point and the binary32 AO direction
+ * about normals[i] (ray type 1) and the shadow direction about `light`
+ * with cone half angle `cone_half_angle` (ray type 0) -- the same device
+ * functions the trace kernel uses.  All arrays are device memory:
+ * px, py uint32 [n]; normals float [n][3]; light float [3];
+ * disk_* float [n][2]; dir_* float [n][3]. */
+dhr_status dhr_sample_directions(const uint32_t* px, const uint32_t* py, int64_t n,
+                                 uint32_t frame, uint32_t seed, uint32_t sample,
+                                 const float* normals, const float* light, float cone_half_angle,
+                                 float* disk_ao, float* dir_ao, float* disk_sh, float* dir_sh,
+                                 void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Modified SVGF (Section 3.3)                                             */
+/* ---------------------------------------------------------------------- */
+/* History (colour, moments, history length) for one W x H stream of frames. */
+dhr_status dhr_svgf_create(int32_t width, int32_t height, dhr_precision precision,
+                           dhr_svgf_state** out);
+void dhr_svgf_destroy(dhr_svgf_state* state);
+dhr_status dhr_svgf_get_buffers(dhr_svgf_state* state, dhr_svgf_buffers* out);
+
+/* One frame: temporal reprojection + accumulation + variance, then
+ * `levels` edge-stopping a-trous iterations.
+ *  cur, prev: G-buffers of this and the previous frame (prev = NULL: no
+ *  history, e.g. the first frame or a reset); both in the state's
+ *  precision and size.  cam, cam_prev: their cameras (cam_prev unused when
+ *  prev is NULL).  shadow_mask, ao_count: device bytes [W*H] (bit 0 of the
+ *  mask is filtered).  ao_out, shadow_out: device float [W*H] (filtered
+ *  AO in [0, 1] and filtered light-0 visibility; 1 on background).
+ * Errors: DHR_ERR_INVALID (sizes, precision mismatch, levels > 8,
+ * ao_spp outside 1..255, null pointers), DHR_ERR_CUDA. */
+dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur,
+                                const dhr_gbuffer* prev, const dhr_camera* cam,
+                                const dhr_camera* cam_prev, const uint8_t* shadow_mask,
+                                const uint8_t* ao_count, const dhr_svgf_params* params,
+                                float* ao_out, float* shadow_out, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Session: trace + SVGF per frame with library-owned G-buffer ping-pong   */
+/* ---------------------------------------------------------------------- */
+dhr_status dhr_session_create(const dhr_scene* scene, int32_t width, int32_t height,
+                              dhr_precision precision, const dhr_trace_params* trace,
+                              const dhr_svgf_params* svgf, dhr_session** out);
+void dhr_session_destroy(dhr_session* session);
+
+/* Trace + reconstruct one frame seen by `cam` (frame index `frame` feeds
+ * the hash).  ao_out, shadow_out: device float [W*H] or NULL (results stay
+ * in the session).  Asynchronous on `stream`. */
+dhr_status dhr_step_frame(dhr_session* session, const dhr_camera* cam, uint32_t frame,
+                          float* ao_out, float* shadow_out, void* stream);
+
+/* Same, writing the filtered AO and shadow into HOST memory (pinned memory
+ * gives the fastest copy); returns after the results are in host memory. */
+dhr_status dhr_step_frame_host(dhr_session* session, const dhr_camera* cam, uint32_t frame,
+                               float* ao_host, float* shadow_host, void* stream);
+
+/* Device views of the session's current G-buffer and raw trace outputs. */
+dhr_status dhr_session_get_frame(dhr_session* session, dhr_gbuffer* gbuf,
+                                 uint8_t** shadow_mask, uint8_t** ao_count);
+
+/* Drops the SVGF history: the next frame starts without history. */
+dhr_status dhr_session_reset(dhr_session* session);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DHRS_H */

@@ -144,7 +144,7 @@ def tan_f32(angle_rad: float) -> float:
 # --------------------------------------------------------------------------
 # geometry
 # --------------------------------------------------------------------------
-DEFAULT_MARGIN = (3e-5, 6e-5)
+DEFAULT_MARGIN = (1e-6, 1e-6)
 
 
 class Scene:

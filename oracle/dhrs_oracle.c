@@ -458,6 +458,16 @@ static void camera_ray(const orc_camera* c, int x, int y, double o[3], double D[
     }
 }
 
+/* 16 units in the last place of a binary32 value of magnitude m (m taken
+ * as at least 2^-20): 16 * 2^(floor(log2 m) - 23), an exact power of two. */
+static double surface_offset(double m)
+{
+    int ex;
+    if (m < 0x1p-20) m = 0x1p-20;
+    frexp(m, &ex);                   /* m = f 2^ex, f in [0.5, 1) */
+    return ldexp(16.0, ex - 1 - 23);
+}
+
 /*
  * Trace pixels: G-buffer (closest hit of the pixel-centre ray), one
  * cone-jittered shadow ray per light, ao_spp cosine-weighted AO rays of
@@ -471,7 +481,8 @@ static void camera_ray(const orc_camera* c, int x, int y, double o[3], double D[
  * (ao_spp on a miss).  Ambiguity
  * outputs: amb_primary, amb_shadow (bit per light), amb_ao (count of AO
  * rays whose outcome is within the margin).
- * Secondary rays start at X and accept hits with t > 1e-9 (1 + |X|_inf).
+ * Secondary rays start at X moved along n by 16 binary32 ulps of the hit
+ * triangle's largest vertex coordinate and accept hits with t > 0.
  */
 void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params* tp,
                const orc_margin* mg, const int32_t* pixels /*[np][2] (x, y)*/, int64_t np,
@@ -511,7 +522,21 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
         for (int k = 0; k < 3; ++k) { normal[3 * i + k] = n[k]; pos[3 * i + k] = X[k]; }
         tri[i] = pr.tri;
         mesh[i] = s->mesh[pr.tri];
-        double tmin = 1e-9 * (1.0 + inf_norm3(X));
+        /* secondary rays start at X moved along n by 16 ulps (binary32) of
+         * the largest vertex coordinate of the hit triangle; t > 0 */
+        double O[3];
+        {
+            double m = 0.0;
+            const double *v0 = s->v0 + 3 * pr.tri, *e1 = s->e1 + 3 * pr.tri, *e2 = s->e2 + 3 * pr.tri;
+            for (int k = 0; k < 3; ++k) {
+                m = fmax(m, fabs(v0[k]));
+                m = fmax(m, fabs(v0[k] + e1[k]));
+                m = fmax(m, fabs(v0[k] + e2[k]));
+            }
+            double delta = surface_offset(m);
+            for (int k = 0; k < 3; ++k) O[k] = X[k] + delta * n[k];
+        }
+        double tmin = 0.0;
         /* shadow rays, one per light */
         uint8_t m = 0, am = 0;
         for (int k = 0; k < tp->n_lights; ++k) {
@@ -524,7 +549,7 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
             double facing = dot3(d, n);
             if (fabs(facing) < 1e-6) am |= (uint8_t)(1u << k);
             if (facing <= 0.0) continue;
-            cast_result sr = cast_any(s, X, d, tmin, INFINITY, mg);
+            cast_result sr = cast_any(s, O, d, tmin, INFINITY, mg);
             if (!sr.hit) m |= (uint8_t)(1u << k);
             if (sr.ambiguous) am |= (uint8_t)(1u << k);
         }
@@ -537,7 +562,7 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
             orc_disk_point((uint32_t)x, (uint32_t)y, tp->frame, tp->seed, 1u, (uint32_t)j, xy);
             double d[3];
             ao_dir_f64(n, xy[0], xy[1], d);
-            cast_result ar = cast_any(s, X, d, tmin, (double)tp->ao_radius, mg);
+            cast_result ar = cast_any(s, O, d, tmin, (double)tp->ao_radius, mg);
             if (!ar.hit) ++cnt;
             if (ar.ambiguous) ++amb;
         }

@@ -1,0 +1,397 @@
+"""Python binding of libdhrs (ctypes): argument marshalling only.
+
+Every step of the DHR+S server hot path -- LBVH build, primary/shadow/AO
+tracing, modified SVGF -- runs in the CUDA library ``libdhrs.so`` built
+in-tree from ``csrc/`` for sm_103a.  PyTorch supplies device memory and
+streams.  There is no fallback: if the library is missing or no CUDA
+device is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdhrs.so")
+
+DHR_FP32, DHR_FP16 = 0, 1
+BACKGROUND = 0xFFFFFFFF
+MAX_LIGHTS = 8
+STATUS = {0: "DHR_OK", 1: "DHR_ERR_INVALID", 2: "DHR_ERR_OOM", 3: "DHR_ERR_CUDA",
+          4: "DHR_ERR_TIMEOUT", 5: "DHR_ERR_ADMISSION", 6: "DHR_ERR_STATE"}
+
+
+class DhrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("forward", C.c_float * 3), ("right", C.c_float * 3),
+                ("up", C.c_float * 3), ("tan_half_fov_y", C.c_float), ("width", C.c_int32),
+                ("height", C.c_int32)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("vertices", C.c_void_p), ("indices", C.c_void_p), ("mesh_ids", C.c_void_p),
+                ("n_vertices", C.c_uint32), ("n_triangles", C.c_uint32)]
+
+
+class SceneInfo(C.Structure):
+    _fields_ = [("n_triangles", C.c_uint32), ("n_nodes", C.c_uint32), ("height", C.c_uint32),
+                ("device_bytes", C.c_uint64), ("build_ms", C.c_float)]
+
+
+class TraceParamsC(C.Structure):
+    _fields_ = [("n_lights", C.c_uint32), ("light_dir", (C.c_float * 3) * MAX_LIGHTS),
+                ("cone_half_angle", C.c_float * MAX_LIGHTS), ("ao_radius", C.c_float),
+                ("ao_spp", C.c_uint32), ("frame", C.c_uint32), ("seed", C.c_uint32)]
+
+
+class GBufferC(C.Structure):
+    _fields_ = [("precision", C.c_int), ("width", C.c_int32), ("height", C.c_int32),
+                ("depth_normal", C.c_void_p), ("mesh_id", C.c_void_p)]
+
+
+class SvgfParamsC(C.Structure):
+    _fields_ = [("alpha", C.c_float), ("sigma_z", C.c_float), ("sigma_n", C.c_float),
+                ("sigma_l", C.c_float), ("eps_z", C.c_float), ("eps_l", C.c_float),
+                ("ao_spp", C.c_uint32), ("levels", C.c_uint32), ("fixed_alpha", C.c_uint32),
+                ("wl_in_atrous", C.c_uint32)]
+
+
+class SvgfBuffersC(C.Structure):
+    _fields_ = [("illum", C.c_void_p), ("moments", C.c_void_p), ("color_hist", C.c_void_p),
+                ("histlen", C.c_void_p)]
+
+
+_P = C.c_void_p
+_SIGNATURES = {
+    "dhr_last_error": ([], C.c_char_p),
+    "dhr_create_scene": ([_P, _P, _P], C.c_int),
+    "dhr_destroy_scene": ([_P], None),
+    "dhr_scene_get_info": ([_P, _P], C.c_int),
+    "dhr_trace_visibility": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_cast_rays": ([_P, _P, _P, _P, _P, C.c_int32, C.c_int64, _P, _P, _P], C.c_int),
+    "dhr_trace_stats": ([_P, _P, _P, _P, _P], C.c_int),
+    "dhr_sample_directions": ([_P, _P, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32, _P, _P,
+                               C.c_float, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_svgf_create": ([C.c_int32, C.c_int32, C.c_int, _P], C.c_int),
+    "dhr_svgf_destroy": ([_P], None),
+    "dhr_svgf_get_buffers": ([_P, _P], C.c_int),
+    "dhr_svgf_reconstruct": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_session_create": ([_P, C.c_int32, C.c_int32, C.c_int, _P, _P, _P], C.c_int),
+    "dhr_session_destroy": ([_P], None),
+    "dhr_step_frame": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
+    "dhr_step_frame_host": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
+    "dhr_session_get_frame": ([_P, _P, _P, _P], C.c_int),
+    "dhr_session_reset": ([_P], C.c_int),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libdhrs.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdhrs.so not built ({LIB_PATH}); run "
+                               "`python -m paper_2406_06963_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise DhrError(status, lib().dhr_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(*tensors):
+    for t in tensors:
+        if t is not None and not t.is_cuda:
+            raise ValueError("libdhrs expects CUDA tensors")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("libdhrs expects contiguous tensors")
+
+
+# --------------------------------------------------------------- structs
+def camera(cam) -> Camera:
+    """workloads.Camera (or any object with the same fields) -> dhr_camera."""
+    c = Camera()
+    c.pos[:] = [float(x) for x in cam.pos]
+    c.forward[:] = [float(x) for x in cam.forward]
+    c.right[:] = [float(x) for x in cam.right]
+    c.up[:] = [float(x) for x in cam.up]
+    c.tan_half_fov_y = float(cam.tan_half_fov_y)
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    return c
+
+
+@dataclass
+class TraceParams:
+    light_dirs: list = field(default_factory=lambda: [(0.3, 1.0, 0.2)])
+    cone_half_angle_deg: list = field(default_factory=lambda: [0.5])
+    ao_radius: float = 1.0
+    ao_spp: int = 1
+    frame: int = 0
+    seed: int = 0
+
+    def to_c(self) -> TraceParamsC:
+        p = TraceParamsC()
+        p.n_lights = len(self.light_dirs)
+        for k, l in enumerate(self.light_dirs):
+            l = np.asarray(l, np.float64)
+            p.light_dir[k][:] = [float(x) for x in (l / np.linalg.norm(l)).astype(np.float32)]
+            p.cone_half_angle[k] = math.radians(self.cone_half_angle_deg[k])
+        p.ao_radius = self.ao_radius
+        p.ao_spp = self.ao_spp
+        p.frame = self.frame
+        p.seed = self.seed
+        return p
+
+
+@dataclass
+class SvgfParams:
+    alpha: float = 0.2
+    sigma_z: float = 1.0
+    sigma_n: float = 128.0
+    sigma_l: float = 4.0
+    eps_z: float = 1e-6
+    eps_l: float = 1e-10
+    ao_spp: int = 1
+    levels: int = 5
+    fixed_alpha: bool = False
+    wl_in_atrous: bool = True
+
+    def to_c(self) -> SvgfParamsC:
+        return SvgfParamsC(self.alpha, self.sigma_z, self.sigma_n, self.sigma_l, self.eps_z,
+                           self.eps_l, self.ao_spp, self.levels, int(self.fixed_alpha),
+                           int(self.wl_in_atrous))
+
+
+# --------------------------------------------------------------- G-buffer
+class GBuffer:
+    """Device G-buffer: depth_normal [H, W, 4] (float32 or float16) + mesh [H, W] int32
+    (bit pattern of the uint32 mesh id)."""
+
+    def __init__(self, width, height, precision=DHR_FP32, device="cuda"):
+        import torch
+        self.width, self.height, self.precision = width, height, precision
+        dt = torch.float16 if precision == DHR_FP16 else torch.float32
+        self.depth_normal = torch.empty((height, width, 4), dtype=dt, device=device)
+        self.mesh = torch.empty((height, width), dtype=torch.int32, device=device)
+
+    @classmethod
+    def from_arrays(cls, zn, mesh, precision=DHR_FP32, device="cuda"):
+        import torch
+        H, W = mesh.shape
+        g = cls(W, H, precision, device)
+        g.depth_normal.copy_(torch.from_numpy(np.ascontiguousarray(zn)).to(g.depth_normal.dtype))
+        g.mesh.copy_(torch.from_numpy(np.ascontiguousarray(mesh).view(np.int32)))
+        return g
+
+    def c(self) -> GBufferC:
+        return GBufferC(self.precision, self.width, self.height, self.depth_normal.data_ptr(),
+                        self.mesh.data_ptr())
+
+    def mesh_u32(self) -> np.ndarray:
+        return self.mesh.cpu().numpy().view(np.uint32)
+
+
+# --------------------------------------------------------------- scene
+class Scene:
+    """Device scene + LBVH built from a host triangle soup (workloads dict)."""
+
+    def __init__(self, scene: dict, stream=None):
+        v = np.ascontiguousarray(scene["vertices"], np.float32)
+        i = np.ascontiguousarray(scene["indices"], np.uint32)
+        m = np.ascontiguousarray(scene["mesh_ids"], np.uint32)
+        d = SceneDesc(v.ctypes.data, i.ctypes.data, m.ctypes.data, len(v), len(i))
+        h = C.c_void_p()
+        _check(lib().dhr_create_scene(C.byref(d), _stream(stream), C.byref(h)))
+        self.h = h
+
+    def info(self) -> dict:
+        s = SceneInfo()
+        _check(lib().dhr_scene_get_info(self.h, C.byref(s)))
+        return dict(n_triangles=s.n_triangles, n_nodes=s.n_nodes, height=s.height,
+                    device_bytes=s.device_bytes, build_ms=s.build_ms)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dhr_destroy_scene(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace_visibility(scene: Scene, cam, params: TraceParams, gbuf: GBuffer, mask, ao, stream=None):
+    _need_cuda(gbuf.depth_normal, gbuf.mesh, mask, ao)
+    c = camera(cam)
+    p = params.to_c()
+    g = gbuf.c()
+    _check(lib().dhr_trace_visibility(scene.h, C.byref(c), C.byref(p), C.byref(g), _ptr(mask),
+                                      _ptr(ao), _stream(stream)))
+
+
+def trace_stats(scene: Scene, cam, params: TraceParams, stream=None) -> dict:
+    """Rays, BVH node visits and triangle tests of one frame, per ray type."""
+    c = camera(cam)
+    p = params.to_c()
+    out = (C.c_uint64 * 9)()
+    _check(lib().dhr_trace_stats(scene.h, C.byref(c), C.byref(p), out, _stream(stream)))
+    v = list(out)
+    return dict(rays=v[0:3], visits=v[3:6], tests=v[6:9])
+
+
+def cast_rays(scene: Scene, origins, dirs, tmin, tmax, any_hit=False, stream=None):
+    import torch
+    _need_cuda(origins, dirs, tmin, tmax)
+    n = origins.shape[0]
+    t = torch.empty(n, dtype=torch.float32, device=origins.device)
+    tri = torch.empty(n, dtype=torch.int32, device=origins.device)
+    _check(lib().dhr_cast_rays(scene.h, _ptr(origins), _ptr(dirs), _ptr(tmin), _ptr(tmax),
+                               int(any_hit), n, _ptr(t), _ptr(tri), _stream(stream)))
+    return t, tri
+
+
+def sample_directions(px, py, frame, seed, sample, normals, light, cone_half_angle, stream=None):
+    import torch
+    _need_cuda(px, py, normals, light)
+    n = px.shape[0]
+    dev = px.device
+    out = dict(disk_ao=torch.empty((n, 2), device=dev), dir_ao=torch.empty((n, 3), device=dev),
+               disk_sh=torch.empty((n, 2), device=dev), dir_sh=torch.empty((n, 3), device=dev))
+    _check(lib().dhr_sample_directions(_ptr(px), _ptr(py), n, frame, seed, sample, _ptr(normals),
+                                       _ptr(light), float(cone_half_angle), _ptr(out["disk_ao"]),
+                                       _ptr(out["dir_ao"]), _ptr(out["disk_sh"]),
+                                       _ptr(out["dir_sh"]), _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------- SVGF
+class SvgfState:
+    def __init__(self, width, height, precision=DHR_FP32):
+        h = C.c_void_p()
+        _check(lib().dhr_svgf_create(width, height, precision, C.byref(h)))
+        self.h, self.width, self.height, self.precision = h, width, height, precision
+
+    def reconstruct(self, cur: GBuffer, prev, cam, cam_prev, mask, ao, params: SvgfParams,
+                    ao_out, sh_out, stream=None):
+        _need_cuda(mask, ao, ao_out, sh_out)
+        c, cp = camera(cam), (camera(cam_prev) if cam_prev is not None else None)
+        gc = cur.c()
+        gp = prev.c() if prev is not None else None
+        p = params.to_c()
+        _check(lib().dhr_svgf_reconstruct(self.h, C.byref(gc), C.byref(gp) if gp else None,
+                                          C.byref(c), C.byref(cp) if cp else None, _ptr(mask),
+                                          _ptr(ao), C.byref(p), _ptr(ao_out), _ptr(sh_out),
+                                          _stream(stream)))
+
+    def buffers(self) -> dict:
+        """Device pointers of the state's buffers (illum, moments, colour history, histlen)."""
+        b = SvgfBuffersC()
+        _check(lib().dhr_svgf_get_buffers(self.h, C.byref(b)))
+        return dict(illum=b.illum, moments=b.moments, color_hist=b.color_hist, histlen=b.histlen)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dhr_svgf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevArray:
+    """Minimal __cuda_array_interface__ wrapper of a raw device pointer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = dict(shape=tuple(shape), typestr=typestr, data=(int(ptr), False),
+                                             version=2, strides=None)
+
+
+_TYPESTR = {"float32": "<f4", "float16": "<f2", "uint8": "|u1", "int32": "<i4"}
+
+
+def device_copy(ptr: int, shape, dtype: str):
+    """Copy a library-owned device buffer into a new torch tensor."""
+    import torch
+    torch.cuda.synchronize()
+    return torch.as_tensor(_DevArray(ptr, shape, _TYPESTR[dtype]), device="cuda").clone()
+
+
+# --------------------------------------------------------------- session
+class Session:
+    """trace + SVGF per frame with library-owned buffers (dhr_step_frame)."""
+
+    def __init__(self, scene: Scene, width, height, precision=DHR_FP32, trace=None, svgf=None):
+        self.trace = trace or TraceParams()
+        self.svgf = svgf or SvgfParams(ao_spp=self.trace.ao_spp)
+        h = C.c_void_p()
+        tp, sp = self.trace.to_c(), self.svgf.to_c()
+        _check(lib().dhr_session_create(scene.h, width, height, precision, C.byref(tp), C.byref(sp),
+                                        C.byref(h)))
+        self.h, self.scene = h, scene
+        self.width, self.height, self.precision = width, height, precision
+
+    def step(self, cam, frame, ao_out=None, sh_out=None, stream=None):
+        _need_cuda(ao_out, sh_out)
+        c = camera(cam)
+        _check(lib().dhr_step_frame(self.h, C.byref(c), frame, _ptr(ao_out), _ptr(sh_out),
+                                    _stream(stream)))
+
+    def step_host(self, cam, frame, ao_host, sh_host, stream=None):
+        """Host-output step; ao_host/sh_host: CPU tensors (pinned for speed)."""
+        c = camera(cam)
+        _check(lib().dhr_step_frame_host(self.h, C.byref(c), frame, C.c_void_p(ao_host.data_ptr()),
+                                         C.c_void_p(sh_host.data_ptr()), _stream(stream)))
+
+    def frame_buffers(self) -> dict:
+        g = GBufferC()
+        m, a = C.c_void_p(), C.c_void_p()
+        _check(lib().dhr_session_get_frame(self.h, C.byref(g), C.byref(m), C.byref(a)))
+        return dict(depth_normal=g.depth_normal, mesh=g.mesh_id, mask=m.value, ao=a.value)
+
+    def reset(self):
+        _check(lib().dhr_session_reset(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dhr_session_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

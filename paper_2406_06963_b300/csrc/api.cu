@@ -1,0 +1,258 @@
+// C ABI of libdhrs: errors, scenes, tracing entry point and sessions.
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dhr {
+
+static thread_local std::string g_error;
+
+dhr_status set_error(dhr_status s, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return s;
+}
+
+void clear_error() { g_error.clear(); }
+
+dhr_status svgf_create(int32_t w, int32_t h, dhr_precision prec, dhr_svgf_state** out);
+void svgf_free(dhr_svgf_state* s);
+dhr_status svgf_run(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev, const dhr_camera* cam,
+                    const dhr_camera* cam_prev, const uint8_t* mask, const uint8_t* ao,
+                    const dhr_svgf_params* prm, float* ao_out, float* sh_out, cudaStream_t st);
+dhr_status check_svgf_params(const dhr_svgf_params* p);
+
+static dhr_status check_camera(const dhr_camera* c) {
+    DHR_CHECK_ARG(c, "camera: null");
+    DHR_CHECK_ARG(c->width > 0 && c->height > 0 && c->width <= 16384 && c->height <= 16384,
+                  "camera: bad size %dx%d", c->width, c->height);
+    DHR_CHECK_ARG(c->tan_half_fov_y > 0.0f, "camera: tan_half_fov_y must be > 0");
+    return DHR_OK;
+}
+
+static dhr_status check_gbuffer(const dhr_gbuffer* g, int w, int h) {
+    DHR_CHECK_ARG(g && g->depth_normal && g->mesh_id, "gbuffer: null pointer");
+    DHR_CHECK_ARG(g->width == w && g->height == h, "gbuffer: size %dx%d does not match %dx%d", g->width,
+                  g->height, w, h);
+    DHR_CHECK_ARG(g->precision == DHR_FP32 || g->precision == DHR_FP16, "gbuffer: bad precision");
+    DHR_CHECK_ARG(((uintptr_t)g->depth_normal & 15u) == 0, "gbuffer: depth_normal not 16-byte aligned");
+    return DHR_OK;
+}
+
+}  // namespace dhr
+
+using namespace dhr;
+
+extern "C" const char* dhr_last_error(void) { return g_error.c_str(); }
+
+// ------------------------------------------------------------------ scene
+extern "C" dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream, dhr_scene** out) {
+    clear_error();
+    DHR_CHECK_ARG(desc && out, "create_scene: null pointer");
+    *out = nullptr;
+    DHR_CHECK_ARG(desc->n_triangles == 0 || (desc->vertices && desc->indices),
+                  "create_scene: null vertex or index array");
+    DHR_CHECK_ARG(desc->n_triangles < (1u << 31), "create_scene: too many triangles");
+    cudaStream_t st = as_stream(stream);
+    auto* sc = new dhr_scene();
+    float* v = nullptr;
+    uint32_t* idx = nullptr;
+    uint32_t* mesh = nullptr;
+    dhr_status s = DHR_OK;
+    const size_t nv = desc->n_vertices, nt = desc->n_triangles;
+    if (nt > 0) {
+        cudaError_t e = cudaMalloc(&v, nv * 12 + 16);
+        if (!e) e = cudaMalloc(&idx, nt * 12 + 16);
+        if (!e && desc->mesh_ids) e = cudaMalloc(&mesh, nt * 4 + 16);
+        if (!e) e = cudaMemcpyAsync(v, desc->vertices, nv * 12, cudaMemcpyHostToDevice, st);
+        if (!e) e = cudaMemcpyAsync(idx, desc->indices, nt * 12, cudaMemcpyHostToDevice, st);
+        if (!e && mesh) e = cudaMemcpyAsync(mesh, desc->mesh_ids, nt * 4, cudaMemcpyHostToDevice, st);
+        if (e)
+            s = set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA, "create_scene: %s",
+                          cudaGetErrorString(e));
+        if (s == DHR_OK) s = build_lbvh(v, idx, mesh, desc->n_vertices, desc->n_triangles, st, sc);
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(v);
+    cudaFree(idx);
+    cudaFree(mesh);
+    if (s != DHR_OK) {
+        dhr_destroy_scene(sc);
+        return s;
+    }
+    *out = sc;
+    return DHR_OK;
+}
+
+extern "C" void dhr_destroy_scene(dhr_scene* sc) {
+    if (!sc) return;
+    cudaFree(sc->nodes);
+    cudaFree(sc->tris);
+    delete sc;
+}
+
+extern "C" dhr_status dhr_scene_get_info(const dhr_scene* sc, dhr_scene_info* out) {
+    clear_error();
+    DHR_CHECK_ARG(sc && out, "scene_get_info: null pointer");
+    out->n_triangles = sc->n_tris;
+    out->n_nodes = sc->n_nodes;
+    out->height = sc->height;
+    out->device_bytes = sc->bytes;
+    out->build_ms = sc->build_ms;
+    return DHR_OK;
+}
+
+// ------------------------------------------------------------------ trace
+extern "C" dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_camera* cam,
+                                           const dhr_trace_params* params, dhr_gbuffer* gbuf_out,
+                                           uint8_t* shadow_mask_out, uint8_t* ao_count_out, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(scene, "trace_visibility: null scene");
+    DHR_TRY(check_camera(cam));
+    DHR_TRY(check_trace_params(params));
+    DHR_TRY(check_gbuffer(gbuf_out, cam->width, cam->height));
+    DHR_CHECK_ARG(shadow_mask_out && ao_count_out, "trace_visibility: null output");
+    return launch_trace(scene, cam, params, gbuf_out, shadow_mask_out, ao_count_out, as_stream(stream));
+}
+
+// ---------------------------------------------------------------- session
+struct dhr_session {
+    const dhr_scene* scene = nullptr;
+    int32_t w = 0, h = 0;
+    dhr_precision prec = DHR_FP32;
+    dhr_trace_params tp{};
+    dhr_svgf_params sp{};
+    void* gdn[2] = {nullptr, nullptr};
+    uint32_t* gmesh[2] = {nullptr, nullptr};
+    uint8_t* mask = nullptr;
+    uint8_t* ao = nullptr;
+    float* out = nullptr;         // [2][W*H]: filtered AO, filtered shadow
+    dhr_svgf_state* svgf = nullptr;
+    dhr_camera cam_prev{};
+    bool has_prev = false;
+    int cur = 0;
+};
+
+extern "C" void dhr_session_destroy(dhr_session* s) {
+    if (!s) return;
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(s->gdn[i]);
+        cudaFree(s->gmesh[i]);
+    }
+    cudaFree(s->mask);
+    cudaFree(s->ao);
+    cudaFree(s->out);
+    svgf_free(s->svgf);
+    delete s;
+}
+
+extern "C" dhr_status dhr_session_create(const dhr_scene* scene, int32_t width, int32_t height,
+                                         dhr_precision precision, const dhr_trace_params* trace,
+                                         const dhr_svgf_params* svgf, dhr_session** out) {
+    clear_error();
+    DHR_CHECK_ARG(scene && out, "session_create: null pointer");
+    DHR_CHECK_ARG(width > 0 && height > 0 && width <= 16384 && height <= 16384, "session_create: bad size");
+    DHR_TRY(check_trace_params(trace));
+    DHR_TRY(check_svgf_params(svgf));
+    *out = nullptr;
+    auto* s = new dhr_session();
+    s->scene = scene;
+    s->w = width;
+    s->h = height;
+    s->prec = precision;
+    s->tp = *trace;
+    s->sp = *svgf;
+    const size_t n = (size_t)width * height;
+    const size_t gb = precision == DHR_FP16 ? 8 : 16;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && !e; ++i) {
+        e = cudaMalloc(&s->gdn[i], n * gb);
+        if (!e) e = cudaMalloc((void**)&s->gmesh[i], n * 4);
+    }
+    if (!e) e = cudaMalloc((void**)&s->mask, n);
+    if (!e) e = cudaMalloc((void**)&s->ao, n);
+    if (!e) e = cudaMalloc((void**)&s->out, 2 * n * sizeof(float));
+    if (e) {
+        cudaGetLastError();
+        dhr_session_destroy(s);
+        return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA, "session_create: %s",
+                         cudaGetErrorString(e));
+    }
+    dhr_status st = svgf_create(width, height, precision, &s->svgf);
+    if (st != DHR_OK) {
+        dhr_session_destroy(s);
+        return st;
+    }
+    *out = s;
+    return DHR_OK;
+}
+
+static dhr_gbuffer session_gbuf(const dhr_session* s, int i) {
+    dhr_gbuffer g;
+    g.precision = s->prec;
+    g.width = s->w;
+    g.height = s->h;
+    g.depth_normal = s->gdn[i];
+    g.mesh_id = s->gmesh[i];
+    return g;
+}
+
+extern "C" dhr_status dhr_step_frame(dhr_session* s, const dhr_camera* cam, uint32_t frame, float* ao_out,
+                                     float* shadow_out, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(s, "step_frame: null session");
+    DHR_TRY(check_camera(cam));
+    DHR_CHECK_ARG(cam->width == s->w && cam->height == s->h, "step_frame: camera size %dx%d, session %dx%d",
+                  cam->width, cam->height, s->w, s->h);
+    cudaStream_t st = as_stream(stream);
+    const int cur = s->cur ^ 1;
+    dhr_gbuffer g = session_gbuf(s, cur);
+    dhr_gbuffer gp = session_gbuf(s, s->cur);
+    dhr_trace_params tp = s->tp;
+    tp.frame = frame;
+    DHR_TRY(launch_trace(s->scene, cam, &tp, &g, s->mask, s->ao, st));
+    const size_t n = (size_t)s->w * s->h;
+    float* ao = ao_out ? ao_out : s->out;
+    float* sh = shadow_out ? shadow_out : s->out + n;
+    DHR_TRY(svgf_run(s->svgf, &g, s->has_prev ? &gp : nullptr, cam, s->has_prev ? &s->cam_prev : nullptr,
+                     s->mask, s->ao, &s->sp, ao, sh, st));
+    s->cur = cur;
+    s->cam_prev = *cam;
+    s->has_prev = true;
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_step_frame_host(dhr_session* s, const dhr_camera* cam, uint32_t frame, float* ao_host,
+                                          float* shadow_host, void* stream) {
+    DHR_CHECK_ARG(ao_host && shadow_host, "step_frame_host: null output");
+    DHR_TRY(dhr_step_frame(s, cam, frame, nullptr, nullptr, stream));
+    cudaStream_t st = as_stream(stream);
+    const size_t n = (size_t)s->w * s->h;
+    DHR_CUDA_TRY(cudaMemcpyAsync(ao_host, s->out, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    DHR_CUDA_TRY(cudaMemcpyAsync(shadow_host, s->out + n, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_session_get_frame(dhr_session* s, dhr_gbuffer* gbuf, uint8_t** shadow_mask,
+                                            uint8_t** ao_count) {
+    clear_error();
+    DHR_CHECK_ARG(s, "session_get_frame: null session");
+    if (gbuf) *gbuf = session_gbuf(s, s->cur);
+    if (shadow_mask) *shadow_mask = s->mask;
+    if (ao_count) *ao_count = s->ao;
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_session_reset(dhr_session* s) {
+    clear_error();
+    DHR_CHECK_ARG(s, "session_reset: null session");
+    s->has_prev = false;
+    return DHR_OK;
+}

@@ -1,0 +1,320 @@
+// LBVH construction on the device.
+//
+// Section 3.2 relies on grouping the scene hierarchically into bounding
+// volumes so that most rays skip most geometry.  B300 has no ray-tracing
+// cores, so the hierarchy is built here: Morton codes of triangle centroids
+// (63 bits, 21 per axis), a device radix sort, the parallel binary radix
+// tree construction of Karras ("Maximizing Parallelism in the Construction
+// of BVHs, Octrees, and k-d Trees", HPG 2012), and a bottom-up box refit in
+// which the second thread to reach a node computes its box.
+#include <cub/device/device_radix_sort.cuh>
+
+#include "common.cuh"
+
+namespace dhr {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint32_t float_flip(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_unflip(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+struct Tri3 {
+    float3 a, b, c;
+};
+
+__device__ __forceinline__ Tri3 load_tri(const float* v, const uint32_t* idx, uint32_t t) {
+    const uint32_t i0 = idx[3 * t], i1 = idx[3 * t + 1], i2 = idx[3 * t + 2];
+    Tri3 r;
+    r.a = make_float3(v[3 * i0], v[3 * i0 + 1], v[3 * i0 + 2]);
+    r.b = make_float3(v[3 * i1], v[3 * i1 + 1], v[3 * i1 + 2]);
+    r.c = make_float3(v[3 * i2], v[3 * i2 + 1], v[3 * i2 + 2]);
+    return r;
+}
+
+// Validates indices and accumulates the centroid bounds (order-preserving
+// integer encoding so that atomicMin/Max work on floats).
+__global__ void centroid_bounds_kernel(const float* v, const uint32_t* idx, uint32_t n_tris,
+                                       uint32_t n_verts, uint32_t* bounds /*[6] flipped*/,
+                                       uint32_t* bad_index) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tris; t += gridDim.x * blockDim.x) {
+        const uint32_t i0 = idx[3 * t], i1 = idx[3 * t + 1], i2 = idx[3 * t + 2];
+        if (i0 >= n_verts || i1 >= n_verts || i2 >= n_verts) {
+            atomicExch(bad_index, 1u);
+            continue;
+        }
+        const Tri3 r = load_tri(v, idx, t);
+        const float c[3] = {(r.a.x + r.b.x + r.c.x) * (1.0f / 3.0f), (r.a.y + r.b.y + r.c.y) * (1.0f / 3.0f),
+                            (r.a.z + r.b.z + r.c.z) * (1.0f / 3.0f)};
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], c[k]);
+            hi[k] = fmaxf(hi[k], c[k]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&bounds[k], float_flip(lo[k]));
+            atomicMax(&bounds[3 + k], float_flip(hi[k]));
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t spread21(uint32_t x) {
+    uint64_t v = x & 0x1FFFFFu;
+    v = (v | (v << 32)) & 0x1F00000000FFFFull;
+    v = (v | (v << 16)) & 0x1F0000FF0000FFull;
+    v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+    v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__global__ void morton_kernel(const float* v, const uint32_t* idx, uint32_t n_tris,
+                              const uint32_t* bounds, uint64_t* keys, uint32_t* values) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tris) return;
+    const Tri3 r = load_tri(v, idx, t);
+    const float c[3] = {(r.a.x + r.b.x + r.c.x) * (1.0f / 3.0f), (r.a.y + r.b.y + r.c.y) * (1.0f / 3.0f),
+                        (r.a.z + r.b.z + r.c.z) * (1.0f / 3.0f)};
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        const float lo = float_unflip(bounds[k]), hi = float_unflip(bounds[3 + k]);
+        const float ext = hi - lo;
+        float u = ext > 0.0f ? (c[k] - lo) / ext : 0.5f;
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        q[k] = min((uint32_t)(u * 2097152.0f), 2097151u);
+    }
+    keys[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    values[t] = t;
+}
+
+// Longest common prefix of keys i and j (index bits break ties); -1 outside.
+__device__ __forceinline__ int delta(const uint64_t* keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    const uint64_t a = keys[i], b = keys[j];
+    if (a == b) return 64 + __clz((uint32_t)i ^ (uint32_t)j);
+    return __clzll(a ^ b);
+}
+
+// Karras 2012: internal node i covers a key range [first, last] found by an
+// exponential then binary search; its split is the highest differing bit.
+__global__ void karras_kernel(const uint64_t* keys, int n, int2* children, int* parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const int c0 = (lo == gamma) ? ~gamma : gamma;          // leaf refs are ~index
+    const int c1 = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    children[i] = make_int2(c0, c1);
+    parent[c0 >= 0 ? c0 : (n - 1) + ~c0] = i;
+    parent[c1 >= 0 ? c1 : (n - 1) + ~c1] = i;
+}
+
+// Node slots 0..n-2 internal, n-1.. leaves.
+__device__ __forceinline__ int slot_of(int ref, int n) { return ref >= 0 ? ref : (n - 1) + ~ref; }
+
+// Leaves: write sorted triangle data and leaf boxes, then climb.  The second
+// thread to arrive at a node computes its box and height and goes on.
+__global__ void refit_kernel(const float* v, const uint32_t* idx, const uint32_t* mesh,
+                             const uint32_t* order, int n, const int2* children, const int* parent,
+                             float4* lo, float4* hi, int* height, uint32_t* visits, float4* tris) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t t = order[k];
+    const Tri3 r = load_tri(v, idx, t);
+    tris[3 * k + 0] = make_float4(r.a.x, r.a.y, r.a.z, __uint_as_float(t));
+    tris[3 * k + 1] = make_float4(r.b.x, r.b.y, r.b.z, __uint_as_float(mesh ? mesh[t] : 0u));
+    tris[3 * k + 2] = make_float4(r.c.x, r.c.y, r.c.z, 0.0f);
+    const int leaf = (n - 1) + k;
+    lo[leaf] = make_float4(fminf(r.a.x, fminf(r.b.x, r.c.x)), fminf(r.a.y, fminf(r.b.y, r.c.y)),
+                           fminf(r.a.z, fminf(r.b.z, r.c.z)), 0.0f);
+    hi[leaf] = make_float4(fmaxf(r.a.x, fmaxf(r.b.x, r.c.x)), fmaxf(r.a.y, fmaxf(r.b.y, r.c.y)),
+                           fmaxf(r.a.z, fmaxf(r.b.z, r.c.z)), 0.0f);
+    height[leaf] = 0;
+    if (n == 1) return;
+    int node = parent[leaf];
+    for (int level = 0; level < 4096; ++level) {   // a tree deeper than this is rejected below
+        __threadfence();
+        if (atomicAdd(&visits[node], 1u) == 0u) return;   // sibling not done yet
+        __threadfence();
+        const int2 ch = children[node];
+        const int a = slot_of(ch.x, n), b = slot_of(ch.y, n);
+        const float4 la = __ldcg(&lo[a]), lb = __ldcg(&lo[b]);
+        const float4 ha = __ldcg(&hi[a]), hb = __ldcg(&hi[b]);
+        lo[node] = make_float4(fminf(la.x, lb.x), fminf(la.y, lb.y), fminf(la.z, lb.z), 0.0f);
+        hi[node] = make_float4(fmaxf(ha.x, hb.x), fmaxf(ha.y, hb.y), fmaxf(ha.z, hb.z), 0.0f);
+        height[node] = 1 + max(__ldcg(&height[a]), __ldcg(&height[b]));
+        if (node == 0) return;
+        node = parent[node];
+    }
+    height[0] = 1 << 20;   // climb did not reach the root: flag a corrupt tree
+}
+
+__global__ void pack_kernel(int n, const int2* children, const float4* lo, const float4* hi,
+                            float4* nodes) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int2 ch = children[i];
+    const int a = slot_of(ch.x, n), b = slot_of(ch.y, n);
+    const float4 la = lo[a], ha = hi[a], lb = lo[b], hb = hi[b];
+    nodes[4 * i + 0] = make_float4(la.x, ha.x, la.y, ha.y);
+    nodes[4 * i + 1] = make_float4(lb.x, hb.x, lb.y, hb.y);
+    nodes[4 * i + 2] = make_float4(la.z, ha.z, lb.z, hb.z);
+    nodes[4 * i + 3] = make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.0f, 0.0f);
+}
+
+// One triangle: a root node whose two children are the same leaf.
+__global__ void single_kernel(const float* v, const uint32_t* idx, const uint32_t* mesh,
+                              float4* nodes, float4* tris) {
+    const Tri3 r = load_tri(v, idx, 0);
+    tris[0] = make_float4(r.a.x, r.a.y, r.a.z, __uint_as_float(0u));
+    tris[1] = make_float4(r.b.x, r.b.y, r.b.z, __uint_as_float(mesh ? mesh[0] : 0u));
+    tris[2] = make_float4(r.c.x, r.c.y, r.c.z, 0.0f);
+    const float lx = fminf(r.a.x, fminf(r.b.x, r.c.x)), hx = fmaxf(r.a.x, fmaxf(r.b.x, r.c.x));
+    const float ly = fminf(r.a.y, fminf(r.b.y, r.c.y)), hy = fmaxf(r.a.y, fmaxf(r.b.y, r.c.y));
+    const float lz = fminf(r.a.z, fminf(r.b.z, r.c.z)), hz = fmaxf(r.a.z, fmaxf(r.b.z, r.c.z));
+    nodes[0] = make_float4(lx, hx, ly, hy);
+    nodes[1] = make_float4(lx, hx, ly, hy);
+    nodes[2] = make_float4(lz, hz, lz, hz);
+    nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
+}
+
+template <class T>
+dhr_status dmalloc(T** p, size_t count, const char* what) {
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+    if (e != cudaSuccess)
+        return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
+                         "cudaMalloc(%s, %zu bytes): %s", what, count * sizeof(T),
+                         cudaGetErrorString(e));
+    return DHR_OK;
+}
+
+struct Scratch {
+    uint32_t* bounds = nullptr;
+    uint64_t* keys = nullptr;
+    uint64_t* keys_sorted = nullptr;
+    uint32_t* vals = nullptr;
+    uint32_t* vals_sorted = nullptr;
+    int2* children = nullptr;
+    int* parent = nullptr;
+    float4* lo = nullptr;
+    float4* hi = nullptr;
+    int* height = nullptr;
+    uint32_t* visits = nullptr;
+    void* cub_tmp = nullptr;
+    ~Scratch() {
+        cudaFree(bounds); cudaFree(keys); cudaFree(keys_sorted); cudaFree(vals);
+        cudaFree(vals_sorted); cudaFree(children); cudaFree(parent); cudaFree(lo);
+        cudaFree(hi); cudaFree(height); cudaFree(visits); cudaFree(cub_tmp);
+    }
+};
+
+}  // namespace
+
+dhr_status build_lbvh(const float* v, const uint32_t* idx, const uint32_t* mesh, uint32_t n_verts,
+                      uint32_t n_tris, cudaStream_t st, dhr_scene* sc) {
+    sc->n_tris = n_tris;
+    if (n_tris == 0) return DHR_OK;
+    cudaEvent_t e0, e1;
+    DHR_CUDA_TRY(cudaEventCreate(&e0));
+    DHR_CUDA_TRY(cudaEventCreate(&e1));
+    DHR_CUDA_TRY(cudaEventRecord(e0, st));
+    const int n = (int)n_tris;
+    const int n_int = n > 1 ? n - 1 : 1;
+    DHR_TRY(dmalloc(&sc->nodes, (size_t)4 * n_int, "bvh nodes"));
+    DHR_TRY(dmalloc(&sc->tris, (size_t)3 * n, "bvh triangles"));
+    sc->n_nodes = n_int;
+    sc->bytes = (uint64_t)n_int * 64 + (uint64_t)n * 48;
+    Scratch s;
+    DHR_TRY(dmalloc(&s.bounds, 7, "bounds"));
+    {
+        uint32_t init[7];
+        for (int k = 0; k < 3; ++k) { init[k] = 0xFFFFFFFFu; init[3 + k] = 0u; }
+        init[6] = 0u;
+        DHR_CUDA_TRY(cudaMemcpyAsync(s.bounds, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    }
+    const int grid = (n + kThreads - 1) / kThreads;
+    centroid_bounds_kernel<<<min(grid, 148 * 8), kThreads, 0, st>>>(v, idx, n_tris, n_verts, s.bounds,
+                                                                   s.bounds + 6);
+    DHR_CUDA_TRY(cudaGetLastError());
+    uint32_t bad = 0;
+    DHR_CUDA_TRY(cudaMemcpyAsync(&bad, s.bounds + 6, 4, cudaMemcpyDeviceToHost, st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad) return set_error(DHR_ERR_INVALID, "create_scene: a triangle index is >= n_vertices");
+    if (n == 1) {
+        single_kernel<<<1, 1, 0, st>>>(v, idx, mesh, sc->nodes, sc->tris);
+        DHR_CUDA_TRY(cudaGetLastError());
+        sc->height = 1;
+    } else {
+        DHR_TRY(dmalloc(&s.keys, n, "keys"));
+        DHR_TRY(dmalloc(&s.keys_sorted, n, "keys"));
+        DHR_TRY(dmalloc(&s.vals, n, "vals"));
+        DHR_TRY(dmalloc(&s.vals_sorted, n, "vals"));
+        DHR_TRY(dmalloc(&s.children, n - 1, "children"));
+        DHR_TRY(dmalloc(&s.parent, 2 * n - 1, "parent"));
+        DHR_TRY(dmalloc(&s.lo, 2 * n - 1, "lo"));
+        DHR_TRY(dmalloc(&s.hi, 2 * n - 1, "hi"));
+        DHR_TRY(dmalloc(&s.height, 2 * n - 1, "height"));
+        DHR_TRY(dmalloc(&s.visits, n - 1, "visits"));
+        DHR_CUDA_TRY(cudaMemsetAsync(s.visits, 0, sizeof(uint32_t) * (n - 1), st));
+        morton_kernel<<<grid, kThreads, 0, st>>>(v, idx, n_tris, s.bounds, s.keys, s.vals);
+        DHR_CUDA_TRY(cudaGetLastError());
+        size_t tmp_bytes = 0;
+        DHR_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, s.keys, s.keys_sorted, s.vals,
+                                                     s.vals_sorted, n, 0, 63, st));
+        DHR_CUDA_TRY(cudaMalloc(&s.cub_tmp, tmp_bytes));
+        DHR_CUDA_TRY(cub::DeviceRadixSort::SortPairs(s.cub_tmp, tmp_bytes, s.keys, s.keys_sorted,
+                                                     s.vals, s.vals_sorted, n, 0, 63, st));
+        karras_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(s.keys_sorted, n,
+                                                                              s.children, s.parent);
+        DHR_CUDA_TRY(cudaGetLastError());
+        refit_kernel<<<grid, kThreads, 0, st>>>(v, idx, mesh, s.vals_sorted, n, s.children, s.parent,
+                                                s.lo, s.hi, s.height, s.visits, sc->tris);
+        DHR_CUDA_TRY(cudaGetLastError());
+        pack_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, s.children, s.lo, s.hi,
+                                                                           sc->nodes);
+        DHR_CUDA_TRY(cudaGetLastError());
+        int h = 0;
+        DHR_CUDA_TRY(cudaMemcpyAsync(&h, s.height, sizeof(int), cudaMemcpyDeviceToHost, st));
+        DHR_CUDA_TRY(cudaStreamSynchronize(st));
+        sc->height = (uint32_t)h;
+    }
+    DHR_CUDA_TRY(cudaEventRecord(e1, st));
+    DHR_CUDA_TRY(cudaEventSynchronize(e1));
+    DHR_CUDA_TRY(cudaEventElapsedTime(&sc->build_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (sc->height >= (uint32_t)kStackSize)
+        return set_error(DHR_ERR_INVALID,
+                         "create_scene: BVH height %u exceeds the traversal stack (%d)", sc->height,
+                         kStackSize);
+    return DHR_OK;
+}
+
+}  // namespace dhr

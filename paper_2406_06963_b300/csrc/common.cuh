@@ -1,0 +1,83 @@
+// Internal declarations shared by the libdhrs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "dhrs.h"
+
+namespace dhr {
+
+// ---------------------------------------------------------------- errors
+dhr_status set_error(dhr_status s, const char* fmt, ...);
+void clear_error();
+
+#define DHR_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::dhr::set_error(e_ == cudaErrorMemoryAllocation ? DHR_ERR_OOM       \
+                                                                    : DHR_ERR_CUDA,     \
+                                    "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),    \
+                                    __FILE__, __LINE__);                                \
+    } while (0)
+
+#define DHR_CHECK_ARG(cond, ...)                                                        \
+    do {                                                                                \
+        if (!(cond)) return ::dhr::set_error(DHR_ERR_INVALID, __VA_ARGS__);             \
+    } while (0)
+
+#define DHR_TRY(expr)                     \
+    do {                                  \
+        dhr_status s_ = (expr);           \
+        if (s_ != DHR_OK) return s_;      \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------- scene
+// BVH node, 64 bytes: the boxes of both children plus their references.
+//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   d = (child0, child1, -, -) as int bits; >= 0 internal node, < 0 leaf ~i
+// Leaf i holds sorted triangle i: 3 float4 (v0, orig index bits),
+// (v1, mesh id bits), (v2, 0).
+struct SceneView {
+    const float4* nodes;
+    const float4* tris;
+    int32_t n_tris;
+};
+
+constexpr int kStackSize = 64;
+
+}  // namespace dhr
+
+struct dhr_scene {
+    float4* nodes = nullptr;
+    float4* tris = nullptr;
+    uint32_t n_tris = 0;
+    uint32_t n_nodes = 0;
+    uint32_t height = 0;
+    uint64_t bytes = 0;
+    float build_ms = 0.f;
+    dhr::SceneView view() const { return dhr::SceneView{nodes, tris, (int32_t)n_tris}; }
+};
+
+namespace dhr {
+
+// ------------------------------------------------------------ entry points
+dhr_status build_lbvh(const float* verts_d, const uint32_t* idx_d, const uint32_t* mesh_d,
+                      uint32_t n_verts, uint32_t n_tris, cudaStream_t st, dhr_scene* sc);
+
+dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
+                        dhr_gbuffer* g, uint8_t* mask, uint8_t* ao, cudaStream_t st,
+                        unsigned long long* stats = nullptr);
+
+dhr_status check_trace_params(const dhr_trace_params* p);
+
+}  // namespace dhr

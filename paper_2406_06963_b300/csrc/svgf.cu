@@ -1,0 +1,553 @@
+// Modified SVGF reconstruction on the device (Section 3.3).
+//
+//  temporal_kernel: back-project each pixel into the previous frame, keep
+//    the bilinear history taps consistent in mesh id, depth and normal,
+//    accumulate colour and the first two moments with an exponential moving
+//    average (alpha_eff = max(alpha, 1/n)), and estimate the variance:
+//    from the moments when the history holds n >= 4 frames, else from a 7x7
+//    window of the current frame weighted by depth and normal only (the
+//    paper's modification: no luminance term in the variance estimate).
+//  atrous_kernel: one edge-stopping a-trous iteration (5x5 B3-spline taps at
+//    step 2^i, weights from depth, normal and luminance with a 3x3 Gaussian
+//    of the variance); the first iteration's colour is the next frame's
+//    colour history and the last iteration writes the outputs.
+//
+// Storage precision is a template parameter: FP32 keeps every buffer in
+// binary32; FP16 stores the G-buffer (depth, normal), the colour history and
+// the moments in binary16 and keeps the variance-carrying buffer in binary32
+// (its mu2 - mu1^2 cancellation needs the precision); arithmetic is binary32.
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace dhr {
+
+template <dhr_precision P>
+struct Store;
+
+template <>
+struct Store<DHR_FP32> {
+    using G = float4;
+    using Col = float2;
+    using Mom = float4;
+    static __device__ __forceinline__ float4 g(const G* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ float2 col(const Col* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = v; }
+    static __device__ __forceinline__ float4 mom(const Mom* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void put_mom(Mom* p, size_t i, float4 v) { p[i] = v; }
+};
+
+template <>
+struct Store<DHR_FP16> {
+    using G = ushort4;
+    using Col = __half2;
+    using Mom = ushort4;
+    static __device__ __forceinline__ float h(unsigned short u) { return __half2float(__ushort_as_half(u)); }
+    static __device__ __forceinline__ unsigned short q(float f) { return __half_as_ushort(__float2half_rn(f)); }
+    static __device__ __forceinline__ float4 g(const G* p, size_t i) {
+        const ushort4 u = __ldg(p + i);
+        const float z = h(u.x);
+        float3 n = make_float3(h(u.y), h(u.z), h(u.w));
+        const float l2 = n.x * n.x + n.y * n.y + n.z * n.z;
+        if (l2 > 0.0f) {                      // renormalise the quantised normal
+            const float r = rsqrtf(l2);
+            n = make_float3(n.x * r, n.y * r, n.z * r);
+        }
+        return make_float4(z, n.x, n.y, n.z);
+    }
+    static __device__ __forceinline__ float2 col(const Col* p, size_t i) { return __half22float2(p[i]); }
+    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = __float22half2_rn(v); }
+    static __device__ __forceinline__ float4 mom(const Mom* p, size_t i) {
+        const ushort4 u = __ldg(p + i);
+        return make_float4(h(u.x), h(u.y), h(u.z), h(u.w));
+    }
+    static __device__ __forceinline__ void put_mom(Mom* p, size_t i, float4 v) {
+        p[i] = make_ushort4(q(v.x), q(v.y), q(v.z), q(v.w));
+    }
+};
+
+struct SvgfConsts {
+    int W, H;
+    float alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
+    float inv_spp;
+    int fixed_alpha, wl_in_atrous;
+};
+
+__device__ __forceinline__ bool is_fg(float z) { return z < INFINITY; }
+
+// max(0, c)^sigma_n with 0^0 = 1
+__device__ __forceinline__ float pow_normal(float c, float sigma_n) {
+    if (sigma_n == 0.0f) return 1.0f;
+    c = fmaxf(c, 0.0f);
+    return c > 0.0f ? exp2f(sigma_n * __log2f(c)) : 0.0f;
+}
+
+__device__ __forceinline__ float w_depth(float zp, float zq, float2 g, float ox, float oy, float sz, float ez) {
+    return __expf(-fabsf(zp - zq) / (sz * fabsf(fmaf(g.x, ox, g.y * oy)) + ez));
+}
+
+// per-axis one-sided depth difference of smaller magnitude (0 if none)
+template <class S>
+__device__ __forceinline__ float2 depth_grad(const typename S::G* g, int W, int H, int x, int y, float zp) {
+    float r[2];
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const int xp = x + (ax == 0), yp = y + (ax == 1), xm = x - (ax == 0), ym = y - (ax == 1);
+        bool hp = false, hm = false;
+        float dp = 0.f, dm = 0.f;
+        if (xp < W && yp < H) {
+            const float z = S::g(g, (size_t)yp * W + xp).x;
+            if (is_fg(z)) { dp = z - zp; hp = true; }
+        }
+        if (xm >= 0 && ym >= 0) {
+            const float z = S::g(g, (size_t)ym * W + xm).x;
+            if (is_fg(z)) { dm = zp - z; hm = true; }
+        }
+        r[ax] = (hp && hm) ? (fabsf(dm) < fabsf(dp) ? dm : dp) : (hp ? dp : (hm ? dm : 0.f));
+    }
+    return make_float2(r[0], r[1]);
+}
+
+__device__ __forceinline__ float2 noisy(const uint8_t* mask, const uint8_t* ao, size_t i, float inv_spp) {
+    return make_float2((float)__ldg(ao + i) * inv_spp, (__ldg(mask + i) & 1u) ? 1.0f : 0.0f);
+}
+
+// Back-projection into the previous frame: the binary32 operation sequence
+// below (each step rounded once, no contraction) decides which history taps
+// are valid; it is the specification shared with the CPU oracle.
+struct Reproj {
+    int x0, y0;
+    float w[4];
+    int ok;          // bit k: tap k valid (00, 10, 01, 11)
+    float sumw;
+};
+
+template <class S>
+__device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera& p, int W, int H, int x, int y,
+                                          float4 znp, uint32_t mp, const typename S::G* g_prev,
+                                          const uint32_t* mesh_prev, Reproj& r) {
+    const float Wf = (float)W, Hf = (float)H;
+    const float aspect = __fdiv_rn(Wf, Hf);
+    const float fx = __fadd_rn((float)x, 0.5f), fy = __fadd_rn((float)y, 0.5f);
+    const float qx = __fdiv_rn(__fmul_rn(2.0f, fx), Wf), qy = __fdiv_rn(__fmul_rn(2.0f, fy), Hf);
+    const float ndx = __fsub_rn(qx, 1.0f), ndy = __fsub_rn(1.0f, qy);
+    const float sx = __fmul_rn(__fmul_rn(ndx, c.tan_half_fov_y), aspect);
+    const float sy = __fmul_rn(ndy, c.tan_half_fov_y);
+    float rr[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float D = __fadd_rn(__fadd_rn(c.forward[k], __fmul_rn(sx, c.right[k])), __fmul_rn(sy, c.up[k]));
+        const float X = __fadd_rn(c.pos[k], __fmul_rn(znp.x, D));
+        rr[k] = __fsub_rn(X, p.pos[k]);
+    }
+    const float zp = __fadd_rn(__fadd_rn(__fmul_rn(rr[0], p.forward[0]), __fmul_rn(rr[1], p.forward[1])),
+                               __fmul_rn(rr[2], p.forward[2]));
+    const float rx = __fadd_rn(__fadd_rn(__fmul_rn(rr[0], p.right[0]), __fmul_rn(rr[1], p.right[1])),
+                               __fmul_rn(rr[2], p.right[2]));
+    const float ry = __fadd_rn(__fadd_rn(__fmul_rn(rr[0], p.up[0]), __fmul_rn(rr[1], p.up[1])),
+                               __fmul_rn(rr[2], p.up[2]));
+    if (!(zp > 0.0f)) return false;
+    const float zt = __fmul_rn(zp, p.tan_half_fov_y);
+    const float zta = __fmul_rn(zt, aspect);
+    const float su = __fdiv_rn(rx, zta), sv = __fdiv_rn(ry, zt);
+    const float pxc = __fmul_rn(__fmul_rn(__fadd_rn(su, 1.0f), 0.5f), Wf);
+    const float pyc = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, sv), 0.5f), Hf);
+    const float gx = __fsub_rn(pxc, 0.5f), gy = __fsub_rn(pyc, 0.5f);
+    if (!(gx > -1.0f && gx < Wf && gy > -1.0f && gy < Hf)) return false;
+    const float x0f = floorf(gx), y0f = floorf(gy);
+    const float ax = __fsub_rn(gx, x0f), ay = __fsub_rn(gy, y0f);
+    const float bx = __fsub_rn(1.0f, ax), by = __fsub_rn(1.0f, ay);
+    r.w[0] = __fmul_rn(bx, by);
+    r.w[1] = __fmul_rn(ax, by);
+    r.w[2] = __fmul_rn(bx, ay);
+    r.w[3] = __fmul_rn(ax, ay);
+    r.x0 = (int)x0f;
+    r.y0 = (int)y0f;
+    const float zlim = __fmul_rn(0.01f, zp);
+    float sumw = 0.0f;
+    int ok = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int qx2 = r.x0 + (k & 1), qy2 = r.y0 + (k >> 1);
+        if (qx2 < 0 || qy2 < 0 || qx2 >= W || qy2 >= H) continue;
+        const size_t q = (size_t)qy2 * W + qx2;
+        if (__ldg(mesh_prev + q) != mp) continue;
+        const float4 gq = S::g(g_prev, q);
+        if (!(fabsf(__fsub_rn(gq.x, zp)) <= zlim)) continue;
+        const float nd = __fadd_rn(__fadd_rn(__fmul_rn(znp.y, gq.y), __fmul_rn(znp.z, gq.z)), __fmul_rn(znp.w, gq.w));
+        if (!(nd >= 0.9f)) continue;
+        ok |= 1 << k;
+        sumw = __fadd_rn(sumw, r.w[k]);
+    }
+    r.ok = ok;
+    r.sumw = sumw;
+    return sumw >= 1e-4f;
+}
+
+template <dhr_precision P>
+__global__ void __launch_bounds__(256) temporal_kernel(
+    SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const typename Store<P>::G* g_cur,
+    const uint32_t* mesh_cur, const typename Store<P>::G* g_prev, const uint32_t* mesh_prev,
+    const uint8_t* mask, const uint8_t* ao, const typename Store<P>::Col* col_hist,
+    const typename Store<P>::Mom* mom_in, const uint8_t* hist_in, typename Store<P>::Mom* mom_out,
+    uint8_t* hist_out, float4* illum) {
+    using S = Store<P>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= k.W || y >= k.H) return;
+    const size_t p = (size_t)y * k.W + x;
+    const float4 zn = S::g(g_cur, p);
+    if (!is_fg(zn.x)) {
+        illum[p] = make_float4(1.f, 1.f, 0.f, 0.f);
+        S::put_mom(mom_out, p, make_float4(1.f, 1.f, 1.f, 1.f));
+        hist_out[p] = 0;
+        return;
+    }
+    const float2 s = noisy(mask, ao, p, k.inv_spp);
+    float2 ch = make_float2(0.f, 0.f);
+    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f);
+    int n = 1;
+    bool valid = false;
+    if (g_prev) {
+        Reproj r;
+        if (reproject<S>(cam, cam_prev, k.W, k.H, x, y, zn, __ldg(mesh_cur + p), g_prev, mesh_prev, r)) {
+            valid = true;
+            const float inv = 1.0f / r.sumw;
+            int hmin = 255;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (!(r.ok & (1 << t))) continue;
+                const size_t q = (size_t)(r.y0 + (t >> 1)) * k.W + (r.x0 + (t & 1));
+                const float w = r.w[t] * inv;
+                const float2 c = S::col(col_hist, q);
+                const float4 m = S::mom(mom_in, q);
+                ch.x = fmaf(w, c.x, ch.x);
+                ch.y = fmaf(w, c.y, ch.y);
+                mh.x = fmaf(w, m.x, mh.x);
+                mh.y = fmaf(w, m.y, mh.y);
+                mh.z = fmaf(w, m.z, mh.z);
+                mh.w = fmaf(w, m.w, mh.w);
+                hmin = min(hmin, (int)__ldg(hist_in + q));
+            }
+            n = min(hmin + 1, 255);
+        }
+    }
+    const float a = valid ? (k.fixed_alpha ? k.alpha : fmaxf(k.alpha, 1.0f / (float)n)) : 1.0f;
+    const float b = 1.0f - a;
+    const float2 c = make_float2(b * ch.x + a * s.x, b * ch.y + a * s.y);
+    const float4 m = make_float4(b * mh.x + a * s.x, b * mh.y + a * s.y, b * mh.z + a * s.x * s.x,
+                                 b * mh.w + a * s.y * s.y);
+    S::put_mom(mom_out, p, m);
+    hist_out[p] = (uint8_t)n;
+    if (n >= 4) {
+        illum[p] = make_float4(c.x, c.y, fmaxf(0.f, m.z - m.x * m.x), fmaxf(0.f, m.w - m.y * m.y));
+        return;
+    }
+    // short history: 7x7 spatial estimate weighted by depth and normal only
+    const float2 gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
+    float sw = 0.f;
+    float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
+    for (int dy = -3; dy <= 3; ++dy) {
+        const int qy = y + dy;
+        if (qy < 0 || qy >= k.H) continue;
+        for (int dx = -3; dx <= 3; ++dx) {
+            const int qx = x + dx;
+            if (qx < 0 || qx >= k.W) continue;
+            const size_t q = (size_t)qy * k.W + qx;
+            const float4 zq = S::g(g_cur, q);
+            if (!is_fg(zq.x)) continue;
+            float w = 1.0f;
+            if (dx || dy)
+                w = w_depth(zn.x, zq.x, gz, (float)-dx, (float)-dy, k.sigma_z, k.eps_z) *
+                    pow_normal(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
+            const float2 sq = noisy(mask, ao, q, k.inv_spp);
+            sw += w;
+            s1.x = fmaf(w, sq.x, s1.x);
+            s1.y = fmaf(w, sq.y, s1.y);
+            s2.x = fmaf(w, sq.x * sq.x, s2.x);
+            s2.y = fmaf(w, sq.y * sq.y, s2.y);
+        }
+    }
+    const float iw = 1.0f / sw;
+    const float m1x = s1.x * iw, m1y = s1.y * iw;
+    illum[p] = make_float4(m1x, m1y, fmaxf(0.f, s2.x * iw - m1x * m1x), fmaxf(0.f, s2.y * iw - m1y * m1y));
+}
+
+// one a-trous iteration; kMode 0: write illum_out; 1: also colour history;
+// 2: last iteration, write the two output planes only
+template <dhr_precision P, int kMode>
+__global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
+                                                     const float4* in, float4* out,
+                                                     typename Store<P>::Col* col_hist, float* ao_out,
+                                                     float* sh_out) {
+    using S = Store<P>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= k.W || y >= k.H) return;
+    const size_t p = (size_t)y * k.W + x;
+    const float4 zn = S::g(g, p);
+    if (!is_fg(zn.x)) {
+        if (kMode == 2) {
+            ao_out[p] = 1.f;
+            sh_out[p] = 1.f;
+        } else {
+            out[p] = make_float4(1.f, 1.f, 0.f, 0.f);
+            if (kMode == 1) S::put_col(col_hist, p, make_float2(1.f, 1.f));
+        }
+        return;
+    }
+    const float4 cp = __ldg(in + p);
+    // 3x3 Gaussian of the variance, renormalised over foreground taps
+    float gv0 = 0.f, gv1 = 0.f, gw = 0.f;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int qx = x + dx, qy = y + dy;
+            if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
+            const size_t q = (size_t)qy * k.W + qx;
+            if (!is_fg(S::g(g, q).x)) continue;
+            const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
+            const float4 v = __ldg(in + q);
+            gw += kk;
+            gv0 = fmaf(kk, v.z, gv0);
+            gv1 = fmaf(kk, v.w, gv1);
+        }
+    }
+    const float il0 = k.wl_in_atrous ? 1.0f / (k.sigma_l * sqrtf(fmaxf(0.f, gv0 / gw)) + k.eps_l) : 0.f;
+    const float il1 = k.wl_in_atrous ? 1.0f / (k.sigma_l * sqrtf(fmaxf(0.f, gv1 / gw)) + k.eps_l) : 0.f;
+    const float2 gz = depth_grad<S>(g, k.W, k.H, x, y, zn.x);
+    const float kc = 0.375f * 0.375f;
+    float sw0 = kc, sw1 = kc;
+    float sc0 = kc * cp.x, sc1 = kc * cp.y;
+    float sv0 = kc * kc * cp.z, sv1 = kc * kc * cp.w;
+    const float h5[5] = {1.f / 16, 1.f / 4, 3.f / 8, 1.f / 4, 1.f / 16};
+#pragma unroll
+    for (int j = -2; j <= 2; ++j) {
+        const int qy = y + j * step;
+        if (qy < 0 || qy >= k.H) continue;
+#pragma unroll
+        for (int i = -2; i <= 2; ++i) {
+            if (i == 0 && j == 0) continue;
+            const int qx = x + i * step;
+            if (qx < 0 || qx >= k.W) continue;
+            const size_t q = (size_t)qy * k.W + qx;
+            const float4 zq = S::g(g, q);
+            if (!is_fg(zq.x)) continue;
+            const float4 cq = __ldg(in + q);
+            const float wzn = h5[i + 2] * h5[j + 2] *
+                              w_depth(zn.x, zq.x, gz, (float)(-i * step), (float)(-j * step), k.sigma_z, k.eps_z) *
+                              pow_normal(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
+            const float w0 = wzn * __expf(-fabsf(cp.x - cq.x) * il0);
+            const float w1 = wzn * __expf(-fabsf(cp.y - cq.y) * il1);
+            sw0 += w0;
+            sw1 += w1;
+            sc0 = fmaf(w0, cq.x, sc0);
+            sc1 = fmaf(w1, cq.y, sc1);
+            sv0 = fmaf(w0 * w0, cq.z, sv0);
+            sv1 = fmaf(w1 * w1, cq.w, sv1);
+        }
+    }
+    const float i0 = 1.0f / sw0, i1 = 1.0f / sw1;
+    const float c0 = sc0 * i0, c1 = sc1 * i1;
+    if (kMode == 2) {
+        ao_out[p] = c0;
+        sh_out[p] = c1;
+    } else {
+        out[p] = make_float4(c0, c1, sv0 * i0 * i0, sv1 * i1 * i1);
+        if (kMode == 1) S::put_col(col_hist, p, make_float2(c0, c1));
+    }
+}
+
+// levels == 0: the temporal colour is the output and the colour history
+template <dhr_precision P>
+__global__ void passthrough_kernel(int n, const float4* illum, typename Store<P>::Col* col_hist, float* ao_out,
+                                   float* sh_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = illum[i];
+    Store<P>::put_col(col_hist, i, make_float2(v.x, v.y));
+    ao_out[i] = v.x;
+    sh_out[i] = v.y;
+}
+
+}  // namespace dhr
+
+// ------------------------------------------------------------------ state
+struct dhr_svgf_state {
+    int32_t w = 0, h = 0;
+    dhr_precision prec = DHR_FP32;
+    void* col = nullptr;        // colour history
+    void* mom[2] = {nullptr, nullptr};
+    uint8_t* hist[2] = {nullptr, nullptr};
+    float4* illum = nullptr;    // temporal output
+    float4* pp[2] = {nullptr, nullptr};
+    int cur = 0;                // index of the moments/history written last
+};
+
+namespace dhr {
+
+void svgf_free(dhr_svgf_state* s);
+
+dhr_status svgf_create(int32_t w, int32_t h, dhr_precision prec, dhr_svgf_state** out) {
+    DHR_CHECK_ARG(out, "svgf_create: null out");
+    DHR_CHECK_ARG(w > 0 && h > 0 && (int64_t)w * h <= (1ll << 28), "svgf_create: bad size %dx%d", w, h);
+    DHR_CHECK_ARG(prec == DHR_FP32 || prec == DHR_FP16, "svgf_create: bad precision");
+    auto* s = new dhr_svgf_state();
+    s->w = w;
+    s->h = h;
+    s->prec = prec;
+    const size_t n = (size_t)w * h;
+    const size_t col_b = prec == DHR_FP16 ? 4 : 8, mom_b = prec == DHR_FP16 ? 8 : 16;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&s->col, n * col_b);
+    e = e ? e : cudaMalloc(&s->mom[0], n * mom_b);
+    e = e ? e : cudaMalloc(&s->mom[1], n * mom_b);
+    e = e ? e : cudaMalloc((void**)&s->hist[0], n);
+    e = e ? e : cudaMalloc((void**)&s->hist[1], n);
+    e = e ? e : cudaMalloc((void**)&s->illum, n * 16);
+    e = e ? e : cudaMalloc((void**)&s->pp[0], n * 16);
+    e = e ? e : cudaMalloc((void**)&s->pp[1], n * 16);
+    e = e ? e : cudaMemset(s->hist[0], 0, n);
+    e = e ? e : cudaMemset(s->hist[1], 0, n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        svgf_free(s);
+        return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA, "svgf_create: %s",
+                         cudaGetErrorString(e));
+    }
+    *out = s;
+    return DHR_OK;
+}
+
+void svgf_free(dhr_svgf_state* s) {
+    if (!s) return;
+    cudaFree(s->col);
+    cudaFree(s->mom[0]);
+    cudaFree(s->mom[1]);
+    cudaFree(s->hist[0]);
+    cudaFree(s->hist[1]);
+    cudaFree(s->illum);
+    cudaFree(s->pp[0]);
+    cudaFree(s->pp[1]);
+    delete s;
+}
+
+dhr_status check_svgf_params(const dhr_svgf_params* p) {
+    DHR_CHECK_ARG(p, "svgf params: null");
+    DHR_CHECK_ARG(p->levels <= 8, "svgf: levels %u > 8", p->levels);
+    DHR_CHECK_ARG(p->ao_spp >= 1 && p->ao_spp <= 255, "svgf: ao_spp %u not in 1..255", p->ao_spp);
+    DHR_CHECK_ARG(p->alpha > 0.0f && p->alpha <= 1.0f, "svgf: alpha not in (0, 1]");
+    DHR_CHECK_ARG(p->sigma_n >= 0.0f && p->sigma_z >= 0.0f && p->sigma_l >= 0.0f, "svgf: negative sigma");
+    return DHR_OK;
+}
+
+template <dhr_precision P>
+static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev,
+                           const dhr_camera* cam, const dhr_camera* cam_prev, const uint8_t* mask,
+                           const uint8_t* ao, const dhr_svgf_params* prm, float* ao_out, float* sh_out,
+                           cudaStream_t st) {
+    using S = Store<P>;
+    SvgfConsts k;
+    k.W = s->w;
+    k.H = s->h;
+    k.alpha = prm->alpha;
+    k.sigma_z = prm->sigma_z;
+    k.sigma_n = prm->sigma_n;
+    k.sigma_l = prm->sigma_l;
+    k.eps_z = prm->eps_z;
+    k.eps_l = prm->eps_l;
+    k.inv_spp = 1.0f / (float)prm->ao_spp;
+    k.fixed_alpha = (int)prm->fixed_alpha;
+    k.wl_in_atrous = (int)prm->wl_in_atrous;
+    const int src = s->cur, dst = s->cur ^ 1;
+    const dim3 blk(32, 8), grid((s->w + 31) / 32, (s->h + 7) / 8);
+    const auto* gc = static_cast<const typename S::G*>(cur->depth_normal);
+    const auto* gp = prev ? static_cast<const typename S::G*>(prev->depth_normal) : nullptr;
+    temporal_kernel<P><<<grid, blk, 0, st>>>(
+        k, *cam, prev ? *cam_prev : *cam, gc, cur->mesh_id, gp, prev ? prev->mesh_id : nullptr, mask, ao,
+        static_cast<const typename S::Col*>(s->col), static_cast<const typename S::Mom*>(s->mom[src]),
+        s->hist[src], static_cast<typename S::Mom*>(s->mom[dst]), s->hist[dst], s->illum);
+    DHR_CUDA_TRY(cudaGetLastError());
+    s->cur = dst;
+    auto* col = static_cast<typename S::Col*>(s->col);
+    const int L = (int)prm->levels;
+    if (L == 0) {
+        const int n = s->w * s->h;
+        passthrough_kernel<P><<<(n + 255) / 256, 256, 0, st>>>(n, s->illum, col, ao_out, sh_out);
+        DHR_CUDA_TRY(cudaGetLastError());
+        return DHR_OK;
+    }
+    const float4* in = s->illum;
+    for (int l = 0; l < L; ++l) {
+        float4* out = s->pp[l & 1];
+        const int step = 1 << l;
+        if (l == L - 1 && L == 1) {
+            // single iteration: it is both the history source and the output
+            atrous_kernel<P, 1><<<grid, blk, 0, st>>>(k, step, gc, in, out, col, nullptr, nullptr);
+            DHR_CUDA_TRY(cudaGetLastError());
+            passthrough_kernel<P><<<(s->w * s->h + 255) / 256, 256, 0, st>>>(s->w * s->h, out, col, ao_out,
+                                                                             sh_out);
+        } else if (l == L - 1) {
+            atrous_kernel<P, 2><<<grid, blk, 0, st>>>(k, step, gc, in, nullptr, nullptr, ao_out, sh_out);
+        } else if (l == 0) {
+            atrous_kernel<P, 1><<<grid, blk, 0, st>>>(k, step, gc, in, out, col, nullptr, nullptr);
+        } else {
+            atrous_kernel<P, 0><<<grid, blk, 0, st>>>(k, step, gc, in, out, nullptr, nullptr, nullptr);
+        }
+        DHR_CUDA_TRY(cudaGetLastError());
+        in = out;
+    }
+    return DHR_OK;
+}
+
+dhr_status svgf_run(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev, const dhr_camera* cam,
+                    const dhr_camera* cam_prev, const uint8_t* mask, const uint8_t* ao,
+                    const dhr_svgf_params* prm, float* ao_out, float* sh_out, cudaStream_t st) {
+    DHR_CHECK_ARG(s && cur && cam && mask && ao && ao_out && sh_out, "svgf_reconstruct: null pointer");
+    DHR_TRY(check_svgf_params(prm));
+    DHR_CHECK_ARG(cur->width == s->w && cur->height == s->h && cam->width == s->w && cam->height == s->h,
+                  "svgf_reconstruct: size mismatch (state %dx%d)", s->w, s->h);
+    DHR_CHECK_ARG(cur->precision == s->prec, "svgf_reconstruct: G-buffer precision differs from the state");
+    DHR_CHECK_ARG(cur->depth_normal && cur->mesh_id, "svgf_reconstruct: null G-buffer");
+    if (prev) {
+        DHR_CHECK_ARG(cam_prev, "svgf_reconstruct: prev G-buffer without cam_prev");
+        DHR_CHECK_ARG(prev->width == s->w && prev->height == s->h && prev->precision == s->prec &&
+                          prev->depth_normal && prev->mesh_id && cam_prev->width == s->w &&
+                          cam_prev->height == s->h,
+                      "svgf_reconstruct: previous G-buffer does not match the state");
+    }
+    if (s->prec == DHR_FP16)
+        return run_svgf<DHR_FP16>(s, cur, prev, cam, cam_prev, mask, ao, prm, ao_out, sh_out, st);
+    return run_svgf<DHR_FP32>(s, cur, prev, cam, cam_prev, mask, ao, prm, ao_out, sh_out, st);
+}
+
+}  // namespace dhr
+
+using namespace dhr;
+
+extern "C" dhr_status dhr_svgf_create(int32_t width, int32_t height, dhr_precision precision,
+                                      dhr_svgf_state** out) {
+    clear_error();
+    return svgf_create(width, height, precision, out);
+}
+
+extern "C" void dhr_svgf_destroy(dhr_svgf_state* state) { svgf_free(state); }
+
+extern "C" dhr_status dhr_svgf_get_buffers(dhr_svgf_state* s, dhr_svgf_buffers* out) {
+    clear_error();
+    DHR_CHECK_ARG(s && out, "svgf_get_buffers: null pointer");
+    out->illum = s->illum;
+    out->moments = s->mom[s->cur];
+    out->color_hist = s->col;
+    out->histlen = s->hist[s->cur];
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur, const dhr_gbuffer* prev,
+                                           const dhr_camera* cam, const dhr_camera* cam_prev,
+                                           const uint8_t* shadow_mask, const uint8_t* ao_count,
+                                           const dhr_svgf_params* params, float* ao_out, float* shadow_out,
+                                           void* stream) {
+    clear_error();
+    return svgf_run(state, cur, prev, cam, cam_prev, shadow_mask, ao_count, params, ao_out, shadow_out,
+                    as_stream(stream));
+}

@@ -1,0 +1,52 @@
+"""Host-side checks of the C ABI and of the oracle/CUDA separation (no GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(dhr_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2406_06963_b300 as dhrs
+    from paper_2406_06963_b300 import build
+    build.build()
+    L = ctypes.CDLL(dhrs.LIB_PATH)
+    names = _declared_symbols()
+    assert len(names) >= 17
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding wraps every declared entry point
+    assert names <= set(dhrs._SIGNATURES), sorted(names - set(dhrs._SIGNATURES))
+
+
+def test_binding_loads_without_gpu():
+    import paper_2406_06963_b300 as dhrs
+    L = dhrs.lib()
+    assert L.dhr_last_error() == b""
+
+
+def test_oracle_and_cuda_share_no_code():
+    """The oracle and the CUDA library include nothing from each other and
+    the product package never imports the oracle."""
+    csrc = glob.glob(os.path.join(ROOT, "paper_2406_06963_b300", "csrc", "*"))
+    for f in csrc:
+        t = open(f).read()
+        for inc in re.findall(r"#include\s*[<\"]([^>\"]+)", t):
+            assert "oracle" not in inc and "orc_" not in inc, (f, inc)
+        assert "orc_" not in t, f
+    for f in glob.glob(os.path.join(ROOT, "paper_2406_06963_b300", "*.py")):
+        t = open(f).read()
+        assert not re.search(r"^\s*(from|import)\s+oracle", t, re.M), f
+    oc = open(os.path.join(ROOT, "oracle", "dhrs_oracle.c")).read()
+    for inc in re.findall(r"#include\s*[<\"]([^>\"]+)", oc):
+        assert inc in ("math.h", "stdint.h", "stdlib.h", "string.h", "omp.h"), inc

@@ -1,0 +1,60 @@
+"""dhr_step_frame (trace + SVGF with library-owned ping-pong buffers) gives
+exactly what the two component calls give, and the host-output variant
+returns the same bytes."""
+import numpy as np
+import pytest
+
+import paper_2406_06963_b300 as dhrs
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_step_frame_equals_components():
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    W, H = 160, 96
+    cams = wl.orbit_path(5, W, H, degrees=6.0)
+    tp = dhrs.TraceParams(ao_spp=2)
+    sp = dhrs.SvgfParams(ao_spp=2)
+    sess = dhrs.Session(sc, W, H, dhrs.DHR_FP32, tp, sp)
+    st = dhrs.SvgfState(W, H)
+    a1, s1 = torch.empty((H, W), device="cuda"), torch.empty((H, W), device="cuda")
+    a2, s2 = torch.empty_like(a1), torch.empty_like(a1)
+    prev = None
+    for f, cam in enumerate(cams):
+        sess.step(cam, f, a1, s1)
+        g = dhrs.GBuffer(W, H)
+        m = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        a = torch.empty_like(m)
+        tpf = dhrs.TraceParams(ao_spp=2, frame=f)
+        dhrs.trace_visibility(sc, cam, tpf, g, m, a)
+        st.reconstruct(g, prev[0] if prev else None, cam, prev[1] if prev else None, m, a, sp, a2, s2)
+        prev = (g, cam)
+        torch.cuda.synchronize()
+        assert torch.equal(a1, a2) and torch.equal(s1, s2), f
+    ah = torch.empty((H, W), pin_memory=True)
+    sh = torch.empty((H, W), pin_memory=True)
+    sess2 = dhrs.Session(sc, W, H, dhrs.DHR_FP32, tp, sp)
+    for f, cam in enumerate(cams):
+        sess2.step_host(cam, f, ah, sh)
+    assert torch.equal(ah, a1.cpu()) and torch.equal(sh, s1.cpu())
+
+
+def test_session_reset_drops_history():
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    cam = wl.boxes_camera(64, 64)
+    sess = dhrs.Session(sc, 64, 64)
+    o1 = torch.empty((64, 64), device="cuda")
+    o2 = torch.empty_like(o1)
+    sh = torch.empty_like(o1)
+    sess.step(cam, 0, o1, sh)
+    sess.step(cam, 1, o2, sh)
+    sess.reset()
+    o3 = torch.empty_like(o1)
+    sess.step(cam, 0, o3, sh)          # same frame index, no history: same as the first frame
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o3)
+    assert not torch.equal(o1, o2)

@@ -1,0 +1,191 @@
+"""GPU parity of the sampling, LBVH traversal and visibility tracing against
+the CPU oracle (Sections 3.1, 3.2).
+
+Bars: hash, disk points and ray directions bit-exact; visibility (primary
+hit, shadow bit, AO count) disagreeing on at most 1e-4 of all rays, and
+only on rays the oracle flags as within its grazing margin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import paper_2406_06963_b300 as dhrs
+import workloads as wl
+from gpu_util import compare_trace, gpu_params, trace_gpu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def boxes():
+    s = wl.scene_boxes()
+    return s, dhrs.Scene(s), orc.Scene(s)
+
+
+@pytest.fixture(scope="module")
+def terrain():
+    s = wl.scene_terrain()
+    return s, dhrs.Scene(s), orc.Scene(s)
+
+
+def test_sample_directions_bit_exact():
+    """Hash, disk rejection, ONB, cosine and cone directions: the CUDA
+    functions and the oracle give identical bits on a 256^2 x 4 grid."""
+    r = np.random.default_rng(0)
+    ys, xs = np.mgrid[0:256, 0:256]
+    px = xs.ravel().astype(np.uint32)
+    py = ys.ravel().astype(np.uint32)
+    n = r.normal(size=(len(px), 3))
+    n = (n / np.linalg.norm(n, axis=1, keepdims=True)).astype(np.float32)
+    n[:7] = [[0, 0, 1], [0, 0, -1], [0, 1, 0], [1, 0, 0], [0, -1, 0], [-1, 0, 0], [0.6, 0, -0.8]]
+    light = (np.array([0.3, 1.0, 0.2]) / np.linalg.norm([0.3, 1.0, 0.2])).astype(np.float32)
+    for frame, seed in ((0, 0), (17, 12345)):
+        for sample in range(4):
+            for deg in (0.5, 10.0):
+                ang = math.radians(deg)
+                ref = orc.sample_batch(px, py, frame, seed, sample, n, light, orc.tan_f32(ang))
+                out = dhrs.sample_directions(torch.from_numpy(px.view(np.int32)).cuda(),
+                                             torch.from_numpy(py.view(np.int32)).cuda(), frame, seed,
+                                             sample, torch.from_numpy(n).cuda(),
+                                             torch.from_numpy(light).cuda(), ang)
+                for k in ("disk_ao", "dir_ao", "disk_sh", "dir_sh"):
+                    g = out[k].cpu().numpy()
+                    assert np.array_equal(g.view(np.uint32), ref[k].view(np.uint32)), (k, frame, sample, deg)
+
+
+def _check(res, max_frac=1e-4):
+    assert res["primary_unexplained"] == 0, res
+    assert res["shadow_unexplained"] == 0, res
+    assert res["ao_unexplained"] == 0, res
+    assert res["disagree_frac"] <= max_frac, res
+    assert res["depth_rel_max"] < 2e-5, res
+    assert res["normal_abs_max"] < 2e-5, res
+
+
+@pytest.mark.parametrize("frame,lights,spp", [(0, 1, 1), (1, 1, 1), (7, 3, 8)])
+def test_trace_boxes_full_frame(boxes, frame, lights, spp):
+    """256x256, 194 triangles: every pixel and ray against the oracle."""
+    s, g_scene, o_scene = boxes
+    cam = wl.boxes_camera(256, 256)
+    dirs = [(0.3, 1.0, 0.2), (-0.5, 0.8, 0.1), (0.1, 0.6, -0.7)][:lights]
+    tp = orc.TraceParams(light_dirs=dirs, cone_half_angle_deg=[0.5, 3.0, 8.0][:lights], ao_spp=spp,
+                         frame=frame)
+    ref = orc.trace(o_scene, cam, tp)
+    gpu = trace_gpu(g_scene, cam, gpu_params(tp))
+    res = compare_trace(gpu, ref, np.arange(256 * 256), lights, spp)
+    _check(res)
+
+
+@pytest.mark.parametrize("w,h", [(37, 23), (1, 1), (17, 129), (300, 7)])
+def test_trace_ragged_sizes(boxes, w, h):
+    s, g_scene, o_scene = boxes
+    cam = wl.look_at((1.0, 5.0, 9.0), (0.0, 0.5, 0.0), w, h)
+    tp = orc.TraceParams(ao_spp=4, frame=3)
+    ref = orc.trace(o_scene, cam, tp)
+    gpu = trace_gpu(g_scene, cam, gpu_params(tp))
+    _check(compare_trace(gpu, ref, np.arange(w * h), 1, 4), max_frac=1.0)
+
+
+def test_trace_terrain_1080p_sampled(terrain):
+    """1920x1080, 776,050 triangles, the configuration bench.py times: the
+    full GPU frame against 1024 seeded pixels traced one by one by the
+    oracle.  Every disagreement must be a grazing ray."""
+    s, g_scene, o_scene = terrain
+    info = g_scene.info()
+    assert info["n_triangles"] == 776050 and info["n_nodes"] == 776049
+    assert 0 < info["height"] < 64
+    cams = wl.spline_path(s["terrain"], 60, 1920, 1080)
+    r = np.random.default_rng(42)
+    tot = None
+    for f in (0, 37):
+        tp = orc.TraceParams(frame=f)
+        gpu = trace_gpu(g_scene, cams[f], gpu_params(tp))
+        pix = np.stack([r.integers(0, 1920, 512), r.integers(0, 1080, 512)], -1)
+        ref = orc.trace(o_scene, cams[f], tp, pixels=pix)
+        res = compare_trace(gpu, ref, pix[:, 1] * 1920 + pix[:, 0], 1, 1)
+        _check(res, max_frac=1.0)
+        tot = res if tot is None else {k: tot[k] + res[k] for k in res}
+    # at most a handful of grazing disagreements among ~3000 rays
+    assert tot["disagree"] <= 3, tot
+
+
+def test_cast_rays_matches_brute_force(boxes):
+    s, g_scene, o_scene = boxes
+    r = np.random.default_rng(5)
+    n = 4000
+    o = np.concatenate([r.uniform(-6, 6, (n, 1)), r.uniform(0.05, 4, (n, 1)), r.uniform(-6, 6, (n, 1))], 1)
+    d = r.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o32, d32 = o.astype(np.float32), d.astype(np.float32)
+    tmin = np.zeros(n, np.float32)
+    tmax = np.full(n, np.inf, np.float32)
+    tmax[::2] = 1.5
+    for any_hit in (False, True):
+        t, tri = dhrs.cast_rays(g_scene, torch.from_numpy(o32).cuda(), torch.from_numpy(d32).cuda(),
+                                torch.from_numpy(tmin).cuda(), torch.from_numpy(tmax).cuda(), any_hit)
+        t, tri = t.cpu().numpy(), tri.cpu().numpy()
+        bad = 0
+        for i in range(n):
+            ref = orc.cast(o_scene, o32[i].astype(float), d32[i].astype(float), 0.0, float(tmax[i]),
+                           any_hit=any_hit)
+            if ref["ambiguous"]:
+                continue
+            assert (tri[i] >= 0) == ref["hit"], (i, ref, tri[i])
+            if ref["hit"] and not any_hit:
+                bad += tri[i] != ref["tri"]
+                assert abs(t[i] - ref["t"]) <= 1e-5 * max(1.0, ref["t"]), (i, t[i], ref)
+        assert bad == 0
+
+
+def test_trace_empty_and_single_triangle():
+    cam = wl.look_at((0, 2, 3), (0, 0, 0), 40, 30)
+    empty = dict(vertices=np.zeros((0, 3), np.float32), indices=np.zeros((0, 3), np.uint32),
+                 mesh_ids=np.zeros(0, np.uint32))
+    sc = dhrs.Scene(empty)
+    gpu = trace_gpu(sc, cam, dhrs.TraceParams(ao_spp=3))
+    assert (gpu["mesh"] == 0xFFFFFFFF).all() and np.isinf(gpu["depth"]).all()
+    assert (gpu["ao_count"] == 3).all() and (gpu["shadow_mask"] == 1).all()
+    one = wl.scene_quad([[-1, 0, -1], [-1, 0, 1], [1, 0, 1], [1, 0, -1]], 9)
+    one = dict(vertices=one["vertices"], indices=one["indices"][:1], mesh_ids=one["mesh_ids"][:1])
+    tp = orc.TraceParams(ao_spp=2)
+    ref = orc.trace(orc.Scene(one), cam, tp)
+    gpu = trace_gpu(dhrs.Scene(one), cam, gpu_params(tp))
+    _check(compare_trace(gpu, ref, np.arange(40 * 30), 1, 2), max_frac=1.0)
+
+
+def test_trace_degenerate_triangles(boxes):
+    """Zero-area triangles (repeated and collinear vertices) never hit."""
+    s = wl.scene_boxes()
+    v = np.concatenate([s["vertices"], np.array([[0, 1, 0], [1, 1, 0], [2, 1, 0]], np.float32)])
+    k = len(s["vertices"])
+    idx = np.concatenate([s["indices"], np.array([[k, k, k], [k, k + 1, k + 2]], np.uint32)])
+    mesh = np.concatenate([s["mesh_ids"], np.array([99, 99], np.uint32)])
+    sc = dict(vertices=v, indices=idx, mesh_ids=mesh)
+    cam = wl.boxes_camera(128, 128)
+    tp = orc.TraceParams(ao_spp=2)
+    ref = orc.trace(orc.Scene(sc), cam, tp)
+    gpu = trace_gpu(dhrs.Scene(sc), cam, gpu_params(tp))
+    assert not (gpu["mesh"] == 99).any()
+    _check(compare_trace(gpu, ref, np.arange(128 * 128), 1, 2), max_frac=1e-3)
+
+
+def test_invalid_arguments_are_rejected(boxes):
+    s, g_scene, _ = boxes
+    cam = wl.boxes_camera(16, 16)
+    g = dhrs.GBuffer(16, 16)
+    m = torch.empty((16, 16), dtype=torch.uint8, device="cuda")
+    a = torch.empty_like(m)
+    for bad in (dict(ao_spp=0), dict(ao_spp=256), dict(ao_radius=0.0), dict(cone_half_angle_deg=[95.0])):
+        with pytest.raises(dhrs.DhrError) as e:
+            dhrs.trace_visibility(g_scene, cam, dhrs.TraceParams(**bad), g, m, a)
+        assert e.value.status == 1
+    with pytest.raises(dhrs.DhrError):
+        dhrs.trace_visibility(g_scene, wl.boxes_camera(17, 16), dhrs.TraceParams(), g, m, a)
+    bad_idx = dict(vertices=np.zeros((3, 3), np.float32), indices=np.array([[0, 1, 5]], np.uint32),
+                   mesh_ids=np.zeros(1, np.uint32))
+    with pytest.raises(dhrs.DhrError):
+        dhrs.Scene(bad_idx)
