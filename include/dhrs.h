@@ -127,7 +127,7 @@ typedef struct dhr_svgf_state dhr_svgf_state;
 
 /* Device views of an SVGF state's buffers (owned by the state). */
 typedef struct {
-    void* illum;        /* FP32: float4 [W*H] temporal colour AO, shadow, variance AO, shadow */
+    void* illum;        /* float4 [W*H] temporal colour AO, shadow, variance AO, shadow (variance -1 on background) */
     void* moments;      /* FP32: float4 [W*H] mu1 AO, mu1 shadow, mu2 AO, mu2 shadow (current) */
     void* color_hist;   /* FP32: float2 [W*H] colour history for the next frame */
     uint8_t* histlen;   /* [W*H] history length n (current) */

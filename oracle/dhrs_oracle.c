@@ -776,26 +776,30 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
                                            zn_prev, mesh_prev, hist_in);
                 if (r.valid) {
                     valid = 1;
+                    /* weighted mean over the valid taps: (sum w v) / (sum w) */
                     double sw = 0.0;
-                    for (int k = 0; k < 4; ++k) if (r.ok[k]) sw += (double)r.w[k];
                     for (int k = 0; k < 4; ++k) {
                         if (!r.ok[k]) continue;
                         int64_t q = (int64_t)r.ty[k] * W + r.tx[k];
-                        double w = (double)r.w[k] / sw;
+                        double w = (double)r.w[k];
+                        sw += w;
                         ch[0] += w * col_hist[2 * q]; ch[1] += w * col_hist[2 * q + 1];
                         for (int c = 0; c < 4; ++c) mh[c] += w * mom_in[4 * q + c];
                     }
+                    ch[0] /= sw; ch[1] /= sw;
+                    for (int c = 0; c < 4; ++c) mh[c] /= sw;
                     n = r.histlen_min + 1;
                     if (n > 255) n = 255;
                 }
             }
             if (valid_out) valid_out[p] = valid;
             double a = valid ? (P->fixed_alpha ? P->alpha : fmax(P->alpha, 1.0 / n)) : 1.0;
+            /* exponential moving average, written h + a (s - h) */
             double c[2], m[4];
             for (int k = 0; k < 2; ++k) {
-                c[k] = (1.0 - a) * ch[k] + a * s[k];
-                m[k] = (1.0 - a) * mh[k] + a * s[k];
-                m[2 + k] = (1.0 - a) * mh[2 + k] + a * s[k] * s[k];
+                c[k] = ch[k] + a * (s[k] - ch[k]);
+                m[k] = mh[k] + a * (s[k] - mh[k]);
+                m[2 + k] = mh[2 + k] + a * (s[k] * s[k] - mh[2 + k]);
             }
             for (int k = 0; k < 4; ++k) mom_out[4 * p + k] = m[k];
             hist_out[p] = n;

@@ -71,15 +71,26 @@ struct SvgfConsts {
     float alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
     float inv_spp;
     int fixed_alpha, wl_in_atrous;
+    int sigma_n_int;    // sigma_n when it is an integer in 1..1024, else 0
 };
 
 __device__ __forceinline__ bool is_fg(float z) { return z < INFINITY; }
 
-// max(0, c)^sigma_n with 0^0 = 1
-__device__ __forceinline__ float pow_normal(float c, float sigma_n) {
+// max(0, c)^sigma_n with 0^0 = 1.  Integer exponents up to 1024 (the usual
+// case, e.g. 128) use repeated squaring: a few multiplies and relative error
+// ~1e-6, where exp2(sigma_n log2 c) would amplify the log2 error sigma_n-fold.
+__device__ __forceinline__ float pow_normal(float c, float sigma_n, int int_exp) {
     if (sigma_n == 0.0f) return 1.0f;
     c = fmaxf(c, 0.0f);
-    return c > 0.0f ? exp2f(sigma_n * __log2f(c)) : 0.0f;
+    if (int_exp > 0) {
+        float r = 1.0f, b = c;
+        for (int e = int_exp; e; e >>= 1) {
+            if (e & 1) r *= b;
+            b *= b;
+        }
+        return r;
+    }
+    return c > 0.0f ? exp2f(sigma_n * log2f(c)) : 0.0f;
 }
 
 __device__ __forceinline__ float w_depth(float zp, float zq, float2 g, float ox, float oy, float sz, float ez) {
@@ -184,6 +195,13 @@ __device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera&
     return sumw >= 1e-4f;
 }
 
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Background pixels carry variance -1 in the illum buffers (a sentinel
+// that lets the a-trous passes test membership from the buffer they read).
+__device__ __forceinline__ bool fg_var(float v) { return v >= 0.0f; }
+
 template <dhr_precision P>
 __global__ void __launch_bounds__(256) temporal_kernel(
     SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const typename Store<P>::G* g_cur,
@@ -192,32 +210,32 @@ __global__ void __launch_bounds__(256) temporal_kernel(
     const typename Store<P>::Mom* mom_in, const uint8_t* hist_in, typename Store<P>::Mom* mom_out,
     uint8_t* hist_out, float4* illum) {
     using S = Store<P>;
+    // one warp = 32 consecutive pixels of a row; every lane stays to the end
+    // because the short-history estimate below is computed by the whole warp
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= k.W || y >= k.H) return;
-    const size_t p = (size_t)y * k.W + x;
-    const float4 zn = S::g(g_cur, p);
-    if (!is_fg(zn.x)) {
-        illum[p] = make_float4(1.f, 1.f, 0.f, 0.f);
-        S::put_mom(mom_out, p, make_float4(1.f, 1.f, 1.f, 1.f));
-        hist_out[p] = 0;
-        return;
-    }
-    const float2 s = noisy(mask, ao, p, k.inv_spp);
-    float2 ch = make_float2(0.f, 0.f);
-    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31;
+    const bool inside = x < k.W && y < k.H;
+    const size_t p = inside ? (size_t)y * k.W + x : 0;
+    float4 zn = make_float4(INFINITY, 0.f, 0.f, 0.f);
+    if (inside) zn = S::g(g_cur, p);
+    const bool fg = inside && is_fg(zn.x);
     int n = 1;
-    bool valid = false;
-    if (g_prev) {
+    if (fg) {
+        const float2 s = noisy(mask, ao, p, k.inv_spp);
+        float2 ch = make_float2(0.f, 0.f);
+        float4 mh = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool valid = false;
         Reproj r;
-        if (reproject<S>(cam, cam_prev, k.W, k.H, x, y, zn, __ldg(mesh_cur + p), g_prev, mesh_prev, r)) {
+        if (g_prev && reproject<S>(cam, cam_prev, k.W, k.H, x, y, zn, __ldg(mesh_cur + p), g_prev, mesh_prev, r)) {
+            // weighted mean of the valid taps as (sum w v) / (sum w), summed in the
+            // same order as sum w so that a constant history stays exactly constant
             valid = true;
-            const float inv = 1.0f / r.sumw;
             int hmin = 255;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 if (!(r.ok & (1 << t))) continue;
                 const size_t q = (size_t)(r.y0 + (t >> 1)) * k.W + (r.x0 + (t & 1));
-                const float w = r.w[t] * inv;
+                const float w = r.w[t];
                 const float2 c = S::col(col_hist, q);
                 const float4 m = S::mom(mom_in, q);
                 ch.x = fmaf(w, c.x, ch.x);
@@ -228,53 +246,91 @@ __global__ void __launch_bounds__(256) temporal_kernel(
                 mh.w = fmaf(w, m.w, mh.w);
                 hmin = min(hmin, (int)__ldg(hist_in + q));
             }
+            ch = make_float2(ch.x / r.sumw, ch.y / r.sumw);
+            mh = make_float4(mh.x / r.sumw, mh.y / r.sumw, mh.z / r.sumw, mh.w / r.sumw);
             n = min(hmin + 1, 255);
         }
+        const float a = valid ? (k.fixed_alpha ? k.alpha : fmaxf(k.alpha, 1.0f / (float)n)) : 1.0f;
+        // exponential moving average written h + a (s - h)
+        const float2 c = make_float2(fmaf(a, s.x - ch.x, ch.x), fmaf(a, s.y - ch.y, ch.y));
+        const float4 m = make_float4(fmaf(a, s.x - mh.x, mh.x), fmaf(a, s.y - mh.y, mh.y),
+                                     fmaf(a, s.x * s.x - mh.z, mh.z), fmaf(a, s.y * s.y - mh.w, mh.w));
+        S::put_mom(mom_out, p, m);
+        hist_out[p] = (uint8_t)n;
+        if (n >= 4)
+            illum[p] = make_float4(c.x, c.y, fmaxf(0.f, m.z - m.x * m.x), fmaxf(0.f, m.w - m.y * m.y));
+    } else if (inside) {
+        illum[p] = make_float4(1.f, 1.f, -1.f, -1.f);
+        S::put_mom(mom_out, p, make_float4(1.f, 1.f, 1.f, 1.f));
+        hist_out[p] = 0;
     }
-    const float a = valid ? (k.fixed_alpha ? k.alpha : fmaxf(k.alpha, 1.0f / (float)n)) : 1.0f;
-    const float b = 1.0f - a;
-    const float2 c = make_float2(b * ch.x + a * s.x, b * ch.y + a * s.y);
-    const float4 m = make_float4(b * mh.x + a * s.x, b * mh.y + a * s.y, b * mh.z + a * s.x * s.x,
-                                 b * mh.w + a * s.y * s.y);
-    S::put_mom(mom_out, p, m);
-    hist_out[p] = (uint8_t)n;
-    if (n >= 4) {
-        illum[p] = make_float4(c.x, c.y, fmaxf(0.f, m.z - m.x * m.x), fmaxf(0.f, m.w - m.y * m.y));
-        return;
-    }
-    // short history: 7x7 spatial estimate weighted by depth and normal only
-    const float2 gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
-    float sw = 0.f;
-    float2 s1 = make_float2(0.f, 0.f), s2 = make_float2(0.f, 0.f);
-    for (int dy = -3; dy <= 3; ++dy) {
-        const int qy = y + dy;
-        if (qy < 0 || qy >= k.H) continue;
-        for (int dx = -3; dx <= 3; ++dx) {
-            const int qx = x + dx;
-            if (qx < 0 || qx >= k.W) continue;
+    // short history (n < 4): 7x7 spatial estimate of the current frame's
+    // signal weighted by depth and normal only.  The lanes that need it are
+    // served one after another by the whole warp: lane l takes taps l and
+    // l + 32 of the 49, then the sums are reduced across the warp.
+    const bool need = fg && n < 4;
+    float2 gz = make_float2(0.f, 0.f);
+    if (need) gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
+    unsigned todo = __ballot_sync(kFull, need);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int px = __shfl_sync(kFull, x, src), py = __shfl_sync(kFull, y, src);
+        const float zp = __shfl_sync(kFull, zn.x, src);
+        const float nx = __shfl_sync(kFull, zn.y, src), ny = __shfl_sync(kFull, zn.z, src),
+                    nz = __shfl_sync(kFull, zn.w, src);
+        const float gx = __shfl_sync(kFull, gz.x, src), gy = __shfl_sync(kFull, gz.y, src);
+        float sw = 0.f, a1 = 0.f, b1 = 0.f, a2 = 0.f, b2 = 0.f;
+        for (int t = lane; t < 49; t += 32) {
+            const int dx = t % 7 - 3, dy = t / 7 - 3;
+            const int qx = px + dx, qy = py + dy;
+            if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
             const size_t q = (size_t)qy * k.W + qx;
             const float4 zq = S::g(g_cur, q);
             if (!is_fg(zq.x)) continue;
             float w = 1.0f;
             if (dx || dy)
-                w = w_depth(zn.x, zq.x, gz, (float)-dx, (float)-dy, k.sigma_z, k.eps_z) *
-                    pow_normal(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
+                w = w_depth(zp, zq.x, make_float2(gx, gy), (float)-dx, (float)-dy, k.sigma_z, k.eps_z) *
+                    pow_normal(nx * zq.y + ny * zq.z + nz * zq.w, k.sigma_n, k.sigma_n_int);
             const float2 sq = noisy(mask, ao, q, k.inv_spp);
             sw += w;
-            s1.x = fmaf(w, sq.x, s1.x);
-            s1.y = fmaf(w, sq.y, s1.y);
-            s2.x = fmaf(w, sq.x * sq.x, s2.x);
-            s2.y = fmaf(w, sq.y * sq.y, s2.y);
+            a1 = fmaf(w, sq.x, a1);
+            b1 = fmaf(w, sq.y, b1);
+            a2 = fmaf(w, sq.x * sq.x, a2);
+            b2 = fmaf(w, sq.y * sq.y, b2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sw += __shfl_xor_sync(kFull, sw, o);
+            a1 += __shfl_xor_sync(kFull, a1, o);
+            b1 += __shfl_xor_sync(kFull, b1, o);
+            a2 += __shfl_xor_sync(kFull, a2, o);
+            b2 += __shfl_xor_sync(kFull, b2, o);
+        }
+        if (lane == src) {
+            const float m1x = a1 / sw, m1y = b1 / sw;
+            illum[p] = make_float4(m1x, m1y, fmaxf(0.f, a2 / sw - m1x * m1x), fmaxf(0.f, b2 / sw - m1y * m1y));
         }
     }
-    const float iw = 1.0f / sw;
-    const float m1x = s1.x * iw, m1y = s1.y * iw;
-    illum[p] = make_float4(m1x, m1y, fmaxf(0.f, s2.x * iw - m1x * m1x), fmaxf(0.f, s2.y * iw - m1y * m1y));
+}
+
+// max(0, c)^sigma_n for the a-trous taps: 2^kNsq by kNsq squarings, or the
+// generic path (kNsq < 0)
+template <int kNsq>
+__device__ __forceinline__ float pow_n(float c, float sigma_n, int sigma_n_int) {
+    if (kNsq >= 0) {
+        float r = fmaxf(c, 0.0f);
+#pragma unroll
+        for (int i = 0; i < kNsq; ++i) r *= r;
+        return r;
+    }
+    return pow_normal(c, sigma_n, sigma_n_int);
 }
 
 // one a-trous iteration; kMode 0: write illum_out; 1: also colour history;
-// 2: last iteration, write the two output planes only
-template <dhr_precision P, int kMode>
+// 2: last iteration, write the two output planes only.  kNsq >= 0: sigma_n
+// is 2^kNsq.
+template <dhr_precision P, int kMode, int kNsq>
 __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
                                                      const float4* in, float4* out,
                                                      typename Store<P>::Col* col_hist, float* ao_out,
@@ -282,19 +338,19 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
     using S = Store<P>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= k.W || y >= k.H) return;
-    const size_t p = (size_t)y * k.W + x;
-    const float4 zn = S::g(g, p);
-    if (!is_fg(zn.x)) {
+    const int p = y * k.W + x;
+    const float4 cp = __ldg(in + p);
+    if (!fg_var(cp.z)) {
         if (kMode == 2) {
             ao_out[p] = 1.f;
             sh_out[p] = 1.f;
         } else {
-            out[p] = make_float4(1.f, 1.f, 0.f, 0.f);
+            out[p] = make_float4(1.f, 1.f, -1.f, -1.f);
             if (kMode == 1) S::put_col(col_hist, p, make_float2(1.f, 1.f));
         }
         return;
     }
-    const float4 cp = __ldg(in + p);
+    const float4 zn = S::g(g, p);
     // 3x3 Gaussian of the variance, renormalised over foreground taps
     float gv0 = 0.f, gv1 = 0.f, gw = 0.f;
 #pragma unroll
@@ -303,18 +359,27 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
         for (int dx = -1; dx <= 1; ++dx) {
             const int qx = x + dx, qy = y + dy;
             if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-            const size_t q = (size_t)qy * k.W + qx;
-            if (!is_fg(S::g(g, q).x)) continue;
+            const float4 v = __ldg(in + (qy * k.W + qx));
+            if (!fg_var(v.z)) continue;
             const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
-            const float4 v = __ldg(in + q);
             gw += kk;
             gv0 = fmaf(kk, v.z, gv0);
             gv1 = fmaf(kk, v.w, gv1);
         }
     }
-    const float il0 = k.wl_in_atrous ? 1.0f / (k.sigma_l * sqrtf(fmaxf(0.f, gv0 / gw)) + k.eps_l) : 0.f;
-    const float il1 = k.wl_in_atrous ? 1.0f / (k.sigma_l * sqrtf(fmaxf(0.f, gv1 / gw)) + k.eps_l) : 0.f;
+    // luminance terms folded with log2(e): w_l = 2^(-|dc| il)
+    const float il0 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv0 / gw) + k.eps_l) : 0.f;
+    const float il1 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv1 / gw) + k.eps_l) : 0.f;
+    // depth terms: log2(e) / (sigma_z |grad z . (p - q)| + eps_z) for the 12
+    // offset directions (i, j) ~ (-i, -j) of the 5x5 footprint
     const float2 gz = depth_grad<S>(g, k.W, k.H, x, y, zn.x);
+    const float sg = k.sigma_z * (float)step;
+    float rz[13];
+#pragma unroll
+    for (int t = 0; t < 13; ++t) {
+        const int i = t % 5 - 2, j = t / 5 - 2;      // t = 0..12 covers j < 0, and j = 0, i < 0 (t = 10, 11) + centre (12)
+        rz[t] = __fdividef(kLog2e, fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
+    }
     const float kc = 0.375f * 0.375f;
     float sw0 = kc, sw1 = kc;
     float sc0 = kc * cp.x, sc1 = kc * cp.y;
@@ -329,15 +394,16 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
             if (i == 0 && j == 0) continue;
             const int qx = x + i * step;
             if (qx < 0 || qx >= k.W) continue;
-            const size_t q = (size_t)qy * k.W + qx;
-            const float4 zq = S::g(g, q);
-            if (!is_fg(zq.x)) continue;
+            const int q = qy * k.W + qx;
             const float4 cq = __ldg(in + q);
-            const float wzn = h5[i + 2] * h5[j + 2] *
-                              w_depth(zn.x, zq.x, gz, (float)(-i * step), (float)(-j * step), k.sigma_z, k.eps_z) *
-                              pow_normal(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
-            const float w0 = wzn * __expf(-fabsf(cp.x - cq.x) * il0);
-            const float w1 = wzn * __expf(-fabsf(cp.y - cq.y) * il1);
+            if (!fg_var(cq.z)) continue;
+            const float4 zq = S::g(g, q);
+            const int t = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
+            const float ez = fabsf(zn.x - zq.x) * rz[t];
+            const float kw = h5[i + 2] * h5[j + 2] *
+                             pow_n<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n, k.sigma_n_int);
+            const float w0 = kw * exp2f(-fmaf(fabsf(cp.x - cq.x), il0, ez));
+            const float w1 = kw * exp2f(-fmaf(fabsf(cp.y - cq.y), il1, ez));
             sw0 += w0;
             sw1 += w1;
             sc0 = fmaf(w0, cq.x, sc0);
@@ -346,13 +412,13 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
             sv1 = fmaf(w1 * w1, cq.w, sv1);
         }
     }
-    const float i0 = 1.0f / sw0, i1 = 1.0f / sw1;
-    const float c0 = sc0 * i0, c1 = sc1 * i1;
+    // (sum w c) / (sum w): a constant neighbourhood stays exactly constant
+    const float c0 = sc0 / sw0, c1 = sc1 / sw1;
     if (kMode == 2) {
         ao_out[p] = c0;
         sh_out[p] = c1;
     } else {
-        out[p] = make_float4(c0, c1, sv0 * i0 * i0, sv1 * i1 * i1);
+        out[p] = make_float4(c0, c1, sv0 / (sw0 * sw0), sv1 / (sw1 * sw1));
         if (kMode == 1) S::put_col(col_hist, p, make_float2(c0, c1));
     }
 }
@@ -440,6 +506,30 @@ dhr_status check_svgf_params(const dhr_svgf_params* p) {
     return DHR_OK;
 }
 
+template <dhr_precision P, int kMode>
+static void launch_atrous_mode(int nsq, dim3 grid, dim3 blk, cudaStream_t st, const SvgfConsts& k, int step,
+                               const typename Store<P>::G* g, const float4* in, float4* out,
+                               typename Store<P>::Col* col, float* ao_out, float* sh_out) {
+    if (nsq == 7)
+        atrous_kernel<P, kMode, 7><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
+    else
+        atrous_kernel<P, kMode, -1><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
+}
+
+template <dhr_precision P>
+static dhr_status launch_atrous(int mode, int nsq, dim3 grid, dim3 blk, cudaStream_t st, const SvgfConsts& k,
+                                int step, const typename Store<P>::G* g, const float4* in, float4* out,
+                                typename Store<P>::Col* col, float* ao_out, float* sh_out) {
+    if (mode == 2)
+        launch_atrous_mode<P, 2>(nsq, grid, blk, st, k, step, g, in, nullptr, nullptr, ao_out, sh_out);
+    else if (mode == 1)
+        launch_atrous_mode<P, 1>(nsq, grid, blk, st, k, step, g, in, out, col, nullptr, nullptr);
+    else
+        launch_atrous_mode<P, 0>(nsq, grid, blk, st, k, step, g, in, out, nullptr, nullptr, nullptr);
+    DHR_CUDA_TRY(cudaGetLastError());
+    return DHR_OK;
+}
+
 template <dhr_precision P>
 static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev,
                            const dhr_camera* cam, const dhr_camera* cam_prev, const uint8_t* mask,
@@ -458,6 +548,8 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
     k.inv_spp = 1.0f / (float)prm->ao_spp;
     k.fixed_alpha = (int)prm->fixed_alpha;
     k.wl_in_atrous = (int)prm->wl_in_atrous;
+    k.sigma_n_int = (prm->sigma_n >= 1.0f && prm->sigma_n <= 1024.0f && prm->sigma_n == floorf(prm->sigma_n))
+                        ? (int)prm->sigma_n : 0;
     const int src = s->cur, dst = s->cur ^ 1;
     const dim3 blk(32, 8), grid((s->w + 31) / 32, (s->h + 7) / 8);
     const auto* gc = static_cast<const typename S::G*>(cur->depth_normal);
@@ -477,23 +569,18 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
         return DHR_OK;
     }
     const float4* in = s->illum;
+    const int nsq = (prm->sigma_n == 128.0f) ? 7 : -1;
     for (int l = 0; l < L; ++l) {
         float4* out = s->pp[l & 1];
         const int step = 1 << l;
-        if (l == L - 1 && L == 1) {
+        const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
+        DHR_TRY(launch_atrous<P>(mode, nsq, grid, blk, st, k, step, gc, in, out, col, ao_out, sh_out));
+        if (L == 1) {
             // single iteration: it is both the history source and the output
-            atrous_kernel<P, 1><<<grid, blk, 0, st>>>(k, step, gc, in, out, col, nullptr, nullptr);
-            DHR_CUDA_TRY(cudaGetLastError());
             passthrough_kernel<P><<<(s->w * s->h + 255) / 256, 256, 0, st>>>(s->w * s->h, out, col, ao_out,
                                                                              sh_out);
-        } else if (l == L - 1) {
-            atrous_kernel<P, 2><<<grid, blk, 0, st>>>(k, step, gc, in, nullptr, nullptr, ao_out, sh_out);
-        } else if (l == 0) {
-            atrous_kernel<P, 1><<<grid, blk, 0, st>>>(k, step, gc, in, out, col, nullptr, nullptr);
-        } else {
-            atrous_kernel<P, 0><<<grid, blk, 0, st>>>(k, step, gc, in, out, nullptr, nullptr, nullptr);
+            DHR_CUDA_TRY(cudaGetLastError());
         }
-        DHR_CUDA_TRY(cudaGetLastError());
         in = out;
     }
     return DHR_OK;

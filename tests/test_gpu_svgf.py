@@ -54,8 +54,11 @@ def _run_both(frames, cams, op: "orc.SvgfParams", precision=dhrs.DHR_FP32, check
             hist = dhrs.device_copy(b["histlen"], (H, W), "uint8").cpu().numpy()
             assert np.array_equal(hist.astype(np.int32), np.where(fg, ost.hist, 0)), f
             illum = dhrs.device_copy(b["illum"], (H, W, 4), "float32").cpu().numpy()
-            assert np.abs(illum - ref["illum"])[fg].max() < 1e-4, f
+            # the temporal colour carries last frame's level-0 colour, so it
+            # inherits that pass's binary32 accumulation error
+            assert np.abs(illum - ref["illum"])[fg].max() < 5e-4, f
         prev = (g, cams[f])
+    print(f"svgf parity {W}x{H} x{len(frames)} frames: max |gpu - oracle| = {worst:.3g}")
     return worst
 
 
