@@ -592,7 +592,10 @@ static inline int is_fg(const float* zn, int64_t p) { return isfinite(zn[4 * p])
 
 /* Temporal reprojection decision in binary32 (Section 3.3: back-project the
  * pixel's world position into the previous frame; discard history samples
- * inconsistent in projected depth, normal or mesh id).  The written order of
+ * inconsistent in projected depth, normal or mesh id).  Depth consistency:
+ * |z_prev(q) - z'| <= 0.01 z' + 2 max(|dz/dx|, |dz/dy|), the slope term
+ * covering the one-pixel footprint of a bilinear tap on surfaces seen at
+ * grazing angles.  The written order of
  * operations is the specification shared with the GPU kernel; each
  * intermediate is rounded to binary32.
  * Returns 1 with the four bilinear taps (valid flags and weights, history
@@ -605,9 +608,39 @@ typedef struct {
     int histlen_min;
 } reproj_t;
 
+/* binary32 one-sided depth difference of smaller magnitude along each axis
+ * among the foreground neighbours (0 if none), as used by the history
+ * decision; returns max(|gx|, |gy|). */
+static float depth_slope_f32(int W, int H, const float* zn, int x, int y)
+{
+    int64_t p = (int64_t)y * W + x;
+    float zp = zn[4 * p];
+    float g[2];
+    for (int ax = 0; ax < 2; ++ax) {
+        int has_p = 0, has_m = 0;
+        volatile float dp = 0.0f, dm = 0.0f;
+        int xp = x + (ax == 0), yp = y + (ax == 1);
+        int xm = x - (ax == 0), ym = y - (ax == 1);
+        if (xp < W && yp < H) {
+            int64_t q = (int64_t)yp * W + xp;
+            if (is_fg(zn, q)) { dp = zn[4 * q] - zp; has_p = 1; }
+        }
+        if (xm >= 0 && ym >= 0) {
+            int64_t q = (int64_t)ym * W + xm;
+            if (is_fg(zn, q)) { dm = zp - zn[4 * q]; has_m = 1; }
+        }
+        if (has_p && has_m) g[ax] = (fabsf(dm) < fabsf(dp)) ? dm : dp;
+        else if (has_p) g[ax] = dp;
+        else if (has_m) g[ax] = dm;
+        else g[ax] = 0.0f;
+    }
+    return fmaxf(fabsf(g[0]), fabsf(g[1]));
+}
+
 static reproj_t reproject_f32(int W, int H, int x, int y, const float* znp, uint32_t mp,
                               const orc_camera* cc, const orc_camera* cp,
-                              const float* zn_prev, const uint32_t* mesh_prev, const int32_t* hist)
+                              const float* zn_prev, const uint32_t* mesh_prev, const int32_t* hist,
+                              float slope)
 {
     reproj_t r;
     memset(&r, 0, sizeof(r));
@@ -660,7 +693,10 @@ static reproj_t reproject_f32(int W, int H, int x, int y, const float* znp, uint
     int dxs[4] = {0, 1, 0, 1}, dys[4] = {0, 0, 1, 1};
     volatile float sumw = 0.0f;
     int hmin = 1 << 30;
-    volatile float zlim = 0.01f * zp;
+    /* projected depths agree within 1 % plus two pixels of the local depth slope */
+    volatile float zrel = 0.01f * zp;
+    volatile float zsl = 2.0f * slope;
+    volatile float zlim = zrel + zsl;
     for (int k = 0; k < 4; ++k) {
         int qx2 = x0 + dxs[k], qy2 = y0 + dys[k];
         r.tx[k] = qx2; r.ty[k] = qy2; r.w[k] = wt[k]; r.ok[k] = 0;
@@ -773,7 +809,8 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
             int n = 1, valid = 0;
             if (zn_prev) {
                 reproj_t r = reproject_f32(W, H, x, y, zn + 4 * p, mesh[p], cam, cam_prev,
-                                           zn_prev, mesh_prev, hist_in);
+                                           zn_prev, mesh_prev, hist_in,
+                                           depth_slope_f32(W, H, zn, x, y));
                 if (r.valid) {
                     valid = 1;
                     /* weighted mean over the valid taps: (sum w v) / (sum w) */

@@ -125,7 +125,8 @@ __device__ __forceinline__ float2 noisy(const uint8_t* mask, const uint8_t* ao, 
 
 // Back-projection into the previous frame: the binary32 operation sequence
 // below (each step rounded once, no contraction) decides which history taps
-// are valid; it is the specification shared with the CPU oracle.
+// are valid; it is the specification shared with the CPU oracle.  Depth
+// consistency: |z_prev(q) - z'| <= 0.01 z' + 2 max(|dz/dx|, |dz/dy|).
 struct Reproj {
     int x0, y0;
     float w[4];
@@ -135,7 +136,7 @@ struct Reproj {
 
 template <class S>
 __device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera& p, int W, int H, int x, int y,
-                                          float4 znp, uint32_t mp, const typename S::G* g_prev,
+                                          float4 znp, uint32_t mp, float slope, const typename S::G* g_prev,
                                           const uint32_t* mesh_prev, Reproj& r) {
     const float Wf = (float)W, Hf = (float)H;
     const float aspect = __fdiv_rn(Wf, Hf);
@@ -174,7 +175,8 @@ __device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera&
     r.w[3] = __fmul_rn(ax, ay);
     r.x0 = (int)x0f;
     r.y0 = (int)y0f;
-    const float zlim = __fmul_rn(0.01f, zp);
+    // projected depths agree within 1 % plus two pixels of the local depth slope
+    const float zlim = __fadd_rn(__fmul_rn(0.01f, zp), __fmul_rn(2.0f, slope));
     float sumw = 0.0f;
     int ok = 0;
 #pragma unroll
@@ -220,13 +222,17 @@ __global__ void __launch_bounds__(256) temporal_kernel(
     if (inside) zn = S::g(g_cur, p);
     const bool fg = inside && is_fg(zn.x);
     int n = 1;
+    float2 gz = make_float2(0.f, 0.f);
     if (fg) {
         const float2 s = noisy(mask, ao, p, k.inv_spp);
         float2 ch = make_float2(0.f, 0.f);
         float4 mh = make_float4(0.f, 0.f, 0.f, 0.f);
         bool valid = false;
         Reproj r;
-        if (g_prev && reproject<S>(cam, cam_prev, k.W, k.H, x, y, zn, __ldg(mesh_cur + p), g_prev, mesh_prev, r)) {
+        gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
+        const float slope = fmaxf(fabsf(gz.x), fabsf(gz.y));
+        if (g_prev &&
+            reproject<S>(cam, cam_prev, k.W, k.H, x, y, zn, __ldg(mesh_cur + p), slope, g_prev, mesh_prev, r)) {
             // weighted mean of the valid taps as (sum w v) / (sum w), summed in the
             // same order as sum w so that a constant history stays exactly constant
             valid = true;
@@ -269,8 +275,6 @@ __global__ void __launch_bounds__(256) temporal_kernel(
     // served one after another by the whole warp: lane l takes taps l and
     // l + 32 of the 49, then the sums are reduced across the warp.
     const bool need = fg && n < 4;
-    float2 gz = make_float2(0.f, 0.f);
-    if (need) gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
     unsigned todo = __ballot_sync(kFull, need);
     while (todo) {
         const int src = __ffs(todo) - 1;
@@ -327,6 +331,54 @@ __device__ __forceinline__ float pow_n(float c, float sigma_n, int sigma_n_int) 
     return pow_normal(c, sigma_n, sigma_n_int);
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct Acc {
+    float sw0, sw1, sc0, sc1, sv0, sv1;
+};
+
+// The 24 non-centre taps of one a-trous iteration.  Background taps (depth
+// +inf, variance sentinel -1) get weight 0 without a branch.
+template <class S, int kNsq, bool kCheck>
+__device__ __forceinline__ void atrous_taps(const SvgfConsts& k, int step, int x, int y, float4 zn, float4 cp,
+                                            float il0, float il1, const float (&rz)[13],
+                                            const typename S::G* g, const float4* in, Acc& a) {
+    const float h5[5] = {1.f / 16, 1.f / 4, 3.f / 8, 1.f / 4, 1.f / 16};
+#pragma unroll
+    for (int j = -2; j <= 2; ++j) {
+        const int qy = y + j * step;
+        if (kCheck && (qy < 0 || qy >= k.H)) continue;
+#pragma unroll
+        for (int i = -2; i <= 2; ++i) {
+            if (i == 0 && j == 0) continue;
+            const int qx = x + i * step;
+            if (kCheck && (qx < 0 || qx >= k.W)) continue;
+            const int q = qy * k.W + qx;
+            const float4 cq = __ldg(in + q);
+            const float4 zq = S::g(g, q);
+            const int t = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
+            const float ez = fabsf(zn.x - zq.x) * rz[t];
+            float kw = h5[i + 2] * h5[j + 2] *
+                       pow_n<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n, k.sigma_n_int);
+            kw = fg_var(cq.z) ? kw : 0.0f;
+            float w0 = kw * ex2_approx(-fmaf(fabsf(cp.x - cq.x), il0, ez));
+            float w1 = kw * ex2_approx(-fmaf(fabsf(cp.y - cq.y), il1, ez));
+            w0 = fg_var(cq.z) ? w0 : 0.0f;    // NaN-safe for whatever a background pixel holds
+            w1 = fg_var(cq.z) ? w1 : 0.0f;
+            a.sw0 += w0;
+            a.sw1 += w1;
+            a.sc0 = fmaf(w0, cq.x, a.sc0);
+            a.sc1 = fmaf(w1, cq.y, a.sc1);
+            a.sv0 = fmaf(w0 * w0, cq.z, a.sv0);
+            a.sv1 = fmaf(w1 * w1, cq.w, a.sv1);
+        }
+    }
+}
+
 // one a-trous iteration; kMode 0: write illum_out; 1: also colour history;
 // 2: last iteration, write the two output planes only.  kNsq >= 0: sigma_n
 // is 2^kNsq.
@@ -381,37 +433,22 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
         rz[t] = __fdividef(kLog2e, fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
     }
     const float kc = 0.375f * 0.375f;
-    float sw0 = kc, sw1 = kc;
-    float sc0 = kc * cp.x, sc1 = kc * cp.y;
-    float sv0 = kc * kc * cp.z, sv1 = kc * kc * cp.w;
-    const float h5[5] = {1.f / 16, 1.f / 4, 3.f / 8, 1.f / 4, 1.f / 16};
-#pragma unroll
-    for (int j = -2; j <= 2; ++j) {
-        const int qy = y + j * step;
-        if (qy < 0 || qy >= k.H) continue;
-#pragma unroll
-        for (int i = -2; i <= 2; ++i) {
-            if (i == 0 && j == 0) continue;
-            const int qx = x + i * step;
-            if (qx < 0 || qx >= k.W) continue;
-            const int q = qy * k.W + qx;
-            const float4 cq = __ldg(in + q);
-            if (!fg_var(cq.z)) continue;
-            const float4 zq = S::g(g, q);
-            const int t = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
-            const float ez = fabsf(zn.x - zq.x) * rz[t];
-            const float kw = h5[i + 2] * h5[j + 2] *
-                             pow_n<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n, k.sigma_n_int);
-            const float w0 = kw * exp2f(-fmaf(fabsf(cp.x - cq.x), il0, ez));
-            const float w1 = kw * exp2f(-fmaf(fabsf(cp.y - cq.y), il1, ez));
-            sw0 += w0;
-            sw1 += w1;
-            sc0 = fmaf(w0, cq.x, sc0);
-            sc1 = fmaf(w1, cq.y, sc1);
-            sv0 = fmaf(w0 * w0, cq.z, sv0);
-            sv1 = fmaf(w1 * w1, cq.w, sv1);
-        }
-    }
+    Acc acc;
+    acc.sw0 = kc;
+    acc.sw1 = kc;
+    acc.sc0 = kc * cp.x;
+    acc.sc1 = kc * cp.y;
+    acc.sv0 = kc * kc * cp.z;
+    acc.sv1 = kc * kc * cp.w;
+    // blocks whose 5x5 footprint lies inside the image skip the bounds tests
+    const int bx0 = blockIdx.x * blockDim.x, by0 = blockIdx.y * blockDim.y;
+    const bool interior = bx0 - 2 * step >= 0 && by0 - 2 * step >= 0 &&
+                          bx0 + (int)blockDim.x - 1 + 2 * step < k.W && by0 + (int)blockDim.y - 1 + 2 * step < k.H;
+    if (interior)
+        atrous_taps<S, kNsq, false>(k, step, x, y, zn, cp, il0, il1, rz, g, in, acc);
+    else
+        atrous_taps<S, kNsq, true>(k, step, x, y, zn, cp, il0, il1, rz, g, in, acc);
+    const float sw0 = acc.sw0, sw1 = acc.sw1, sc0 = acc.sc0, sc1 = acc.sc1, sv0 = acc.sv0, sv1 = acc.sv1;
     // (sum w c) / (sum w): a constant neighbourhood stays exactly constant
     const float c0 = sc0 / sw0, c1 = sc1 / sw1;
     if (kMode == 2) {
