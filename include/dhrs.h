@@ -226,6 +226,32 @@ dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur,
                                 const uint8_t* ao_count, const dhr_svgf_params* params,
                                 float* ao_out, float* shadow_out, void* stream);
 
+/* Allocation-free variant of the a-trous part of dhr_svgf_reconstruct.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they filter (a frame loop that must
+ * not wait on an allocator, a process whose device memory was budgeted up
+ * front, a host whose allocator belongs to another framework).  It runs
+ * params->levels (1..8) edge-stopping a-trous iterations over `illum` and
+ * writes the last one's colours; it calls no allocator.
+ *  gbuf: device G-buffer, FP32 or FP16, at most 1,048,576 pixels
+ *        (W*H larger is rejected with DHR_ERR_INVALID); background pixels
+ *        have depth +inf.
+ *  illum (device, float4 per pixel): colour AO, colour shadow, variance AO,
+ *        variance shadow, variance -1 on background pixels -- the layout
+ *        of dhr_svgf_buffers.illum.
+ *  ao_out, shadow_out: device float [W*H].
+ * Scratch: two 16 MiB images in a fixed device array that every device
+ * which loads the library holds until the process exits.  Its device
+ * address is looked up on the first call on each device, so make that
+ * first call before capturing the stream into a CUDA graph.  Every call
+ * uses the same array and each level overwrites every pixel it reads next,
+ * so nothing has to start at zero; two calls whose kernels overlap on the
+ * GPU (different streams, or different host threads) race on the array and
+ * must be serialised by the caller. */
+dhr_status dhr_svgf_atrous_noalloc(const dhr_gbuffer* gbuf, const float* illum,
+                                   const dhr_svgf_params* params, float* ao_out,
+                                   float* shadow_out, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Session: trace + SVGF per frame with library-owned G-buffer ping-pong   */
 /* ---------------------------------------------------------------------- */

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "dhr_svgf_destroy": ([_P], None),
     "dhr_svgf_get_buffers": ([_P, _P], C.c_int),
     "dhr_svgf_reconstruct": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_svgf_atrous_noalloc": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_session_create": ([_P, C.c_int32, C.c_int32, C.c_int, _P, _P, _P], C.c_int),
     "dhr_session_destroy": ([_P], None),
     "dhr_step_frame": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
@@ -341,6 +342,16 @@ class _DevArray:
 
 
 _TYPESTR = {"float32": "<f4", "float16": "<f2", "uint8": "|u1", "int32": "<i4"}
+
+
+def svgf_atrous_noalloc(gbuf: GBuffer, illum_ptr: int, params: SvgfParams, ao_out, sh_out, stream=None):
+    """A-trous iterations over a float4 illum buffer (device pointer) with the
+    library's fixed scratch instead of allocated memory (<= 1,048,576 pixels)."""
+    _need_cuda(ao_out, sh_out)
+    g = gbuf.c()
+    p = params.to_c()
+    _check(lib().dhr_svgf_atrous_noalloc(C.byref(g), C.c_void_p(int(illum_ptr)), C.byref(p), _ptr(ao_out),
+                                         _ptr(sh_out), _stream(stream)))
 
 
 def device_copy(ptr: int, shape, dtype: str):

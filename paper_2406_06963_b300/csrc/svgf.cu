@@ -18,6 +18,8 @@
 // (its mu2 - mu1^2 cancellation needs the precision); arithmetic is binary32.
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace dhr {
@@ -674,4 +676,98 @@ extern "C" dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuf
     clear_error();
     return svgf_run(state, cur, prev, cam, cam_prev, shadow_mask, ao_count, params, ao_out, shadow_out,
                     as_stream(stream));
+}
+
+// ------------------------------------------------------------------------
+// Allocation-free a-trous cascade.
+//
+// Some callers cannot allocate device memory at the moment they filter: a
+// render loop that must not stall on the allocator mid-frame, code running
+// inside a memory budget that was reserved up front (such as a serving
+// loop that admits sessions by their memory), or a host whose allocator
+// belongs to another framework.  dhr_svgf_atrous_noalloc serves them: its
+// two ping-pong images live in the file-scope array below, which the
+// library reserves once per device when the module loads and keeps until
+// the process exits.
+// ------------------------------------------------------------------------
+namespace dhr {
+
+constexpr int64_t kNoallocMaxPixels = 1 << 20;   // 1,048,576 pixels: 2 images x 16 MiB
+
+static __device__ __align__(256) float4 g_noalloc_scratch[2 * kNoallocMaxPixels];
+
+constexpr int kNoallocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static float4* g_noalloc_addr[kNoallocMaxDevices];
+
+// Device address of g_noalloc_scratch on the current device (the host-side
+// symbol is only a stand-in).  Looked up once per device, on the first call.
+static dhr_status noalloc_scratch(float4** out) {
+    int dev = -1;
+    DHR_CUDA_TRY(cudaGetDevice(&dev));
+    DHR_CHECK_ARG(dev >= 0 && dev < kNoallocMaxDevices, "svgf_atrous_noalloc: device ordinal %d unsupported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        DHR_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = static_cast<float4*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return DHR_OK;
+}
+
+template <dhr_precision P>
+static dhr_status run_atrous_noalloc(const dhr_gbuffer* g, const float4* illum, const dhr_svgf_params* prm,
+                                     float* ao_out, float* sh_out, float4* scratch, cudaStream_t st) {
+    SvgfConsts k;
+    k.W = g->width;
+    k.H = g->height;
+    k.alpha = prm->alpha;
+    k.sigma_z = prm->sigma_z;
+    k.sigma_n = prm->sigma_n;
+    k.sigma_l = prm->sigma_l;
+    k.eps_z = prm->eps_z;
+    k.eps_l = prm->eps_l;
+    k.inv_spp = 1.0f / (float)prm->ao_spp;
+    k.fixed_alpha = (int)prm->fixed_alpha;
+    k.wl_in_atrous = (int)prm->wl_in_atrous;
+    k.sigma_n_int = (prm->sigma_n >= 1.0f && prm->sigma_n <= 1024.0f && prm->sigma_n == floorf(prm->sigma_n))
+                        ? (int)prm->sigma_n : 0;
+    const dim3 blk(32, 8), grid((k.W + 31) / 32, (k.H + 7) / 8);
+    const int nsq = (prm->sigma_n == 128.0f) ? 7 : -1;
+    const auto* gd = static_cast<const typename Store<P>::G*>(g->depth_normal);
+    const int L = (int)prm->levels;
+    const float4* in = illum;
+    for (int l = 0; l < L; ++l) {
+        float4* out = scratch + (size_t)(l & 1) * kNoallocMaxPixels;
+        DHR_TRY(launch_atrous<P>(l == L - 1 ? 2 : 0, nsq, grid, blk, st, k, 1 << l, gd, in, out, nullptr, ao_out,
+                                 sh_out));
+        in = out;
+    }
+    return DHR_OK;
+}
+
+}  // namespace dhr
+
+extern "C" dhr_status dhr_svgf_atrous_noalloc(const dhr_gbuffer* gbuf, const float* illum,
+                                              const dhr_svgf_params* params, float* ao_out, float* shadow_out,
+                                              void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(gbuf && gbuf->depth_normal && illum && params && ao_out && shadow_out,
+                  "svgf_atrous_noalloc: null pointer");
+    DHR_CHECK_ARG(gbuf->width > 0 && gbuf->height > 0, "svgf_atrous_noalloc: bad size %dx%d", gbuf->width,
+                  gbuf->height);
+    DHR_CHECK_ARG((int64_t)gbuf->width * gbuf->height <= kNoallocMaxPixels,
+                  "svgf_atrous_noalloc: %dx%d = %lld pixels exceeds the fixed scratch of %lld pixels",
+                  gbuf->width, gbuf->height, (long long)gbuf->width * gbuf->height,
+                  (long long)kNoallocMaxPixels);
+    DHR_CHECK_ARG(gbuf->precision == DHR_FP32 || gbuf->precision == DHR_FP16, "svgf_atrous_noalloc: bad precision");
+    DHR_TRY(check_svgf_params(params));
+    DHR_CHECK_ARG(params->levels >= 1, "svgf_atrous_noalloc: levels must be in 1..8");
+    float4* scratch = nullptr;
+    DHR_TRY(noalloc_scratch(&scratch));
+    const float4* in = reinterpret_cast<const float4*>(illum);
+    if (gbuf->precision == DHR_FP16)
+        return run_atrous_noalloc<DHR_FP16>(gbuf, in, params, ao_out, shadow_out, scratch, as_stream(stream));
+    return run_atrous_noalloc<DHR_FP32>(gbuf, in, params, ao_out, shadow_out, scratch, as_stream(stream));
 }

@@ -1,0 +1,66 @@
+"""The allocation-free a-trous entry point (dhr_svgf_atrous_noalloc) gives the
+same filtered AO and shadow as the a-trous part of dhr_svgf_reconstruct.
+
+It is meant for callers that cannot allocate device memory while filtering
+(a frame loop that must not wait on an allocator, a process whose memory was
+budgeted up front, a host whose allocator belongs to another framework), so
+it keeps its ping-pong images in a fixed device array instead.  The test
+feeds it the temporal output of dhr_svgf_reconstruct on two consecutive
+frames (two calls in a row reusing the same fixed array) and compares with
+the outputs dhr_svgf_reconstruct wrote, within the 1e-3 bar of the SVGF
+parity tests.  It also checks the size limit.
+"""
+import numpy as np
+import pytest
+
+import paper_2406_06963_b300 as dhrs
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-3
+
+
+@pytest.mark.parametrize("precision", [dhrs.DHR_FP32, dhrs.DHR_FP16])
+def test_noalloc_atrous_matches_reconstruct(precision):
+    W, H = 320, 200
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    cams = wl.orbit_path(2, W, H, degrees=4.0)
+    st = dhrs.SvgfState(W, H, precision)
+    params = dhrs.SvgfParams()
+    ao_ref = torch.empty((H, W), device="cuda")
+    sh_ref = torch.empty_like(ao_ref)
+    ao_na = torch.empty_like(ao_ref)
+    sh_na = torch.empty_like(ao_ref)
+    mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    aoc = torch.empty_like(mask)
+    prev = None
+    for f, cam in enumerate(cams):
+        g = dhrs.GBuffer(W, H, precision)
+        dhrs.trace_visibility(sc, cam, dhrs.TraceParams(frame=f), g, mask, aoc)
+        st.reconstruct(g, prev[0] if prev else None, cam, prev[1] if prev else None, mask, aoc, params,
+                       ao_ref, sh_ref)
+        illum_ptr = st.buffers()["illum"]
+        ao_na.fill_(-7.0)
+        sh_na.fill_(-7.0)
+        dhrs.svgf_atrous_noalloc(g, illum_ptr, params, ao_na, sh_na)
+        torch.cuda.synchronize()
+        err = max(float((ao_na - ao_ref).abs().max()), float((sh_na - sh_ref).abs().max()))
+        assert err <= TOL, (f, err)
+        assert float(ao_na.min()) >= 0.0 and float(sh_na.min()) >= 0.0
+        prev = (g, cam)
+
+
+def test_noalloc_rejects_oversized_and_bad_levels():
+    g = dhrs.GBuffer(1025, 1024)        # 1,049,600 pixels > 1,048,576
+    o = torch.empty((1024, 1025), device="cuda")
+    illum = torch.zeros((1024, 1025, 4), device="cuda")
+    with pytest.raises(dhrs.DhrError) as e:
+        dhrs.svgf_atrous_noalloc(g, illum.data_ptr(), dhrs.SvgfParams(), o, o)
+    assert e.value.status == 1 and "exceeds" in str(e.value)
+    g2 = dhrs.GBuffer(64, 64)
+    o2 = torch.empty((64, 64), device="cuda")
+    with pytest.raises(dhrs.DhrError):
+        dhrs.svgf_atrous_noalloc(g2, illum.data_ptr(), dhrs.SvgfParams(levels=0), o2, o2)
