@@ -65,6 +65,14 @@ typedef struct {
     int32_t height;
 } dhr_camera;
 
+/* BVH builders.  Both start from 63-bit Morton codes of the triangle
+ * centroids sorted on the device.  PLOC (parallel locally-ordered
+ * clustering) merges mutual nearest neighbours by surface area and gives
+ * a tree close to a sweep-SAH build; LBVH (Karras 2012) splits on the Morton
+ * bits and builds faster. */
+#define DHR_BUILD_PLOC 0u
+#define DHR_BUILD_LBVH 1u
+
 /* Triangle soup, host memory; read during dhr_create_scene only. */
 typedef struct {
     const float* vertices;     /* [n_vertices][3] */
@@ -72,6 +80,7 @@ typedef struct {
     const uint32_t* mesh_ids;  /* [n_triangles]; NULL = all 0 */
     uint32_t n_vertices;
     uint32_t n_triangles;
+    uint32_t builder;          /* DHR_BUILD_PLOC (0, default) or DHR_BUILD_LBVH */
 } dhr_scene_desc;
 
 typedef struct dhr_scene dhr_scene;

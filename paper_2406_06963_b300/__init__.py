@@ -37,9 +37,12 @@ class Camera(C.Structure):
                 ("height", C.c_int32)]
 
 
+BUILD_PLOC, BUILD_LBVH = 0, 1
+
+
 class SceneDesc(C.Structure):
     _fields_ = [("vertices", C.c_void_p), ("indices", C.c_void_p), ("mesh_ids", C.c_void_p),
-                ("n_vertices", C.c_uint32), ("n_triangles", C.c_uint32)]
+                ("n_vertices", C.c_uint32), ("n_triangles", C.c_uint32), ("builder", C.c_uint32)]
 
 
 class SceneInfo(C.Structure):
@@ -225,11 +228,11 @@ class GBuffer:
 class Scene:
     """Device scene + LBVH built from a host triangle soup (workloads dict)."""
 
-    def __init__(self, scene: dict, stream=None):
+    def __init__(self, scene: dict, stream=None, builder=BUILD_PLOC):
         v = np.ascontiguousarray(scene["vertices"], np.float32)
         i = np.ascontiguousarray(scene["indices"], np.uint32)
         m = np.ascontiguousarray(scene["mesh_ids"], np.uint32)
-        d = SceneDesc(v.ctypes.data, i.ctypes.data, m.ctypes.data, len(v), len(i))
+        d = SceneDesc(v.ctypes.data, i.ctypes.data, m.ctypes.data, len(v), len(i), builder)
         h = C.c_void_p()
         _check(lib().dhr_create_scene(C.byref(d), _stream(stream), C.byref(h)))
         self.h = h

@@ -59,6 +59,7 @@ extern "C" dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream,
     DHR_CHECK_ARG(desc->n_triangles == 0 || (desc->vertices && desc->indices),
                   "create_scene: null vertex or index array");
     DHR_CHECK_ARG(desc->n_triangles < (1u << 31), "create_scene: too many triangles");
+    DHR_CHECK_ARG(desc->builder == DHR_BUILD_PLOC || desc->builder == DHR_BUILD_LBVH, "create_scene: bad builder");
     cudaStream_t st = as_stream(stream);
     auto* sc = new dhr_scene();
     float* v = nullptr;
@@ -76,7 +77,7 @@ extern "C" dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream,
         if (e)
             s = set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA, "create_scene: %s",
                           cudaGetErrorString(e));
-        if (s == DHR_OK) s = build_lbvh(v, idx, mesh, desc->n_vertices, desc->n_triangles, st, sc);
+        if (s == DHR_OK) s = build_lbvh(v, idx, mesh, desc->n_vertices, desc->n_triangles, st, sc, desc->builder);
         cudaStreamSynchronize(st);
     }
     cudaFree(v);

@@ -8,6 +8,7 @@
 // of BVHs, Octrees, and k-d Trees", HPG 2012), and a bottom-up box refit in
 // which the second thread to reach a node computes its box.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include "common.cuh"
 
@@ -205,6 +206,135 @@ __global__ void single_kernel(const float* v, const uint32_t* idx, const uint32_
     nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
 }
 
+// ---------------------------------------------------------------- PLOC
+// Parallel locally-ordered clustering (Meister & Bittner, "Parallel
+// Locally-Ordered Clustering for Bounding Volume Hierarchy Construction",
+// IEEE TVCG 2018): clusters stay in Morton order; each finds, within a
+// window of +-r positions, the neighbour whose merged box has the smallest
+// surface area; mutual nearest neighbours merge into a new node; the array
+// is compacted; repeat until one cluster remains.
+
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ float4 fmin4(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.f);
+}
+__device__ __forceinline__ float4 fmax4(float4 a, float4 b) {
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), 0.f);
+}
+
+// sorted triangle data + one cluster per leaf
+__global__ void ploc_leaves_kernel(const float* v, const uint32_t* idx, const uint32_t* mesh, const uint32_t* order,
+                                   int n, float4* tris, int* cl_ref, float4* cl_lo, float4* cl_hi,
+                                   float4* leaf_lo, float4* leaf_hi) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t t = order[k];
+    const Tri3 r = load_tri(v, idx, t);
+    tris[3 * k + 0] = make_float4(r.a.x, r.a.y, r.a.z, __uint_as_float(t));
+    tris[3 * k + 1] = make_float4(r.b.x, r.b.y, r.b.z, __uint_as_float(mesh ? mesh[t] : 0u));
+    tris[3 * k + 2] = make_float4(r.c.x, r.c.y, r.c.z, 0.0f);
+    const float4 lo = make_float4(fminf(r.a.x, fminf(r.b.x, r.c.x)), fminf(r.a.y, fminf(r.b.y, r.c.y)),
+                                  fminf(r.a.z, fminf(r.b.z, r.c.z)), 0.0f);
+    const float4 hi = make_float4(fmaxf(r.a.x, fmaxf(r.b.x, r.c.x)), fmaxf(r.a.y, fmaxf(r.b.y, r.c.y)),
+                                  fmaxf(r.a.z, fmaxf(r.b.z, r.c.z)), 0.0f);
+    cl_ref[k] = ~k;
+    cl_lo[k] = lo;
+    cl_hi[k] = hi;
+    leaf_lo[k] = lo;
+    leaf_hi[k] = hi;
+}
+
+// nearest neighbour by merged surface area within +-r (ties: smaller index)
+__global__ void ploc_nn_kernel(int C, int r, const float4* lo, const float4* hi, int* nn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const float4 li = lo[i], hi_ = hi[i];
+    float best = INFINITY;
+    int bj = -1;
+    const int j0 = max(0, i - r), j1 = min(C - 1, i + r);
+    for (int j = j0; j <= j1; ++j) {
+        if (j == i) continue;
+        const float d = half_area(fmin4(li, __ldg(lo + j)), fmax4(hi_, __ldg(hi + j)));
+        if (d < best || (d == best && j < bj)) {
+            best = d;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+// merge flag (the smaller index of a mutual pair creates the node) and
+// survive flag (the larger index of a mutual pair disappears)
+__global__ void ploc_flags_kernel(int C, const int* nn, int* merge, int* keep) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C) return;
+    const int j = nn[i];
+    const bool mutual = j >= 0 && nn[j] == i;
+    merge[i] = (mutual && i < j) ? 1 : 0;
+    keep[i] = (mutual && i > j) ? 0 : 1;
+}
+
+__device__ __forceinline__ int ref_height(int ref, const int* nheight) { return ref < 0 ? 0 : nheight[ref]; }
+
+// create the merged nodes and scatter the surviving clusters, in order
+__global__ void ploc_merge_kernel(int C, const int* nn, const int* merge, const int* merge_ofs, const int* keep,
+                                  const int* keep_ofs, int node_base, const int* cl_ref, const float4* cl_lo,
+                                  const float4* cl_hi, int2* children, float4* nlo, float4* nhi, int* nheight,
+                                  int* out_ref, float4* out_lo, float4* out_hi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C || !keep[i]) return;
+    int ref = cl_ref[i];
+    float4 lo = cl_lo[i], hi = cl_hi[i];
+    if (merge[i]) {
+        const int j = nn[i];
+        const int node = node_base + merge_ofs[i];
+        const int rj = cl_ref[j];
+        lo = fmin4(lo, cl_lo[j]);
+        hi = fmax4(hi, cl_hi[j]);
+        children[node] = make_int2(ref, rj);
+        nlo[node] = lo;
+        nhi[node] = hi;
+        nheight[node] = 1 + max(ref_height(ref, nheight), ref_height(rj, nheight));
+        ref = node;
+    }
+    const int o = keep_ofs[i];
+    out_ref[o] = ref;
+    out_lo[o] = lo;
+    out_hi[o] = hi;
+}
+
+// creation order m (root = n - 2, created last) -> traversal order n-2-m (root = 0)
+__global__ void ploc_pack_kernel(int n, const int2* children, const float4* nlo, const float4* nhi,
+                                 const float4* leaf_lo, const float4* leaf_hi, float4* nodes) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n - 1) return;
+    const int2 ch = children[m];
+    const int refs[2] = {ch.x, ch.y};
+    float4 lo[2], hi[2];
+    int out_ref[2];
+    for (int c = 0; c < 2; ++c) {
+        const int r = refs[c];
+        if (r < 0) {
+            lo[c] = leaf_lo[~r];
+            hi[c] = leaf_hi[~r];
+            out_ref[c] = r;
+        } else {
+            lo[c] = nlo[r];
+            hi[c] = nhi[r];
+            out_ref[c] = (n - 2) - r;
+        }
+    }
+    const int i = (n - 2) - m;
+    nodes[4 * i + 0] = make_float4(lo[0].x, hi[0].x, lo[0].y, hi[0].y);
+    nodes[4 * i + 1] = make_float4(lo[1].x, hi[1].x, lo[1].y, hi[1].y);
+    nodes[4 * i + 2] = make_float4(lo[0].z, hi[0].z, lo[1].z, hi[1].z);
+    nodes[4 * i + 3] = make_float4(__int_as_float(out_ref[0]), __int_as_float(out_ref[1]), 0.0f, 0.0f);
+}
+
 template <class T>
 dhr_status dmalloc(T** p, size_t count, const char* what) {
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
@@ -228,17 +358,91 @@ struct Scratch {
     int* height = nullptr;
     uint32_t* visits = nullptr;
     void* cub_tmp = nullptr;
+    // PLOC
+    int* cl_ref[2] = {nullptr, nullptr};
+    float4* cl_lo[2] = {nullptr, nullptr};
+    float4* cl_hi[2] = {nullptr, nullptr};
+    int* nn = nullptr;
+    int* merge = nullptr;
+    int* merge_ofs = nullptr;
+    int* keep = nullptr;
+    int* keep_ofs = nullptr;
+    void* scan_tmp = nullptr;
     ~Scratch() {
         cudaFree(bounds); cudaFree(keys); cudaFree(keys_sorted); cudaFree(vals);
         cudaFree(vals_sorted); cudaFree(children); cudaFree(parent); cudaFree(lo);
         cudaFree(hi); cudaFree(height); cudaFree(visits); cudaFree(cub_tmp);
+        for (int i = 0; i < 2; ++i) { cudaFree(cl_ref[i]); cudaFree(cl_lo[i]); cudaFree(cl_hi[i]); }
+        cudaFree(nn); cudaFree(merge); cudaFree(merge_ofs); cudaFree(keep); cudaFree(keep_ofs);
+        cudaFree(scan_tmp);
     }
 };
+
+// PLOC over the Morton-sorted leaves (s.vals_sorted); nodes in s.children,
+// boxes in s.lo / s.hi ([0, n-1) internal, [n-1, 2n-1) leaves).
+dhr_status build_ploc(const float* v, const uint32_t* idx, const uint32_t* mesh, int n, cudaStream_t st,
+                      dhr_scene* sc, Scratch& s) {
+    constexpr int kRadius = 16;
+    for (int b = 0; b < 2; ++b) {
+        DHR_TRY(dmalloc(&s.cl_ref[b], n, "clusters"));
+        DHR_TRY(dmalloc(&s.cl_lo[b], n, "clusters"));
+        DHR_TRY(dmalloc(&s.cl_hi[b], n, "clusters"));
+    }
+    DHR_TRY(dmalloc(&s.nn, n, "nn"));
+    DHR_TRY(dmalloc(&s.merge, n, "merge"));
+    DHR_TRY(dmalloc(&s.merge_ofs, n, "merge"));
+    DHR_TRY(dmalloc(&s.keep, n, "keep"));
+    DHR_TRY(dmalloc(&s.keep_ofs, n, "keep"));
+    size_t scan_bytes = 0;
+    DHR_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, s.merge, s.merge_ofs, n, st));
+    DHR_CUDA_TRY(cudaMalloc(&s.scan_tmp, scan_bytes));
+    float4* leaf_lo = s.lo + (n - 1);
+    float4* leaf_hi = s.hi + (n - 1);
+    ploc_leaves_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+        v, idx, mesh, s.vals_sorted, n, sc->tris, s.cl_ref[0], s.cl_lo[0], s.cl_hi[0], leaf_lo, leaf_hi);
+    DHR_CUDA_TRY(cudaGetLastError());
+    int C = n, cur = 0, node_base = 0;
+    for (int it = 0; C > 1; ++it) {
+        if (it >= 4096) return set_error(DHR_ERR_CUDA, "create_scene: PLOC did not converge");
+        const int g = (C + kThreads - 1) / kThreads;
+        ploc_nn_kernel<<<g, kThreads, 0, st>>>(C, kRadius, s.cl_lo[cur], s.cl_hi[cur], s.nn);
+        ploc_flags_kernel<<<g, kThreads, 0, st>>>(C, s.nn, s.merge, s.keep);
+        DHR_CUDA_TRY(cudaGetLastError());
+        DHR_CUDA_TRY(cub::DeviceScan::ExclusiveSum(s.scan_tmp, scan_bytes, s.merge, s.merge_ofs, C, st));
+        DHR_CUDA_TRY(cub::DeviceScan::ExclusiveSum(s.scan_tmp, scan_bytes, s.keep, s.keep_ofs, C, st));
+        ploc_merge_kernel<<<g, kThreads, 0, st>>>(C, s.nn, s.merge, s.merge_ofs, s.keep, s.keep_ofs, node_base,
+                                                  s.cl_ref[cur], s.cl_lo[cur], s.cl_hi[cur], s.children, s.lo,
+                                                  s.hi, s.height, s.cl_ref[cur ^ 1], s.cl_lo[cur ^ 1],
+                                                  s.cl_hi[cur ^ 1]);
+        DHR_CUDA_TRY(cudaGetLastError());
+        int tail[4];
+        DHR_CUDA_TRY(cudaMemcpyAsync(&tail[0], s.merge + C - 1, 4, cudaMemcpyDeviceToHost, st));
+        DHR_CUDA_TRY(cudaMemcpyAsync(&tail[1], s.merge_ofs + C - 1, 4, cudaMemcpyDeviceToHost, st));
+        DHR_CUDA_TRY(cudaMemcpyAsync(&tail[2], s.keep + C - 1, 4, cudaMemcpyDeviceToHost, st));
+        DHR_CUDA_TRY(cudaMemcpyAsync(&tail[3], s.keep_ofs + C - 1, 4, cudaMemcpyDeviceToHost, st));
+        DHR_CUDA_TRY(cudaStreamSynchronize(st));
+        const int merges = tail[0] + tail[1], left = tail[2] + tail[3];
+        if (merges == 0) return set_error(DHR_ERR_CUDA, "create_scene: PLOC made no progress");
+        node_base += merges;
+        C = left;
+        cur ^= 1;
+    }
+    if (node_base != n - 1) return set_error(DHR_ERR_CUDA, "create_scene: PLOC built %d nodes for %d leaves",
+                                             node_base, n);
+    ploc_pack_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, s.children, s.lo, s.hi, leaf_lo,
+                                                                            leaf_hi, sc->nodes);
+    DHR_CUDA_TRY(cudaGetLastError());
+    int h = 0;
+    DHR_CUDA_TRY(cudaMemcpyAsync(&h, s.height + (n - 2), sizeof(int), cudaMemcpyDeviceToHost, st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    sc->height = (uint32_t)h;
+    return DHR_OK;
+}
 
 }  // namespace
 
 dhr_status build_lbvh(const float* v, const uint32_t* idx, const uint32_t* mesh, uint32_t n_verts,
-                      uint32_t n_tris, cudaStream_t st, dhr_scene* sc) {
+                      uint32_t n_tris, cudaStream_t st, dhr_scene* sc, uint32_t builder) {
     sc->n_tris = n_tris;
     if (n_tris == 0) return DHR_OK;
     cudaEvent_t e0, e1;
@@ -291,19 +495,23 @@ dhr_status build_lbvh(const float* v, const uint32_t* idx, const uint32_t* mesh,
         DHR_CUDA_TRY(cudaMalloc(&s.cub_tmp, tmp_bytes));
         DHR_CUDA_TRY(cub::DeviceRadixSort::SortPairs(s.cub_tmp, tmp_bytes, s.keys, s.keys_sorted,
                                                      s.vals, s.vals_sorted, n, 0, 63, st));
-        karras_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(s.keys_sorted, n,
-                                                                              s.children, s.parent);
-        DHR_CUDA_TRY(cudaGetLastError());
-        refit_kernel<<<grid, kThreads, 0, st>>>(v, idx, mesh, s.vals_sorted, n, s.children, s.parent,
-                                                s.lo, s.hi, s.height, s.visits, sc->tris);
-        DHR_CUDA_TRY(cudaGetLastError());
-        pack_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, s.children, s.lo, s.hi,
-                                                                           sc->nodes);
-        DHR_CUDA_TRY(cudaGetLastError());
-        int h = 0;
-        DHR_CUDA_TRY(cudaMemcpyAsync(&h, s.height, sizeof(int), cudaMemcpyDeviceToHost, st));
-        DHR_CUDA_TRY(cudaStreamSynchronize(st));
-        sc->height = (uint32_t)h;
+        if (builder == DHR_BUILD_LBVH) {
+            karras_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(s.keys_sorted, n,
+                                                                                  s.children, s.parent);
+            DHR_CUDA_TRY(cudaGetLastError());
+            refit_kernel<<<grid, kThreads, 0, st>>>(v, idx, mesh, s.vals_sorted, n, s.children, s.parent,
+                                                    s.lo, s.hi, s.height, s.visits, sc->tris);
+            DHR_CUDA_TRY(cudaGetLastError());
+            pack_kernel<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, s.children, s.lo, s.hi,
+                                                                               sc->nodes);
+            DHR_CUDA_TRY(cudaGetLastError());
+            int h = 0;
+            DHR_CUDA_TRY(cudaMemcpyAsync(&h, s.height, sizeof(int), cudaMemcpyDeviceToHost, st));
+            DHR_CUDA_TRY(cudaStreamSynchronize(st));
+            sc->height = (uint32_t)h;
+        } else {
+            DHR_TRY(build_ploc(v, idx, mesh, n, st, sc, s));
+        }
     }
     DHR_CUDA_TRY(cudaEventRecord(e1, st));
     DHR_CUDA_TRY(cudaEventSynchronize(e1));

@@ -72,7 +72,7 @@ namespace dhr {
 
 // ------------------------------------------------------------ entry points
 dhr_status build_lbvh(const float* verts_d, const uint32_t* idx_d, const uint32_t* mesh_d,
-                      uint32_t n_verts, uint32_t n_tris, cudaStream_t st, dhr_scene* sc);
+                      uint32_t n_verts, uint32_t n_tris, cudaStream_t st, dhr_scene* sc, uint32_t builder);
 
 dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
                         dhr_gbuffer* g, uint8_t* mask, uint8_t* ao, cudaStream_t st,

@@ -20,10 +20,10 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.fixture(scope="module")
-def boxes():
+@pytest.fixture(scope="module", params=[dhrs.BUILD_PLOC, dhrs.BUILD_LBVH], ids=["ploc", "lbvh"])
+def boxes(request):
     s = wl.scene_boxes()
-    return s, dhrs.Scene(s), orc.Scene(s)
+    return s, dhrs.Scene(s, builder=request.param), orc.Scene(s)
 
 
 @pytest.fixture(scope="module")
@@ -98,6 +98,8 @@ def test_trace_terrain_1080p_sampled(terrain):
     info = g_scene.info()
     assert info["n_triangles"] == 776050 and info["n_nodes"] == 776049
     assert 0 < info["height"] < 64
+    lb = dhrs.Scene(s, builder=dhrs.BUILD_LBVH).info()
+    assert lb["n_nodes"] == 776049 and 0 < lb["height"] < 64
     cams = wl.spline_path(s["terrain"], 60, 1920, 1080)
     r = np.random.default_rng(42)
     tot = None
