@@ -44,24 +44,32 @@ def _peaks():
         return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def _csrc_hash():
+# sources each profiled kernel is compiled from
+KERNEL_SOURCES = {
+    "trace_kernel": ["trace.cu", "sampling.cuh", "common.cuh"],
+    "atrous_kernel": ["svgf.cu", "common.cuh"],
+    "temporal_kernel": ["svgf.cu", "common.cuh"],
+}
+
+
+def csrc_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2406_06963_b300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2406_06963_b300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel sources changed since the capture."""
+    kernel's sources changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
     except OSError:
         return None
     e = t.get(kernel)
-    if not e or e.get("csrc_sha") != _csrc_hash():
+    if not e or e.get("csrc_sha") != csrc_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

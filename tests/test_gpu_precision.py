@@ -1,0 +1,94 @@
+"""FP16 storage form: G-buffer (depth, normal), colour history and moments
+stored in binary16, arithmetic, intersection and the variance buffer in
+binary32.  Per-buffer error against the fp64 oracle (same inputs, the
+oracle's G-buffer rounded to binary16 for the GPU) and against the FP32
+path, reported and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+import paper_2406_06963_b300 as dhrs
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _stats(err):
+    err = np.abs(np.asarray(err, np.float64)).ravel()
+    return dict(max=float(err.max()), mean=float(err.mean()), p99=float(np.percentile(err, 99)))
+
+
+def test_fp16_storage_vs_fp64_oracle():
+    """256x256 box scene, 8 frames: per-buffer errors of the FP16 form."""
+    W = H = 256
+    s = wl.scene_boxes()
+    S = orc.Scene(s)
+    cams = wl.orbit_path(8, W, H, degrees=8.0)
+    op = orc.SvgfParams()
+    ost = orc.SvgfState(W, H)
+    gst = dhrs.SvgfState(W, H, dhrs.DHR_FP16)
+    ao_o = torch.empty((H, W), device="cuda")
+    sh_o = torch.empty_like(ao_o)
+    prev = None
+    table = {k: [] for k in ("depth", "normal", "moments", "color_hist", "ao", "shadow")}
+    for f, cam in enumerate(cams):
+        tr = orc.trace(S, cam, orc.TraceParams(frame=f))
+        zn, mesh = orc.gbuffer_f32(tr, W, H)
+        mask = tr["shadow_mask"].reshape(H, W)
+        cnt = tr["ao_count"].reshape(H, W)
+        ref = ost.frame(zn, mesh, cam, mask, cnt, op)
+        g = dhrs.GBuffer.from_arrays(zn, mesh, dhrs.DHR_FP16)
+        gst.reconstruct(g, prev[0] if prev else None, cam, prev[1] if prev else None,
+                        torch.from_numpy(mask).cuda(), torch.from_numpy(cnt).cuda(), dhrs.SvgfParams(), ao_o, sh_o)
+        torch.cuda.synchronize()
+        fg = np.isfinite(zn[..., 0])
+        gz = g.depth_normal.float().cpu().numpy()
+        table["depth"].append((gz[..., 0][fg] - tr["depth"].reshape(H, W)[fg]) / tr["depth"].reshape(H, W)[fg])
+        table["normal"].append((gz[..., 1:] - tr["normal"].reshape(H, W, 3))[fg])
+        b = gst.buffers()
+        mom = dhrs.device_copy(b["moments"], (H, W, 4), "float16").float().cpu().numpy()
+        col = dhrs.device_copy(b["color_hist"], (H, W, 2), "float16").float().cpu().numpy()
+        table["moments"].append((mom - ost.mom)[fg])
+        table["color_hist"].append((col - ost.col)[fg])
+        table["ao"].append(ao_o.cpu().numpy() - ref["ao"])
+        table["shadow"].append(sh_o.cpu().numpy() - ref["shadow"])
+        prev = (g, cam)
+    rep = {k: _stats(np.concatenate([np.ravel(x) for x in v])) for k, v in table.items()}
+    for k, v in rep.items():
+        print(f"fp16 vs fp64 oracle  {k:10s} max {v['max']:.3g}  p99 {v['p99']:.3g}  mean {v['mean']:.3g}")
+    assert rep["depth"]["max"] < 1e-3            # binary16: relative 2^-11
+    assert rep["normal"]["max"] < 1e-3
+    for k in ("ao", "shadow"):
+        assert rep[k]["p99"] <= 1e-3 and rep[k]["mean"] <= 1e-4, (k, rep[k])
+
+
+@pytest.mark.slow
+def test_fp16_vs_fp32_path_4k():
+    """3840x2160, 776,050 triangles, 20 frames of the camera spline: the FP16
+    storage path against the FP32 path (same rays and samples)."""
+    W, H = 3840, 2160
+    s = wl.scene_terrain()
+    sc = dhrs.Scene(s)
+    cams = wl.spline_path(s["terrain"], 60, W, H)
+    s32 = dhrs.Session(sc, W, H, dhrs.DHR_FP32)
+    s16 = dhrs.Session(sc, W, H, dhrs.DHR_FP16)
+    a32, h32 = torch.empty((H, W), device="cuda"), torch.empty((H, W), device="cuda")
+    a16, h16 = torch.empty_like(a32), torch.empty_like(a32)
+    errs = []
+    for f in range(20):
+        s32.step(cams[f], f, a32, h32)
+        s16.step(cams[f], f, a16, h16)
+        torch.cuda.synchronize()
+        # identical visibility: intersection stays binary32 in both forms
+        b32, b16 = s32.frame_buffers(), s16.frame_buffers()
+        m32 = dhrs.device_copy(b32["ao"], (H, W), "uint8")
+        m16 = dhrs.device_copy(b16["ao"], (H, W), "uint8")
+        assert torch.equal(m32, m16)
+        errs.append(max(float((a16 - a32).abs().max()), float((h16 - h32).abs().max())))
+        if f == 19:
+            e = torch.cat([(a16 - a32).abs().ravel(), (h16 - h32).abs().ravel()]).cpu().numpy()
+            print(f"fp16 vs fp32 4K frame {f}: max {e.max():.3g} p99 {np.percentile(e, 99):.3g} "
+                  f"mean {e.mean():.3g}")
+            assert np.percentile(e, 99) <= 1e-3 and e.mean() <= 1e-4
