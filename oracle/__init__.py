@@ -72,6 +72,7 @@ def _declare(L):
     L.orc_svgf_temporal.argtypes = [C.c_int, C.c_int] + [P] * 15
     L.orc_svgf_atrous.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P]
     L.orc_svgf_frame.argtypes = [C.c_int, C.c_int] + [P] * 16
+    L.orc_svgf_seq_grad.argtypes = [C.c_int, C.c_int, C.c_int] + [P] * 9
 
 
 def _p(a):
@@ -343,3 +344,22 @@ def svgf_atrous(zn, illum, step, params: SvgfParams):
     pp = params.to_c()
     lib().orc_svgf_atrous(W, H, _p(zn), _p(illum), int(step), C.byref(pp), _p(out))
     return out
+
+
+def svgf_seq_grad(zn, mesh, cams, sig, params: SvgfParams, g_out):
+    """Forward + hand-derived fp64 adjoint of the SVGF over F frames starting
+    without history.  zn [F,H,W,4], mesh [F,H,W], cams (F), sig [F,H,W,2],
+    g_out [F,H,W,2].  Returns (out [F,H,W,2], g_sig [F,H,W,2], g_sigma[3])."""
+    zn = _c(zn, np.float32)
+    F, H, W = zn.shape[:3]
+    mesh = _c(mesh, np.uint32)
+    sig = _c(sig, np.float64)
+    g_out = _c(g_out, np.float64)
+    cam_arr = (OrcCamera * F)(*[make_camera(c) for c in cams])
+    out = np.zeros((F, H, W, 2))
+    g_sig = np.zeros((F, H, W, 2))
+    g_sigma = np.zeros(3)
+    pp = params.to_c()
+    lib().orc_svgf_seq_grad(F, W, H, _p(zn), _p(mesh), C.cast(cam_arr, C.c_void_p), _p(sig), C.byref(pp),
+                            _p(g_out), _p(out), _p(g_sig), _p(g_sigma))
+    return out, g_sig, g_sigma

@@ -81,6 +81,14 @@ typedef struct {
     int32_t ao_spp, levels, fixed_alpha, wl_in_atrous;
 } orc_svgf_params;
 
+/* per-pixel record of the temporal step (used by the adjoint) */
+typedef struct {
+    int fg, valid, n, spatial;
+    int x0, y0, ok;        /* bilinear taps (x0 + (k&1), y0 + (k>>1)), valid bits */
+    double a;              /* effective alpha */
+    double beta[4];        /* normalised weights of the valid taps */
+} orc_trec;
+
 /* ======================================================================== */
 /* 1. Random numbers: pcg4d of Jarzynski & Olano, "Hash Functions for GPU   */
 /*    Rendering", JCGT 9(3), 2020.  The paper only says the jitter is       */
@@ -783,18 +791,19 @@ static inline void noisy(const uint8_t* mask, const uint8_t* ao, int64_t p, int 
  * of the current frame's signal weighted by depth and normal only (the
  * paper's modification: no luminance term), whose mean is also the colour.
  */
-void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
-                       const float* zn_prev, const uint32_t* mesh_prev,
-                       const orc_camera* cam, const orc_camera* cam_prev,
-                       const uint8_t* mask, const uint8_t* ao, const orc_svgf_params* P,
-                       const double* col_hist, const double* mom_in, const int32_t* hist_in,
-                       double* mom_out, int32_t* hist_out, double* illum,
-                       int32_t* valid_out /* optional [H][W] */)
+static void temporal_core(int W, int H, const float* zn, const uint32_t* mesh,
+                          const float* zn_prev, const uint32_t* mesh_prev,
+                          const orc_camera* cam, const orc_camera* cam_prev,
+                          const double* sig, const orc_svgf_params* P,
+                          const double* col_hist, const double* mom_in, const int32_t* hist_in,
+                          double* mom_out, int32_t* hist_out, double* illum,
+                          int32_t* valid_out, orc_trec* rec)
 {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
             int64_t p = (int64_t)y * W + x;
+            if (rec) memset(rec + p, 0, sizeof(orc_trec));
             if (!is_fg(zn, p)) {
                 illum[4 * p + 0] = 1.0; illum[4 * p + 1] = 1.0;
                 illum[4 * p + 2] = 0.0; illum[4 * p + 3] = 0.0;
@@ -803,8 +812,7 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
                 if (valid_out) valid_out[p] = 0;
                 continue;
             }
-            double s[2];
-            noisy(mask, ao, p, P->ao_spp, s);
+            double s[2] = {sig[2 * p], sig[2 * p + 1]};
             double ch[2] = {0, 0}, mh[4] = {0, 0, 0, 0};
             int n = 1, valid = 0;
             if (zn_prev) {
@@ -825,12 +833,23 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
                     }
                     ch[0] /= sw; ch[1] /= sw;
                     for (int c = 0; c < 4; ++c) mh[c] /= sw;
+                    if (rec) {
+                        rec[p].x0 = r.tx[0]; rec[p].y0 = r.ty[0];
+                        for (int k = 0; k < 4; ++k) {
+                            rec[p].ok |= r.ok[k] << k;
+                            rec[p].beta[k] = r.ok[k] ? (double)r.w[k] / sw : 0.0;
+                        }
+                    }
                     n = r.histlen_min + 1;
                     if (n > 255) n = 255;
                 }
             }
             if (valid_out) valid_out[p] = valid;
             double a = valid ? (P->fixed_alpha ? P->alpha : fmax(P->alpha, 1.0 / n)) : 1.0;
+            if (rec) {
+                rec[p].fg = 1; rec[p].valid = valid; rec[p].n = n; rec[p].a = a;
+                rec[p].spatial = n < 4;
+            }
             /* exponential moving average, written h + a (s - h) */
             double c[2], m[4];
             for (int k = 0; k < 2; ++k) {
@@ -859,8 +878,7 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
                         if (dx || dy)
                             w = w_depth(zn[4 * p], zn[4 * q], g, -dx, -dy, P)
                                 * w_normal(zn + 4 * p + 1, zn + 4 * q + 1, P->sigma_n);
-                        double sq[2];
-                        noisy(mask, ao, q, P->ao_spp, sq);
+                        double sq[2] = {sig[2 * q], sig[2 * q + 1]};
                         sw += w;
                         for (int k = 0; k < 2; ++k) { s1[k] += w * sq[k]; s2[k] += w * sq[k] * sq[k]; }
                     }
@@ -873,6 +891,27 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
             }
         }
     }
+}
+
+static double* signals_from_counts(int64_t n, const uint8_t* mask, const uint8_t* ao, int spp)
+{
+    double* sig = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+    for (int64_t p = 0; p < n; ++p) noisy(mask, ao, p, spp, sig + 2 * p);
+    return sig;
+}
+
+void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
+                       const float* zn_prev, const uint32_t* mesh_prev,
+                       const orc_camera* cam, const orc_camera* cam_prev,
+                       const uint8_t* mask, const uint8_t* ao, const orc_svgf_params* P,
+                       const double* col_hist, const double* mom_in, const int32_t* hist_in,
+                       double* mom_out, int32_t* hist_out, double* illum,
+                       int32_t* valid_out /* optional [H][W] */)
+{
+    double* sig = signals_from_counts((int64_t)W * H, mask, ao, P->ao_spp);
+    temporal_core(W, H, zn, mesh, zn_prev, mesh_prev, cam, cam_prev, sig, P, col_hist, mom_in, hist_in,
+                  mom_out, hist_out, illum, valid_out, NULL);
+    free(sig);
 }
 
 /*
@@ -966,8 +1005,10 @@ void orc_svgf_frame(int W, int H, const float* zn, const uint32_t* mesh,
     double* b = (double*)malloc(sizeof(double) * 4 * (size_t)n);
     double* mom2 = (double*)malloc(sizeof(double) * 4 * (size_t)n);
     int32_t* hist2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    orc_svgf_temporal(W, H, zn, mesh, zn_prev, mesh_prev, cam, cam_prev, mask, ao, P,
-                      col_hist, mom, hist, mom2, hist2, a, NULL);
+    double* sig = signals_from_counts(n, mask, ao, P->ao_spp);
+    temporal_core(W, H, zn, mesh, zn_prev, mesh_prev, cam, cam_prev, sig, P,
+                  col_hist, mom, hist, mom2, hist2, a, NULL, NULL);
+    free(sig);
     memcpy(mom, mom2, sizeof(double) * 4 * (size_t)n);
     memcpy(hist, hist2, sizeof(int32_t) * (size_t)n);
     if (illum_out) memcpy(illum_out, a, sizeof(double) * 4 * (size_t)n);
@@ -982,4 +1023,320 @@ void orc_svgf_frame(int W, int H, const float* zn, const uint32_t* mesh,
     }
     for (int64_t p = 0; p < n; ++p) { ao_out[p] = a[4 * p]; sh_out[p] = a[4 * p + 1]; }
     free(a); free(b); free(mom2); free(hist2);
+}
+
+/* ======================================================================== */
+/* 4. Adjoint of the modified SVGF over a sequence of frames (double)       */
+/*                                                                          */
+/* Loss gradient g_out = dL/d(filtered colour) per frame.  Returned: dL/ds  */
+/* for the per-pixel noisy signals s (AO and shadow) of every frame and     */
+/* dL/d(sigma_z, sigma_n, sigma_l).  The temporal recursion is not cut:     */
+/* frame f's level-0 colour and moments feed frame f+1.  The reprojection   */
+/* taps, validity and history lengths depend only on G-buffers and cameras  */
+/* and are constants.  Conventions: d|x|/dx = sign(x) with sign(0) = 0;     */
+/* d max(0, x)/dx = [x > 0]; d sqrt(g)/dg = 0 at g = 0; d w_n/d sigma_n =   */
+/* w_n ln(n.n') where n.n' > 0, else 0.  Written in scatter form: every     */
+/* output pixel pushes its contributions to the inputs it read.             */
+/* ======================================================================== */
+static inline double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+
+/* backward of one a-trous iteration.  in: the iteration's input (colour x2,
+ * variance x2); gc_out, gv_out: dL/d its output colour and variance
+ * ([N][2] each).  Adds dL/d input into gc_in, gv_in ([N][2]) and the sigma
+ * gradients into gsig[3]. */
+static void atrous_backward(int W, int H, const float* zn, const double* in, int step,
+                            const orc_svgf_params* P, const double* gc_out, const double* gv_out,
+                            double* gc_in, double* gv_in, double* gsig)
+{
+    static const double k5[5] = {1.0 / 16, 1.0 / 4, 3.0 / 8, 1.0 / 4, 1.0 / 16};
+    static const double k3[3] = {1.0 / 4, 1.0 / 2, 1.0 / 4};
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t p = (int64_t)y * W + x;
+            if (!is_fg(zn, p)) continue;
+            /* forward quantities at p */
+            double gv[2] = {0, 0}, gw = 0.0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                    int64_t q = (int64_t)qy * W + qx;
+                    if (!is_fg(zn, q)) continue;
+                    double k = k3[dx + 1] * k3[dy + 1];
+                    gw += k;
+                    gv[0] += k * in[4 * q + 2];
+                    gv[1] += k * in[4 * q + 3];
+                }
+            gv[0] /= gw; gv[1] /= gw;
+            double gz[2];
+            depth_grad(W, H, zn, x, y, gz);
+            for (int ch = 0; ch < 2; ++ch) {
+                double root = sqrt(fmax(0.0, gv[ch]));
+                double il = 1.0 / (P->sigma_l * root + P->eps_l);
+                /* pass 1: W, A, B */
+                double Wsum = 0.0, A = 0.0, B = 0.0;
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        int qx = x + i * step, qy = y + j * step;
+                        if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                        int64_t q = (int64_t)qy * W + qx;
+                        if (!is_fg(zn, q)) continue;
+                        double k = k5[i + 2] * k5[j + 2], w = k;
+                        if (i || j) {
+                            double wz = w_depth(zn[4 * p], zn[4 * q], gz, -(double)i * step,
+                                                -(double)j * step, P);
+                            double wn = w_normal(zn + 4 * p + 1, zn + 4 * q + 1, P->sigma_n);
+                            double wl = P->wl_in_atrous
+                                ? exp(-fabs(in[4 * p + ch] - in[4 * q + ch]) * il) : 1.0;
+                            w = k * wz * wn * wl;
+                        }
+                        Wsum += w;
+                        A += w * in[4 * q + ch];
+                        B += w * w * in[4 * q + 2 + ch];
+                    }
+                double cp_out = A / Wsum, vp_out = B / (Wsum * Wsum);
+                double Gc = gc_out[2 * p + ch], Gv = gv_out[2 * p + ch];
+                double Gil = 0.0;
+                /* pass 2: push gradients to the taps */
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        int qx = x + i * step, qy = y + j * step;
+                        if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                        int64_t q = (int64_t)qy * W + qx;
+                        if (!is_fg(zn, q)) continue;
+                        double k = k5[i + 2] * k5[j + 2], w = k;
+                        double wz = 1.0, wn = 1.0, wl = 1.0, a_off = 0.0, D = 1.0, dlt = 0.0;
+                        double nd = 1.0;
+                        if (i || j) {
+                            a_off = fabs(gz[0] * (-(double)i * step) + gz[1] * (-(double)j * step));
+                            D = P->sigma_z * a_off + P->eps_z;
+                            wz = exp(-fabs((double)zn[4 * p] - (double)zn[4 * q]) / D);
+                            const float* np_ = zn + 4 * p + 1;
+                            const float* nq_ = zn + 4 * q + 1;
+                            nd = (double)np_[0] * nq_[0] + (double)np_[1] * nq_[1] + (double)np_[2] * nq_[2];
+                            wn = w_normal(np_, nq_, P->sigma_n);
+                            dlt = in[4 * p + ch] - in[4 * q + ch];
+                            if (P->wl_in_atrous) wl = exp(-fabs(dlt) * il);
+                            w = k * wz * wn * wl;
+                        }
+                        double cq = in[4 * q + ch], vq = in[4 * q + 2 + ch];
+                        /* direct dependence of the output on the tap values */
+                        gc_in[2 * q + ch] += Gc * w / Wsum;
+                        gv_in[2 * q + ch] += Gv * w * w / (Wsum * Wsum);
+                        if (!(i || j)) continue;          /* centre weight is a constant */
+                        /* dependence through the weight */
+                        double Gw = Gc * (cq - cp_out) / Wsum
+                                    + Gv * (2.0 * w * vq / (Wsum * Wsum) - 2.0 * vp_out / Wsum);
+                        if (P->wl_in_atrous) {
+                            double dwdc = w * il * sgn(dlt);            /* dw/dc_q; dw/dc_p = -dwdc */
+                            gc_in[2 * q + ch] += Gw * dwdc;
+                            gc_in[2 * p + ch] -= Gw * dwdc;
+                            Gil += Gw * (-w * fabs(dlt));
+                        }
+                        double dz = fabs((double)zn[4 * p] - (double)zn[4 * q]);
+                        gsig[0] += Gw * w * dz * a_off / (D * D);
+                        if (nd > 0.0) gsig[1] += Gw * w * log(nd);
+                    }
+                /* il = 1 / (sigma_l sqrt(g) + eps_l) */
+                if (P->wl_in_atrous) {
+                    gsig[2] += Gil * (-il * il * root);
+                    if (gv[ch] > 0.0) {
+                        double Gg = Gil * (-il * il * P->sigma_l * 0.5 / root);
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int qx = x + dx, qy = y + dy;
+                                if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                                int64_t q = (int64_t)qy * W + qx;
+                                if (!is_fg(zn, q)) continue;
+                                gv_in[2 * q + ch] += Gg * k3[dx + 1] * k3[dy + 1] / gw;
+                            }
+                    }
+                }
+            }
+        }
+    }
+}
+
+/* backward of the temporal step of one frame.  gc, gv: dL/d illum colour
+ * and variance ([N][2]); gmom: dL/d this frame's moments output ([N][4]).
+ * Adds dL/ds into gsig_s ([N][2]), dL/d the previous frame's colour history
+ * and moments into gcol_prev ([N][2]), gmom_prev ([N][4]), sigma gradients
+ * of the spatial estimate into gsig[0..1]. */
+static void temporal_backward(int W, int H, const float* zn, const double* sig, const double* mom,
+                              const orc_trec* rec, const orc_svgf_params* P, const double* gc,
+                              const double* gv, const double* gmom, double* gsig_s,
+                              double* gcol_prev, double* gmom_prev, double* gsig)
+{
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t p = (int64_t)y * W + x;
+            const orc_trec* r = rec + p;
+            if (!r->fg) continue;
+            double a = r->a;
+            double Gc_ema[2] = {0, 0}, Gm[4];
+            for (int k = 0; k < 4; ++k) Gm[k] = gmom[4 * p + k];
+            if (!r->spatial) {
+                for (int ch = 0; ch < 2; ++ch) {
+                    Gc_ema[ch] = gc[2 * p + ch];
+                    double mu1 = mom[4 * p + ch], mu2 = mom[4 * p + 2 + ch];
+                    if (mu2 - mu1 * mu1 > 0.0) {            /* var = max(0, mu2 - mu1^2) */
+                        Gm[2 + ch] += gv[2 * p + ch];
+                        Gm[ch] += -2.0 * mu1 * gv[2 * p + ch];
+                    }
+                }
+            } else {
+                /* colour = m1, var = max(0, m2 - m1^2), m_k = sum w s^k / sum w
+                 * over the 7x7 window with w = w_z w_n (centre 1) */
+                double gz[2];
+                depth_grad(W, H, zn, x, y, gz);
+                double sw = 0.0, s1[2] = {0, 0}, s2[2] = {0, 0};
+                for (int pass = 0; pass < 2; ++pass) {
+                    double m1[2], m2[2], Gm1[2], Gm2[2];
+                    if (pass == 1) {
+                        for (int ch = 0; ch < 2; ++ch) {
+                            m1[ch] = s1[ch] / sw;
+                            m2[ch] = s2[ch] / sw;
+                            double var = m2[ch] - m1[ch] * m1[ch];
+                            Gm1[ch] = gc[2 * p + ch] - (var > 0.0 ? 2.0 * m1[ch] * gv[2 * p + ch] : 0.0);
+                            Gm2[ch] = var > 0.0 ? gv[2 * p + ch] : 0.0;
+                        }
+                    }
+                    for (int dy = -3; dy <= 3; ++dy)
+                        for (int dx = -3; dx <= 3; ++dx) {
+                            int qx = x + dx, qy = y + dy;
+                            if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                            int64_t q = (int64_t)qy * W + qx;
+                            if (!is_fg(zn, q)) continue;
+                            double w = 1.0, a_off = 0.0, D = 1.0, nd = 1.0;
+                            if (dx || dy) {
+                                a_off = fabs(gz[0] * (double)(-dx) + gz[1] * (double)(-dy));
+                                D = P->sigma_z * a_off + P->eps_z;
+                                nd = (double)zn[4 * p + 1] * zn[4 * q + 1] + (double)zn[4 * p + 2] * zn[4 * q + 2]
+                                     + (double)zn[4 * p + 3] * zn[4 * q + 3];
+                                w = w_depth(zn[4 * p], zn[4 * q], gz, -dx, -dy, P)
+                                    * w_normal(zn + 4 * p + 1, zn + 4 * q + 1, P->sigma_n);
+                            }
+                            if (pass == 0) {
+                                sw += w;
+                                for (int ch = 0; ch < 2; ++ch) {
+                                    s1[ch] += w * sig[2 * q + ch];
+                                    s2[ch] += w * sig[2 * q + ch] * sig[2 * q + ch];
+                                }
+                                continue;
+                            }
+                            double Gw = 0.0;
+                            for (int ch = 0; ch < 2; ++ch) {
+                                double sq = sig[2 * q + ch];
+                                gsig_s[2 * q + ch] += Gm1[ch] * w / sw + Gm2[ch] * 2.0 * sq * w / sw;
+                                Gw += Gm1[ch] * (sq - m1[ch]) / sw + Gm2[ch] * (sq * sq - m2[ch]) / sw;
+                            }
+                            if (dx || dy) {
+                                double dz = fabs((double)zn[4 * p] - (double)zn[4 * q]);
+                                gsig[0] += Gw * w * dz * a_off / (D * D);
+                                if (nd > 0.0) gsig[1] += Gw * w * log(nd);
+                            }
+                        }
+                }
+            }
+            /* moving averages c = c_h + a (s - c_h), mu1 likewise, mu2 with s^2 */
+            for (int ch = 0; ch < 2; ++ch) {
+                double sv = sig[2 * p + ch];
+                gsig_s[2 * p + ch] += a * Gc_ema[ch] + a * Gm[ch] + 2.0 * a * sv * Gm[2 + ch];
+            }
+            if (!r->valid) continue;
+            double Gch[2] = {(1.0 - a) * Gc_ema[0], (1.0 - a) * Gc_ema[1]};
+            double Gmh[4];
+            for (int k = 0; k < 4; ++k) Gmh[k] = (1.0 - a) * Gm[k];
+            for (int t = 0; t < 4; ++t) {
+                if (!(r->ok & (1 << t))) continue;
+                int64_t q = (int64_t)(r->y0 + (t >> 1)) * W + (r->x0 + (t & 1));
+                double b = r->beta[t];
+                gcol_prev[2 * q] += b * Gch[0];
+                gcol_prev[2 * q + 1] += b * Gch[1];
+                for (int k = 0; k < 4; ++k) gmom_prev[4 * q + k] += b * Gmh[k];
+            }
+        }
+    }
+}
+
+/*
+ * Forward and adjoint of the modified SVGF over F consecutive frames that
+ * start without history.  zn [F][H][W][4], mesh [F][H][W], cams [F],
+ * sig [F][H][W][2] (noisy AO and shadow in [0, 1]), g_out [F][H][W][2]
+ * (dL/d filtered colour).  Outputs out [F][H][W][2], g_sig [F][H][W][2],
+ * g_sigma[3] = dL/d(sigma_z, sigma_n, sigma_l).
+ */
+void orc_svgf_seq_grad(int F, int W, int H, const float* zn, const uint32_t* mesh,
+                       const orc_camera* cams, const double* sig, const orc_svgf_params* P,
+                       const double* g_out, double* out, double* g_sig, double* g_sigma)
+{
+    int64_t N = (int64_t)W * H;
+    int L = P->levels;
+    /* recordings */
+    double* lev = (double*)calloc((size_t)F * (L + 1) * N * 4, sizeof(double));
+    double* mom = (double*)calloc((size_t)F * N * 4, sizeof(double));
+    orc_trec* rec = (orc_trec*)calloc((size_t)F * N, sizeof(orc_trec));
+    double* col = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* mom_prev = (double*)calloc((size_t)N * 4, sizeof(double));
+    int32_t* hist = (int32_t*)calloc((size_t)N, sizeof(int32_t));
+    int32_t* hist2 = (int32_t*)calloc((size_t)N, sizeof(int32_t));
+    for (int f = 0; f < F; ++f) {
+        const float* znf = zn + (size_t)f * N * 4;
+        const float* znp = f ? zn + (size_t)(f - 1) * N * 4 : NULL;
+        const uint32_t* mp = f ? mesh + (size_t)(f - 1) * N : NULL;
+        double* illum = lev + ((size_t)f * (L + 1)) * N * 4;
+        double* momf = mom + (size_t)f * N * 4;
+        temporal_core(W, H, znf, mesh + (size_t)f * N, znp, mp, cams + f, f ? cams + f - 1 : cams + f,
+                      sig + (size_t)f * N * 2, P, col, mom_prev, hist, momf, hist2, illum, NULL,
+                      rec + (size_t)f * N);
+        memcpy(mom_prev, momf, sizeof(double) * 4 * (size_t)N);
+        memcpy(hist, hist2, sizeof(int32_t) * (size_t)N);
+        for (int l = 0; l < L; ++l)
+            orc_svgf_atrous(W, H, znf, illum + (size_t)l * N * 4, 1 << l, P, illum + (size_t)(l + 1) * N * 4);
+        const double* first = illum + (size_t)(L ? 1 : 0) * N * 4;
+        const double* last = illum + (size_t)L * N * 4;
+        for (int64_t p = 0; p < N; ++p) {
+            col[2 * p] = first[4 * p];
+            col[2 * p + 1] = first[4 * p + 1];
+            out[(size_t)f * N * 2 + 2 * p] = last[4 * p];
+            out[(size_t)f * N * 2 + 2 * p + 1] = last[4 * p + 1];
+        }
+    }
+    /* backward */
+    double* gc = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* gv = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* gc2 = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* gv2 = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* gcol_next = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* gmom_next = (double*)calloc((size_t)N * 4, sizeof(double));
+    double* gcol_prev = (double*)calloc((size_t)N * 2, sizeof(double));
+    double* gmom_prev = (double*)calloc((size_t)N * 4, sizeof(double));
+    memset(g_sig, 0, sizeof(double) * (size_t)F * N * 2);
+    g_sigma[0] = g_sigma[1] = g_sigma[2] = 0.0;
+    for (int f = F - 1; f >= 0; --f) {
+        const float* znf = zn + (size_t)f * N * 4;
+        double* illum = lev + ((size_t)f * (L + 1)) * N * 4;
+        memcpy(gc, g_out + (size_t)f * N * 2, sizeof(double) * 2 * (size_t)N);
+        memset(gv, 0, sizeof(double) * 2 * (size_t)N);
+        for (int l = L - 1; l >= 0; --l) {
+            if (l == 0)   /* level-0 colour is also next frame's colour history */
+                for (int64_t i = 0; i < 2 * N; ++i) gc[i] += gcol_next[i];
+            memset(gc2, 0, sizeof(double) * 2 * (size_t)N);
+            memset(gv2, 0, sizeof(double) * 2 * (size_t)N);
+            atrous_backward(W, H, znf, illum + (size_t)l * N * 4, 1 << l, P, gc, gv, gc2, gv2, g_sigma);
+            memcpy(gc, gc2, sizeof(double) * 2 * (size_t)N);
+            memcpy(gv, gv2, sizeof(double) * 2 * (size_t)N);
+        }
+        if (L == 0)
+            for (int64_t i = 0; i < 2 * N; ++i) gc[i] += gcol_next[i];
+        memset(gcol_prev, 0, sizeof(double) * 2 * (size_t)N);
+        memset(gmom_prev, 0, sizeof(double) * 4 * (size_t)N);
+        temporal_backward(W, H, znf, sig + (size_t)f * N * 2, mom + (size_t)f * N * 4, rec + (size_t)f * N, P,
+                          gc, gv, gmom_next, g_sig + (size_t)f * N * 2, gcol_prev, gmom_prev, g_sigma);
+        memcpy(gcol_next, gcol_prev, sizeof(double) * 2 * (size_t)N);
+        memcpy(gmom_next, gmom_prev, sizeof(double) * 4 * (size_t)N);
+    }
+    free(lev); free(mom); free(rec); free(col); free(mom_prev); free(hist); free(hist2);
+    free(gc); free(gv); free(gc2); free(gv2); free(gcol_next); free(gmom_next); free(gcol_prev);
+    free(gmom_prev);
 }
