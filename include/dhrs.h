@@ -235,6 +235,38 @@ dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur,
                                 const uint8_t* ao_count, const dhr_svgf_params* params,
                                 float* ao_out, float* shadow_out, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Differentiable form of the modified SVGF (no counterpart in the paper,  */
+/* which only runs the filter forward; this is its adjoint, Section 3.3)   */
+/* ---------------------------------------------------------------------- */
+typedef struct dhr_svgf_tape dhr_svgf_tape;
+
+/* Recording space for F frames of W x H (FP32): per frame the temporal
+ * output, moments and history lengths (33 B/px), plus work buffers. */
+dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_t frames, dhr_svgf_tape** out);
+void dhr_svgf_tape_destroy(dhr_svgf_tape* tape);
+
+/* Forward over F consecutive frames starting without history, recording
+ * into `tape`.  gbufs, cams: host arrays of F FP32 G-buffer descriptors and
+ * cameras (the G-buffers are device memory and must stay unchanged until
+ * the backward call).  sig (device, float [F][2][H][W]): noisy AO and
+ * shadow signals in [0, 1] (planes).  out (device, float [F][2][H][W]):
+ * filtered AO and shadow. */
+dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, const dhr_camera* cams,
+                                const float* sig, const dhr_svgf_params* params, float* out,
+                                void* stream);
+
+/* Backward of the last dhr_svgf_seq_forward on `tape` (same arguments):
+ * g_out (device, [F][2][H][W]) = dL/d out.  Writes g_sig (device,
+ * [F][2][H][W]) = dL/d sig and g_sigma (device, float [3]) = dL/d
+ * (sigma_z, sigma_n, sigma_l).  The a-trous levels are recomputed from the
+ * recorded temporal outputs; history scatter and the short-history
+ * variance estimate accumulate with atomics (summation order may vary).
+ * Errors: DHR_ERR_STATE without a preceding forward. */
+dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, const dhr_camera* cams,
+                                 const float* sig, const dhr_svgf_params* params, const float* g_out,
+                                 float* g_sig, float* g_sigma, void* stream);
+
 /* Allocation-free variant of the a-trous part of dhr_svgf_reconstruct.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they filter (a frame loop that must

@@ -89,6 +89,10 @@ _SIGNATURES = {
     "dhr_svgf_get_buffers": ([_P, _P], C.c_int),
     "dhr_svgf_reconstruct": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_svgf_atrous_noalloc": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_svgf_tape_create": ([C.c_int32, C.c_int32, C.c_int32, _P], C.c_int),
+    "dhr_svgf_tape_destroy": ([_P], None),
+    "dhr_svgf_seq_forward": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_svgf_seq_backward": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_session_create": ([_P, C.c_int32, C.c_int32, C.c_int, _P, _P, _P], C.c_int),
     "dhr_session_destroy": ([_P], None),
     "dhr_step_frame": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
@@ -409,3 +413,93 @@ class Session:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------- adjoint
+class SvgfTape:
+    """Recording of the differentiable SVGF over F frames (FP32)."""
+
+    def __init__(self, width, height, frames):
+        h = C.c_void_p()
+        _check(lib().dhr_svgf_tape_create(width, height, frames, C.byref(h)))
+        self.h, self.width, self.height, self.frames = h, width, height, frames
+
+    @staticmethod
+    def _arrays(gbufs, cams):
+        g = (GBufferC * len(gbufs))(*[x.c() for x in gbufs])
+        c = (Camera * len(cams))(*[camera(x) for x in cams])
+        return g, c
+
+    def forward(self, gbufs, cams, sig, params: SvgfParams, stream=None):
+        """sig: CUDA float32 [F, 2, H, W] -> filtered [F, 2, H, W]."""
+        import torch
+        _need_cuda(sig)
+        out = torch.empty_like(sig)
+        g, c = self._arrays(gbufs, cams)
+        p = params.to_c()
+        _check(lib().dhr_svgf_seq_forward(self.h, g, c, _ptr(sig), C.byref(p), _ptr(out), _stream(stream)))
+        return out
+
+    def backward(self, gbufs, cams, sig, params: SvgfParams, g_out, stream=None):
+        """-> (dL/d sig [F, 2, H, W], dL/d (sigma_z, sigma_n, sigma_l) [3])."""
+        import torch
+        g_out = g_out.contiguous()
+        _need_cuda(sig, g_out)
+        g_sig = torch.empty_like(sig)
+        g_sigma = torch.empty(3, dtype=torch.float32, device=sig.device)
+        g, c = self._arrays(gbufs, cams)
+        p = params.to_c()
+        _check(lib().dhr_svgf_seq_backward(self.h, g, c, _ptr(sig), C.byref(p), _ptr(g_out), _ptr(g_sig),
+                                           _ptr(g_sigma), _stream(stream)))
+        return g_sig, g_sigma
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dhr_svgf_tape_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _svgf_function():
+    import torch
+
+    class SVGFSequence(torch.autograd.Function):
+        """out = SVGF(sig; sigma_z, sigma_n, sigma_l) over a frame sequence;
+        backward = the hand-written CUDA adjoint (levels recomputed)."""
+
+        @staticmethod
+        def forward(ctx, sig, sigmas, gbufs, cams, params, tape):
+            sz, sn, sl = [float(v) for v in sigmas.detach().cpu()]
+            p = SvgfParams(**{**params.__dict__, "sigma_z": sz, "sigma_n": sn, "sigma_l": sl})
+            sig_c = sig.detach().contiguous()
+            out = tape.forward(gbufs, cams, sig_c, p)
+            ctx.tape, ctx.gbufs, ctx.cams, ctx.p, ctx.sig = tape, gbufs, cams, p, sig_c
+            ctx.sigmas_meta = (sigmas.dtype, sigmas.device)
+            return out
+
+        @staticmethod
+        def backward(ctx, g_out):
+            g_sig, g_sigma = ctx.tape.backward(ctx.gbufs, ctx.cams, ctx.sig, ctx.p, g_out)
+            dt, dev = ctx.sigmas_meta
+            return g_sig, g_sigma.to(device=dev, dtype=dt), None, None, None, None
+
+    return SVGFSequence
+
+
+_SVGF_FN = None
+
+
+def svgf_sequence(sig, sigmas, gbufs, cams, params: SvgfParams = None, tape: SvgfTape = None):
+    """Differentiable SVGF: sig [F, 2, H, W] (CUDA float32, may require grad),
+    sigmas [3] = (sigma_z, sigma_n, sigma_l) (may require grad)."""
+    global _SVGF_FN
+    if _SVGF_FN is None:
+        _SVGF_FN = _svgf_function()
+    F, _, H, W = sig.shape
+    tape = tape or SvgfTape(W, H, F)
+    return _SVGF_FN.apply(sig, sigmas, gbufs, cams, params or SvgfParams(), tape)

@@ -79,5 +79,6 @@ dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_tr
                         unsigned long long* stats = nullptr);
 
 dhr_status check_trace_params(const dhr_trace_params* p);
+dhr_status check_svgf_params(const dhr_svgf_params* p);
 
 }  // namespace dhr
