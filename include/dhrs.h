@@ -107,7 +107,10 @@ typedef struct {
 /* G-buffer (caller-owned device memory, W*H pixels).
  *  FP32: depth_normal = float4 per pixel (linear view depth, unit normal x,
  *        y, z facing the camera);
- *  FP16: depth_normal = 4 x binary16 per pixel, same fields.
+ *  FP16: depth_normal = 8 bytes per pixel: binary32 linear depth, then the
+ *        normal as two binary16 octahedral coordinates (depth stays
+ *        binary32: the depth edge-stopping weight of Section 3.3 compares
+ *        depth differences below binary16 resolution).
  *  mesh_id = uint32 per pixel (DHR_BACKGROUND on a miss).
  *  Both pointers must be 16-byte aligned. */
 typedef struct {
@@ -188,6 +191,11 @@ dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_camera* cam,
 dhr_status dhr_cast_rays(const dhr_scene* scene, const float* origins, const float* dirs,
                          const float* tmin, const float* tmax, int32_t any_hit, int64_t n,
                          float* t_out, int32_t* tri_out, void* stream);
+
+/* Converts a G-buffer between the FP32 and FP16 storage forms (device to
+ * device, same size; mesh ids are copied).  Errors: DHR_ERR_INVALID for
+ * size mismatch or equal precisions. */
+dhr_status dhr_gbuffer_convert(const dhr_gbuffer* src, dhr_gbuffer* dst, void* stream);
 
 /* Traversal work counters of one dhr_trace_visibility frame (runs a
  * counting variant of the trace kernel into scratch buffers it allocates;

@@ -82,6 +82,7 @@ _SIGNATURES = {
     "dhr_trace_visibility": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_cast_rays": ([_P, _P, _P, _P, _P, C.c_int32, C.c_int64, _P, _P, _P], C.c_int),
     "dhr_trace_stats": ([_P, _P, _P, _P, _P], C.c_int),
+    "dhr_gbuffer_convert": ([_P, _P, _P], C.c_int),
     "dhr_sample_directions": ([_P, _P, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32, _P, _P,
                                C.c_float, _P, _P, _P, _P, _P], C.c_int),
     "dhr_svgf_create": ([C.c_int32, C.c_int32, C.c_int, _P], C.c_int),
@@ -201,24 +202,40 @@ class SvgfParams:
 
 # --------------------------------------------------------------- G-buffer
 class GBuffer:
-    """Device G-buffer: depth_normal [H, W, 4] (float32 or float16) + mesh [H, W] int32
-    (bit pattern of the uint32 mesh id)."""
+    """Device G-buffer + mesh ids [H, W] int32 (bit pattern of the uint32 id).
+    FP32: depth_normal float32 [H, W, 4] (depth, normal).  FP16: int32
+    [H, W, 2] = (binary32 depth bits, two binary16 octahedral normal
+    coordinates) -- use to_fp32() to read it."""
 
     def __init__(self, width, height, precision=DHR_FP32, device="cuda"):
         import torch
         self.width, self.height, self.precision = width, height, precision
-        dt = torch.float16 if precision == DHR_FP16 else torch.float32
-        self.depth_normal = torch.empty((height, width, 4), dtype=dt, device=device)
+        if precision == DHR_FP16:
+            self.depth_normal = torch.empty((height, width, 2), dtype=torch.int32, device=device)
+        else:
+            self.depth_normal = torch.empty((height, width, 4), dtype=torch.float32, device=device)
         self.mesh = torch.empty((height, width), dtype=torch.int32, device=device)
 
     @classmethod
     def from_arrays(cls, zn, mesh, precision=DHR_FP32, device="cuda"):
+        """Upload a float32 [H, W, 4] G-buffer; FP16 is packed on the device."""
         import torch
         H, W = mesh.shape
-        g = cls(W, H, precision, device)
-        g.depth_normal.copy_(torch.from_numpy(np.ascontiguousarray(zn)).to(g.depth_normal.dtype))
-        g.mesh.copy_(torch.from_numpy(np.ascontiguousarray(mesh).view(np.int32)))
+        g32 = cls(W, H, DHR_FP32, device)
+        g32.depth_normal.copy_(torch.from_numpy(np.ascontiguousarray(zn, np.float32)))
+        g32.mesh.copy_(torch.from_numpy(np.ascontiguousarray(mesh).view(np.int32)))
+        if precision == DHR_FP32:
+            return g32
+        return g32.convert(precision)
+
+    def convert(self, precision):
+        g = GBuffer(self.width, self.height, precision, self.depth_normal.device)
+        a, b = self.c(), g.c()
+        _check(lib().dhr_gbuffer_convert(C.byref(a), C.byref(b), _stream(None)))
         return g
+
+    def to_fp32(self):
+        return self if self.precision == DHR_FP32 else self.convert(DHR_FP32)
 
     def c(self) -> GBufferC:
         return GBufferC(self.precision, self.width, self.height, self.depth_normal.data_ptr(),

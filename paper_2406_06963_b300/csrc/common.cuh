@@ -1,6 +1,7 @@
 // Internal declarations shared by the libdhrs translation units.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,6 +55,42 @@ struct SceneView {
 };
 
 constexpr int kStackSize = 64;
+
+// Reduced-precision G-buffer element (DHR_FP16 form), 8 bytes: x = binary32
+// linear depth, y = unit normal as two binary16 octahedral coordinates
+// (Cigolle et al., "A Survey of Efficient Representations for Independent
+// Unit Vectors", JCGT 2014).  Depth stays binary32: the depth edge-stopping
+// weight compares depth differences far below binary16 resolution.
+__device__ __forceinline__ float oct_sign(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ uint2 pack_gbuf16(float depth, float3 n) {
+    const float s = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
+    float ex = 0.0f, ey = 0.0f;
+    if (s > 0.0f) {
+        ex = n.x / s;
+        ey = n.y / s;
+        if (n.z < 0.0f) {
+            const float tx = (1.0f - fabsf(ey)) * oct_sign(ex), ty = (1.0f - fabsf(ex)) * oct_sign(ey);
+            ex = tx;
+            ey = ty;
+        }
+    }
+    const __half2 h = __floats2half2_rn(ex, ey);
+    return make_uint2(__float_as_uint(depth), *reinterpret_cast<const uint32_t*>(&h));
+}
+
+__device__ __forceinline__ float4 unpack_gbuf16(uint2 u) {
+    const uint32_t hb = u.y;
+    const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&hb));
+    float3 v = make_float3(e.x, e.y, 1.0f - fabsf(e.x) - fabsf(e.y));
+    if (v.z < 0.0f) {
+        const float tx = (1.0f - fabsf(e.y)) * oct_sign(e.x), ty = (1.0f - fabsf(e.x)) * oct_sign(e.y);
+        v.x = tx;
+        v.y = ty;
+    }
+    const float r = rsqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    return make_float4(__uint_as_float(u.x), v.x * r, v.y * r, v.z * r);
+}
 
 }  // namespace dhr
 

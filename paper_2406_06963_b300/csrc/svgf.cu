@@ -184,6 +184,49 @@ extern "C" dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuf
 }
 
 // ------------------------------------------------------------------------
+// G-buffer precision conversion (FP32 <-> FP16 storage form)
+// ------------------------------------------------------------------------
+namespace dhr {
+namespace {
+__global__ void gbuf_to16_kernel(int n, const float4* src, uint2* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = src[i];
+    dst[i] = pack_gbuf16(v.x, make_float3(v.y, v.z, v.w));
+}
+__global__ void gbuf_to32_kernel(int n, const uint2* src, float4* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 u = src[i];
+    float4 v = unpack_gbuf16(u);
+    if (!(v.x < INFINITY)) v = make_float4(v.x, 0.f, 0.f, 0.f);
+    dst[i] = v;
+}
+}  // namespace
+}  // namespace dhr
+
+extern "C" dhr_status dhr_gbuffer_convert(const dhr_gbuffer* src, dhr_gbuffer* dst, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(src && dst && src->depth_normal && dst->depth_normal && src->mesh_id && dst->mesh_id,
+                  "gbuffer_convert: null pointer");
+    DHR_CHECK_ARG(src->width == dst->width && src->height == dst->height && src->width > 0 && src->height > 0,
+                  "gbuffer_convert: size mismatch");
+    DHR_CHECK_ARG(src->precision != dst->precision, "gbuffer_convert: same precision");
+    const int n = src->width * src->height;
+    cudaStream_t st = as_stream(stream);
+    if (src->precision == DHR_FP32)
+        gbuf_to16_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, static_cast<const float4*>(src->depth_normal),
+                                                          static_cast<uint2*>(dst->depth_normal));
+    else
+        gbuf_to32_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, static_cast<const uint2*>(src->depth_normal),
+                                                          static_cast<float4*>(dst->depth_normal));
+    DHR_CUDA_TRY(cudaGetLastError());
+    if (src->mesh_id != dst->mesh_id)
+        DHR_CUDA_TRY(cudaMemcpyAsync(dst->mesh_id, src->mesh_id, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    return DHR_OK;
+}
+
+// ------------------------------------------------------------------------
 // Allocation-free a-trous cascade.
 //
 // Some callers cannot allocate device memory at the moment they filter: a

@@ -14,9 +14,10 @@
 //    colour history and the last iteration writes the outputs.
 //
 // Storage precision is a template parameter: FP32 keeps every buffer in
-// binary32; FP16 stores the G-buffer (depth, normal), the colour history and
-// the moments in binary16 and keeps the variance-carrying buffer in binary32
-// (its mu2 - mu1^2 cancellation needs the precision); arithmetic is binary32.
+// binary32; FP16 stores the normal (octahedral), the colour history and the
+// moments in binary16 and keeps depth and the variance-carrying buffer in
+// binary32 (depth differences far below binary16 resolution drive w_z, and
+// the variance mu2 - mu1^2 cancels); arithmetic is binary32.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -42,22 +43,12 @@ struct Store<DHR_FP32> {
 
 template <>
 struct Store<DHR_FP16> {
-    using G = ushort4;
+    using G = uint2;
     using Col = __half2;
     using Mom = ushort4;
     static __device__ __forceinline__ float h(unsigned short u) { return __half2float(__ushort_as_half(u)); }
     static __device__ __forceinline__ unsigned short q(float f) { return __half_as_ushort(__float2half_rn(f)); }
-    static __device__ __forceinline__ float4 g(const G* p, size_t i) {
-        const ushort4 u = __ldg(p + i);
-        const float z = h(u.x);
-        float3 n = make_float3(h(u.y), h(u.z), h(u.w));
-        const float l2 = n.x * n.x + n.y * n.y + n.z * n.z;
-        if (l2 > 0.0f) {                      // renormalise the quantised normal
-            const float r = rsqrtf(l2);
-            n = make_float3(n.x * r, n.y * r, n.z * r);
-        }
-        return make_float4(z, n.x, n.y, n.z);
-    }
+    static __device__ __forceinline__ float4 g(const G* p, size_t i) { return unpack_gbuf16(__ldg(p + i)); }
     static __device__ __forceinline__ float2 col(const Col* p, size_t i) { return __half22float2(p[i]); }
     static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = __float22half2_rn(v); }
     static __device__ __forceinline__ float4 mom(const Mom* p, size_t i) {

@@ -243,8 +243,7 @@ __global__ void __launch_bounds__(128) trace_kernel(SceneView sc, TraceConsts k,
     }
     if (leaf < 0) {
         if (kHalf) {
-            reinterpret_cast<ushort4*>(gbuf_dn)[pix] =
-                make_ushort4(__half_as_ushort(__float2half_rn(INFINITY)), 0, 0, 0);
+            reinterpret_cast<uint2*>(gbuf_dn)[pix] = pack_gbuf16(INFINITY, make_float3(0.f, 0.f, 0.f));
         } else {
             reinterpret_cast<float4*>(gbuf_dn)[pix] = make_float4(INFINITY, 0.f, 0.f, 0.f);
         }
@@ -266,9 +265,7 @@ __global__ void __launch_bounds__(128) trace_kernel(SceneView sc, TraceConsts k,
     if (dot(n, D) > 0.0f) n = make_float3(-n.x, -n.y, -n.z);
     const float depth = dot(sub(X, eye), fw);
     if (kHalf) {
-        reinterpret_cast<ushort4*>(gbuf_dn)[pix] = make_ushort4(
-            __half_as_ushort(__float2half_rn(depth)), __half_as_ushort(__float2half_rn(n.x)),
-            __half_as_ushort(__float2half_rn(n.y)), __half_as_ushort(__float2half_rn(n.z)));
+        reinterpret_cast<uint2*>(gbuf_dn)[pix] = pack_gbuf16(depth, n);
     } else {
         reinterpret_cast<float4*>(gbuf_dn)[pix] = make_float4(depth, n.x, n.y, n.z);
     }

@@ -12,7 +12,7 @@ def trace_gpu(scene, cam, params, precision=dhrs.DHR_FP32):
     ao = torch.empty_like(mask)
     dhrs.trace_visibility(scene, cam, params, g, mask, ao)
     torch.cuda.synchronize()
-    zn = g.depth_normal.float().cpu().numpy().reshape(-1, 4)
+    zn = g.to_fp32().depth_normal.cpu().numpy().reshape(-1, 4)
     return dict(depth=zn[:, 0].astype(np.float64), normal=zn[:, 1:].astype(np.float64),
                 mesh=g.mesh_u32().ravel(), shadow_mask=mask.cpu().numpy().ravel(),
                 ao_count=ao.cpu().numpy().ravel(), gbuf=g, mask_t=mask, ao_t=ao)

@@ -1,8 +1,13 @@
-"""FP16 storage form: G-buffer (depth, normal), colour history and moments
-stored in binary16, arithmetic, intersection and the variance buffer in
-binary32.  Per-buffer error against the fp64 oracle (same inputs, the
-oracle's G-buffer rounded to binary16 for the GPU) and against the FP32
-path, reported and bounded.
+"""FP16 storage form: the normal (two binary16 octahedral coordinates), the
+colour history and the moments in binary16; depth, the variance buffer,
+intersection and all arithmetic in binary32.  Per-buffer error against the
+fp64 oracle (same inputs; the oracle's G-buffer packed into the FP16 form for
+the GPU) and against the FP32 path, reported and bounded.
+
+(An earlier layout also stored depth in binary16: surfaces whose depth
+changes by less than one binary16 step per pixel then get a zero depth
+gradient, the depth weight exp(-|dz| / eps_z) removes every tap and those
+regions stop being filtered -- AO p99 error 2.5e-2.)
 """
 import numpy as np
 import pytest
@@ -44,7 +49,7 @@ def test_fp16_storage_vs_fp64_oracle():
                         torch.from_numpy(mask).cuda(), torch.from_numpy(cnt).cuda(), dhrs.SvgfParams(), ao_o, sh_o)
         torch.cuda.synchronize()
         fg = np.isfinite(zn[..., 0])
-        gz = g.depth_normal.float().cpu().numpy()
+        gz = g.to_fp32().depth_normal.cpu().numpy()
         table["depth"].append((gz[..., 0][fg] - tr["depth"].reshape(H, W)[fg]) / tr["depth"].reshape(H, W)[fg])
         table["normal"].append((gz[..., 1:] - tr["normal"].reshape(H, W, 3))[fg])
         b = gst.buffers()
@@ -58,8 +63,8 @@ def test_fp16_storage_vs_fp64_oracle():
     rep = {k: _stats(np.concatenate([np.ravel(x) for x in v])) for k, v in table.items()}
     for k, v in rep.items():
         print(f"fp16 vs fp64 oracle  {k:10s} max {v['max']:.3g}  p99 {v['p99']:.3g}  mean {v['mean']:.3g}")
-    assert rep["depth"]["max"] < 1e-3            # binary16: relative 2^-11
-    assert rep["normal"]["max"] < 1e-3
+    assert rep["depth"]["max"] < 1e-6            # binary32 depth
+    assert rep["normal"]["max"] < 2e-3           # octahedral binary16
     for k in ("ao", "shadow"):
         assert rep[k]["p99"] <= 1e-3 and rep[k]["mean"] <= 1e-4, (k, rep[k])
 
