@@ -327,6 +327,92 @@ dhr_status dhr_session_get_frame(dhr_session* session, dhr_gbuffer* gbuf,
 /* Drops the SVGF history: the next frame starts without history. */
 dhr_status dhr_session_reset(dhr_session* session);
 
+/* ---------------------------------------------------------------------- */
+/* Serving: many thin-client sessions with continuous batching             */
+/* (Section 1 and Section 4.1 describe one remote server per client and    */
+/* delayed camera data; this serves many sessions from one GPU)            */
+/* ---------------------------------------------------------------------- */
+typedef struct dhr_server dhr_server;
+
+typedef struct {
+    uint64_t request_id;
+    int32_t session;
+    uint32_t frame;
+    uint64_t t_arrival_ns;   /* as given to dhr_server_submit (dhr_server_now_ns clock) */
+    uint64_t t_start_ns;     /* host time its batch was launched */
+    uint64_t t_done_ns;      /* device completion of its batch, on the same clock */
+    uint32_t batch_size;     /* requests in that batch */
+    uint32_t dropped;        /* 1: replaced by a newer request of its session; never ran */
+} dhr_completion;
+
+typedef struct {
+    uint64_t budget_bytes;
+    uint64_t used_bytes;
+    int32_t open_sessions;
+    uint64_t batches;
+    uint64_t frames;
+    uint64_t dropped;
+} dhr_server_stats;
+
+/* Delay reprojection (Section 4.1: camera data reaches the server late;
+ * Fig. 5): warps filtered AO/shadow computed for the pose cam_source (with
+ * its FP32 G-buffer `source`) to the pose cam_target (with its FP32
+ * G-buffer `target`).  Each target pixel takes the value of the nearest
+ * valid source pixel -- the temporal step's history-tap rule (mesh id,
+ * depth within 1 % + 2 depth slopes, normal cos >= 0.9), nearest = largest
+ * bilinear weight among the valid taps -- else 1.  All pointers device,
+ * float [H][W]. */
+dhr_status dhr_delay_warp(const dhr_gbuffer* target, const dhr_camera* cam_target,
+                          const dhr_gbuffer* source, const dhr_camera* cam_source,
+                          const float* src_ao, const float* src_shadow, float* out_ao,
+                          float* out_shadow, void* stream);
+
+/* Monotonic host clock (ns) used for request arrival and completion times. */
+uint64_t dhr_server_now_ns(void);
+
+/* Device bytes one session of width x height holds (admission cost). */
+uint64_t dhr_server_session_bytes(int32_t width, int32_t height);
+
+/* Server over a scene with a device-memory budget for sessions; all
+ * sessions share the trace and SVGF parameters (FP32 storage).  Captures
+ * one CUDA graph per batch slot (2 slots, 2 streams). */
+dhr_status dhr_server_create(const dhr_scene* scene, uint64_t budget_bytes,
+                             const dhr_trace_params* trace, const dhr_svgf_params* svgf,
+                             dhr_server** out);
+void dhr_server_destroy(dhr_server* server);
+
+/* Admits a session if its buffers fit the remaining budget, else
+ * DHR_ERR_ADMISSION (retry after other sessions close). */
+dhr_status dhr_server_open(dhr_server* server, int32_t width, int32_t height, int32_t* session_out);
+
+/* Closes a session; its memory returns to the budget once its frame in
+ * flight (if any) completes; a queued request is reported as dropped. */
+dhr_status dhr_server_close(dhr_server* server, int32_t session);
+
+/* Queues a frame request: trace + filter the pose `cam`; if cam_target is
+ * not NULL, warp the result to that pose (delay reprojection: each target
+ * pixel takes the nearest valid pixel of the traced pose by the history
+ * validity rule, else 1).  A newer request replaces a queued one of the
+ * same session (reported as dropped).  Host memory only; no GPU work. */
+dhr_status dhr_server_submit(dhr_server* server, int32_t session, const dhr_camera* cam,
+                             const dhr_camera* cam_target, uint32_t frame, uint64_t t_arrival_ns,
+                             uint64_t request_id);
+
+/* Collects finished batches, then launches one batch if a slot is free:
+ * at most one queued request per session without a frame in flight.
+ * *launched = number of requests launched (0 if none).  Non-blocking. */
+dhr_status dhr_server_pump(dhr_server* server, int32_t* launched);
+
+/* Returns up to `max` completed or dropped requests.  wait = 1 blocks until
+ * a batch completes when nothing is ready. */
+dhr_status dhr_server_poll(dhr_server* server, dhr_completion* out, int32_t max, int32_t* n_out,
+                           int32_t wait);
+
+/* Device pointers (float [H][W]) of the session's last completed output. */
+dhr_status dhr_server_output(dhr_server* server, int32_t session, float** ao, float** shadow);
+
+dhr_status dhr_server_get_stats(dhr_server* server, dhr_server_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,7 @@ def _declare(L):
     L.orc_svgf_atrous.argtypes = [C.c_int, C.c_int, P, P, C.c_int, P, P]
     L.orc_svgf_frame.argtypes = [C.c_int, C.c_int] + [P] * 16
     L.orc_svgf_seq_grad.argtypes = [C.c_int, C.c_int, C.c_int] + [P] * 9
+    L.orc_delay_warp.argtypes = [C.c_int, C.c_int] + [P] * 11
 
 
 def _p(a):
@@ -363,3 +364,16 @@ def svgf_seq_grad(zn, mesh, cams, sig, params: SvgfParams, g_out):
     lib().orc_svgf_seq_grad(F, W, H, _p(zn), _p(mesh), C.cast(cam_arr, C.c_void_p), _p(sig), C.byref(pp),
                             _p(g_out), _p(out), _p(g_sig), _p(g_sigma))
     return out, g_sig, g_sigma
+
+
+def delay_warp(zn_t, mesh_t, cam_t, zn_s, mesh_s, cam_s, src_ao, src_sh):
+    """Warp source-pose values to the target pose (nearest valid pixel, else 1)."""
+    H, W = mesh_t.shape
+    out_ao, out_sh = np.zeros((H, W)), np.zeros((H, W))
+    valid = np.zeros((H, W), np.int32)
+    ct, cs = make_camera(cam_t), make_camera(cam_s)
+    lib().orc_delay_warp(W, H, _p(_c(zn_t, np.float32)), _p(_c(mesh_t, np.uint32)), C.byref(ct),
+                         _p(_c(zn_s, np.float32)), _p(_c(mesh_s, np.uint32)), C.byref(cs),
+                         _p(_c(src_ao, np.float64)), _p(_c(src_sh, np.float64)), _p(out_ao), _p(out_sh),
+                         _p(valid))
+    return out_ao, out_sh, valid

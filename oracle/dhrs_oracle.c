@@ -1340,3 +1340,41 @@ void orc_svgf_seq_grad(int F, int W, int H, const float* zn, const uint32_t* mes
     free(gc); free(gv); free(gc2); free(gv2); free(gcol_next); free(gmom_next); free(gcol_prev);
     free(gmom_prev);
 }
+
+/* ======================================================================== */
+/* 5. Delay reprojection (Section 4.1, Fig. 5: camera data reaches the       */
+/*    server late; the result is shown at a newer pose)                     */
+/* ======================================================================== */
+/* Each pixel of the target pose (G-buffer zn_t, mesh_t, camera cam_t) takes
+ * the value of the nearest valid pixel of the source pose: the history-tap
+ * rule of the temporal step (binary32 decision, reproject_f32), nearest =
+ * largest bilinear weight among the valid taps (ties: first tap).  Without
+ * a valid tap, or on background, the value is 1 and valid = 0. */
+void orc_delay_warp(int W, int H, const float* zn_t, const uint32_t* mesh_t, const orc_camera* cam_t,
+                    const float* zn_s, const uint32_t* mesh_s, const orc_camera* cam_s,
+                    const double* src_ao, const double* src_sh, double* out_ao, double* out_sh,
+                    int32_t* valid)
+{
+    int32_t* zero_hist = (int32_t*)calloc((size_t)W * H, sizeof(int32_t));
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t p = (int64_t)y * W + x;
+            out_ao[p] = 1.0;
+            out_sh[p] = 1.0;
+            valid[p] = 0;
+            if (!is_fg(zn_t, p)) continue;
+            reproj_t r = reproject_f32(W, H, x, y, zn_t + 4 * p, mesh_t[p], cam_t, cam_s, zn_s, mesh_s,
+                                       zero_hist, depth_slope_f32(W, H, zn_t, x, y));
+            if (!r.valid) continue;
+            int best = -1;
+            float bw = -1.0f;
+            for (int k = 0; k < 4; ++k)
+                if (r.ok[k] && r.w[k] > bw) { bw = r.w[k]; best = k; }
+            int64_t q = (int64_t)r.ty[best] * W + r.tx[best];
+            out_ao[p] = src_ao[q];
+            out_sh[p] = src_sh[q];
+            valid[p] = 1;
+        }
+    }
+    free(zero_hist);
+}

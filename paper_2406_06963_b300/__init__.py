@@ -94,6 +94,18 @@ _SIGNATURES = {
     "dhr_svgf_tape_destroy": ([_P], None),
     "dhr_svgf_seq_forward": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_svgf_seq_backward": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_delay_warp": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "dhr_server_now_ns": ([], C.c_uint64),
+    "dhr_server_session_bytes": ([C.c_int32, C.c_int32], C.c_uint64),
+    "dhr_server_create": ([_P, C.c_uint64, _P, _P, _P], C.c_int),
+    "dhr_server_destroy": ([_P], None),
+    "dhr_server_open": ([_P, C.c_int32, C.c_int32, _P], C.c_int),
+    "dhr_server_close": ([_P, C.c_int32], C.c_int),
+    "dhr_server_submit": ([_P, C.c_int32, _P, _P, C.c_uint32, C.c_uint64, C.c_uint64], C.c_int),
+    "dhr_server_pump": ([_P, _P], C.c_int),
+    "dhr_server_poll": ([_P, _P, C.c_int32, _P, C.c_int32], C.c_int),
+    "dhr_server_output": ([_P, C.c_int32, _P, _P], C.c_int),
+    "dhr_server_get_stats": ([_P, _P], C.c_int),
     "dhr_session_create": ([_P, C.c_int32, C.c_int32, C.c_int, _P, _P, _P], C.c_int),
     "dhr_session_destroy": ([_P], None),
     "dhr_step_frame": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
@@ -520,3 +532,97 @@ def svgf_sequence(sig, sigmas, gbufs, cams, params: SvgfParams = None, tape: Svg
     F, _, H, W = sig.shape
     tape = tape or SvgfTape(W, H, F)
     return _SVGF_FN.apply(sig, sigmas, gbufs, cams, params or SvgfParams(), tape)
+
+
+# --------------------------------------------------------------- serving
+class Completion(C.Structure):
+    _fields_ = [("request_id", C.c_uint64), ("session", C.c_int32), ("frame", C.c_uint32),
+                ("t_arrival_ns", C.c_uint64), ("t_start_ns", C.c_uint64), ("t_done_ns", C.c_uint64),
+                ("batch_size", C.c_uint32), ("dropped", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("used_bytes", C.c_uint64), ("open_sessions", C.c_int32),
+                ("batches", C.c_uint64), ("frames", C.c_uint64), ("dropped", C.c_uint64)]
+
+
+def delay_warp(target: GBuffer, cam_target, source: GBuffer, cam_source, src_ao, src_sh, out_ao, out_sh,
+               stream=None):
+    _need_cuda(src_ao, src_sh, out_ao, out_sh)
+    t, s_ = target.c(), source.c()
+    ct, cs = camera(cam_target), camera(cam_source)
+    _check(lib().dhr_delay_warp(C.byref(t), C.byref(ct), C.byref(s_), C.byref(cs), _ptr(src_ao), _ptr(src_sh),
+                                _ptr(out_ao), _ptr(out_sh), _stream(stream)))
+
+
+def now_ns() -> int:
+    return int(lib().dhr_server_now_ns())
+
+
+def session_bytes(width, height) -> int:
+    return int(lib().dhr_server_session_bytes(width, height))
+
+
+class Server:
+    """Continuous-batching server of many sessions (dhr_server_*)."""
+
+    def __init__(self, scene: Scene, budget_bytes, trace=None, svgf=None):
+        self.trace = trace or TraceParams()
+        self.svgf = svgf or SvgfParams(ao_spp=self.trace.ao_spp)
+        h = C.c_void_p()
+        tp, sp = self.trace.to_c(), self.svgf.to_c()
+        _check(lib().dhr_server_create(scene.h, int(budget_bytes), C.byref(tp), C.byref(sp), C.byref(h)))
+        self.h, self.scene = h, scene
+        self._buf = (Completion * 4096)()
+
+    def open(self, width, height) -> int:
+        sid = C.c_int32()
+        _check(lib().dhr_server_open(self.h, width, height, C.byref(sid)))
+        return sid.value
+
+    def close_session(self, sid):
+        _check(lib().dhr_server_close(self.h, sid))
+
+    def submit(self, sid, cam, frame, t_arrival_ns, request_id, cam_target=None):
+        c = camera(cam)
+        ct = camera(cam_target) if cam_target is not None else None
+        _check(lib().dhr_server_submit(self.h, sid, C.byref(c), C.byref(ct) if ct else None, frame,
+                                       int(t_arrival_ns), int(request_id)))
+
+    def pump(self) -> int:
+        n = C.c_int32()
+        _check(lib().dhr_server_pump(self.h, C.byref(n)))
+        return n.value
+
+    def poll(self, wait=False):
+        n = C.c_int32()
+        _check(lib().dhr_server_poll(self.h, self._buf, len(self._buf), C.byref(n), int(wait)))
+        out = []
+        for i in range(n.value):
+            c = self._buf[i]
+            out.append(dict(request_id=c.request_id, session=c.session, frame=c.frame, t_arrival_ns=c.t_arrival_ns,
+                            t_start_ns=c.t_start_ns, t_done_ns=c.t_done_ns, batch_size=c.batch_size,
+                            dropped=bool(c.dropped)))
+        return out
+
+    def output(self, sid, width, height):
+        """Copies of the session's last completed (warped) AO and shadow."""
+        a, s_ = C.c_void_p(), C.c_void_p()
+        _check(lib().dhr_server_output(self.h, sid, C.byref(a), C.byref(s_)))
+        return device_copy(a.value, (height, width), "float32"), device_copy(s_.value, (height, width), "float32")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().dhr_server_get_stats(self.h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dhr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

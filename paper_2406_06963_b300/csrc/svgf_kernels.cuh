@@ -216,17 +216,18 @@ constexpr float kLog2e = 1.4426950408889634f;
 // that lets the a-trous passes test membership from the buffer they read).
 __device__ __forceinline__ bool fg_var(float v) { return v >= 0.0f; }
 
+// Temporal step for the 32x8 tile at (bx0, by0), run by a 32x8 block.
 template <dhr_precision P, class Sig>
-__global__ void __launch_bounds__(256) temporal_kernel(
-    SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const typename Store<P>::G* g_cur,
+__device__ __forceinline__ void temporal_tile(
+    const SvgfConsts& k, const dhr_camera& cam, const dhr_camera& cam_prev, const typename Store<P>::G* g_cur,
     const uint32_t* mesh_cur, const typename Store<P>::G* g_prev, const uint32_t* mesh_prev,
-    Sig sig, const typename Store<P>::Col* col_hist,
+    const Sig& sig, const typename Store<P>::Col* col_hist,
     const typename Store<P>::Mom* mom_in, const uint8_t* hist_in, typename Store<P>::Mom* mom_out,
-    uint8_t* hist_out, float4* illum) {
+    uint8_t* hist_out, float4* illum, int bx0, int by0) {
     using S = Store<P>;
     // one warp = 32 consecutive pixels of a row; every lane stays to the end
     // because the short-history estimate below is computed by the whole warp
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = bx0 + threadIdx.x, y = by0 + threadIdx.y;
     const int lane = threadIdx.x & 31;
     const bool inside = x < k.W && y < k.H;
     const size_t p = inside ? (size_t)y * k.W + x : 0;
@@ -330,6 +331,17 @@ __global__ void __launch_bounds__(256) temporal_kernel(
     }
 }
 
+template <dhr_precision P, class Sig>
+__global__ void __launch_bounds__(256) temporal_kernel(
+    SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const typename Store<P>::G* g_cur,
+    const uint32_t* mesh_cur, const typename Store<P>::G* g_prev, const uint32_t* mesh_prev,
+    Sig sig, const typename Store<P>::Col* col_hist,
+    const typename Store<P>::Mom* mom_in, const uint8_t* hist_in, typename Store<P>::Mom* mom_out,
+    uint8_t* hist_out, float4* illum) {
+    temporal_tile<P, Sig>(k, cam, cam_prev, g_cur, mesh_cur, g_prev, mesh_prev, sig, col_hist, mom_in, hist_in,
+                          mom_out, hist_out, illum, blockIdx.x * 32, blockIdx.y * 8);
+}
+
 // max(0, c)^sigma_n for the a-trous taps: 2^kNsq by kNsq squarings, or the
 // generic path (kNsq < 0)
 template <int kNsq>
@@ -395,12 +407,11 @@ __device__ __forceinline__ void atrous_taps(const SvgfConsts& k, int step, int x
 // 2: last iteration, write the two output planes only.  kNsq >= 0: sigma_n
 // is 2^kNsq.
 template <dhr_precision P, int kMode, int kNsq>
-__global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
-                                                     const float4* in, float4* out,
-                                                     typename Store<P>::Col* col_hist, float* ao_out,
-                                                     float* sh_out) {
+__device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, const typename Store<P>::G* g,
+                                            const float4* in, float4* out, typename Store<P>::Col* col_hist,
+                                            float* ao_out, float* sh_out, int bx0, int by0) {
     using S = Store<P>;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int x = bx0 + threadIdx.x, y = by0 + threadIdx.y;
     if (x >= k.W || y >= k.H) return;
     const int p = y * k.W + x;
     const float4 cp = __ldg(in + p);
@@ -453,7 +464,6 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
     acc.sv0 = kc * kc * cp.z;
     acc.sv1 = kc * kc * cp.w;
     // blocks whose 5x5 footprint lies inside the image skip the bounds tests
-    const int bx0 = blockIdx.x * blockDim.x, by0 = blockIdx.y * blockDim.y;
     const bool interior = bx0 - 2 * step >= 0 && by0 - 2 * step >= 0 &&
                           bx0 + (int)blockDim.x - 1 + 2 * step < k.W && by0 + (int)blockDim.y - 1 + 2 * step < k.H;
     if (interior)
@@ -470,6 +480,15 @@ __global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, con
         out[p] = make_float4(c0, c1, sv0 / (sw0 * sw0), sv1 / (sw1 * sw1));
         if (kMode == 1) S::put_col(col_hist, p, make_float2(c0, c1));
     }
+}
+
+template <dhr_precision P, int kMode, int kNsq>
+__global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
+                                                     const float4* in, float4* out,
+                                                     typename Store<P>::Col* col_hist, float* ao_out,
+                                                     float* sh_out) {
+    atrous_tile<P, kMode, kNsq>(k, step, g, in, out, col_hist, ao_out, sh_out, blockIdx.x * blockDim.x,
+                                blockIdx.y * blockDim.y);
 }
 
 // levels == 0: the temporal colour is the output and the colour history

@@ -1,216 +1,13 @@
-// Visibility tracing on the device: primary G-buffer rays (closest hit),
+// Visibility tracing entry points (single image): primary G-buffer rays,
 // cone-jittered shadow rays (Section 3.1) and radius-bounded cosine-weighted
-// AO rays (Section 3.2, Eqs. 1-3), all by software traversal of the LBVH.
-//
-// Traversal: depth-first over the 2-wide BVH with a per-thread stack, near
-// child first; any-hit rays stop at the first accepted hit, and AO rays
-// carry tmax = r so that short rays prune most of the tree (Section 3.2).
-// Triangle test: the watertight ray/triangle intersection of Woop, Benthin
-// and Wald (JCGT 2013) in binary32, with its double-precision fallback for
-// edge functions that are exactly zero.  Ray/box test: slabs with the
-// exit distance scaled by 1 + 2 gamma(3) (Ize, JCGT 2013) so that rounding
-// never culls a box the ray touches.
-#include <cuda_fp16.h>
-
+// AO rays (Section 3.2, Eqs. 1-3).  The per-pixel device code is in
+// trace_device.cuh.
 #include <cmath>
 
-#include "common.cuh"
-#include "sampling.cuh"
+#include "trace_device.cuh"
 
 namespace dhr {
 namespace {
-
-__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
-__device__ __forceinline__ float3 sub(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float3 cross(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-
-// Per-ray constants of the watertight test and of the slab test.
-struct Ray {
-    float3 o, d;
-    float3 idir;       // 1 / d (tiny components clamped away from zero)
-    float3 oidir;      // o / d
-    int kx, ky, kz;
-    float sx, sy, sz;
-};
-
-__device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
-    Ray r;
-    r.o = o;
-    r.d = d;
-    const float eps = 1e-20f;
-    const float dx = fabsf(d.x) > eps ? d.x : copysignf(eps, d.x);
-    const float dy = fabsf(d.y) > eps ? d.y : copysignf(eps, d.y);
-    const float dz = fabsf(d.z) > eps ? d.z : copysignf(eps, d.z);
-    r.idir = make_float3(1.0f / dx, 1.0f / dy, 1.0f / dz);
-    r.oidir = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
-    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    r.kx = r.kz == 2 ? 0 : r.kz + 1;
-    r.ky = r.kx == 2 ? 0 : r.kx + 1;
-    if (comp(d, r.kz) < 0.0f) {
-        const int t = r.kx;
-        r.kx = r.ky;
-        r.ky = t;
-    }
-    const float dkz = comp(d, r.kz);
-    r.sx = comp(d, r.kx) / dkz;
-    r.sy = comp(d, r.ky) / dkz;
-    r.sz = 1.0f / dkz;
-    return r;
-}
-
-// Watertight test; on a hit with tmin < t < tmax returns t and the scaled
-// barycentrics (b0, b1, b2 of v0, v1, v2, summing to 1).
-__device__ __forceinline__ bool hit_triangle(const Ray& r, float3 v0, float3 v1, float3 v2, float tmin,
-                                             float tmax, float& t_out, float3& bary) {
-    const float3 A = sub(v0, r.o), B = sub(v1, r.o), C = sub(v2, r.o);
-    const float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
-    const float Ax = comp(A, r.kx) - r.sx * Akz, Ay = comp(A, r.ky) - r.sy * Akz;
-    const float Bx = comp(B, r.kx) - r.sx * Bkz, By = comp(B, r.ky) - r.sy * Bkz;
-    const float Cx = comp(C, r.kx) - r.sx * Ckz, Cy = comp(C, r.ky) - r.sy * Ckz;
-    float U = Cx * By - Cy * Bx;
-    float V = Ax * Cy - Ay * Cx;
-    float W = Bx * Ay - By * Ax;
-    if (U == 0.0f || V == 0.0f || W == 0.0f) {
-        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
-    }
-    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
-    const float det = U + V + W;
-    if (det == 0.0f) return false;
-    const float T = U * (r.sz * Akz) + V * (r.sz * Bkz) + W * (r.sz * Ckz);
-    const float t = T / det;
-    if (!(t > tmin && t < tmax)) return false;
-    t_out = t;
-    const float inv = 1.0f / det;
-    bary = make_float3(U * inv, V * inv, W * inv);
-    return true;
-}
-
-__device__ __forceinline__ void slab(const Ray& r, float lox, float hix, float loy, float hiy, float loz,
-                                     float hiz, float tmin, float tmax, float& enter, bool& hit) {
-    const float x0 = fmaf(lox, r.idir.x, -r.oidir.x), x1 = fmaf(hix, r.idir.x, -r.oidir.x);
-    const float y0 = fmaf(loy, r.idir.y, -r.oidir.y), y1 = fmaf(hiy, r.idir.y, -r.oidir.y);
-    const float z0 = fmaf(loz, r.idir.z, -r.oidir.z), z1 = fmaf(hiz, r.idir.z, -r.oidir.z);
-    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
-    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
-    enter = tn;
-    hit = tn <= tf * 1.00000024f;   // 1 + 2 gamma(3) with unit roundoff 2^-24
-}
-
-// Closest hit (any_hit = false) or first hit (true) with tmin < t < tmax.
-// Returns the sorted leaf index (or -1), t and barycentrics.  Ties in t
-// go to the smaller original triangle index.
-constexpr uint32_t kMaxSteps = 1u << 24;
-
-// Work counters of one traversal (compiled in only by the statistics kernel).
-struct Work {
-    uint32_t visits = 0;   // internal nodes fetched (two child boxes tested each)
-    uint32_t tests = 0;    // triangles tested
-};
-
-template <bool kAnyHit, bool kStats = false>
-__device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tmax, float3& bary,
-                        int skip_leaf = -1, Work* work = nullptr) {
-    if (sc.n_tris == 0) return -1;
-    int stack[kStackSize];
-    int sp = 0;
-    int node = 0;
-    int best = -1;
-    uint32_t best_orig = 0xFFFFFFFFu;
-    // a valid tree visits each node at most once per ray; the cap only
-    // guards against a corrupt tree
-    for (uint32_t guard = 0; guard < kMaxSteps; ++guard) {
-        if (node >= 0) {
-            if (kStats) ++work->visits;
-            const float4* nd = sc.nodes + 4 * node;
-            const float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), d = __ldg(nd + 3);
-            float e0, e1;
-            bool h0, h1;
-            slab(r, a.x, a.y, a.z, a.w, c.x, c.y, tmin, tmax, e0, h0);
-            slab(r, b.x, b.y, b.z, b.w, c.z, c.w, tmin, tmax, e1, h1);
-            int c0 = __float_as_int(d.x), c1 = __float_as_int(d.y);
-            if (h0 && h1) {
-                if (e1 < e0) {
-                    const int t = c0;
-                    c0 = c1;
-                    c1 = t;
-                }
-                if (sp < kStackSize) stack[sp++] = c1;   // height < kStackSize is checked at build
-                node = c0;
-                continue;
-            }
-            if (h0) { node = c0; continue; }
-            if (h1) { node = c1; continue; }
-        } else {
-            const int leaf = ~node;
-            if (leaf == skip_leaf) goto pop;
-            if (kStats) ++work->tests;
-            const float4* tr = sc.tris + 3 * leaf;
-            const float4 p0 = __ldg(tr), p1 = __ldg(tr + 1), p2 = __ldg(tr + 2);
-            float t;
-            float3 b;
-            // closest hit admits t == tmax so that ties can go to the smaller index
-            const float tlim = (kAnyHit || !(tmax < INFINITY)) ? tmax : __int_as_float(__float_as_int(tmax) + 1);
-            if (hit_triangle(r, f3(p0), f3(p1), f3(p2), tmin, tlim, t, b)) {
-                const uint32_t orig = __float_as_uint(p0.w);
-                if (kAnyHit) {
-                    tmax = t;
-                    bary = b;
-                    return leaf;
-                }
-                if (t < tmax || orig < best_orig) {
-                    tmax = t;
-                    bary = b;
-                    best = leaf;
-                    best_orig = orig;
-                }
-            }
-        }
-    pop:
-        if (sp == 0) break;
-        node = stack[--sp];
-    }
-    return best;
-}
-
-// Secondary-ray origin: the hit point moved along the normal by 16 units in
-// the last place (binary32) of the largest vertex coordinate of the hit
-// triangle -- an exact power of two, larger than the rounding error of the
-// barycentric hit point -- so that the ray starts on the correct side of the
-// surface.  The hit triangle itself is also skipped by secondary rays.
-__device__ __forceinline__ float3 surface_origin(float3 X, float3 n, float3 v0, float3 v1, float3 v2) {
-    float m = fmaxf(fmaxf(fmaxf(fabsf(v0.x), fabsf(v0.y)), fmaxf(fabsf(v0.z), fabsf(v1.x))),
-                    fmaxf(fmaxf(fabsf(v1.y), fabsf(v1.z)), fmaxf(fmaxf(fabsf(v2.x), fabsf(v2.y)), fabsf(v2.z))));
-    m = fmaxf(m, 9.5367431640625e-07f);                       // 2^-20
-    const int e = (__float_as_int(m) >> 23) & 0xFF;            // biased exponent of m
-    const float delta = __int_as_float((e - 19) << 23);        // 2^(e - 127 - 23 + 4)
-    return make_float3(fmaf(delta, n.x, X.x), fmaf(delta, n.y, X.y), fmaf(delta, n.z, X.z));
-}
-
-struct TraceConsts {
-    dhr_camera cam;
-    float3 light[DHR_MAX_LIGHTS];
-    float tan_cone[DHR_MAX_LIGHTS];
-    uint32_t n_lights;
-    float ao_radius;
-    uint32_t ao_spp;
-    uint32_t frame;
-    uint32_t seed;
-};
-
-// Pixel of a thread: each warp covers an 8x4 tile; a 128-thread block
-// covers 16x8 pixels.
-__device__ __forceinline__ int2 thread_pixel() {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    return make_int2(blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7),
-                     blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3));
-}
 
 // kStats: also count rays, node visits and triangle tests per ray type into
 // stats[0..8] = rays {primary, shadow, AO}, visits {..}, tests {..}.
@@ -218,91 +15,7 @@ template <bool kHalf, bool kStats = false>
 __global__ void __launch_bounds__(128) trace_kernel(SceneView sc, TraceConsts k, void* gbuf_dn,
                                                     uint32_t* gbuf_mesh, uint8_t* mask_out,
                                                     uint8_t* ao_out, unsigned long long* stats = nullptr) {
-    const int2 px = thread_pixel();
-    const int W = k.cam.width, H = k.cam.height;
-    if (px.x >= W || px.y >= H) return;
-    const size_t pix = (size_t)px.y * W + px.x;
-    // primary ray through the pixel centre; its parameter is the linear depth
-    const float sx = (2.0f * (px.x + 0.5f) / W - 1.0f) * k.cam.tan_half_fov_y * ((float)W / (float)H);
-    const float sy = (1.0f - 2.0f * (px.y + 0.5f) / H) * k.cam.tan_half_fov_y;
-    const float3 eye = make_float3(k.cam.pos[0], k.cam.pos[1], k.cam.pos[2]);
-    const float3 fw = make_float3(k.cam.forward[0], k.cam.forward[1], k.cam.forward[2]);
-    const float3 D = make_float3(fw.x + sx * k.cam.right[0] + sy * k.cam.up[0],
-                                 fw.y + sx * k.cam.right[1] + sy * k.cam.up[1],
-                                 fw.z + sx * k.cam.right[2] + sy * k.cam.up[2]);
-    const Ray pr = make_ray(eye, D);
-    float tp = INFINITY;
-    float3 bary;
-    Work wp, ws, wa;
-    uint32_t n_sh = 0, n_ao = 0;
-    const int leaf = traverse<false, kStats>(sc, pr, 0.0f, tp, bary, -1, &wp);
-    if (kStats) {
-        atomicAdd(stats + 0, 1ull);
-        atomicAdd(stats + 3, (unsigned long long)wp.visits);
-        atomicAdd(stats + 6, (unsigned long long)wp.tests);
-    }
-    if (leaf < 0) {
-        if (kHalf) {
-            reinterpret_cast<uint2*>(gbuf_dn)[pix] = pack_gbuf16(INFINITY, make_float3(0.f, 0.f, 0.f));
-        } else {
-            reinterpret_cast<float4*>(gbuf_dn)[pix] = make_float4(INFINITY, 0.f, 0.f, 0.f);
-        }
-        gbuf_mesh[pix] = DHR_BACKGROUND;
-        mask_out[pix] = (uint8_t)((1u << k.n_lights) - 1u);
-        ao_out[pix] = (uint8_t)k.ao_spp;
-        return;
-    }
-    const float4* tr = sc.tris + 3 * leaf;
-    const float4 p0 = __ldg(tr), p1 = __ldg(tr + 1), p2 = __ldg(tr + 2);
-    const float3 v0 = f3(p0), v1 = f3(p1), v2 = f3(p2);
-    // hit point from barycentrics (more accurate than eye + t D far away)
-    const float3 X = make_float3(bary.x * v0.x + bary.y * v1.x + bary.z * v2.x,
-                                 bary.x * v0.y + bary.y * v1.y + bary.z * v2.y,
-                                 bary.x * v0.z + bary.y * v1.z + bary.z * v2.z);
-    float3 n = cross(sub(v1, v0), sub(v2, v0));
-    const float inv_len = rsqrtf(dot(n, n));
-    n = make_float3(n.x * inv_len, n.y * inv_len, n.z * inv_len);
-    if (dot(n, D) > 0.0f) n = make_float3(-n.x, -n.y, -n.z);
-    const float depth = dot(sub(X, eye), fw);
-    if (kHalf) {
-        reinterpret_cast<uint2*>(gbuf_dn)[pix] = pack_gbuf16(depth, n);
-    } else {
-        reinterpret_cast<float4*>(gbuf_dn)[pix] = make_float4(depth, n.x, n.y, n.z);
-    }
-    gbuf_mesh[pix] = __float_as_uint(p1.w);
-
-    const float3 o = surface_origin(X, n, v0, v1, v2);
-    // shadow rays: one per light, direction jittered inside the light's cone
-    uint32_t mask = 0;
-    for (uint32_t l = 0; l < k.n_lights; ++l) {
-        const float2 xy = disk_point(px.x, px.y, k.frame, k.seed, kShadowRay, l);
-        const float3 d = cone_direction(k.light[l], k.tan_cone[l], xy);
-        if (dot(d, n) <= 0.0f) continue;       // blocked by the surface itself
-        float tm = INFINITY;
-        float3 b;
-        ++n_sh;
-        if (traverse<true, kStats>(sc, make_ray(o, d), 0.0f, tm, b, leaf, &ws) < 0) mask |= 1u << l;
-    }
-    mask_out[pix] = (uint8_t)mask;
-    // AO rays: cosine-weighted, a hit closer than r occludes (Eq. 2-3)
-    uint32_t unocc = 0;
-    for (uint32_t j = 0; j < k.ao_spp; ++j) {
-        const float2 xy = disk_point(px.x, px.y, k.frame, k.seed, kAoRay, j);
-        const float3 d = ao_direction(n, xy);
-        float tm = k.ao_radius;
-        float3 b;
-        ++n_ao;
-        if (traverse<true, kStats>(sc, make_ray(o, d), 0.0f, tm, b, leaf, &wa) < 0) ++unocc;
-    }
-    ao_out[pix] = (uint8_t)unocc;
-    if (kStats) {
-        atomicAdd(stats + 1, (unsigned long long)n_sh);
-        atomicAdd(stats + 2, (unsigned long long)n_ao);
-        atomicAdd(stats + 4, (unsigned long long)ws.visits);
-        atomicAdd(stats + 5, (unsigned long long)wa.visits);
-        atomicAdd(stats + 7, (unsigned long long)ws.tests);
-        atomicAdd(stats + 8, (unsigned long long)wa.tests);
-    }
+    trace_pixel<kHalf, kStats, false>(sc, k, thread_pixel(), gbuf_dn, gbuf_mesh, mask_out, ao_out, stats);
 }
 
 __global__ void cast_kernel(SceneView sc, const float* orig, const float* dirs, const float* tmin,
@@ -360,22 +73,7 @@ dhr_status check_trace_params(const dhr_trace_params* p) {
 dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
                         dhr_gbuffer* g, uint8_t* mask, uint8_t* ao, cudaStream_t st,
                         unsigned long long* stats) {
-    TraceConsts k;
-    k.cam = *cam;
-    for (uint32_t l = 0; l < DHR_MAX_LIGHTS; ++l) {
-        if (l < p->n_lights) {
-            k.light[l] = make_float3(p->light_dir[l][0], p->light_dir[l][1], p->light_dir[l][2]);
-            k.tan_cone[l] = cone_tan(p->cone_half_angle[l]);
-        } else {
-            k.light[l] = make_float3(0.f, 1.f, 0.f);
-            k.tan_cone[l] = 0.f;
-        }
-    }
-    k.n_lights = p->n_lights;
-    k.ao_radius = p->ao_radius;
-    k.ao_spp = p->ao_spp;
-    k.frame = p->frame;
-    k.seed = p->seed;
+    const TraceConsts k = make_trace_consts(*cam, *p);
     const dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
     if (stats) {
         trace_kernel<false, true><<<grid, 128, 0, st>>>(sc->view(), k, g->depth_normal, g->mesh_id, mask, ao,

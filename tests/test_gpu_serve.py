@@ -1,0 +1,147 @@
+"""Serving form: continuous batching of many sessions (dhr_server_*) and the
+delay reprojection (dhr_delay_warp, Section 4.1 / Fig. 5).
+
+- dhr_delay_warp equals the oracle's warp on the oracle's own inputs.
+- A session served by the batching server gives exactly what dhr_step_frame
+  gives, alone and in a mix of sessions of other resolutions (same kernels,
+  same per-pixel arithmetic: bit-identical, well inside 1e-3).
+- Admission by device-memory budget, latest-wins request replacement.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+import paper_2406_06963_b300 as dhrs
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_delay_warp_matches_oracle():
+    s = wl.scene_boxes()
+    S = orc.Scene(s)
+    W, H = 160, 120
+    cams = wl.orbit_path(6, W, H, degrees=12.0)
+    cs, ct = cams[0], cams[5]
+    zs, ms = orc.gbuffer_f32(orc.trace(S, cs, orc.TraceParams()), W, H)
+    zt, mt = orc.gbuffer_f32(orc.trace(S, ct, orc.TraceParams()), W, H)
+    r = np.random.default_rng(3)
+    a = r.random((H, W)).astype(np.float32)
+    b = r.random((H, W)).astype(np.float32)
+    ra, rb, valid = orc.delay_warp(zt, mt, ct, zs, ms, cs, a.astype(np.float64), b.astype(np.float64))
+    oa = torch.empty((H, W), device="cuda")
+    ob = torch.empty_like(oa)
+    dhrs.delay_warp(dhrs.GBuffer.from_arrays(zt, mt), ct, dhrs.GBuffer.from_arrays(zs, ms), cs,
+                    torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), oa, ob)
+    torch.cuda.synchronize()
+    assert valid.mean() > 0.3 and (valid == 0).sum() > 0
+    assert np.array_equal(oa.cpu().numpy(), ra.astype(np.float32))
+    assert np.array_equal(ob.cpu().numpy(), rb.astype(np.float32))
+
+
+def _run_server(sc, sessions, frames, budget=8 << 30):
+    """sessions: list of (W, H, path); returns outputs[session][frame]."""
+    srv = dhrs.Server(sc, budget)
+    ids = [srv.open(w, h) for (w, h, _) in sessions]
+    outs = {i: [] for i in range(len(sessions))}
+    for f in range(frames):
+        for k, (w, h, path) in enumerate(sessions):
+            srv.submit(ids[k], path[f], f, dhrs.now_ns(), 1000 * k + f)
+        assert srv.pump() == len(sessions)
+        done = srv.poll(wait=True)
+        while len([d for d in done if not d["dropped"]]) < len(sessions):
+            done += srv.poll(wait=True)
+        assert all(d["batch_size"] == len(sessions) for d in done)
+        for k, (w, h, _) in enumerate(sessions):
+            a, b = srv.output(ids[k], w, h)
+            outs[k].append((a.cpu().numpy(), b.cpu().numpy()))
+    return outs, srv
+
+
+def test_server_equals_step_frame_alone_and_in_mix():
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    A = (200, 120, wl.orbit_path(4, 200, 120, degrees=6.0))
+    others = [(96, 64, wl.orbit_path(4, 96, 64, degrees=9.0, start_deg=40)),
+              (333, 77, wl.orbit_path(4, 333, 77, degrees=3.0, start_deg=-30)),
+              (64, 200, wl.orbit_path(4, 64, 200, degrees=5.0, start_deg=90))]
+    alone, _ = _run_server(sc, [A], 4)
+    mix, _ = _run_server(sc, others[:1] + [A] + others[1:], 4)
+    sess = dhrs.Session(sc, 200, 120)
+    a = torch.empty((120, 200), device="cuda")
+    b = torch.empty_like(a)
+    for f in range(4):
+        sess.step(A[2][f], f, a, b)
+        torch.cuda.synchronize()
+        ref = (a.cpu().numpy(), b.cpu().numpy())
+        for got in (alone[0][f], mix[1][f]):
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), f
+
+
+def test_server_admission_by_memory_budget():
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    need = dhrs.session_bytes(256, 256)
+    srv = dhrs.Server(sc, 2 * need + need // 2)
+    a = srv.open(256, 256)
+    srv.open(256, 256)
+    with pytest.raises(dhrs.DhrError) as e:
+        srv.open(256, 256)
+    assert e.value.status == 5
+    small = srv.open(64, 64)              # a smaller session still fits
+    srv.close_session(a)
+    srv.open(256, 256)                    # memory freed: admitted
+    st = srv.stats()
+    assert st["open_sessions"] == 3 and st["used_bytes"] <= st["budget_bytes"]
+    srv.close_session(small)
+
+
+def test_server_latest_request_wins():
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    path = wl.orbit_path(3, 64, 48)
+    srv = dhrs.Server(sc, 1 << 30)
+    sid = srv.open(64, 48)
+    srv.submit(sid, path[0], 0, dhrs.now_ns(), 1)
+    srv.submit(sid, path[1], 1, dhrs.now_ns(), 2)     # replaces request 1
+    assert srv.pump() == 1
+    done = srv.poll(wait=True)
+    done += srv.poll(wait=True)
+    by_id = {d["request_id"]: d for d in done}
+    assert by_id[1]["dropped"] and not by_id[2]["dropped"]
+    assert by_id[2]["t_done_ns"] >= by_id[2]["t_arrival_ns"]
+    assert srv.stats()["dropped"] == 1
+
+
+def test_server_delay_warp_equals_components():
+    """A request with a target pose = trace + SVGF at the sent pose, then
+    dhr_delay_warp onto a G-buffer of the target pose."""
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    W, H = 128, 96
+    path = wl.orbit_path(8, W, H, degrees=14.0)
+    srv = dhrs.Server(sc, 1 << 30)
+    sid = srv.open(W, H)
+    sess = dhrs.Session(sc, W, H)
+    a = torch.empty((H, W), device="cuda")
+    b = torch.empty_like(a)
+    oa, ob = torch.empty_like(a), torch.empty_like(a)
+    for f in range(4):
+        tgt = path[f + 3]
+        srv.submit(sid, path[f], f, dhrs.now_ns(), f, cam_target=tgt)
+        srv.pump()
+        srv.poll(wait=True)
+        ga, gb = srv.output(sid, W, H)
+        sess.step(path[f], f, a, b)
+        gt = dhrs.GBuffer(W, H)
+        m = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        dhrs.trace_visibility(sc, tgt, dhrs.TraceParams(frame=f), gt, m, m.clone())
+        fb = sess.frame_buffers()
+        gs = dhrs.GBuffer(W, H)
+        gs.depth_normal.copy_(dhrs.device_copy(fb["depth_normal"], (H, W, 4), "float32"))
+        gs.mesh.copy_(dhrs.device_copy(fb["mesh"], (H, W), "int32"))
+        dhrs.delay_warp(gt, tgt, gs, path[f], a, b, oa, ob)
+        torch.cuda.synchronize()
+        assert torch.equal(ga, oa) and torch.equal(gb, ob), f
+        assert float((ga == 1).float().mean()) < 0.9
