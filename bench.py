@@ -283,12 +283,179 @@ def run_ours(args):
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }
+    if not args.no_forms:
+        res["serving"] = run_serving(sc, scene_d, seconds=args.serve_seconds)
+        res["precision_form"] = run_precision_form(sc, scene_d)
+        res["adjoint"] = run_adjoint(sc, scene_d)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(scene_d, cams, sample_px=args.cpu_pixels)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return res if rank == 0 else None
+
+
+def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30):
+    """32 thin-client sessions, resolutions drawn from {640x360, 1280x720,
+    1920x1080, 2560x1440}, each sending camera poses as a 60 Hz Poisson
+    process along its own seeded spline, with a network delay U[0, 200] ms
+    per session (the request arrives late and its result is warped to the
+    pose at arrival).  Real-time simulation for `seconds`; latency = device
+    completion - arrival at the server (network delay excluded)."""
+    import numpy as np
+
+    import paper_2406_06963_b300 as dhrs
+    import workloads as wl
+    r = wl.rng_for(4)
+    sizes = [(640, 360), (1280, 720), (1920, 1080), (2560, 1440)]
+    srv = dhrs.Server(sc, budget)
+    n_poses = int((seconds + 0.3) * 60) + 2
+    events, refused, admitted, px_of = [], 0, 0, {}
+    for k in range(n_sessions):
+        w, h = sizes[int(r.integers(0, 4))]
+        d = float(r.uniform(0.0, 0.2))
+        try:
+            sid = srv.open(w, h)
+        except dhrs.DhrError as e:
+            if e.status != 5:
+                raise
+            refused += 1
+            continue
+        admitted += 1
+        px_of[sid] = w * h
+        path = wl.spline_path(scene_d["terrain"], n_poses, w, h, index=4, stream=k)
+        t = float(r.exponential(1 / 60))
+        i = 0
+        while t < seconds:
+            fi = min(int(round(t * 60)), n_poses - 1)
+            ti = min(int(round((t + d) * 60)), n_poses - 1)
+            events.append((t + d, sid, path[fi], path[ti] if ti != fi else None, i))
+            t += float(r.exponential(1 / 60))
+            i += 1
+    events.sort(key=lambda e: e[0])
+    lat, done_px, batches = [], 0, []
+    dropped = 0
+    start = dhrs.now_ns() + 20_000_000
+    idx = 0
+    rid = 0
+    while True:
+        now = (dhrs.now_ns() - start) * 1e-9
+        while idx < len(events) and events[idx][0] <= now:
+            ta, sid, cam, tgt, fr = events[idx]
+            srv.submit(sid, cam, fr, start + int(ta * 1e9), rid, cam_target=tgt)
+            rid += 1
+            idx += 1
+        srv.pump()
+        for c in srv.poll(wait=idx >= len(events)):
+            if c["dropped"]:
+                dropped += 1
+                continue
+            lat.append((c["t_done_ns"] - c["t_arrival_ns"]) * 1e-6)
+            done_px += px_of[c["session"]]
+            batches.append(c["batch_size"])
+        if idx >= len(events) and len(lat) + dropped >= len(events):
+            break
+    wall = (dhrs.now_ns() - start) * 1e-9
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"workload": "32 sessions x 60 Hz Poisson, delay U[0,200] ms, terrain776k",
+            "sessions_admitted": admitted, "sessions_refused": refused, "requests": len(events),
+            "completed": int(len(lat)), "dropped_latest_wins": dropped,
+            "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "frames_per_s": round(len(lat) / wall, 1), "mpx_per_s": round(done_px / wall / 1e6, 1),
+            "mean_batch": round(float(np.mean(batches)), 2), "batches": int(st["batches"]),
+            "device_bytes": int(st["used_bytes"]) if st["open_sessions"] else None, "seconds": round(wall, 3)}
+
+
+def run_precision_form(sc, scene_d, frames=10, warm=3):
+    """Same scene and path at 3840x2160: FP16-storage form vs FP32 path."""
+    import numpy as np
+    import torch
+
+    import paper_2406_06963_b300 as dhrs
+    import workloads as wl
+    W4, H4 = 3840, 2160
+    cams = wl.spline_path(scene_d["terrain"], N_FRAMES, W4, H4)
+    res = {}
+    outs = {}
+    for name, prec in (("fp32", dhrs.DHR_FP32), ("fp16", dhrs.DHR_FP16)):
+        sess = dhrs.Session(sc, W4, H4, prec)
+        a = torch.empty((H4, W4), device="cuda")
+        b = torch.empty_like(a)
+        for i in range(warm):
+            sess.step(cams[i], i, a, b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(warm, warm + frames):
+            sess.step(cams[i], i, a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms_per_frame"] = round(e0.elapsed_time(e1) / frames, 4)
+        outs[name] = torch.stack([a, b]).clone()
+        sess.close()
+    e = (outs["fp16"] - outs["fp32"]).abs().flatten().cpu().numpy()
+    res["fp16_vs_fp32_abs_err"] = {"max": float(e.max()), "p99": float(np.percentile(e, 99)),
+                                   "mean": float(e.mean())}
+    res["workload"] = "terrain776k_3840x2160"
+    return res
+
+
+def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
+    """Differentiable SVGF over 8 frames at 1280x720: forward + backward
+    time, L2 loss against a 255-spp AO reference, a few Adam steps on
+    log(sigma_z, sigma_n, sigma_l)."""
+    import torch
+
+    import paper_2406_06963_b300 as dhrs
+    import workloads as wl
+    cams = wl.spline_path(scene_d["terrain"], N_FRAMES, W, H)[:frames]
+    gbufs, sig, ref = [], [], []
+    for f, cam in enumerate(cams):
+        g = dhrs.GBuffer(W, H)
+        m = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        a = torch.empty_like(m)
+        dhrs.trace_visibility(sc, cam, dhrs.TraceParams(ao_spp=1, frame=f), g, m, a)
+        gbufs.append(g)
+        sig.append(torch.stack([a.float(), (m & 1).float()]))
+        g2 = dhrs.GBuffer(W, H)
+        a2 = torch.empty_like(m)
+        dhrs.trace_visibility(sc, cam, dhrs.TraceParams(ao_spp=255, frame=f), g2, m.clone(), a2)
+        ref.append(a2.float() / 255.0)
+    sig = torch.stack(sig).contiguous()
+    ref = torch.stack(ref)
+    tape = dhrs.SvgfTape(W, H, frames)
+    p = dhrs.SvgfParams()
+    out = tape.forward(gbufs, cams, sig, p)
+    g_out = torch.zeros_like(out)
+    g_out[:, 0] = 2 * (out[:, 0] - ref)
+    tape.backward(gbufs, cams, sig, p, g_out)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    out = tape.forward(gbufs, cams, sig, p)
+    e[1].record()
+    g_out[:, 0] = 2 * (out[:, 0] - ref)
+    tape.backward(gbufs, cams, sig, p, g_out)
+    e[2].record()
+    torch.cuda.synchronize()
+    fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    # algorithmic bytes per pixel and frame: forward 340; backward: 10 level
+    # recomputations x 48, 5 x (pass A 112 + pass B 112), temporal 100
+    bytes_fb = frames * W * H * (340 + 480 + 5 * 224 + 100)
+    log_s = torch.tensor([0.0, 4.852, 1.386], device="cuda").requires_grad_(True)  # log(1, 128, 4)
+    opt = torch.optim.Adam([log_s], lr=0.05)
+    losses = []
+    for _ in range(fit_steps):
+        opt.zero_grad()
+        o = dhrs.svgf_sequence(sig, log_s.exp(), gbufs, cams, p, tape)
+        loss = ((o[:, 0] - ref) ** 2).mean()
+        loss.backward()
+        opt.step()
+        losses.append(round(float(loss.detach()), 6))
+    return {"workload": f"{frames} frames x {W}x{H}, terrain776k", "forward_ms": round(fwd, 3),
+            "backward_ms": round(bwd, 3), "algorithmic_gb_per_s": round(bytes_fb / ((fwd + bwd) * 1e-3) / 1e9, 1),
+            "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.exp()]}
 
 
 def cpu_baseline(scene_d, cams, sample_px=1024, seed=7):
@@ -357,6 +524,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the serving, FP16 and adjoint measurements")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--cpu-pixels", type=int, default=1024)
     ap.add_argument("--ref-pixels", type=int, default=24)
     args = ap.parse_args()

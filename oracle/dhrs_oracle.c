@@ -1140,7 +1140,7 @@ static void atrous_backward(int W, int H, const float* zn, const double* in, int
                 /* il = 1 / (sigma_l sqrt(g) + eps_l) */
                 if (P->wl_in_atrous) {
                     gsig[2] += Gil * (-il * il * root);
-                    if (gv[ch] > 0.0) {
+                    if (gv[ch] > 1e-12) {       /* d sqrt(g)/dg taken as 0 below g = 1e-12 */
                         double Gg = Gil * (-il * il * P->sigma_l * 0.5 / root);
                         for (int dy = -1; dy <= 1; ++dy)
                             for (int dx = -1; dx <= 1; ++dx) {

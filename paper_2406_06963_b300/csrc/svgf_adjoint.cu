@@ -18,7 +18,7 @@
 //     contains q (and the 9 whose variance Gaussian does).
 // The reprojection taps and history lengths depend only on G-buffers and
 // cameras and are constants of the adjoint.  Conventions as in the CPU
-// reference: sign(0) = 0, d max(0, x) = [x > 0], d sqrt(g)/dg = 0 at g = 0,
+// reference: sign(0) = 0, d max(0, x) = [x > 0], d sqrt(g)/dg = 0 for g < 1e-12,
 // d w_n/d sigma_n = w_n ln(n.n') for n.n' > 0.
 #include <vector>
 
@@ -171,8 +171,10 @@ __global__ void __launch_bounds__(kThreadsA) atrous_bwd_a(SvgfConsts k, int step
         float Gg0 = 0.f, Gg1 = 0.f;
         if (k.wl_in_atrous) {
             gsl += Gil0 * (-il0 * il0 * root0) + Gil1 * (-il1 * il1 * root1);
-            if (root0 > 0.f) Gg0 = Gil0 * (-il0 * il0 * k.sigma_l * 0.5f / root0) / gw;
-            if (root1 > 0.f) Gg1 = Gil1 * (-il1 * il1 * k.sigma_l * 0.5f / root1) / gw;
+            // d sqrt(g)/dg is taken as 0 below g = 1e-12 (it grows without bound
+            // toward g = 0, where the weight is already insensitive)
+            if (root0 > 1e-6f) Gg0 = Gil0 * (-il0 * il0 * k.sigma_l * 0.5f / root0) / gw;
+            if (root1 > 1e-6f) Gg1 = Gil1 * (-il1 * il1 * k.sigma_l * 0.5f / root1) / gw;
         }
         rec[4 * p + 0] = make_float4(a10, a20, a30, il0);
         rec[4 * p + 1] = make_float4(a11, a21, a31, il1);
