@@ -46,9 +46,9 @@ def _peaks():
 
 # sources each profiled kernel is compiled from
 KERNEL_SOURCES = {
-    "trace_kernel": ["trace.cu", "sampling.cuh", "common.cuh"],
-    "atrous_kernel": ["svgf.cu", "common.cuh"],
-    "temporal_kernel": ["svgf.cu", "common.cuh"],
+    "trace_kernel": ["trace.cu", "trace_device.cuh", "sampling.cuh", "common.cuh"],
+    "atrous_kernel": ["svgf.cu", "svgf_kernels.cuh", "common.cuh"],
+    "temporal_kernel": ["svgf.cu", "svgf_kernels.cuh", "common.cuh"],
 }
 
 

@@ -114,22 +114,23 @@ __global__ void __launch_bounds__(256) serve_temporal_kernel(const BatchTable* t
 }
 
 template <int kMode, int kNsq>
-__device__ __forceinline__ void serve_atrous_tile(const ServeItem& it, int l, int2 o) {
+__device__ __forceinline__ void serve_atrous_tile(const ServeItem& it, int l, int t, AtrousSmem& sm) {
     const float4* in = l == 0 ? it.illum : it.pp[(l - 1) & 1];
-    atrous_tile<DHR_FP32, kMode, kNsq>(it.sk, 1 << l, it.g_cur, in, it.pp[l & 1], it.col, it.out_ao, it.out_sh,
-                                       o.x, o.y);
+    atrous_tile<DHR_FP32, kMode, kNsq>(it.sk, 1 << l, t - it.tile_begin, it.g_cur, in, it.pp[l & 1], it.col,
+                                       it.out_ao, it.out_sh, sm);
 }
 
-// level l of every session; mode: 1 writes the colour history, 2 the outputs
+// level l of every session; mode: 1 writes the colour history, 2 the outputs.
+// The session's a-trous tiles are its 32x8 pixel tiles.
 template <int kNsq>
 __global__ void __launch_bounds__(256) serve_atrous_kernel(const BatchTable* tb, int l, int mode) {
+    __shared__ AtrousSmem sm;
     const BatchTable& b = *tb;
     for (int t = blockIdx.x; t < b.n_tiles; t += gridDim.x) {
         const ServeItem& it = b.items[find_item(b, t)];
-        const int2 o = tile_origin(it, t);
-        if (mode == 2) serve_atrous_tile<2, kNsq>(it, l, o);
-        else if (mode == 1) serve_atrous_tile<1, kNsq>(it, l, o);
-        else serve_atrous_tile<0, kNsq>(it, l, o);
+        if (mode == 2) serve_atrous_tile<2, kNsq>(it, l, t, sm);
+        else if (mode == 1) serve_atrous_tile<1, kNsq>(it, l, t, sm);
+        else serve_atrous_tile<0, kNsq>(it, l, t, sm);
     }
 }
 

@@ -118,7 +118,7 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
         float4* out = s->pp[l & 1];
         const int step = 1 << l;
         const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-        DHR_TRY(launch_atrous<P>(mode, nsq, grid, blk, st, k, step, gc, in, out, col, ao_out, sh_out));
+        DHR_TRY(launch_atrous<P>(mode, nsq, st, k, step, gc, in, out, col, ao_out, sh_out));
         if (L == 1) {
             // single iteration: it is both the history source and the output
             passthrough_kernel<P><<<(s->w * s->h + 255) / 256, 256, 0, st>>>(s->w * s->h, out, col, ao_out,
@@ -288,7 +288,7 @@ static dhr_status run_atrous_noalloc(const dhr_gbuffer* g, const float4* illum, 
     const float4* in = illum;
     for (int l = 0; l < L; ++l) {
         float4* out = scratch + (size_t)(l & 1) * kNoallocMaxPixels;
-        DHR_TRY(launch_atrous<P>(l == L - 1 ? 2 : 0, nsq, grid, blk, st, k, 1 << l, gd, in, out, nullptr, ao_out,
+        DHR_TRY(launch_atrous<P>(l == L - 1 ? 2 : 0, nsq, st, k, 1 << l, gd, in, out, nullptr, ao_out,
                                  sh_out));
         in = out;
     }

@@ -511,7 +511,7 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
         for (int l = 0; l < L; ++l) {
             float4* o = t->lev[l & 1];
             const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-            DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, grid, blk, st, k, 1 << l, gc, in, o, t->col, ao, sh));
+            DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, st, k, 1 << l, gc, in, o, t->col, ao, sh));
             if (L == 1) {
                 passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, o, t->col, ao, sh);
                 DHR_CUDA_TRY(cudaGetLastError());
@@ -556,7 +556,7 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
             // recompute the input of level l from the recorded temporal output
             const float4* xin = illum;
             for (int i = 0; i < l; ++i) {
-                DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, grid, blk, st, k, 1 << i, gcur, xin, t->lev[i & 1], nullptr,
+                DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, st, k, 1 << i, gcur, xin, t->lev[i & 1], nullptr,
                                                 nullptr, nullptr));
                 xin = t->lev[i & 1];
             }

@@ -142,6 +142,7 @@ struct SigPlanar {
 struct Reproj {
     int x0, y0;
     float w[4];
+    int q[4];        // tap addresses, clamped into the image
     int ok;          // bit k: tap k valid (00, 10, 01, 11)
     float sumw;
 };
@@ -189,17 +190,27 @@ __device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera&
     r.y0 = (int)y0f;
     // projected depths agree within 1 % plus two pixels of the local depth slope
     const float zlim = __fadd_rn(__fmul_rn(0.01f, zp), __fmul_rn(2.0f, slope));
+    // the four taps' loads are issued together (addresses clamped into the
+    // image); taps outside the image are rejected afterwards
+    uint32_t mq[4];
+    float4 gq[4];
+    bool inb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int qx2 = r.x0 + (k & 1), qy2 = r.y0 + (k >> 1);
+        inb[k] = qx2 >= 0 && qy2 >= 0 && qx2 < W && qy2 < H;
+        r.q[k] = min(max(qy2, 0), H - 1) * W + min(max(qx2, 0), W - 1);
+        mq[k] = __ldg(mesh_prev + r.q[k]);
+        gq[k] = S::g(g_prev, r.q[k]);
+    }
     float sumw = 0.0f;
     int ok = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int qx2 = r.x0 + (k & 1), qy2 = r.y0 + (k >> 1);
-        if (qx2 < 0 || qy2 < 0 || qx2 >= W || qy2 >= H) continue;
-        const size_t q = (size_t)qy2 * W + qx2;
-        if (__ldg(mesh_prev + q) != mp) continue;
-        const float4 gq = S::g(g_prev, q);
-        if (!(fabsf(__fsub_rn(gq.x, zp)) <= zlim)) continue;
-        const float nd = __fadd_rn(__fadd_rn(__fmul_rn(znp.y, gq.y), __fmul_rn(znp.z, gq.z)), __fmul_rn(znp.w, gq.w));
+        if (!inb[k] || mq[k] != mp) continue;
+        if (!(fabsf(__fsub_rn(gq[k].x, zp)) <= zlim)) continue;
+        const float nd = __fadd_rn(__fadd_rn(__fmul_rn(znp.y, gq[k].y), __fmul_rn(znp.z, gq[k].z)),
+                                   __fmul_rn(znp.w, gq[k].w));
         if (!(nd >= 0.9f)) continue;
         ok |= 1 << k;
         sumw = __fadd_rn(sumw, r.w[k]);
@@ -211,6 +222,19 @@ __device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera&
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x and log2(x) by the hardware approximations (ftz)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Background pixels carry variance -1 in the illum buffers (a sentinel
 // that lets the a-trous passes test membership from the buffer they read).
@@ -250,20 +274,28 @@ __device__ __forceinline__ void temporal_tile(
             // same order as sum w so that a constant history stays exactly constant
             valid = true;
             int hmin = 255;
+            float2 cv[4];
+            float4 mv[4];
+            int hv[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {       // loads first, all four taps at once
+                cv[t] = S::col(col_hist, r.q[t]);
+                mv[t] = S::mom(mom_in, r.q[t]);
+                hv[t] = __ldg(hist_in + r.q[t]);
+            }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 if (!(r.ok & (1 << t))) continue;
-                const size_t q = (size_t)(r.y0 + (t >> 1)) * k.W + (r.x0 + (t & 1));
                 const float w = r.w[t];
-                const float2 c = S::col(col_hist, q);
-                const float4 m = S::mom(mom_in, q);
+                const float2 c = cv[t];
+                const float4 m = mv[t];
                 ch.x = fmaf(w, c.x, ch.x);
                 ch.y = fmaf(w, c.y, ch.y);
                 mh.x = fmaf(w, m.x, mh.x);
                 mh.y = fmaf(w, m.y, mh.y);
                 mh.z = fmaf(w, m.z, mh.z);
                 mh.w = fmaf(w, m.w, mh.w);
-                hmin = min(hmin, (int)__ldg(hist_in + q));
+                hmin = min(hmin, hv[t]);
             }
             ch = make_float2(ch.x / r.sumw, ch.y / r.sumw);
             mh = make_float4(mh.x / r.sumw, mh.y / r.sumw, mh.z / r.sumw, mh.w / r.sumw);
@@ -298,18 +330,25 @@ __device__ __forceinline__ void temporal_tile(
                     nz = __shfl_sync(kFull, zn.w, src);
         const float gx = __shfl_sync(kFull, gz.x, src), gy = __shfl_sync(kFull, gz.y, src);
         float sw = 0.f, a1 = 0.f, b1 = 0.f, a2 = 0.f, b2 = 0.f;
-        for (int t = lane; t < 49; t += 32) {
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const int t = lane + 32 * it;
             const int dx = t % 7 - 3, dy = t / 7 - 3;
             const int qx = px + dx, qy = py + dy;
-            if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-            const size_t q = (size_t)qy * k.W + qx;
+            if (t >= 49 || qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
+            const int q = qy * k.W + qx;
             const float4 zq = S::g(g_cur, q);
+            const float2 sq = sig(q);
             if (!is_fg(zq.x)) continue;
+            // w_z w_n = 2^(-|dz| log2(e) / (sigma_z |grad z . d| + eps_z) + sigma_n log2(n.n_q))
             float w = 1.0f;
             if (dx || dy)
-                w = w_depth(zp, zq.x, make_float2(gx, gy), (float)-dx, (float)-dy, k.sigma_z, k.eps_z) *
-                    pow_normal(nx * zq.y + ny * zq.z + nz * zq.w, k.sigma_n, k.sigma_n_int);
-            const float2 sq = sig(q);
+                w = ex2_approx(fmaf(-fabsf(zp - zq.x),
+                                    __fdividef(kLog2e, fmaf(k.sigma_z, fabsf(fmaf(gx, (float)-dx, gy * (float)-dy)),
+                                                            k.eps_z)),
+                                    k.sigma_n == 0.0f ? 0.0f
+                                                      : k.sigma_n * lg2_approx(fmaxf(nx * zq.y + ny * zq.z + nz * zq.w,
+                                                                                     0.0f))));
             sw += w;
             a1 = fmaf(w, sq.x, a1);
             b1 = fmaf(w, sq.y, b1);
@@ -355,44 +394,128 @@ __device__ __forceinline__ float pow_n(float c, float sigma_n, int sigma_n_int) 
     return pow_normal(c, sigma_n, sigma_n_int);
 }
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+
+
+
+// log2 of the normal weight max(0, c)^sigma_n: -inf when c <= 0 (weight 0),
+// 0 when sigma_n == 0 (weight 1, the 0^0 = 1 convention)
+template <int kNsq>
+__device__ __forceinline__ float log2_normal(float c, float sigma_n) {
+    const float l = lg2_approx(fmaxf(c, 0.0f));
+    if constexpr (kNsq >= 0) return (float)(1 << kNsq) * l;
+    else return sigma_n == 0.0f ? 0.0f : sigma_n * l;
 }
 
-struct Acc {
+// Tiling of one a-trous iteration at step s.
+//
+// Step 1: a block takes a 32x8 pixel tile and stages the 36x12 pixels
+// around it (illum and G-buffer) in shared memory once; the 24 taps, the
+// 3x3 variance Gaussian and the depth gradient of every pixel then read
+// shared memory only.  Pixels outside the image are staged as background
+// (variance -1, depth +inf), which gives them weight exactly 0, as if they
+// were skipped.
+//
+// Steps >= 2: the 5x5 footprint spans 4s + 1 pixels, so a staged tile
+// would mostly hold halo; the taps are loaded directly (L1/L2 hits: the
+// level's input and G-buffer stay resident in L2) and the per-pixel terms
+// come from the pixel's immediate neighbours, which adjacent threads share.
+//
+// Both cover the image with the same 32x8 tiles, ceil(W/32) x ceil(H/8).
+constexpr int kAtW = 32, kAtH = 8, kAtHalo = 2;
+constexpr int kAtSW = kAtW + 2 * kAtHalo, kAtSH = kAtH + 2 * kAtHalo;
+
+struct AtrousSmem {
+    float4 c[kAtSH][kAtSW];    // (ao, shadow, var_ao, var_shadow)
+    float4 g[kAtSH][kAtSW];    // (depth, normal)
+};
+
+__host__ __device__ inline int atrous_tiles_x(int W) { return (W + kAtW - 1) / kAtW; }
+__host__ __device__ inline int atrous_tiles(int W, int H) { return atrous_tiles_x(W) * ((H + kAtH - 1) / kAtH); }
+
+// per-axis one-sided depth difference of smaller magnitude (0 if none) from
+// the four neighbour depths (+inf: background or outside the image)
+__device__ __forceinline__ float2 grad_from(float zp, float zxp, float zxm, float zyp, float zym) {
+    const float n[2][2] = {{zxp, zxm}, {zyp, zym}};
+    float r[2];
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        const bool hp = is_fg(n[ax][0]), hm = is_fg(n[ax][1]);
+        const float dp = hp ? n[ax][0] - zp : 0.f, dm = hm ? zp - n[ax][1] : 0.f;
+        r[ax] = (hp && hm) ? (fabsf(dm) < fabsf(dp) ? dm : dp) : (hp ? dp : (hm ? dm : 0.f));
+    }
+    return make_float2(r[0], r[1]);
+}
+
+// tap sources: the staged tile, or the buffers (with or without bounds
+// tests; a tap outside the image reads as background)
+struct TapsSmem {
+    const AtrousSmem& sm;
+    int tx, ty;
+    __device__ __forceinline__ void operator()(int i, int j, float4& c, float4& z) const {
+        c = sm.c[ty + j][tx + i];
+        z = sm.g[ty + j][tx + i];
+    }
+};
+
+template <class S, bool kCheck>
+struct TapsGlobal {
+    const typename S::G* g;
+    const float4* in;
+    int W, H, x, y, step;
+    __device__ __forceinline__ void operator()(int i, int j, float4& c, float4& z) const {
+        const int qx = x + i * step, qy = y + j * step;
+        if (kCheck && (qx < 0 || qy < 0 || qx >= W || qy >= H)) {
+            c = make_float4(1.f, 1.f, -1.f, -1.f);
+            z = make_float4(INFINITY, 0.f, 0.f, 0.f);
+            return;
+        }
+        const int q = qy * W + qx;
+        c = __ldg(in + q);
+        z = S::g(g, q);
+    }
+};
+
+// The weighted sums of one pixel over its 5x5 footprint.  Each tap's weight
+// for channel c, h_i h_j w_n w_z w_l,c, is evaluated as one power of two,
+//   2^(log2(h_i h_j) + sigma_n log2(n.n_q) - |dz| rz - |dc| il_c)
+// (rz and il_c carry log2(e)): one lg2 per tap and one ex2 per channel.
+// Background taps (variance sentinel -1) get exponent -inf, i.e. weight 0.
+struct AtrousSums {
     float sw0, sw1, sc0, sc1, sv0, sv1;
 };
 
-// The 24 non-centre taps of one a-trous iteration.  Background taps (depth
-// +inf, variance sentinel -1) get weight 0 without a branch.
-template <class S, int kNsq, bool kCheck>
-__device__ __forceinline__ void atrous_taps(const SvgfConsts& k, int step, int x, int y, float4 zn, float4 cp,
-                                            float il0, float il1, const float (&rz)[13],
-                                            const typename S::G* g, const float4* in, Acc& a) {
-    const float h5[5] = {1.f / 16, 1.f / 4, 3.f / 8, 1.f / 4, 1.f / 16};
+template <int kNsq, class Taps>
+__device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step, float4 cp, float4 zn, float gv0,
+                                                  float gv1, float gw, float2 gz, const Taps& taps) {
+    // luminance terms folded with log2(e): w_l = 2^(-|dc| il)
+    const float il0 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv0 / gw) + k.eps_l) : 0.f;
+    const float il1 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv1 / gw) + k.eps_l) : 0.f;
+    // depth terms: log2(e) / (sigma_z |grad z . (p - q)| + eps_z) for the 12
+    // offset directions (i, j) ~ (-i, -j) of the 5x5 footprint
+    const float sg = k.sigma_z * (float)step;
+    float rz[13];
+#pragma unroll
+    for (int m = 0; m < 13; ++m) {
+        const int i = m % 5 - 2, j = m / 5 - 2;    // j < 0, or j = 0 and i < 0 (+ centre, m = 12)
+        rz[m] = __fdividef(kLog2e, fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
+    }
+    const float kc = 0.375f * 0.375f;
+    AtrousSums a{kc, kc, kc * cp.x, kc * cp.y, kc * kc * cp.z, kc * kc * cp.w};
+    // log2 of the B3-spline taps 1/16, 1/4, 3/8, 1/4, 1/16
+    const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
 #pragma unroll
     for (int j = -2; j <= 2; ++j) {
-        const int qy = y + j * step;
-        if (kCheck && (qy < 0 || qy >= k.H)) continue;
 #pragma unroll
         for (int i = -2; i <= 2; ++i) {
             if (i == 0 && j == 0) continue;
-            const int qx = x + i * step;
-            if (kCheck && (qx < 0 || qx >= k.W)) continue;
-            const int q = qy * k.W + qx;
-            const float4 cq = __ldg(in + q);
-            const float4 zq = S::g(g, q);
-            const int t = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
-            const float ez = fabsf(zn.x - zq.x) * rz[t];
-            float kw = h5[i + 2] * h5[j + 2] *
-                       pow_n<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n, k.sigma_n_int);
-            kw = fg_var(cq.z) ? kw : 0.0f;
-            float w0 = kw * ex2_approx(-fmaf(fabsf(cp.x - cq.x), il0, ez));
-            float w1 = kw * ex2_approx(-fmaf(fabsf(cp.y - cq.y), il1, ez));
-            w0 = fg_var(cq.z) ? w0 : 0.0f;    // NaN-safe for whatever a background pixel holds
-            w1 = fg_var(cq.z) ? w1 : 0.0f;
+            float4 cq, zq;
+            taps(i, j, cq, zq);
+            const int m = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
+            float e = fmaf(-fabsf(zn.x - zq.x), rz[m], l5[i + 2] + l5[j + 2]);
+            e += log2_normal<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
+            e = fg_var(cq.z) ? e : -INFINITY;
+            const float w0 = ex2_approx(fmaf(-fabsf(cp.x - cq.x), il0, e));
+            const float w1 = ex2_approx(fmaf(-fabsf(cp.y - cq.y), il1, e));
             a.sw0 += w0;
             a.sw1 += w1;
             a.sc0 = fmaf(w0, cq.x, a.sc0);
@@ -401,94 +524,139 @@ __device__ __forceinline__ void atrous_taps(const SvgfConsts& k, int step, int x
             a.sv1 = fmaf(w1 * w1, cq.w, a.sv1);
         }
     }
+    return a;
 }
 
-// one a-trous iteration; kMode 0: write illum_out; 1: also colour history;
-// 2: last iteration, write the two output planes only.  kNsq >= 0: sigma_n
-// is 2^kNsq.
-template <dhr_precision P, int kMode, int kNsq>
-__device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, const typename Store<P>::G* g,
-                                            const float4* in, float4* out, typename Store<P>::Col* col_hist,
-                                            float* ao_out, float* sh_out, int bx0, int by0) {
-    using S = Store<P>;
-    const int x = bx0 + threadIdx.x, y = by0 + threadIdx.y;
-    if (x >= k.W || y >= k.H) return;
-    const int p = y * k.W + x;
-    const float4 cp = __ldg(in + p);
-    if (!fg_var(cp.z)) {
-        if (kMode == 2) {
-            ao_out[p] = 1.f;
-            sh_out[p] = 1.f;
-        } else {
-            out[p] = make_float4(1.f, 1.f, -1.f, -1.f);
-            if (kMode == 1) S::put_col(col_hist, p, make_float2(1.f, 1.f));
-        }
-        return;
-    }
-    const float4 zn = S::g(g, p);
-    // 3x3 Gaussian of the variance, renormalised over foreground taps
-    float gv0 = 0.f, gv1 = 0.f, gw = 0.f;
+// 3x3 Gaussian of the variance, renormalised over foreground taps; v[dy][dx]
+__device__ __forceinline__ void var_gauss(const float4 (&v)[3][3], float& gv0, float& gv1, float& gw) {
+    gv0 = gv1 = gw = 0.f;
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
+    for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int qx = x + dx, qy = y + dy;
-            if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-            const float4 v = __ldg(in + (qy * k.W + qx));
-            if (!fg_var(v.z)) continue;
-            const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
+        for (int dx = 0; dx < 3; ++dx) {
+            if (!fg_var(v[dy][dx].z)) continue;
+            const float kk = (dx == 1 ? 0.5f : 0.25f) * (dy == 1 ? 0.5f : 0.25f);
             gw += kk;
-            gv0 = fmaf(kk, v.z, gv0);
-            gv1 = fmaf(kk, v.w, gv1);
+            gv0 = fmaf(kk, v[dy][dx].z, gv0);
+            gv1 = fmaf(kk, v[dy][dx].w, gv1);
         }
-    }
-    // luminance terms folded with log2(e): w_l = 2^(-|dc| il)
-    const float il0 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv0 / gw) + k.eps_l) : 0.f;
-    const float il1 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv1 / gw) + k.eps_l) : 0.f;
-    // depth terms: log2(e) / (sigma_z |grad z . (p - q)| + eps_z) for the 12
-    // offset directions (i, j) ~ (-i, -j) of the 5x5 footprint
-    const float2 gz = depth_grad<S>(g, k.W, k.H, x, y, zn.x);
-    const float sg = k.sigma_z * (float)step;
-    float rz[13];
-#pragma unroll
-    for (int t = 0; t < 13; ++t) {
-        const int i = t % 5 - 2, j = t / 5 - 2;      // t = 0..12 covers j < 0, and j = 0, i < 0 (t = 10, 11) + centre (12)
-        rz[t] = __fdividef(kLog2e, fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
-    }
-    const float kc = 0.375f * 0.375f;
-    Acc acc;
-    acc.sw0 = kc;
-    acc.sw1 = kc;
-    acc.sc0 = kc * cp.x;
-    acc.sc1 = kc * cp.y;
-    acc.sv0 = kc * kc * cp.z;
-    acc.sv1 = kc * kc * cp.w;
-    // blocks whose 5x5 footprint lies inside the image skip the bounds tests
-    const bool interior = bx0 - 2 * step >= 0 && by0 - 2 * step >= 0 &&
-                          bx0 + (int)blockDim.x - 1 + 2 * step < k.W && by0 + (int)blockDim.y - 1 + 2 * step < k.H;
-    if (interior)
-        atrous_taps<S, kNsq, false>(k, step, x, y, zn, cp, il0, il1, rz, g, in, acc);
-    else
-        atrous_taps<S, kNsq, true>(k, step, x, y, zn, cp, il0, il1, rz, g, in, acc);
-    const float sw0 = acc.sw0, sw1 = acc.sw1, sc0 = acc.sc0, sc1 = acc.sc1, sv0 = acc.sv0, sv1 = acc.sv1;
+}
+
+template <dhr_precision P, int kMode>
+__device__ __forceinline__ void atrous_store(const AtrousSums& a, int p, float4* out,
+                                             typename Store<P>::Col* col_hist, float* ao_out, float* sh_out) {
     // (sum w c) / (sum w): a constant neighbourhood stays exactly constant
-    const float c0 = sc0 / sw0, c1 = sc1 / sw1;
+    const float c0 = a.sc0 / a.sw0, c1 = a.sc1 / a.sw1;
     if (kMode == 2) {
         ao_out[p] = c0;
         sh_out[p] = c1;
     } else {
-        out[p] = make_float4(c0, c1, sv0 / (sw0 * sw0), sv1 / (sw1 * sw1));
-        if (kMode == 1) S::put_col(col_hist, p, make_float2(c0, c1));
+        out[p] = make_float4(c0, c1, a.sv0 / (a.sw0 * a.sw0), a.sv1 / (a.sw1 * a.sw1));
+        if (kMode == 1) Store<P>::put_col(col_hist, p, make_float2(c0, c1));
     }
 }
 
+template <dhr_precision P, int kMode>
+__device__ __forceinline__ void atrous_background(int p, float4* out, typename Store<P>::Col* col_hist,
+                                                  float* ao_out, float* sh_out) {
+    if (kMode == 2) {
+        ao_out[p] = 1.f;
+        sh_out[p] = 1.f;
+    } else {
+        out[p] = make_float4(1.f, 1.f, -1.f, -1.f);
+        if (kMode == 1) Store<P>::put_col(col_hist, p, make_float2(1.f, 1.f));
+    }
+}
+
+// One a-trous iteration over the 32x8 tile t; kMode 0: write illum_out;
+// 1: also the colour history; 2: last iteration, write the two output
+// planes only.  kNsq >= 0: sigma_n is 2^kNsq.  Every thread of the block
+// must call it (block barriers at step 1).
 template <dhr_precision P, int kMode, int kNsq>
-__global__ void __launch_bounds__(256) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
+__device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t, const typename Store<P>::G* g,
+                                            const float4* in, float4* out, typename Store<P>::Col* col_hist,
+                                            float* ao_out, float* sh_out, AtrousSmem& sm) {
+    using S = Store<P>;
+    const int ntx = atrous_tiles_x(k.W);
+    const int bx0 = (t % ntx) * kAtW, by0 = (t / ntx) * kAtH;
+    const int x = bx0 + (int)threadIdx.x, y = by0 + (int)threadIdx.y;
+    const bool inside = x < k.W && y < k.H;
+    const int p = y * k.W + x;
+    if (step == 1) {
+        for (int i = threadIdx.y * kAtW + threadIdx.x; i < kAtSW * kAtSH; i += kAtW * kAtH) {
+            const int sy = i / kAtSW, sx = i - sy * kAtSW;
+            const int qx = bx0 - kAtHalo + sx, qy = by0 - kAtHalo + sy;
+            float4 c = make_float4(1.f, 1.f, -1.f, -1.f), z = make_float4(INFINITY, 0.f, 0.f, 0.f);
+            if (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H) {
+                const int q = qy * k.W + qx;
+                c = __ldg(in + q);
+                z = S::g(g, q);
+            }
+            sm.c[sy][sx] = c;
+            sm.g[sy][sx] = z;
+        }
+        __syncthreads();
+        const int tx = threadIdx.x + kAtHalo, ty = threadIdx.y + kAtHalo;
+        const float4 cp = sm.c[ty][tx];
+        if (inside) {
+            if (!fg_var(cp.z)) {
+                atrous_background<P, kMode>(p, out, col_hist, ao_out, sh_out);
+            } else {
+                const float4 zn = sm.g[ty][tx];
+                float4 v[3][3];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) v[dy][dx] = sm.c[ty + dy - 1][tx + dx - 1];
+                float gv0, gv1, gw;
+                var_gauss(v, gv0, gv1, gw);
+                const float2 gz = grad_from(zn.x, sm.g[ty][tx + 1].x, sm.g[ty][tx - 1].x, sm.g[ty + 1][tx].x,
+                                            sm.g[ty - 1][tx].x);
+                const AtrousSums a = atrous_sums<kNsq>(k, 1, cp, zn, gv0, gv1, gw, gz, TapsSmem{sm, tx, ty});
+                atrous_store<P, kMode>(a, p, out, col_hist, ao_out, sh_out);
+            }
+        }
+        __syncthreads();    // the staging area is reused by the block's next tile
+        return;
+    }
+    if (!inside) return;
+    const float4 cp = __ldg(in + p);
+    if (!fg_var(cp.z)) {
+        atrous_background<P, kMode>(p, out, col_hist, ao_out, sh_out);
+        return;
+    }
+    const float4 zn = S::g(g, p);
+    float4 v[3][3];
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int qx = x + dx, qy = y + dy;
+            v[dy + 1][dx + 1] = (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) ? make_float4(1.f, 1.f, -1.f, -1.f)
+                                                                              : __ldg(in + (qy * k.W + qx));
+        }
+    float gv0, gv1, gw;
+    var_gauss(v, gv0, gv1, gw);
+    const float2 gz = grad_from(zn.x, x + 1 < k.W ? S::g(g, p + 1).x : INFINITY, x > 0 ? S::g(g, p - 1).x : INFINITY,
+                                y + 1 < k.H ? S::g(g, p + k.W).x : INFINITY, y > 0 ? S::g(g, p - k.W).x : INFINITY);
+    // blocks whose 5x5 footprint lies inside the image skip the bounds tests
+    const bool interior = bx0 - 2 * step >= 0 && by0 - 2 * step >= 0 && bx0 + kAtW - 1 + 2 * step < k.W &&
+                          by0 + kAtH - 1 + 2 * step < k.H;
+    AtrousSums a;
+    if (interior)
+        a = atrous_sums<kNsq>(k, step, cp, zn, gv0, gv1, gw, gz, TapsGlobal<S, false>{g, in, k.W, k.H, x, y, step});
+    else
+        a = atrous_sums<kNsq>(k, step, cp, zn, gv0, gv1, gw, gz, TapsGlobal<S, true>{g, in, k.W, k.H, x, y, step});
+    atrous_store<P, kMode>(a, p, out, col_hist, ao_out, sh_out);
+}
+
+template <dhr_precision P, int kMode, int kNsq>
+__global__ void __launch_bounds__(256, 4) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
                                                      const float4* in, float4* out,
                                                      typename Store<P>::Col* col_hist, float* ao_out,
                                                      float* sh_out) {
-    atrous_tile<P, kMode, kNsq>(k, step, g, in, out, col_hist, ao_out, sh_out, blockIdx.x * blockDim.x,
-                                blockIdx.y * blockDim.y);
+    __shared__ AtrousSmem sm;
+    atrous_tile<P, kMode, kNsq>(k, step, blockIdx.x, g, in, out, col_hist, ao_out, sh_out, sm);
 }
 
 // levels == 0: the temporal colour is the output and the colour history
@@ -525,25 +693,27 @@ inline SvgfConsts make_consts(int W, int H, const dhr_svgf_params* prm) {
 inline int atrous_nsq(const dhr_svgf_params* prm) { return prm->sigma_n == 128.0f ? 7 : -1; }
 
 template <dhr_precision P, int kMode>
-inline void launch_atrous_mode(int nsq, dim3 grid, dim3 blk, cudaStream_t st, const SvgfConsts& k, int step,
+inline void launch_atrous_mode(int nsq, cudaStream_t st, const SvgfConsts& k, int step,
                                const typename Store<P>::G* g, const float4* in, float4* out,
                                typename Store<P>::Col* col, float* ao_out, float* sh_out) {
+    const dim3 grid(atrous_tiles(k.W, k.H)), blk(kAtW, kAtH);
     if (nsq == 7)
         atrous_kernel<P, kMode, 7><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
     else
         atrous_kernel<P, kMode, -1><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
 }
 
+// one a-trous iteration at `step` over the whole W x H image of `k`
 template <dhr_precision P>
-inline dhr_status launch_atrous(int mode, int nsq, dim3 grid, dim3 blk, cudaStream_t st, const SvgfConsts& k,
-                                int step, const typename Store<P>::G* g, const float4* in, float4* out,
+inline dhr_status launch_atrous(int mode, int nsq, cudaStream_t st, const SvgfConsts& k, int step,
+                                const typename Store<P>::G* g, const float4* in, float4* out,
                                 typename Store<P>::Col* col, float* ao_out, float* sh_out) {
     if (mode == 2)
-        launch_atrous_mode<P, 2>(nsq, grid, blk, st, k, step, g, in, nullptr, nullptr, ao_out, sh_out);
+        launch_atrous_mode<P, 2>(nsq, st, k, step, g, in, nullptr, nullptr, ao_out, sh_out);
     else if (mode == 1)
-        launch_atrous_mode<P, 1>(nsq, grid, blk, st, k, step, g, in, out, col, nullptr, nullptr);
+        launch_atrous_mode<P, 1>(nsq, st, k, step, g, in, out, col, nullptr, nullptr);
     else
-        launch_atrous_mode<P, 0>(nsq, grid, blk, st, k, step, g, in, out, nullptr, nullptr, nullptr);
+        launch_atrous_mode<P, 0>(nsq, st, k, step, g, in, out, nullptr, nullptr, nullptr);
     DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
 }

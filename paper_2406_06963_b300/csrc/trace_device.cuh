@@ -95,13 +95,25 @@ __device__ __forceinline__ bool hit_triangle(const Ray& r, float3 v0, float3 v1,
     return true;
 }
 
+// three-operand min / max (one instruction on sm_100 and later)
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ void slab(const Ray& r, float lox, float hix, float loy, float hiy, float loz,
                                      float hiz, float tmin, float tmax, float& enter, bool& hit) {
     const float x0 = fmaf(lox, r.idir.x, -r.oidir.x), x1 = fmaf(hix, r.idir.x, -r.oidir.x);
     const float y0 = fmaf(loy, r.idir.y, -r.oidir.y), y1 = fmaf(hiy, r.idir.y, -r.oidir.y);
     const float z0 = fmaf(loz, r.idir.z, -r.oidir.z), z1 = fmaf(hiz, r.idir.z, -r.oidir.z);
-    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
-    const float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    const float tn = max3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), tmin));
+    const float tf = min3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), tmax));
     enter = tn;
     hit = tn <= tf * 1.00000024f;   // 1 + 2 gamma(3) with unit roundoff 2^-24
 }
