@@ -74,6 +74,13 @@ def _traffic(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
+def _svgf_traffic():
+    """DRAM bytes of one frame's SVGF (temporal + 5 a-trous launches) from the
+    committed captures, or None when either kernel changed since."""
+    t, a = _traffic("temporal_kernel"), _traffic("atrous_kernel")
+    return None if t is None or a is None else t + 5 * a
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -267,7 +274,8 @@ def run_ours(args):
                      "peak_source": "148 SMs x 128 fp32 lanes x max SM clock (%s)" % peak_src},
         "roofline_svgf": {"bound": "hbm", "achieved": round(svgf_gbs, 1), "peak": peaks["hbm_gbs"],
                           "unit": "GB/s", "frac": round(svgf_gbs / peaks["hbm_gbs"], 4),
-                          "algorithmic_bytes_per_px": 340, "peak_source": peak_src},
+                          "algorithmic_bytes_per_px": 340, "peak_source": peak_src,
+                          "traffic_per_frame": _svgf_traffic()},
         "e2e": {"value": round(e2e_value, 2), "unit": "Mrays/s", "h2d_bytes_per_step": 60,
                 "d2h_bytes_per_step": 2 * 4 * W * H,
                 "ms_per_step": round(e2e_s * 1e3 / K, 4)},

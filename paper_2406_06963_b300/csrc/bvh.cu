@@ -382,7 +382,7 @@ struct Scratch {
 // boxes in s.lo / s.hi ([0, n-1) internal, [n-1, 2n-1) leaves).
 dhr_status build_ploc(const float* v, const uint32_t* idx, const uint32_t* mesh, int n, cudaStream_t st,
                       dhr_scene* sc, Scratch& s) {
-    constexpr int kRadius = 16;
+    constexpr int kRadius = 32;
     for (int b = 0; b < 2; ++b) {
         DHR_TRY(dmalloc(&s.cl_ref[b], n, "clusters"));
         DHR_TRY(dmalloc(&s.cl_lo[b], n, "clusters"));
