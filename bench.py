@@ -440,9 +440,9 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
     e[2].record()
     torch.cuda.synchronize()
     fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-    # algorithmic bytes per pixel and frame: forward 340; backward: 10 level
+    # algorithmic bytes per pixel and frame: forward 340; backward: 4 level
     # recomputations x 48, 5 x (pass A 112 + pass B 112), temporal 100
-    bytes_fb = frames * W * H * (340 + 480 + 5 * 224 + 100)
+    bytes_fb = frames * W * H * (340 + 4 * 48 + 5 * 224 + 100)
     log_s = torch.tensor([0.0, 4.852, 1.386], device="cuda").requires_grad_(True)  # log(1, 128, 4)
     opt = torch.optim.Adam([log_s], lr=0.05)
     losses = []

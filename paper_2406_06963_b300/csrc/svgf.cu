@@ -79,20 +79,7 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
                            const uint8_t* ao, const dhr_svgf_params* prm, float* ao_out, float* sh_out,
                            cudaStream_t st) {
     using S = Store<P>;
-    SvgfConsts k;
-    k.W = s->w;
-    k.H = s->h;
-    k.alpha = prm->alpha;
-    k.sigma_z = prm->sigma_z;
-    k.sigma_n = prm->sigma_n;
-    k.sigma_l = prm->sigma_l;
-    k.eps_z = prm->eps_z;
-    k.eps_l = prm->eps_l;
-    k.inv_spp = 1.0f / (float)prm->ao_spp;
-    k.fixed_alpha = (int)prm->fixed_alpha;
-    k.wl_in_atrous = (int)prm->wl_in_atrous;
-    k.sigma_n_int = (prm->sigma_n >= 1.0f && prm->sigma_n <= 1024.0f && prm->sigma_n == floorf(prm->sigma_n))
-                        ? (int)prm->sigma_n : 0;
+    const SvgfConsts k = make_consts(s->w, s->h, prm);
     const int src = s->cur, dst = s->cur ^ 1;
     const dim3 blk(32, 8), grid((s->w + 31) / 32, (s->h + 7) / 8);
     const auto* gc = static_cast<const typename S::G*>(cur->depth_normal);
@@ -113,7 +100,7 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
         return DHR_OK;
     }
     const float4* in = s->illum;
-    const int nsq = (prm->sigma_n == 128.0f) ? 7 : -1;
+    const int nsq = atrous_nsq(prm);
     for (int l = 0; l < L; ++l) {
         float4* out = s->pp[l & 1];
         const int step = 1 << l;
@@ -267,22 +254,8 @@ static dhr_status noalloc_scratch(float4** out) {
 template <dhr_precision P>
 static dhr_status run_atrous_noalloc(const dhr_gbuffer* g, const float4* illum, const dhr_svgf_params* prm,
                                      float* ao_out, float* sh_out, float4* scratch, cudaStream_t st) {
-    SvgfConsts k;
-    k.W = g->width;
-    k.H = g->height;
-    k.alpha = prm->alpha;
-    k.sigma_z = prm->sigma_z;
-    k.sigma_n = prm->sigma_n;
-    k.sigma_l = prm->sigma_l;
-    k.eps_z = prm->eps_z;
-    k.eps_l = prm->eps_l;
-    k.inv_spp = 1.0f / (float)prm->ao_spp;
-    k.fixed_alpha = (int)prm->fixed_alpha;
-    k.wl_in_atrous = (int)prm->wl_in_atrous;
-    k.sigma_n_int = (prm->sigma_n >= 1.0f && prm->sigma_n <= 1024.0f && prm->sigma_n == floorf(prm->sigma_n))
-                        ? (int)prm->sigma_n : 0;
-    const dim3 blk(32, 8), grid((k.W + 31) / 32, (k.H + 7) / 8);
-    const int nsq = (prm->sigma_n == 128.0f) ? 7 : -1;
+    const SvgfConsts k = make_consts(g->width, g->height, prm);
+    const int nsq = atrous_nsq(prm);
     const auto* gd = static_cast<const typename Store<P>::G*>(g->depth_normal);
     const int L = (int)prm->levels;
     const float4* in = illum;

@@ -70,20 +70,21 @@ struct TapW {
     float nd;         // n_p . n_q
 };
 
+// The weight is evaluated as one power of two, as in the forward kernel:
+// 2^(log2(h_i h_j) + sigma_n log2(n.n_q) - log2(e) (|dz| / D + |dc| il)).
 template <int kNsq>
 __device__ __forceinline__ TapW tap_weight(const SvgfConsts& k, int step, int i, int j, float4 zp, float2 gz,
                                            float cp0, float cp1, float il0, float il1, float4 zq, float cq0,
                                            float cq1) {
-    const float h5[5] = {1.f / 16, 1.f / 4, 3.f / 8, 1.f / 4, 1.f / 16};
+    const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
     TapW t;
     t.a_off = (float)step * fabsf(fmaf(gz.x, (float)i, gz.y * (float)j));
     t.D = fmaf(k.sigma_z, t.a_off, k.eps_z);
     t.dz = fabsf(zp.x - zq.x);
     t.nd = zp.y * zq.y + zp.z * zq.z + zp.w * zq.w;
-    const float kw = h5[i + 2] * h5[j + 2] * pow_n<kNsq>(t.nd, k.sigma_n, k.sigma_n_int);
-    const float ez = t.dz / t.D;
-    t.w0 = kw * __expf(-(ez + fabsf(cp0 - cq0) * il0));
-    t.w1 = kw * __expf(-(ez + fabsf(cp1 - cq1) * il1));
+    const float e = fmaf(-kLog2e, __fdividef(t.dz, t.D), l5[i + 2] + l5[j + 2]) + log2_normal<kNsq>(t.nd, k.sigma_n);
+    t.w0 = ex2_approx(fmaf(-kLog2e * il0, fabsf(cp0 - cq0), e));
+    t.w1 = ex2_approx(fmaf(-kLog2e * il1, fabsf(cp1 - cq1), e));
     return t;
 }
 
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(kThreadsA) atrous_bwd_a(SvgfConsts k, int step
                     Gil1 -= Gw1 * t.w1 * fabsf(d1);
                 }
                 const float gw01 = Gw0 * t.w0 + Gw1 * t.w1;
-                gsz += gw01 * t.dz * t.a_off / (t.D * t.D);
+                gsz += __fdividef(gw01 * t.dz * t.a_off, t.D * t.D);
                 if (t.nd > 0.f) gsn += gw01 * __logf(t.nd);
             }
         float Gg0 = 0.f, Gg1 = 0.f;
@@ -308,10 +309,7 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                     const int q = qy * k.W + qx;
                     const float4 zq = S::g(g_cur, q);
                     if (!is_fg(zq.x)) continue;
-                    float w = 1.f;
-                    if (dx || dy)
-                        w = w_depth(zn.x, zq.x, gz, (float)-dx, (float)-dy, k.sigma_z, k.eps_z) *
-                            pow_normal(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n, k.sigma_n_int);
+                    const float w = w_spatial(k, zn.x, make_float3(zn.y, zn.z, zn.w), gz, dx, dy, zq);
                     const float sx = sig[q], sy = sig[N + q];
                     sw += w;
                     s1x = fmaf(w, sx, s1x);
@@ -330,21 +328,20 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                     const int q = qy * k.W + qx;
                     const float4 zq = S::g(g_cur, q);
                     if (!is_fg(zq.x)) continue;
-                    float w = 1.f, a_off = 0.f, D = 1.f, nd = 1.f;
+                    float a_off = 0.f, D = 1.f, nd = 1.f;
                     if (dx || dy) {
-                        a_off = fabsf(gz.x * (float)-dx + gz.y * (float)-dy);
+                        a_off = fabsf(fmaf(gz.x, (float)-dx, gz.y * (float)-dy));
                         D = fmaf(k.sigma_z, a_off, k.eps_z);
                         nd = zn.y * zq.y + zn.z * zq.z + zn.w * zq.w;
-                        w = w_depth(zn.x, zq.x, gz, (float)-dx, (float)-dy, k.sigma_z, k.eps_z) *
-                            pow_normal(nd, k.sigma_n, k.sigma_n_int);
                     }
+                    const float w = w_spatial(k, zn.x, make_float3(zn.y, zn.z, zn.w), gz, dx, dy, zq);
                     const float sx = sig[q], sy = sig[N + q];
                     atomicAdd(g_sig + q, (G1x + G2x * 2.f * sx) * w / sw);
                     atomicAdd(g_sig + N + q, (G1y + G2y * 2.f * sy) * w / sw);
                     if (dx || dy) {
                         const float Gw = (G1x * (sx - m1x) + G2x * (sx * sx - m2x) + G1y * (sy - m1y) +
                                           G2y * (sy * sy - m2y)) / sw;
-                        gsz += Gw * w * fabsf(zn.x - zq.x) * a_off / (D * D);
+                        gsz += __fdividef(Gw * w * fabsf(zn.x - zq.x) * a_off, D * D);
                         if (nd > 0.f) gsn += Gw * w * __logf(nd);
                     }
                 }
@@ -370,13 +367,33 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
     block_sum3(gsz, gsn, 0.f, partial);
 }
 
-// sum the per-block partials in a fixed order into acc[3] (double)
-__global__ void reduce_partials_kernel(int nblocks, const float* partial, double* acc) {
-    const int c = threadIdx.x;
-    if (c >= 3) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += (double)partial[3 * b + c];
-    acc[c] += s;
+// sum the per-block partials into acc[3] (double) with one block of
+// kReduceThreads threads: a fixed assignment of partials to threads and a
+// fixed tree, so the sum is the same on every run
+constexpr int kReduceThreads = 256;
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(int nblocks, const float* partial,
+                                                                         double* acc) {
+    __shared__ double sh[3][kReduceThreads];
+    const int t = threadIdx.x;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int b = t; b < nblocks; b += kReduceThreads) {
+        s0 += (double)partial[3 * b + 0];
+        s1 += (double)partial[3 * b + 1];
+        s2 += (double)partial[3 * b + 2];
+    }
+    sh[0][t] = s0;
+    sh[1][t] = s1;
+    sh[2][t] = s2;
+    __syncthreads();
+    for (int o = kReduceThreads / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            sh[0][t] += sh[0][t + o];
+            sh[1][t] += sh[1][t + o];
+            sh[2][t] += sh[2][t + o];
+        }
+        __syncthreads();
+    }
+    if (t < 3) acc[t] += sh[t][0];
 }
 
 __global__ void finish_sigma_kernel(const double* acc, float* out) {
@@ -395,6 +412,8 @@ struct dhr_svgf_tape {
     uint8_t* hist = nullptr;   // [F][N] history lengths
     float2* col = nullptr;     // [N] colour history (forward)
     float4* lev[2] = {nullptr, nullptr};
+    float4* lvin = nullptr;    // [levels - 1][N] inputs of levels 1.. (backward scratch)
+    int lvin_levels = 0;
     float2* gc[2] = {nullptr, nullptr};
     float2* gv[2] = {nullptr, nullptr};
     float2* gcol[2] = {nullptr, nullptr};
@@ -421,6 +440,7 @@ static void tape_free(dhr_svgf_tape* t) {
         cudaFree(t->gmom[i]);
     }
     cudaFree(t->rec);
+    cudaFree(t->lvin);
     cudaFree(t->partial);
     cudaFree(t->acc);
     delete t;
@@ -540,6 +560,18 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
     const dim3 blk(32, 8), grid((t->W + 31) / 32, (t->H + 7) / 8);
     const int eb = (n + 255) / 256;
     const int L = (int)params->levels;
+    if (L > 1 && t->lvin_levels < L - 1) {   // inputs of levels 1..L-1, allocated on first use
+        cudaFree(t->lvin);
+        t->lvin = nullptr;
+        t->lvin_levels = 0;
+        const cudaError_t e = cudaMalloc((void**)&t->lvin, (size_t)(L - 1) * N * 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
+                             "svgf_seq_backward: level scratch: %s", cudaGetErrorString(e));
+        }
+        t->lvin_levels = L - 1;
+    }
     DHR_CUDA_TRY(cudaMemsetAsync(g_sig, 0, (size_t)t->F * 2 * N * sizeof(float), st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->acc, 0, 3 * sizeof(double), st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[0], 0, N * 8, st));
@@ -552,14 +584,12 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
         gather_planes_kernel<<<eb, 256, 0, st>>>(n, g_out + (size_t)f * 2 * N, L == 0 ? t->gcol[nx] : nullptr,
                                                 t->gc[0], t->gv[0]);
         DHR_CUDA_TRY(cudaGetLastError());
+        // recompute the inputs of levels 1..L-1 from the recorded temporal output
+        for (int i = 0; i + 1 < L; ++i)
+            DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, st, k, 1 << i, gcur, i == 0 ? illum : t->lvin + (size_t)(i - 1) * N,
+                                            t->lvin + (size_t)i * N, nullptr, nullptr, nullptr));
         for (int l = L - 1; l >= 0; --l) {
-            // recompute the input of level l from the recorded temporal output
-            const float4* xin = illum;
-            for (int i = 0; i < l; ++i) {
-                DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, st, k, 1 << i, gcur, xin, t->lev[i & 1], nullptr,
-                                                nullptr, nullptr));
-                xin = t->lev[i & 1];
-            }
+            const float4* xin = l == 0 ? illum : t->lvin + (size_t)(l - 1) * N;
             if (l == 0) {   // level-0 colour is also next frame's colour history
                 add2_kernel<<<eb, 256, 0, st>>>(n, t->gc[cur], t->gcol[nx]);
                 DHR_CUDA_TRY(cudaGetLastError());
@@ -570,7 +600,7 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
                 atrous_bwd_a<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->gc[cur], t->gv[cur], t->rec,
                                                        t->partial);
             DHR_CUDA_TRY(cudaGetLastError());
-            reduce_partials_kernel<<<1, 32, 0, st>>>(t->nblocks, t->partial, t->acc);
+            reduce_partials_kernel<<<1, kReduceThreads, 0, st>>>(t->nblocks, t->partial, t->acc);
             if (nsq == 7)
                 atrous_bwd_b<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc[cur ^ 1], t->gv[cur ^ 1]);
             else
@@ -588,7 +618,7 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
             sig + (size_t)f * 2 * N, t->mom + (size_t)f * N, t->hist + (size_t)f * N, t->gc[cur], t->gv[cur],
             t->gmom[nx], g_sig + (size_t)f * 2 * N, t->gcol[pv], t->gmom[pv], t->partial);
         DHR_CUDA_TRY(cudaGetLastError());
-        reduce_partials_kernel<<<1, 32, 0, st>>>(t->nblocks, t->partial, t->acc);
+        reduce_partials_kernel<<<1, kReduceThreads, 0, st>>>(t->nblocks, t->partial, t->acc);
         nx = pv;
     }
     finish_sigma_kernel<<<1, 32, 0, st>>>(t->acc, g_sigma);

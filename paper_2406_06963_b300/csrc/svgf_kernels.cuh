@@ -65,31 +65,9 @@ struct SvgfConsts {
     float alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
     float inv_spp;
     int fixed_alpha, wl_in_atrous;
-    int sigma_n_int;    // sigma_n when it is an integer in 1..1024, else 0
 };
 
 __device__ __forceinline__ bool is_fg(float z) { return z < INFINITY; }
-
-// max(0, c)^sigma_n with 0^0 = 1.  Integer exponents up to 1024 (the usual
-// case, e.g. 128) use repeated squaring: a few multiplies and relative error
-// ~1e-6, where exp2(sigma_n log2 c) would amplify the log2 error sigma_n-fold.
-__device__ __forceinline__ float pow_normal(float c, float sigma_n, int int_exp) {
-    if (sigma_n == 0.0f) return 1.0f;
-    c = fmaxf(c, 0.0f);
-    if (int_exp > 0) {
-        float r = 1.0f, b = c;
-        for (int e = int_exp; e; e >>= 1) {
-            if (e & 1) r *= b;
-            b *= b;
-        }
-        return r;
-    }
-    return c > 0.0f ? exp2f(sigma_n * log2f(c)) : 0.0f;
-}
-
-__device__ __forceinline__ float w_depth(float zp, float zq, float2 g, float ox, float oy, float sz, float ez) {
-    return __expf(-fabsf(zp - zq) / (sz * fabsf(fmaf(g.x, ox, g.y * oy)) + ez));
-}
 
 // per-axis one-sided depth difference of smaller magnitude (0 if none)
 template <class S>
@@ -240,6 +218,19 @@ __device__ __forceinline__ float lg2_approx(float x) {
 // that lets the a-trous passes test membership from the buffer they read).
 __device__ __forceinline__ bool fg_var(float v) { return v >= 0.0f; }
 
+// w_z w_n of the 7x7 short-history estimate for the tap at offset (dx, dy)
+// from a centre of depth zp, normal np and depth gradient gz:
+//   2^(-|dz| log2(e) / (sigma_z |grad z . (p - q)| + eps_z) + sigma_n log2(n.n_q))
+__device__ __forceinline__ float w_spatial(const SvgfConsts& k, float zp, float3 np, float2 gz, int dx, int dy,
+                                           float4 zq) {
+    if (!(dx || dy)) return 1.0f;
+    const float rz = __fdividef(kLog2e, fmaf(k.sigma_z, fabsf(fmaf(gz.x, (float)-dx, gz.y * (float)-dy)), k.eps_z));
+    const float ln = k.sigma_n == 0.0f
+                         ? 0.0f
+                         : k.sigma_n * lg2_approx(fmaxf(np.x * zq.y + np.y * zq.z + np.z * zq.w, 0.0f));
+    return ex2_approx(fmaf(-fabsf(zp - zq.x), rz, ln));
+}
+
 // Temporal step for the 32x8 tile at (bx0, by0), run by a 32x8 block.
 template <dhr_precision P, class Sig>
 __device__ __forceinline__ void temporal_tile(
@@ -340,15 +331,7 @@ __device__ __forceinline__ void temporal_tile(
             const float4 zq = S::g(g_cur, q);
             const float2 sq = sig(q);
             if (!is_fg(zq.x)) continue;
-            // w_z w_n = 2^(-|dz| log2(e) / (sigma_z |grad z . d| + eps_z) + sigma_n log2(n.n_q))
-            float w = 1.0f;
-            if (dx || dy)
-                w = ex2_approx(fmaf(-fabsf(zp - zq.x),
-                                    __fdividef(kLog2e, fmaf(k.sigma_z, fabsf(fmaf(gx, (float)-dx, gy * (float)-dy)),
-                                                            k.eps_z)),
-                                    k.sigma_n == 0.0f ? 0.0f
-                                                      : k.sigma_n * lg2_approx(fmaxf(nx * zq.y + ny * zq.z + nz * zq.w,
-                                                                                     0.0f))));
+            const float w = w_spatial(k, zp, make_float3(nx, ny, nz), make_float2(gx, gy), dx, dy, zq);
             sw += w;
             a1 = fmaf(w, sq.x, a1);
             b1 = fmaf(w, sq.y, b1);
@@ -380,22 +363,6 @@ __global__ void __launch_bounds__(256) temporal_kernel(
     temporal_tile<P, Sig>(k, cam, cam_prev, g_cur, mesh_cur, g_prev, mesh_prev, sig, col_hist, mom_in, hist_in,
                           mom_out, hist_out, illum, blockIdx.x * 32, blockIdx.y * 8);
 }
-
-// max(0, c)^sigma_n for the a-trous taps: 2^kNsq by kNsq squarings, or the
-// generic path (kNsq < 0)
-template <int kNsq>
-__device__ __forceinline__ float pow_n(float c, float sigma_n, int sigma_n_int) {
-    if (kNsq >= 0) {
-        float r = fmaxf(c, 0.0f);
-#pragma unroll
-        for (int i = 0; i < kNsq; ++i) r *= r;
-        return r;
-    }
-    return pow_normal(c, sigma_n, sigma_n_int);
-}
-
-
-
 
 // log2 of the normal weight max(0, c)^sigma_n: -inf when c <= 0 (weight 0),
 // 0 when sigma_n == 0 (weight 1, the 0^0 = 1 convention)
@@ -685,8 +652,6 @@ inline SvgfConsts make_consts(int W, int H, const dhr_svgf_params* prm) {
     k.inv_spp = 1.0f / (float)prm->ao_spp;
     k.fixed_alpha = (int)prm->fixed_alpha;
     k.wl_in_atrous = (int)prm->wl_in_atrous;
-    k.sigma_n_int = (prm->sigma_n >= 1.0f && prm->sigma_n <= 1024.0f && prm->sigma_n == floorf(prm->sigma_n))
-                        ? (int)prm->sigma_n : 0;
     return k;
 }
 
