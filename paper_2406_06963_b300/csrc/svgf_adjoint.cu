@@ -82,7 +82,7 @@ __device__ __forceinline__ TapW tap_weight(const SvgfConsts& k, int step, int i,
     t.D = fmaf(k.sigma_z, t.a_off, k.eps_z);
     t.dz = fabsf(zp.x - zq.x);
     t.nd = zp.y * zq.y + zp.z * zq.z + zp.w * zq.w;
-    const float e = fmaf(-kLog2e, __fdividef(t.dz, t.D), l5[i + 2] + l5[j + 2]) + log2_normal<kNsq>(t.nd, k.sigma_n);
+    const float e = fmaf(-kLog2e, t.dz * rcp_approx(t.D), l5[i + 2] + l5[j + 2]) + log2_normal<kNsq>(t.nd, k.sigma_n);
     t.w0 = ex2_approx(fmaf(-kLog2e * il0, fabsf(cp0 - cq0), e));
     t.w1 = ex2_approx(fmaf(-kLog2e * il1, fabsf(cp1 - cq1), e));
     return t;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreadsA) atrous_bwd_a(SvgfConsts k, int step
                     Gil1 -= Gw1 * t.w1 * fabsf(d1);
                 }
                 const float gw01 = Gw0 * t.w0 + Gw1 * t.w1;
-                gsz += __fdividef(gw01 * t.dz * t.a_off, t.D * t.D);
+                gsz += gw01 * t.dz * t.a_off * rcp_approx(t.D * t.D);
                 if (t.nd > 0.f) gsn += gw01 * __logf(t.nd);
             }
         float Gg0 = 0.f, Gg1 = 0.f;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                     if (dx || dy) {
                         const float Gw = (G1x * (sx - m1x) + G2x * (sx * sx - m2x) + G1y * (sy - m1y) +
                                           G2y * (sy * sy - m2y)) / sw;
-                        gsz += __fdividef(Gw * w * fabsf(zn.x - zq.x) * a_off, D * D);
+                        gsz += Gw * w * fabsf(zn.x - zq.x) * a_off * rcp_approx(D * D);
                         if (nd > 0.f) gsn += Gw * w * __logf(nd);
                     }
                 }

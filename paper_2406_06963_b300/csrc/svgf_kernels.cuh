@@ -214,6 +214,20 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
+// 1/x and sqrt(x) by the hardware approximations (ftz): one special-function
+// instruction each, for weights and scales that need no correct rounding
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Background pixels carry variance -1 in the illum buffers (a sentinel
 // that lets the a-trous passes test membership from the buffer they read).
 __device__ __forceinline__ bool fg_var(float v) { return v >= 0.0f; }
@@ -224,7 +238,7 @@ __device__ __forceinline__ bool fg_var(float v) { return v >= 0.0f; }
 __device__ __forceinline__ float w_spatial(const SvgfConsts& k, float zp, float3 np, float2 gz, int dx, int dy,
                                            float4 zq) {
     if (!(dx || dy)) return 1.0f;
-    const float rz = __fdividef(kLog2e, fmaf(k.sigma_z, fabsf(fmaf(gz.x, (float)-dx, gz.y * (float)-dy)), k.eps_z));
+    const float rz = kLog2e * rcp_approx(fmaf(k.sigma_z, fabsf(fmaf(gz.x, (float)-dx, gz.y * (float)-dy)), k.eps_z));
     const float ln = k.sigma_n == 0.0f
                          ? 0.0f
                          : k.sigma_n * lg2_approx(fmaxf(np.x * zq.y + np.y * zq.z + np.z * zq.w, 0.0f));
@@ -455,8 +469,9 @@ template <int kNsq, class Taps>
 __device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step, float4 cp, float4 zn, float gv0,
                                                   float gv1, float gw, float2 gz, const Taps& taps) {
     // luminance terms folded with log2(e): w_l = 2^(-|dc| il)
-    const float il0 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv0 / gw) + k.eps_l) : 0.f;
-    const float il1 = k.wl_in_atrous ? kLog2e / (k.sigma_l * sqrtf(gv1 / gw) + k.eps_l) : 0.f;
+    const float rgw = rcp_approx(gw);
+    const float il0 = k.wl_in_atrous ? kLog2e * rcp_approx(fmaf(k.sigma_l, sqrt_approx(gv0 * rgw), k.eps_l)) : 0.f;
+    const float il1 = k.wl_in_atrous ? kLog2e * rcp_approx(fmaf(k.sigma_l, sqrt_approx(gv1 * rgw), k.eps_l)) : 0.f;
     // depth terms: log2(e) / (sigma_z |grad z . (p - q)| + eps_z) for the 12
     // offset directions (i, j) ~ (-i, -j) of the 5x5 footprint
     const float sg = k.sigma_z * (float)step;
@@ -464,7 +479,7 @@ __device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step,
 #pragma unroll
     for (int m = 0; m < 13; ++m) {
         const int i = m % 5 - 2, j = m / 5 - 2;    // j < 0, or j = 0 and i < 0 (+ centre, m = 12)
-        rz[m] = __fdividef(kLog2e, fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
+        rz[m] = kLog2e * rcp_approx(fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
     }
     const float kc = 0.375f * 0.375f;
     AtrousSums a{kc, kc, kc * cp.x, kc * cp.y, kc * kc * cp.z, kc * kc * cp.w};
@@ -512,13 +527,15 @@ __device__ __forceinline__ void var_gauss(const float4 (&v)[3][3], float& gv0, f
 template <dhr_precision P, int kMode>
 __device__ __forceinline__ void atrous_store(const AtrousSums& a, int p, float4* out,
                                              typename Store<P>::Col* col_hist, float* ao_out, float* sh_out) {
-    // (sum w c) / (sum w): a constant neighbourhood stays exactly constant
+    // (sum w c) / (sum w) correctly rounded: a constant neighbourhood stays
+    // exactly constant; the variance (sum w^2 v) / (sum w)^2 needs no such care
     const float c0 = a.sc0 / a.sw0, c1 = a.sc1 / a.sw1;
     if (kMode == 2) {
         ao_out[p] = c0;
         sh_out[p] = c1;
     } else {
-        out[p] = make_float4(c0, c1, a.sv0 / (a.sw0 * a.sw0), a.sv1 / (a.sw1 * a.sw1));
+        const float r0 = rcp_approx(a.sw0), r1 = rcp_approx(a.sw1);
+        out[p] = make_float4(c0, c1, a.sv0 * r0 * r0, a.sv1 * r1 * r1);
         if (kMode == 1) Store<P>::put_col(col_hist, p, make_float2(c0, c1));
     }
 }
