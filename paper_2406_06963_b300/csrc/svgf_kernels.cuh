@@ -245,6 +245,11 @@ __device__ __forceinline__ float w_spatial(const SvgfConsts& k, float zp, float3
     return ex2_approx(fmaf(-fabsf(zp - zq.x), rz, ln));
 }
 
+// A warp with at least this many short-history lanes lets each of them
+// compute its own 7x7 estimate; with fewer, the warp serves them one after
+// another (each a single pass of the whole warp over the 49 taps).
+constexpr int kShortPerLane = 8;
+
 // Temporal step for the 32x8 tile at (bx0, by0), run by a 32x8 block.
 template <dhr_precision P, class Sig>
 __device__ __forceinline__ void temporal_tile(
@@ -321,11 +326,42 @@ __device__ __forceinline__ void temporal_tile(
         hist_out[p] = 0;
     }
     // short history (n < 4): 7x7 spatial estimate of the current frame's
-    // signal weighted by depth and normal only.  The lanes that need it are
-    // served one after another by the whole warp: lane l takes taps l and
-    // l + 32 of the 49, then the sums are reduced across the warp.
+    // signal weighted by depth and normal only.  With few such lanes in the
+    // warp they are served one after another by the whole warp (lane l takes
+    // taps l and l + 32 of the 49, then the sums are reduced across the
+    // warp); with many, each lane sums its own 49 taps.
     const bool need = fg && n < 4;
     unsigned todo = __ballot_sync(kFull, need);
+    if (__popc(todo) >= kShortPerLane) {
+        // many short-history lanes (first frames, large disocclusions): each
+        // computes its own 49 taps, cheaper than one warp pass per lane
+        if (need) {
+            float sw = 0.f, a1 = 0.f, b1 = 0.f, a2 = 0.f, b2 = 0.f;
+            const float3 np = make_float3(zn.y, zn.z, zn.w);
+            for (int dy = -3; dy <= 3; ++dy) {
+                const int qy = y + dy;
+                if (qy < 0 || qy >= k.H) continue;
+#pragma unroll
+                for (int dx = -3; dx <= 3; ++dx) {
+                    const int qx = x + dx;
+                    if (qx < 0 || qx >= k.W) continue;
+                    const int q = qy * k.W + qx;
+                    const float4 zq = S::g(g_cur, q);
+                    const float2 sq = sig(q);
+                    if (!is_fg(zq.x)) continue;
+                    const float w = w_spatial(k, zn.x, np, gz, dx, dy, zq);
+                    sw += w;
+                    a1 = fmaf(w, sq.x, a1);
+                    b1 = fmaf(w, sq.y, b1);
+                    a2 = fmaf(w, sq.x * sq.x, a2);
+                    b2 = fmaf(w, sq.y * sq.y, b2);
+                }
+            }
+            const float m1x = a1 / sw, m1y = b1 / sw;
+            illum[p] = make_float4(m1x, m1y, fmaxf(0.f, a2 / sw - m1x * m1x), fmaxf(0.f, b2 / sw - m1y * m1y));
+        }
+        return;
+    }
     while (todo) {
         const int src = __ffs(todo) - 1;
         todo &= todo - 1;
