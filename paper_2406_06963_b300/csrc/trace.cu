@@ -12,7 +12,7 @@ namespace {
 // kStats: also count rays, node visits and triangle tests per ray type into
 // stats[0..8] = rays {primary, shadow, AO}, visits {..}, tests {..}.
 template <bool kHalf, bool kStats = false>
-__global__ void __launch_bounds__(128) trace_kernel(SceneView sc, TraceConsts k, void* gbuf_dn,
+__global__ void __launch_bounds__(128, 10) trace_kernel(SceneView sc, TraceConsts k, void* gbuf_dn,
                                                     uint32_t* gbuf_mesh, uint8_t* mask_out,
                                                     uint8_t* ao_out, unsigned long long* stats = nullptr) {
     trace_pixel<kHalf, kStats, false>(sc, k, thread_pixel(), gbuf_dn, gbuf_mesh, mask_out, ao_out, stats);
