@@ -13,6 +13,7 @@ struct dhr_svgf_state {
     uint8_t* hist[2] = {nullptr, nullptr};
     float4* illum = nullptr;    // temporal output
     float4* pp[2] = {nullptr, nullptr};
+    float4* gdec = nullptr;     // FP16 states: the current G-buffer decoded, read by the a-trous levels
     int cur = 0;                // index of the moments/history written last
 };
 
@@ -39,6 +40,7 @@ dhr_status svgf_create(int32_t w, int32_t h, dhr_precision prec, dhr_svgf_state*
     e = e ? e : cudaMalloc((void**)&s->illum, n * 16);
     e = e ? e : cudaMalloc((void**)&s->pp[0], n * 16);
     e = e ? e : cudaMalloc((void**)&s->pp[1], n * 16);
+    if (prec == DHR_FP16) e = e ? e : cudaMalloc((void**)&s->gdec, n * 16);
     e = e ? e : cudaMemset(s->hist[0], 0, n);
     e = e ? e : cudaMemset(s->hist[1], 0, n);
     if (e != cudaSuccess) {
@@ -61,7 +63,17 @@ void svgf_free(dhr_svgf_state* s) {
     cudaFree(s->illum);
     cudaFree(s->pp[0]);
     cudaFree(s->pp[1]);
+    cudaFree(s->gdec);
     delete s;
+}
+
+// FP16 G-buffer element -> float4 (depth, unit normal); background keeps depth +inf, normal 0
+__global__ void gbuf_decode_kernel(int n, const uint2* src, float4* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 v = unpack_gbuf16(src[i]);
+    if (!(v.x < INFINITY)) v = make_float4(v.x, 0.f, 0.f, 0.f);
+    dst[i] = v;
 }
 
 dhr_status check_svgf_params(const dhr_svgf_params* p) {
@@ -101,11 +113,20 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
     }
     const float4* in = s->illum;
     const int nsq = atrous_nsq(prm);
+    if (P == DHR_FP16) {
+        const int n = s->w * s->h;
+        gbuf_decode_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, reinterpret_cast<const uint2*>(gc), s->gdec);
+        DHR_CUDA_TRY(cudaGetLastError());
+    }
     for (int l = 0; l < L; ++l) {
         float4* out = s->pp[l & 1];
         const int step = 1 << l;
         const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-        DHR_TRY(launch_atrous<P>(mode, nsq, st, k, step, gc, in, out, col, ao_out, sh_out));
+        if (P == DHR_FP16)
+            DHR_TRY(launch_atrous<kFP16Decoded>(mode, nsq, st, k, step, s->gdec, in, out,
+                                                reinterpret_cast<__half2*>(col), ao_out, sh_out));
+        else
+            DHR_TRY(launch_atrous<P>(mode, nsq, st, k, step, gc, in, out, col, ao_out, sh_out));
         if (L == 1) {
             // single iteration: it is both the history source and the output
             passthrough_kernel<P><<<(s->w * s->h + 255) / 256, 256, 0, st>>>(s->w * s->h, out, col, ao_out,
@@ -181,14 +202,6 @@ __global__ void gbuf_to16_kernel(int n, const float4* src, uint2* dst) {
     const float4 v = src[i];
     dst[i] = pack_gbuf16(v.x, make_float3(v.y, v.z, v.w));
 }
-__global__ void gbuf_to32_kernel(int n, const uint2* src, float4* dst) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint2 u = src[i];
-    float4 v = unpack_gbuf16(u);
-    if (!(v.x < INFINITY)) v = make_float4(v.x, 0.f, 0.f, 0.f);
-    dst[i] = v;
-}
 }  // namespace
 }  // namespace dhr
 
@@ -205,7 +218,7 @@ extern "C" dhr_status dhr_gbuffer_convert(const dhr_gbuffer* src, dhr_gbuffer* d
         gbuf_to16_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, static_cast<const float4*>(src->depth_normal),
                                                           static_cast<uint2*>(dst->depth_normal));
     else
-        gbuf_to32_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, static_cast<const uint2*>(src->depth_normal),
+        gbuf_decode_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, static_cast<const uint2*>(src->depth_normal),
                                                           static_cast<float4*>(dst->depth_normal));
     DHR_CUDA_TRY(cudaGetLastError());
     if (src->mesh_id != dst->mesh_id)

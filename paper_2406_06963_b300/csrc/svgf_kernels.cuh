@@ -60,6 +60,20 @@ struct Store<DHR_FP16> {
     }
 };
 
+// Internal storage tag for the a-trous levels of an FP16 state: binary16
+// colour history as in FP16, the G-buffer read from a float4 copy decoded
+// once per frame (instead of decoding the octahedral normal at every tap).
+constexpr dhr_precision kFP16Decoded = static_cast<dhr_precision>(0x10);
+
+template <>
+struct Store<kFP16Decoded> {
+    using G = float4;
+    using Col = __half2;
+    using Mom = ushort4;
+    static __device__ __forceinline__ float4 g(const G* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = __float22half2_rn(v); }
+};
+
 struct SvgfConsts {
     int W, H;
     float alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
