@@ -184,9 +184,9 @@ __global__ void pack_kernel(int n, const int2* children, const float4* lo, const
     const int2 ch = children[i];
     const int a = slot_of(ch.x, n), b = slot_of(ch.y, n);
     const float4 la = lo[a], ha = hi[a], lb = lo[b], hb = hi[b];
-    nodes[4 * i + 0] = make_float4(la.x, ha.x, la.y, ha.y);
-    nodes[4 * i + 1] = make_float4(lb.x, hb.x, lb.y, hb.y);
-    nodes[4 * i + 2] = make_float4(la.z, ha.z, lb.z, hb.z);
+    nodes[4 * i + 0] = make_float4(la.x, lb.x, ha.x, hb.x);
+    nodes[4 * i + 1] = make_float4(la.y, lb.y, ha.y, hb.y);
+    nodes[4 * i + 2] = make_float4(la.z, lb.z, ha.z, hb.z);
     nodes[4 * i + 3] = make_float4(__int_as_float(ch.x), __int_as_float(ch.y), 0.0f, 0.0f);
 }
 
@@ -200,9 +200,9 @@ __global__ void single_kernel(const float* v, const uint32_t* idx, const uint32_
     const float lx = fminf(r.a.x, fminf(r.b.x, r.c.x)), hx = fmaxf(r.a.x, fmaxf(r.b.x, r.c.x));
     const float ly = fminf(r.a.y, fminf(r.b.y, r.c.y)), hy = fmaxf(r.a.y, fmaxf(r.b.y, r.c.y));
     const float lz = fminf(r.a.z, fminf(r.b.z, r.c.z)), hz = fmaxf(r.a.z, fmaxf(r.b.z, r.c.z));
-    nodes[0] = make_float4(lx, hx, ly, hy);
-    nodes[1] = make_float4(lx, hx, ly, hy);
-    nodes[2] = make_float4(lz, hz, lz, hz);
+    nodes[0] = make_float4(lx, lx, hx, hx);
+    nodes[1] = make_float4(ly, ly, hy, hy);
+    nodes[2] = make_float4(lz, lz, hz, hz);
     nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
 }
 
@@ -329,9 +329,9 @@ __global__ void ploc_pack_kernel(int n, const int2* children, const float4* nlo,
         }
     }
     const int i = (n - 2) - m;
-    nodes[4 * i + 0] = make_float4(lo[0].x, hi[0].x, lo[0].y, hi[0].y);
-    nodes[4 * i + 1] = make_float4(lo[1].x, hi[1].x, lo[1].y, hi[1].y);
-    nodes[4 * i + 2] = make_float4(lo[0].z, hi[0].z, lo[1].z, hi[1].z);
+    nodes[4 * i + 0] = make_float4(lo[0].x, lo[1].x, hi[0].x, hi[1].x);
+    nodes[4 * i + 1] = make_float4(lo[0].y, lo[1].y, hi[0].y, hi[1].y);
+    nodes[4 * i + 2] = make_float4(lo[0].z, lo[1].z, hi[0].z, hi[1].z);
     nodes[4 * i + 3] = make_float4(__int_as_float(out_ref[0]), __int_as_float(out_ref[1]), 0.0f, 0.0f);
 }
 

@@ -41,10 +41,11 @@ void clear_error();
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // ---------------------------------------------------------------- scene
-// BVH node, 64 bytes: the boxes of both children plus their references.
-//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+// BVH node, 64 bytes: the boxes of both children plus their references,
+// paired by plane so that one f32x2 fma gives both children's distances:
+//   a = (c0.lo.x, c1.lo.x, c0.hi.x, c1.hi.x)
+//   b = (c0.lo.y, c1.lo.y, c0.hi.y, c1.hi.y)
+//   c = (c0.lo.z, c1.lo.z, c0.hi.z, c1.hi.z)
 //   d = (child0, child1, -, -) as int bits; >= 0 internal node, < 0 leaf ~i
 // Leaf i holds sorted triangle i: 3 float4 (v0, orig index bits),
 // (v1, mesh id bits), (v2, 0).

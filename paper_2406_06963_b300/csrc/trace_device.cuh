@@ -31,11 +31,28 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 }
 __device__ __forceinline__ float comp(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
 
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+// (a0 b0 + c0, a1 b1 + c1), each rounded once
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Per-ray constants of the watertight test and of the slab test.
 struct Ray {
     float3 o, d;
-    float3 idir;       // 1 / d (tiny components clamped away from zero)
-    float3 oidir;      // o / d
+    unsigned long long idir2[3];   // per axis (1/d, 1/d), packed for f32x2 (tiny d clamped away from zero)
+    unsigned long long noid2[3];   // per axis (-o/d, -o/d)
     int kx, ky, kz;
     float sx, sy, sz;
 };
@@ -48,8 +65,14 @@ __device__ __forceinline__ Ray make_ray(float3 o, float3 d) {
     const float dx = fabsf(d.x) > eps ? d.x : copysignf(eps, d.x);
     const float dy = fabsf(d.y) > eps ? d.y : copysignf(eps, d.y);
     const float dz = fabsf(d.z) > eps ? d.z : copysignf(eps, d.z);
-    r.idir = make_float3(1.0f / dx, 1.0f / dy, 1.0f / dz);
-    r.oidir = make_float3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+    const float3 idir = make_float3(1.0f / dx, 1.0f / dy, 1.0f / dz);
+    const float3 oidir = make_float3(o.x * idir.x, o.y * idir.y, o.z * idir.z);
+    r.idir2[0] = pack2(idir.x, idir.x);
+    r.idir2[1] = pack2(idir.y, idir.y);
+    r.idir2[2] = pack2(idir.z, idir.z);
+    r.noid2[0] = pack2(-oidir.x, -oidir.x);
+    r.noid2[1] = pack2(-oidir.y, -oidir.y);
+    r.noid2[2] = pack2(-oidir.z, -oidir.z);
     const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     r.kx = r.kz == 2 ? 0 : r.kz + 1;
@@ -107,15 +130,25 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
     return r;
 }
 
-__device__ __forceinline__ void slab(const Ray& r, float lox, float hix, float loy, float hiy, float loz,
-                                     float hiz, float tmin, float tmax, float& enter, bool& hit) {
-    const float x0 = fmaf(lox, r.idir.x, -r.oidir.x), x1 = fmaf(hix, r.idir.x, -r.oidir.x);
-    const float y0 = fmaf(loy, r.idir.y, -r.oidir.y), y1 = fmaf(hiy, r.idir.y, -r.oidir.y);
-    const float z0 = fmaf(loz, r.idir.z, -r.oidir.z), z1 = fmaf(hiz, r.idir.z, -r.oidir.z);
-    const float tn = max3(fminf(x0, x1), fminf(y0, y1), fmaxf(fminf(z0, z1), tmin));
-    const float tf = min3(fmaxf(x0, x1), fmaxf(y0, y1), fminf(fmaxf(z0, z1), tmax));
-    enter = tn;
-    hit = tn <= tf * 1.00000024f;   // 1 + 2 gamma(3) with unit roundoff 2^-24
+// Slab tests of a node's two child boxes (node layout in common.cuh): the
+// distances to both children's planes of an axis come from one f32x2 fma
+// (each lane rounded once, as a scalar fma), then per child
+// tn = max(near planes, tmin), tf = min(far planes, tmax); the exit distance
+// is scaled by 1 + 2 gamma(3) (unit roundoff 2^-24) so that rounding never
+// culls a box the ray touches.
+__device__ __forceinline__ void slab2(const Ray& r, ulonglong2 ax, ulonglong2 ay, ulonglong2 az, float tmin,
+                                      float tmax, float& e0, bool& h0, float& e1, bool& h1) {
+    const float2 lx = unpack2(fma2(ax.x, r.idir2[0], r.noid2[0])), hx = unpack2(fma2(ax.y, r.idir2[0], r.noid2[0]));
+    const float2 ly = unpack2(fma2(ay.x, r.idir2[1], r.noid2[1])), hy = unpack2(fma2(ay.y, r.idir2[1], r.noid2[1]));
+    const float2 lz = unpack2(fma2(az.x, r.idir2[2], r.noid2[2])), hz = unpack2(fma2(az.y, r.idir2[2], r.noid2[2]));
+    const float tn0 = max3(fminf(lx.x, hx.x), fminf(ly.x, hy.x), fmaxf(fminf(lz.x, hz.x), tmin));
+    const float tf0 = min3(fmaxf(lx.x, hx.x), fmaxf(ly.x, hy.x), fminf(fmaxf(lz.x, hz.x), tmax));
+    const float tn1 = max3(fminf(lx.y, hx.y), fminf(ly.y, hy.y), fmaxf(fminf(lz.y, hz.y), tmin));
+    const float tf1 = min3(fmaxf(lx.y, hx.y), fmaxf(ly.y, hy.y), fminf(fmaxf(lz.y, hz.y), tmax));
+    e0 = tn0;
+    e1 = tn1;
+    h0 = tn0 <= tf0 * 1.00000024f;
+    h1 = tn1 <= tf1 * 1.00000024f;
 }
 
 // Closest hit (any_hit = false) or first hit (true) with tmin < t < tmax.
@@ -143,12 +176,12 @@ __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tm
     for (uint32_t guard = 0; guard < kMaxSteps; ++guard) {
         if (node >= 0) {
             if (kStats) ++work->visits;
-            const float4* nd = sc.nodes + 4 * node;
-            const float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), d = __ldg(nd + 3);
+            const ulonglong2* nd = reinterpret_cast<const ulonglong2*>(sc.nodes + 4 * node);
+            const ulonglong2 ax = __ldg(nd), ay = __ldg(nd + 1), az = __ldg(nd + 2);
+            const float4 d = __ldg(sc.nodes + 4 * node + 3);
             float e0, e1;
             bool h0, h1;
-            slab(r, a.x, a.y, a.z, a.w, c.x, c.y, tmin, tmax, e0, h0);
-            slab(r, b.x, b.y, b.z, b.w, c.z, c.w, tmin, tmax, e1, h1);
+            slab2(r, ax, ay, az, tmin, tmax, e0, h0, e1, h1);
             int c0 = __float_as_int(d.x), c1 = __float_as_int(d.y);
             if (h0 && h1) {
                 if (e1 < e0) {
