@@ -532,7 +532,9 @@ __device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step,
         rz[m] = kLog2e * rcp_approx(fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
     }
     const float kc = 0.375f * 0.375f;
-    AtrousSums a{kc, kc, kc * cp.x, kc * cp.y, kc * kc * cp.z, kc * kc * cp.w};
+    // the two channels' sums (w, w c, w^2 var) as f32x2 pairs
+    unsigned long long sw = pack2(kc, kc), sc = pack2(kc * cp.x, kc * cp.y);
+    unsigned long long sv = pack2(kc * kc * cp.z, kc * kc * cp.w);
     // log2 of the B3-spline taps 1/16, 1/4, 3/8, 1/4, 1/16
     const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
 #pragma unroll
@@ -546,17 +548,15 @@ __device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step,
             float e = fmaf(-fabsf(zn.x - zq.x), rz[m], l5[i + 2] + l5[j + 2]);
             e += log2_normal<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
             e = fg_var(cq.z) ? e : -INFINITY;
-            const float w0 = ex2_approx(fmaf(-fabsf(cp.x - cq.x), il0, e));
-            const float w1 = ex2_approx(fmaf(-fabsf(cp.y - cq.y), il1, e));
-            a.sw0 += w0;
-            a.sw1 += w1;
-            a.sc0 = fmaf(w0, cq.x, a.sc0);
-            a.sc1 = fmaf(w1, cq.y, a.sc1);
-            a.sv0 = fmaf(w0 * w0, cq.z, a.sv0);
-            a.sv1 = fmaf(w1 * w1, cq.w, a.sv1);
+            const unsigned long long w = pack2(ex2_approx(fmaf(-fabsf(cp.x - cq.x), il0, e)),
+                                               ex2_approx(fmaf(-fabsf(cp.y - cq.y), il1, e)));
+            sw = add2(sw, w);
+            sc = fma2(w, pack2(cq.x, cq.y), sc);
+            sv = fma2(mul2(w, w), pack2(cq.z, cq.w), sv);
         }
     }
-    return a;
+    const float2 w = unpack2(sw), c = unpack2(sc), v = unpack2(sv);
+    return AtrousSums{w.x, w.y, c.x, c.y, v.x, v.y};
 }
 
 // 3x3 Gaussian of the variance, renormalised over foreground taps; v[dy][dx]
