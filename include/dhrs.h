@@ -320,6 +320,26 @@ dhr_status dhr_step_frame(dhr_session* session, const dhr_camera* cam, uint32_t 
 dhr_status dhr_step_frame_host(dhr_session* session, const dhr_camera* cam, uint32_t frame,
                                float* ao_host, float* shadow_host, void* stream);
 
+/* Streaming host output.  Enqueues the frame (trace + reconstruct on
+ * `stream`, into one of two session-owned device output buffers) and the
+ * copy of its filtered AO and shadow into ao_host / shadow_host (float
+ * [W*H] each) on the session's own copy stream, then returns without
+ * waiting: the copy of frame N runs while frame N + 1 is traced.  The host
+ * buffers must be pinned (page-locked; pageable memory makes the copy
+ * synchronous) and must stay untouched until dhr_session_wait has returned
+ * for the frame's ticket.  *out_ticket receives an increasing id (1, 2, ...).
+ * A frame's device output buffer is reused two frames later; the library
+ * orders that reuse after the earlier copy on the device.  Errors as
+ * dhr_step_frame; DHR_ERR_CUDA if an enqueue fails. */
+dhr_status dhr_step_frame_host_async(dhr_session* session, const dhr_camera* cam, uint32_t frame,
+                                     float* ao_host, float* shadow_host, void* stream,
+                                     uint64_t* out_ticket);
+
+/* Blocks until the host copy of `ticket` has completed (if later frames
+ * were enqueued since, it may also wait for their copies).  ticket 0 or a
+ * ticket not issued yet: DHR_ERR_INVALID. */
+dhr_status dhr_session_wait(dhr_session* session, uint64_t ticket);
+
 /* Device views of the session's current G-buffer and raw trace outputs. */
 dhr_status dhr_session_get_frame(dhr_session* session, dhr_gbuffer* gbuf,
                                  uint8_t** shadow_mask, uint8_t** ao_count);

@@ -110,6 +110,8 @@ _SIGNATURES = {
     "dhr_session_destroy": ([_P], None),
     "dhr_step_frame": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
     "dhr_step_frame_host": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
+    "dhr_step_frame_host_async": ([_P, _P, C.c_uint32, _P, _P, _P, _P], C.c_int),
+    "dhr_session_wait": ([_P, C.c_uint64], C.c_int),
     "dhr_session_get_frame": ([_P, _P, _P, _P], C.c_int),
     "dhr_session_reset": ([_P], C.c_int),
 }
@@ -422,6 +424,19 @@ class Session:
         c = camera(cam)
         _check(lib().dhr_step_frame_host(self.h, C.byref(c), frame, C.c_void_p(ao_host.data_ptr()),
                                          C.c_void_p(sh_host.data_ptr()), _stream(stream)))
+
+    def step_host_async(self, cam, frame, ao_host, sh_host, stream=None) -> int:
+        """Streaming host-output step: enqueues the frame and the copy of its
+        results into ao_host / sh_host (pinned CPU tensors) and returns a
+        ticket; the tensors are valid after wait(ticket)."""
+        c = camera(cam)
+        t = C.c_uint64()
+        _check(lib().dhr_step_frame_host_async(self.h, C.byref(c), frame, C.c_void_p(ao_host.data_ptr()),
+                                               C.c_void_p(sh_host.data_ptr()), _stream(stream), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int):
+        _check(lib().dhr_session_wait(self.h, C.c_uint64(ticket)))
 
     def frame_buffers(self) -> dict:
         g = GBufferC()

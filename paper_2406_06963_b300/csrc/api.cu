@@ -134,6 +134,10 @@ struct dhr_session {
     uint8_t* mask = nullptr;
     uint8_t* ao = nullptr;
     float* out = nullptr;         // [2][W*H]: filtered AO, filtered shadow
+    float* out_b = nullptr;       // second output buffer of the streaming host path
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    uint64_t tickets = 0;         // streaming frames issued
     dhr_svgf_state* svgf = nullptr;
     dhr_camera cam_prev{};
     bool has_prev = false;
@@ -142,6 +146,13 @@ struct dhr_session {
 
 extern "C" void dhr_session_destroy(dhr_session* s) {
     if (!s) return;
+    if (s->copy_st) cudaStreamSynchronize(s->copy_st);
+    for (int i = 0; i < 2; ++i) {
+        if (s->computed[i]) cudaEventDestroy(s->computed[i]);
+        if (s->copied[i]) cudaEventDestroy(s->copied[i]);
+    }
+    if (s->copy_st) cudaStreamDestroy(s->copy_st);
+    cudaFree(s->out_b);
     for (int i = 0; i < 2; ++i) {
         cudaFree(s->gdn[i]);
         cudaFree(s->gmesh[i]);
@@ -179,6 +190,12 @@ extern "C" dhr_status dhr_session_create(const dhr_scene* scene, int32_t width, 
     if (!e) e = cudaMalloc((void**)&s->mask, n);
     if (!e) e = cudaMalloc((void**)&s->ao, n);
     if (!e) e = cudaMalloc((void**)&s->out, 2 * n * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&s->out_b, 2 * n * sizeof(float));
+    if (!e) e = cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && !e; ++i) {
+        e = cudaEventCreateWithFlags(&s->computed[i], cudaEventDisableTiming);
+        if (!e) e = cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming);
+    }
     if (e) {
         cudaGetLastError();
         dhr_session_destroy(s);
@@ -221,6 +238,8 @@ extern "C" dhr_status dhr_step_frame(dhr_session* s, const dhr_camera* cam, uint
     const size_t n = (size_t)s->w * s->h;
     float* ao = ao_out ? ao_out : s->out;
     float* sh = shadow_out ? shadow_out : s->out + n;
+    // the session's own output buffer may still be read by a streaming copy
+    if (!ao_out || !shadow_out) DHR_CUDA_TRY(cudaStreamWaitEvent(st, s->copied[0], 0));
     DHR_TRY(svgf_run(s->svgf, &g, s->has_prev ? &gp : nullptr, cam, s->has_prev ? &s->cam_prev : nullptr,
                      s->mask, s->ao, &s->sp, ao, sh, st));
     s->cur = cur;
@@ -238,6 +257,36 @@ extern "C" dhr_status dhr_step_frame_host(dhr_session* s, const dhr_camera* cam,
     DHR_CUDA_TRY(cudaMemcpyAsync(ao_host, s->out, n * sizeof(float), cudaMemcpyDeviceToHost, st));
     DHR_CUDA_TRY(cudaMemcpyAsync(shadow_host, s->out + n, n * sizeof(float), cudaMemcpyDeviceToHost, st));
     DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_step_frame_host_async(dhr_session* s, const dhr_camera* cam, uint32_t frame,
+                                                float* ao_host, float* shadow_host, void* stream,
+                                                uint64_t* out_ticket) {
+    DHR_CHECK_ARG(s && ao_host && shadow_host && out_ticket, "step_frame_host_async: null pointer");
+    cudaStream_t st = as_stream(stream);
+    const size_t n = (size_t)s->w * s->h;
+    const int slot = (int)(s->tickets & 1);
+    float* dev = slot ? s->out_b : s->out;
+    // the copy of the frame that last used this output buffer reads it: wait on the device
+    DHR_CUDA_TRY(cudaStreamWaitEvent(st, s->copied[slot], 0));
+    DHR_TRY(dhr_step_frame(s, cam, frame, dev, dev + n, stream));
+    DHR_CUDA_TRY(cudaEventRecord(s->computed[slot], st));
+    DHR_CUDA_TRY(cudaStreamWaitEvent(s->copy_st, s->computed[slot], 0));
+    DHR_CUDA_TRY(cudaMemcpyAsync(ao_host, dev, n * sizeof(float), cudaMemcpyDeviceToHost, s->copy_st));
+    DHR_CUDA_TRY(cudaMemcpyAsync(shadow_host, dev + n, n * sizeof(float), cudaMemcpyDeviceToHost, s->copy_st));
+    DHR_CUDA_TRY(cudaEventRecord(s->copied[slot], s->copy_st));
+    *out_ticket = ++s->tickets;
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_session_wait(dhr_session* s, uint64_t ticket) {
+    clear_error();
+    DHR_CHECK_ARG(s, "session_wait: null session");
+    DHR_CHECK_ARG(ticket >= 1 && ticket <= s->tickets, "session_wait: ticket %llu not issued (last %llu)",
+                  (unsigned long long)ticket, (unsigned long long)s->tickets);
+    // ticket t used output slot (t - 1) & 1; that slot's event is the copy of t or of a later frame
+    DHR_CUDA_TRY(cudaEventSynchronize(s->copied[(ticket - 1) & 1]));
     return DHR_OK;
 }
 

@@ -58,3 +58,40 @@ def test_session_reset_drops_history():
     torch.cuda.synchronize()
     assert torch.equal(o1, o3)
     assert not torch.equal(o1, o2)
+
+
+def test_streaming_host_output_equals_synchronous():
+    """dhr_step_frame_host_async with two alternating pinned buffers returns,
+    after dhr_session_wait, exactly what the synchronous host path returns;
+    tickets increase and an unissued ticket is rejected."""
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    W, H = 160, 96
+    cams = wl.orbit_path(6, W, H, degrees=6.0)
+    ref = dhrs.Session(sc, W, H)
+    a_ref = [torch.empty((H, W), pin_memory=True) for _ in cams]
+    s_ref = [torch.empty((H, W), pin_memory=True) for _ in cams]
+    for f, cam in enumerate(cams):
+        ref.step_host(cam, f, a_ref[f], s_ref[f])
+    sess = dhrs.Session(sc, W, H)
+    bufs = [(torch.empty((H, W), pin_memory=True), torch.empty((H, W), pin_memory=True)) for _ in range(2)]
+    prev = None
+    for f, cam in enumerate(cams):
+        ab, sb = bufs[f & 1]
+        t = sess.step_host_async(cam, f, ab, sb)
+        assert t == f + 1
+        if prev is not None:
+            pf, pt = prev
+            sess.wait(pt)
+            pa, ps = bufs[pf & 1]
+            assert torch.equal(pa, a_ref[pf]) and torch.equal(ps, s_ref[pf]), pf
+        prev = (f, t)
+    sess.wait(prev[1])
+    pa, ps = bufs[prev[0] & 1]
+    assert torch.equal(pa, a_ref[prev[0]]) and torch.equal(ps, s_ref[prev[0]])
+    with pytest.raises(dhrs.DhrError):
+        sess.wait(prev[1] + 1)
+    # the synchronous path on the same session still works after streaming
+    a2, s2 = torch.empty((H, W), pin_memory=True), torch.empty((H, W), pin_memory=True)
+    sess.step_host(cams[0], 99, a2, s2)
+    assert bool(torch.isfinite(a2).all())
