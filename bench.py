@@ -301,7 +301,12 @@ def run_ours(args):
     return res if rank == 0 else None
 
 
-def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30):
+# pixel cap of one serving batch (dhr_server_set_max_batch_pixels; 0 = none;
+# the library default is 2^21)
+SERVE_BATCH_PX = int(os.environ.get("DHR_SERVE_BATCH_PX", str(2 << 20)))
+
+
+def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30, max_batch_px=SERVE_BATCH_PX):
     """32 thin-client sessions, resolutions drawn from {640x360, 1280x720,
     1920x1080, 2560x1440}, each sending camera poses as a 60 Hz Poisson
     process along its own seeded spline, with a network delay U[0, 200] ms
@@ -315,6 +320,7 @@ def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30):
     r = wl.rng_for(4)
     sizes = [(640, 360), (1280, 720), (1920, 1080), (2560, 1440)]
     srv = dhrs.Server(sc, budget)
+    srv.set_max_batch_pixels(max_batch_px)
     n_poses = int((seconds + 0.3) * 60) + 2
     events, refused, admitted, px_of = [], 0, 0, {}
     for k in range(n_sessions):
@@ -371,6 +377,7 @@ def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30):
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "frames_per_s": round(len(lat) / wall, 1), "mpx_per_s": round(done_px / wall / 1e6, 1),
             "mean_batch": round(float(np.mean(batches)), 2), "batches": int(st["batches"]),
+            "max_batch_pixels": max_batch_px,
             "device_bytes": int(st["used_bytes"]) if st["open_sessions"] else None, "seconds": round(wall, 3)}
 
 

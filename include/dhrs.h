@@ -418,6 +418,14 @@ dhr_status dhr_server_submit(dhr_server* server, int32_t session, const dhr_came
                              const dhr_camera* cam_target, uint32_t frame, uint64_t t_arrival_ns,
                              uint64_t request_id);
 
+/* Caps the pixels of one batch: a batch takes sessions in request order
+ * until the next would push it past max_pixels (it always takes at least
+ * one).  Smaller batches finish sooner, so a request waits less behind the
+ * batch in flight.  Default 2^21 pixels (about one 1920x1080 frame);
+ * 0 = no cap (all ready sessions, up to 64).
+ * Errors: DHR_ERR_INVALID for a null server. */
+dhr_status dhr_server_set_max_batch_pixels(dhr_server* server, uint64_t max_pixels);
+
 /* Collects finished batches, then launches one batch if a slot is free:
  * at most one queued request per session without a frame in flight.
  * *launched = number of requests launched (0 if none).  Non-blocking. */

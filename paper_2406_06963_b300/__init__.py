@@ -102,6 +102,7 @@ _SIGNATURES = {
     "dhr_server_open": ([_P, C.c_int32, C.c_int32, _P], C.c_int),
     "dhr_server_close": ([_P, C.c_int32], C.c_int),
     "dhr_server_submit": ([_P, C.c_int32, _P, _P, C.c_uint32, C.c_uint64, C.c_uint64], C.c_int),
+    "dhr_server_set_max_batch_pixels": ([_P, C.c_uint64], C.c_int),
     "dhr_server_pump": ([_P, _P], C.c_int),
     "dhr_server_poll": ([_P, _P, C.c_int32, _P, C.c_int32], C.c_int),
     "dhr_server_output": ([_P, C.c_int32, _P, _P], C.c_int),
@@ -603,6 +604,10 @@ class Server:
         ct = camera(cam_target) if cam_target is not None else None
         _check(lib().dhr_server_submit(self.h, sid, C.byref(c), C.byref(ct) if ct else None, frame,
                                        int(t_arrival_ns), int(request_id)))
+
+    def set_max_batch_pixels(self, max_pixels: int):
+        """Pixel cap of one batch (0: none)."""
+        _check(lib().dhr_server_set_max_batch_pixels(self.h, C.c_uint64(max_pixels)))
 
     def pump(self) -> int:
         n = C.c_int32()

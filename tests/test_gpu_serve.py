@@ -145,3 +145,28 @@ def test_server_delay_warp_equals_components():
         torch.cuda.synchronize()
         assert torch.equal(ga, oa) and torch.equal(gb, ob), f
         assert float((ga == 1).float().mean()) < 0.9
+
+
+def test_server_batch_pixel_cap():
+    """A batch takes sessions in request order until the next would pass the
+    pixel cap (at least one); cap 0 takes every ready session."""
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    W = H = 1024
+    path = wl.orbit_path(2, W, H)
+    for cap, expect in ((2 * W * H, [2, 1]), (W * H - 1, [1, 1]), (0, [3])):
+        srv = dhrs.Server(sc, 8 << 30)
+        srv.set_max_batch_pixels(cap)
+        ids = [srv.open(W, H) for _ in range(3)]
+        for k, sid in enumerate(ids):
+            srv.submit(sid, path[0], 0, dhrs.now_ns(), k)
+        launched = [srv.pump(), srv.pump()]
+        assert [n for n in launched if n] == expect[:2], (cap, launched)
+        done = []
+        while len(done) < 3:
+            done += srv.poll(wait=True)
+            if len(done) < 3:
+                n = srv.pump()
+                assert n in (0, 1)
+        assert sum(1 for d in done if not d["dropped"]) == 3
+        assert max(d["batch_size"] for d in done) == max(expect)
