@@ -510,7 +510,9 @@ struct TapsGlobal {
 // for channel c, h_i h_j w_n w_z w_l,c, is evaluated as one power of two,
 //   2^(log2(h_i h_j) + sigma_n log2(n.n_q) - |dz| rz - |dc| il_c)
 // (rz and il_c carry log2(e)): one lg2 per tap and one ex2 per channel.
-// Background taps (variance sentinel -1) get exponent -inf, i.e. weight 0.
+// Background taps (depth +inf, outside the image staged likewise) get
+// |dz| rz = +inf, so exponent -inf and weight exactly 0; their illum holds
+// the finite sentinel (1, 1, -1, -1), so the sums stay unchanged.
 struct AtrousSums {
     float sw0, sw1, sc0, sc1, sv0, sv1;
 };
@@ -547,7 +549,6 @@ __device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step,
             const int m = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
             float e = fmaf(-fabsf(zn.x - zq.x), rz[m], l5[i + 2] + l5[j + 2]);
             e += log2_normal<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
-            e = fg_var(cq.z) ? e : -INFINITY;
             const unsigned long long w = pack2(ex2_approx(fmaf(-fabsf(cp.x - cq.x), il0, e)),
                                                ex2_approx(fmaf(-fabsf(cp.y - cq.y), il1, e)));
             sw = add2(sw, w);
