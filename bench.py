@@ -293,6 +293,7 @@ def run_ours(args):
         res["serving"] = run_serving(sc, scene_d, seconds=args.serve_seconds)
         res["precision_form"] = run_precision_form(sc, scene_d)
         res["adjoint"] = run_adjoint(sc, scene_d)
+        res["denoise_variants"] = run_denoise_variants(sc, scene_d)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(scene_d, cams, sample_px=args.cpu_pixels)
     if ws > 1:
@@ -471,12 +472,17 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
             "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.exp()]}
 
 
-def cpu_baseline(scene_d, cams, sample_px=1024, seed=7):
+def cpu_baseline(scene_d, cams, sample_px=4096, seed=7):
     """The oracle as it stands (brute force over all triangles, fp64, OpenMP
-    on every host core) on a bounded sample of the same workload."""
+    on every host core) on a bounded sample of the same workload: primary,
+    shadow and AO rays of `sample_px` seeded pixels of frame 0, and the
+    full-frame SVGF at 1920x1080 (second frame, warm history) on G-buffers the
+    oracle traces from the 194-triangle box scene (a brute-force trace of the
+    776k-triangle frame would take hours)."""
     import numpy as np
 
     import oracle as orc
+    import workloads as wl
     S = orc.Scene(scene_d)
     r = np.random.default_rng(seed)
     pix = np.stack([r.integers(0, W, sample_px), r.integers(0, H, sample_px)], -1)
@@ -485,10 +491,74 @@ def cpu_baseline(scene_d, cams, sample_px=1024, seed=7):
     dt = time.perf_counter() - t0
     fg = int((tr["mesh"] != 0xFFFFFFFF).sum())
     n_rays = sample_px + 2 * fg
+    B = orc.Scene(wl.scene_boxes())
+    bc = wl.orbit_path(2, W, H, degrees=2.0)
+    st = orc.SvgfState(W, H)
+    svgf_s = 0.0
+    for f, cam in enumerate(bc):
+        t = orc.trace(B, cam, orc.TraceParams(frame=f))
+        zn, mesh = orc.gbuffer_f32(t, W, H)
+        t1 = time.perf_counter()
+        st.frame(zn, mesh, cam, t["shadow_mask"].reshape(H, W), t["ao_count"].reshape(H, W), orc.SvgfParams())
+        svgf_s = time.perf_counter() - t1
     return {"value": round(n_rays / dt / 1e6, 6), "unit": "Mrays/s", "cores": orc.num_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "ns_per_ray": round(dt / n_rays * 1e9, 1),
+            "svgf_ms_per_frame_1080p": round(svgf_s * 1e3, 1),
             "sample": f"{sample_px} seeded pixels of frame 0 (primary + shadow + AO rays, "
-                      f"{n_rays} rays, {dt:.1f} s) of the 1920x1080 776,050-triangle workload"}
+                      f"{n_rays} rays, {dt:.1f} s) of the 1920x1080 776,050-triangle workload; "
+                      f"SVGF: one full 1920x1080 frame with history (box-scene G-buffers)"}
+
+
+def run_denoise_variants(sc, scene_d, frames=12, W=1280, H=720, levels=(0, 1, 2, 5)):
+    """Lightweight denoiser variants: the same noisy 1-spp frames filtered
+    with 0, 1, 2 and 5 a-trous levels; error of the filtered AO of the last
+    4 frames against a 255-spp AO reference, and SVGF time per frame."""
+    import numpy as np
+    import torch
+
+    import paper_2406_06963_b300 as dhrs
+    import workloads as wl
+    cams = wl.spline_path(scene_d["terrain"], N_FRAMES, W, H)[:frames]
+    gbufs, masks, aos, refs = [], [], [], []
+    for f, cam in enumerate(cams):
+        g = dhrs.GBuffer(W, H)
+        m = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+        a = torch.empty_like(m)
+        dhrs.trace_visibility(sc, cam, dhrs.TraceParams(ao_spp=1, frame=f), g, m, a)
+        g2 = dhrs.GBuffer(W, H)
+        a2 = torch.empty_like(m)
+        dhrs.trace_visibility(sc, cam, dhrs.TraceParams(ao_spp=255, frame=f), g2, m.clone(), a2)
+        gbufs.append(g)
+        masks.append(m)
+        aos.append(a)
+        refs.append(a2.float() / 255.0)
+    out = {}
+    ao = torch.empty((H, W), device="cuda")
+    sh = torch.empty_like(ao)
+    for L in levels:
+        p = dhrs.SvgfParams(ao_spp=1, levels=L)
+        st = dhrs.SvgfState(W, H)
+        errs, ms = [], []
+        for f, cam in enumerate(cams):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st.reconstruct(gbufs[f], gbufs[f - 1] if f else None, cam, cams[f - 1] if f else None, masks[f],
+                           aos[f], p, ao, sh)
+            e1.record()
+            torch.cuda.synchronize()
+            if f >= frames - 4:
+                fg = torch.isfinite(gbufs[f].depth_normal[..., 0])
+                d = (ao - refs[f])[fg]
+                errs.append((float((d * d).mean()), float(d.abs().mean())))
+                ms.append(e0.elapsed_time(e1))
+        out[f"levels_{L}"] = {"ao_rmse": round(float(np.sqrt(np.mean([e[0] for e in errs]))), 5),
+                              "ao_mean_abs": round(float(np.mean([e[1] for e in errs])), 5),
+                              "svgf_ms": round(float(np.median(ms)), 4)}
+    noisy = [float(((aos[f].float() - refs[f])[torch.isfinite(gbufs[f].depth_normal[..., 0])] ** 2).mean())
+             for f in range(frames - 4, frames)]
+    out["noisy_1spp_ao_rmse"] = round(float(np.sqrt(np.mean(noisy))), 5)
+    out["workload"] = f"{frames} frames x {W}x{H}, terrain776k, 1 spp, reference 255 spp, last 4 frames"
+    return out
 
 
 def run_reference(args):
@@ -539,7 +609,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the serving, FP16 and adjoint measurements")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--cpu-pixels", type=int, default=1024)
+    ap.add_argument("--cpu-pixels", type=int, default=4096)
     ap.add_argument("--ref-pixels", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:
