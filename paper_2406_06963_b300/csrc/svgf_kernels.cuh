@@ -418,7 +418,7 @@ __device__ __forceinline__ void temporal_tile(
 }
 
 template <dhr_precision P, class Sig>
-__global__ void __launch_bounds__(256) temporal_kernel(
+__global__ void __launch_bounds__(256, 5) temporal_kernel(
     SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const typename Store<P>::G* g_cur,
     const uint32_t* mesh_cur, const typename Store<P>::G* g_prev, const uint32_t* mesh_prev,
     Sig sig, const typename Store<P>::Col* col_hist,
