@@ -74,6 +74,19 @@ def _traffic(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
+def _ncu_field(kernel: str, field: str):
+    """Another figure of the committed capture of `kernel` (None when the
+    kernel's sources changed since)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            e = json.load(f).get(kernel)
+    except OSError:
+        return None
+    if not e or e.get("csrc_sha") != csrc_hash(kernel):
+        return None
+    return e.get(field)
+
+
 def _svgf_traffic():
     """DRAM bytes of one frame's SVGF (temporal + 5 a-trous launches) from the
     committed captures, or None when either kernel changed since."""
@@ -277,7 +290,12 @@ def run_ours(args):
         "roofline": {"kernel": "trace_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(alu_peak, 2), "unit": "Tops/s (fp32 lane ops)",
                      "frac": round(achieved / alu_peak, 4), "traffic": _traffic("trace_kernel"),
-                     "peak_source": "148 SMs x 128 fp32 lanes x max SM clock (%s)" % peak_src},
+                     "peak_source": "148 SMs x 128 fp32 lanes x max SM clock (%s)" % peak_src,
+                     # the limiters ncu measures for this kernel (committed capture):
+                     # instruction issue and the L1/tex pipe (node fetches, local stack)
+                     "ncu_issue_active_pct": _ncu_field("trace_kernel", "issue_active_pct"),
+                     "ncu_l1tex_throughput_pct": _ncu_field("trace_kernel", "l1tex_throughput_pct"),
+                     "ncu_l2_throughput_pct": _ncu_field("trace_kernel", "lts_throughput_pct")},
         "roofline_svgf": {"bound": "hbm", "achieved": round(svgf_gbs, 1), "peak": peaks["hbm_gbs"],
                           "unit": "GB/s", "frac": round(svgf_gbs / peaks["hbm_gbs"], 4),
                           "algorithmic_bytes_per_px": 340, "peak_source": peak_src,
