@@ -133,6 +133,10 @@ typedef struct {
     uint32_t levels;      /* a-trous iterations, 0..8 (step 2^i) */
     uint32_t fixed_alpha; /* 1: effective alpha = alpha once history exists */
     uint32_t wl_in_atrous;/* 1: luminance term in the a-trous weights */
+    uint32_t shadow_light;/* which light's visibility bit (0..DHR_MAX_LIGHTS-1) is the
+                             shadow channel filtered from a u8 bitmask; one SVGF state
+                             per light gives every light's filtered shadow.  Unused by
+                             the differentiable form (real-valued planes). */
 } dhr_svgf_params;
 
 typedef struct dhr_svgf_state dhr_svgf_state;

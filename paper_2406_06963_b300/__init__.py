@@ -65,7 +65,7 @@ class SvgfParamsC(C.Structure):
     _fields_ = [("alpha", C.c_float), ("sigma_z", C.c_float), ("sigma_n", C.c_float),
                 ("sigma_l", C.c_float), ("eps_z", C.c_float), ("eps_l", C.c_float),
                 ("ao_spp", C.c_uint32), ("levels", C.c_uint32), ("fixed_alpha", C.c_uint32),
-                ("wl_in_atrous", C.c_uint32)]
+                ("wl_in_atrous", C.c_uint32), ("shadow_light", C.c_uint32)]
 
 
 class SvgfBuffersC(C.Structure):
@@ -208,11 +208,12 @@ class SvgfParams:
     levels: int = 5
     fixed_alpha: bool = False
     wl_in_atrous: bool = True
+    shadow_light: int = 0
 
     def to_c(self) -> SvgfParamsC:
         return SvgfParamsC(self.alpha, self.sigma_z, self.sigma_n, self.sigma_l, self.eps_z,
                            self.eps_l, self.ao_spp, self.levels, int(self.fixed_alpha),
-                           int(self.wl_in_atrous))
+                           int(self.wl_in_atrous), int(self.shadow_light))
 
 
 # --------------------------------------------------------------- G-buffer

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) serve_temporal_kernel(const BatchTable* t
         temporal_tile<DHR_FP32, SigCounts>(it.sk, it.tk.cam, it.has_prev ? it.cam_prev : it.tk.cam, it.g_cur,
                                            it.m_cur, it.has_prev ? it.g_prev : nullptr,
                                            it.has_prev ? it.m_prev : nullptr,
-                                           SigCounts{it.mask, it.ao, it.sk.inv_spp}, it.col, it.mom_in, it.hist_in,
+                                           SigCounts{it.mask, it.ao, it.sk.inv_spp, it.sk.shadow_bit}, it.col, it.mom_in, it.hist_in,
                                            it.mom_out, it.hist_out, it.illum, o.x, o.y);
     }
 }

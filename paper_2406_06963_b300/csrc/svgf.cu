@@ -82,6 +82,8 @@ dhr_status check_svgf_params(const dhr_svgf_params* p) {
     DHR_CHECK_ARG(p->ao_spp >= 1 && p->ao_spp <= 255, "svgf: ao_spp %u not in 1..255", p->ao_spp);
     DHR_CHECK_ARG(p->alpha > 0.0f && p->alpha <= 1.0f, "svgf: alpha not in (0, 1]");
     DHR_CHECK_ARG(p->sigma_n >= 0.0f && p->sigma_z >= 0.0f && p->sigma_l >= 0.0f, "svgf: negative sigma");
+    DHR_CHECK_ARG(p->shadow_light < DHR_MAX_LIGHTS, "svgf: shadow_light %u not in 0..%d", p->shadow_light,
+                  DHR_MAX_LIGHTS - 1);
     return DHR_OK;
 }
 
@@ -98,7 +100,7 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
     const auto* gp = prev ? static_cast<const typename S::G*>(prev->depth_normal) : nullptr;
     temporal_kernel<P, SigCounts><<<grid, blk, 0, st>>>(
         k, *cam, prev ? *cam_prev : *cam, gc, cur->mesh_id, gp, prev ? prev->mesh_id : nullptr,
-        SigCounts{mask, ao, k.inv_spp},
+        SigCounts{mask, ao, k.inv_spp, k.shadow_bit},
         static_cast<const typename S::Col*>(s->col), static_cast<const typename S::Mom*>(s->mom[src]),
         s->hist[src], static_cast<typename S::Mom*>(s->mom[dst]), s->hist[dst], s->illum);
     DHR_CUDA_TRY(cudaGetLastError());

@@ -79,6 +79,7 @@ struct SvgfConsts {
     float alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
     float inv_spp;
     int fixed_alpha, wl_in_atrous;
+    uint32_t shadow_bit;   // light whose visibility bit is the shadow channel
 };
 
 __device__ __forceinline__ bool is_fg(float z) { return z < INFINITY; }
@@ -105,17 +106,20 @@ __device__ __forceinline__ float2 depth_grad(const typename S::G* g, int W, int 
     return make_float2(r[0], r[1]);
 }
 
-__device__ __forceinline__ float2 noisy(const uint8_t* mask, const uint8_t* ao, size_t i, float inv_spp) {
-    return make_float2((float)__ldg(ao + i) * inv_spp, (__ldg(mask + i) & 1u) ? 1.0f : 0.0f);
+__device__ __forceinline__ float2 noisy(const uint8_t* mask, const uint8_t* ao, size_t i, float inv_spp,
+                                       uint32_t bit) {
+    return make_float2((float)__ldg(ao + i) * inv_spp, ((__ldg(mask + i) >> bit) & 1u) ? 1.0f : 0.0f);
 }
 
 // noisy signals of the current frame: from the 8-bit trace outputs
-// (AO = N_unoccluded / N, Eq. 3; shadow = bit 0 of the visibility mask) ...
+// (AO = N_unoccluded / N, Eq. 3; shadow = bit `bit` of the visibility mask,
+// one bit per light) ...
 struct SigCounts {
     const uint8_t* mask;
     const uint8_t* ao;
     float inv_spp;
-    __device__ __forceinline__ float2 operator()(size_t i) const { return noisy(mask, ao, i, inv_spp); }
+    uint32_t bit;
+    __device__ __forceinline__ float2 operator()(size_t i) const { return noisy(mask, ao, i, inv_spp, bit); }
 };
 
 // ... or real-valued planes [2][H][W] (the differentiable form)
@@ -720,6 +724,7 @@ inline SvgfConsts make_consts(int W, int H, const dhr_svgf_params* prm) {
     k.inv_spp = 1.0f / (float)prm->ao_spp;
     k.fixed_alpha = (int)prm->fixed_alpha;
     k.wl_in_atrous = (int)prm->wl_in_atrous;
+    k.shadow_bit = prm->shadow_light;
     return k;
 }
 

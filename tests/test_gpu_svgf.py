@@ -30,17 +30,19 @@ def _oracle_frames(scene, cams, tp_kw=None):
     return out
 
 
-def _run_both(frames, cams, op: "orc.SvgfParams", precision=dhrs.DHR_FP32, check_internal=True):
+def _run_both(frames, cams, op: "orc.SvgfParams", precision=dhrs.DHR_FP32, check_internal=True, shadow_light=0):
+    """shadow_light = k: the GPU filters bit k of the full bitmask, the oracle
+    (which filters bit 0) is given the bitmask shifted right by k."""
     W, H = cams[0].width, cams[0].height
     ost = orc.SvgfState(W, H)
     gst = dhrs.SvgfState(W, H, precision)
-    gp = dhrs.SvgfParams(**op.__dict__)
+    gp = dhrs.SvgfParams(**op.__dict__, shadow_light=shadow_light)
     prev = None
     worst = 0.0
     ao_o = torch.empty((H, W), device="cuda")
     sh_o = torch.empty((H, W), device="cuda")
     for f, (zn, mesh, mask, ao) in enumerate(frames):
-        ref = ost.frame(zn, mesh, cams[f], mask, ao, op)
+        ref = ost.frame(zn, mesh, cams[f], mask >> shadow_light, ao, op)
         g = dhrs.GBuffer.from_arrays(zn, mesh, precision)
         gst.reconstruct(g, prev[0] if prev else None, cams[f], prev[1] if prev else None,
                         torch.from_numpy(mask).cuda(), torch.from_numpy(ao).cuda(), gp, ao_o, sh_o)
@@ -87,6 +89,20 @@ def test_svgf_fixed_alpha_no_luminance_multi_spp():
     assert _run_both(frames, cams, p) <= TOL
 
 
+@pytest.mark.parametrize("light", [1, 2])
+def test_svgf_filters_the_selected_light(light):
+    """Three lights with different cone angles: shadow_light = k filters bit k
+    of the visibility bitmask (the oracle gets that bit as its bit 0)."""
+    s = wl.scene_boxes()
+    cams = wl.orbit_path(4, 96, 64, degrees=6.0)
+    tp = dict(light_dirs=[(0.3, 1.0, 0.2), (-0.6, 0.8, 0.3), (0.2, 0.5, -0.8)],
+              cone_half_angle_deg=[0.5, 3.0, 1.5])
+    frames = _oracle_frames(s, cams, tp)
+    bits = np.stack([f[2] for f in frames])
+    assert ((bits >> light) & 1).mean() != (bits & 1).mean()      # the lights differ
+    assert _run_both(frames, cams, orc.SvgfParams(), shadow_light=light) <= TOL
+
+
 @pytest.mark.slow
 def test_svgf_1080p():
     """Full 1920x1080 frames (the launch configuration bench.py times), 3
@@ -103,7 +119,7 @@ def test_svgf_rejects_bad_arguments():
     cam = wl.boxes_camera(16, 16)
     m = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
     o = torch.empty((16, 16), device="cuda")
-    for bad in (dict(levels=9), dict(ao_spp=0), dict(alpha=0.0)):
+    for bad in (dict(levels=9), dict(ao_spp=0), dict(alpha=0.0), dict(shadow_light=8)):
         with pytest.raises(dhrs.DhrError):
             st.reconstruct(g, None, cam, None, m, m, dhrs.SvgfParams(**bad), o, o)
     g16 = dhrs.GBuffer(16, 16, dhrs.DHR_FP16)
