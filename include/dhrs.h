@@ -315,7 +315,12 @@ void dhr_session_destroy(dhr_session* session);
 
 /* Trace + reconstruct one frame seen by `cam` (frame index `frame` feeds
  * the hash).  ao_out, shadow_out: device float [W*H] or NULL (results stay
- * in the session).  Asynchronous on `stream`. */
+ * in the session).  Asynchronous: the trace runs on a stream of the
+ * session and may overlap the filtering of the previous frame; the filter
+ * starts after the work queued on `stream` before this call, and `stream`
+ * waits for it, so the results are complete in `stream` order.  The session
+ * keeps three G-buffer / raw-output slots in rotation (and one pair of
+ * internal output planes). */
 dhr_status dhr_step_frame(dhr_session* session, const dhr_camera* cam, uint32_t frame,
                           float* ao_out, float* shadow_out, void* stream);
 

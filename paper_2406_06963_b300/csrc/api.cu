@@ -123,16 +123,27 @@ extern "C" dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_cam
 }
 
 // ---------------------------------------------------------------- session
+// Consecutive frames are pipelined: the trace of frame N+1 runs on the
+// session's trace stream while the SVGF of frame N runs on its SVGF stream
+// (the trace is bound by instruction issue and L1, the filter by latency and
+// special-function throughput, so the two overlap well).  G-buffers and raw
+// trace outputs rotate through kRing slots; a slot is traced into again only
+// after the SVGF of the frame that last read it (as history) has finished.
+constexpr int kRing = 3;
+
 struct dhr_session {
     const dhr_scene* scene = nullptr;
     int32_t w = 0, h = 0;
     dhr_precision prec = DHR_FP32;
     dhr_trace_params tp{};
     dhr_svgf_params sp{};
-    void* gdn[2] = {nullptr, nullptr};
-    uint32_t* gmesh[2] = {nullptr, nullptr};
-    uint8_t* mask = nullptr;
-    uint8_t* ao = nullptr;
+    void* gdn[kRing] = {};
+    uint32_t* gmesh[kRing] = {};
+    uint8_t* mask[kRing] = {};
+    uint8_t* ao[kRing] = {};
+    cudaStream_t trace_st = nullptr, svgf_st = nullptr;
+    cudaEvent_t traced = nullptr, caller = nullptr;
+    cudaEvent_t filtered[kRing] = {};   // SVGF done for the frame traced into that slot
     float* out = nullptr;         // [2][W*H]: filtered AO, filtered shadow
     float* out_b = nullptr;       // second output buffer of the streaming host path
     cudaStream_t copy_st = nullptr;
@@ -146,19 +157,26 @@ struct dhr_session {
 
 extern "C" void dhr_session_destroy(dhr_session* s) {
     if (!s) return;
+    if (s->trace_st) cudaStreamSynchronize(s->trace_st);
+    if (s->svgf_st) cudaStreamSynchronize(s->svgf_st);
     if (s->copy_st) cudaStreamSynchronize(s->copy_st);
+    for (int i = 0; i < kRing; ++i) {
+        if (s->filtered[i]) cudaEventDestroy(s->filtered[i]);
+        cudaFree(s->gdn[i]);
+        cudaFree(s->gmesh[i]);
+        cudaFree(s->mask[i]);
+        cudaFree(s->ao[i]);
+    }
+    if (s->traced) cudaEventDestroy(s->traced);
+    if (s->caller) cudaEventDestroy(s->caller);
+    if (s->trace_st) cudaStreamDestroy(s->trace_st);
+    if (s->svgf_st) cudaStreamDestroy(s->svgf_st);
     for (int i = 0; i < 2; ++i) {
         if (s->computed[i]) cudaEventDestroy(s->computed[i]);
         if (s->copied[i]) cudaEventDestroy(s->copied[i]);
     }
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
     cudaFree(s->out_b);
-    for (int i = 0; i < 2; ++i) {
-        cudaFree(s->gdn[i]);
-        cudaFree(s->gmesh[i]);
-    }
-    cudaFree(s->mask);
-    cudaFree(s->ao);
     cudaFree(s->out);
     svgf_free(s->svgf);
     delete s;
@@ -183,12 +201,17 @@ extern "C" dhr_status dhr_session_create(const dhr_scene* scene, int32_t width, 
     const size_t n = (size_t)width * height;
     const size_t gb = precision == DHR_FP16 ? 8 : 16;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 2 && !e; ++i) {
+    for (int i = 0; i < kRing && !e; ++i) {
         e = cudaMalloc(&s->gdn[i], n * gb);
         if (!e) e = cudaMalloc((void**)&s->gmesh[i], n * 4);
+        if (!e) e = cudaMalloc((void**)&s->mask[i], n);
+        if (!e) e = cudaMalloc((void**)&s->ao[i], n);
+        if (!e) e = cudaEventCreateWithFlags(&s->filtered[i], cudaEventDisableTiming);
     }
-    if (!e) e = cudaMalloc((void**)&s->mask, n);
-    if (!e) e = cudaMalloc((void**)&s->ao, n);
+    if (!e) e = cudaStreamCreateWithFlags(&s->trace_st, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&s->svgf_st, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&s->traced, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&s->caller, cudaEventDisableTiming);
     if (!e) e = cudaMalloc((void**)&s->out, 2 * n * sizeof(float));
     if (!e) e = cudaMalloc((void**)&s->out_b, 2 * n * sizeof(float));
     if (!e) e = cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking);
@@ -229,20 +252,29 @@ extern "C" dhr_status dhr_step_frame(dhr_session* s, const dhr_camera* cam, uint
     DHR_CHECK_ARG(cam->width == s->w && cam->height == s->h, "step_frame: camera size %dx%d, session %dx%d",
                   cam->width, cam->height, s->w, s->h);
     cudaStream_t st = as_stream(stream);
-    const int cur = s->cur ^ 1;
-    dhr_gbuffer g = session_gbuf(s, cur);
+    const int b = (s->cur + 1) % kRing;     // this frame's slot; s->cur holds the previous frame
+    dhr_gbuffer g = session_gbuf(s, b);
     dhr_gbuffer gp = session_gbuf(s, s->cur);
     dhr_trace_params tp = s->tp;
     tp.frame = frame;
-    DHR_TRY(launch_trace(s->scene, cam, &tp, &g, s->mask, s->ao, st));
+    // slot b was last read (as history) by the SVGF of the frame two steps back
+    DHR_CUDA_TRY(cudaStreamWaitEvent(s->trace_st, s->filtered[(b + 1) % kRing], 0));
+    DHR_TRY(launch_trace(s->scene, cam, &tp, &g, s->mask[b], s->ao[b], s->trace_st));
+    DHR_CUDA_TRY(cudaEventRecord(s->traced, s->trace_st));
     const size_t n = (size_t)s->w * s->h;
     float* ao = ao_out ? ao_out : s->out;
     float* sh = shadow_out ? shadow_out : s->out + n;
     // the session's own output buffer may still be read by a streaming copy
     if (!ao_out || !shadow_out) DHR_CUDA_TRY(cudaStreamWaitEvent(st, s->copied[0], 0));
+    // the filter writes caller memory: after the caller's earlier work on `stream`
+    DHR_CUDA_TRY(cudaEventRecord(s->caller, st));
+    DHR_CUDA_TRY(cudaStreamWaitEvent(s->svgf_st, s->caller, 0));
+    DHR_CUDA_TRY(cudaStreamWaitEvent(s->svgf_st, s->traced, 0));
     DHR_TRY(svgf_run(s->svgf, &g, s->has_prev ? &gp : nullptr, cam, s->has_prev ? &s->cam_prev : nullptr,
-                     s->mask, s->ao, &s->sp, ao, sh, st));
-    s->cur = cur;
+                     s->mask[b], s->ao[b], &s->sp, ao, sh, s->svgf_st));
+    DHR_CUDA_TRY(cudaEventRecord(s->filtered[b], s->svgf_st));
+    DHR_CUDA_TRY(cudaStreamWaitEvent(st, s->filtered[b], 0));   // results in `stream` order
+    s->cur = b;
     s->cam_prev = *cam;
     s->has_prev = true;
     return DHR_OK;
@@ -295,8 +327,8 @@ extern "C" dhr_status dhr_session_get_frame(dhr_session* s, dhr_gbuffer* gbuf, u
     clear_error();
     DHR_CHECK_ARG(s, "session_get_frame: null session");
     if (gbuf) *gbuf = session_gbuf(s, s->cur);
-    if (shadow_mask) *shadow_mask = s->mask;
-    if (ao_count) *ao_count = s->ao;
+    if (shadow_mask) *shadow_mask = s->mask[s->cur];
+    if (ao_count) *ao_count = s->ao[s->cur];
     return DHR_OK;
 }
 
