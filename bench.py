@@ -232,21 +232,22 @@ def run_ours(args):
 
     # end to end through the host-output entry point (camera in, filtered AO and
     # shadow out to pinned host memory every step)
-    # (streaming form: frame i's copy to pinned host memory overlaps frame
-    # i + 1's trace; each result is waited for before its buffer is reused)
-    hbuf = [(torch.empty((H, W), pin_memory=True), torch.empty((H, W), pin_memory=True)) for _ in range(2)]
+    # (streaming form: frame i's copy to pinned host memory overlaps the next
+    # frames; a frame's result is waited for two frames later, before its
+    # host buffers are reused)
+    hbuf = [(torch.empty((H, W), pin_memory=True), torch.empty((H, W), pin_memory=True)) for _ in range(3)]
     sess2 = dhrs.Session(sc, W, H, dhrs.DHR_FP32, tp, sp)
     for i in range(Wm):
         sess2.step_host(cams[i % N_FRAMES], i, *hbuf[0])
     _barrier(ws)
     t0 = time.perf_counter()
-    last = None
+    tickets = []
     for i in range(K):
-        t = sess2.step_host_async(cams[(Wm + i) % N_FRAMES], Wm + i, *hbuf[i & 1])
-        if last is not None:
-            sess2.wait(last)          # frame i - 1 is in host memory
-        last = t
-    sess2.wait(last)
+        tickets.append(sess2.step_host_async(cams[(Wm + i) % N_FRAMES], Wm + i, *hbuf[i % 3]))
+        if i >= 2:
+            sess2.wait(tickets[i - 2])   # frame i - 2 is in host memory
+    for t in tickets[-2:]:
+        sess2.wait(t)
     e2e_own_s = time.perf_counter() - t0
 
     # rays and traversal work of every frame of the path (counting variant of

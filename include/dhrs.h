@@ -344,9 +344,10 @@ dhr_status dhr_step_frame_host_async(dhr_session* session, const dhr_camera* cam
                                      float* ao_host, float* shadow_host, void* stream,
                                      uint64_t* out_ticket);
 
-/* Blocks until the host copy of `ticket` has completed (if later frames
- * were enqueued since, it may also wait for their copies).  ticket 0 or a
- * ticket not issued yet: DHR_ERR_INVALID. */
+/* Blocks until the host copy of `ticket` has completed.  Waiting for any of
+ * the last four tickets waits for that copy alone (so a caller can keep
+ * several frames in flight); an older ticket may also wait for later
+ * copies.  ticket 0 or a ticket not issued yet: DHR_ERR_INVALID. */
 dhr_status dhr_session_wait(dhr_session* session, uint64_t ticket);
 
 /* Device views of the session's current G-buffer and raw trace outputs. */

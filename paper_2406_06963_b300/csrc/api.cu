@@ -148,6 +148,7 @@ struct dhr_session {
     float* out_b = nullptr;       // second output buffer of the streaming host path
     cudaStream_t copy_st = nullptr;
     cudaEvent_t computed[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    cudaEvent_t ticket_done[4] = {};   // copy of ticket t done: ticket_done[(t - 1) % 4]
     uint64_t tickets = 0;         // streaming frames issued
     dhr_svgf_state* svgf = nullptr;
     dhr_camera cam_prev{};
@@ -175,6 +176,8 @@ extern "C" void dhr_session_destroy(dhr_session* s) {
         if (s->computed[i]) cudaEventDestroy(s->computed[i]);
         if (s->copied[i]) cudaEventDestroy(s->copied[i]);
     }
+    for (int i = 0; i < 4; ++i)
+        if (s->ticket_done[i]) cudaEventDestroy(s->ticket_done[i]);
     if (s->copy_st) cudaStreamDestroy(s->copy_st);
     cudaFree(s->out_b);
     cudaFree(s->out);
@@ -219,6 +222,7 @@ extern "C" dhr_status dhr_session_create(const dhr_scene* scene, int32_t width, 
         e = cudaEventCreateWithFlags(&s->computed[i], cudaEventDisableTiming);
         if (!e) e = cudaEventCreateWithFlags(&s->copied[i], cudaEventDisableTiming);
     }
+    for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreateWithFlags(&s->ticket_done[i], cudaEventDisableTiming);
     if (e) {
         cudaGetLastError();
         dhr_session_destroy(s);
@@ -308,6 +312,7 @@ extern "C" dhr_status dhr_step_frame_host_async(dhr_session* s, const dhr_camera
     DHR_CUDA_TRY(cudaMemcpyAsync(ao_host, dev, n * sizeof(float), cudaMemcpyDeviceToHost, s->copy_st));
     DHR_CUDA_TRY(cudaMemcpyAsync(shadow_host, dev + n, n * sizeof(float), cudaMemcpyDeviceToHost, s->copy_st));
     DHR_CUDA_TRY(cudaEventRecord(s->copied[slot], s->copy_st));
+    DHR_CUDA_TRY(cudaEventRecord(s->ticket_done[s->tickets % 4], s->copy_st));
     *out_ticket = ++s->tickets;
     return DHR_OK;
 }
@@ -317,8 +322,9 @@ extern "C" dhr_status dhr_session_wait(dhr_session* s, uint64_t ticket) {
     DHR_CHECK_ARG(s, "session_wait: null session");
     DHR_CHECK_ARG(ticket >= 1 && ticket <= s->tickets, "session_wait: ticket %llu not issued (last %llu)",
                   (unsigned long long)ticket, (unsigned long long)s->tickets);
-    // ticket t used output slot (t - 1) & 1; that slot's event is the copy of t or of a later frame
-    DHR_CUDA_TRY(cudaEventSynchronize(s->copied[(ticket - 1) & 1]));
+    // the event of ticket t, or (after 4 more tickets reused it) of a later
+    // copy on the same stream, which completes after t's
+    DHR_CUDA_TRY(cudaEventSynchronize(s->ticket_done[(ticket - 1) % 4]));
     return DHR_OK;
 }
 
