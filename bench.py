@@ -250,6 +250,20 @@ def run_ours(args):
         sess2.wait(t)
     e2e_own_s = time.perf_counter() - t0
 
+    # transport: the last frame's raw trace outputs, packed losslessly
+    fb = sess.frame_buffers()
+    m_last = dhrs.device_copy(fb["mask"], (H, W), "uint8")
+    a_last = dhrs.device_copy(fb["ao"], (H, W), "uint8")
+    dhrs.pack_visibility(m_last, a_last, 1, 1)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    packed = dhrs.pack_visibility(m_last, a_last, 1, 1)
+    p1.record()
+    torch.cuda.synchronize()
+    transport = {"raw_bytes_per_frame": 2 * W * H, "packed_bytes_per_frame": packed.numel() * 4,
+                 "pack_ms_incl_size_readback": round(p0.elapsed_time(p1), 4),
+                 "format": "bit planes x 32x8 tiles, uniform tiles 2 bits (dhr_visibility_pack)"}
+
     # rays and traversal work of every frame of the path (counting variant of
     # the trace kernel, run after the timed regions)
     stats = [dhrs.trace_stats(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=f)) for f in range(N_FRAMES)]
@@ -307,6 +321,7 @@ def run_ours(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "Mrays/s", "h2d_bytes_per_step": 60,
                 "d2h_bytes_per_step": 2 * 4 * W * H,
                 "ms_per_step": round(e2e_s * 1e3 / K, 4)},
+        "transport": transport,
         "gpu_launches": 7 * K,
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),

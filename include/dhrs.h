@@ -306,6 +306,39 @@ dhr_status dhr_svgf_atrous_noalloc(const dhr_gbuffer* gbuf, const float* illum,
                                    float* shadow_out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Lossless packing of the raw trace outputs for transport (the paper       */
+/* streams compressed frames to its clients, Sections 4.3.2 and 5)          */
+/* ---------------------------------------------------------------------- */
+/* The bitmask (one bit per light) and the AO count are split into bit
+ * planes (the n_lights bits, then ceil(log2(ao_spp + 1)) bits of the count),
+ * each plane into 32x8-pixel tiles; a tile whose pixels inside the image are
+ * all 0 or all 1 costs 2 bits, any other tile 2 bits + 256 bits.  Stream of
+ * 32-bit little-endian words:
+ *   [0] 0x56524844, [1] W, [2] H, [3] n_lights | ao_bits << 8,
+ *   [4] M = number of mixed (plane, tile) pairs,
+ *   ceil(P*T/16) words of 2-bit classes (pair k = plane*T + tile at bits
+ *   2(k%16).. of word k/16; 0 all zero, 1 all one, 2 mixed), then 8 words per
+ *   mixed pair in increasing k (word r = tile row r, bit i = pixel x0 + i;
+ *   0 outside the image).  T = ceil(W/32) * ceil(H/8) tiles, row-major.
+ * Size in bytes: 4 * (5 + ceil(P*T/16) + 8*M), known on the host after
+ * reading word 4.  The library allocates nothing here. */
+
+/* Largest stream for these parameters (bytes; 0 for invalid ones). */
+uint64_t dhr_visibility_pack_bound(int32_t width, int32_t height, uint32_t n_lights, uint32_t ao_spp);
+
+/* Device scratch the packer needs (bytes; 0 for invalid parameters). */
+uint64_t dhr_visibility_pack_work(int32_t width, int32_t height, uint32_t n_lights, uint32_t ao_spp);
+
+/* Packs shadow_mask, ao_count (device u8 [H][W], as written by
+ * dhr_trace_visibility with these n_lights / ao_spp) into out (device,
+ * dhr_visibility_pack_bound bytes), using work (device, 256-byte aligned,
+ * dhr_visibility_pack_work bytes).  Asynchronous on `stream`.
+ * DHR_ERR_INVALID for bad sizes or parameters, null or misaligned buffers. */
+dhr_status dhr_visibility_pack(const uint8_t* shadow_mask, const uint8_t* ao_count, int32_t width,
+                               int32_t height, uint32_t n_lights, uint32_t ao_spp, void* work,
+                               uint32_t* out, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Session: trace + SVGF per frame with library-owned G-buffer ping-pong   */
 /* ---------------------------------------------------------------------- */
 dhr_status dhr_session_create(const dhr_scene* scene, int32_t width, int32_t height,

@@ -103,6 +103,9 @@ _SIGNATURES = {
     "dhr_server_close": ([_P, C.c_int32], C.c_int),
     "dhr_server_submit": ([_P, C.c_int32, _P, _P, C.c_uint32, C.c_uint64, C.c_uint64], C.c_int),
     "dhr_server_set_max_batch_pixels": ([_P, C.c_uint64], C.c_int),
+    "dhr_visibility_pack_bound": ([C.c_int32, C.c_int32, C.c_uint32, C.c_uint32], C.c_uint64),
+    "dhr_visibility_pack_work": ([C.c_int32, C.c_int32, C.c_uint32, C.c_uint32], C.c_uint64),
+    "dhr_visibility_pack": ([_P, _P, C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, _P, _P, _P], C.c_int),
     "dhr_server_pump": ([_P, _P], C.c_int),
     "dhr_server_poll": ([_P, _P, C.c_int32, _P, C.c_int32], C.c_int),
     "dhr_server_output": ([_P, C.c_int32, _P, _P], C.c_int),
@@ -392,6 +395,28 @@ def svgf_atrous_noalloc(gbuf: GBuffer, illum_ptr: int, params: SvgfParams, ao_ou
     p = params.to_c()
     _check(lib().dhr_svgf_atrous_noalloc(C.byref(g), C.c_void_p(int(illum_ptr)), C.byref(p), _ptr(ao_out),
                                          _ptr(sh_out), _stream(stream)))
+
+
+def pack_visibility(mask, ao, n_lights: int, ao_spp: int, stream=None):
+    """Lossless packed stream (torch uint32 words on the device, trimmed to
+    its size) of a frame's bitmask and AO count; the format is in dhrs.h."""
+    import torch
+    _need_cuda(mask, ao)
+    H, W = mask.shape
+    bound = lib().dhr_visibility_pack_bound(W, H, n_lights, ao_spp)
+    if bound == 0:
+        raise DhrError(1, "pack_visibility: bad parameters")
+    work = torch.empty(int(lib().dhr_visibility_pack_work(W, H, n_lights, ao_spp)) + 256, dtype=torch.uint8,
+                       device=mask.device)
+    wp = (work.data_ptr() + 255) & ~255
+    out = torch.empty(int(bound) // 4, dtype=torch.int32, device=mask.device)
+    _check(lib().dhr_visibility_pack(_ptr(mask), _ptr(ao), W, H, n_lights, ao_spp, C.c_void_p(wp), _ptr(out),
+                                     _stream(stream)))
+    n_mixed = int(out[4].item())
+    T = ((W + 31) // 32) * ((H + 7) // 8)
+    planes = n_lights + int(ao_spp).bit_length()
+    n_words = 5 + (planes * T + 15) // 16 + 8 * n_mixed
+    return out[:n_words]
 
 
 def device_copy(ptr: int, shape, dtype: str):
