@@ -332,7 +332,8 @@ def run_ours(args):
         res["adjoint"] = run_adjoint(sc, scene_d)
         res["denoise_variants"] = run_denoise_variants(sc, scene_d)
     if rank == 0 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(scene_d, cams, sample_px=args.cpu_pixels)
+        res["cpu_baseline"] = cpu_baseline(scene_d, cams, sample_px=args.cpu_pixels,
+                                           rays_per_frame=res["rays_per_frame"])
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -509,7 +510,7 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
             "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.exp()]}
 
 
-def cpu_baseline(scene_d, cams, sample_px=4096, seed=7):
+def cpu_baseline(scene_d, cams, sample_px=4096, seed=7, rays_per_frame=None):
     """The oracle as it stands (brute force over all triangles, fp64, OpenMP
     on every host core) on a bounded sample of the same workload: primary,
     shadow and AO rays of `sample_px` seeded pixels of frame 0, and the
@@ -541,6 +542,7 @@ def cpu_baseline(scene_d, cams, sample_px=4096, seed=7):
     return {"value": round(n_rays / dt / 1e6, 6), "unit": "Mrays/s", "cores": orc.num_threads(),
             "kind": "oracle", "ns_per_ray": round(dt / n_rays * 1e9, 1),
             "svgf_ms_per_frame_1080p": round(svgf_s * 1e3, 1),
+            "trace_s_per_frame_extrapolated": (round(dt / n_rays * rays_per_frame, 1) if rays_per_frame else None),
             "sample": f"{sample_px} seeded pixels of frame 0 (primary + shadow + AO rays, "
                       f"{n_rays} rays, {dt:.1f} s) of the 1920x1080 776,050-triangle workload; "
                       f"SVGF: one full 1920x1080 frame with history (box-scene G-buffers)"}
