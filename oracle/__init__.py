@@ -49,6 +49,11 @@ class OrcSvgfParams(C.Structure):
                 ("wl_in_atrous", C.c_int32)]
 
 
+class OrcSmapFrame(C.Structure):
+    _fields_ = [("res", C.c_int32), ("L", C.c_double * 3), ("eu", C.c_double * 3), ("ev", C.c_double * 3),
+                ("u0", C.c_double), ("v0", C.c_double), ("w", C.c_double), ("h", C.c_double)]
+
+
 P = C.c_void_p
 
 
@@ -74,6 +79,9 @@ def _declare(L):
     L.orc_svgf_frame.argtypes = [C.c_int, C.c_int] + [P] * 16
     L.orc_svgf_seq_grad.argtypes = [C.c_int, C.c_int, C.c_int] + [P] * 9
     L.orc_delay_warp.argtypes = [C.c_int, C.c_int] + [P] * 11
+    L.orc_smap_frame_make.argtypes = [P, P, C.c_int32, P]
+    L.orc_smap_render.argtypes = [P, P, P, P, C.c_int64, P, P]
+    L.orc_smap_classify.argtypes = [P, P, P, C.c_double, C.c_int64, P, P, P, C.c_double, C.c_double, P, P]
 
 
 def _p(a):
@@ -377,3 +385,93 @@ def delay_warp(zn_t, mesh_t, cam_t, zn_s, mesh_s, cam_s, src_ao, src_sh):
                          _p(_c(src_ao, np.float64)), _p(_c(src_sh, np.float64)), _p(out_ao), _p(out_sh),
                          _p(valid))
     return out_ao, out_sh, valid
+
+
+# --------------------------------------------------------------------------
+# selective shadow rays (Section 5: shadow-map ray mask)
+# --------------------------------------------------------------------------
+CLS_TRACE, CLS_LIT, CLS_UMBRA = 0, 1, 2
+
+
+class ShadowMap:
+    """Oracle shadow map of one directional light: the frame (double) and,
+    when ``full``, every texel's depth and ambiguity flag (brute force:
+    R^2 closest-hit casts over every triangle)."""
+
+    def __init__(self, scene: Scene, light_dir, res: int, full: bool = True, margin=DEFAULT_MARGIN):
+        l = np.asarray(light_dir, np.float64)
+        self.light = (l / np.linalg.norm(l)).astype(np.float32)
+        self.frame = OrcSmapFrame()
+        lib().orc_smap_frame_make(scene.h, _p(_c(self.light, np.float32)), int(res), C.byref(self.frame))
+        self.res = int(res)
+        self.scene = scene
+        self.margin = margin
+        self.depth = self.amb = None
+        if full:
+            self.depth = np.zeros((res, res))
+            self.amb = np.zeros((res, res), np.uint8)
+            mg = OrcMargin(*margin)
+            lib().orc_smap_render(scene.h, C.byref(self.frame), C.byref(mg), None, 0, _p(self.depth),
+                                  _p(self.amb))
+
+    def frame_dict(self):
+        f = self.frame
+        return dict(res=f.res, L=np.array(f.L[:]), eu=np.array(f.eu[:]), ev=np.array(f.ev[:]), u0=f.u0,
+                    v0=f.v0, w=f.w, h=f.h)
+
+    def texels(self, ij):
+        """Depth and ambiguity of the texels ij ([n, 2] int (i, j))."""
+        ij = _c(ij, np.int32).reshape(-1, 2)
+        d = np.zeros(len(ij))
+        a = np.zeros(len(ij), np.uint8)
+        mg = OrcMargin(*self.margin)
+        lib().orc_smap_render(self.scene.h, C.byref(self.frame), C.byref(mg), _p(ij), len(ij), _p(d), _p(a))
+        return d, a
+
+    def classify(self, pos, normal, fg, theta, tol_t=2e-3, tol_z=None):
+        """Per-pixel class (CLS_*) and ambiguity flag for cone half angle theta."""
+        assert self.depth is not None, "classification needs the full map"
+        if tol_z is None:
+            tol_z = 1e-5 * (1.0 + self.scene_extent())
+        pos = _c(pos, np.float64).reshape(-1, 3)
+        normal = _c(normal, np.float64).reshape(-1, 3)
+        fg = _c(fg, np.uint8).ravel()
+        n = len(pos)
+        cls = np.zeros(n, np.uint8)
+        amb = np.zeros(n, np.uint8)
+        lib().orc_smap_classify(C.byref(self.frame), _p(_c(self.depth, np.float64)), _p(_c(self.amb, np.uint8)),
+                                float(theta), n, _p(pos), _p(normal), _p(fg), float(tol_t), float(tol_z),
+                                _p(cls), _p(amb))
+        return cls, amb
+
+    def scene_extent(self):
+        return float(np.abs(self.scene.v).max()) if len(self.scene.v) else 1.0
+
+
+def trace_selective(scene: Scene, cam, params: TraceParams, maps, pixels=None, margin=DEFAULT_MARGIN):
+    """The full trace with each light's shadow bit replaced by its shadow-map
+    verdict wherever the classification is LIT (bit 1) or UMBRA (bit 0).
+    maps: one ShadowMap (full) or None (trace everywhere) per light.  Adds
+    'cls' [n, n_lights], 'amb_cls' [n, n_lights], 'traced' (bit k = light k's
+    ray traced) and 'shadow_mask_full' (the full method's bits)."""
+    tr = trace(scene, cam, params, pixels, margin)
+    n = len(tr["depth"])
+    nl = len(params.light_dirs)
+    fg = np.isfinite(tr["depth"]).astype(np.uint8)
+    cls = np.zeros((n, nl), np.uint8)
+    amb = np.zeros((n, nl), np.uint8)
+    full = tr["shadow_mask"].copy()
+    sel = full.copy()
+    traced = np.zeros(n, np.uint8)
+    for k in range(nl):
+        if maps[k] is None:
+            traced |= (fg << k).astype(np.uint8)
+            continue
+        c, a = maps[k].classify(tr["pos"], tr["normal"], fg, math.radians(params.cone_half_angle_deg[k]))
+        cls[:, k], amb[:, k] = c, a
+        bit = np.uint8(1 << k)
+        sel = np.where((fg == 1) & (c == CLS_LIT), sel | bit, sel)
+        sel = np.where((fg == 1) & (c == CLS_UMBRA), sel & ~bit, sel)
+        traced |= np.where((fg == 1) & (c == CLS_TRACE), bit, np.uint8(0)).astype(np.uint8)
+    tr.update(cls=cls, amb_cls=amb, traced=traced, shadow_mask_full=full, shadow_mask=sel.astype(np.uint8))
+    return tr

@@ -74,6 +74,7 @@ typedef struct {
     double *nrm;             /* [n][3] unit geometric normal (e1 x e2) */
     uint32_t *mesh;
     double extent;           /* largest |coordinate| of any vertex */
+    double bmin[3], bmax[3]; /* bounds of the triangles' vertices (0 without triangles) */
 } orc_scene;
 
 typedef struct {
@@ -296,10 +297,18 @@ orc_scene* orc_scene_create(const float* verts, const uint32_t* idx, const uint3
     double ext = 0.0;
     for (int64_t v = 0; v < n_vertices * 3; ++v) ext = fmax(ext, fabs((double)verts[v]));
     s->extent = ext;
+    for (int c = 0; c < 3; ++c) {
+        s->bmin[c] = n_tris > 0 ? INFINITY : 0.0;
+        s->bmax[c] = n_tris > 0 ? -INFINITY : 0.0;
+    }
     for (int64_t i = 0; i < n_tris; ++i) {
         double p[3][3];
         for (int k = 0; k < 3; ++k)
-            for (int c = 0; c < 3; ++c) p[k][c] = (double)verts[3 * (int64_t)idx[3 * i + k] + c];
+            for (int c = 0; c < 3; ++c) {
+                p[k][c] = (double)verts[3 * (int64_t)idx[3 * i + k] + c];
+                s->bmin[c] = fmin(s->bmin[c], p[k][c]);
+                s->bmax[c] = fmax(s->bmax[c], p[k][c]);
+            }
         double *v0 = s->v0 + 3 * i, *e1 = s->e1 + 3 * i, *e2 = s->e2 + 3 * i;
         memcpy(v0, p[0], sizeof(double) * 3);
         sub3(p[1], p[0], e1);
@@ -1377,4 +1386,195 @@ void orc_delay_warp(int W, int H, const float* zn_t, const uint32_t* mesh_t, con
         }
     }
     free(zero_hist);
+}
+
+/* ======================================================================== */
+/* 8. Selective shadow rays (Section 5: the shadow-map ray mask of          */
+/*    Lauterbach and Manocha that the paper plans to adopt)                 */
+/* ======================================================================== */
+/*
+ * The method: a shadow map from the light marks the pixels whose shadow
+ * verdict it cannot give reliably; those pixels, widened by a radius set by
+ * the light's angular size and the distance to the occluder, form a ray
+ * mask.  Masked pixels are ray traced; the others take the shadow map's
+ * verdict (lit, or umbra).  The reading written out here (gather form):
+ *
+ * Map frame, in double, from the unit light direction L (toward the light)
+ * and the bounds [bmin, bmax] of the triangles' vertices:
+ *   helper a = (0, 1, 0) if |L.y| < 0.9 else (1, 0, 0);
+ *   eu = (a x L) / |a x L|, ev = L x eu;
+ *   u, v, t = eu.c, ev.c, L.c over the 8 bound corners c -> [umin, umax],
+ *   [vmin, vmax], tmax; E = max(umax - umin, vmax - vmin) (1 if not > 0);
+ *   texel size w = E (1 + 2^-10) / R; the R x R map is centred on the
+ *   projected bounds: u0 = (umin + umax) / 2 - w R / 2 (v0 alike);
+ *   light plane h = tmax + E / 64; depth of a point x is h - L.x.
+ * Map S[j][i] (texel i along eu, j along ev): depth of the closest surface
+ *   met by the ray from h L + (u0 + (i + 1/2) w) eu + (v0 + (j + 1/2) w) ev
+ *   along -L, +inf when it meets none.
+ * Classification of a pixel (hit point X, unit normal n) for a light whose
+ *   cone has half angle theta (tau = tan theta):
+ *   1. g = sin theta + 0.05.  n.L < -g: the whole cone is below the
+ *      surface -> UMBRA; n.L <= g: the cone grazes the surface -> TRACE.
+ *   2. a = (eu.X - u0) / w - 1/2, b = (ev.X - v0) / w - 1/2 (texel
+ *      coordinates, centres at integers), z = h - L.X.
+ *   3. Occluder bound: a cone ray that has moved r texels sideways is at
+ *      least r w / tau closer to the light, so no occluder above
+ *      zmin = min S can be met beyond r0 = max(0, (z - zmin) tau / w)
+ *      texels.  The texel range [floor(a - r0), ceil(a + r0)] (and b
+ *      alike), clamped to the map, spans s texels; at the smallest level
+ *      l with 2^l >= s the range meets at most 2 x 2 cells of 2^l x 2^l
+ *      texels, and zocc = min S over those cells.
+ *   4. Penumbra radius r = max(0, (z - zocc) tau / w) texels (the light's
+ *      angular size times the distance to the nearest possible occluder).
+ *      r + 1 > 4 -> TRACE (footprint wider than the 9 x 9 window).
+ *   5. Window: texels i in [ceil(a - r - 1), floor(a + r + 1)] (and j
+ *      alike), clamped to the map.  Texel (i, j) is occluded when
+ *      S[j][i] < z + ((i - a) n.eu + (j - b) n.ev) w / n.L - w, i.e. a
+ *      surface lies more than one texel size above the receiver's tangent
+ *      plane there.  All free -> LIT; all occluded -> UMBRA; else TRACE.
+ * The ray mask is the set of TRACE pixels; they take the ray-traced bit of
+ * the full method, LIT pixels bit 1, UMBRA pixels bit 0.
+ */
+#define ORC_SMAP_WINDOW 4           /* largest window radius r + 1, texels */
+#define ORC_SMAP_GRAZE 0.05         /* margin of n.L over sin theta */
+#define ORC_CLS_TRACE 0
+#define ORC_CLS_LIT 1
+#define ORC_CLS_UMBRA 2
+
+typedef struct {
+    int32_t res;               /* R, a power of two */
+    double L[3], eu[3], ev[3];
+    double u0, v0, w, h;
+} orc_smap_frame;
+
+void orc_smap_frame_make(const orc_scene* s, const float light[3], int32_t res, orc_smap_frame* f)
+{
+    double l[3] = {light[0], light[1], light[2]};
+    double ln = norm3(l);
+    for (int k = 0; k < 3; ++k) f->L[k] = l[k] / ln;
+    double a[3] = {0.0, 0.0, 0.0};
+    if (fabs(f->L[1]) < 0.9) a[1] = 1.0; else a[0] = 1.0;
+    double c[3];
+    cross3(a, f->L, c);
+    double cn = norm3(c);
+    for (int k = 0; k < 3; ++k) f->eu[k] = c[k] / cn;
+    cross3(f->L, f->eu, f->ev);
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY, tmax = -INFINITY;
+    for (int k = 0; k < 8; ++k) {
+        double p[3] = {(k & 1) ? s->bmax[0] : s->bmin[0], (k & 2) ? s->bmax[1] : s->bmin[1],
+                       (k & 4) ? s->bmax[2] : s->bmin[2]};
+        double u = dot3(f->eu, p), v = dot3(f->ev, p), t = dot3(f->L, p);
+        umin = fmin(umin, u); umax = fmax(umax, u);
+        vmin = fmin(vmin, v); vmax = fmax(vmax, v);
+        tmax = fmax(tmax, t);
+    }
+    double E = fmax(umax - umin, vmax - vmin);
+    if (!(E > 0.0)) E = 1.0;
+    f->res = res;
+    f->w = E * (1.0 + 1.0 / 1024.0) / res;
+    f->u0 = 0.5 * (umin + umax) - 0.5 * f->w * res;
+    f->v0 = 0.5 * (vmin + vmax) - 0.5 * f->w * res;
+    f->h = tmax + E / 64.0;
+}
+
+/* Depth of texels (i, j) = texels[2k], texels[2k + 1] (all R x R texels in
+ * row-major order when texels is NULL), with the closest-hit ambiguity flag. */
+void orc_smap_render(const orc_scene* s, const orc_smap_frame* f, const orc_margin* mg,
+                     const int32_t* texels, int64_t n, double* depth, uint8_t* amb)
+{
+    int64_t R = f->res;
+    if (!texels) n = R * R;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i = texels ? texels[2 * k] : k % R, j = texels ? texels[2 * k + 1] : k / R;
+        double u = f->u0 + ((double)i + 0.5) * f->w, v = f->v0 + ((double)j + 0.5) * f->w;
+        double o[3], d[3];
+        for (int c = 0; c < 3; ++c) {
+            o[c] = f->h * f->L[c] + u * f->eu[c] + v * f->ev[c];
+            d[c] = -f->L[c];
+        }
+        cast_result r = cast_closest(s, o, d, 0.0, INFINITY, mg);
+        depth[k] = r.hit ? r.t : INFINITY;
+        amb[k] = (uint8_t)r.ambiguous;
+    }
+}
+
+static int near_integer(double x, double tol) { return fabs(x - nearbyint(x)) < tol; }
+
+static int64_t clampi(int64_t x, int64_t lo, int64_t hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* Classify np pixels (pos, nrm: [np][3]; fg[i] = 0 skips background) for a
+ * light of cone half angle theta against a full map S ([R][R], S_amb its
+ * ambiguity flags).  cls: ORC_CLS_*; amb = 1 where a decision of the
+ * classification lies within tol_t texels (integer bounds, the window cap)
+ * or tol_z world units (texel tests, grazing test in units of n.L) of
+ * flipping, or reads an ambiguous texel. */
+void orc_smap_classify(const orc_smap_frame* f, const double* S, const uint8_t* S_amb, double theta,
+                       int64_t np, const double* pos, const double* nrm, const uint8_t* fg,
+                       double tol_t, double tol_z, uint8_t* cls, uint8_t* amb)
+{
+    const int64_t R = f->res;
+    const double tau = tan(theta), g = sin(theta) + ORC_SMAP_GRAZE;
+    double zmin = INFINITY, zmin_sure = INFINITY;
+    for (int64_t k = 0; k < R * R; ++k) {
+        zmin = fmin(zmin, S[k]);
+        if (!S_amb[k]) zmin_sure = fmin(zmin_sure, S[k]);
+    }
+    const int zmin_amb = zmin != zmin_sure;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < np; ++p) {
+        cls[p] = ORC_CLS_LIT;
+        amb[p] = 0;
+        if (fg && !fg[p]) continue;
+        const double* X = pos + 3 * p;
+        const double* n = nrm + 3 * p;
+        int am = zmin_amb;
+        double nL = dot3(n, f->L);
+        if (fabs(nL - g) < 1e-5 || fabs(nL + g) < 1e-5) am = 1;
+        if (nL < -g) { cls[p] = ORC_CLS_UMBRA; amb[p] = (uint8_t)am; continue; }
+        if (nL <= g) { cls[p] = ORC_CLS_TRACE; amb[p] = (uint8_t)am; continue; }
+        double a = (dot3(f->eu, X) - f->u0) / f->w - 0.5;
+        double b = (dot3(f->ev, X) - f->v0) / f->w - 0.5;
+        double z = f->h - dot3(f->L, X);
+        /* 3. occluder bound over the pyramid cells */
+        double r0 = fmax(0.0, (z - zmin) * tau / f->w);
+        if (near_integer(a - r0, tol_t) || near_integer(a + r0, tol_t) || near_integer(b - r0, tol_t) ||
+            near_integer(b + r0, tol_t))
+            am = 1;
+        int64_t ilo = clampi((int64_t)floor(a - r0), 0, R - 1), ihi = clampi((int64_t)ceil(a + r0), 0, R - 1);
+        int64_t jlo = clampi((int64_t)floor(b - r0), 0, R - 1), jhi = clampi((int64_t)ceil(b + r0), 0, R - 1);
+        int64_t span = (ihi - ilo > jhi - jlo ? ihi - ilo : jhi - jlo) + 1;
+        int lv = 0;
+        while (((int64_t)1 << lv) < span) ++lv;
+        int64_t ci0 = (ilo >> lv) << lv, ci1 = ((ihi >> lv) + 1) << lv;
+        int64_t cj0 = (jlo >> lv) << lv, cj1 = ((jhi >> lv) + 1) << lv;
+        double zocc = INFINITY;
+        for (int64_t j = cj0; j < cj1; ++j)
+            for (int64_t i = ci0; i < ci1; ++i) {
+                zocc = fmin(zocc, S[j * R + i]);
+                if (S_amb[j * R + i]) am = 1;
+            }
+        /* 4. penumbra radius */
+        double r = fmax(0.0, (z - zocc) * tau / f->w);
+        if (fabs(r + 1.0 - ORC_SMAP_WINDOW) < tol_t) am = 1;
+        if (r + 1.0 > ORC_SMAP_WINDOW) { cls[p] = ORC_CLS_TRACE; amb[p] = (uint8_t)am; continue; }
+        /* 5. window of tangent-plane shadow tests */
+        if (near_integer(a - r - 1.0, tol_t) || near_integer(a + r + 1.0, tol_t) ||
+            near_integer(b - r - 1.0, tol_t) || near_integer(b + r + 1.0, tol_t))
+            am = 1;
+        int64_t wi0 = clampi((int64_t)ceil(a - r - 1.0), 0, R - 1), wi1 = clampi((int64_t)floor(a + r + 1.0), 0, R - 1);
+        int64_t wj0 = clampi((int64_t)ceil(b - r - 1.0), 0, R - 1), wj1 = clampi((int64_t)floor(b + r + 1.0), 0, R - 1);
+        double gu = dot3(n, f->eu) / nL * f->w, gv = dot3(n, f->ev) / nL * f->w;
+        double tz = tol_z + tol_t * (fabs(gu) + fabs(gv));
+        int occ = 0, fre = 0;
+        for (int64_t j = wj0; j <= wj1; ++j)
+            for (int64_t i = wi0; i <= wi1; ++i) {
+                double plane = z + ((double)i - a) * gu + ((double)j - b) * gv - f->w;
+                double sv = S[j * R + i];
+                if (S_amb[j * R + i] || fabs(sv - plane) < tz) am = 1;
+                if (sv < plane) occ = 1; else fre = 1;
+            }
+        cls[p] = (uint8_t)(occ && fre ? ORC_CLS_TRACE : (occ ? ORC_CLS_UMBRA : ORC_CLS_LIT));
+        amb[p] = (uint8_t)am;
+    }
 }
