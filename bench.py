@@ -331,6 +331,7 @@ def run_ours(args):
         res["precision_form"] = run_precision_form(sc, scene_d)
         res["adjoint"] = run_adjoint(sc, scene_d)
         res["denoise_variants"] = run_denoise_variants(sc, scene_d)
+        res["selective_shadows"] = run_selective(sc, scene_d)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(scene_d, cams, sample_px=args.cpu_pixels,
                                            rays_per_frame=res["rays_per_frame"])
@@ -507,7 +508,7 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
         losses.append(round(float(loss.detach()), 6))
     return {"workload": f"{frames} frames x {W}x{H}, terrain776k", "forward_ms": round(fwd, 3),
             "backward_ms": round(bwd, 3), "algorithmic_gb_per_s": round(bytes_fb / ((fwd + bwd) * 1e-3) / 1e9, 1),
-            "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.exp()]}
+            "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.detach().exp()]}
 
 
 def cpu_baseline(scene_d, cams, sample_px=4096, seed=7, rays_per_frame=None):
@@ -598,6 +599,61 @@ def run_denoise_variants(sc, scene_d, frames=12, W=1280, H=720, levels=(0, 1, 2,
     out["noisy_1spp_ao_rmse"] = round(float(np.sqrt(np.mean(noisy))), 5)
     out["workload"] = f"{frames} frames x {W}x{H}, terrain776k, 1 spp, reference 255 spp, last 4 frames"
     return out
+
+
+def run_selective(sc, scene_d, frames=30, resolution=4096):
+    """Selective shadow rays (Section 5): the 1080p trace with shadow rays
+    only where a 4096^2 shadow map cannot decide, against the full trace.
+    Trace-only device time per frame (median, L2 flushed before each
+    frame), share of foreground pixels whose shadow ray is called, and share
+    whose shadow bit differs from the full trace's ray."""
+    import numpy as np
+    import torch
+
+    import paper_2406_06963_b300 as dhrs
+    import workloads as wl
+    cams = wl.spline_path(scene_d["terrain"], N_FRAMES, W, H)
+    light = dhrs.TraceParams().light_dirs[0]
+    sm = dhrs.ShadowMap(sc, light, resolution)
+    g = dhrs.GBuffer(W, H)
+    mask = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+    ao = torch.empty_like(mask)
+    rm = torch.empty_like(mask)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        ts = []
+        for f in range(frames):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(f)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts[3:]))
+
+    full_ms = timed(lambda f: dhrs.trace_visibility(sc, cams[f % N_FRAMES], dhrs.TraceParams(frame=f), g, mask, ao))
+    sel_ms = timed(lambda f: dhrs.trace_visibility_selective(sc, cams[f % N_FRAMES], dhrs.TraceParams(frame=f),
+                                                             [sm], g, mask, ao, rm))
+    n_fg = n_called = n_diff = 0
+    for f in (0, 15, 30, 45):
+        p = dhrs.TraceParams(frame=f)
+        dhrs.trace_visibility(sc, cams[f], p, g, mask, ao)
+        full = mask.clone()
+        dhrs.trace_visibility_selective(sc, cams[f], p, [sm], g, mask, ao, rm)
+        fg = g.mesh.view(torch.int32) != -1
+        called = (rm & 1) == 1
+        n_fg += int(fg.sum())
+        n_called += int((called & fg).sum())
+        n_diff += int((fg & (full != mask)).sum())
+    info = sm.info()
+    return {"map_resolution": resolution, "map_build_ms": round(info["build_ms"], 3),
+            "map_mb": round(info["bytes"] / 2**20, 1),
+            "trace_ms_full": round(full_ms, 4), "trace_ms_selective": round(sel_ms, 4),
+            "shadow_rays_called_frac": round(n_called / n_fg, 5),
+            "shadow_bits_differing_frac": n_diff / n_fg,
+            "workload": f"terrain776k 1920x1080, {frames} spline frames, 1 light, 0.5 deg cone"}
 
 
 def run_reference(args):

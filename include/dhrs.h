@@ -209,6 +209,73 @@ dhr_status dhr_gbuffer_convert(const dhr_gbuffer* src, dhr_gbuffer* dst, void* s
 dhr_status dhr_trace_stats(const dhr_scene* scene, const dhr_camera* cam,
                            const dhr_trace_params* params, uint64_t* counters, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Selective shadow rays (Section 5: a shadow map marks the pixels whose    */
+/* shadow it cannot decide -- potential penumbra, widened by the light's    */
+/* angular size times the distance to the occluder -- and only those are   */
+/* ray traced; the rest take the map's verdict, after Lauterbach and        */
+/* Manocha).                                                                */
+/* ---------------------------------------------------------------------- */
+typedef struct dhr_shadow_map dhr_shadow_map;
+
+typedef struct {
+    int32_t resolution;      /* R texels per side (power of two) */
+    int32_t levels;          /* log2(R) + 1: level 0 the depths, level l the
+                                minimum over 2^l x 2^l texels */
+    float light_dir[3];      /* unit L, toward the light */
+    float axis_u[3], axis_v[3]; /* map plane axes (L, axis_u, axis_v orthonormal) */
+    float u0, v0, texel;     /* texel (i, j) centre: u0 + (i + 1/2) texel along
+                                axis_u, v0 + (j + 1/2) texel along axis_v */
+    float plane;             /* depth of a point x is plane - L . x */
+    float depth_min;         /* smallest depth in the map (+inf when empty) */
+    const float* depth;      /* device, owned by the map: level 0 as [R][R]
+                                (row j, column i), then levels 1.. each
+                                [R >> l][R >> l], level l starting at element
+                                4 (R^2 - (R >> l)^2) / 3; +inf where the texel
+                                ray meets no surface */
+    uint64_t bytes;          /* device bytes held */
+    float build_ms;          /* device time of the build */
+} dhr_shadow_map_info;
+
+/* Renders the shadow map of one directional light over the whole scene:
+ * the R x R texels cover the scene's bounds projected along the light,
+ * each holding the depth of the closest surface met by a ray cast from the
+ * light plane along -L through its centre (closest hit through the BVH),
+ * plus the min pyramid.  light_dir: host float[3], any nonzero length
+ * (normalised here).  resolution: power of two in 16..8192 (4/3 R^2 floats
+ * of device memory).  Synchronises `stream`.  The map belongs to `scene` and
+ * stays valid while the scene lives.  Errors: DHR_ERR_INVALID (null
+ * pointer, bad resolution, zero or non-finite direction), DHR_ERR_OOM,
+ * DHR_ERR_CUDA. */
+dhr_status dhr_shadow_map_create(const dhr_scene* scene, const float* light_dir, int32_t resolution,
+                                 void* stream, dhr_shadow_map** out);
+void dhr_shadow_map_destroy(dhr_shadow_map* map);
+dhr_status dhr_shadow_map_get_info(const dhr_shadow_map* map, dhr_shadow_map_info* out);
+
+/* dhr_trace_visibility with the ray mask: for light k with maps[k] set,
+ * each receiver is classified against the map --
+ *   lit   (no texel of its penumbra footprint lies more than one texel
+ *          size above its tangent plane): bit k = 1, no ray;
+ *   umbra (every footprint texel does, or the light's cone lies wholly
+ *          below the surface): bit k = 0, no ray;
+ *   else  (mixed footprint, grazing cone, footprint radius + 1 > 4 texels):
+ *          the cone-jittered ray of dhr_trace_visibility, same bit.
+ * The footprint radius is (receiver depth - nearest possible occluder
+ * depth) tan(cone half angle) / texel, the occluder bounded through the min
+ * pyramid.  maps: n_lights entries (NULL entries, or maps == NULL: that
+ * light is traced everywhere); each must belong to `scene` and to the
+ * light direction params->light_dir[k].  ray_mask_out (device, W*H bytes,
+ * may be NULL): bit k = light k's ray was called for (0 on background).
+ * G-buffer and AO outputs are those of dhr_trace_visibility.  The map's
+ * verdict is an approximation (it sees the scene through texel centres
+ * only); a called ray is the exact method's ray.  Errors: as
+ * dhr_trace_visibility, and DHR_ERR_INVALID for a map of another scene or
+ * light direction. */
+dhr_status dhr_trace_visibility_selective(const dhr_scene* scene, const dhr_camera* cam,
+                                          const dhr_trace_params* params, const dhr_shadow_map* const* maps,
+                                          dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out,
+                                          uint8_t* ao_count_out, uint8_t* ray_mask_out, void* stream);
+
 /* Sampling check entry: for each of n (px, py) and the given frame, seed
  * and sample index, the accepted disk point and the binary32 AO direction
  * about normals[i] (ray type 1) and the shadow direction about `light`

@@ -118,6 +118,10 @@ _SIGNATURES = {
     "dhr_session_wait": ([_P, C.c_uint64], C.c_int),
     "dhr_session_get_frame": ([_P, _P, _P, _P], C.c_int),
     "dhr_session_reset": ([_P], C.c_int),
+    "dhr_shadow_map_create": ([_P, _P, C.c_int32, _P, _P], C.c_int),
+    "dhr_shadow_map_destroy": ([_P], None),
+    "dhr_shadow_map_get_info": ([_P, _P], C.c_int),
+    "dhr_trace_visibility_selective": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
 }
 
 _lib = None
@@ -302,6 +306,69 @@ def trace_visibility(scene: Scene, cam, params: TraceParams, gbuf: GBuffer, mask
     g = gbuf.c()
     _check(lib().dhr_trace_visibility(scene.h, C.byref(c), C.byref(p), C.byref(g), _ptr(mask),
                                       _ptr(ao), _stream(stream)))
+
+
+class ShadowMapInfoC(C.Structure):
+    _fields_ = [("resolution", C.c_int32), ("levels", C.c_int32), ("light_dir", C.c_float * 3),
+                ("axis_u", C.c_float * 3), ("axis_v", C.c_float * 3), ("u0", C.c_float), ("v0", C.c_float),
+                ("texel", C.c_float), ("plane", C.c_float), ("depth_min", C.c_float), ("depth", C.c_void_p),
+                ("bytes", C.c_uint64), ("build_ms", C.c_float)]
+
+
+class ShadowMap:
+    """Device shadow map of one directional light over ``scene`` (R x R
+    texels plus its min pyramid), for the selective trace."""
+
+    def __init__(self, scene: Scene, light_dir, resolution: int = 4096, stream=None):
+        l = np.asarray(light_dir, np.float64)
+        nl = np.linalg.norm(l)
+        self.light = (l / nl if nl > 0 else l).astype(np.float32)   # zero: rejected by the library
+        h = C.c_void_p()
+        _check(lib().dhr_shadow_map_create(scene.h, self.light.ctypes.data_as(C.c_void_p), int(resolution),
+                                           _stream(stream), C.byref(h)))
+        self.h = h
+        self.scene = scene      # the map must not outlive its scene
+
+    def info(self) -> dict:
+        i = ShadowMapInfoC()
+        _check(lib().dhr_shadow_map_get_info(self.h, C.byref(i)))
+        return dict(resolution=i.resolution, levels=i.levels, light_dir=list(i.light_dir),
+                    axis_u=list(i.axis_u), axis_v=list(i.axis_v), u0=i.u0, v0=i.v0, texel=i.texel,
+                    plane=i.plane, depth_min=i.depth_min, depth=i.depth, bytes=i.bytes, build_ms=i.build_ms)
+
+    def depth(self):
+        """Level 0 as a [R, R] float32 CUDA tensor (a copy)."""
+        import torch
+        i = self.info()
+        R = i["resolution"]
+        return torch.as_tensor(_DevArray(i["depth"], (R, R), "<f4"), device="cuda").clone()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dhr_shadow_map_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def trace_visibility_selective(scene: Scene, cam, params: TraceParams, maps, gbuf: GBuffer, mask, ao,
+                               ray_mask=None, stream=None):
+    """trace_visibility with shadow rays only where light k's map (maps[k],
+    or None = trace everywhere) cannot decide; ray_mask (uint8 [H, W],
+    optional) receives bit k = light k's ray was called for."""
+    _need_cuda(gbuf.depth_normal, gbuf.mesh, mask, ao, ray_mask)
+    c = camera(cam)
+    p = params.to_c()
+    g = gbuf.c()
+    arr = (C.c_void_p * MAX_LIGHTS)()
+    for k, m in enumerate(maps or []):
+        arr[k] = m.h.value if m is not None else None
+    _check(lib().dhr_trace_visibility_selective(scene.h, C.byref(c), C.byref(p), arr, C.byref(g), _ptr(mask),
+                                                _ptr(ao), _ptr(ray_mask), _stream(stream)))
 
 
 def trace_stats(scene: Scene, cam, params: TraceParams, stream=None) -> dict:

@@ -122,6 +122,21 @@ extern "C" dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_cam
     return launch_trace(scene, cam, params, gbuf_out, shadow_mask_out, ao_count_out, as_stream(stream));
 }
 
+extern "C" dhr_status dhr_trace_visibility_selective(const dhr_scene* scene, const dhr_camera* cam,
+                                                     const dhr_trace_params* params,
+                                                     const dhr_shadow_map* const* maps, dhr_gbuffer* gbuf_out,
+                                                     uint8_t* shadow_mask_out, uint8_t* ao_count_out,
+                                                     uint8_t* ray_mask_out, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(scene, "trace_visibility_selective: null scene");
+    DHR_TRY(check_camera(cam));
+    DHR_TRY(check_trace_params(params));
+    DHR_TRY(check_gbuffer(gbuf_out, cam->width, cam->height));
+    DHR_CHECK_ARG(shadow_mask_out && ao_count_out, "trace_visibility_selective: null output");
+    return launch_trace_selective(scene, cam, params, maps, gbuf_out, shadow_mask_out, ao_count_out, ray_mask_out,
+                                  as_stream(stream));
+}
+
 // ---------------------------------------------------------------- session
 // Consecutive frames are pipelined: the trace of frame N+1 runs on the
 // session's trace stream while the SVGF of frame N runs on its SVGF stream

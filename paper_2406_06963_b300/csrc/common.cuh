@@ -145,6 +145,10 @@ dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_tr
                         dhr_gbuffer* g, uint8_t* mask, uint8_t* ao, cudaStream_t st,
                         unsigned long long* stats = nullptr);
 
+dhr_status launch_trace_selective(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
+                                  const dhr_shadow_map* const* maps, dhr_gbuffer* g, uint8_t* mask, uint8_t* ao,
+                                  uint8_t* ray_mask, cudaStream_t st);
+
 dhr_status check_trace_params(const dhr_trace_params* p);
 dhr_status check_svgf_params(const dhr_svgf_params* p);
 

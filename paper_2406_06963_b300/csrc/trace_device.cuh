@@ -257,6 +257,93 @@ inline TraceConsts make_trace_consts(const dhr_camera& cam, const dhr_trace_para
     return k;
 }
 
+// ------------------------------------------------ selective shadow rays
+// Shadow map of one directional light (Section 5: a shadow map decides the
+// pixels it can, a ray mask holds the rest).  Frame: unit L toward the
+// light, eu, ev spanning the map plane; texel (i, j) has its centre at
+// u0 + (i + 1/2) w along eu and v0 + (j + 1/2) w along ev; depth of a point
+// x is h - L.x.  Level 0 is the R x R depth map (+inf where the texel ray
+// meets nothing); level l (R >> l texels per side) holds the minimum over
+// 2^l x 2^l texels, stored after level l - 1.
+struct SmapView {
+    const float* S;        // nullptr: this light is traced everywhere
+    int res;
+    float3 L, eu, ev;
+    float u0, v0, w, inv_w, h;
+    float zmin;            // minimum of level 0 (the top level)
+    float tau;             // tan of the cone half angle
+    float graze;           // sin of the cone half angle + kSmapGraze
+};
+
+struct SmapSet {
+    SmapView m[DHR_MAX_LIGHTS];
+};
+
+constexpr int kClsTrace = 0, kClsLit = 1, kClsUmbra = 2;
+constexpr float kSmapWindow = 4.0f;   // largest window radius r + 1 (texels)
+constexpr double kSmapGraze = 0.05;   // margin of n.L over sin(cone half angle)
+
+// offset of level l in a map of R x R texels: sum of (R >> k)^2, k < l
+__host__ __device__ __forceinline__ size_t smap_level_offset(int R, int l) {
+    const size_t s = (size_t)(R >> l);
+    return 4 * ((size_t)R * R - s * s) / 3;
+}
+
+__device__ __forceinline__ int smap_clampi(float x, int hi) {
+    return (int)fminf(fmaxf(x, 0.0f), (float)hi);
+}
+
+// Class of the receiver X (unit normal n facing the camera) for one light:
+//  1. the cone lies below the surface (n.L < -g) -> umbra; it grazes the
+//     surface (|n.L| <= g) -> trace;
+//  2. a cone ray that has moved r texels sideways is at least r w / tan
+//     closer to the light, so occluders met by the cone lie within
+//     r0 = (z - zmin) tan / w texels; the minimum depth zocc over the 2 x 2
+//     pyramid cells covering that range bounds the nearest occluder;
+//  3. penumbra radius r = (z - zocc) tan / w texels; r + 1 > 4 -> trace;
+//  4. each texel within r + 1 (Chebyshev) is occluded when its depth lies
+//     more than one texel size above the receiver's tangent plane there;
+//     all free -> lit, all occluded -> umbra, mixed -> trace.
+__device__ __forceinline__ int smap_classify(const SmapView& m, float3 X, float3 n) {
+    const float nL = dot(n, m.L);
+    if (nL < -m.graze) return kClsUmbra;
+    if (nL <= m.graze) return kClsTrace;
+    const float a = (dot(m.eu, X) - m.u0) * m.inv_w - 0.5f;
+    const float b = (dot(m.ev, X) - m.v0) * m.inv_w - 0.5f;
+    const float z = m.h - dot(m.L, X);
+    const int R1 = m.res - 1;
+    const float r0 = fmaxf(0.0f, (z - m.zmin) * m.tau * m.inv_w);
+    const int ilo = smap_clampi(floorf(a - r0), R1), ihi = smap_clampi(ceilf(a + r0), R1);
+    const int jlo = smap_clampi(floorf(b - r0), R1), jhi = smap_clampi(ceilf(b + r0), R1);
+    const int span = max(ihi - ilo, jhi - jlo) + 1;
+    const int lv = 32 - __clz(span - 1);              // smallest l with 2^l >= span
+    const float* M = m.S + smap_level_offset(m.res, lv);
+    const int Rl = m.res >> lv;
+    const int ci0 = ilo >> lv, ci1 = ihi >> lv, cj0 = jlo >> lv, cj1 = jhi >> lv;
+    const float zocc = fminf(fminf(__ldg(M + (size_t)cj0 * Rl + ci0), __ldg(M + (size_t)cj0 * Rl + ci1)),
+                             fminf(__ldg(M + (size_t)cj1 * Rl + ci0), __ldg(M + (size_t)cj1 * Rl + ci1)));
+    const float r = fmaxf(0.0f, (z - zocc) * m.tau * m.inv_w);
+    if (!(r + 1.0f <= kSmapWindow)) return kClsTrace;
+    // at most 9 x 9 texels (r + 1 <= 4); the explicit cap also holds for
+    // non-finite coordinates
+    const int wi0 = smap_clampi(ceilf(a - r - 1.0f), R1), wi1 = min(smap_clampi(floorf(a + r + 1.0f), R1), wi0 + 8);
+    const int wj0 = smap_clampi(ceilf(b - r - 1.0f), R1), wj1 = min(smap_clampi(floorf(b + r + 1.0f), R1), wj0 + 8);
+    const float inv_nL = 1.0f / nL;
+    const float gu = dot(n, m.eu) * inv_nL * m.w, gv = dot(n, m.ev) * inv_nL * m.w;
+    bool occ = false, fre = false;
+    for (int j = wj0; j <= wj1; ++j) {
+        const float base = z + ((float)j - b) * gv - m.w;
+        const float* row = m.S + (size_t)j * m.res;
+        for (int i = wi0; i <= wi1; ++i) {
+            const float plane = base + ((float)i - a) * gu;
+            if (__ldg(row + i) < plane) occ = true;
+            else fre = true;
+        }
+        if (occ && fre) return kClsTrace;
+    }
+    return occ ? kClsUmbra : kClsLit;
+}
+
 // Pixel of a thread: each warp covers an 8x4 tile; a 128-thread block
 // covers 16x8 pixels.
 __device__ __forceinline__ int2 thread_pixel() {
@@ -269,10 +356,14 @@ __device__ __forceinline__ int2 thread_pixel() {
 // stats[0..8] = rays {primary, shadow, AO}, visits {..}, tests {..}.
 // One pixel of the trace: primary ray -> G-buffer; unless kPrimaryOnly,
 // the shadow and AO rays -> bitmask and count.
-template <bool kHalf, bool kStats, bool kPrimaryOnly>
+// kSel: shadow rays only for the pixels the lights' shadow maps cannot
+// decide (smap_classify); ray_mask (optional) receives bit l = light l's
+// ray was called for.
+template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false>
 __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceConsts& k, int2 px, void* gbuf_dn,
                                             uint32_t* gbuf_mesh, uint8_t* mask_out, uint8_t* ao_out,
-                                            unsigned long long* stats) {
+                                            unsigned long long* stats, const SmapSet* sel = nullptr,
+                                            uint8_t* ray_mask = nullptr) {
     const int W = k.cam.width, H = k.cam.height;
     if (px.x >= W || px.y >= H) return;
     const size_t pix = (size_t)px.y * W + px.x;
@@ -305,6 +396,9 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
         if (kPrimaryOnly) return;
         mask_out[pix] = (uint8_t)((1u << k.n_lights) - 1u);
         ao_out[pix] = (uint8_t)k.ao_spp;
+        if constexpr (kSel) {
+            if (ray_mask) ray_mask[pix] = 0;
+        }
         return;
     }
     const float4* tr = sc.tris + 3 * leaf;
@@ -329,8 +423,16 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
 
     const float3 o = surface_origin(X, n, v0, v1, v2);
     // shadow rays: one per light, direction jittered inside the light's cone
-    uint32_t mask = 0;
+    uint32_t mask = 0, called = 0;
     for (uint32_t l = 0; l < k.n_lights; ++l) {
+        if constexpr (kSel) {
+            if (sel->m[l].S) {
+                const int c = smap_classify(sel->m[l], X, n);
+                if (c == kClsLit) mask |= 1u << l;
+                if (c != kClsTrace) continue;
+            }
+            called |= 1u << l;
+        }
         const float2 xy = disk_point(px.x, px.y, k.frame, k.seed, kShadowRay, l);
         const float3 d = cone_direction(k.light[l], k.tan_cone[l], xy);
         if (dot(d, n) <= 0.0f) continue;       // blocked by the surface itself
@@ -340,6 +442,9 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
         if (traverse<true, kStats>(sc, make_ray(o, d), 0.0f, tm, b, leaf, &ws) < 0) mask |= 1u << l;
     }
     mask_out[pix] = (uint8_t)mask;
+    if constexpr (kSel) {
+        if (ray_mask) ray_mask[pix] = (uint8_t)called;
+    }
     // AO rays: cosine-weighted, a hit closer than r occludes (Eq. 2-3)
     uint32_t unocc = 0;
     for (uint32_t j = 0; j < k.ao_spp; ++j) {

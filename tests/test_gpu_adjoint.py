@@ -101,6 +101,6 @@ def test_autograd_function_and_fit():
         l = ((out - ref) ** 2).sum()
         l.backward()
         opt.step()
-        losses.append(float(l))
+        losses.append(float(l.detach()))
     print("fit losses", losses)
     assert losses[-1] < losses[0]
