@@ -706,9 +706,18 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--cpu-pixels", type=int, default=4096)
     ap.add_argument("--ref-pixels", type=int, default=24)
+    ap.add_argument("--selective-only", action="store_true",
+                    help="print only the selective shadow ray measurement (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.selective_only:
+        import paper_2406_06963_b300 as dhrs
+        import workloads as wl
+        scene_d = wl.scene_terrain()
+        print(json.dumps({"selective_shadows": run_selective(dhrs.Scene(scene_d), scene_d,
+                                                             frames=args.steps + args.warmup)}), flush=True)
+        return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
         print(json.dumps(res), flush=True)
