@@ -304,7 +304,14 @@ def run_ours(args):
         "rays_per_frame": round(step_rays / K),
         "bvh": {"height": info["height"], "build_ms": round(info["build_ms"], 3),
                 "visits_per_ray": round(visits / (step_rays / K), 2),
-                "tests_per_ray": round(tests / (step_rays / K), 2)},
+                "tests_per_ray": round(tests / (step_rays / K), 2),
+                # per ray type {primary, shadow, AO}, over all frames of the path
+                "by_type": {t: {"rays_per_frame": round(sum(st["rays"][i] for st in stats) / N_FRAMES),
+                                "visits_per_ray": round(sum(st["visits"][i] for st in stats)
+                                                        / max(1, sum(st["rays"][i] for st in stats)), 2),
+                                "tests_per_ray": round(sum(st["tests"][i] for st in stats)
+                                                       / max(1, sum(st["rays"][i] for st in stats)), 2)}
+                            for i, t in enumerate(("primary", "shadow", "ao"))}},
         "roofline": {"kernel": "trace_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(alu_peak, 2), "unit": "Tops/s (fp32 lane ops)",
                      "frac": round(achieved / alu_peak, 4), "traffic": _traffic("trace_kernel"),

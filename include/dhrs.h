@@ -102,7 +102,24 @@ typedef struct {
     uint32_t ao_spp;                        /* N in 1..255 (8-bit count, Section 3.2) */
     uint32_t frame;                         /* hash input: frame index */
     uint32_t seed;                          /* hash input: xored into the frame */
+    uint32_t primary;                       /* how the primary G-buffer is found (both give
+                                               identical outputs): DHR_PRIMARY_TRAVERSE
+                                               (0, default) or DHR_PRIMARY_RASTER */
 } dhr_trace_params;
+
+/* Primary visibility (Section 1 and Section 3.3: the client rasterises the
+ * G-buffer).  TRAVERSE: one closest-hit ray per pixel through the BVH.
+ * RASTER: every triangle is binned into the 8 x 4-pixel tiles its clipped
+ * screen bounds overlap and tested against those pixels' centre rays with
+ * the same watertight test, each pixel keeping the nearest hit (ties: the
+ * smaller original triangle index) -- the closest hit of the pixel-centre
+ * ray by construction; tiles with long lists are traversed.  Its bins live
+ * in the mesh-id buffer and its per-pixel keys in the G-buffer's depth
+ * storage, so it needs no memory of its own (images under about 300 pixels
+ * are traversed).  Only dhr_trace_visibility(_selective) and sessions honour
+ * RASTER; the server and dhr_trace_stats always traverse. */
+#define DHR_PRIMARY_TRAVERSE 0u
+#define DHR_PRIMARY_RASTER 1u
 
 /* G-buffer (caller-owned device memory, W*H pixels).
  *  FP32: depth_normal = float4 per pixel (linear view depth, unit normal x,

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libdhrs.so")
 DHR_FP32, DHR_FP16 = 0, 1
 BACKGROUND = 0xFFFFFFFF
 MAX_LIGHTS = 8
+PRIMARY_TRAVERSE, PRIMARY_RASTER = 0, 1
 STATUS = {0: "DHR_OK", 1: "DHR_ERR_INVALID", 2: "DHR_ERR_OOM", 3: "DHR_ERR_CUDA",
           4: "DHR_ERR_TIMEOUT", 5: "DHR_ERR_ADMISSION", 6: "DHR_ERR_STATE"}
 
@@ -53,7 +54,8 @@ class SceneInfo(C.Structure):
 class TraceParamsC(C.Structure):
     _fields_ = [("n_lights", C.c_uint32), ("light_dir", (C.c_float * 3) * MAX_LIGHTS),
                 ("cone_half_angle", C.c_float * MAX_LIGHTS), ("ao_radius", C.c_float),
-                ("ao_spp", C.c_uint32), ("frame", C.c_uint32), ("seed", C.c_uint32)]
+                ("ao_spp", C.c_uint32), ("frame", C.c_uint32), ("seed", C.c_uint32),
+                ("primary", C.c_uint32)]
 
 
 class GBufferC(C.Structure):
@@ -188,6 +190,7 @@ class TraceParams:
     ao_spp: int = 1
     frame: int = 0
     seed: int = 0
+    primary: int = 0        # PRIMARY_TRAVERSE (default) or PRIMARY_RASTER (identical outputs)
 
     def to_c(self) -> TraceParamsC:
         p = TraceParamsC()
@@ -200,6 +203,7 @@ class TraceParams:
         p.ao_spp = self.ao_spp
         p.frame = self.frame
         p.seed = self.seed
+        p.primary = self.primary
         return p
 
 

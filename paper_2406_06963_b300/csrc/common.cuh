@@ -53,6 +53,7 @@ struct SceneView {
     const float4* nodes;
     const float4* tris;
     int32_t n_tris;
+    const uint32_t* leaf_of;   // original triangle index -> leaf (sorted) index
 };
 
 constexpr int kStackSize = 64;
@@ -127,12 +128,13 @@ __device__ __forceinline__ float4 unpack_gbuf16(uint2 u) {
 struct dhr_scene {
     float4* nodes = nullptr;
     float4* tris = nullptr;
+    uint32_t* leaf_of = nullptr;
     uint32_t n_tris = 0;
     uint32_t n_nodes = 0;
     uint32_t height = 0;
     uint64_t bytes = 0;
     float build_ms = 0.f;
-    dhr::SceneView view() const { return dhr::SceneView{nodes, tris, (int32_t)n_tris}; }
+    dhr::SceneView view() const { return dhr::SceneView{nodes, tris, (int32_t)n_tris, leaf_of}; }
 };
 
 namespace dhr {
@@ -148,6 +150,15 @@ dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_tr
 dhr_status launch_trace_selective(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
                                   const dhr_shadow_map* const* maps, dhr_gbuffer* g, uint8_t* mask, uint8_t* ao,
                                   uint8_t* ray_mask, cudaStream_t st);
+
+// Rasterised primary visibility (raster.cu): leaves in the G-buffer's depth
+// storage, per pixel, the key (t bits << 32 | original index) of the nearest
+// hit of the pixel-centre ray, or ~0 where there is none.  Returns false (and
+// launches nothing) when the camera basis is singular; the caller then traces
+// primary rays instead.
+dhr_status build_leaf_map(dhr_scene* sc, cudaStream_t st);
+dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer* g, cudaStream_t st,
+                         bool* launched);
 
 dhr_status check_trace_params(const dhr_trace_params* p);
 dhr_status check_svgf_params(const dhr_svgf_params* p);

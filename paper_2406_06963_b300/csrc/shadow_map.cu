@@ -87,12 +87,12 @@ __global__ void smap_min_kernel(const float* in, float* out, int Rl) {
     out[k] = fminf(fminf(a[0], a[1]), fminf(a[2 * Rl], a[2 * Rl + 1]));
 }
 
-template <bool kHalf>
+template <bool kHalf, bool kRaster>
 __global__ void __launch_bounds__(128, 10) trace_sel_kernel(SceneView sc, TraceConsts k, const __grid_constant__ SmapSet sel,
                                                         void* gbuf_dn, uint32_t* gbuf_mesh, uint8_t* mask_out,
                                                         uint8_t* ao_out, uint8_t* ray_mask) {
-    trace_pixel<kHalf, false, false, true>(sc, k, thread_pixel(), gbuf_dn, gbuf_mesh, mask_out, ao_out, nullptr,
-                                           &sel, ray_mask);
+    trace_pixel<kHalf, false, false, true, kRaster>(sc, k, thread_pixel(), gbuf_dn, gbuf_mesh, mask_out, ao_out,
+                                                    nullptr, &sel, ray_mask);
 }
 
 void cross_d(const double* a, const double* b, double* o) {
@@ -185,12 +185,16 @@ dhr_status launch_trace_selective(const dhr_scene* sc, const dhr_camera* cam, co
     }
     const TraceConsts k = make_trace_consts(*cam, *p);
     const dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
-    if (g->precision == DHR_FP16)
-        trace_sel_kernel<true><<<grid, 128, 0, st>>>(sc->view(), k, sel, g->depth_normal, g->mesh_id, mask, ao,
-                                                     ray_mask);
-    else
-        trace_sel_kernel<false><<<grid, 128, 0, st>>>(sc->view(), k, sel, g->depth_normal, g->mesh_id, mask, ao,
-                                                      ray_mask);
+    bool raster = false;
+    if (p->primary == DHR_PRIMARY_RASTER) DHR_TRY(launch_raster(sc, cam, g, st, &raster));
+    void* dn = g->depth_normal;
+    if (g->precision == DHR_FP16) {
+        if (raster) trace_sel_kernel<true, true><<<grid, 128, 0, st>>>(sc->view(), k, sel, dn, g->mesh_id, mask, ao, ray_mask);
+        else trace_sel_kernel<true, false><<<grid, 128, 0, st>>>(sc->view(), k, sel, dn, g->mesh_id, mask, ao, ray_mask);
+    } else {
+        if (raster) trace_sel_kernel<false, true><<<grid, 128, 0, st>>>(sc->view(), k, sel, dn, g->mesh_id, mask, ao, ray_mask);
+        else trace_sel_kernel<false, false><<<grid, 128, 0, st>>>(sc->view(), k, sel, dn, g->mesh_id, mask, ao, ray_mask);
+    }
     DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
 }

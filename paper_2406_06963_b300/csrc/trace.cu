@@ -11,11 +11,13 @@ namespace {
 
 // kStats: also count rays, node visits and triangle tests per ray type into
 // stats[0..8] = rays {primary, shadow, AO}, visits {..}, tests {..}.
-template <bool kHalf, bool kStats = false>
+// kRaster: the primary hit comes from the rasterised keys (raster.cu).
+template <bool kHalf, bool kStats = false, bool kRaster = false>
 __global__ void __launch_bounds__(128, 10) trace_kernel(SceneView sc, TraceConsts k, void* gbuf_dn,
                                                     uint32_t* gbuf_mesh, uint8_t* mask_out,
                                                     uint8_t* ao_out, unsigned long long* stats = nullptr) {
-    trace_pixel<kHalf, kStats, false>(sc, k, thread_pixel(), gbuf_dn, gbuf_mesh, mask_out, ao_out, stats);
+    trace_pixel<kHalf, kStats, false, false, kRaster>(sc, k, thread_pixel(), gbuf_dn, gbuf_mesh, mask_out, ao_out,
+                                                      stats);
 }
 
 __global__ void cast_kernel(SceneView sc, const float* orig, const float* dirs, const float* tmin,
@@ -64,6 +66,8 @@ dhr_status check_trace_params(const dhr_trace_params* p) {
                   p->n_lights, DHR_MAX_LIGHTS);
     DHR_CHECK_ARG(p->ao_spp >= 1 && p->ao_spp <= 255, "ao_spp %u not in 1..255", p->ao_spp);
     DHR_CHECK_ARG(p->ao_radius > 0.0f, "ao_radius must be > 0");
+    DHR_CHECK_ARG(p->primary == DHR_PRIMARY_TRAVERSE || p->primary == DHR_PRIMARY_RASTER,
+                  "primary %u is neither DHR_PRIMARY_TRAVERSE nor DHR_PRIMARY_RASTER", p->primary);
     for (uint32_t l = 0; l < p->n_lights; ++l)
         DHR_CHECK_ARG(p->cone_half_angle[l] >= 0.0f && p->cone_half_angle[l] < 1.5707963f,
                       "cone_half_angle[%u] not in [0, pi/2)", l);
@@ -81,10 +85,16 @@ dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_tr
         DHR_CUDA_TRY(cudaGetLastError());
         return DHR_OK;
     }
-    if (g->precision == DHR_FP16)
-        trace_kernel<true><<<grid, 128, 0, st>>>(sc->view(), k, g->depth_normal, g->mesh_id, mask, ao);
-    else
-        trace_kernel<false><<<grid, 128, 0, st>>>(sc->view(), k, g->depth_normal, g->mesh_id, mask, ao);
+    bool raster = false;
+    if (p->primary == DHR_PRIMARY_RASTER) DHR_TRY(launch_raster(sc, cam, g, st, &raster));
+    auto* dn = g->depth_normal;
+    if (g->precision == DHR_FP16) {
+        if (raster) trace_kernel<true, false, true><<<grid, 128, 0, st>>>(sc->view(), k, dn, g->mesh_id, mask, ao);
+        else trace_kernel<true><<<grid, 128, 0, st>>>(sc->view(), k, dn, g->mesh_id, mask, ao);
+    } else {
+        if (raster) trace_kernel<false, false, true><<<grid, 128, 0, st>>>(sc->view(), k, dn, g->mesh_id, mask, ao);
+        else trace_kernel<false><<<grid, 128, 0, st>>>(sc->view(), k, dn, g->mesh_id, mask, ao);
+    }
     DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
 }

@@ -344,6 +344,19 @@ __device__ __forceinline__ int smap_classify(const SmapView& m, float3 X, float3
     return occ ? kClsUmbra : kClsLit;
 }
 
+// Unnormalised direction of the ray through the centre of pixel (x, y), row 0
+// at the top: D = forward + sx right + sy up, so that the ray parameter of a
+// hit is its linear view depth.  Shared by the traced and the rasterised
+// primary visibility so that both test the same ray.
+__device__ __forceinline__ float3 primary_dir(const dhr_camera& c, int x, int y) {
+    const int W = c.width, H = c.height;
+    const float sx = (2.0f * (x + 0.5f) / W - 1.0f) * c.tan_half_fov_y * ((float)W / (float)H);
+    const float sy = (1.0f - 2.0f * (y + 0.5f) / H) * c.tan_half_fov_y;
+    return make_float3(c.forward[0] + sx * c.right[0] + sy * c.up[0],
+                       c.forward[1] + sx * c.right[1] + sy * c.up[1],
+                       c.forward[2] + sx * c.right[2] + sy * c.up[2]);
+}
+
 // Pixel of a thread: each warp covers an 8x4 tile; a 128-thread block
 // covers 16x8 pixels.
 __device__ __forceinline__ int2 thread_pixel() {
@@ -359,7 +372,10 @@ __device__ __forceinline__ int2 thread_pixel() {
 // kSel: shadow rays only for the pixels the lights' shadow maps cannot
 // decide (smap_classify); ray_mask (optional) receives bit l = light l's
 // ray was called for.
-template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false>
+// kRaster: the primary hit comes from the rasterised key in the G-buffer's
+// depth storage (launch_raster) instead of a traversal; the hit is then
+// re-intersected with the same test for its barycentrics.
+template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false, bool kRaster = false>
 __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceConsts& k, int2 px, void* gbuf_dn,
                                             uint32_t* gbuf_mesh, uint8_t* mask_out, uint8_t* ao_out,
                                             unsigned long long* stats, const SmapSet* sel = nullptr,
@@ -368,19 +384,28 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
     if (px.x >= W || px.y >= H) return;
     const size_t pix = (size_t)px.y * W + px.x;
     // primary ray through the pixel centre; its parameter is the linear depth
-    const float sx = (2.0f * (px.x + 0.5f) / W - 1.0f) * k.cam.tan_half_fov_y * ((float)W / (float)H);
-    const float sy = (1.0f - 2.0f * (px.y + 0.5f) / H) * k.cam.tan_half_fov_y;
     const float3 eye = make_float3(k.cam.pos[0], k.cam.pos[1], k.cam.pos[2]);
     const float3 fw = make_float3(k.cam.forward[0], k.cam.forward[1], k.cam.forward[2]);
-    const float3 D = make_float3(fw.x + sx * k.cam.right[0] + sy * k.cam.up[0],
-                                 fw.y + sx * k.cam.right[1] + sy * k.cam.up[1],
-                                 fw.z + sx * k.cam.right[2] + sy * k.cam.up[2]);
+    const float3 D = primary_dir(k.cam, px.x, px.y);
     const Ray pr = make_ray(eye, D);
     float tp = INFINITY;
     float3 bary;
     Work wp, ws, wa;
     uint32_t n_sh = 0, n_ao = 0;
-    const int leaf = traverse<false, kStats>(sc, pr, 0.0f, tp, bary, -1, &wp);
+    int leaf;
+    if constexpr (kRaster) {
+        const unsigned long long key =
+            reinterpret_cast<const unsigned long long*>(gbuf_dn)[pix * (kHalf ? 1 : 2)];
+        leaf = -1;
+        if (key != ~0ull) {
+            const int l = (int)__ldg(sc.leaf_of + (uint32_t)key);
+            const float4* tr = sc.tris + 3 * l;
+            if (hit_triangle(pr, f3(__ldg(tr)), f3(__ldg(tr + 1)), f3(__ldg(tr + 2)), 0.0f, INFINITY, tp, bary))
+                leaf = l;
+        }
+    } else {
+        leaf = traverse<false, kStats>(sc, pr, 0.0f, tp, bary, -1, &wp);
+    }
     if (kStats) {
         atomicAdd(stats + 0, 1ull);
         atomicAdd(stats + 3, (unsigned long long)wp.visits);
