@@ -172,7 +172,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sc = dhrs.Scene(scene_d)
     info = sc.info()
-    tp = dhrs.TraceParams(ao_spp=1)
+    primary = dhrs.PRIMARY_RASTER if args.primary == "raster" else dhrs.PRIMARY_TRAVERSE
+    tp = dhrs.TraceParams(ao_spp=1, primary=primary)
     sp = dhrs.SvgfParams(ao_spp=1, levels=5, alpha=0.2)
     sess = dhrs.Session(sc, W, H, dhrs.DHR_FP32, tp, sp)
     ao_out = torch.empty((H, W), device="cuda")
@@ -218,7 +219,9 @@ def run_ours(args):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         flush.fill_(float(i))
         e0.record(stream)
-        dhrs.trace_visibility(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=Wm + i), g, mask, aoc)
+        # the traversal form: one kernel with all three ray types (the roofline's kernel)
+        dhrs.trace_visibility(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=Wm + i,
+                                                            primary=dhrs.PRIMARY_TRAVERSE), g, mask, aoc)
         e1.record(stream)
         st.reconstruct(g, gp if prev_cam is not None else None, cams[f], prev_cam, mask, aoc, sp, ao_out, sh_out)
         e2.record(stream)
@@ -228,6 +231,17 @@ def run_ours(args):
             sv_ms.append(e1.elapsed_time(e2))
         g, gp = gp, g
         prev_cam = cams[f]
+    # the trace call in the session's form (rasterised primary visibility by default)
+    tr_sess_ms = []
+    for i in range(K):
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        flush.fill_(float(i))
+        e0.record(stream)
+        dhrs.trace_visibility(sc, cams[(Wm + i) % N_FRAMES], dhrs.TraceParams(ao_spp=1, frame=Wm + i, primary=primary),
+                              g, mask, aoc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr_sess_ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
 
     # end to end through the host-output entry point (camera in, filtered AO and
@@ -297,8 +311,9 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": ws, "steps": K,
         "warmup": Wm, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": bench_config(ws, info["n_triangles"]),
+        "config": dict(bench_config(ws, info["n_triangles"]), primary_visibility=args.primary),
         "ms_per_frame": {"trace_svgf": round(total_ms / K, 4), "trace": round(trace_ms, 4),
+                         "trace_session_form": round(statistics.mean(tr_sess_ms), 4),
                          "svgf": round(svgf_ms, 4)},
         "secondary_mrays_s": round(job_sec / (total_ms * 1e-3) / 1e6, 2),
         "rays_per_frame": round(step_rays / K),
@@ -329,7 +344,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * 4 * W * H,
                 "ms_per_step": round(e2e_s * 1e3 / K, 4)},
         "transport": transport,
-        "gpu_launches": 7 * K,
+        # per session frame: trace (+ clear, count, 3 scans, fill and per-tile
+        # primary kernels when rasterised), temporal, 5 a-trous levels
+        "gpu_launches": (14 if primary == dhrs.PRIMARY_RASTER else 7) * K,
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }
@@ -713,6 +730,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--cpu-pixels", type=int, default=4096)
     ap.add_argument("--ref-pixels", type=int, default=24)
+    ap.add_argument("--primary", default="raster", choices=["raster", "traverse"],
+                    help="primary visibility of the session frames: the rasteriser (default) or BVH "
+                         "traversal (same outputs)")
     ap.add_argument("--selective-only", action="store_true",
                     help="print only the selective shadow ray measurement (profiling aid)")
     args = ap.parse_args()

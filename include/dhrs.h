@@ -103,8 +103,8 @@ typedef struct {
     uint32_t frame;                         /* hash input: frame index */
     uint32_t seed;                          /* hash input: xored into the frame */
     uint32_t primary;                       /* how the primary G-buffer is found (both give
-                                               identical outputs): DHR_PRIMARY_TRAVERSE
-                                               (0, default) or DHR_PRIMARY_RASTER */
+                                               identical outputs): DHR_PRIMARY_RASTER
+                                               (0, default) or DHR_PRIMARY_TRAVERSE */
 } dhr_trace_params;
 
 /* Primary visibility (Section 1 and Section 3.3: the client rasterises the
@@ -118,8 +118,8 @@ typedef struct {
  * storage, so it needs no memory of its own (images under about 300 pixels
  * are traversed).  Only dhr_trace_visibility(_selective) and sessions honour
  * RASTER; the server and dhr_trace_stats always traverse. */
-#define DHR_PRIMARY_TRAVERSE 0u
-#define DHR_PRIMARY_RASTER 1u
+#define DHR_PRIMARY_RASTER 0u
+#define DHR_PRIMARY_TRAVERSE 1u
 
 /* G-buffer (caller-owned device memory, W*H pixels).
  *  FP32: depth_normal = float4 per pixel (linear view depth, unit normal x,

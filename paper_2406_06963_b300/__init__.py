@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libdhrs.so")
 DHR_FP32, DHR_FP16 = 0, 1
 BACKGROUND = 0xFFFFFFFF
 MAX_LIGHTS = 8
-PRIMARY_TRAVERSE, PRIMARY_RASTER = 0, 1
+PRIMARY_RASTER, PRIMARY_TRAVERSE = 0, 1
 STATUS = {0: "DHR_OK", 1: "DHR_ERR_INVALID", 2: "DHR_ERR_OOM", 3: "DHR_ERR_CUDA",
           4: "DHR_ERR_TIMEOUT", 5: "DHR_ERR_ADMISSION", 6: "DHR_ERR_STATE"}
 
@@ -190,7 +190,7 @@ class TraceParams:
     ao_spp: int = 1
     frame: int = 0
     seed: int = 0
-    primary: int = 0        # PRIMARY_TRAVERSE (default) or PRIMARY_RASTER (identical outputs)
+    primary: int = 0        # PRIMARY_RASTER (default) or PRIMARY_TRAVERSE (identical outputs)
 
     def to_c(self) -> TraceParamsC:
         p = TraceParamsC()

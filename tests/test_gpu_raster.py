@@ -1,9 +1,9 @@
-"""Rasterised primary visibility (DHR_PRIMARY_RASTER) against the traversed
-primary rays (DHR_PRIMARY_TRAVERSE, the default): both define the G-buffer
+"""Rasterised primary visibility (DHR_PRIMARY_RASTER, the default) against
+the traversed primary rays (DHR_PRIMARY_TRAVERSE): both define the G-buffer
 as the closest hit of the pixel-centre ray (ties to the smaller original
 triangle index), so every output -- depth/normal bytes, mesh ids, shadow
-bits, AO counts -- must be identical, byte for byte, so the oracle parity of
-the traversed path (test_gpu_trace.py) carries over.
+bits, AO counts -- must be identical, byte for byte.  The oracle parity tests
+(test_gpu_trace.py and the rest) run the default, rasterised path.
 
 Cases: both storage forms, ragged and tiny images, the 1080p terrain frames
 of the benchmark (the camera flies low over terrain, so triangles cross the
