@@ -177,12 +177,16 @@ constexpr int kTileW = 8, kTileH = 4;   // the trace's warp tile
 constexpr int kMaxBin = 48;             // longer lists: traverse the tile
 constexpr int kScanBlock = 1024;
 
+constexpr int kBigTiles = 256;          // more tiles: binned by a whole block
+constexpr int kBigGrid = 148 * 4;
+
 struct BinLayout {
     uint32_t* count;     // [n_tiles]
     uint32_t* offset;    // [n_tiles + 1], exclusive scan of count
     uint32_t* bsum;      // [n_blocks] block totals of the scan
+    uint32_t* big;       // [1 + big_cap]: number of big triangles, then their leaves
     uint32_t* list;      // [cap] leaf indices, tile by tile
-    uint32_t n_tiles, n_blocks, cap;
+    uint32_t n_tiles, n_blocks, big_cap, cap;
     int tiles_x;
 };
 
@@ -218,7 +222,8 @@ __device__ __forceinline__ void bin_tiles(const BinLayout& b, int tx0, int ty0, 
 }
 
 // One thread per triangle; a triangle overlapping more than 32 tiles is
-// binned by its whole warp (lanes stride over its tiles).
+// binned by its whole warp (lanes stride over its tiles), one overlapping
+// more than kBigTiles is listed (count pass) for bin_big_kernel.
 template <bool kCount>
 __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
     const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
@@ -233,7 +238,11 @@ __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc,
     const int ntx = any ? tx1 - tx0 + 1 : 0, nty = any ? ty1 - ty0 + 1 : 0;
     const int nt = ntx * nty;
     if (nt > 0 && nt <= 32) bin_tiles<kCount>(b, tx0, ty0, ntx, 0, 1, nt, (uint32_t)leaf);
-    unsigned big = __ballot_sync(0xffffffffu, nt > 32);
+    if (kCount && nt > kBigTiles) {
+        const uint32_t slot = atomicAdd(b.big, 1u);
+        if (slot < b.big_cap) b.big[1 + slot] = (uint32_t)leaf;   // else: bins unused (all tiles traversed)
+    }
+    unsigned big = __ballot_sync(0xffffffffu, nt > 32 && nt <= kBigTiles);
     while (big) {
         const int src = __ffs(big) - 1;
         big &= big - 1;
@@ -244,9 +253,26 @@ __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc,
     }
 }
 
-__global__ void bin_clear_kernel(uint32_t* count, uint32_t n) {
+// the listed big triangles, one block each (threads stride over its tiles)
+template <bool kCount>
+__global__ void __launch_bounds__(128) bin_big_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
+    const uint32_t n = min(b.big[0], b.big_cap);
+    for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+        const uint32_t leaf = b.big[1 + k];
+        const float4* tr = sc.tris + 3 * (size_t)leaf;
+        int x0, x1, y0, y1;
+        tri_bounds(rc, f3(__ldg(tr)), f3(__ldg(tr + 1)), f3(__ldg(tr + 2)), x0, x1, y0, y1);
+        if (x0 > x1 || y0 > y1) continue;   // not for a listed triangle (same bounds as when listed)
+        const int tx0 = x0 / kTileW, ty0 = y0 / kTileH;
+        const int ntx = x1 / kTileW - tx0 + 1, nt = ntx * (y1 / kTileH - ty0 + 1);
+        bin_tiles<kCount>(b, tx0, ty0, ntx, threadIdx.x, blockDim.x, nt, leaf);
+    }
+}
+
+__global__ void bin_clear_kernel(uint32_t* count, uint32_t n, uint32_t* big) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) count[i] = 0u;
+    if (i == 0) big[0] = 0u;
 }
 
 // exclusive scan of count into offset, 1024 elements per block; block totals to bsum
@@ -330,7 +356,8 @@ __global__ void __launch_bounds__(128) primary_bin_kernel(SceneView sc, RasterCo
     const uint32_t tile = (uint32_t)(px.y / kTileH) * b.tiles_x + (uint32_t)(px.x / kTileW);
     const uint32_t o0 = b.offset[tile], o1 = b.offset[tile + 1];
     unsigned long long key = ~0ull;
-    if (o1 - o0 <= (uint32_t)kMaxBin && o1 <= b.cap) {
+    // bins are complete unless the big-triangle list overflowed
+    if (o1 - o0 <= (uint32_t)kMaxBin && o1 <= b.cap && b.big[0] <= b.big_cap) {
         float best_t = INFINITY;
         uint32_t best_o = 0xFFFFFFFFu;
         for (uint32_t j = o0; j < o1; ++j) {
@@ -394,7 +421,8 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     b.n_tiles = (uint32_t)b.tiles_x * (uint32_t)((H + kTileH - 1) / kTileH);
     b.n_blocks = (b.n_tiles + kScanBlock - 1) / kScanBlock;
     const uint64_t words = (uint64_t)W * H;                  // the mesh-id buffer
-    const uint64_t fixed = 2ull * b.n_tiles + 1 + b.n_blocks;
+    b.big_cap = (uint32_t)std::min<uint64_t>(4096, std::max<uint64_t>(16, words / 64));
+    const uint64_t fixed = 2ull * b.n_tiles + 1 + b.n_blocks + 1 + b.big_cap;
     if (words < fixed + 256) return DHR_OK;                  // too small: traverse
     double inv[3][3];
     for (int r = 0; r < 3; ++r)
@@ -421,15 +449,18 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     b.count = w;
     b.offset = w + b.n_tiles;
     b.bsum = b.offset + b.n_tiles + 1;
-    b.list = b.bsum + b.n_blocks;
+    b.big = b.bsum + b.n_blocks;
+    b.list = b.big + 1 + b.big_cap;
     b.cap = (uint32_t)std::min<uint64_t>(words - fixed, 0xFFFFFFFFull);
     const unsigned tri_blocks = (sc->n_tris + 127) / 128;
-    bin_clear_kernel<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.count, b.n_tiles);
+    bin_clear_kernel<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.count, b.n_tiles, b.big);
     bin_kernel<true><<<tri_blocks, 128, 0, st>>>(sc->view(), rc, b);
+    bin_big_kernel<true><<<kBigGrid, 128, 0, st>>>(sc->view(), rc, b);
     scan_block_kernel<<<b.n_blocks, kScanBlock, 0, st>>>(b.count, b.offset, b.bsum, b.n_tiles);
     scan_top_kernel<<<1, kScanBlock, 0, st>>>(b.bsum, b.n_blocks, b.offset, b.n_tiles);
     scan_add_kernel<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.offset, b.bsum, b.n_tiles);
     bin_kernel<false><<<tri_blocks, 128, 0, st>>>(sc->view(), rc, b);
+    bin_big_kernel<false><<<kBigGrid, 128, 0, st>>>(sc->view(), rc, b);
     const dim3 grid((W + 15) / 16, (H + 7) / 8);
     auto* zb = reinterpret_cast<unsigned long long*>(g->depth_normal);
     if (g->precision == DHR_FP16) primary_bin_kernel<true><<<grid, 128, 0, st>>>(sc->view(), rc, b, zb);
