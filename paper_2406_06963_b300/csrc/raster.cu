@@ -29,6 +29,7 @@ struct RasterConsts {
     float3 eye;
     float3 mf, mr, mu;          // rows of [forward | right | up]^-1: (a_f, a_r, a_u) of P - eye
     float kx, ky;               // tan(half fov) * aspect, tan(half fov)
+    float inv_kx, inv_ky;
     float sx_lo, sx_hi, sy_lo, sy_hi;   // pixel-centre range widened by one pixel
     int tiles_x;
 };
@@ -59,9 +60,12 @@ __device__ __forceinline__ void add_point(const RasterConsts& rc, float3 p, floa
         ymax = fmaxf(ymax, (float)H);
         return;
     }
-    // pixel coordinates of the direction (sx, sy) = (a_r, a_u) / a_f
-    const float px = (p.y / p.x / rc.kx + 1.0f) * (0.5f * W) - 0.5f;
-    const float py = (1.0f - p.z / p.x / rc.ky) * (0.5f * H) - 0.5f;
+    // pixel coordinates of the direction (sx, sy) = (a_r, a_u) / a_f; an
+    // approximate reciprocal (relative error ~1e-7, ~1e-4 pixel) is well
+    // inside the box's margin
+    const float ir = __fdividef(1.0f, p.x);
+    const float px = (p.y * ir * rc.inv_kx + 1.0f) * (0.5f * W) - 0.5f;
+    const float py = (1.0f - p.z * ir * rc.inv_ky) * (0.5f * H) - 0.5f;
     xmin = fminf(xmin, px);
     xmax = fmaxf(xmax, px);
     ymin = fminf(ymin, py);
@@ -198,6 +202,9 @@ struct BinLayout {
 // round trips overlap.
 constexpr int kBatch = 8;
 
+// list entries: leaf index | kThinBit for a triangle of (near) zero area
+constexpr uint32_t kThinBit = 0x80000000u;
+
 template <bool kCount>
 __device__ __forceinline__ void bin_tiles(const BinLayout& b, int tx0, int ty0, int ntx, int first, int step, int n,
                                           uint32_t leaf) {
@@ -229,15 +236,18 @@ __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc,
     const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    uint32_t entry = (uint32_t)leaf;
     if (leaf < sc.n_tris) {
         const float4* tr = sc.tris + 3 * leaf;
-        tri_bounds(rc, f3(__ldg(tr)), f3(__ldg(tr + 1)), f3(__ldg(tr + 2)), x0, x1, y0, y1);
+        const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
+        tri_bounds(rc, v0, v1, v2, x0, x1, y0, y1);
+        if (!kCount && sliver(v0, v1, v2)) entry |= kThinBit;
     }
     const bool any = x0 <= x1 && y0 <= y1;
     const int tx0 = x0 / kTileW, tx1 = x1 / kTileW, ty0 = y0 / kTileH, ty1 = y1 / kTileH;
     const int ntx = any ? tx1 - tx0 + 1 : 0, nty = any ? ty1 - ty0 + 1 : 0;
     const int nt = ntx * nty;
-    if (nt > 0 && nt <= 32) bin_tiles<kCount>(b, tx0, ty0, ntx, 0, 1, nt, (uint32_t)leaf);
+    if (nt > 0 && nt <= 32) bin_tiles<kCount>(b, tx0, ty0, ntx, 0, 1, nt, entry);
     if (kCount && nt > kBigTiles) {
         const uint32_t slot = atomicAdd(b.big, 1u);
         if (slot < b.big_cap) b.big[1 + slot] = (uint32_t)leaf;   // else: bins unused (all tiles traversed)
@@ -248,8 +258,8 @@ __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc,
         big &= big - 1;
         const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
         const int s_ntx = __shfl_sync(0xffffffffu, ntx, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
-        const int s_leaf = __shfl_sync(0xffffffffu, leaf, src);
-        bin_tiles<kCount>(b, s_tx0, s_ty0, s_ntx, lane, 32, s_nt, (uint32_t)s_leaf);
+        const uint32_t s_entry = __shfl_sync(0xffffffffu, entry, src);
+        bin_tiles<kCount>(b, s_tx0, s_ty0, s_ntx, lane, 32, s_nt, s_entry);
     }
 }
 
@@ -260,12 +270,14 @@ __global__ void __launch_bounds__(128) bin_big_kernel(SceneView sc, RasterConsts
     for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
         const uint32_t leaf = b.big[1 + k];
         const float4* tr = sc.tris + 3 * (size_t)leaf;
+        const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
         int x0, x1, y0, y1;
-        tri_bounds(rc, f3(__ldg(tr)), f3(__ldg(tr + 1)), f3(__ldg(tr + 2)), x0, x1, y0, y1);
+        tri_bounds(rc, v0, v1, v2, x0, x1, y0, y1);
+        const uint32_t entry = leaf | (sliver(v0, v1, v2) ? kThinBit : 0u);
         if (x0 > x1 || y0 > y1) continue;   // not for a listed triangle (same bounds as when listed)
         const int tx0 = x0 / kTileW, ty0 = y0 / kTileH;
         const int ntx = x1 / kTileW - tx0 + 1, nt = ntx * (y1 / kTileH - ty0 + 1);
-        bin_tiles<kCount>(b, tx0, ty0, ntx, threadIdx.x, blockDim.x, nt, leaf);
+        bin_tiles<kCount>(b, tx0, ty0, ntx, threadIdx.x, blockDim.x, nt, entry);
     }
 }
 
@@ -361,12 +373,12 @@ __global__ void __launch_bounds__(128) primary_bin_kernel(SceneView sc, RasterCo
         float best_t = INFINITY;
         uint32_t best_o = 0xFFFFFFFFu;
         for (uint32_t j = o0; j < o1; ++j) {
-            const uint32_t lf = b.list[j];
+            const uint32_t e = b.list[j], lf = e & ~kThinBit;
             if (lf >= (uint32_t)sc.n_tris) continue;   // only if the 32-bit offsets wrapped
             const float4* tr = sc.tris + 3 * (size_t)lf;
             const float4 p0 = __ldg(tr), p1 = __ldg(tr + 1), p2 = __ldg(tr + 2);
             const float3 v0 = f3(p0), v1 = f3(p1), v2 = f3(p2);
-            if (sliver(v0, v1, v2) && !leaf_box_hit(r, v0, v1, v2)) continue;
+            if ((e & kThinBit) && !leaf_box_hit(r, v0, v1, v2)) continue;
             float t;
             float3 bc;
             if (!hit_triangle(r, v0, v1, v2, 0.0f, INFINITY, t, bc)) continue;
@@ -439,6 +451,8 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     const double kx = (double)cam->tan_half_fov_y * ((double)W / (double)H), ky = cam->tan_half_fov_y;
     rc.kx = (float)kx;
     rc.ky = (float)ky;
+    rc.inv_kx = (float)(1.0 / kx);
+    rc.inv_ky = (float)(1.0 / ky);
     // pixel centres x in [-1, W] and y in [-1, H] (one pixel beyond the image), widened by 1e-3
     rc.sx_hi = (float)((1.0 + 1.0 / W) * kx * 1.001);
     rc.sx_lo = -rc.sx_hi;
