@@ -293,6 +293,14 @@ dhr_status dhr_trace_visibility_selective(const dhr_scene* scene, const dhr_came
                                           dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out,
                                           uint8_t* ao_count_out, uint8_t* ray_mask_out, void* stream);
 
+/* dhr_trace_visibility (same arguments, outputs and errors) timed on the
+ * device: ms (host, 2 values) receives the time of the primary-visibility
+ * pre-pass (the rasteriser's kernels; about 0 when traversed) and of the
+ * trace kernel.  Synchronises `stream`. */
+dhr_status dhr_trace_timed(const dhr_scene* scene, const dhr_camera* cam, const dhr_trace_params* params,
+                           dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out, uint8_t* ao_count_out,
+                           float* ms, void* stream);
+
 /* Sampling check entry: for each of n (px, py) and the given frame, seed
  * and sample index, the accepted disk point and the binary32 AO direction
  * about normals[i] (ray type 1) and the shadow direction about `light`

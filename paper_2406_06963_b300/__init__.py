@@ -84,6 +84,7 @@ _SIGNATURES = {
     "dhr_trace_visibility": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_cast_rays": ([_P, _P, _P, _P, _P, C.c_int32, C.c_int64, _P, _P, _P], C.c_int),
     "dhr_trace_stats": ([_P, _P, _P, _P, _P], C.c_int),
+    "dhr_trace_timed": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_gbuffer_convert": ([_P, _P, _P], C.c_int),
     "dhr_sample_directions": ([_P, _P, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32, _P, _P,
                                C.c_float, _P, _P, _P, _P, _P], C.c_int),
@@ -373,6 +374,18 @@ def trace_visibility_selective(scene: Scene, cam, params: TraceParams, maps, gbu
         arr[k] = m.h.value if m is not None else None
     _check(lib().dhr_trace_visibility_selective(scene.h, C.byref(c), C.byref(p), arr, C.byref(g), _ptr(mask),
                                                 _ptr(ao), _ptr(ray_mask), _stream(stream)))
+
+
+def trace_timed(scene: Scene, cam, params: TraceParams, gbuf: GBuffer, mask, ao, stream=None):
+    """trace_visibility timed on the device: (primary pre-pass ms, trace kernel ms)."""
+    _need_cuda(gbuf.depth_normal, gbuf.mesh, mask, ao)
+    c = camera(cam)
+    p = params.to_c()
+    g = gbuf.c()
+    ms = (C.c_float * 2)()
+    _check(lib().dhr_trace_timed(scene.h, C.byref(c), C.byref(p), C.byref(g), _ptr(mask), _ptr(ao), ms,
+                                 _stream(stream)))
+    return float(ms[0]), float(ms[1])
 
 
 def trace_stats(scene: Scene, cam, params: TraceParams, stream=None) -> dict:

@@ -112,16 +112,25 @@ extern "C" dhr_status dhr_scene_get_info(const dhr_scene* sc, dhr_scene_info* ou
 }
 
 // ------------------------------------------------------------------ trace
-extern "C" dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_camera* cam,
-                                           const dhr_trace_params* params, dhr_gbuffer* gbuf_out,
-                                           uint8_t* shadow_mask_out, uint8_t* ao_count_out, void* stream) {
-    clear_error();
+namespace dhr {
+dhr_status dhr_trace_visibility_events(const dhr_scene* scene, const dhr_camera* cam, const dhr_trace_params* params,
+                                       dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out, uint8_t* ao_count_out,
+                                       cudaStream_t st, cudaEvent_t after_primary) {
     DHR_CHECK_ARG(scene, "trace_visibility: null scene");
     DHR_TRY(check_camera(cam));
     DHR_TRY(check_trace_params(params));
     DHR_TRY(check_gbuffer(gbuf_out, cam->width, cam->height));
     DHR_CHECK_ARG(shadow_mask_out && ao_count_out, "trace_visibility: null output");
-    return launch_trace(scene, cam, params, gbuf_out, shadow_mask_out, ao_count_out, as_stream(stream));
+    return launch_trace(scene, cam, params, gbuf_out, shadow_mask_out, ao_count_out, st, nullptr, after_primary);
+}
+}  // namespace dhr
+
+extern "C" dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_camera* cam,
+                                           const dhr_trace_params* params, dhr_gbuffer* gbuf_out,
+                                           uint8_t* shadow_mask_out, uint8_t* ao_count_out, void* stream) {
+    clear_error();
+    return dhr_trace_visibility_events(scene, cam, params, gbuf_out, shadow_mask_out, ao_count_out,
+                                       as_stream(stream), nullptr);
 }
 
 extern "C" dhr_status dhr_trace_visibility_selective(const dhr_scene* scene, const dhr_camera* cam,

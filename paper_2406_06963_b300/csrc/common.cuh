@@ -143,9 +143,16 @@ namespace dhr {
 dhr_status build_lbvh(const float* verts_d, const uint32_t* idx_d, const uint32_t* mesh_d,
                       uint32_t n_verts, uint32_t n_tris, cudaStream_t st, dhr_scene* sc, uint32_t builder);
 
+// after_primary (optional): recorded on st once the primary pre-pass (if any)
+// is enqueued, before the trace kernel
 dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
                         dhr_gbuffer* g, uint8_t* mask, uint8_t* ao, cudaStream_t st,
-                        unsigned long long* stats = nullptr);
+                        unsigned long long* stats = nullptr, cudaEvent_t after_primary = nullptr);
+
+// dhr_trace_visibility's checks and launch, with launch_trace's event
+dhr_status dhr_trace_visibility_events(const dhr_scene* scene, const dhr_camera* cam, const dhr_trace_params* params,
+                                       dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out, uint8_t* ao_count_out,
+                                       cudaStream_t st, cudaEvent_t after_primary);
 
 dhr_status launch_trace_selective(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
                                   const dhr_shadow_map* const* maps, dhr_gbuffer* g, uint8_t* mask, uint8_t* ao,

@@ -76,7 +76,7 @@ dhr_status check_trace_params(const dhr_trace_params* p) {
 
 dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_trace_params* p,
                         dhr_gbuffer* g, uint8_t* mask, uint8_t* ao, cudaStream_t st,
-                        unsigned long long* stats) {
+                        unsigned long long* stats, cudaEvent_t after_primary) {
     const TraceConsts k = make_trace_consts(*cam, *p);
     const dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
     if (stats) {
@@ -87,6 +87,7 @@ dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_tr
     }
     bool raster = false;
     if (p->primary == DHR_PRIMARY_RASTER) DHR_TRY(launch_raster(sc, cam, g, st, &raster));
+    if (after_primary) DHR_CUDA_TRY(cudaEventRecord(after_primary, st));
     auto* dn = g->depth_normal;
     if (g->precision == DHR_FP16) {
         if (raster) trace_kernel<true, false, true><<<grid, 128, 0, st>>>(sc->view(), k, dn, g->mesh_id, mask, ao);
@@ -169,5 +170,29 @@ extern "C" dhr_status dhr_trace_stats(const dhr_scene* scene, const dhr_camera* 
     cudaFree(mesh);
     cudaFree(mb);
     if (e) return set_error(DHR_ERR_CUDA, "trace_stats: %s", cudaGetErrorString(e));
+    return s;
+}
+
+extern "C" dhr_status dhr_trace_timed(const dhr_scene* scene, const dhr_camera* cam, const dhr_trace_params* params,
+                                      dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out, uint8_t* ao_count_out,
+                                      float* ms, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(ms, "trace_timed: null ms");
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < 3 && !err; ++i) err = cudaEventCreate(&e[i]);
+    dhr_status s = DHR_OK;
+    if (!err) err = cudaEventRecord(e[0], st);
+    if (!err) {
+        s = dhr_trace_visibility_events(scene, cam, params, gbuf_out, shadow_mask_out, ao_count_out, st, e[1]);
+        if (s == DHR_OK) err = cudaEventRecord(e[2], st);
+    }
+    if (s == DHR_OK && !err) err = cudaEventSynchronize(e[2]);
+    if (s == DHR_OK && !err) err = cudaEventElapsedTime(&ms[0], e[0], e[1]);
+    if (s == DHR_OK && !err) err = cudaEventElapsedTime(&ms[1], e[1], e[2]);
+    for (int i = 0; i < 3; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    if (err) return set_error(DHR_ERR_CUDA, "trace_timed: %s", cudaGetErrorString(err));
     return s;
 }

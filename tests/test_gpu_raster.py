@@ -127,3 +127,19 @@ def test_bad_primary_mode_rejected(boxes):
     with pytest.raises(dhrs.DhrError) as e:
         _run(boxes, cam, dhrs.TraceParams(primary=2))
     assert e.value.status == 1
+
+
+def test_trace_timed_outputs_and_parts(boxes):
+    """dhr_trace_timed: the same outputs as dhr_trace_visibility, and the two
+    device times (primary pre-pass ~0 when traversed)."""
+    cam = wl.boxes_camera(200, 150)
+    ref = _run(boxes, cam, dhrs.TraceParams(frame=6))
+    g = dhrs.GBuffer(200, 150)
+    mask = torch.empty((150, 200), dtype=torch.uint8, device="cuda")
+    ao = torch.empty_like(mask)
+    pre, ker = dhrs.trace_timed(boxes, cam, dhrs.TraceParams(frame=6), g, mask, ao)
+    assert pre > 0.0 and ker > 0.0
+    assert np.array_equal(g.depth_normal.cpu().numpy().view(np.uint8), ref["dn"])
+    assert np.array_equal(mask.cpu().numpy(), ref["mask"]) and np.array_equal(ao.cpu().numpy(), ref["ao"])
+    pre_t, ker_t = dhrs.trace_timed(boxes, cam, dhrs.TraceParams(frame=6, primary=dhrs.PRIMARY_TRAVERSE), g, mask, ao)
+    assert 0.0 <= pre_t < 0.05 and ker_t > 0.0
