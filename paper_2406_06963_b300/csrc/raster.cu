@@ -9,8 +9,9 @@
 // traversed instead, with the same result.
 //
 // Passes (all on the caller's stream): clear the tile counts; count (one
-// thread per triangle, or one warp for a triangle spanning many tiles); an
-// exclusive scan of the counts; fill; then one thread per pixel writes the
+// thread per triangle, one warp for a triangle over more than 32 tiles, one
+// block for one over more than kBigTiles); an exclusive scan of the counts;
+// fill (the same split); then one thread per pixel writes the
 // key (t bits << 32 | original index, ~0 for none) into the G-buffer's depth
 // storage, which the trace kernel reads before it overwrites it.  Counts,
 // offsets and lists live in the mesh-id buffer (the trace kernel overwrites
@@ -31,7 +32,6 @@ struct RasterConsts {
     float kx, ky;               // tan(half fov) * aspect, tan(half fov)
     float inv_kx, inv_ky;
     float sx_lo, sx_hi, sy_lo, sy_hi;   // pixel-centre range widened by one pixel
-    int tiles_x;
 };
 
 __device__ __forceinline__ float3 cam_coords(const RasterConsts& rc, float3 p) {
@@ -155,7 +155,9 @@ __device__ __forceinline__ void tri_bounds(const RasterConsts& rc, float3 v0, fl
 // The traversal only tests a triangle whose leaf box the ray passes (slab2).
 // For a triangle of (near) zero area the watertight test's edge functions are
 // rounding noise and could report a hit that the box test rules out, so such
-// triangles take the same box test here (scalar form of slab2's lanes).
+// triangles take the same box test here (scalar form of slab2's lanes, with
+// tmax = +inf: the traversal's tmax is the best hit so far, and a box beyond
+// it holds no hit that could win).
 __device__ __forceinline__ bool sliver(float3 v0, float3 v1, float3 v2) {
     const float3 e1 = sub(v1, v0), e2 = sub(v2, v0), c = cross(e1, e2);
     return !(dot(c, c) > 1e-12f * dot(e1, e1) * dot(e2, e2));
@@ -458,7 +460,6 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     rc.sx_lo = -rc.sx_hi;
     rc.sy_hi = (float)((1.0 + 1.0 / H) * ky * 1.001);
     rc.sy_lo = -rc.sy_hi;
-    rc.tiles_x = b.tiles_x;
     uint32_t* w = g->mesh_id;
     b.count = w;
     b.offset = w + b.n_tiles;
