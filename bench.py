@@ -323,7 +323,8 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": ws, "steps": K,
         "warmup": Wm, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(bench_config(ws, info["n_triangles"]), primary_visibility=args.primary),
+        "config": bench_config(ws, info["n_triangles"]),
+        "primary_visibility": args.primary,
         "ms_per_frame": {"trace_svgf": round(total_ms / K, 4), "trace": round(trace_ms, 4),
                          "trace_session_form": round(statistics.mean(tr_sess_ms), 4),
                          "trace_session_form_parts": {"primary_prepass": round(statistics.mean(tr_pre_ms), 4),
