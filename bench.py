@@ -366,9 +366,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * 4 * W * H,
                 "ms_per_step": round(e2e_s * 1e3 / K, 4)},
         "transport": transport,
-        # per session frame: trace (+ clear, count, 3 scans, fill and per-tile
-        # primary kernels when rasterised), temporal, 5 a-trous levels
-        "gpu_launches": (14 if primary == dhrs.PRIMARY_RASTER else 7) * K,
+        # per session frame: trace (+ clear, count, big-triangle count, 3 scans,
+        # fill, big-triangle fill and per-tile primary kernels when rasterised),
+        # temporal, 5 a-trous levels
+        "gpu_launches": (16 if primary == dhrs.PRIMARY_RASTER else 7) * K,
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }
