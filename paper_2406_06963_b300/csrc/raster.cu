@@ -1,21 +1,20 @@
 // Rasterised primary visibility.  The paper's clients rasterise the G-buffer
 // (Section 1, Section 3.3).  Here every triangle is binned into the 8 x 4-pixel
 // tiles its clipped screen bounds overlap (one warp of the trace covers one
-// such tile), and the warp of a tile tests its 32 pixel-centre rays against
-// the tile's list with the same watertight test (hit_triangle) and the same
-// rays (primary_dir) as the traversal, keeping per pixel the smallest
-// (t, original index): the traversal's closest hit, bit for bit.  A tile
-// whose list is longer than kMaxBin (far, dense geometry) or did not fit is
-// traversed instead, with the same result.
+// such tile); the trace kernel's warp then tests its 32 pixel-centre rays
+// against the tile's list with the same watertight test (hit_triangle) and
+// the same rays (primary_dir) as the traversal, keeping per pixel the
+// smallest (t, original index): the traversal's closest hit, bit for bit.  A
+// tile whose list is longer than kMaxBin (far, dense geometry) or did not fit
+// is traversed instead, with the same result.
 //
-// Passes (all on the caller's stream): clear the tile counts; count (one
-// thread per triangle, one warp for a triangle over more than 32 tiles, one
-// block for one over more than kBigTiles); an exclusive scan of the counts;
-// fill (the same split); then one thread per pixel writes the
-// key (t bits << 32 | original index, ~0 for none) into the G-buffer's depth
-// storage, which the trace kernel reads before it overwrites it.  Counts,
-// offsets and lists live in the mesh-id buffer (the trace kernel overwrites
-// it afterwards), so the rasteriser needs no memory of its own.
+// Each tile's list lives in the tile's own G-buffer depth storage (TileStore
+// in trace_device.cuh), so the rasteriser needs no memory of its own; the
+// list of big triangles (binned by whole blocks) lives in the mesh-id
+// buffer.  Passes (all on the caller's stream): clear the tile counts; bin
+// (one thread per triangle, one warp for a triangle over more than 32 tiles;
+// one over more than kBigTiles is listed); bin the listed big triangles, one
+// block each.
 #include <cmath>
 
 #include "trace_device.cuh"
@@ -152,88 +151,45 @@ __device__ __forceinline__ void tri_bounds(const RasterConsts& rc, float3 v0, fl
     y1 = (int)fy1;
 }
 
-// The traversal only tests a triangle whose leaf box the ray passes (slab2).
-// For a triangle of (near) zero area the watertight test's edge functions are
-// rounding noise and could report a hit that the box test rules out, so such
-// triangles take the same box test here (scalar form of slab2's lanes, with
-// tmax = +inf: the traversal's tmax is the best hit so far, and a box beyond
-// it holds no hit that could win).
-__device__ __forceinline__ bool sliver(float3 v0, float3 v1, float3 v2) {
-    const float3 e1 = sub(v1, v0), e2 = sub(v2, v0), c = cross(e1, e2);
-    return !(dot(c, c) > 1e-12f * dot(e1, e1) * dot(e2, e2));
-}
-
-__device__ __forceinline__ bool leaf_box_hit(const Ray& r, float3 v0, float3 v1, float3 v2) {
-    const float3 lo = make_float3(fminf(fminf(v0.x, v1.x), v2.x), fminf(fminf(v0.y, v1.y), v2.y),
-                                  fminf(fminf(v0.z, v1.z), v2.z));
-    const float3 hi = make_float3(fmaxf(fmaxf(v0.x, v1.x), v2.x), fmaxf(fmaxf(v0.y, v1.y), v2.y),
-                                  fmaxf(fmaxf(v0.z, v1.z), v2.z));
-    const float2 ix = unpack2(r.idir2[0]), iy = unpack2(r.idir2[1]), iz = unpack2(r.idir2[2]);
-    const float2 nx = unpack2(r.noid2[0]), ny = unpack2(r.noid2[1]), nz = unpack2(r.noid2[2]);
-    const float lx = fmaf(lo.x, ix.x, nx.x), hx = fmaf(hi.x, ix.x, nx.x);
-    const float ly = fmaf(lo.y, iy.x, ny.x), hy = fmaf(hi.y, iy.x, ny.x);
-    const float lz = fmaf(lo.z, iz.x, nz.x), hz = fmaf(hi.z, iz.x, nz.x);
-    const float tn = max3(fminf(lx, hx), fminf(ly, hy), fmaxf(fminf(lz, hz), 0.0f));
-    const float tf = min3(fmaxf(lx, hx), fmaxf(ly, hy), fminf(fmaxf(lz, hz), INFINITY));
-    return tn <= tf * 1.00000024f;
-}
-
 // ---------------------------------------------------------------- binning
-constexpr int kTileW = 8, kTileH = 4;   // the trace's warp tile
-constexpr int kMaxBin = 48;             // longer lists: traverse the tile
-constexpr int kScanBlock = 1024;
-
 constexpr int kBigTiles = 256;          // more tiles: binned by a whole block
 constexpr int kBigGrid = 148 * 4;
 
 struct BinLayout {
-    uint32_t* count;     // [n_tiles]
-    uint32_t* offset;    // [n_tiles + 1], exclusive scan of count
-    uint32_t* bsum;      // [n_blocks] block totals of the scan
+    TileStore ts;        // the tiles' lists (G-buffer depth storage)
     uint32_t* big;       // [1 + big_cap]: number of big triangles, then their leaves
-    uint32_t* list;      // [cap] leaf indices, tile by tile
-    uint32_t n_tiles, n_blocks, big_cap, cap;
-    int tiles_x;
+    uint32_t big_cap;
+    int tiles_x, n_tiles;
 };
 
-// Tiles first + step, first + 2 step, ... (below n) of a triangle whose
-// tiles form ntx columns from (tx0, ty0): kCount adds 1 to each tile's count
-// (no value returned); else each takes a slot by atomicSub and stores the
-// leaf there (dropped beyond the list's capacity: that tile is then
-// traversed).  The slot atomics are issued kBatch at a time so that their
-// round trips overlap.
+// Tiles first + step, first + 2 step, ... (below n) of a triangle whose tiles
+// form ntx columns from (tx0, ty0): each takes the next slot of its tile's
+// list (the returned count) and, if the list has room, stores the entry
+// there; a count beyond the room makes the trace traverse that tile.  The
+// slot atomics are issued kBatch at a time so that their round trips overlap.
 constexpr int kBatch = 8;
 
-// list entries: leaf index | kThinBit for a triangle of (near) zero area
-constexpr uint32_t kThinBit = 0x80000000u;
-
-template <bool kCount>
 __device__ __forceinline__ void bin_tiles(const BinLayout& b, int tx0, int ty0, int ntx, int first, int step, int n,
-                                          uint32_t leaf) {
+                                          uint32_t entry) {
     for (int i0 = first; i0 < n; i0 += step * kBatch) {
-        uint32_t tile[kBatch], slot[kBatch];
+        int tx[kBatch], ty[kBatch];
+        uint32_t slot[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int i = i0 + u * step;
-            tile[u] = i < n ? (uint32_t)((ty0 + i / ntx) * b.tiles_x + tx0 + i % ntx) : 0u;
-            if (i >= n) continue;
-            if (kCount) atomicAdd(b.count + tile[u], 1u);
-            else slot[u] = atomicSub(b.count + tile[u], 1u);
+            tx[u] = tx0 + (i < n ? i % ntx : 0);
+            ty[u] = ty0 + (i < n ? i / ntx : 0);
+            if (i < n) slot[u] = atomicAdd(tile_word(b.ts, tx[u], ty[u], 0), 1u);
         }
-        if (kCount) continue;
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (i0 + u * step >= n) continue;
-            const uint32_t pos = b.offset[tile[u]] + slot[u] - 1u;
-            if (pos < b.cap) b.list[pos] = leaf;
+            if (slot[u] < (uint32_t)tile_capacity(b.ts, tx[u], ty[u]))
+                *tile_word(b.ts, tx[u], ty[u], (int)slot[u] + 1) = entry;
         }
     }
 }
 
-// One thread per triangle; a triangle overlapping more than 32 tiles is
-// binned by its whole warp (lanes stride over its tiles), one overlapping
-// more than kBigTiles is listed (count pass) for bin_big_kernel.
-template <bool kCount>
 __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
     const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -243,16 +199,16 @@ __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc,
         const float4* tr = sc.tris + 3 * leaf;
         const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
         tri_bounds(rc, v0, v1, v2, x0, x1, y0, y1);
-        if (!kCount && sliver(v0, v1, v2)) entry |= kThinBit;
+        if (sliver(v0, v1, v2)) entry |= kThinBit;
     }
     const bool any = x0 <= x1 && y0 <= y1;
-    const int tx0 = x0 / kTileW, tx1 = x1 / kTileW, ty0 = y0 / kTileH, ty1 = y1 / kTileH;
+    const int tx0 = x0 / kRasterTileW, tx1 = x1 / kRasterTileW, ty0 = y0 / kRasterTileH, ty1 = y1 / kRasterTileH;
     const int ntx = any ? tx1 - tx0 + 1 : 0, nty = any ? ty1 - ty0 + 1 : 0;
     const int nt = ntx * nty;
-    if (nt > 0 && nt <= 32) bin_tiles<kCount>(b, tx0, ty0, ntx, 0, 1, nt, entry);
-    if (kCount && nt > kBigTiles) {
+    if (nt > 0 && nt <= 32) bin_tiles(b, tx0, ty0, ntx, 0, 1, nt, entry);
+    if (nt > kBigTiles) {
         const uint32_t slot = atomicAdd(b.big, 1u);
-        if (slot < b.big_cap) b.big[1 + slot] = (uint32_t)leaf;   // else: bins unused (all tiles traversed)
+        if (slot < b.big_cap) b.big[1 + slot] = (uint32_t)leaf;   // else: bin_big_kernel marks every tile
     }
     unsigned big = __ballot_sync(0xffffffffu, nt > 32 && nt <= kBigTiles);
     while (big) {
@@ -261,143 +217,38 @@ __global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc,
         const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
         const int s_ntx = __shfl_sync(0xffffffffu, ntx, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
         const uint32_t s_entry = __shfl_sync(0xffffffffu, entry, src);
-        bin_tiles<kCount>(b, s_tx0, s_ty0, s_ntx, lane, 32, s_nt, s_entry);
+        bin_tiles(b, s_tx0, s_ty0, s_ntx, lane, 32, s_nt, s_entry);
     }
 }
 
-// the listed big triangles, one block each (threads stride over its tiles)
-template <bool kCount>
+// the listed big triangles, one block each (threads stride over its tiles);
+// if the list overflowed, the bins are incomplete and every tile is marked
+// to be traversed instead
 __global__ void __launch_bounds__(128) bin_big_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
-    const uint32_t n = min(b.big[0], b.big_cap);
-    for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) {
+    const uint32_t nb = b.big[0];
+    if (nb > b.big_cap) {
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < b.n_tiles; t += gridDim.x * blockDim.x)
+            *tile_word(b.ts, t % b.tiles_x, t / b.tiles_x, 0) = 0xFFFFFFFFu;
+        return;
+    }
+    for (uint32_t k = blockIdx.x; k < nb; k += gridDim.x) {
         const uint32_t leaf = b.big[1 + k];
         const float4* tr = sc.tris + 3 * (size_t)leaf;
         const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
         int x0, x1, y0, y1;
         tri_bounds(rc, v0, v1, v2, x0, x1, y0, y1);
-        const uint32_t entry = leaf | (sliver(v0, v1, v2) ? kThinBit : 0u);
         if (x0 > x1 || y0 > y1) continue;   // not for a listed triangle (same bounds as when listed)
-        const int tx0 = x0 / kTileW, ty0 = y0 / kTileH;
-        const int ntx = x1 / kTileW - tx0 + 1, nt = ntx * (y1 / kTileH - ty0 + 1);
-        bin_tiles<kCount>(b, tx0, ty0, ntx, threadIdx.x, blockDim.x, nt, entry);
+        const uint32_t entry = leaf | (sliver(v0, v1, v2) ? kThinBit : 0u);
+        const int tx0 = x0 / kRasterTileW, ty0 = y0 / kRasterTileH;
+        const int ntx = x1 / kRasterTileW - tx0 + 1, nt = ntx * (y1 / kRasterTileH - ty0 + 1);
+        bin_tiles(b, tx0, ty0, ntx, threadIdx.x, blockDim.x, nt, entry);
     }
 }
 
-__global__ void bin_clear_kernel(uint32_t* count, uint32_t n, uint32_t* big) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) count[i] = 0u;
-    if (i == 0) big[0] = 0u;
-}
-
-// exclusive scan of count into offset, 1024 elements per block; block totals to bsum
-__global__ void __launch_bounds__(kScanBlock) scan_block_kernel(const uint32_t* count, uint32_t* offset, uint32_t* bsum,
-                                                                uint32_t n) {
-    __shared__ uint32_t warp_tot[32];
-    const uint32_t i = blockIdx.x * kScanBlock + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t v = i < n ? count[i] : 0u;
-    uint32_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t t = warp_tot[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += y;
-        }
-        warp_tot[lane] = t;   // inclusive totals of warps 0..lane
-    }
-    __syncthreads();
-    const uint32_t before = (warp ? warp_tot[warp - 1] : 0u) + x - v;
-    if (i < n) offset[i] = before;
-    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = warp_tot[31];
-}
-
-// exclusive scan of the block totals (one block, 1024 at a time with a carry);
-// offset[n] = the grand total
-__global__ void __launch_bounds__(kScanBlock) scan_top_kernel(uint32_t* bsum, uint32_t nb, uint32_t* offset, uint32_t n) {
-    __shared__ uint32_t warp_tot[32];
-    __shared__ uint32_t carry;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0u;
-    __syncthreads();
-    for (uint32_t base = 0; base < nb; base += kScanBlock) {
-        const uint32_t i = base + threadIdx.x;
-        const uint32_t v = i < nb ? bsum[i] : 0u;
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_tot[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t t = warp_tot[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            warp_tot[lane] = t;
-        }
-        __syncthreads();
-        const uint32_t c = carry;
-        if (i < nb) bsum[i] = c + (warp ? warp_tot[warp - 1] : 0u) + x - v;
-        __syncthreads();
-        if (threadIdx.x == 0) carry = c + warp_tot[31];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) offset[n] = carry;
-}
-
-__global__ void scan_add_kernel(uint32_t* offset, const uint32_t* bsum, uint32_t n) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) offset[i] += bsum[i / kScanBlock];
-}
-
-// One thread per pixel, warps on the trace's 8 x 4 tiles: the closest hit of
-// the pixel-centre ray among the tile's list (or by traversal), as a key.
-template <bool kHalf>
-__global__ void __launch_bounds__(128) primary_bin_kernel(SceneView sc, RasterConsts rc, BinLayout b,
-                                                          unsigned long long* zb) {
-    const int2 px = thread_pixel();
-    const int W = rc.cam.width, H = rc.cam.height;
-    if (px.x >= W || px.y >= H) return;
-    const Ray r = make_ray(rc.eye, primary_dir(rc.cam, px.x, px.y));
-    const uint32_t tile = (uint32_t)(px.y / kTileH) * b.tiles_x + (uint32_t)(px.x / kTileW);
-    const uint32_t o0 = b.offset[tile], o1 = b.offset[tile + 1];
-    unsigned long long key = ~0ull;
-    // bins are complete unless the big-triangle list overflowed
-    if (o1 - o0 <= (uint32_t)kMaxBin && o1 <= b.cap && b.big[0] <= b.big_cap) {
-        float best_t = INFINITY;
-        uint32_t best_o = 0xFFFFFFFFu;
-        for (uint32_t j = o0; j < o1; ++j) {
-            const uint32_t e = b.list[j], lf = e & ~kThinBit;
-            if (lf >= (uint32_t)sc.n_tris) continue;   // only if the 32-bit offsets wrapped
-            const float4* tr = sc.tris + 3 * (size_t)lf;
-            const float4 p0 = __ldg(tr), p1 = __ldg(tr + 1), p2 = __ldg(tr + 2);
-            const float3 v0 = f3(p0), v1 = f3(p1), v2 = f3(p2);
-            if ((e & kThinBit) && !leaf_box_hit(r, v0, v1, v2)) continue;
-            float t;
-            float3 bc;
-            if (!hit_triangle(r, v0, v1, v2, 0.0f, INFINITY, t, bc)) continue;
-            const uint32_t orig = __float_as_uint(p0.w);
-            if (t < best_t || (t == best_t && orig < best_o)) {
-                best_t = t;
-                best_o = orig;
-            }
-        }
-        if (best_o != 0xFFFFFFFFu) key = ((unsigned long long)__float_as_uint(best_t) << 32) | best_o;
-    } else {
-        float tm = INFINITY;
-        float3 bc;
-        const int leaf = traverse<false>(sc, r, 0.0f, tm, bc);
-        if (leaf >= 0) key = ((unsigned long long)__float_as_uint(tm) << 32) | __float_as_uint(__ldg(sc.tris + 3 * leaf).w);
-    }
-    zb[((size_t)px.y * W + px.x) * (kHalf ? 1 : 2)] = key;
+__global__ void bin_clear_kernel(BinLayout b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < b.n_tiles) *tile_word(b.ts, t % b.tiles_x, t / b.tiles_x, 0) = 0u;
+    if (t == 0) b.big[0] = 0u;
 }
 
 __global__ void leaf_map_kernel(const float4* tris, int n, uint32_t* leaf_of) {
@@ -431,13 +282,12 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     if (!(std::fabs(det) > 1e-6) || !(cam->tan_half_fov_y > 0.0f)) return DHR_OK;
     const int W = cam->width, H = cam->height;
     BinLayout b;
-    b.tiles_x = (W + kTileW - 1) / kTileW;
-    b.n_tiles = (uint32_t)b.tiles_x * (uint32_t)((H + kTileH - 1) / kTileH);
-    b.n_blocks = (b.n_tiles + kScanBlock - 1) / kScanBlock;
-    const uint64_t words = (uint64_t)W * H;                  // the mesh-id buffer
-    b.big_cap = (uint32_t)std::min<uint64_t>(4096, std::max<uint64_t>(16, words / 64));
-    const uint64_t fixed = 2ull * b.n_tiles + 1 + b.n_blocks + 1 + b.big_cap;
-    if (words < fixed + 256) return DHR_OK;                  // too small: traverse
+    b.tiles_x = (W + kRasterTileW - 1) / kRasterTileW;
+    const int64_t n_tiles = (int64_t)b.tiles_x * ((H + kRasterTileH - 1) / kRasterTileH);
+    const uint64_t words = (uint64_t)W * H;                  // the mesh-id buffer holds the big list
+    b.big_cap = (uint32_t)std::min<uint64_t>(4096, words / 64);
+    if (b.big_cap < 16 || n_tiles >= (1ll << 31)) return DHR_OK;   // tiny or huge image: traverse
+    b.n_tiles = (int)n_tiles;
     double inv[3][3];
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) {
@@ -460,26 +310,11 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     rc.sx_lo = -rc.sx_hi;
     rc.sy_hi = (float)((1.0 + 1.0 / H) * ky * 1.001);
     rc.sy_lo = -rc.sy_hi;
-    uint32_t* w = g->mesh_id;
-    b.count = w;
-    b.offset = w + b.n_tiles;
-    b.bsum = b.offset + b.n_tiles + 1;
-    b.big = b.bsum + b.n_blocks;
-    b.list = b.big + 1 + b.big_cap;
-    b.cap = (uint32_t)std::min<uint64_t>(words - fixed, 0xFFFFFFFFull);
-    const unsigned tri_blocks = (sc->n_tris + 127) / 128;
-    bin_clear_kernel<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.count, b.n_tiles, b.big);
-    bin_kernel<true><<<tri_blocks, 128, 0, st>>>(sc->view(), rc, b);
-    bin_big_kernel<true><<<kBigGrid, 128, 0, st>>>(sc->view(), rc, b);
-    scan_block_kernel<<<b.n_blocks, kScanBlock, 0, st>>>(b.count, b.offset, b.bsum, b.n_tiles);
-    scan_top_kernel<<<1, kScanBlock, 0, st>>>(b.bsum, b.n_blocks, b.offset, b.n_tiles);
-    scan_add_kernel<<<(b.n_tiles + 255) / 256, 256, 0, st>>>(b.offset, b.bsum, b.n_tiles);
-    bin_kernel<false><<<tri_blocks, 128, 0, st>>>(sc->view(), rc, b);
-    bin_big_kernel<false><<<kBigGrid, 128, 0, st>>>(sc->view(), rc, b);
-    const dim3 grid((W + 15) / 16, (H + 7) / 8);
-    auto* zb = reinterpret_cast<unsigned long long*>(g->depth_normal);
-    if (g->precision == DHR_FP16) primary_bin_kernel<true><<<grid, 128, 0, st>>>(sc->view(), rc, b, zb);
-    else primary_bin_kernel<false><<<grid, 128, 0, st>>>(sc->view(), rc, b, zb);
+    b.ts = TileStore{reinterpret_cast<uint32_t*>(g->depth_normal), W, H, g->precision == DHR_FP16 ? 2 : 4};
+    b.big = g->mesh_id;
+    bin_clear_kernel<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(b);
+    bin_kernel<<<(sc->n_tris + 127) / 128, 128, 0, st>>>(sc->view(), rc, b);
+    bin_big_kernel<<<kBigGrid, 128, 0, st>>>(sc->view(), rc, b);
     DHR_CUDA_TRY(cudaGetLastError());
     *launched = true;
     return DHR_OK;

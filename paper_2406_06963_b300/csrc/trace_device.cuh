@@ -357,6 +357,57 @@ __device__ __forceinline__ float3 primary_dir(const dhr_camera& c, int x, int y)
                        c.forward[2] + sx * c.right[2] + sy * c.up[2]);
 }
 
+// ------------------------------------------ rasterised primary visibility
+// The traversal only tests a triangle whose leaf box the ray passes (slab2).
+// For a triangle of (near) zero area the watertight test's edge functions are
+// rounding noise and could report a hit that the box test rules out, so such
+// triangles take the same box test when rasterised (scalar form of slab2's
+// lanes, with tmax = +inf: the traversal's tmax is the best hit so far, and a
+// box beyond it holds no hit that could win).
+__device__ __forceinline__ bool sliver(float3 v0, float3 v1, float3 v2) {
+    const float3 e1 = sub(v1, v0), e2 = sub(v2, v0), c = cross(e1, e2);
+    return !(dot(c, c) > 1e-12f * dot(e1, e1) * dot(e2, e2));
+}
+
+__device__ __forceinline__ bool leaf_box_hit(const Ray& r, float3 v0, float3 v1, float3 v2) {
+    const float3 lo = make_float3(fminf(fminf(v0.x, v1.x), v2.x), fminf(fminf(v0.y, v1.y), v2.y),
+                                  fminf(fminf(v0.z, v1.z), v2.z));
+    const float3 hi = make_float3(fmaxf(fmaxf(v0.x, v1.x), v2.x), fmaxf(fmaxf(v0.y, v1.y), v2.y),
+                                  fmaxf(fmaxf(v0.z, v1.z), v2.z));
+    const float2 ix = unpack2(r.idir2[0]), iy = unpack2(r.idir2[1]), iz = unpack2(r.idir2[2]);
+    const float2 nx = unpack2(r.noid2[0]), ny = unpack2(r.noid2[1]), nz = unpack2(r.noid2[2]);
+    const float lx = fmaf(lo.x, ix.x, nx.x), hx = fmaf(hi.x, ix.x, nx.x);
+    const float ly = fmaf(lo.y, iy.x, ny.x), hy = fmaf(hi.y, iy.x, ny.x);
+    const float lz = fmaf(lo.z, iz.x, nz.x), hz = fmaf(hi.z, iz.x, nz.x);
+    const float tn = max3(fminf(lx, hx), fminf(ly, hy), fmaxf(fminf(lz, hz), 0.0f));
+    const float tf = min3(fmaxf(lx, hx), fmaxf(ly, hy), fminf(fmaxf(lz, hz), INFINITY));
+    return tn <= tf * 1.00000024f;
+}
+
+// Triangle list of the 8 x 4-pixel tile (tx, ty) (one warp of the trace),
+// kept in the tile's own G-buffer depth storage until the warp overwrites it:
+// the tile's rows of elements (ew 32-bit words each: 4 in FP32, 2 in FP16)
+// one after the other; word 0 = number of entries, words 1.. = entries
+// (leaf index | kThinBit for a triangle of (near) zero area).
+constexpr uint32_t kThinBit = 0x80000000u;
+constexpr int kRasterTileW = 8, kRasterTileH = 4;
+constexpr int kMaxBin = 48;             // longer lists: the tile is traversed
+
+struct TileStore {
+    uint32_t* base;   // the G-buffer depth storage as words
+    int W, H, ew;
+};
+
+__device__ __forceinline__ int tile_row_words(const TileStore& s, int tx) { return min(kRasterTileW, s.W - kRasterTileW * tx) * s.ew; }
+__device__ __forceinline__ int tile_capacity(const TileStore& s, int tx, int ty) {
+    return min(kRasterTileH, s.H - kRasterTileH * ty) * tile_row_words(s, tx) - 1;
+}
+// word k of the tile (the tile's origin must lie inside the image)
+__device__ __forceinline__ uint32_t* tile_word(const TileStore& s, int tx, int ty, int k) {
+    const int wpr = tile_row_words(s, tx);
+    return s.base + ((size_t)(kRasterTileH * ty + k / wpr) * s.W + kRasterTileW * tx) * s.ew + k % wpr;
+}
+
 // Pixel of a thread: each warp covers an 8x4 tile; a 128-thread block
 // covers 16x8 pixels.
 __device__ __forceinline__ int2 thread_pixel() {
@@ -372,15 +423,35 @@ __device__ __forceinline__ int2 thread_pixel() {
 // kSel: shadow rays only for the pixels the lights' shadow maps cannot
 // decide (smap_classify); ray_mask (optional) receives bit l = light l's
 // ray was called for.
-// kRaster: the primary hit comes from the rasterised key in the G-buffer's
-// depth storage (launch_raster) instead of a traversal; the hit is then
-// re-intersected with the same test for its barycentrics.
+// kRaster: the primary hit is the closest among the triangles binned to the
+// warp's tile (launch_raster), read from the tile's G-buffer storage before
+// the warp overwrites it; a tile whose list is too long or did not fit is
+// traversed.
 template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false, bool kRaster = false>
 __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceConsts& k, int2 px, void* gbuf_dn,
                                             uint32_t* gbuf_mesh, uint8_t* mask_out, uint8_t* ao_out,
                                             unsigned long long* stats, const SmapSet* sel = nullptr,
                                             uint8_t* ray_mask = nullptr) {
     const int W = k.cam.width, H = k.cam.height;
+    int n_list = -1;             // kRaster: entries of the warp's tile list to test (-1: traverse)
+    const uint32_t* list = nullptr;
+    if constexpr (kRaster) {
+        // the whole warp copies its tile's list to shared memory before any
+        // lane writes its pixel (which holds part of the list)
+        __shared__ uint32_t s_list[4][kMaxBin];   // 128-thread blocks: 4 warps
+        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+        list = s_list[wib];
+        const int tx = px.x / kRasterTileW, ty = px.y / kRasterTileH;
+        const TileStore ts{reinterpret_cast<uint32_t*>(gbuf_dn), W, H, kHalf ? 2 : 4};
+        if (kRasterTileW * tx < W && kRasterTileH * ty < H) {
+            const uint32_t n = *tile_word(ts, tx, ty, 0);
+            if (n <= (uint32_t)min(kMaxBin, tile_capacity(ts, tx, ty))) {
+                n_list = (int)n;
+                for (int i = lane; i < n_list; i += 32) s_list[wib][i] = *tile_word(ts, tx, ty, i + 1);
+            }
+        }
+        __syncwarp();
+    }
     if (px.x >= W || px.y >= H) return;
     const size_t pix = (size_t)px.y * W + px.x;
     // primary ray through the pixel centre; its parameter is the linear depth
@@ -392,16 +463,29 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
     float3 bary;
     Work wp, ws, wa;
     uint32_t n_sh = 0, n_ao = 0;
-    int leaf;
-    if constexpr (kRaster) {
-        const unsigned long long key =
-            reinterpret_cast<const unsigned long long*>(gbuf_dn)[pix * (kHalf ? 1 : 2)];
-        leaf = -1;
-        if (key != ~0ull) {
-            const int l = (int)__ldg(sc.leaf_of + (uint32_t)key);
-            const float4* tr = sc.tris + 3 * l;
-            if (hit_triangle(pr, f3(__ldg(tr)), f3(__ldg(tr + 1)), f3(__ldg(tr + 2)), 0.0f, INFINITY, tp, bary))
-                leaf = l;
+    int leaf = -1;
+    if (kRaster && n_list >= 0) {
+        // closest hit among the tile's list: smallest (t, original index), as
+        // the traversal's closest hit
+        uint32_t best_o = 0xFFFFFFFFu;
+        for (int j = 0; j < n_list; ++j) {
+            const uint32_t e = list[j];
+            const int lf = (int)(e & ~kThinBit);
+            if (lf >= sc.n_tris) continue;
+            const float4* tr = sc.tris + 3 * lf;
+            const float4 p0 = __ldg(tr), p1 = __ldg(tr + 1), p2 = __ldg(tr + 2);
+            const float3 v0 = f3(p0), v1 = f3(p1), v2 = f3(p2);
+            if ((e & kThinBit) && !leaf_box_hit(pr, v0, v1, v2)) continue;
+            float t;
+            float3 b;
+            if (!hit_triangle(pr, v0, v1, v2, 0.0f, INFINITY, t, b)) continue;
+            const uint32_t orig = __float_as_uint(p0.w);
+            if (t < tp || (t == tp && orig < best_o)) {
+                tp = t;
+                best_o = orig;
+                bary = b;
+                leaf = lf;
+            }
         }
     } else {
         leaf = traverse<false, kStats>(sc, pr, 0.0f, tp, bary, -1, &wp);
