@@ -280,7 +280,12 @@ def run_ours(args):
 
     # rays and traversal work of every frame of the path (counting variant of
     # the trace kernel, run after the timed regions)
-    stats = [dhrs.trace_stats(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=f)) for f in range(N_FRAMES)]
+    stats = [dhrs.trace_stats(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=f, primary=dhrs.PRIMARY_TRAVERSE))
+             for f in range(N_FRAMES)]
+    # the session form's work (rasterised primaries: tile-list tests; only
+    # traversed tiles visit nodes)
+    stats_s = stats if primary == dhrs.PRIMARY_TRAVERSE else \
+        [dhrs.trace_stats(sc, cams[f], dhrs.TraceParams(ao_spp=1, frame=f, primary=primary)) for f in range(N_FRAMES)]
     rays = [sum(s["rays"]) for s in stats]
     sec_rays = [s["rays"][1] + s["rays"][2] for s in stats]
     step_rays = sum(rays[(Wm + i) % N_FRAMES] for i in range(K))
@@ -305,15 +310,12 @@ def run_ours(args):
     ops = visits * 36 + tests * 48
     alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # lane-ops/s, Tops
     achieved = ops / (trace_ms * 1e-3) / 1e12
-    # the session's trace kernel (rasterised primary visibility): shadow and AO
-    # traversals plus one watertight re-test of each foreground pixel's hit
-    # (foreground pixels = AO rays at 1 spp); with traversed primaries, all rays
-    if primary == dhrs.PRIMARY_RASTER:
-        ops_s = statistics.mean(sum(stats[f]["visits"][1:]) * 36 + sum(stats[f]["tests"][1:]) * 48
-                                + stats[f]["rays"][2] * 48 for f in sub)
-        kernel_s = "trace_kernel<0, 0, 1> (shadow + AO rays; primary hits from the rasteriser)"
-    else:
-        ops_s, kernel_s = ops, "trace_kernel<0, 0, 0> (primary + shadow + AO rays)"
+    # the session's trace kernel: with rasterised primaries it tests each
+    # pixel's ray against its tile's list (counted as triangle tests; dense
+    # tiles traversed) and traces the shadow and AO rays
+    ops_s = statistics.mean(sum(stats_s[f]["visits"]) * 36 + sum(stats_s[f]["tests"]) * 48 for f in sub)
+    kernel_s = ("trace_kernel<0, 0, 1> (tile-list primary tests + shadow + AO rays)" if primary == dhrs.PRIMARY_RASTER
+                else "trace_kernel<0, 0, 0> (primary + shadow + AO rays)")
     ker_ms = statistics.mean(tr_ker_ms)
     achieved_s = ops_s / (ker_ms * 1e-3) / 1e12
     traffic_key = "trace_kernel_raster_form" if primary == dhrs.PRIMARY_RASTER else "trace_kernel"
@@ -366,10 +368,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": 2 * 4 * W * H,
                 "ms_per_step": round(e2e_s * 1e3 / K, 4)},
         "transport": transport,
-        # per session frame: trace (+ clear, count, big-triangle count, 3 scans,
-        # fill, big-triangle fill and per-tile primary kernels when rasterised),
-        # temporal, 5 a-trous levels
-        "gpu_launches": (16 if primary == dhrs.PRIMARY_RASTER else 7) * K,
+        # per session frame: trace (+ tile-count clear, binning and big-triangle
+        # binning when rasterised), temporal, 5 a-trous levels
+        "gpu_launches": (10 if primary == dhrs.PRIMARY_RASTER else 7) * K,
         "clocks": clk,
         "wall_s_timed_region": round(t_wall, 3),
     }

@@ -222,7 +222,10 @@ dhr_status dhr_gbuffer_convert(const dhr_gbuffer* src, dhr_gbuffer* dst, void* s
  * counting variant of the trace kernel into scratch buffers it allocates;
  * synchronises `stream`).  counters (host, 9 values): rays traced
  * {primary, shadow, AO}, internal BVH nodes visited {primary, shadow, AO},
- * triangles tested {primary, shadow, AO}.  Errors as dhr_trace_visibility. */
+ * triangles tested {primary, shadow, AO}.  With params->primary =
+ * DHR_PRIMARY_RASTER the primary figures are the rasterised ones: each
+ * tile-list entry a pixel tests counts as a triangle test, and only the
+ * traversed tiles visit nodes.  Errors as dhr_trace_visibility. */
 dhr_status dhr_trace_stats(const dhr_scene* scene, const dhr_camera* cam,
                            const dhr_trace_params* params, uint64_t* counters, void* stream);
 

@@ -80,8 +80,14 @@ dhr_status launch_trace(const dhr_scene* sc, const dhr_camera* cam, const dhr_tr
     const TraceConsts k = make_trace_consts(*cam, *p);
     const dim3 grid((cam->width + 15) / 16, (cam->height + 7) / 8);
     if (stats) {
-        trace_kernel<false, true><<<grid, 128, 0, st>>>(sc->view(), k, g->depth_normal, g->mesh_id, mask, ao,
-                                                        stats);
+        bool raster = false;
+        if (p->primary == DHR_PRIMARY_RASTER) DHR_TRY(launch_raster(sc, cam, g, st, &raster));
+        if (raster)
+            trace_kernel<false, true, true><<<grid, 128, 0, st>>>(sc->view(), k, g->depth_normal, g->mesh_id, mask,
+                                                                  ao, stats);
+        else
+            trace_kernel<false, true><<<grid, 128, 0, st>>>(sc->view(), k, g->depth_normal, g->mesh_id, mask, ao,
+                                                            stats);
         DHR_CUDA_TRY(cudaGetLastError());
         return DHR_OK;
     }

@@ -467,6 +467,7 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
     if (kRaster && n_list >= 0) {
         // closest hit among the tile's list: smallest (t, original index), as
         // the traversal's closest hit
+        if (kStats) wp.tests += (uint32_t)n_list;   // each entry: one triangle test
         uint32_t best_o = 0xFFFFFFFFu;
         for (int j = 0; j < n_list; ++j) {
             const uint32_t e = list[j];
