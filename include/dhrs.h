@@ -113,11 +113,12 @@ typedef struct {
  * screen bounds overlap and tested against those pixels' centre rays with
  * the same watertight test, each pixel keeping the nearest hit (ties: the
  * smaller original triangle index) -- the closest hit of the pixel-centre
- * ray by construction; tiles with long lists are traversed.  Its bins live
- * in the mesh-id buffer and its per-pixel keys in the G-buffer's depth
- * storage, so it needs no memory of its own (images under about 300 pixels
- * are traversed).  Only dhr_trace_visibility(_selective) and sessions honour
- * RASTER; the server and dhr_trace_stats always traverse. */
+ * ray by construction; tiles with long lists are traversed.  Each tile's
+ * list is kept in the tile's own G-buffer depth storage and the list of
+ * screen-filling triangles in the mesh-id buffer, until the trace overwrites
+ * them, so it needs no memory of its own (images under 1024 pixels are
+ * traversed).  dhr_trace_visibility(_selective), dhr_trace_timed,
+ * dhr_trace_stats and sessions honour RASTER; the server always traverses. */
 #define DHR_PRIMARY_RASTER 0u
 #define DHR_PRIMARY_TRAVERSE 1u
 
