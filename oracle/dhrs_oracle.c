@@ -16,7 +16,9 @@
  *     O = N_unoccluded / N (Section 3.2, Eqs. 1-3);
  *   - modified SVGF: temporal reprojection + exponential moving average,
  *     moment variance with a 7x7 depth/normal-weighted spatial fallback, and
- *     edge-stopping a-trous iterations (Section 3.3).
+ *     edge-stopping a-trous iterations (Section 3.3);
+ *   - selective shadow rays: a shadow map per light and the classification
+ *     of each receiver as lit, umbra or to be ray traced (Section 5).
  *
  * Precision: geometry, intersection and filtering run in double.  Where a
  * floating-point value decides an integer (disk-sample rejection, validity
