@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -19,9 +20,13 @@ _lib = None
 
 
 def lib():
+    """The compiled oracle.  ORC_LIB, when set, names another build of the
+    same source to load instead (the pin tests load copies with a planted
+    mistake through it and must then fail)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        path = os.environ.get("ORC_LIB") or _build.build()
+        _lib = C.CDLL(path)
         _declare(_lib)
     return _lib
 
@@ -79,6 +84,7 @@ def _declare(L):
     L.orc_svgf_frame.argtypes = [C.c_int, C.c_int] + [P] * 16
     L.orc_svgf_seq_grad.argtypes = [C.c_int, C.c_int, C.c_int] + [P] * 9
     L.orc_delay_warp.argtypes = [C.c_int, C.c_int] + [P] * 11
+    L.orc_reproject_check.argtypes = [C.c_int, C.c_int] + [P] * 9
     L.orc_smap_frame_make.argtypes = [P, P, C.c_int32, P]
     L.orc_smap_render.argtypes = [P, P, P, P, C.c_int64, P, P]
     L.orc_smap_classify.argtypes = [P, P, P, C.c_double, C.c_int64, P, P, P, C.c_double, C.c_double, P, P]
@@ -343,6 +349,25 @@ def svgf_temporal(zn, mesh, cam, mask, ao, params: SvgfParams, prev=None, col_hi
                             _p(col_hist), _p(mom), _p(hist), _p(mom_out), _p(hist_out), _p(illum),
                             _p(valid))
     return dict(illum=illum, mom=mom_out, hist=hist_out, valid=valid)
+
+
+def reproject_check(zn, mesh, cam, prev):
+    """Reprojection decisions of every pixel taken twice: in binary32 with
+    the written operation order the temporal step uses, and in double as
+    the plain definition.  prev = (zn, mesh, camera) of the previous frame.
+    Returns dec32, dec64 [H,W,4] = (valid, x0, y0, ok bits) and the double
+    decision's margins [H,W,4] = (pixels to a bound or the integer grid,
+    relative depth to its limit, normal cosine to 0.9, weight sum to
+    1e-4)."""
+    H, W = zn.shape[:2]
+    dec32 = np.zeros((H, W, 4), np.int32)
+    dec64 = np.zeros((H, W, 4), np.int32)
+    margin = np.zeros((H, W, 4))
+    c, cp = make_camera(cam), make_camera(prev[2])
+    lib().orc_reproject_check(W, H, _p(_c(zn, np.float32)), _p(_c(mesh, np.uint32)),
+                              _p(_c(prev[0], np.float32)), _p(_c(prev[1], np.uint32)), C.byref(c),
+                              C.byref(cp), _p(dec32), _p(dec64), _p(margin))
+    return dec32, dec64, margin
 
 
 def svgf_atrous(zn, illum, step, params: SvgfParams):

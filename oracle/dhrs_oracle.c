@@ -24,8 +24,10 @@
  * floating-point value decides an integer (disk-sample rejection, validity
  * of reprojected history taps) the decision is taken in binary32 with every
  * operation written out and correctly rounded, so that a binary32 GPU kernel
- * can take the same decision.  Compile with -ffp-contract=off and without
- * -ffast-math.
+ * can take the same decision.  The reprojection decision is also written as
+ * its plain definition in double (reproject_f64, orc_reproject_check); the
+ * two must agree wherever the double decision is not within a small margin
+ * of a threshold.  Compile with -ffp-contract=off and without -ffast-math.
  *
  * Intersection is brute force over every triangle (Moller-Trumbore in double);
  * there is no acceleration structure here.
@@ -738,6 +740,123 @@ static reproj_t reproject_f32(int W, int H, int x, int y, const float* znp, uint
     r.valid = (sumw >= 1e-4f);
     r.histlen_min = r.valid ? hmin : 0;
     return r;
+}
+
+static void depth_grad(int W, int H, const float* zn, int x, int y, double g[2]);
+
+/*
+ * The same back-projection as its plain definition in double (Section 3.3),
+ * written independently of the binary32 operation order above: the world
+ * position of pixel p is X = eye + z D(p) with D the pixel-centre direction
+ * of camera_ray; z' = (X - eye') . f' is its depth in the previous camera
+ * and (u', v') its continuous pixel position there; the taps are the 2x2
+ * pixels around (u' - 1/2, v' - 1/2) with bilinear weights; a tap is valid
+ * when it lies in the image, carries the same mesh id, its depth is within
+ * 0.01 z' + 2 max(|dz/dx|, |dz/dy|) of z' (one-sided differences of smaller
+ * magnitude) and its normal has cosine >= 0.9 with p's; history exists
+ * when the valid weights sum to at least 1e-4.
+ *
+ * Besides the decision it reports how near each of its comparisons came to
+ * flipping: m_px = distance in pixels of (u' - 1/2, v' - 1/2) to the image
+ * bounds and to the integer grid (where floor() changes), m_z = smallest
+ * | |z_prev(q) - z'| - limit | / z' over in-image taps of p's mesh, m_n =
+ * smallest |cos - 0.9| over taps that passed the depth test, m_w =
+ * |sum of valid weights - 1e-4|.
+ */
+typedef struct {
+    int valid, x0, y0, ok;   /* ok: bit k = tap k (00, 10, 01, 11) valid */
+    double m_px, m_z, m_n, m_w;
+} reproj64_t;
+
+static reproj64_t reproject_f64(int W, int H, int x, int y, const float* zn, const uint32_t* mesh,
+                                const orc_camera* cc, const orc_camera* cp,
+                                const float* zn_prev, const uint32_t* mesh_prev)
+{
+    reproj64_t r;
+    memset(&r, 0, sizeof(r));
+    r.m_px = r.m_z = r.m_n = r.m_w = INFINITY;
+    int64_t p = (int64_t)y * W + x;
+    double o[3], D[3], X[3], rel[3];
+    camera_ray(cc, x, y, o, D);
+    double z = zn[4 * p];
+    for (int k = 0; k < 3; ++k) { X[k] = o[k] + z * D[k]; rel[k] = X[k] - cp->pos[k]; }
+    double fp[3] = {cp->fwd[0], cp->fwd[1], cp->fwd[2]};
+    double rp[3] = {cp->right[0], cp->right[1], cp->right[2]};
+    double up[3] = {cp->up[0], cp->up[1], cp->up[2]};
+    double zq = dot3(rel, fp);
+    r.m_z = fabs(zq) / fmax(z, 1e-300);
+    if (!(zq > 0.0)) return r;
+    double t = cp->tan_half_fov_y, aspect = (double)W / (double)H;
+    double u = (dot3(rel, rp) / (zq * t * aspect) + 1.0) * 0.5 * W - 0.5;
+    double v = (1.0 - dot3(rel, up) / (zq * t)) * 0.5 * H - 0.5;
+    r.m_px = fmin(fmin(fabs(u + 1.0), fabs(u - W)), fmin(fabs(v + 1.0), fabs(v - H)));
+    if (!(u > -1.0 && u < W && v > -1.0 && v < H)) return r;
+    r.m_px = fmin(r.m_px, fmin(fabs(u - nearbyint(u)), fabs(v - nearbyint(v))));
+    double fu = floor(u), fv = floor(v);
+    r.x0 = (int)fu;
+    r.y0 = (int)fv;
+    double au = u - fu, av = v - fv;
+    double wt[4] = {(1 - au) * (1 - av), au * (1 - av), (1 - au) * av, au * av};
+    double g[2];
+    depth_grad(W, H, zn, x, y, g);
+    double lim = 0.01 * zq + 2.0 * fmax(fabs(g[0]), fabs(g[1]));
+    double sumw = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int qx = r.x0 + (k & 1), qy = r.y0 + (k >> 1);
+        if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+        int64_t q = (int64_t)qy * W + qx;
+        if (mesh_prev[q] != mesh[p]) continue;
+        double dz = fabs((double)zn_prev[4 * q] - zq);
+        r.m_z = fmin(r.m_z, fabs(dz - lim) / zq);
+        if (!(dz <= lim)) continue;
+        double c = (double)zn[4 * p + 1] * zn_prev[4 * q + 1] + (double)zn[4 * p + 2] * zn_prev[4 * q + 2]
+                   + (double)zn[4 * p + 3] * zn_prev[4 * q + 3];
+        r.m_n = fmin(r.m_n, fabs(c - 0.9));
+        if (!(c >= 0.9)) continue;
+        r.ok |= 1 << k;
+        sumw += wt[k];
+    }
+    r.m_w = fabs(sumw - 1e-4);
+    r.valid = sumw >= 1e-4;
+    return r;
+}
+
+/* Both reprojection decisions for every foreground pixel of a frame:
+ * dec32, dec64 [H][W][4] = (valid, x0, y0, ok bits), zero on background
+ * or without history; margin [H][W][4] = (m_px, m_z, m_n, m_w) of the
+ * double decision (+inf where a comparison was not reached). */
+void orc_reproject_check(int W, int H, const float* zn, const uint32_t* mesh,
+                         const float* zn_prev, const uint32_t* mesh_prev,
+                         const orc_camera* cam, const orc_camera* cam_prev,
+                         int32_t* dec32, int32_t* dec64, double* margin)
+{
+    int32_t* hist = (int32_t*)calloc((size_t)W * H, sizeof(int32_t));
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            int64_t p = (int64_t)y * W + x;
+            for (int k = 0; k < 4; ++k) { dec32[4 * p + k] = 0; dec64[4 * p + k] = 0; margin[4 * p + k] = INFINITY; }
+            if (!is_fg(zn, p)) continue;
+            reproj_t a = reproject_f32(W, H, x, y, zn + 4 * p, mesh[p], cam, cam_prev, zn_prev, mesh_prev,
+                                       hist, depth_slope_f32(W, H, zn, x, y));
+            if (a.valid) {
+                dec32[4 * p] = 1;
+                dec32[4 * p + 1] = a.tx[0];
+                dec32[4 * p + 2] = a.ty[0];
+                for (int k = 0; k < 4; ++k) dec32[4 * p + 3] |= a.ok[k] << k;
+            }
+            reproj64_t b = reproject_f64(W, H, x, y, zn, mesh, cam, cam_prev, zn_prev, mesh_prev);
+            if (b.valid) {
+                dec64[4 * p] = 1;
+                dec64[4 * p + 1] = b.x0;
+                dec64[4 * p + 2] = b.y0;
+                dec64[4 * p + 3] = b.ok;
+            }
+            margin[4 * p] = b.m_px; margin[4 * p + 1] = b.m_z;
+            margin[4 * p + 2] = b.m_n; margin[4 * p + 3] = b.m_w;
+        }
+    }
+    free(hist);
 }
 
 /* depth gradient at p: per axis the one-sided difference of smaller

@@ -320,3 +320,34 @@ def test_svgf_output_is_convex(orc):
                        tr["ao_count"].reshape(64, 64), orc.SvgfParams())
         for k in ("ao", "shadow"):
             assert res[k].min() >= -1e-12 and res[k].max() <= 1 + 1e-12
+
+
+@pytest.mark.parametrize("step", [1, 2, 4])
+@pytest.mark.parametrize("sigma_z", [1.0, 2.5])
+def test_atrous_depth_weight_on_a_tilted_plane(orc, step, sigma_z):
+    """Depth linear in the pixel coordinates, z = 10 + x/4 + y/32 (exact in
+    binary32): the one-sided differences are the gradient, |z_p - z_q| =
+    |grad z . (p - q)| at every tap, so with eps_z = 0 the depth weight is
+    w_z = exp(-1 / sigma_z) for every tap but the centre (Section 3.3).  With
+    w_n = w_l = 1 the pass is the B3 kernel with its off-centre taps scaled
+    by that constant; colour and variance follow in closed form."""
+    r = np.random.default_rng(20 + step)
+    H, W = 36, 44
+    ys, xs = np.mgrid[0:H, 0:W]
+    zn, _ = _flat_gbuffer(H, W)
+    zn[..., 0] = (10.0 + xs / 4.0 + ys / 32.0).astype(np.float32)
+    illum = r.uniform(0.05, 1, (H, W, 4))
+    out = orc.svgf_atrous(zn, illum, step, orc.SvgfParams(sigma_z=sigma_z, eps_z=0.0, **P_TEXTBOOK))
+    E = math.exp(-1.0 / sigma_z)
+    k = _dilated(step)
+    kc = (3 / 8) ** 2
+    wk = k * E
+    wk[2 * step, 2 * step] = kc           # the centre tap keeps its kernel weight
+    m = 2 * step
+    inner = (slice(m, H - m), slice(m, W - m))
+    for ch in range(2):
+        num = ndimage.correlate(illum[..., ch], wk, mode="constant")
+        num_v = ndimage.correlate(illum[..., 2 + ch], wk * wk, mode="constant")
+        den = kc + E * (1 - kc)
+        assert np.allclose(out[inner + (ch,)], (num / den)[inner], atol=1e-12)
+        assert np.allclose(out[inner + (2 + ch,)], (num_v / den ** 2)[inner], atol=1e-12)
