@@ -301,26 +301,60 @@ def run_ours(args):
     peaks, peak_src = _peaks()
     trace_ms = statistics.mean(tr_ms)
     svgf_ms = statistics.mean(sv_ms)
-    # dominant kernel: trace.  Algorithmic ALU work per frame from the
-    # counters: 2 slab tests (12 FMA + 12 min/max) per node visit and one
-    # watertight test (~24 FMA/FMUL + 12 other) per triangle test.
+    # dominant kernel: trace.  Algorithmic work per frame from the counting
+    # variant: a node visit is two slab tests (24 fp32 lane-ops) and fetches
+    # one 64-byte node, a triangle test is one watertight test (30 lane-ops)
+    # on 36 bytes of vertices.  Held against the fp32 lane-op rate and the
+    # measured L2 read bandwidth; the larger fraction is the roofline's.
     sub = [(Wm + i) % N_FRAMES for i in range(K)]
     visits = statistics.mean(sum(stats[f]["visits"]) for f in sub)
     tests = statistics.mean(sum(stats[f]["tests"]) for f in sub)
-    ops = visits * 36 + tests * 48
     alu_peak = 148 * 128 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12   # lane-ops/s, Tops
-    achieved = ops / (trace_ms * 1e-3) / 1e12
-    # the session's trace kernel: with rasterised primaries it tests each
-    # pixel's ray against its tile's list (counted as triangle tests; dense
-    # tiles traversed) and traces the shadow and AO rays
-    ops_s = statistics.mean(sum(stats_s[f]["visits"]) * 36 + sum(stats_s[f]["tests"]) * 48 for f in sub)
-    kernel_s = ("trace_kernel<0, 0, 1> (tile-list primary tests + shadow + AO rays)" if primary == dhrs.PRIMARY_RASTER
+    l2_gbs = dhrs.l2_read_bandwidth()
+
+    def work(st_list, types, prim_hits=False):
+        """(lane-ops, bytes) per frame over the frames timed; prim_hits: the
+        primary rays counted as one closest-hit triangle test per foreground
+        pixel (rasterised primaries: the binning candidates that miss their
+        pixel are not the method's work)."""
+        ops, byt = [], []
+        for f in sub:
+            v = sum(st_list[f]["visits"][i] for i in types)
+            t = sum(st_list[f]["tests"][i] for i in types)
+            if prim_hits:
+                t += st_list[f]["rays"][2]          # foreground pixels (one AO ray each)
+            ops.append(24 * v + 30 * t)
+            byt.append(64 * v + 36 * t)
+        return statistics.mean(ops), statistics.mean(byt)
+
+    def roof(ops, byt, ms):
+        a_alu = ops / (ms * 1e-3) / 1e12
+        a_l2 = byt / (ms * 1e-3) / 1e9
+        f_alu, f_l2 = a_alu / alu_peak, a_l2 / l2_gbs
+        return {"bound": "l2" if f_l2 >= f_alu else "alu",
+                "achieved": round(a_l2 if f_l2 >= f_alu else a_alu, 3),
+                "peak": round(l2_gbs if f_l2 >= f_alu else alu_peak, 2),
+                "unit": "GB/s" if f_l2 >= f_alu else "Tops/s (fp32 lane ops)",
+                "frac": round(max(f_alu, f_l2), 4),
+                "alu": {"achieved": round(a_alu, 3), "peak": round(alu_peak, 2), "unit": "Tops/s (fp32 lane ops)",
+                        "frac": round(f_alu, 4)},
+                "l2": {"achieved": round(a_l2, 1), "peak": round(l2_gbs, 1), "unit": "GB/s", "frac": round(f_l2, 4)}}
+
+    # the traversal form: all three ray types traversed (stage split)
+    ops_t, byt_t = work(stats, (0, 1, 2))
+    # the session's trace kernel: rasterised primaries (one closest-hit test
+    # per foreground pixel), shadow and AO rays traversed
+    raster = primary == dhrs.PRIMARY_RASTER
+    ops_s, byt_s = work(stats_s, (1, 2), prim_hits=True) if raster else (ops_t, byt_t)
+    kernel_s = ("trace_kernel<0, 0, 1> (rasterised primary visibility + shadow + AO rays)" if raster
                 else "trace_kernel<0, 0, 0> (primary + shadow + AO rays)")
     ker_ms = statistics.mean(tr_ker_ms)
-    achieved_s = ops_s / (ker_ms * 1e-3) / 1e12
-    traffic_key = "trace_kernel_raster_form" if primary == dhrs.PRIMARY_RASTER else "trace_kernel"
-    svgf_bytes = W * H * 340
-    svgf_gbs = svgf_bytes / (svgf_ms * 1e-3) / 1e9
+    traffic_key = "trace_kernel_raster_form" if raster else "trace_kernel"
+    # the counts a first version reported: 36 lane-ops per visit, 48 per
+    # test, every tile-list candidate a test
+    ops_b = statistics.mean(sum(stats_s[f]["visits"]) * 36 + sum(stats_s[f]["tests"]) * 48 for f in sub)
+    svgf_bpp = 358        # per pixel: temporal 106 + 5 levels x 52 - 8 (the last writes no variance)
+    svgf_gbs = W * H * svgf_bpp / (svgf_ms * 1e-3) / 1e9
     res = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mrays/s", "n_gpus": ws, "steps": K,
         "warmup": Wm, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True,
@@ -346,23 +380,27 @@ def run_ours(args):
                             for i, t in enumerate(("primary", "shadow", "ao"))}},
         # dominant kernel of the session frames (the headline's path), timed
         # alone after an L2 flush through dhr_trace_timed
-        "roofline": {"kernel": kernel_s, "bound": "alu", "achieved": round(achieved_s, 3),
-                     "peak": round(alu_peak, 2), "unit": "Tops/s (fp32 lane ops)",
-                     "frac": round(achieved_s / alu_peak, 4), "traffic": _traffic(traffic_key),
-                     "peak_source": "148 SMs x 128 fp32 lanes x max SM clock (%s)" % peak_src,
+        "roofline": {"kernel": kernel_s, **roof(ops_s, byt_s, ker_ms), "traffic": _traffic(traffic_key),
+                     "work_per_frame": {"lane_ops": round(ops_s), "bytes": round(byt_s),
+                                        "counts": "24 lane-ops + 64 B per node visit, 30 lane-ops + 36 B per "
+                                                  "triangle test; rasterised primaries: one test per "
+                                                  "foreground pixel"},
+                     "peak_source": {"alu": "148 SMs x 128 fp32 lanes x max SM clock (%s)" % peak_src,
+                                     "l2": "dhr_l2_read_bandwidth: 48 MB L2-resident buffer read 40 times "
+                                           "with L2-only loads, this run"},
+                     # first version's count (36 / 48 lane-ops, every tile-list candidate a test)
+                     "builder_count_frac_alu": round(ops_b / (ker_ms * 1e-3) / 1e12 / alu_peak, 4),
                      # the limiters ncu measures for this kernel (committed capture):
                      # instruction issue and the L1/tex pipe (node fetches, local stack)
                      "ncu_issue_active_pct": _ncu_field(traffic_key, "issue_active_pct"),
                      "ncu_l1tex_throughput_pct": _ncu_field(traffic_key, "l1tex_throughput_pct"),
                      "ncu_l2_throughput_pct": _ncu_field(traffic_key, "lts_throughput_pct")},
         # the same kernel with traversed primaries (all three ray types), stage split
-        "roofline_traversal_form": {"kernel": "trace_kernel<0, 0, 0>", "bound": "alu",
-                                    "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
-                                    "unit": "Tops/s (fp32 lane ops)", "frac": round(achieved / alu_peak, 4),
+        "roofline_traversal_form": {"kernel": "trace_kernel<0, 0, 0>", **roof(ops_t, byt_t, trace_ms),
                                     "traffic": _traffic("trace_kernel")},
         "roofline_svgf": {"bound": "hbm", "achieved": round(svgf_gbs, 1), "peak": peaks["hbm_gbs"],
                           "unit": "GB/s", "frac": round(svgf_gbs / peaks["hbm_gbs"], 4),
-                          "algorithmic_bytes_per_px": 340, "peak_source": peak_src,
+                          "algorithmic_bytes_per_px": svgf_bpp, "peak_source": peak_src,
                           "traffic_per_frame": _svgf_traffic()},
         "e2e": {"value": round(e2e_value, 2), "unit": "Mrays/s", "h2d_bytes_per_step": 60,
                 "d2h_bytes_per_step": 2 * 4 * W * H,
@@ -563,9 +601,11 @@ def cpu_baseline(scene_d, cams, sample_px=4096, seed=7, rays_per_frame=None):
     """The oracle as it stands (brute force over all triangles, fp64, OpenMP
     on every host core) on a bounded sample of the same workload: primary,
     shadow and AO rays of `sample_px` seeded pixels of frame 0, and the
-    full-frame SVGF at 1920x1080 (second frame, warm history) on G-buffers the
-    oracle traces from the 194-triangle box scene (a brute-force trace of the
-    776k-triangle frame would take hours)."""
+    full-frame SVGF at 1920x1080 (second frame, warm history) on the first
+    two frames of the terrain camera spline over a coarse copy of the terrain
+    scene (the same seeded heightfield on a 24 x 24 grid, 8 icospheres, 8
+    boxes; 1,794 triangles), which the oracle traces in seconds (a
+    brute-force trace of the 776k-triangle frame would take hours)."""
     import numpy as np
 
     import oracle as orc
@@ -578,8 +618,9 @@ def cpu_baseline(scene_d, cams, sample_px=4096, seed=7, rays_per_frame=None):
     dt = time.perf_counter() - t0
     fg = int((tr["mesh"] != 0xFFFFFFFF).sum())
     n_rays = sample_px + 2 * fg
-    B = orc.Scene(wl.scene_boxes())
-    bc = wl.orbit_path(2, W, H, degrees=2.0)
+    coarse = wl.scene_terrain(n_spheres=8, n_boxes=8, sphere_level=1, terrain_n=24)
+    B = orc.Scene(coarse)
+    bc = wl.spline_path(coarse["terrain"], N_FRAMES, W, H)[:2]
     st = orc.SvgfState(W, H)
     svgf_s = 0.0
     for f, cam in enumerate(bc):
@@ -594,13 +635,15 @@ def cpu_baseline(scene_d, cams, sample_px=4096, seed=7, rays_per_frame=None):
             "trace_s_per_frame_extrapolated": (round(dt / n_rays * rays_per_frame, 1) if rays_per_frame else None),
             "sample": f"{sample_px} seeded pixels of frame 0 (primary + shadow + AO rays, "
                       f"{n_rays} rays, {dt:.1f} s) of the 1920x1080 776,050-triangle workload; "
-                      f"SVGF: one full 1920x1080 frame with history (box-scene G-buffers)"}
+                      f"SVGF: one full 1920x1080 frame with history (terrain spline frame 1 over the "
+                      f"1,794-triangle coarse terrain, traced by the oracle)"}
 
 
-def run_denoise_variants(sc, scene_d, frames=12, W=1280, H=720, levels=(0, 1, 2, 5)):
+def run_denoise_variants(sc, scene_d, frames=12, W=1280, H=720, levels=(0, 1, 2, 5, (1, 3), (2, 3))):
     """Lightweight denoiser variants: the same noisy 1-spp frames filtered
-    with 0, 1, 2 and 5 a-trous levels; error of the filtered AO of the last
-    4 frames against a 255-spp AO reference, and SVGF time per frame."""
+    with 0, 1, 2 and 5 a-trous levels of the 5x5 kernel, and 1 and 2 levels
+    of the smaller 3x3 kernel; error of the filtered AO of the last 4 frames
+    against a 255-spp AO reference, and SVGF time per frame."""
     import numpy as np
     import torch
 
@@ -624,7 +667,8 @@ def run_denoise_variants(sc, scene_d, frames=12, W=1280, H=720, levels=(0, 1, 2,
     ao = torch.empty((H, W), device="cuda")
     sh = torch.empty_like(ao)
     for L in levels:
-        p = dhrs.SvgfParams(ao_spp=1, levels=L)
+        L, width = (L, 5) if isinstance(L, int) else L
+        p = dhrs.SvgfParams(ao_spp=1, levels=L, kernel_width=width)
         st = dhrs.SvgfState(W, H)
         errs, ms = [], []
         for f, cam in enumerate(cams):
@@ -639,7 +683,7 @@ def run_denoise_variants(sc, scene_d, frames=12, W=1280, H=720, levels=(0, 1, 2,
                 d = (ao - refs[f])[fg]
                 errs.append((float((d * d).mean()), float(d.abs().mean())))
                 ms.append(e0.elapsed_time(e1))
-        out[f"levels_{L}"] = {"ao_rmse": round(float(np.sqrt(np.mean([e[0] for e in errs]))), 5),
+        out[f"levels_{L}" + ("" if width == 5 else "_kernel_3x3")] = {"ao_rmse": round(float(np.sqrt(np.mean([e[0] for e in errs]))), 5),
                               "ao_mean_abs": round(float(np.mean([e[1] for e in errs])), 5),
                               "svgf_ms": round(float(np.median(ms)), 4)}
     noisy = [float(((aos[f].float() - refs[f])[torch.isfinite(gbufs[f].depth_normal[..., 0])] ** 2).mean())

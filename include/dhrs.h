@@ -96,7 +96,9 @@ typedef struct {
 /* Visibility tracing parameters (Sections 3.1, 3.2). */
 typedef struct {
     uint32_t n_lights;                      /* 1..DHR_MAX_LIGHTS directional lights */
-    float light_dir[DHR_MAX_LIGHTS][3];     /* unit vector toward light k */
+    float light_dir[DHR_MAX_LIGHTS][3];     /* direction toward light k, any nonzero finite
+                                               length: the library normalises it in double
+                                               and rounds once to binary32 */
     float cone_half_angle[DHR_MAX_LIGHTS];  /* radians in [0, pi/2); 0 = hard shadow */
     float ao_radius;                        /* r > 0: a hit at t < r occludes */
     uint32_t ao_spp;                        /* N in 1..255 (8-bit count, Section 3.2) */
@@ -125,10 +127,11 @@ typedef struct {
 /* G-buffer (caller-owned device memory, W*H pixels).
  *  FP32: depth_normal = float4 per pixel (linear view depth, unit normal x,
  *        y, z facing the camera);
- *  FP16: depth_normal = 8 bytes per pixel: binary32 linear depth, then the
- *        normal as two binary16 octahedral coordinates (depth stays
- *        binary32: the depth edge-stopping weight of Section 3.3 compares
- *        depth differences below binary16 resolution).
+ *  FP16 (the 16-bit storage form): depth_normal = 8 bytes per pixel:
+ *        binary32 linear depth, then the normal as two octahedral
+ *        coordinates in 16-bit signed-normalised fixed point (q / 32767;
+ *        depth stays binary32: the depth edge-stopping weight of Section 3.3
+ *        compares depth differences below 16-bit resolution).
  *  mesh_id = uint32 per pixel (DHR_BACKGROUND on a miss).
  *  Both pointers must be 16-byte aligned. */
 typedef struct {
@@ -155,6 +158,11 @@ typedef struct {
                              shadow channel filtered from a u8 bitmask; one SVGF state
                              per light gives every light's filtered shadow.  Unused by
                              the differentiable form (real-valued planes). */
+    uint32_t kernel_width;/* a-trous footprint: 5 (or 0) = 5x5 B3-spline taps
+                             (1/16, 1/4, 3/8, 1/4, 1/16) per axis; 3 = 3x3 taps (1/4, 1/2,
+                             1/4) per axis, the smaller kernel of the lightweight denoiser
+                             Section 3.3 proposes (with levels = 1).  The differentiable
+                             form takes 5 only. */
 } dhr_svgf_params;
 
 typedef struct dhr_svgf_state dhr_svgf_state;
@@ -162,8 +170,11 @@ typedef struct dhr_svgf_state dhr_svgf_state;
 /* Device views of an SVGF state's buffers (owned by the state). */
 typedef struct {
     void* illum;        /* float4 [W*H] temporal colour AO, shadow, variance AO, shadow (variance -1 on background) */
-    void* moments;      /* FP32: float4 [W*H] mu1 AO, mu1 shadow, mu2 AO, mu2 shadow (current) */
-    void* color_hist;   /* FP32: float2 [W*H] colour history for the next frame */
+    void* moments;      /* current moments.  FP32: float4 [W*H] mu1 AO, mu1 shadow, mu2 AO, mu2 shadow.
+                           FP16: 12-byte records [W*H]: mu1 AO, mu1 shadow as 16-bit
+                           unsigned-normalised values (q / 65535), then the variances
+                           mu2 - mu1^2 of AO and shadow as binary32 */
+    void* color_hist;   /* float2 [W*H] colour history for the next frame (binary32 in both forms) */
     uint8_t* histlen;   /* [W*H] history length n (current) */
 } dhr_svgf_buffers;
 
@@ -199,8 +210,8 @@ dhr_status dhr_scene_get_info(const dhr_scene* scene, dhr_scene_info* out);
  *  ao_count_out (device, W*H bytes): N_unoccluded in 0..ao_spp (Eq. 3);
  *            ao_spp on background.
  * Errors: DHR_ERR_INVALID (sizes, ao_spp outside 1..255, n_lights outside
- * 1..8, cone angle outside [0, pi/2), ao_radius <= 0, null pointers),
- * DHR_ERR_CUDA. */
+ * 1..8, cone angle outside [0, pi/2), zero or non-finite light direction,
+ * ao_radius <= 0, null pointers), DHR_ERR_CUDA. */
 dhr_status dhr_trace_visibility(const dhr_scene* scene, const dhr_camera* cam,
                                 const dhr_trace_params* params, dhr_gbuffer* gbuf_out,
                                 uint8_t* shadow_mask_out, uint8_t* ao_count_out, void* stream);
@@ -305,6 +316,15 @@ dhr_status dhr_trace_timed(const dhr_scene* scene, const dhr_camera* cam, const 
                            dhr_gbuffer* gbuf_out, uint8_t* shadow_mask_out, uint8_t* ao_count_out,
                            float* ms, void* stream);
 
+/* Measurement helper (not a step of the method): the L2 read bandwidth, in
+ * GB/s, of a kernel that reads a zero-filled buffer of `bytes` (a multiple
+ * of 16 in [1 MiB, 96 MiB], so that it stays in the 126 MB L2) `passes`
+ * times with L2-only loads, the best of five timed launches after one warm
+ * pass.  The traversal's node and triangle fetches are held against it.
+ * Allocates and frees its buffer; synchronises `stream`.  Errors:
+ * DHR_ERR_INVALID (sizes), DHR_ERR_OOM, DHR_ERR_CUDA. */
+dhr_status dhr_l2_read_bandwidth(int64_t bytes, int32_t passes, float* gbs, void* stream);
+
 /* Sampling check entry: for each of n (px, py) and the given frame, seed
  * and sample index, the accepted disk point and the binary32 AO direction
  * about normals[i] (ray type 1) and the shadow direction about `light`
@@ -385,14 +405,17 @@ dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, 
  *  gbuf: device G-buffer, FP32 or FP16, at most 1,048,576 pixels
  *        (W*H larger is rejected with DHR_ERR_INVALID); background pixels
  *        have depth +inf.
- *  illum (device, float4 per pixel): colour AO, colour shadow, variance AO,
- *        variance shadow, variance -1 on background pixels -- the layout
- *        of dhr_svgf_buffers.illum.
+ *  illum (device, float4 per pixel, 16-byte aligned; DHR_ERR_INVALID
+ *        otherwise): colour AO, colour shadow, variance AO, variance shadow,
+ *        variance -1 on background pixels -- the layout of
+ *        dhr_svgf_buffers.illum.
  *  ao_out, shadow_out: device float [W*H].
  * Scratch: two 16 MiB images in a fixed device array that every device
  * which loads the library holds until the process exits.  Its device
  * address is looked up on the first call on each device, so make that
- * first call before capturing the stream into a CUDA graph.  Every call
+ * first call before capturing the stream into a CUDA graph.  The address
+ * stays valid while the device's context lives: after cudaDeviceReset on
+ * that device, do not call this entry point again in the process.  Every call
  * uses the same array and each level overwrites every pixel it reads next,
  * so nothing has to start at zero; two calls whose kernels overlap on the
  * GPU (different streams, or different host threads) race on the array and

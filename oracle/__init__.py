@@ -51,7 +51,7 @@ class OrcSvgfParams(C.Structure):
     _fields_ = [("alpha", C.c_double), ("sigma_z", C.c_double), ("sigma_n", C.c_double),
                 ("sigma_l", C.c_double), ("eps_z", C.c_double), ("eps_l", C.c_double),
                 ("ao_spp", C.c_int32), ("levels", C.c_int32), ("fixed_alpha", C.c_int32),
-                ("wl_in_atrous", C.c_int32)]
+                ("wl_in_atrous", C.c_int32), ("kernel_width", C.c_int32)]
 
 
 class OrcSmapFrame(C.Structure):
@@ -211,9 +211,10 @@ class TraceParams:
     seed: int = 0
 
     def unit_lights(self):
+        """Each direction as binary32, normalised in double, rounded once."""
         out = []
         for l in self.light_dirs:
-            l = np.asarray(l, np.float64)
+            l = np.asarray(l, np.float32).astype(np.float64)
             out.append((l / np.linalg.norm(l)).astype(np.float32))
         return out
 
@@ -275,17 +276,18 @@ class SvgfParams:
     sigma_z: float = 1.0
     sigma_n: float = 128.0
     sigma_l: float = 4.0
-    eps_z: float = 1e-6
-    eps_l: float = 1e-10
+    eps_z: float = 1e-2         # world units: far above the binary32 resolution of depth
+    eps_l: float = 1e-3         # far above the binary32 rounding of the colours
     ao_spp: int = 1
     levels: int = 5
     fixed_alpha: bool = False
     wl_in_atrous: bool = True
+    kernel_width: int = 5       # 5: 5x5 B3-spline taps; 3: 3x3 (1/4, 1/2, 1/4) taps
 
     def to_c(self) -> OrcSvgfParams:
         return OrcSvgfParams(self.alpha, self.sigma_z, self.sigma_n, self.sigma_l, self.eps_z,
                              self.eps_l, self.ao_spp, self.levels, int(self.fixed_alpha),
-                             int(self.wl_in_atrous))
+                             int(self.wl_in_atrous), int(self.kernel_width))
 
 
 class SvgfState:
@@ -383,7 +385,10 @@ def svgf_atrous(zn, illum, step, params: SvgfParams):
 def svgf_seq_grad(zn, mesh, cams, sig, params: SvgfParams, g_out):
     """Forward + hand-derived fp64 adjoint of the SVGF over F frames starting
     without history.  zn [F,H,W,4], mesh [F,H,W], cams (F), sig [F,H,W,2],
-    g_out [F,H,W,2].  Returns (out [F,H,W,2], g_sig [F,H,W,2], g_sigma[3])."""
+    g_out [F,H,W,2].  Returns (out [F,H,W,2], g_sig [F,H,W,2], g_sigma[3]).
+    The 5x5 kernel only."""
+    if params.kernel_width not in (0, 5):
+        raise ValueError("the adjoint is written for the 5x5 kernel")
     zn = _c(zn, np.float32)
     F, H, W = zn.shape[:3]
     mesh = _c(mesh, np.uint32)
@@ -424,8 +429,7 @@ class ShadowMap:
     R^2 closest-hit casts over every triangle)."""
 
     def __init__(self, scene: Scene, light_dir, res: int, full: bool = True, margin=DEFAULT_MARGIN):
-        l = np.asarray(light_dir, np.float64)
-        self.light = (l / np.linalg.norm(l)).astype(np.float32)
+        self.light = np.asarray(light_dir, np.float32)      # normalised in double by the oracle
         self.frame = OrcSmapFrame()
         lib().orc_smap_frame_make(scene.h, _p(_c(self.light, np.float32)), int(res), C.byref(self.frame))
         self.res = int(res)

@@ -84,6 +84,7 @@ typedef struct {
 typedef struct {
     double alpha, sigma_z, sigma_n, sigma_l, eps_z, eps_l;
     int32_t ao_spp, levels, fixed_alpha, wl_in_atrous;
+    int32_t kernel_width;    /* 5 (or 0): B3-spline taps; 3: (1/4, 1/2, 1/4) */
 } orc_svgf_params;
 
 /* per-pixel record of the temporal step (used by the adjoint) */
@@ -182,19 +183,6 @@ void orc_onb_f32(const float n[3], float T[3], float B[3])
     B[2] = -n[1];
 }
 
-static void onb_f64(const double n[3], double T[3], double B[3])
-{
-    double sgn = copysign(1.0, n[2]);
-    double a = -1.0 / (sgn + n[2]);
-    double b = n[0] * n[1] * a;
-    T[0] = 1.0 + sgn * n[0] * n[0] * a;
-    T[1] = sgn * b;
-    T[2] = -sgn * n[0];
-    B[0] = b;
-    B[1] = sgn + n[1] * n[1] * a;
-    B[2] = -n[1];
-}
-
 /* Cosine-weighted direction about n (Malley's method: a uniform disk point
  * lifted to the hemisphere); Section 3.2 samples AO directions with a
  * cosine-weighted pdf.  binary32: d = (x T + y B) + z n. */
@@ -238,26 +226,6 @@ void orc_cone_dir_f32(const float l[3], float tan_theta, float x, float y, float
     for (int k = 0; k < 3; ++k) d[k] = q[k] / len;
 }
 
-static void ao_dir_f64(const double n[3], double x, double y, double d[3])
-{
-    double T[3], B[3];
-    onb_f64(n, T, B);
-    double z = sqrt(fmax(0.0, 1.0 - x * x - y * y));
-    for (int k = 0; k < 3; ++k) d[k] = x * T[k] + y * B[k] + z * n[k];
-}
-
-static void cone_dir_f64(const double l[3], double tan_theta, double x, double y, double d[3])
-{
-    double T[3], B[3];
-    onb_f64(l, T, B);
-    double q[3], s = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        q[k] = l[k] + tan_theta * (x * T[k] + y * B[k]);
-        s += q[k] * q[k];
-    }
-    s = sqrt(s);
-    for (int k = 0; k < 3; ++k) d[k] = q[k] / s;
-}
 
 /* Batch form used by the bit-exactness test: for each (pixel, sample) the
  * accepted disk point and both binary32 directions. */
@@ -425,7 +393,14 @@ static cast_result cast_closest(const orc_scene* s, const double* o, const doubl
     return r;
 }
 
-/* Any hit with t in (tmin, tmax) (occlusion test). */
+/* Any hit with t in (tmin, tmax) (occlusion test).  The outcome is
+ * ambiguous when a perturbation of the ray within the margin could change
+ * it: a surface near a triangle edge, near tmax, or crossing the ray within
+ * four binary32 units in the last place of the origin's largest coordinate
+ * behind it (the origin of a secondary ray is derived from a hit point that
+ * each implementation rounds in its own precision, so a surface that close
+ * may lie on either side of it; the hit surface itself lies 16 such units
+ * behind and is not counted). */
 static cast_result cast_any(const orc_scene* s, const double* o, const double* d,
                             double tmin, double tmax, const orc_margin* mg)
 {
@@ -433,16 +408,21 @@ static cast_result cast_any(const orc_scene* s, const double* o, const double* d
     double dl = norm3(d);
     double oinf = inf_norm3(o);
     int loose = 0, strict = 0;
-    double tmax_w = tmax * dl;
+    double tmax_w = tmax * dl, tmin_w = tmin * dl;
+    double eps_o = 4.0 * ldexp(fmax(oinf, 0x1p-20), -23);
     for (int64_t i = 0; i < s->n; ++i) {
         double t, u, v;
         if (!mt_plane(s, i, o, d, &t, &u, &v)) continue;
-        if (!(t > tmin)) continue;
         double tw = t * dl;
-        double eps = mg->eps_abs + mg->eps_rel * (oinf + fmin(tw, 4.0 * s->extent));
+        double eps = mg->eps_abs + mg->eps_rel * (oinf + fmin(fabs(tw), 4.0 * s->extent));
         double cosang = fabs(dot3(d, s->nrm + 3 * i)) / dl;
         double eps_t = eps / fmax(cosang, 1e-3);
         double m = edge_margin(s, i, u, v);
+        if (!(t > tmin)) {
+            /* behind the origin: a surface within the rounding of it */
+            if (m >= -eps && tw > tmin_w - eps_o / fmax(cosang, 1e-3)) loose = 1;
+            continue;
+        }
         if (m >= 0.0 && t < tmax) {
             r.hit = 1;
             if (r.tri < 0) { r.tri = i; r.t = t; }
@@ -479,6 +459,37 @@ static void camera_ray(const orc_camera* c, int x, int y, double o[3], double D[
     }
 }
 
+/* Unit normal of triangle i in binary32 with a written operation order (the
+ * specification shared with the GPU kernel, each step rounded once, no
+ * fused multiply-add): a = v1 - v0, b = v2 - v0, c = a x b component by
+ * component as (a_y b_z - a_z b_y, a_z b_x - a_x b_z, a_x b_y - a_y b_x),
+ * l = sqrt((c_x^2 + c_y^2) + c_z^2) correctly rounded, n = c / l.  The
+ * sample frame of the AO rays is built from it: a frame built from a
+ * normal's sign bits (Duff et al.) switches where a component is zero, so
+ * both sides must hold the same bits. */
+static void normal_f32(const orc_scene* s, int64_t i, float n[3])
+{
+    const double *v0 = s->v0 + 3 * i, *e1 = s->e1 + 3 * i, *e2 = s->e2 + 3 * i;
+    volatile float a[3], b[3];
+    for (int k = 0; k < 3; ++k) {
+        /* v1 - v0 rounded once: the double difference of two binary32 values is exact */
+        a[k] = (float)e1[k];
+        b[k] = (float)e2[k];
+    }
+    (void)v0;
+    volatile float p0 = a[1] * b[2], q0 = a[2] * b[1];
+    volatile float p1 = a[2] * b[0], q1 = a[0] * b[2];
+    volatile float p2 = a[0] * b[1], q2 = a[1] * b[0];
+    volatile float cx = p0 - q0, cy = p1 - q1, cz = p2 - q2;
+    volatile float xx = cx * cx, yy = cy * cy, zz = cz * cz;
+    volatile float xy = xx + yy;
+    volatile float q = xy + zz;
+    volatile float l = sqrtf(q);
+    n[0] = cx / l;
+    n[1] = cy / l;
+    n[2] = cz / l;
+}
+
 /* 16 units in the last place of a binary32 value of magnitude m (m taken
  * as at least 2^-20): 16 * 2^(floor(log2 m) - 23), an exact power of two. */
 static double surface_offset(double m)
@@ -511,8 +522,8 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
                uint8_t* shadow_mask, uint8_t* ao_count,
                uint8_t* amb_primary, uint8_t* amb_shadow, uint8_t* amb_ao)
 {
-    double tan_t[ORC_MAX_LIGHTS];
-    for (int k = 0; k < tp->n_lights; ++k) tan_t[k] = tan((double)tp->cone_half_angle[k]);
+    float tan_f[ORC_MAX_LIGHTS];       /* tan of each cone half angle, in double rounded once */
+    for (int k = 0; k < tp->n_lights; ++k) tan_f[k] = (float)tan((double)tp->cone_half_angle[k]);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < np; ++i) {
         int x = pixels[2 * i], y = pixels[2 * i + 1];
@@ -532,10 +543,19 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
             continue;
         }
         double X[3], n[3];
+        float n32[3];
         for (int k = 0; k < 3; ++k) X[k] = o[k] + pr.t * D[k];
+        /* the binary32 normal, facing the eye; a facing decision within
+         * rounding of the grazing angle is ambiguous */
         const double* gn = s->nrm + 3 * pr.tri;
-        double side = dot3(gn, D) > 0.0 ? -1.0 : 1.0;
-        for (int k = 0; k < 3; ++k) n[k] = side * gn[k];
+        double facing_eye = dot3(gn, D) / norm3(D);
+        double side = facing_eye > 0.0 ? -1.0 : 1.0;
+        if (fabs(facing_eye) < 1e-6) amb_primary[i] = 1;
+        normal_f32(s, pr.tri, n32);
+        for (int k = 0; k < 3; ++k) {
+            n32[k] = (float)side * n32[k];
+            n[k] = n32[k];
+        }
         double f[3] = {cam->fwd[0], cam->fwd[1], cam->fwd[2]};
         double rel[3];
         sub3(X, o, rel);
@@ -563,9 +583,10 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
         for (int k = 0; k < tp->n_lights; ++k) {
             float xy[2];
             orc_disk_point((uint32_t)x, (uint32_t)y, tp->frame, tp->seed, 0u, (uint32_t)k, xy);
-            double l[3] = {tp->light_dir[k][0], tp->light_dir[k][1], tp->light_dir[k][2]};
-            double d[3];
-            cone_dir_f64(l, tan_t[k], xy[0], xy[1], d);
+            /* the binary32 sample direction of the specification */
+            float d32[3];
+            orc_cone_dir_f32(tp->light_dir[k], tan_f[k], xy[0], xy[1], d32);
+            double d[3] = {d32[0], d32[1], d32[2]};
             /* a direction below the surface is blocked by the surface itself */
             double facing = dot3(d, n);
             if (fabs(facing) < 1e-6) am |= (uint8_t)(1u << k);
@@ -581,8 +602,9 @@ void orc_trace(const orc_scene* s, const orc_camera* cam, const orc_trace_params
         for (int j = 0; j < tp->ao_spp; ++j) {
             float xy[2];
             orc_disk_point((uint32_t)x, (uint32_t)y, tp->frame, tp->seed, 1u, (uint32_t)j, xy);
-            double d[3];
-            ao_dir_f64(n, xy[0], xy[1], d);
+            float d32[3];
+            orc_ao_dir_f32(n32, xy[0], xy[1], d32);
+            double d[3] = {d32[0], d32[1], d32[2]};
             cast_result ar = cast_any(s, O, d, tmin, (double)tp->ao_radius, mg);
             if (!ar.hit) ++cnt;
             if (ar.ambiguous) ++amb;
@@ -629,9 +651,11 @@ typedef struct {
     int histlen_min;
 } reproj_t;
 
-/* binary32 one-sided depth difference of smaller magnitude along each axis
- * among the foreground neighbours (0 if none), as used by the history
- * decision; returns max(|gx|, |gy|). */
+/* binary32 depth slope along each axis from the one-sided differences
+ * toward the foreground neighbours: with both, the one of smaller magnitude
+ * when they have the same sign and 0 when their signs differ or one is 0
+ * (minmod, continuous in the depths); with one, its difference; with none,
+ * 0.  As used by the history decision; returns max(|gx|, |gy|). */
 static float depth_slope_f32(int W, int H, const float* zn, int x, int y)
 {
     int64_t p = (int64_t)y * W + x;
@@ -650,7 +674,9 @@ static float depth_slope_f32(int W, int H, const float* zn, int x, int y)
             int64_t q = (int64_t)ym * W + xm;
             if (is_fg(zn, q)) { dm = zp - zn[4 * q]; has_m = 1; }
         }
-        if (has_p && has_m) g[ax] = (fabsf(dm) < fabsf(dp)) ? dm : dp;
+        if (has_p && has_m)
+            g[ax] = ((dp > 0.0f && dm > 0.0f) || (dp < 0.0f && dm < 0.0f)) ? ((fabsf(dm) < fabsf(dp)) ? dm : dp)
+                                                                           : 0.0f;
         else if (has_p) g[ax] = dp;
         else if (has_m) g[ax] = dm;
         else g[ax] = 0.0f;
@@ -859,8 +885,10 @@ void orc_reproject_check(int W, int H, const float* zn, const uint32_t* mesh,
     free(hist);
 }
 
-/* depth gradient at p: per axis the one-sided difference of smaller
- * magnitude among the foreground neighbours (0 if none) */
+/* depth gradient at p: per axis the minmod of the one-sided differences
+ * toward the foreground neighbours (the smaller magnitude when both share a
+ * sign, 0 when the signs differ or one is 0; one neighbour: its difference;
+ * none: 0) */
 static void depth_grad(int W, int H, const float* zn, int x, int y, double g[2])
 {
     int64_t p = (int64_t)y * W + x;
@@ -878,7 +906,8 @@ static void depth_grad(int W, int H, const float* zn, int x, int y, double g[2])
             int64_t q = (int64_t)ym * W + xm;
             if (is_fg(zn, q)) { dm = zp - (double)zn[4 * q]; has_m = 1; }
         }
-        if (has_p && has_m) g[ax] = (fabs(dm) < fabs(dp)) ? dm : dp;
+        if (has_p && has_m)
+            g[ax] = ((dp > 0.0 && dm > 0.0) || (dp < 0.0 && dm < 0.0)) ? ((fabs(dm) < fabs(dp)) ? dm : dp) : 0.0;
         else if (has_p) g[ax] = dp;
         else if (has_m) g[ax] = dm;
         else g[ax] = 0.0;
@@ -1050,12 +1079,16 @@ void orc_svgf_temporal(int W, int H, const float* zn, const uint32_t* mesh,
  * output): 5x5 B3-spline taps (1/16, 1/4, 3/8, 1/4, 1/16) at offsets
  * h*{-2..2}, weights k * w_z * w_n * w_l; w_l uses a 3x3 Gaussian of the
  * variance at p.  colour' = sum w c / sum w, variance' = sum w^2 var / (sum w)^2.
+ * kernel_width = 3 takes the smaller kernel of the lightweight denoiser
+ * Section 3.3 proposes: 3x3 taps (1/4, 1/2, 1/4) at offsets h*{-1..1}.
  */
 void orc_svgf_atrous(int W, int H, const float* zn, const double* in, int step,
                      const orc_svgf_params* P, double* out)
 {
-    static const double k5[5] = {1.0 / 16, 1.0 / 4, 3.0 / 8, 1.0 / 4, 1.0 / 16};
+    static const double b3[5] = {1.0 / 16, 1.0 / 4, 3.0 / 8, 1.0 / 4, 1.0 / 16};
     static const double k3[3] = {1.0 / 4, 1.0 / 2, 1.0 / 4};
+    const int R = P->kernel_width == 3 ? 1 : 2;
+    const double* k5 = R == 2 ? b3 : k3;     /* taps k5[i + R], i in -R..R */
 #pragma omp parallel for schedule(dynamic, 4)
     for (int y = 0; y < H; ++y) {
         for (int x = 0; x < W; ++x) {
@@ -1082,13 +1115,13 @@ void orc_svgf_atrous(int W, int H, const float* zn, const double* in, int step,
             double g[2];
             depth_grad(W, H, zn, x, y, g);
             double sw[2] = {0, 0}, sc[2] = {0, 0}, sv[2] = {0, 0};
-            for (int j = -2; j <= 2; ++j) {
-                for (int i = -2; i <= 2; ++i) {
+            for (int j = -R; j <= R; ++j) {
+                for (int i = -R; i <= R; ++i) {
                     int qx = x + i * step, qy = y + j * step;
                     if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
                     int64_t q = (int64_t)qy * W + qx;
                     if (!is_fg(zn, q)) continue;
-                    double k = k5[i + 2] * k5[j + 2];
+                    double k = k5[i + R] * k5[j + R];
                     for (int ch = 0; ch < 2; ++ch) {
                         double w = k;
                         if (i || j) {

@@ -67,7 +67,7 @@ class SvgfParamsC(C.Structure):
     _fields_ = [("alpha", C.c_float), ("sigma_z", C.c_float), ("sigma_n", C.c_float),
                 ("sigma_l", C.c_float), ("eps_z", C.c_float), ("eps_l", C.c_float),
                 ("ao_spp", C.c_uint32), ("levels", C.c_uint32), ("fixed_alpha", C.c_uint32),
-                ("wl_in_atrous", C.c_uint32), ("shadow_light", C.c_uint32)]
+                ("wl_in_atrous", C.c_uint32), ("shadow_light", C.c_uint32), ("kernel_width", C.c_uint32)]
 
 
 class SvgfBuffersC(C.Structure):
@@ -84,6 +84,7 @@ _SIGNATURES = {
     "dhr_trace_visibility": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_cast_rays": ([_P, _P, _P, _P, _P, C.c_int32, C.c_int64, _P, _P, _P], C.c_int),
     "dhr_trace_stats": ([_P, _P, _P, _P, _P], C.c_int),
+    "dhr_l2_read_bandwidth": ([C.c_int64, C.c_int32, _P, _P], C.c_int),
     "dhr_trace_timed": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_gbuffer_convert": ([_P, _P, _P], C.c_int),
     "dhr_sample_directions": ([_P, _P, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32, _P, _P,
@@ -197,8 +198,7 @@ class TraceParams:
         p = TraceParamsC()
         p.n_lights = len(self.light_dirs)
         for k, l in enumerate(self.light_dirs):
-            l = np.asarray(l, np.float64)
-            p.light_dir[k][:] = [float(x) for x in (l / np.linalg.norm(l)).astype(np.float32)]
+            p.light_dir[k][:] = [float(x) for x in l]       # normalised by the library
             p.cone_half_angle[k] = math.radians(self.cone_half_angle_deg[k])
         p.ao_radius = self.ao_radius
         p.ao_spp = self.ao_spp
@@ -214,18 +214,19 @@ class SvgfParams:
     sigma_z: float = 1.0
     sigma_n: float = 128.0
     sigma_l: float = 4.0
-    eps_z: float = 1e-6
-    eps_l: float = 1e-10
+    eps_z: float = 1e-2         # world units: far above the binary32 resolution of depth
+    eps_l: float = 1e-3         # far above the binary32 rounding of the colours
     ao_spp: int = 1
     levels: int = 5
     fixed_alpha: bool = False
     wl_in_atrous: bool = True
     shadow_light: int = 0
+    kernel_width: int = 5       # 5: 5x5 B3-spline taps; 3: 3x3 (1/4, 1/2, 1/4) taps
 
     def to_c(self) -> SvgfParamsC:
         return SvgfParamsC(self.alpha, self.sigma_z, self.sigma_n, self.sigma_l, self.eps_z,
                            self.eps_l, self.ao_spp, self.levels, int(self.fixed_alpha),
-                           int(self.wl_in_atrous), int(self.shadow_light))
+                           int(self.wl_in_atrous), int(self.shadow_light), int(self.kernel_width))
 
 
 # --------------------------------------------------------------- G-buffer
@@ -325,9 +326,7 @@ class ShadowMap:
     texels plus its min pyramid), for the selective trace."""
 
     def __init__(self, scene: Scene, light_dir, resolution: int = 4096, stream=None):
-        l = np.asarray(light_dir, np.float64)
-        nl = np.linalg.norm(l)
-        self.light = (l / nl if nl > 0 else l).astype(np.float32)   # zero: rejected by the library
+        self.light = np.asarray(light_dir, np.float32)   # normalised (or rejected) by the library
         h = C.c_void_p()
         _check(lib().dhr_shadow_map_create(scene.h, self.light.ctypes.data_as(C.c_void_p), int(resolution),
                                            _stream(stream), C.byref(h)))
@@ -396,6 +395,14 @@ def trace_stats(scene: Scene, cam, params: TraceParams, stream=None) -> dict:
     _check(lib().dhr_trace_stats(scene.h, C.byref(c), C.byref(p), out, _stream(stream)))
     v = list(out)
     return dict(rays=v[0:3], visits=v[3:6], tests=v[6:9])
+
+
+def l2_read_bandwidth(nbytes: int = 48 << 20, passes: int = 40, stream=None) -> float:
+    """Measured L2 read bandwidth (GB/s) of an L2-resident buffer (a
+    measurement helper, not a step of the method)."""
+    out = C.c_float()
+    _check(lib().dhr_l2_read_bandwidth(int(nbytes), int(passes), C.byref(out), _stream(stream)))
+    return float(out.value)
 
 
 def cast_rays(scene: Scene, origins, dirs, tmin, tmax, any_hit=False, stream=None):

@@ -88,11 +88,24 @@ __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigne
 }
 
 // Reduced-precision G-buffer element (DHR_FP16 form), 8 bytes: x = binary32
-// linear depth, y = unit normal as two binary16 octahedral coordinates
-// (Cigolle et al., "A Survey of Efficient Representations for Independent
-// Unit Vectors", JCGT 2014).  Depth stays binary32: the depth edge-stopping
-// weight compares depth differences far below binary16 resolution.
+// linear depth, y = unit normal as two octahedral coordinates (Cigolle et
+// al., "A Survey of Efficient Representations for Independent Unit
+// Vectors", JCGT 2014) in 16-bit signed-normalised fixed point, q / 32767:
+// the coordinates lie in [-1, 1], so fixed point spends all 16 bits on that
+// range (binary16 would keep 11 bits of precision there and spend 5 on an
+// exponent range that never occurs).  Depth stays binary32: the depth
+// edge-stopping weight compares depth differences far below 16-bit
+// resolution.
 __device__ __forceinline__ float oct_sign(float v) { return v >= 0.0f ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ uint32_t snorm16(float v) {
+    const int q = __float2int_rn(fminf(fmaxf(v, -1.0f), 1.0f) * 32767.0f);
+    return (uint32_t)(q & 0xFFFF);
+}
+
+__device__ __forceinline__ float unsnorm16(uint32_t u) {
+    return (float)(int16_t)(u & 0xFFFF) * (1.0f / 32767.0f);
+}
 
 __device__ __forceinline__ uint2 pack_gbuf16(float depth, float3 n) {
     const float s = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
@@ -106,16 +119,14 @@ __device__ __forceinline__ uint2 pack_gbuf16(float depth, float3 n) {
             ey = ty;
         }
     }
-    const __half2 h = __floats2half2_rn(ex, ey);
-    return make_uint2(__float_as_uint(depth), *reinterpret_cast<const uint32_t*>(&h));
+    return make_uint2(__float_as_uint(depth), snorm16(ex) | (snorm16(ey) << 16));
 }
 
 __device__ __forceinline__ float4 unpack_gbuf16(uint2 u) {
-    const uint32_t hb = u.y;
-    const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&hb));
-    float3 v = make_float3(e.x, e.y, 1.0f - fabsf(e.x) - fabsf(e.y));
+    const float ex = unsnorm16(u.y), ey = unsnorm16(u.y >> 16);
+    float3 v = make_float3(ex, ey, 1.0f - fabsf(ex) - fabsf(ey));
     if (v.z < 0.0f) {
-        const float tx = (1.0f - fabsf(e.y)) * oct_sign(e.x), ty = (1.0f - fabsf(e.x)) * oct_sign(e.y);
+        const float tx = (1.0f - fabsf(ey)) * oct_sign(ex), ty = (1.0f - fabsf(ex)) * oct_sign(ey);
         v.x = tx;
         v.y = ty;
     }

@@ -118,24 +118,24 @@ __global__ void __launch_bounds__(256) serve_temporal_kernel(const BatchTable* t
     }
 }
 
-template <int kMode, int kNsq>
+template <int kMode, int kNsq, int kR>
 __device__ __forceinline__ void serve_atrous_tile(const ServeItem& it, int l, int t, AtrousSmem& sm) {
     const float4* in = l == 0 ? it.illum : it.pp[(l - 1) & 1];
-    atrous_tile<DHR_FP32, kMode, kNsq>(it.sk, 1 << l, t - it.tile_begin, it.g_cur, in, it.pp[l & 1], it.col,
-                                       it.out_ao, it.out_sh, sm);
+    atrous_tile<DHR_FP32, kMode, kNsq, kR>(it.sk, 1 << l, t - it.tile_begin, it.g_cur, in, it.pp[l & 1], it.col,
+                                           it.out_ao, it.out_sh, sm);
 }
 
 // level l of every session; mode: 1 writes the colour history, 2 the outputs.
 // The session's a-trous tiles are its 32x8 pixel tiles.
-template <int kNsq>
+template <int kNsq, int kR>
 __global__ void __launch_bounds__(256) serve_atrous_kernel(const BatchTable* tb, int l, int mode) {
     __shared__ AtrousSmem sm;
     const BatchTable& b = *tb;
     for (int t = blockIdx.x; t < b.n_tiles; t += gridDim.x) {
         const ServeItem& it = b.items[find_item(b, t)];
-        if (mode == 2) serve_atrous_tile<2, kNsq>(it, l, t, sm);
-        else if (mode == 1) serve_atrous_tile<1, kNsq>(it, l, t, sm);
-        else serve_atrous_tile<0, kNsq>(it, l, t, sm);
+        if (mode == 2) serve_atrous_tile<2, kNsq, kR>(it, l, t, sm);
+        else if (mode == 1) serve_atrous_tile<1, kNsq, kR>(it, l, t, sm);
+        else serve_atrous_tile<0, kNsq, kR>(it, l, t, sm);
     }
 }
 
@@ -346,8 +346,11 @@ static dhr_status capture_slot(dhr_server* s, Slot& sl) {
     const int nsq = s->sp.sigma_n == 128.0f ? 7 : -1;
     for (int l = 0; l < L; ++l) {
         const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-        if (nsq == 7) serve_atrous_kernel<7><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
-        else serve_atrous_kernel<-1><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
+        const bool small = atrous_radius(&s->sp) == 1;
+        if (nsq == 7 && !small) serve_atrous_kernel<7, 2><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
+        else if (!small) serve_atrous_kernel<-1, 2><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
+        else if (nsq == 7) serve_atrous_kernel<7, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
+        else serve_atrous_kernel<-1, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
     }
     if (L <= 1) serve_copy_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table);
     serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, sl.d_table, 1);

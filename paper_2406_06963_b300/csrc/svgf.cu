@@ -30,7 +30,7 @@ dhr_status svgf_create(int32_t w, int32_t h, dhr_precision prec, dhr_svgf_state*
     s->h = h;
     s->prec = prec;
     const size_t n = (size_t)w * h;
-    const size_t col_b = prec == DHR_FP16 ? 4 : 8, mom_b = prec == DHR_FP16 ? 8 : 16;
+    const size_t col_b = 8, mom_b = prec == DHR_FP16 ? sizeof(Mom16) : 16;
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaMalloc(&s->col, n * col_b);
     e = e ? e : cudaMalloc(&s->mom[0], n * mom_b);
@@ -84,6 +84,8 @@ dhr_status check_svgf_params(const dhr_svgf_params* p) {
     DHR_CHECK_ARG(p->sigma_n >= 0.0f && p->sigma_z >= 0.0f && p->sigma_l >= 0.0f, "svgf: negative sigma");
     DHR_CHECK_ARG(p->shadow_light < DHR_MAX_LIGHTS, "svgf: shadow_light %u not in 0..%d", p->shadow_light,
                   DHR_MAX_LIGHTS - 1);
+    DHR_CHECK_ARG(p->kernel_width == 0 || p->kernel_width == 3 || p->kernel_width == 5,
+                  "svgf: kernel_width %u is not 3 or 5", p->kernel_width);
     return DHR_OK;
 }
 
@@ -114,7 +116,7 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
         return DHR_OK;
     }
     const float4* in = s->illum;
-    const int nsq = atrous_nsq(prm);
+    const int nsq = atrous_nsq(prm), R = atrous_radius(prm);
     if (P == DHR_FP16) {
         const int n = s->w * s->h;
         gbuf_decode_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, reinterpret_cast<const uint2*>(gc), s->gdec);
@@ -125,10 +127,10 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
         const int step = 1 << l;
         const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
         if (P == DHR_FP16)
-            DHR_TRY(launch_atrous<kFP16Decoded>(mode, nsq, st, k, step, s->gdec, in, out,
-                                                reinterpret_cast<__half2*>(col), ao_out, sh_out));
+            DHR_TRY(launch_atrous<kFP16Decoded>(mode, nsq, R, st, k, step, s->gdec, in, out, col, ao_out,
+                                                sh_out));
         else
-            DHR_TRY(launch_atrous<P>(mode, nsq, st, k, step, gc, in, out, col, ao_out, sh_out));
+            DHR_TRY(launch_atrous<P>(mode, nsq, R, st, k, step, gc, in, out, col, ao_out, sh_out));
         if (L == 1) {
             // single iteration: it is both the history source and the output
             passthrough_kernel<P><<<(s->w * s->h + 255) / 256, 256, 0, st>>>(s->w * s->h, out, col, ao_out,
@@ -251,7 +253,9 @@ static std::mutex g_noalloc_mu;
 static float4* g_noalloc_addr[kNoallocMaxDevices];
 
 // Device address of g_noalloc_scratch on the current device (the host-side
-// symbol is only a stand-in).  Looked up once per device, on the first call.
+// symbol is only a stand-in).  Looked up once per device, on the first call,
+// and valid for the life of that device's context: a cudaDeviceReset unloads
+// the module, after which the cached address is stale.
 static dhr_status noalloc_scratch(float4** out) {
     int dev = -1;
     DHR_CUDA_TRY(cudaGetDevice(&dev));
@@ -276,8 +280,8 @@ static dhr_status run_atrous_noalloc(const dhr_gbuffer* g, const float4* illum, 
     const float4* in = illum;
     for (int l = 0; l < L; ++l) {
         float4* out = scratch + (size_t)(l & 1) * kNoallocMaxPixels;
-        DHR_TRY(launch_atrous<P>(l == L - 1 ? 2 : 0, nsq, st, k, 1 << l, gd, in, out, nullptr, ao_out,
-                                 sh_out));
+        DHR_TRY(launch_atrous<P>(l == L - 1 ? 2 : 0, nsq, atrous_radius(prm), st, k, 1 << l, gd, in, out, nullptr,
+                                 ao_out, sh_out));
         in = out;
     }
     return DHR_OK;
@@ -298,6 +302,8 @@ extern "C" dhr_status dhr_svgf_atrous_noalloc(const dhr_gbuffer* gbuf, const flo
                   gbuf->width, gbuf->height, (long long)gbuf->width * gbuf->height,
                   (long long)kNoallocMaxPixels);
     DHR_CHECK_ARG(gbuf->precision == DHR_FP32 || gbuf->precision == DHR_FP16, "svgf_atrous_noalloc: bad precision");
+    DHR_CHECK_ARG(((uintptr_t)illum & 15) == 0 && ((uintptr_t)gbuf->depth_normal & 15) == 0,
+                  "svgf_atrous_noalloc: illum and the G-buffer must be 16-byte aligned");
     DHR_TRY(check_svgf_params(params));
     DHR_CHECK_ARG(params->levels >= 1, "svgf_atrous_noalloc: levels must be in 1..8");
     float4* scratch = nullptr;

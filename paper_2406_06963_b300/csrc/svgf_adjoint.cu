@@ -488,6 +488,7 @@ static dhr_status check_seq(const dhr_svgf_tape* t, const dhr_gbuffer* g, const 
                             const dhr_svgf_params* p) {
     DHR_CHECK_ARG(t && g && cams && p, "svgf_seq: null pointer");
     DHR_TRY(check_svgf_params(p));
+    DHR_CHECK_ARG(atrous_radius(p) == 2, "svgf_seq: the differentiable form takes the 5x5 kernel only");
     for (int f = 0; f < t->F; ++f) {
         DHR_CHECK_ARG(g[f].precision == DHR_FP32, "svgf_seq: the differentiable form runs on FP32 G-buffers");
         DHR_CHECK_ARG(g[f].width == t->W && g[f].height == t->H && g[f].depth_normal && g[f].mesh_id &&
@@ -531,7 +532,7 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
         for (int l = 0; l < L; ++l) {
             float4* o = t->lev[l & 1];
             const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-            DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, st, k, 1 << l, gc, in, o, t->col, ao, sh));
+            DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, 2, st, k, 1 << l, gc, in, o, t->col, ao, sh));
             if (L == 1) {
                 passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, o, t->col, ao, sh);
                 DHR_CUDA_TRY(cudaGetLastError());
@@ -586,7 +587,7 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
         DHR_CUDA_TRY(cudaGetLastError());
         // recompute the inputs of levels 1..L-1 from the recorded temporal output
         for (int i = 0; i + 1 < L; ++i)
-            DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, st, k, 1 << i, gcur, i == 0 ? illum : t->lvin + (size_t)(i - 1) * N,
+            DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, 2, st, k, 1 << i, gcur, i == 0 ? illum : t->lvin + (size_t)(i - 1) * N,
                                             t->lvin + (size_t)i * N, nullptr, nullptr, nullptr));
         for (int l = L - 1; l >= 0; --l) {
             const float4* xin = l == 0 ? illum : t->lvin + (size_t)(l - 1) * N;

@@ -14,10 +14,14 @@
 //    colour history and the last iteration writes the outputs.
 //
 // Storage precision is a template parameter: FP32 keeps every buffer in
-// binary32; FP16 stores the normal (octahedral), the colour history and the
-// moments in binary16 and keeps depth and the variance-carrying buffer in
-// binary32 (depth differences far below binary16 resolution drive w_z, and
-// the variance mu2 - mu1^2 cancels); arithmetic is binary32.
+// binary32; the 16-bit form (DHR_FP16) stores the normal (octahedral) and
+// the first moments in 16 bits and keeps depth, the colour history and the
+// variances in binary32; arithmetic is binary32.  Why those in 32 bits:
+// depth differences far below 16-bit resolution drive w_z; a moving average
+// stored in 16 bits stops moving once alpha |s - h| is below half a step
+// (binary16: up to 2^-12 / alpha = 1.2e-3 away from its input near 1), and
+// the colour history feeds the output directly; mu2 - mu1^2 cancels, so the
+// second moment is kept as the variance itself.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -38,40 +42,60 @@ struct Store<DHR_FP32> {
     static __device__ __forceinline__ float2 col(const Col* p, size_t i) { return __ldg(p + i); }
     static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = v; }
     static __device__ __forceinline__ float4 mom(const Mom* p, size_t i) { return __ldg(p + i); }
-    static __device__ __forceinline__ void put_mom(Mom* p, size_t i, float4 v) { p[i] = v; }
+    static __device__ __forceinline__ void put_mom(Mom* p, size_t i, float4 v, float2) { p[i] = v; }
 };
+
+// 16-bit moments record, 12 bytes: mu1 (AO, shadow) as two 16-bit
+// unsigned-normalised values q / 65535 (the signals and their means lie in
+// [0, 1]; every 8-bit AO fraction k / 255 is exact, 65535 = 255 x 257, and a
+// step of 1.5e-5 leaves a moving average at most 3.8e-5 from a constant
+// input, a variance floor far below what the luminance weight resolves),
+// then the two variances mu2 - mu1^2 in binary32.
+__device__ __forceinline__ uint32_t unorm16(float v) {
+    return (uint32_t)__float2uint_rn(fminf(fmaxf(v, 0.0f), 1.0f) * 65535.0f);
+}
+
+struct Mom16 {
+    uint32_t mu1;        // AO in bits 0-15, shadow in bits 16-31
+    float var_ao, var_sh;
+};
+static_assert(sizeof(Mom16) == 12, "16-bit moments record must stay 12 bytes");
 
 template <>
 struct Store<DHR_FP16> {
     using G = uint2;
-    using Col = __half2;
-    using Mom = ushort4;
-    static __device__ __forceinline__ float h(unsigned short u) { return __half2float(__ushort_as_half(u)); }
-    static __device__ __forceinline__ unsigned short q(float f) { return __half_as_ushort(__float2half_rn(f)); }
+    using Col = float2;
+    using Mom = Mom16;
     static __device__ __forceinline__ float4 g(const G* p, size_t i) { return unpack_gbuf16(__ldg(p + i)); }
-    static __device__ __forceinline__ float2 col(const Col* p, size_t i) { return __half22float2(p[i]); }
-    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = __float22half2_rn(v); }
+    static __device__ __forceinline__ float2 col(const Col* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = v; }
+    // (mu1, mu2) with mu2 rebuilt from the stored mu1 and variance, so that
+    // mu2 - mu1^2 gives back the stored variance
     static __device__ __forceinline__ float4 mom(const Mom* p, size_t i) {
-        const ushort4 u = __ldg(p + i);
-        return make_float4(h(u.x), h(u.y), h(u.z), h(u.w));
+        const uint32_t u = __ldg(&p[i].mu1);
+        const float mx = (float)(u & 0xFFFFu) * (1.0f / 65535.0f), my = (float)(u >> 16) * (1.0f / 65535.0f);
+        const float va = __ldg(&p[i].var_ao), vs = __ldg(&p[i].var_sh);
+        return make_float4(mx, my, fmaf(mx, mx, va), fmaf(my, my, vs));
     }
-    static __device__ __forceinline__ void put_mom(Mom* p, size_t i, float4 v) {
-        p[i] = make_ushort4(q(v.x), q(v.y), q(v.z), q(v.w));
+    static __device__ __forceinline__ void put_mom(Mom* p, size_t i, float4 v, float2) {
+        p[i].mu1 = unorm16(v.x) | (unorm16(v.y) << 16);
+        p[i].var_ao = fmaxf(0.f, v.z - v.x * v.x);
+        p[i].var_sh = fmaxf(0.f, v.w - v.y * v.y);
     }
 };
 
-// Internal storage tag for the a-trous levels of an FP16 state: binary16
-// colour history as in FP16, the G-buffer read from a float4 copy decoded
-// once per frame (instead of decoding the octahedral normal at every tap).
+// Internal storage tag for the a-trous levels of an FP16 state: colour
+// history as in FP16, the G-buffer read from a float4 copy decoded once per
+// frame (instead of decoding the octahedral normal at every tap).
 constexpr dhr_precision kFP16Decoded = static_cast<dhr_precision>(0x10);
 
 template <>
 struct Store<kFP16Decoded> {
     using G = float4;
-    using Col = __half2;
-    using Mom = ushort4;
+    using Col = float2;
+    using Mom = Mom16;
     static __device__ __forceinline__ float4 g(const G* p, size_t i) { return __ldg(p + i); }
-    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = __float22half2_rn(v); }
+    static __device__ __forceinline__ void put_col(Col* p, size_t i, float2 v) { p[i] = v; }
 };
 
 struct SvgfConsts {
@@ -84,7 +108,19 @@ struct SvgfConsts {
 
 __device__ __forceinline__ bool is_fg(float z) { return z < INFINITY; }
 
-// per-axis one-sided depth difference of smaller magnitude (0 if none)
+// Depth slope along one axis from the one-sided differences toward the two
+// neighbours (minmod): the one of smaller magnitude when both have the same
+// sign, 0 when their signs differ (a one-pixel ridge or valley) or one is 0;
+// with one foreground neighbour its difference, with none 0.  Unlike "the
+// smaller magnitude" alone it is continuous in the depths, so a rounding
+// change of a depth cannot swing the slope from +d to -d.
+__device__ __forceinline__ float minmod_slope(bool hp, float dp, bool hm, float dm) {
+    if (hp && hm)
+        return ((dp > 0.f && dm > 0.f) || (dp < 0.f && dm < 0.f)) ? (fabsf(dm) < fabsf(dp) ? dm : dp) : 0.f;
+    return hp ? dp : (hm ? dm : 0.f);
+}
+
+// per-axis depth slope (minmod of the one-sided differences)
 template <class S>
 __device__ __forceinline__ float2 depth_grad(const typename S::G* g, int W, int H, int x, int y, float zp) {
     float r[2];
@@ -101,7 +137,7 @@ __device__ __forceinline__ float2 depth_grad(const typename S::G* g, int W, int 
             const float z = S::g(g, (size_t)ym * W + xm).x;
             if (is_fg(z)) { dm = zp - z; hm = true; }
         }
-        r[ax] = (hp && hm) ? (fabsf(dm) < fabsf(dp) ? dm : dp) : (hp ? dp : (hm ? dm : 0.f));
+        r[ax] = minmod_slope(hp, dp, hm, dm);
     }
     return make_float2(r[0], r[1]);
 }
@@ -134,7 +170,8 @@ struct SigPlanar {
 // Back-projection into the previous frame: the binary32 operation sequence
 // below (each step rounded once, no contraction) decides which history taps
 // are valid; it is the specification shared with the CPU oracle.  Depth
-// consistency: |z_prev(q) - z'| <= 0.01 z' + 2 max(|dz/dx|, |dz/dy|).
+// consistency: |z_prev(q) - z'| <= 0.01 z' + 2 max(|dz/dx|, |dz/dy|), the
+// slopes those of depth_grad.
 struct Reproj {
     int x0, y0;
     float w[4];
@@ -334,13 +371,13 @@ __device__ __forceinline__ void temporal_tile(
         const float2 c = make_float2(fmaf(a, s.x - ch.x, ch.x), fmaf(a, s.y - ch.y, ch.y));
         const float4 m = make_float4(fmaf(a, s.x - mh.x, mh.x), fmaf(a, s.y - mh.y, mh.y),
                                      fmaf(a, s.x * s.x - mh.z, mh.z), fmaf(a, s.y * s.y - mh.w, mh.w));
-        S::put_mom(mom_out, p, m);
+        S::put_mom(mom_out, p, m, s);
         hist_out[p] = (uint8_t)n;
         if (n >= 4)
             illum[p] = make_float4(c.x, c.y, fmaxf(0.f, m.z - m.x * m.x), fmaxf(0.f, m.w - m.y * m.y));
     } else if (inside) {
         illum[p] = make_float4(1.f, 1.f, -1.f, -1.f);
-        S::put_mom(mom_out, p, make_float4(1.f, 1.f, 1.f, 1.f));
+        S::put_mom(mom_out, p, make_float4(1.f, 1.f, 1.f, 1.f), make_float2(1.f, 1.f));
         hist_out[p] = 0;
     }
     // short history (n < 4): 7x7 spatial estimate of the current frame's
@@ -467,8 +504,8 @@ struct AtrousSmem {
 __host__ __device__ inline int atrous_tiles_x(int W) { return (W + kAtW - 1) / kAtW; }
 __host__ __device__ inline int atrous_tiles(int W, int H) { return atrous_tiles_x(W) * ((H + kAtH - 1) / kAtH); }
 
-// per-axis one-sided depth difference of smaller magnitude (0 if none) from
-// the four neighbour depths (+inf: background or outside the image)
+// per-axis depth slope (minmod of the one-sided differences) from the four
+// neighbour depths (+inf: background or outside the image)
 __device__ __forceinline__ float2 grad_from(float zp, float zxp, float zxm, float zyp, float zym) {
     const float n[2][2] = {{zxp, zxm}, {zyp, zym}};
     float r[2];
@@ -476,7 +513,7 @@ __device__ __forceinline__ float2 grad_from(float zp, float zxp, float zxm, floa
     for (int ax = 0; ax < 2; ++ax) {
         const bool hp = is_fg(n[ax][0]), hm = is_fg(n[ax][1]);
         const float dp = hp ? n[ax][0] - zp : 0.f, dm = hm ? zp - n[ax][1] : 0.f;
-        r[ax] = (hp && hm) ? (fabsf(dm) < fabsf(dp) ? dm : dp) : (hp ? dp : (hm ? dm : 0.f));
+        r[ax] = minmod_slope(hp, dp, hm, dm);
     }
     return make_float2(r[0], r[1]);
 }
@@ -521,37 +558,54 @@ struct AtrousSums {
     float sw0, sw1, sc0, sc1, sv0, sv1;
 };
 
-template <int kNsq, class Taps>
+// Footprint radius kR: 2 for the 5x5 B3-spline taps (1/16, 1/4, 3/8, 1/4,
+// 1/16), 1 for the 3x3 taps (1/4, 1/2, 1/4) of the lightweight variant.
+template <int kR>
+struct AtrousTaps;
+template <>
+struct AtrousTaps<2> {
+    // log2 of the taps; centre weight (3/8)^2
+    static __device__ __forceinline__ float lg(int i) {
+        return i == 0 ? -1.41503750f : ((i == 1 || i == -1) ? -2.f : -4.f);
+    }
+    static constexpr float kc = 0.375f * 0.375f;
+};
+template <>
+struct AtrousTaps<1> {
+    static __device__ __forceinline__ float lg(int i) { return i == 0 ? -1.f : -2.f; }
+    static constexpr float kc = 0.25f;
+};
+
+template <int kNsq, int kR, class Taps>
 __device__ __forceinline__ AtrousSums atrous_sums(const SvgfConsts& k, int step, float4 cp, float4 zn, float gv0,
                                                   float gv1, float gw, float2 gz, const Taps& taps) {
+    constexpr int kD = 2 * kR + 1, kHalf = kD * kD / 2 + 1;
     // luminance terms folded with log2(e): w_l = 2^(-|dc| il)
     const float rgw = rcp_approx(gw);
     const float il0 = k.wl_in_atrous ? kLog2e * rcp_approx(fmaf(k.sigma_l, sqrt_approx(gv0 * rgw), k.eps_l)) : 0.f;
     const float il1 = k.wl_in_atrous ? kLog2e * rcp_approx(fmaf(k.sigma_l, sqrt_approx(gv1 * rgw), k.eps_l)) : 0.f;
-    // depth terms: log2(e) / (sigma_z |grad z . (p - q)| + eps_z) for the 12
-    // offset directions (i, j) ~ (-i, -j) of the 5x5 footprint
+    // depth terms: log2(e) / (sigma_z |grad z . (p - q)| + eps_z) for the
+    // offset directions (i, j) ~ (-i, -j) of the footprint
     const float sg = k.sigma_z * (float)step;
-    float rz[13];
+    float rz[kHalf];
 #pragma unroll
-    for (int m = 0; m < 13; ++m) {
-        const int i = m % 5 - 2, j = m / 5 - 2;    // j < 0, or j = 0 and i < 0 (+ centre, m = 12)
+    for (int m = 0; m < kHalf; ++m) {
+        const int i = m % kD - kR, j = m / kD - kR;    // j < 0, or j = 0 and i < 0 (+ the centre, last)
         rz[m] = kLog2e * rcp_approx(fmaf(sg, fabsf(fmaf(gz.x, (float)i, gz.y * (float)j)), k.eps_z));
     }
-    const float kc = 0.375f * 0.375f;
+    constexpr float kc = AtrousTaps<kR>::kc;
     // the two channels' sums (w, w c, w^2 var) as f32x2 pairs
     unsigned long long sw = pack2(kc, kc), sc = pack2(kc * cp.x, kc * cp.y);
     unsigned long long sv = pack2(kc * kc * cp.z, kc * kc * cp.w);
-    // log2 of the B3-spline taps 1/16, 1/4, 3/8, 1/4, 1/16
-    const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
 #pragma unroll
-    for (int j = -2; j <= 2; ++j) {
+    for (int j = -kR; j <= kR; ++j) {
 #pragma unroll
-        for (int i = -2; i <= 2; ++i) {
+        for (int i = -kR; i <= kR; ++i) {
             if (i == 0 && j == 0) continue;
             float4 cq, zq;
             taps(i, j, cq, zq);
-            const int m = (j < 0 || (j == 0 && i < 0)) ? (j + 2) * 5 + (i + 2) : (2 - j) * 5 + (2 - i);
-            float e = fmaf(-fabsf(zn.x - zq.x), rz[m], l5[i + 2] + l5[j + 2]);
+            const int m = (j < 0 || (j == 0 && i < 0)) ? (j + kR) * kD + (i + kR) : (kR - j) * kD + (kR - i);
+            float e = fmaf(-fabsf(zn.x - zq.x), rz[m], AtrousTaps<kR>::lg(i) + AtrousTaps<kR>::lg(j));
             e += log2_normal<kNsq>(zn.y * zq.y + zn.z * zq.z + zn.w * zq.w, k.sigma_n);
             const unsigned long long w = pack2(ex2_approx(fmaf(-fabsf(cp.x - cq.x), il0, e)),
                                                ex2_approx(fmaf(-fabsf(cp.y - cq.y), il1, e)));
@@ -609,9 +663,10 @@ __device__ __forceinline__ void atrous_background(int p, float4* out, typename S
 
 // One a-trous iteration over the 32x8 tile t; kMode 0: write illum_out;
 // 1: also the colour history; 2: last iteration, write the two output
-// planes only.  kNsq >= 0: sigma_n is 2^kNsq.  Every thread of the block
-// must call it (block barriers at step 1).
-template <dhr_precision P, int kMode, int kNsq>
+// planes only.  kNsq >= 0: sigma_n is 2^kNsq.  kR: footprint radius (2:
+// 5x5, 1: 3x3).  Every thread of the block must call it (block barriers at
+// step 1).
+template <dhr_precision P, int kMode, int kNsq, int kR = 2>
 __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t, const typename Store<P>::G* g,
                                             const float4* in, float4* out, typename Store<P>::Col* col_hist,
                                             float* ao_out, float* sh_out, AtrousSmem& sm) {
@@ -651,7 +706,7 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
                 var_gauss(v, gv0, gv1, gw);
                 const float2 gz = grad_from(zn.x, sm.g[ty][tx + 1].x, sm.g[ty][tx - 1].x, sm.g[ty + 1][tx].x,
                                             sm.g[ty - 1][tx].x);
-                const AtrousSums a = atrous_sums<kNsq>(k, 1, cp, zn, gv0, gv1, gw, gz, TapsSmem{sm, tx, ty});
+                const AtrousSums a = atrous_sums<kNsq, kR>(k, 1, cp, zn, gv0, gv1, gw, gz, TapsSmem{sm, tx, ty});
                 atrous_store<P, kMode>(a, p, out, col_hist, ao_out, sh_out);
             }
         }
@@ -678,24 +733,27 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
     var_gauss(v, gv0, gv1, gw);
     const float2 gz = grad_from(zn.x, x + 1 < k.W ? S::g(g, p + 1).x : INFINITY, x > 0 ? S::g(g, p - 1).x : INFINITY,
                                 y + 1 < k.H ? S::g(g, p + k.W).x : INFINITY, y > 0 ? S::g(g, p - k.W).x : INFINITY);
-    // blocks whose 5x5 footprint lies inside the image skip the bounds tests
-    const bool interior = bx0 - 2 * step >= 0 && by0 - 2 * step >= 0 && bx0 + kAtW - 1 + 2 * step < k.W &&
-                          by0 + kAtH - 1 + 2 * step < k.H;
+    // blocks whose footprint lies inside the image skip the bounds tests
+    const int reach = kR * step;
+    const bool interior = bx0 - reach >= 0 && by0 - reach >= 0 && bx0 + kAtW - 1 + reach < k.W &&
+                          by0 + kAtH - 1 + reach < k.H;
     AtrousSums a;
     if (interior)
-        a = atrous_sums<kNsq>(k, step, cp, zn, gv0, gv1, gw, gz, TapsGlobal<S, false>{g, in, k.W, k.H, x, y, step});
+        a = atrous_sums<kNsq, kR>(k, step, cp, zn, gv0, gv1, gw, gz,
+                                  TapsGlobal<S, false>{g, in, k.W, k.H, x, y, step});
     else
-        a = atrous_sums<kNsq>(k, step, cp, zn, gv0, gv1, gw, gz, TapsGlobal<S, true>{g, in, k.W, k.H, x, y, step});
+        a = atrous_sums<kNsq, kR>(k, step, cp, zn, gv0, gv1, gw, gz,
+                                  TapsGlobal<S, true>{g, in, k.W, k.H, x, y, step});
     atrous_store<P, kMode>(a, p, out, col_hist, ao_out, sh_out);
 }
 
-template <dhr_precision P, int kMode, int kNsq>
+template <dhr_precision P, int kMode, int kNsq, int kR>
 __global__ void __launch_bounds__(256, 4) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
                                                      const float4* in, float4* out,
                                                      typename Store<P>::Col* col_hist, float* ao_out,
                                                      float* sh_out) {
     __shared__ AtrousSmem sm;
-    atrous_tile<P, kMode, kNsq>(k, step, blockIdx.x, g, in, out, col_hist, ao_out, sh_out, sm);
+    atrous_tile<P, kMode, kNsq, kR>(k, step, blockIdx.x, g, in, out, col_hist, ao_out, sh_out, sm);
 }
 
 // levels == 0: the temporal colour is the output and the colour history
@@ -730,28 +788,42 @@ inline SvgfConsts make_consts(int W, int H, const dhr_svgf_params* prm) {
 
 inline int atrous_nsq(const dhr_svgf_params* prm) { return prm->sigma_n == 128.0f ? 7 : -1; }
 
-template <dhr_precision P, int kMode>
+// footprint radius of the a-trous taps: 1 for kernel_width 3, else 2 (5x5)
+inline int atrous_radius(const dhr_svgf_params* prm) { return prm->kernel_width == 3 ? 1 : 2; }
+
+template <dhr_precision P, int kMode, int kR>
 inline void launch_atrous_mode(int nsq, cudaStream_t st, const SvgfConsts& k, int step,
                                const typename Store<P>::G* g, const float4* in, float4* out,
                                typename Store<P>::Col* col, float* ao_out, float* sh_out) {
     const dim3 grid(atrous_tiles(k.W, k.H)), blk(kAtW, kAtH);
     if (nsq == 7)
-        atrous_kernel<P, kMode, 7><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
+        atrous_kernel<P, kMode, 7, kR><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
     else
-        atrous_kernel<P, kMode, -1><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
+        atrous_kernel<P, kMode, -1, kR><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
 }
 
-// one a-trous iteration at `step` over the whole W x H image of `k`
+template <dhr_precision P, int kR>
+inline void launch_atrous_r(int mode, int nsq, cudaStream_t st, const SvgfConsts& k, int step,
+                            const typename Store<P>::G* g, const float4* in, float4* out,
+                            typename Store<P>::Col* col, float* ao_out, float* sh_out) {
+    if (mode == 2)
+        launch_atrous_mode<P, 2, kR>(nsq, st, k, step, g, in, nullptr, nullptr, ao_out, sh_out);
+    else if (mode == 1)
+        launch_atrous_mode<P, 1, kR>(nsq, st, k, step, g, in, out, col, nullptr, nullptr);
+    else
+        launch_atrous_mode<P, 0, kR>(nsq, st, k, step, g, in, out, nullptr, nullptr, nullptr);
+}
+
+// one a-trous iteration at `step` over the whole W x H image of `k`, with
+// footprint radius R (2: 5x5, 1: 3x3)
 template <dhr_precision P>
-inline dhr_status launch_atrous(int mode, int nsq, cudaStream_t st, const SvgfConsts& k, int step,
+inline dhr_status launch_atrous(int mode, int nsq, int R, cudaStream_t st, const SvgfConsts& k, int step,
                                 const typename Store<P>::G* g, const float4* in, float4* out,
                                 typename Store<P>::Col* col, float* ao_out, float* sh_out) {
-    if (mode == 2)
-        launch_atrous_mode<P, 2>(nsq, st, k, step, g, in, nullptr, nullptr, ao_out, sh_out);
-    else if (mode == 1)
-        launch_atrous_mode<P, 1>(nsq, st, k, step, g, in, out, col, nullptr, nullptr);
+    if (R == 1)
+        launch_atrous_r<P, 1>(mode, nsq, st, k, step, g, in, out, col, ao_out, sh_out);
     else
-        launch_atrous_mode<P, 0>(nsq, st, k, step, g, in, out, nullptr, nullptr, nullptr);
+        launch_atrous_r<P, 2>(mode, nsq, st, k, step, g, in, out, col, ao_out, sh_out);
     DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
 }

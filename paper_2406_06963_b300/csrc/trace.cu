@@ -68,9 +68,13 @@ dhr_status check_trace_params(const dhr_trace_params* p) {
     DHR_CHECK_ARG(p->ao_radius > 0.0f, "ao_radius must be > 0");
     DHR_CHECK_ARG(p->primary == DHR_PRIMARY_TRAVERSE || p->primary == DHR_PRIMARY_RASTER,
                   "primary %u is neither DHR_PRIMARY_TRAVERSE nor DHR_PRIMARY_RASTER", p->primary);
-    for (uint32_t l = 0; l < p->n_lights; ++l)
+    for (uint32_t l = 0; l < p->n_lights; ++l) {
         DHR_CHECK_ARG(p->cone_half_angle[l] >= 0.0f && p->cone_half_angle[l] < 1.5707963f,
                       "cone_half_angle[%u] not in [0, pi/2)", l);
+        const double lx = p->light_dir[l][0], ly = p->light_dir[l][1], lz = p->light_dir[l][2];
+        const double n2 = lx * lx + ly * ly + lz * lz;
+        DHR_CHECK_ARG(n2 > 0.0 && std::isfinite(n2), "light_dir[%u] is zero or not finite", l);
+    }
     return DHR_OK;
 }
 

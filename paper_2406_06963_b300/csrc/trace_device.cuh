@@ -210,6 +210,24 @@ __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tm
     return best;
 }
 
+// Unit normal of a triangle with a written binary32 operation order, each
+// step rounded once (no fused multiply-add), the specification shared with
+// the CPU oracle: a = v1 - v0, b = v2 - v0, c = a x b as (a_y b_z - a_z b_y,
+// a_z b_x - a_x b_z, a_x b_y - a_y b_x), l = sqrt((c_x^2 + c_y^2) + c_z^2),
+// n = c / l, square root and quotients correctly rounded.  The AO sample
+// frame is built from the normal's sign bits (Duff et al.), which switch
+// where a component is zero, so the bits must not depend on the compiler.
+__device__ __forceinline__ float3 unit_normal_rn(float3 v0, float3 v1, float3 v2) {
+    const float ax = __fsub_rn(v1.x, v0.x), ay = __fsub_rn(v1.y, v0.y), az = __fsub_rn(v1.z, v0.z);
+    const float bx = __fsub_rn(v2.x, v0.x), by = __fsub_rn(v2.y, v0.y), bz = __fsub_rn(v2.z, v0.z);
+    const float cx = __fsub_rn(__fmul_rn(ay, bz), __fmul_rn(az, by));
+    const float cy = __fsub_rn(__fmul_rn(az, bx), __fmul_rn(ax, bz));
+    const float cz = __fsub_rn(__fmul_rn(ax, by), __fmul_rn(ay, bx));
+    const float q = __fadd_rn(__fadd_rn(__fmul_rn(cx, cx), __fmul_rn(cy, cy)), __fmul_rn(cz, cz));
+    const float l = __fsqrt_rn(q);
+    return make_float3(__fdiv_rn(cx, l), __fdiv_rn(cy, l), __fdiv_rn(cz, l));
+}
+
 // Secondary-ray origin: the hit point moved along the normal by 16 units in
 // the last place (binary32) of the largest vertex coordinate of the hit
 // triangle -- an exact power of two, larger than the rounding error of the
@@ -235,14 +253,17 @@ struct TraceConsts {
     uint32_t seed;
 };
 
-// trace constants of one frame; tan of each cone half angle is computed in
-// double on the host and rounded once
+// trace constants of one frame; each light direction is normalised and the
+// tan of each cone half angle computed in double on the host, each rounded
+// once to binary32
 inline TraceConsts make_trace_consts(const dhr_camera& cam, const dhr_trace_params& p) {
     TraceConsts k;
     k.cam = cam;
     for (uint32_t l = 0; l < DHR_MAX_LIGHTS; ++l) {
         if (l < p.n_lights) {
-            k.light[l] = make_float3(p.light_dir[l][0], p.light_dir[l][1], p.light_dir[l][2]);
+            const double lx = p.light_dir[l][0], ly = p.light_dir[l][1], lz = p.light_dir[l][2];
+            const double n = std::sqrt(lx * lx + ly * ly + lz * lz);
+            k.light[l] = make_float3((float)(lx / n), (float)(ly / n), (float)(lz / n));
             k.tan_cone[l] = (float)std::tan((double)p.cone_half_angle[l]);
         } else {
             k.light[l] = make_float3(0.f, 1.f, 0.f);
@@ -518,9 +539,7 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
     const float3 X = make_float3(bary.x * v0.x + bary.y * v1.x + bary.z * v2.x,
                                  bary.x * v0.y + bary.y * v1.y + bary.z * v2.y,
                                  bary.x * v0.z + bary.y * v1.z + bary.z * v2.z);
-    float3 n = cross(sub(v1, v0), sub(v2, v0));
-    const float inv_len = rsqrtf(dot(n, n));
-    n = make_float3(n.x * inv_len, n.y * inv_len, n.z * inv_len);
+    float3 n = unit_normal_rn(v0, v1, v2);
     if (dot(n, D) > 0.0f) n = make_float3(-n.x, -n.y, -n.z);
     const float depth = dot(sub(X, eye), fw);
     if (kHalf) {

@@ -1,8 +1,20 @@
-"""FP16 storage form: the normal (two binary16 octahedral coordinates), the
-colour history and the moments in binary16; depth, the variance buffer,
-intersection and all arithmetic in binary32.  Per-buffer error against the
-fp64 oracle (same inputs; the oracle's G-buffer packed into the FP16 form for
-the GPU) and against the FP32 path, reported and bounded.
+"""16-bit storage form (DHR_FP16): the normal (two octahedral coordinates,
+16-bit signed-normalised) and the first moments (16-bit unsigned-normalised)
+in 16 bits; depth, the colour history, the variances, intersection and all
+arithmetic in binary32.  Per-buffer error against the fp64 oracle (same
+inputs; the oracle's G-buffer packed into the 16-bit form for the GPU) and
+against the FP32 path; the filtered AO and shadow must stay within 1e-3 of
+both everywhere.
+
+(A first layout kept the colour history and mu2 in binary16 too: an
+exponential moving average stored in binary16 stops moving once alpha |s - h|
+is below half a unit in the last place -- up to 2^-12 / 0.2 = 1.2e-3 from its
+input near 1 -- and mu2 - mu1^2 cancels; filtered errors reached 2.2e-3 (AO)
+and 3.7e-3 (shadow) against the oracle, 4.9e-3 against FP32 at 4K.  With the
+colour history and variances in binary32 but mu1 and the normal in binary16,
+the oracle bar was met and the FP32 comparison at 4K still reached 3.7e-3:
+11 bits of mu1 leave percent-level errors in (s - mu1)^2 and hence in the
+variance that weighs the luminance term.)
 
 (An earlier layout also stored depth in binary16: surfaces whose depth
 changes by less than one binary16 step per pixel then get a zero depth
@@ -37,7 +49,7 @@ def test_fp16_storage_vs_fp64_oracle():
     ao_o = torch.empty((H, W), device="cuda")
     sh_o = torch.empty_like(ao_o)
     prev = None
-    table = {k: [] for k in ("depth", "normal", "moments", "color_hist", "ao", "shadow")}
+    table = {k: [] for k in ("depth", "normal", "mu1", "variance", "color_hist", "ao", "shadow")}
     for f, cam in enumerate(cams):
         tr = orc.trace(S, cam, orc.TraceParams(frame=f))
         zn, mesh = orc.gbuffer_f32(tr, W, H)
@@ -53,9 +65,12 @@ def test_fp16_storage_vs_fp64_oracle():
         table["depth"].append((gz[..., 0][fg] - tr["depth"].reshape(H, W)[fg]) / tr["depth"].reshape(H, W)[fg])
         table["normal"].append((gz[..., 1:] - tr["normal"].reshape(H, W, 3))[fg])
         b = gst.buffers()
-        mom = dhrs.device_copy(b["moments"], (H, W, 4), "float16").float().cpu().numpy()
-        col = dhrs.device_copy(b["color_hist"], (H, W, 2), "float16").float().cpu().numpy()
-        table["moments"].append((mom - ost.mom)[fg])
+        rec = dhrs.device_copy(b["moments"], (H, W, 12), "uint8").cpu().numpy()
+        mu1 = np.ascontiguousarray(rec[..., :4]).view(np.uint16).astype(np.float64) / 65535.0
+        var = np.ascontiguousarray(rec[..., 4:]).view(np.float32).astype(np.float64)
+        col = dhrs.device_copy(b["color_hist"], (H, W, 2), "float32").cpu().numpy()
+        table["mu1"].append((mu1 - ost.mom[..., :2])[fg])
+        table["variance"].append((var - np.maximum(0, ost.mom[..., 2:] - ost.mom[..., :2] ** 2))[fg])
         table["color_hist"].append((col - ost.col)[fg])
         table["ao"].append(ao_o.cpu().numpy() - ref["ao"])
         table["shadow"].append(sh_o.cpu().numpy() - ref["shadow"])
@@ -64,9 +79,9 @@ def test_fp16_storage_vs_fp64_oracle():
     for k, v in rep.items():
         print(f"fp16 vs fp64 oracle  {k:10s} max {v['max']:.3g}  p99 {v['p99']:.3g}  mean {v['mean']:.3g}")
     assert rep["depth"]["max"] < 1e-6            # binary32 depth
-    assert rep["normal"]["max"] < 2e-3           # octahedral binary16
+    assert rep["normal"]["max"] < 1e-4           # octahedral, 16-bit fixed point
     for k in ("ao", "shadow"):
-        assert rep[k]["p99"] <= 1e-3 and rep[k]["mean"] <= 1e-4, (k, rep[k])
+        assert rep[k]["max"] <= 1e-3 and rep[k]["mean"] <= 1e-4, (k, rep[k])
 
 
 @pytest.mark.slow
@@ -96,4 +111,4 @@ def test_fp16_vs_fp32_path_4k():
             e = torch.cat([(a16 - a32).abs().ravel(), (h16 - h32).abs().ravel()]).cpu().numpy()
             print(f"fp16 vs fp32 4K frame {f}: max {e.max():.3g} p99 {np.percentile(e, 99):.3g} "
                   f"mean {e.mean():.3g}")
-            assert np.percentile(e, 99) <= 1e-3 and e.mean() <= 1e-4
+            assert e.max() <= 1e-3 and e.mean() <= 1e-4

@@ -81,6 +81,16 @@ def test_svgf_ragged_and_levels(levels):
     assert _run_both(frames, cams, orc.SvgfParams(levels=levels)) <= TOL
 
 
+@pytest.mark.parametrize("levels,size", [(1, (96, 64)), (5, (96, 64)), (1, (37, 23)), (2, (37, 23))])
+def test_svgf_small_kernel(levels, size):
+    """The lightweight denoiser's smaller kernel (3x3 taps 1/4, 1/2, 1/4;
+    Section 3.3), one level as proposed and more, full and ragged images."""
+    s = wl.scene_boxes()
+    cams = wl.orbit_path(5, *size, degrees=8.0)
+    frames = _oracle_frames(s, cams)
+    assert _run_both(frames, cams, orc.SvgfParams(levels=levels, kernel_width=3)) <= TOL
+
+
 def test_svgf_fixed_alpha_no_luminance_multi_spp():
     s = wl.scene_boxes()
     cams = wl.orbit_path(6, 96, 64, degrees=6.0)
@@ -119,9 +129,24 @@ def test_svgf_rejects_bad_arguments():
     cam = wl.boxes_camera(16, 16)
     m = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
     o = torch.empty((16, 16), device="cuda")
-    for bad in (dict(levels=9), dict(ao_spp=0), dict(alpha=0.0), dict(shadow_light=8)):
+    for bad in (dict(levels=9), dict(ao_spp=0), dict(alpha=0.0), dict(shadow_light=8), dict(kernel_width=4)):
         with pytest.raises(dhrs.DhrError):
             st.reconstruct(g, None, cam, None, m, m, dhrs.SvgfParams(**bad), o, o)
     g16 = dhrs.GBuffer(16, 16, dhrs.DHR_FP16)
     with pytest.raises(dhrs.DhrError):
         st.reconstruct(g16, None, cam, None, m, m, dhrs.SvgfParams(), o, o)
+
+
+@pytest.mark.slow
+def test_svgf_terrain_spline_1080p():
+    """Three consecutive frames of the terrain camera spline at 1920x1080, the
+    launch configuration bench.py times, on a coarse version of the terrain
+    scene the brute-force oracle can trace in seconds: the same seeded
+    heightfield on a 24 x 24 vertex grid with 8 icospheres and 8 boxes
+    (1,794 triangles).  Distant terrain seen 25 degrees down exercises the
+    depth-slope term of the reprojection test; history lengths must be
+    identical and the filtered outputs within 1e-3 everywhere."""
+    s = wl.scene_terrain(n_spheres=8, n_boxes=8, sphere_level=1, terrain_n=24)
+    cams = wl.spline_path(s["terrain"], 60, 1920, 1080)[:3]
+    frames = _oracle_frames(s, cams)
+    assert _run_both(frames, cams, orc.SvgfParams()) <= TOL

@@ -91,9 +91,11 @@ def test_trace_ragged_sizes(boxes, w, h):
 
 
 def test_trace_terrain_1080p_sampled(terrain):
-    """1920x1080, 776,050 triangles, the configuration bench.py times: the
-    full GPU frame against 1024 seeded pixels traced one by one by the
-    oracle.  Every disagreement must be a grazing ray."""
+    """1920x1080, 776,050 triangles, the configuration bench.py times
+    (rasterised primary visibility, as in its session frames): the full GPU
+    frame against 16,384 seeded pixels of two frames (about 45,000 rays)
+    traced one by one by the oracle.  Every disagreement must be a grazing
+    ray, and disagreements may touch at most 1e-4 of the rays."""
     s, g_scene, o_scene = terrain
     info = g_scene.info()
     assert info["n_triangles"] == 776050 and info["n_nodes"] == 776049
@@ -106,13 +108,15 @@ def test_trace_terrain_1080p_sampled(terrain):
     for f in (0, 37):
         tp = orc.TraceParams(frame=f)
         gpu = trace_gpu(g_scene, cams[f], gpu_params(tp))
-        pix = np.stack([r.integers(0, 1920, 512), r.integers(0, 1080, 512)], -1)
+        pix = np.stack([r.integers(0, 1920, 8192), r.integers(0, 1080, 8192)], -1)
         ref = orc.trace(o_scene, cams[f], tp, pixels=pix)
         res = compare_trace(gpu, ref, pix[:, 1] * 1920 + pix[:, 0], 1, 1)
         _check(res, max_frac=1.0)
         tot = res if tot is None else {k: tot[k] + res[k] for k in res}
-    # at most a handful of grazing disagreements among ~3000 rays
-    assert tot["disagree"] <= 3, tot
+    print(f"terrain 1080p: {tot['rays']} rays, {tot['disagree']} disagree, "
+          f"{tot['ambiguous_rays']} within the oracle's grazing margin")
+    assert tot["rays"] >= 40000, tot
+    assert tot["disagree"] <= 1e-4 * tot["rays"], tot
 
 
 def test_cast_rays_matches_brute_force(boxes):

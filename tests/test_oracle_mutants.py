@@ -26,9 +26,12 @@ MUTANTS = [
      [REPRO + "::test_grazing_floor_keeps_one_pixel_taps"]),
     ("slope term x1", "volatile float zsl = 2.0f * slope;", "volatile float zsl = 1.0f * slope;",
      [REPRO + "::test_depth_tolerance_is_two_slopes"]),
-    ("larger one-sided difference", "if (has_p && has_m) g[ax] = (fabsf(dm) < fabsf(dp)) ? dm : dp;",
-     "if (has_p && has_m) g[ax] = (fabsf(dm) > fabsf(dp)) ? dm : dp;",
-     [REPRO + "::test_depth_step_takes_the_smaller_side"]),
+    ("larger one-sided difference", "? ((fabsf(dm) < fabsf(dp)) ? dm : dp)", "? ((fabsf(dm) > fabsf(dp)) ? dm : dp)",
+     [REPRO + "::test_depth_tolerance_is_two_slopes"]),
+    ("slope without the sign test", "((dp > 0.0f && dm > 0.0f) || (dp < 0.0f && dm < 0.0f))", "1",
+     [REPRO + "::test_ridge_slope_is_zero"]),
+    ("a-trous slope without the sign test", "((dp > 0.0 && dm > 0.0) || (dp < 0.0 && dm < 0.0))", "1",
+     ["tests/test_oracle_svgf.py::test_atrous_ridge_is_filtered_along_itself"]),
     ("depth weight offset without the step",
      "double wz = w_depth(zn[4 * p], zn[4 * q], g, -(double)i * step,\n"
      "                                                -(double)j * step, P);",

@@ -13,9 +13,12 @@ that geometry, not by the oracle:
 * a one-pixel bilinear tap on a grazing floor stays valid because of the
   slope term (without it the tap is rejected and the blend renormalises);
 * a history depth offset of 1.5 slopes (beyond the 1 %) is accepted and
-  one of 2.5 slopes is rejected, which brackets the factor 2;
-* at a depth step the slope is the smaller one-sided difference (0 beside
-  the step), so a 2 % depth change is rejected there as everywhere;
+  one of 2.5 slopes is rejected, which brackets the factor 2 (on the convex
+  floor the far-side difference is up to 1.4 times the near-side one, so
+  this also fixes which side is taken);
+* beside a depth step one difference is 0, and on a one-pixel ridge the two
+  differ in sign: the slope is 0 (minmod) and a 2 % depth change is
+  rejected there as on any flat surface;
 * the binary32 decision the temporal step takes equals the plain double
   definition on every pixel not within a stated margin of a threshold.
 """
@@ -206,3 +209,22 @@ def test_binary32_decision_equals_double_definition_grazing():
     r = _compare(zn, mesh, cam, (znp, meshp, camp))
     assert r["bad"] == 0, r
     assert r["valid"] > 0.5 * r["fg"], r
+
+
+def test_ridge_slope_is_zero():
+    """A one-pixel column 0.5 in front of a fronto-parallel plane at depth 8:
+    its two horizontal one-sided depth differences are +0.5 and -0.5, so its
+    slope is 0 (minmod) and a 2 % depth change of its history is rejected
+    as anywhere on a flat surface, while a 0.5 % change is kept."""
+    cam = wl.look_at((0.0, 0.0, 0.0), (0.0, 0.0, -1.0), W, H)
+    zn = np.zeros((H, W, 4), np.float32)
+    zn[..., 0] = 8.0
+    zn[:, 20, 0] = 7.5
+    zn[..., 3] = 1.0
+    mesh = np.zeros((H, W), np.uint32)
+    for scale, valid in ((1.02, 0), (1.005, 1)):
+        znp = zn.copy()
+        znp[..., 0] *= np.float32(scale)
+        res = orc.svgf_temporal(zn, mesh, cam, np.zeros((H, W), np.uint8), np.zeros((H, W), np.uint8),
+                                orc.SvgfParams(ao_spp=255), prev=(znp, mesh, cam), hist=np.full((H, W), 3, np.int32))
+        assert (res["valid"][:, 20] == valid).all(), scale

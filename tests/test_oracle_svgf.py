@@ -28,9 +28,12 @@ def _flat_gbuffer(H, W, depth=5.0, normal=(0.0, 0.0, 1.0), background=None):
     return zn, mesh
 
 
-def _dilated(step):
-    k = np.zeros(4 * step + 1)
-    k[::step] = B3
+K3 = np.array([1 / 4, 1 / 2, 1 / 4])
+
+
+def _dilated(step, taps=B3):
+    k = np.zeros((len(taps) - 1) * step + 1)
+    k[::step] = taps
     return np.outer(k, k)
 
 
@@ -59,26 +62,29 @@ def test_atrous_constant_image(orc):
     illum[..., 1] = 0.81
     illum[..., 2:] = r.uniform(0, 0.3, (H, W, 2))
     for step in (1, 2, 4, 8, 16):
-        out = orc.svgf_atrous(zn, illum, step, orc.SvgfParams())
-        assert np.allclose(out[~bg, 0], 0.37, atol=1e-12)
-        assert np.allclose(out[~bg, 1], 0.81, atol=1e-12)
-        assert np.all(out[bg, :2] == 1.0)
+        for width in (5, 3):
+            out = orc.svgf_atrous(zn, illum, step, orc.SvgfParams(kernel_width=width))
+            assert np.allclose(out[~bg, 0], 0.37, atol=1e-12)
+            assert np.allclose(out[~bg, 1], 0.81, atol=1e-12)
+            assert np.all(out[bg, :2] == 1.0)
 
 
+@pytest.mark.parametrize("width", [5, 3])
 @pytest.mark.parametrize("step", [1, 2, 4, 8, 16])
-def test_atrous_reduces_to_textbook_b3(orc, step):
+def test_atrous_reduces_to_textbook_b3(orc, step, width):
     """Without edge stopping (flat depth, sigma_n = 0, sigma_l -> inf) the pass
-    is the textbook B3-spline a-trous transform with holes at `step`,
-    renormalised over in-image foreground taps; variance is filtered with
-    the squared kernel."""
+    is the textbook a-trous transform with holes at `step` -- B3-spline taps,
+    or (1/4, 1/2, 1/4) for the smaller kernel of the lightweight denoiser
+    (Section 3.3) -- renormalised over in-image foreground taps; variance is
+    filtered with the squared kernel."""
     r = np.random.default_rng(step)
     H, W = 48, 70
     bg = r.random((H, W)) < 0.08
     zn, _ = _flat_gbuffer(H, W, background=bg)
     illum = r.uniform(0.05, 1, (H, W, 4))
-    out = orc.svgf_atrous(zn, illum, step, orc.SvgfParams(**P_TEXTBOOK))
+    out = orc.svgf_atrous(zn, illum, step, orc.SvgfParams(kernel_width=width, **P_TEXTBOOK))
     m = (~bg).astype(float)
-    k = _dilated(step)
+    k = _dilated(step, B3 if width == 5 else K3)
     for ch in range(2):
         ref_c = _normconv(illum[..., ch], m, k)
         num_v = ndimage.correlate(illum[..., 2 + ch] * m, k * k, mode="constant")
@@ -90,13 +96,16 @@ def test_atrous_reduces_to_textbook_b3(orc, step):
 
 def test_atrous_variance_closed_form(orc):
     """Constant variance v away from borders: v' = v (sum of squared taps)
-    = v (1/16^2 * 2 + 1/4^2 * 2 + (3/8)^2)^2 = 0.07476806640625 v."""
+    = v (1/16^2 * 2 + 1/4^2 * 2 + (3/8)^2)^2 = 0.07476806640625 v, and
+    v (1/4^2 * 2 + 1/2^2)^2 = 0.140625 v for the 3x3 kernel."""
     H, W = 30, 30
     zn, _ = _flat_gbuffer(H, W)
     illum = np.full((H, W, 4), 0.5)
     illum[..., 2:] = 0.2
     out = orc.svgf_atrous(zn, illum, 1, orc.SvgfParams(**P_TEXTBOOK))
     assert np.allclose(out[5:-5, 5:-5, 2:], 0.2 * 0.07476806640625, atol=1e-15)
+    out = orc.svgf_atrous(zn, illum, 1, orc.SvgfParams(kernel_width=3, **P_TEXTBOOK))
+    assert np.allclose(out[5:-5, 5:-5, 2:], 0.2 * 0.140625, atol=1e-15)
 
 
 def test_atrous_depth_edge_stops(orc):
@@ -351,3 +360,33 @@ def test_atrous_depth_weight_on_a_tilted_plane(orc, step, sigma_z):
         den = kc + E * (1 - kc)
         assert np.allclose(out[inner + (ch,)], (num / den)[inner], atol=1e-12)
         assert np.allclose(out[inner + (2 + ch,)], (num_v / den ** 2)[inner], atol=1e-12)
+
+
+@pytest.mark.parametrize("step", [1, 2])
+def test_atrous_ridge_is_filtered_along_itself(orc, step):
+    """A one-pixel column one unit in front of a fronto-parallel plane (depth
+    10 -> 9).  On the column the horizontal one-sided depth differences are
+    +1 and -1, so its depth slope is 0 (minmod) and every tap off the column
+    has w_z = exp(-1 / eps_z) = exp(-100): the column is filtered along
+    itself only, by the 1-D B3 kernel.  Beside it one difference is 0, so the
+    slope is 0 there too and the plane never takes the column's taps."""
+    r = np.random.default_rng(30 + step)
+    H, W = 40, 48
+    zn, _ = _flat_gbuffer(H, W, depth=10.0)
+    c = 23
+    zn[:, c, 0] = 9.0
+    illum = r.uniform(0.05, 1, (H, W, 4))
+    out = orc.svgf_atrous(zn, illum, step, orc.SvgfParams(**P_TEXTBOOK))
+    k1 = np.zeros(4 * step + 1)
+    k1[::step] = B3
+    col = np.zeros((H, W))
+    col[:, c] = 1.0
+    k2 = np.zeros((len(k1), len(k1)))
+    k2[:, 2 * step] = k1                   # vertical taps only
+    for ch in range(2):
+        ref_col = _normconv(illum[..., ch], col, k2)
+        assert np.allclose(out[:, c, ch], ref_col[:, c], atol=1e-12)
+        plane = 1.0 - col
+        ref_plane = _normconv(illum[..., ch], plane, _dilated(step))
+        m = plane.astype(bool)
+        assert np.allclose(out[m, ch], ref_plane[m], atol=1e-12)

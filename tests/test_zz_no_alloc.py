@@ -8,7 +8,9 @@ it keeps its ping-pong images in a fixed device array instead.  The test
 feeds it the temporal output of dhr_svgf_reconstruct on two consecutive
 frames (two calls in a row reusing the same fixed array) and compares with
 the outputs dhr_svgf_reconstruct wrote, within the 1e-3 bar of the SVGF
-parity tests.  It also checks the size limit.
+parity tests, for one, two and five levels (one level writes the outputs
+directly; an even count ends in the second half of the array), the second
+call on a stream of its own.  It also checks the size and alignment limits.
 """
 import numpy as np
 import pytest
@@ -22,14 +24,16 @@ torch = pytest.importorskip("torch")
 TOL = 1e-3
 
 
+@pytest.mark.parametrize("levels", [1, 2, 5])
 @pytest.mark.parametrize("precision", [dhrs.DHR_FP32, dhrs.DHR_FP16])
-def test_noalloc_atrous_matches_reconstruct(precision):
+def test_noalloc_atrous_matches_reconstruct(precision, levels):
     W, H = 320, 200
     s = wl.scene_boxes()
     sc = dhrs.Scene(s)
     cams = wl.orbit_path(2, W, H, degrees=4.0)
     st = dhrs.SvgfState(W, H, precision)
-    params = dhrs.SvgfParams()
+    params = dhrs.SvgfParams(levels=levels)
+    side = torch.cuda.Stream()
     ao_ref = torch.empty((H, W), device="cuda")
     sh_ref = torch.empty_like(ao_ref)
     ao_na = torch.empty_like(ao_ref)
@@ -45,7 +49,11 @@ def test_noalloc_atrous_matches_reconstruct(precision):
         illum_ptr = st.buffers()["illum"]
         ao_na.fill_(-7.0)
         sh_na.fill_(-7.0)
-        dhrs.svgf_atrous_noalloc(g, illum_ptr, params, ao_na, sh_na)
+        if f == 0:
+            dhrs.svgf_atrous_noalloc(g, illum_ptr, params, ao_na, sh_na)
+        else:
+            side.wait_stream(torch.cuda.current_stream())
+            dhrs.svgf_atrous_noalloc(g, illum_ptr, params, ao_na, sh_na, stream=side)
         torch.cuda.synchronize()
         err = max(float((ao_na - ao_ref).abs().max()), float((sh_na - sh_ref).abs().max()))
         assert err <= TOL, (f, err)
@@ -64,3 +72,6 @@ def test_noalloc_rejects_oversized_and_bad_levels():
     o2 = torch.empty((64, 64), device="cuda")
     with pytest.raises(dhrs.DhrError):
         dhrs.svgf_atrous_noalloc(g2, illum.data_ptr(), dhrs.SvgfParams(levels=0), o2, o2)
+    with pytest.raises(dhrs.DhrError) as e:
+        dhrs.svgf_atrous_noalloc(g2, illum.data_ptr() + 4, dhrs.SvgfParams(), o2, o2)
+    assert e.value.status == 1 and "aligned" in str(e.value)
