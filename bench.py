@@ -414,6 +414,7 @@ def run_ours(args):
     }
     if not args.no_forms:
         res["serving"] = run_serving(sc, scene_d, seconds=args.serve_seconds)
+        res["serving_device_loop"] = run_serving(sc, scene_d, seconds=args.serve_seconds, mode="device_loop")
         res["precision_form"] = run_precision_form(sc, scene_d)
         res["adjoint"] = run_adjoint(sc, scene_d)
         res["denoise_variants"] = run_denoise_variants(sc, scene_d)
@@ -432,13 +433,19 @@ def run_ours(args):
 SERVE_BATCH_PX = int(os.environ.get("DHR_SERVE_BATCH_PX", str(2 << 20)))
 
 
-def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30, max_batch_px=SERVE_BATCH_PX):
+def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30, max_batch_px=SERVE_BATCH_PX,
+                mode="host"):
     """32 thin-client sessions, resolutions drawn from {640x360, 1280x720,
     1920x1080, 2560x1440}, each sending camera poses as a 60 Hz Poisson
     process along its own seeded spline, with a network delay U[0, 200] ms
     per session (the request arrives late and its result is warped to the
     pose at arrival).  Real-time simulation for `seconds`; latency = device
-    completion - arrival at the server (network delay excluded)."""
+    completion - arrival at the server (network delay excluded).
+    mode "host": the host forms each batch (dhr_server_pump); "device_loop":
+    the device-resident request loop (dhr_server_loop_start) takes the
+    requests from its mailboxes and forms the batches itself."""
+    import gc
+
     import numpy as np
 
     import paper_2406_06963_b300 as dhrs
@@ -473,6 +480,12 @@ def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30, max_ba
     events.sort(key=lambda e: e[0])
     lat, done_px, batches = [], 0, []
     dropped = 0
+    if mode == "device_loop":
+        # no device-wide synchronisation while the loop runs (a collected
+        # CUDA object would make one)
+        gc.collect()
+        gc.disable()
+        srv.loop_start(idle_ms=2000, max_run_ms=int((seconds + 30) * 1000))
     start = dhrs.now_ns() + 20_000_000
     idx = 0
     rid = 0
@@ -494,10 +507,13 @@ def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30, max_ba
         if idx >= len(events) and len(lat) + dropped >= len(events):
             break
     wall = (dhrs.now_ns() - start) * 1e-9
+    if mode == "device_loop":
+        srv.loop_stop()
+        gc.enable()
     st = srv.stats()
     srv.close()
     lat = np.array(lat)
-    return {"workload": "32 sessions x 60 Hz Poisson, delay U[0,200] ms, terrain776k",
+    return {"workload": "32 sessions x 60 Hz Poisson, delay U[0,200] ms, terrain776k", "mode": mode,
             "sessions_admitted": admitted, "sessions_refused": refused, "requests": len(events),
             "completed": int(len(lat)), "dropped_latest_wins": dropped,
             "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),

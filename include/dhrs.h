@@ -563,8 +563,9 @@ dhr_status dhr_server_create(const dhr_scene* scene, uint64_t budget_bytes,
                              dhr_server** out);
 void dhr_server_destroy(dhr_server* server);
 
-/* Admits a session if its buffers fit the remaining budget, else
- * DHR_ERR_ADMISSION (retry after other sessions close). */
+/* Admits a session if its buffers fit the remaining budget (and fewer than
+ * 1024 sessions are open), else DHR_ERR_ADMISSION (retry after other
+ * sessions close). */
 dhr_status dhr_server_open(dhr_server* server, int32_t width, int32_t height, int32_t* session_out);
 
 /* Closes a session; its memory returns to the budget once its frame in
@@ -598,8 +599,53 @@ dhr_status dhr_server_pump(dhr_server* server, int32_t* launched);
 dhr_status dhr_server_poll(dhr_server* server, dhr_completion* out, int32_t max, int32_t* n_out,
                            int32_t wait);
 
+/* Device-resident request loop.  Instead of the host forming batches
+ * (dhr_server_pump), one graph launch keeps running on the device: a
+ * scheduling kernel reads each session's newest request from a mailbox in
+ * mapped host memory, takes one per session -- oldest arrival first, at most
+ * 64 and the batch pixel cap -- builds the batch table in device memory and
+ * runs the batch's stages (trace, temporal, a-trous, target G-buffer, delay
+ * warp), then writes completion records (device timestamps) to a ring in
+ * mapped memory; a WHILE conditional node repeats this with no host step
+ * between batches.  Two such loops run side by side on two streams over the
+ * same mailboxes (a session is claimed by one of them at a time, so its
+ * frames stay in order), so that one batch's tail overlaps another's head.  While it runs, dhr_server_submit writes the mailbox (a
+ * newer request replaces one the loop has not taken: latest wins),
+ * dhr_server_poll and dhr_server_pump collect its records, and closed
+ * sessions are freed once no batch can still use them.  The loop ends when
+ * dhr_server_loop_stop asks it to, when no request has arrived for idle_ms
+ * (1..600000), or after max_run_ms (1..3600000); each scheduling pass waits
+ * for requests at most 50 us (%globaltimer), so every device-side wait is
+ * bounded.  After the loop ends by a limit, dhr_server_poll(wait = 1) with
+ * nothing to report and dhr_server_loop_stop return DHR_ERR_TIMEOUT.
+ * Session histories carry over between the two modes.  At most 1024
+ * sessions per server.  The library makes no device-wide synchronisation
+ * while the loop runs (session memory is allocated and freed stream
+ * ordered); a device-wide synchronisation elsewhere in the process
+ * (cudaDeviceSynchronize, cudaFree, cudaFreeHost, destroying another scene
+ * or server, or a framework call that makes one) waits until the loop ends,
+ * which the idle limit bounds.
+ * Errors: DHR_ERR_INVALID (limits out of range, loop already running),
+ * DHR_ERR_CUDA. */
+dhr_status dhr_server_loop_start(dhr_server* server, uint32_t idle_ms, uint32_t max_run_ms);
+
+/* Asks the loop to end and waits for it (bounded by its limits), collects its
+ * last records, hands requests it did not take back to the host's queue.
+ * DHR_OK if it ended on this request (or was not running), DHR_ERR_TIMEOUT
+ * if it had already ended at its idle or run-time limit. */
+dhr_status dhr_server_loop_stop(dhr_server* server);
+
+/* *running = 1 while the loop runs; *batches (may be NULL) = scheduling
+ * passes done so far. */
+dhr_status dhr_server_loop_status(dhr_server* server, int32_t* running, uint64_t* batches);
+
 /* Device pointers (float [H][W]) of the session's last completed output. */
 dhr_status dhr_server_output(dhr_server* server, int32_t session, float** ao, float** shadow);
+
+/* Copies the session's last completed output into host memory (float
+ * [H][W] each) on a stream of the server's own and waits for that stream
+ * only, so it may be called while the device loop runs. */
+dhr_status dhr_server_read_output(dhr_server* server, int32_t session, float* ao_host, float* shadow_host);
 
 dhr_status dhr_server_get_stats(dhr_server* server, dhr_server_stats* out);
 

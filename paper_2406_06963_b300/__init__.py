@@ -114,6 +114,10 @@ _SIGNATURES = {
     "dhr_server_poll": ([_P, _P, C.c_int32, _P, C.c_int32], C.c_int),
     "dhr_server_output": ([_P, C.c_int32, _P, _P], C.c_int),
     "dhr_server_get_stats": ([_P, _P], C.c_int),
+    "dhr_server_read_output": ([_P, C.c_int32, _P, _P], C.c_int),
+    "dhr_server_loop_start": ([_P, C.c_uint32, C.c_uint32], C.c_int),
+    "dhr_server_loop_stop": ([_P], C.c_int),
+    "dhr_server_loop_status": ([_P, _P, _P], C.c_int),
     "dhr_session_create": ([_P, C.c_int32, C.c_int32, C.c_int, _P, _P, _P], C.c_int),
     "dhr_session_destroy": ([_P], None),
     "dhr_step_frame": ([_P, _P, C.c_uint32, _P, _P, _P], C.c_int),
@@ -743,10 +747,27 @@ class Server:
         return out
 
     def output(self, sid, width, height):
-        """Copies of the session's last completed (warped) AO and shadow."""
-        a, s_ = C.c_void_p(), C.c_void_p()
-        _check(lib().dhr_server_output(self.h, sid, C.byref(a), C.byref(s_)))
-        return device_copy(a.value, (height, width), "float32"), device_copy(s_.value, (height, width), "float32")
+        """Host copies (numpy float32 [H, W]) of the session's last completed
+        (warped) AO and shadow, made on the server's own stream (so that it
+        does not wait for a running device loop)."""
+        a = np.empty((height, width), np.float32)
+        b = np.empty((height, width), np.float32)
+        _check(lib().dhr_server_read_output(self.h, sid, a.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p)))
+        return a, b
+
+    def loop_start(self, idle_ms: int = 1000, max_run_ms: int = 600000):
+        """Start the device-resident request loop (dhr_server_loop_start)."""
+        _check(lib().dhr_server_loop_start(self.h, int(idle_ms), int(max_run_ms)))
+
+    def loop_stop(self):
+        """End the device loop and wait for it; raises DhrError(status 4) if it
+        had already ended at its idle or run-time limit."""
+        _check(lib().dhr_server_loop_stop(self.h))
+
+    def loop_status(self):
+        r, b = C.c_int32(), C.c_uint64()
+        _check(lib().dhr_server_loop_status(self.h, C.byref(r), C.byref(b)))
+        return bool(r.value), int(b.value)
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -16,8 +16,11 @@
 // levels, target G-buffer, delay warp).  Two slots on two streams let the
 // next batch be staged and launched while the previous one runs.
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <deque>
+#include <map>
+#include <thread>
 #include <vector>
 
 #include "svgf_kernels.cuh"
@@ -217,6 +220,412 @@ __global__ void __launch_bounds__(256) warp_kernel(int W, int H, dhr_camera cam_
     warp_pixel(x, y, W, H, cam_tgt, cam_src, g_tgt, m_tgt, g_src, m_src, src_ao, src_sh, out_ao, out_sh);
 }
 
+// ------------------------------------------------------------------------
+// Device-resident request loop.  One graph launch runs a WHILE conditional
+// node whose body is a scheduling kernel followed by an IF node holding the
+// stages of a batch.  The host only writes requests into per-session
+// mailboxes and reads completion records, both in mapped host memory; the
+// loop picks requests, builds the batch table in device memory, runs the
+// stages and publishes completions without returning to the host.  It ends
+// when the host asks it to stop, when no request has arrived for the idle
+// limit (status DHR_ERR_TIMEOUT), or at a hard limit on its run time and
+// iterations; no kernel of it waits on another kernel, and the one wait it
+// has (for requests, inside a scheduling pass) is bounded by %globaltimer
+// and a pass count.
+// ------------------------------------------------------------------------
+constexpr int kLoopMaxSessions = 1024;
+constexpr uint64_t kRingRecords = 1u << 14;
+constexpr int kLoopPolls = 64;          // polls of the mailboxes in one scheduling pass
+// loops running side by side on their own streams over the same mailboxes
+// (a session is claimed by one of them at a time), so that one batch's
+// tail overlaps the next batch's head, as two host-launched slots do
+constexpr int kLoops = 2;
+
+// host -> device, one per session slot; the host is the only writer.  seq
+// is odd while the host writes and 2k once request k (k = 1, 2, ...) is
+// complete: a newer request replaces an untaken older one (latest wins).
+struct alignas(16) Mailbox {
+    uint32_t seq;
+    uint32_t warp;
+    uint32_t frame;
+    uint32_t pad;
+    uint64_t t_arrival;
+    uint64_t request_id;
+    dhr_camera cam;
+    dhr_camera cam_target;
+};
+
+// host -> device, one per session slot: its buffers.  generation is odd
+// while the host writes and even when stable; a new even value is a new
+// session (the loop resets its per-session state).
+struct alignas(16) SessionSlot {
+    uint32_t generation;
+    int32_t open;
+    int32_t w, h;
+    float4* g[2];
+    uint32_t* m[2];
+    float4* mom[2];
+    uint8_t* hist[2];
+    float4* pp[2];
+    uint8_t* mask;
+    uint8_t* ao;
+    float2* col;
+    float4* illum;
+    float* out_ao;
+    float* out_sh;
+    float4* g_tgt;
+    uint32_t* m_tgt;
+    float* fin_ao;
+    float* fin_sh;
+};
+
+// loop control, mapped; each field has one writer
+struct alignas(64) LoopCtl {
+    uint32_t stop;              // host: 1 = end the loops
+    uint32_t n_slots;           // host: session slots in use
+    uint64_t max_batch_px;      // host: pixel cap of one batch (0: none)
+    uint64_t ring_tail;         // host: completion records consumed
+    uint64_t epoch[kLoops];     // device: scheduling passes done, per loop
+    uint32_t status[kLoops];    // device: DHR_OK or DHR_ERR_TIMEOUT once ended
+    uint32_t running[kLoops];   // device: 0 once that loop has ended
+};
+
+// shared by the loops (device memory)
+struct LoopShared {
+    unsigned long long reserve;     // ring positions handed out
+    unsigned long long last_work;   // %globaltimer of the last request taken by any loop
+    unsigned long long t0;          // %globaltimer when the first loop started
+};
+
+struct alignas(16) LoopRecord {   // device -> host
+    uint64_t request_id;
+    uint64_t t_start;         // %globaltimer when its batch was scheduled
+    uint64_t t_done;          // %globaltimer when its batch completed
+    int32_t session;
+    uint32_t k;               // request index within the session
+    uint32_t frame;
+    uint32_t batch_size;
+    uint32_t generation;      // of the session slot
+    uint32_t pad;
+    uint64_t seq;             // ring position + 1, written last
+};
+
+// per-session state kept by the loop (device memory)
+struct DevSession {
+    uint32_t generation;
+    uint32_t taken;           // index of the last request taken
+    int32_t cur;              // G-buffer / moments index written last
+    int32_t has_prev;
+    dhr_camera cam_prev;
+    uint32_t busy;            // 1 while a loop holds the session (claimed with atomicCAS)
+};
+
+struct LoopLimits {
+    uint64_t idle_ns;
+    uint64_t max_run_ns;
+    uint64_t poll_ns;
+    uint64_t max_iters;
+};
+
+// one loop's own state (device memory)
+struct LoopMeta {
+    uint64_t iters;
+    LoopLimits lim;
+    TraceConsts tk_base;      // lights, cones, AO parameters; camera and frame per request
+    SvgfConsts sk_base;
+    int32_t levels, nsq;
+    int32_t n_items;
+    uint64_t t_batch;
+    int32_t item_session[kMaxItems];
+    uint32_t item_k[kMaxItems];
+    uint32_t item_frame[kMaxItems];
+    uint32_t item_gen[kMaxItems];
+    uint64_t item_request[kMaxItems];
+};
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_acquire_sys64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_sys64(uint64_t* p, uint64_t v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// One scheduling pass of loop `li` (one block of 1024 threads, thread i
+// looks after session slot i): end the loop if asked or past a limit; else
+// wait up to poll_ns for requests of sessions no loop holds, claim one per
+// session -- oldest arrival first, at most kMaxItems and the pixel cap --
+// and build the batch table.
+__global__ void __launch_bounds__(1024) loop_schedule_kernel(int li, LoopCtl* ctl, const Mailbox* mb,
+                                                             const SessionSlot* slots, DevSession* ds,
+                                                             LoopShared* sh, LoopMeta* meta, BatchTable* tb,
+                                                             cudaGraphConditionalHandle h_loop,
+                                                             cudaGraphConditionalHandle h_work) {
+    __shared__ uint64_t key[kLoopMaxSessions];
+    __shared__ uint32_t sreq[kLoopMaxSessions];
+    __shared__ uint32_t sgen[kLoopMaxSessions];
+    __shared__ uint64_t spx[kLoopMaxSessions];
+    __shared__ int order[kLoopMaxSessions];
+    __shared__ int s_end, s_count, s_go, s_n;
+    __shared__ uint64_t s_now;
+    const LoopLimits lim = meta->lim;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const uint64_t now = globaltimer();
+        if (meta->iters == 0) {
+            atomicCAS(&sh->t0, 0ull, (unsigned long long)now);
+            atomicMax(&sh->last_work, (unsigned long long)now);
+        }
+        const uint64_t t0 = *(volatile unsigned long long*)&sh->t0;
+        int end = 0;
+        if (ld_acquire_sys(&ctl->stop)) end = 1;
+        else if (now - t0 > lim.max_run_ns || meta->iters >= lim.max_iters) end = 2;
+        s_end = end;
+        s_now = now;
+    }
+    __syncthreads();
+    const uint32_t n_slots = min(ld_acquire_sys(&ctl->n_slots), (uint32_t)kLoopMaxSessions);
+    // room for both loops' completion records
+    const uint64_t reserved = *(volatile unsigned long long*)&sh->reserve;
+    const bool room = reserved - ld_acquire_sys64(&ctl->ring_tail) + 2 * kLoops * kMaxItems <= kRingRecords;
+    int count = 0;
+    if (!s_end) {
+        for (int pass = 0; pass < kLoopPolls; ++pass) {
+            uint64_t k = ~0ull;
+            if (room && tid < (int)n_slots) {
+                const SessionSlot* sl = slots + tid;
+                const uint32_t g1 = ld_acquire_sys(&sl->generation);
+                DevSession& d = ds[tid];
+                bool fresh = !(g1 & 1u) && g1 != 0u;
+                if (fresh && *(volatile uint32_t*)&d.generation != g1) {
+                    // a new session in this slot: reset its state, holding it
+                    if (atomicCAS(&d.busy, 0u, 1u) == 0u) {
+                        d.generation = g1;
+                        d.taken = 0;
+                        d.cur = 0;
+                        d.has_prev = 0;
+                        __threadfence();
+                        atomicExch(&d.busy, 0u);
+                    }
+                    fresh = false;
+                }
+                if (fresh && *(volatile uint32_t*)&d.busy == 0u) {
+                    const uint32_t s1 = ld_acquire_sys(&mb[tid].seq);
+                    if (!(s1 & 1u) && (s1 >> 1) > *(volatile uint32_t*)&d.taken && sl->open) {
+                        const uint64_t ta = *(volatile const uint64_t*)&mb[tid].t_arrival;
+                        const uint64_t px = (uint64_t)sl->w * (uint64_t)sl->h;
+                        __threadfence_system();
+                        if (ld_acquire_sys(&mb[tid].seq) == s1 && ld_acquire_sys(&sl->generation) == g1) {
+                            k = ta;
+                            sreq[tid] = s1;
+                            sgen[tid] = g1;
+                            spx[tid] = px;
+                        }
+                    }
+                }
+            }
+            if (tid < kLoopMaxSessions) key[tid] = k;
+            count = __syncthreads_count(k != ~0ull);
+            if (tid == 0) s_go = count > 0 || globaltimer() - s_now > lim.poll_ns;
+            __syncthreads();
+            if (s_go) break;
+            __nanosleep(2000);
+        }
+    }
+    if (tid == 0) s_count = count;
+    __syncthreads();
+    // rank the candidates by arrival (ties: slot index)
+    if (!s_end && tid < (int)n_slots && key[tid] != ~0ull) {
+        const uint64_t mine = key[tid];
+        int rank = 0;
+        for (int j = 0; j < (int)n_slots; ++j) {
+            const uint64_t kj = key[j];
+            rank += (kj < mine || (kj == mine && j < tid)) ? 1 : 0;
+        }
+        order[rank] = tid;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int n = 0;
+        if (!s_end) {
+            const uint64_t cap = *(volatile const uint64_t*)&ctl->max_batch_px;
+            uint64_t px = 0;
+            for (int r = 0; r < s_count && n < kMaxItems; ++r) {
+                const int id = order[r];
+                if (cap && n > 0 && px + spx[id] > cap) break;
+                px += spx[id];
+                order[n++] = id;    // order[0..n) now the sessions to claim
+            }
+        }
+        s_n = n;
+    }
+    __syncthreads();
+    // build the items, one thread each; a session the other loop claimed
+    // first, or whose request was replaced while it was read, is left out
+    if (tid < s_n) {
+        const int id = order[tid];
+        const Mailbox& m = mb[id];
+        const SessionSlot& sl = slots[id];
+        DevSession& d = ds[id];
+        ServeItem& it = tb->items[tid];
+        it = ServeItem();
+        const bool claimed = atomicCAS(&d.busy, 0u, 1u) == 0u;
+        __threadfence();
+        bool valid = claimed && *(volatile uint32_t*)&d.generation == sgen[id] &&
+                     (sreq[id] >> 1) > *(volatile uint32_t*)&d.taken;
+        dhr_camera cam, cam_t;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&m.cam);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&cam);
+        for (int w = 0; w < (int)(sizeof(dhr_camera) / 4); ++w) dst[w] = ((volatile const uint32_t*)src)[w];
+        src = reinterpret_cast<const uint32_t*>(&m.cam_target);
+        dst = reinterpret_cast<uint32_t*>(&cam_t);
+        for (int w = 0; w < (int)(sizeof(dhr_camera) / 4); ++w) dst[w] = ((volatile const uint32_t*)src)[w];
+        const uint32_t frame = *(volatile const uint32_t*)&m.frame;
+        const uint32_t warp = *(volatile const uint32_t*)&m.warp;
+        const uint64_t rid = *(volatile const uint64_t*)&m.request_id;
+        it.tk = meta->tk_base;
+        it.tk.cam = cam;
+        it.tk.frame = frame;
+        it.tk_target = meta->tk_base;
+        it.tk_target.cam = cam_t;
+        it.tk_target.frame = frame;
+        it.cam_prev = d.cam_prev;
+        it.sk = meta->sk_base;
+        it.sk.W = sl.w;
+        it.sk.H = sl.h;
+        it.has_prev = d.has_prev;
+        it.warp = warp ? 1 : 0;
+        it.tiles_x = (sl.w + kTileW - 1) / kTileW;
+        const int cur = d.cur ^ 1, prev = d.cur;
+        it.g_cur = sl.g[cur];
+        it.m_cur = sl.m[cur];
+        it.g_prev = sl.g[prev];
+        it.m_prev = sl.m[prev];
+        it.mask = sl.mask;
+        it.ao = sl.ao;
+        it.col = sl.col;
+        it.mom_in = sl.mom[prev];
+        it.hist_in = sl.hist[prev];
+        it.mom_out = sl.mom[cur];
+        it.hist_out = sl.hist[cur];
+        it.illum = sl.illum;
+        it.pp[0] = sl.pp[0];
+        it.pp[1] = sl.pp[1];
+        it.out_ao = sl.out_ao;
+        it.out_sh = sl.out_sh;
+        it.g_tgt = sl.g_tgt;
+        it.m_tgt = sl.m_tgt;
+        it.fin_ao = sl.fin_ao;
+        it.fin_sh = sl.fin_sh;
+        __threadfence_system();
+        valid = valid && ld_acquire_sys(&m.seq) == sreq[id] && ld_acquire_sys(&sl.generation) == sgen[id];
+        if (valid) {
+            d.cur = cur;
+            d.cam_prev = cam;
+            d.has_prev = 1;
+            d.taken = sreq[id] >> 1;
+        } else {
+            it.tiles_x = 0;
+            if (claimed) {
+                __threadfence();
+                atomicExch(&d.busy, 0u);
+            }
+        }
+        meta->item_session[tid] = valid ? id : -1;
+        meta->item_k[tid] = sreq[id] >> 1;
+        meta->item_frame[tid] = frame;
+        meta->item_gen[tid] = sgen[id];
+        meta->item_request[tid] = rid;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int n = s_n;
+        int tiles = 0, live = 0;
+        for (int j = 0; j < n; ++j) {
+            ServeItem& it = tb->items[j];
+            it.tile_begin = tiles;
+            if (it.tiles_x > 0) tiles += it.tiles_x * ((it.sk.H + kTileH - 1) / kTileH);
+            live += meta->item_session[j] >= 0 ? 1 : 0;
+        }
+        tb->n_items = n;
+        tb->n_tiles = tiles;
+        tb->levels = meta->levels;
+        tb->nsq = meta->nsq;
+        meta->n_items = n;
+        meta->t_batch = s_now;
+        meta->iters += 1;
+        st_release_sys64(&ctl->epoch[li], meta->iters);
+        if (live > 0) atomicMax(&sh->last_work, (unsigned long long)s_now);
+        int end = s_end;
+        const uint64_t last = *(volatile unsigned long long*)&sh->last_work;
+        if (!end && live == 0 && s_count == 0 && s_now > last && s_now - last > lim.idle_ns) end = 2;
+        if (end) {
+            st_release_sys(&ctl->status[li], end == 1 ? (uint32_t)DHR_OK : (uint32_t)DHR_ERR_TIMEOUT);
+            st_release_sys(&ctl->running[li], 0u);
+        }
+        cudaGraphSetConditional(h_work, (!end && live > 0) ? 1u : 0u);
+        cudaGraphSetConditional(h_loop, end ? 0u : 1u);
+    }
+}
+
+// completion records of the batch just run (ring positions reserved from
+// the shared counter, each stamped last with its position + 1), then the
+// batch's sessions are released for the next request
+__global__ void loop_complete_kernel(LoopRecord* ring, DevSession* ds, LoopShared* sh, LoopMeta* meta) {
+    const int n = meta->n_items;
+    const uint64_t now = globaltimer();
+    __shared__ int s_slot[kMaxItems];
+    __shared__ unsigned long long s_base;
+    if (threadIdx.x == 0) {
+        int live = 0;
+        for (int j = 0; j < n; ++j) {
+            s_slot[j] = meta->item_session[j] >= 0 ? live : -1;
+            live += meta->item_session[j] >= 0 ? 1 : 0;
+        }
+        s_base = live > 0 ? atomicAdd(&sh->reserve, (unsigned long long)live) : 0ull;
+        for (int j = 0; j < n; ++j)
+            if (s_slot[j] >= 0) s_slot[j] |= live << 16;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (s_slot[j] < 0) continue;
+        const int pos = s_slot[j] & 0xFFFF, live = s_slot[j] >> 16;
+        const uint64_t at = s_base + (uint64_t)pos;
+        LoopRecord* r = ring + at % kRingRecords;
+        r->request_id = meta->item_request[j];
+        r->t_start = meta->t_batch;
+        r->t_done = now;
+        r->session = meta->item_session[j];
+        r->k = meta->item_k[j];
+        r->frame = meta->item_frame[j];
+        r->batch_size = (uint32_t)live;
+        r->generation = meta->item_gen[j];
+        r->pad = 0;
+        __threadfence_system();
+        st_release_sys64(&r->seq, at + 1);
+        DevSession& d = ds[meta->item_session[j]];
+        __threadfence();
+        atomicExch(&d.busy, 0u);
+    }
+}
+
+// %globaltimer read once (host clock calibration)
+__global__ void clock_kernel(uint64_t* out) { *out = globaltimer(); }
+
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -318,6 +727,28 @@ Layout layout(int w, int h) {
 
 }  // namespace
 
+// host side of the device-resident loop
+struct LoopHost {
+    cudaStream_t stream[kLoops] = {};
+    cudaGraphExec_t exec[kLoops] = {};
+    LoopShared* d_shared = nullptr;
+    LoopCtl* ctl = nullptr;               // mapped
+    Mailbox* mb = nullptr;                // mapped [kLoopMaxSessions]
+    SessionSlot* slots = nullptr;         // mapped [kLoopMaxSessions]
+    LoopRecord* ring = nullptr;           // mapped [kRingRecords]
+    uint64_t* clock = nullptr;            // mapped, one %globaltimer sample
+    DevSession* d_sess = nullptr;
+    LoopMeta* d_meta[kLoops] = {};
+    BatchTable* d_table[kLoops] = {};
+    bool active = false;                  // launched and not yet collected by loop_stop
+    int64_t clock_offset = 0;             // host ns - device ns
+    uint32_t generation[kLoopMaxSessions] = {};
+    uint32_t published[kLoopMaxSessions] = {};        // last request index written to the mailbox
+    std::map<uint32_t, Request> outstanding[kLoopMaxSessions];  // published, not yet reported
+    // closed sessions: (id, every loop's epoch at the close)
+    std::vector<std::pair<int, std::array<uint64_t, kLoops>>> to_release;
+};
+
 struct dhr_server {
     const dhr_scene* scene = nullptr;
     uint64_t budget = 0, used = 0;
@@ -332,29 +763,37 @@ struct dhr_server {
     std::vector<dhr_completion> done;  // finished or dropped, not yet polled
     uint64_t n_dropped = 0, n_batches = 0, n_frames = 0;
     uint64_t max_batch_px = kDefaultBatchPx;   // pixel cap of one batch (0: none)
+    cudaStream_t mem_stream = nullptr;  // session allocations (stream ordered)
+    LoopHost loop;
 };
+
+// the stages of one batch on `st`, all reading the batch table `tb`:
+// trace, temporal, a-trous levels, target G-buffer, delay warp
+static void launch_stages(const dhr_server* s, cudaStream_t st, const BatchTable* tb) {
+    const SceneView sv = s->scene->view();
+    serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, tb, 0);
+    serve_temporal_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
+    const int L = (int)s->sp.levels;
+    const int nsq = s->sp.sigma_n == 128.0f ? 7 : -1;
+    for (int l = 0; l < L; ++l) {
+        const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
+        const bool small = atrous_radius(&s->sp) == 1;
+        if (nsq == 7 && !small) serve_atrous_kernel<7, 2><<<s->grid_px, dim3(32, 8), 0, st>>>(tb, l, mode);
+        else if (!small) serve_atrous_kernel<-1, 2><<<s->grid_px, dim3(32, 8), 0, st>>>(tb, l, mode);
+        else if (nsq == 7) serve_atrous_kernel<7, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(tb, l, mode);
+        else serve_atrous_kernel<-1, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(tb, l, mode);
+    }
+    if (L <= 1) serve_copy_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
+    serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, tb, 1);
+    serve_warp_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
+}
 
 static dhr_status capture_slot(dhr_server* s, Slot& sl) {
     cudaStream_t st = sl.stream;
     cudaGraph_t g = nullptr;
     DHR_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     cudaMemcpyAsync(sl.d_table, sl.h_table, sizeof(BatchTable), cudaMemcpyHostToDevice, st);
-    const SceneView sv = s->scene->view();
-    serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, sl.d_table, 0);
-    serve_temporal_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table);
-    const int L = (int)s->sp.levels;
-    const int nsq = s->sp.sigma_n == 128.0f ? 7 : -1;
-    for (int l = 0; l < L; ++l) {
-        const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-        const bool small = atrous_radius(&s->sp) == 1;
-        if (nsq == 7 && !small) serve_atrous_kernel<7, 2><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
-        else if (!small) serve_atrous_kernel<-1, 2><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
-        else if (nsq == 7) serve_atrous_kernel<7, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
-        else serve_atrous_kernel<-1, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table, l, mode);
-    }
-    if (L <= 1) serve_copy_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table);
-    serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, sl.d_table, 1);
-    serve_warp_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(sl.d_table);
+    launch_stages(s, st, sl.d_table);
     const cudaError_t e_launch = cudaGetLastError();
     const cudaError_t e_end = cudaStreamEndCapture(st, &g);
     if (e_launch != cudaSuccess || e_end != cudaSuccess) {
@@ -366,6 +805,239 @@ static dhr_status capture_slot(dhr_server* s, Slot& sl) {
     cudaGraphDestroy(g);
     DHR_CUDA_TRY(e);
     return DHR_OK;
+}
+
+// ------------------------------------------------------- device loop host
+// publishes session slot `id` (open with its buffers, or closed) for the
+// loop; the mailbox restarts at request 0 for a newly opened session
+static void publish_slot(dhr_server* s, int id, bool open) {
+    LoopHost& L = s->loop;
+    if (id >= kLoopMaxSessions || !L.slots) return;
+    SessionSlot& sl = L.slots[id];
+    const uint32_t g = L.generation[id] + 2u;   // even, never 0
+    __atomic_store_n(&sl.generation, g - 1u, __ATOMIC_RELAXED);
+    __atomic_thread_fence(__ATOMIC_RELEASE);
+    if (open) {
+        const Session& se = s->sessions[id];
+        __atomic_store_n(&L.mb[id].seq, 0u, __ATOMIC_RELAXED);
+        L.published[id] = 0;
+        sl.w = se.w;
+        sl.h = se.h;
+        for (int i = 0; i < 2; ++i) {
+            sl.g[i] = se.g[i];
+            sl.m[i] = se.m[i];
+            sl.mom[i] = se.mom[i];
+            sl.hist[i] = se.hist[i];
+            sl.pp[i] = se.pp[i];
+        }
+        sl.mask = se.mask;
+        sl.ao = se.ao;
+        sl.col = se.col;
+        sl.illum = se.illum;
+        sl.out_ao = se.out_ao;
+        sl.out_sh = se.out_sh;
+        sl.g_tgt = se.g_tgt;
+        sl.m_tgt = se.m_tgt;
+        sl.fin_ao = se.fin_ao;
+        sl.fin_sh = se.fin_sh;
+    }
+    sl.open = open ? 1 : 0;
+    __atomic_store_n(&sl.generation, g, __ATOMIC_RELEASE);
+    L.generation[id] = g;
+    uint32_t n = (uint32_t)std::min<size_t>(s->sessions.size(), (size_t)kLoopMaxSessions);
+    __atomic_store_n(&L.ctl->n_slots, n, __ATOMIC_RELEASE);
+}
+
+// writes request k of session id into its mailbox (the loop takes the newest)
+static void publish_request(dhr_server* s, int id, const Request& r) {
+    LoopHost& L = s->loop;
+    const uint32_t k = ++L.published[id];
+    L.outstanding[id][k] = r;
+    Mailbox& m = L.mb[id];
+    __atomic_store_n(&m.seq, 2u * k - 1u, __ATOMIC_RELAXED);
+    __atomic_thread_fence(__ATOMIC_RELEASE);
+    m.warp = r.warp ? 1u : 0u;
+    m.frame = r.frame;
+    m.t_arrival = r.t_arrival;
+    m.request_id = r.id;
+    m.cam = r.cam;
+    m.cam_target = r.cam_target;
+    __atomic_store_n(&m.seq, 2u * k, __ATOMIC_RELEASE);
+}
+
+static dhr_status loop_create(dhr_server* s) {
+    LoopHost& L = s->loop;
+    DHR_CUDA_TRY(cudaHostAlloc((void**)&L.ctl, sizeof(LoopCtl), cudaHostAllocMapped));
+    DHR_CUDA_TRY(cudaHostAlloc((void**)&L.mb, sizeof(Mailbox) * kLoopMaxSessions, cudaHostAllocMapped));
+    DHR_CUDA_TRY(cudaHostAlloc((void**)&L.slots, sizeof(SessionSlot) * kLoopMaxSessions, cudaHostAllocMapped));
+    DHR_CUDA_TRY(cudaHostAlloc((void**)&L.ring, sizeof(LoopRecord) * kRingRecords, cudaHostAllocMapped));
+    DHR_CUDA_TRY(cudaHostAlloc((void**)&L.clock, sizeof(uint64_t), cudaHostAllocMapped));
+    memset(L.ctl, 0, sizeof(LoopCtl));
+    memset(L.mb, 0, sizeof(Mailbox) * kLoopMaxSessions);
+    memset(L.slots, 0, sizeof(SessionSlot) * kLoopMaxSessions);
+    memset(L.ring, 0, sizeof(LoopRecord) * kRingRecords);
+    DHR_CUDA_TRY(cudaMalloc((void**)&L.d_sess, sizeof(DevSession) * kLoopMaxSessions));
+    DHR_CUDA_TRY(cudaMalloc((void**)&L.d_shared, sizeof(LoopShared)));
+    LoopCtl* ctl_d = nullptr;
+    Mailbox* mb_d = nullptr;
+    SessionSlot* slots_d = nullptr;
+    LoopRecord* ring_d = nullptr;
+    DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&ctl_d, L.ctl, 0));
+    DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&mb_d, L.mb, 0));
+    DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&slots_d, L.slots, 0));
+    DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&ring_d, L.ring, 0));
+    for (int li = 0; li < kLoops; ++li) {
+        DHR_CUDA_TRY(cudaStreamCreateWithFlags(&L.stream[li], cudaStreamNonBlocking));
+        DHR_CUDA_TRY(cudaMalloc((void**)&L.d_meta[li], sizeof(LoopMeta)));
+        DHR_CUDA_TRY(cudaMalloc((void**)&L.d_table[li], sizeof(BatchTable)));
+        DHR_CUDA_TRY(cudaMemset(L.d_table[li], 0, sizeof(BatchTable)));
+        cudaStream_t st = L.stream[li];
+        // WHILE (loop) { schedule; IF (work) { stages; completions } }
+        cudaGraph_t g = nullptr;
+        DHR_CUDA_TRY(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h_loop, h_work;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h_loop, g, 1u, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = h_loop;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wnode = nullptr;
+        if (!e) e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp);
+        cudaGraph_t body = e ? nullptr : wp.conditional.phGraph_out[0];
+        if (!e) e = cudaGraphConditionalHandleCreate(&h_work, body, 0u, 0u);
+        cudaGraph_t captured = nullptr;
+        if (!e) e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (!e) {
+            loop_schedule_kernel<<<1, 1024, 0, st>>>(li, ctl_d, mb_d, slots_d, L.d_sess, L.d_shared, L.d_meta[li],
+                                                      L.d_table[li], h_loop, h_work);
+            e = cudaGetLastError();
+            const cudaError_t e2 = cudaStreamEndCapture(st, &captured);
+            if (!e) e = e2;
+        }
+        cudaGraphNode_t sched = nullptr;
+        size_t n_nodes = 1;
+        if (!e) e = cudaGraphGetNodes(body, &sched, &n_nodes);
+        cudaGraphNodeParams ip = {};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = h_work;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t inode = nullptr;
+        if (!e && n_nodes != 1) e = cudaErrorInvalidValue;
+        if (!e) e = cudaGraphAddNode(&inode, body, &sched, nullptr, 1, &ip);
+        if (!e) {
+            cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(st, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (!e) {
+                launch_stages(s, st, L.d_table[li]);
+                loop_complete_kernel<<<1, 64, 0, st>>>(ring_d, L.d_sess, L.d_shared, L.d_meta[li]);
+                e = cudaGetLastError();
+                const cudaError_t e2 = cudaStreamEndCapture(st, &captured);
+                if (!e) e = e2;
+            }
+        }
+        if (!e) e = cudaGraphInstantiate(&L.exec[li], g, 0);
+        cudaGraphDestroy(g);
+        if (e) return set_error(DHR_ERR_CUDA, "server: device loop graph: %s", cudaGetErrorString(e));
+    }
+    return DHR_OK;
+}
+
+static void loop_destroy(LoopHost& L) {
+    for (int li = 0; li < kLoops; ++li) {
+        if (L.exec[li]) cudaGraphExecDestroy(L.exec[li]);
+        if (L.stream[li]) cudaStreamDestroy(L.stream[li]);
+        cudaFree(L.d_meta[li]);
+        cudaFree(L.d_table[li]);
+    }
+    cudaFreeHost(L.ctl);
+    cudaFreeHost(L.mb);
+    cudaFreeHost(L.slots);
+    cudaFreeHost(L.ring);
+    cudaFreeHost(L.clock);
+    cudaFree(L.d_sess);
+    cudaFree(L.d_shared);
+}
+
+// records written by the loop since the last call: completions, and the
+// requests they superseded as dropped
+static void loop_collect(dhr_server* s) {
+    LoopHost& L = s->loop;
+    uint64_t tail = L.ctl->ring_tail;
+    uint64_t last_batch = ~0ull;
+    for (;; ++tail) {
+        // records are stamped with their position + 1 once written (the
+        // loops fill their reserved positions in any order)
+        LoopRecord* slot = L.ring + tail % kRingRecords;
+        if (__atomic_load_n(&slot->seq, __ATOMIC_ACQUIRE) != tail + 1) break;
+        const LoopRecord r = *slot;
+        if (r.session < 0 || r.session >= kLoopMaxSessions || r.generation != L.generation[r.session]) continue;
+        auto& out = L.outstanding[r.session];
+        for (auto it = out.begin(); it != out.end() && it->first <= r.k;) {
+            dhr_completion c{};
+            c.request_id = it->second.id;
+            c.session = r.session;
+            c.frame = it->second.frame;
+            c.t_arrival_ns = it->second.t_arrival;
+            if (it->first == r.k) {
+                c.t_start_ns = (uint64_t)((int64_t)r.t_start + L.clock_offset);
+                c.t_done_ns = (uint64_t)((int64_t)r.t_done + L.clock_offset);
+                c.batch_size = r.batch_size;
+                ++s->n_frames;
+            } else {
+                c.t_done_ns = now_ns();
+                c.dropped = 1;
+                ++s->n_dropped;
+            }
+            s->done.push_back(c);
+            it = out.erase(it);
+        }
+        if (r.t_start != last_batch) {
+            ++s->n_batches;
+            last_batch = r.t_start;
+        }
+    }
+    __atomic_store_n(&L.ctl->ring_tail, tail, __ATOMIC_RELEASE);
+}
+
+// the loop's stream still has work (the graph launch has not ended) and the
+// loop has not reported its end
+static bool loop_running(const dhr_server* s) {
+    if (!s->loop.active) return false;
+    for (int li = 0; li < kLoops; ++li)
+        if (__atomic_load_n(&s->loop.ctl->running[li], __ATOMIC_ACQUIRE) != 0u &&
+            cudaStreamQuery(s->loop.stream[li]) == cudaErrorNotReady)
+            return true;
+    return false;
+}
+
+static std::array<uint64_t, kLoops> loop_epochs(const dhr_server* s) {
+    std::array<uint64_t, kLoops> e;
+    for (int li = 0; li < kLoops; ++li) e[li] = __atomic_load_n(&s->loop.ctl->epoch[li], __ATOMIC_ACQUIRE);
+    return e;
+}
+
+// frees the memory of sessions closed while the loop ran, once no batch can
+// still use it (two scheduling passes later, or the loop has ended)
+static void release_session(dhr_server* s, int id);
+static void loop_release_closed(dhr_server* s) {
+    LoopHost& L = s->loop;
+    const auto epoch = loop_epochs(s);
+    const bool running = loop_running(s);
+    auto& v = L.to_release;
+    for (size_t i = 0; i < v.size();) {
+        bool safe = true;
+        for (int li = 0; li < kLoops; ++li)
+            safe = safe && (__atomic_load_n(&L.ctl->running[li], __ATOMIC_ACQUIRE) == 0u ||
+                            epoch[li] >= v[i].second[li] + 2);
+        if (!running || safe) {
+            release_session(s, v[i].first);
+            v.erase(v.begin() + i);
+        } else {
+            ++i;
+        }
+    }
 }
 
 extern "C" uint64_t dhr_server_now_ns(void) { return now_ns(); }
@@ -394,8 +1066,12 @@ extern "C" uint64_t dhr_server_session_bytes(int32_t width, int32_t height) {
     return layout(width, height).total;
 }
 
+extern "C" dhr_status dhr_server_loop_stop(dhr_server* s);
+
 extern "C" void dhr_server_destroy(dhr_server* s) {
     if (!s) return;
+    if (s->loop.active) dhr_server_loop_stop(s);
+    loop_destroy(s->loop);
     for (auto& sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.graph) cudaGraphExecDestroy(sl.graph);
@@ -404,7 +1080,12 @@ extern "C" void dhr_server_destroy(dhr_server* s) {
         cudaFreeHost(sl.h_table);
         cudaFree(sl.d_table);
     }
-    for (auto& se : s->sessions) cudaFree(se.mem);
+    for (auto& se : s->sessions)
+        if (se.mem) cudaFreeAsync(se.mem, s->mem_stream);
+    if (s->mem_stream) {
+        cudaStreamSynchronize(s->mem_stream);
+        cudaStreamDestroy(s->mem_stream);
+    }
     if (s->ref) cudaEventDestroy(s->ref);
     delete s;
 }
@@ -427,7 +1108,10 @@ extern "C" dhr_status dhr_server_create(const dhr_scene* scene, uint64_t budget_
     s->grid_trace = sms * 4;
     s->grid_px = sms * 8;
     dhr_status st = DHR_OK;
+    if (cudaStreamCreateWithFlags(&s->mem_stream, cudaStreamNonBlocking) != cudaSuccess)
+        st = set_error(DHR_ERR_CUDA, "server_create: cannot create a stream");
     for (auto& sl : s->slots) {
+        if (st != DHR_OK) break;
         cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (!e) e = cudaEventCreateWithFlags(&sl.done, cudaEventDefault);
         if (!e) e = cudaMallocHost((void**)&sl.h_table, sizeof(BatchTable));
@@ -440,6 +1124,7 @@ extern "C" dhr_status dhr_server_create(const dhr_scene* scene, uint64_t budget_
         st = capture_slot(s, sl);
         if (st != DHR_OK) break;
     }
+    if (st == DHR_OK) st = loop_create(s);
     if (st == DHR_OK) {
         cudaError_t e = cudaEventCreate(&s->ref);
         if (!e) e = cudaEventRecord(s->ref, s->slots[0].stream);
@@ -471,15 +1156,20 @@ extern "C" dhr_status dhr_server_open(dhr_server* s, int32_t width, int32_t heig
             break;
         }
     if (id < 0) {
-        if (s->sessions.size() >= 4096) return set_error(DHR_ERR_ADMISSION, "server_open: too many sessions");
+        if (s->sessions.size() >= (size_t)kLoopMaxSessions)
+            return set_error(DHR_ERR_ADMISSION, "server_open: too many sessions (%d)", kLoopMaxSessions);
         s->sessions.emplace_back();
         id = (int)s->sessions.size() - 1;
     }
     Session& se = s->sessions[id];
     se = Session();
     char* base = nullptr;
-    DHR_CUDA_TRY(cudaMalloc((void**)&base, L.total));
-    DHR_CUDA_TRY(cudaMemset(base, 0, L.total));
+    // stream-ordered allocation on the server's own stream: neither this nor
+    // the release below synchronises the device, which would wait for a
+    // running device loop
+    DHR_CUDA_TRY(cudaMallocAsync((void**)&base, L.total, s->mem_stream));
+    DHR_CUDA_TRY(cudaMemsetAsync(base, 0, L.total, s->mem_stream));
+    DHR_CUDA_TRY(cudaStreamSynchronize(s->mem_stream));
     se.mem = base;
     se.open = true;
     se.w = width;
@@ -503,13 +1193,15 @@ extern "C" dhr_status dhr_server_open(dhr_server* s, int32_t width, int32_t heig
     se.fin_ao = reinterpret_cast<float*>(base + L.fin_ao);
     se.fin_sh = reinterpret_cast<float*>(base + L.fin_sh);
     s->used += L.total;
+    s->loop.outstanding[id].clear();
+    publish_slot(s, id, true);
     *session_out = id;
     return DHR_OK;
 }
 
 static void release_session(dhr_server* s, int id) {
     Session& se = s->sessions[id];
-    cudaFree(se.mem);
+    if (se.mem) cudaFreeAsync(se.mem, s->mem_stream);
     s->used -= se.bytes;
     se = Session();
 }
@@ -530,6 +1222,25 @@ extern "C" dhr_status dhr_server_close(dhr_server* s, int32_t id) {
         se.pending = false;
     }
     se.open = false;
+    LoopHost& L = s->loop;
+    publish_slot(s, id, false);
+    for (auto& kv : L.outstanding[id]) {     // published to the loop, never completed
+        dhr_completion c{};
+        c.request_id = kv.second.id;
+        c.session = id;
+        c.frame = kv.second.frame;
+        c.t_arrival_ns = kv.second.t_arrival;
+        c.t_done_ns = now_ns();
+        c.dropped = 1;
+        s->done.push_back(c);
+        ++s->n_dropped;
+    }
+    L.outstanding[id].clear();
+    if (loop_running(s)) {
+        // a batch scheduled before the close may still use the buffers
+        L.to_release.push_back({id, loop_epochs(s)});
+        return DHR_OK;
+    }
     if (se.in_flight) se.closing = true;   // freed when its batch completes
     else release_session(s, id);
     return DHR_OK;
@@ -545,6 +1256,18 @@ extern "C" dhr_status dhr_server_submit(dhr_server* s, int32_t id, const dhr_cam
     DHR_CHECK_ARG(cam->width == se.w && cam->height == se.h &&
                       (!cam_target || (cam_target->width == se.w && cam_target->height == se.h)),
                   "server_submit: camera size does not match the session");
+    if (s->loop.active) {   // the loop takes the newest request of the mailbox
+        Request r;
+        r.id = request_id;
+        r.session = id;
+        r.cam = *cam;
+        r.warp = cam_target != nullptr;
+        r.cam_target = cam_target ? *cam_target : *cam;
+        r.frame = frame;
+        r.t_arrival = t_arrival_ns;
+        publish_request(s, id, r);
+        return DHR_OK;
+    }
     if (se.pending) {   // latest wins: the older request never starts
         dhr_completion c{};
         c.request_id = se.req.id;
@@ -627,6 +1350,11 @@ extern "C" dhr_status dhr_server_pump(dhr_server* s, int32_t* launched) {
     clear_error();
     DHR_CHECK_ARG(s, "server_pump: null server");
     if (launched) *launched = 0;
+    if (s->loop.active) {      // the device loop schedules; collect its records
+        loop_collect(s);
+        loop_release_closed(s);
+        return DHR_OK;
+    }
     DHR_TRY(reap(s, false));
     Slot* sl = nullptr;
     for (auto& c : s->slots)
@@ -716,7 +1444,27 @@ extern "C" dhr_status dhr_server_poll(dhr_server* s, dhr_completion* out, int32_
     clear_error();
     DHR_CHECK_ARG(s && n_out && (max == 0 || out), "server_poll: null pointer");
     *n_out = 0;
-    DHR_TRY(reap(s, wait != 0 && s->done.empty()));
+    if (s->loop.active) {
+        loop_collect(s);
+        loop_release_closed(s);
+        // wait for a record, or for the loop to end
+        while (wait && s->done.empty() && loop_running(s)) {
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            loop_collect(s);
+        }
+        if (wait && s->done.empty() && !loop_running(s)) {
+            loop_collect(s);
+            bool timed_out = false;
+            for (int li = 0; li < kLoops; ++li)
+                timed_out = timed_out ||
+                            __atomic_load_n(&s->loop.ctl->status[li], __ATOMIC_ACQUIRE) == (uint32_t)DHR_ERR_TIMEOUT;
+            if (s->done.empty() && timed_out)
+                return set_error(DHR_ERR_TIMEOUT, "server_poll: the device loop ended after its idle limit "
+                                                  "without a request");
+        }
+    } else {
+        DHR_TRY(reap(s, wait != 0 && s->done.empty()));
+    }
     const int n = std::min<int>(max, (int)s->done.size());
     for (int i = 0; i < n; ++i) out[i] = s->done[i];
     s->done.erase(s->done.begin(), s->done.begin() + n);
@@ -732,6 +1480,18 @@ extern "C" dhr_status dhr_server_output(dhr_server* s, int32_t id, float** ao, f
     return DHR_OK;
 }
 
+extern "C" dhr_status dhr_server_read_output(dhr_server* s, int32_t id, float* ao_host, float* shadow_host) {
+    clear_error();
+    DHR_CHECK_ARG(s && ao_host && shadow_host, "server_read_output: null pointer");
+    DHR_CHECK_ARG(id >= 0 && id < (int)s->sessions.size() && s->sessions[id].open, "server_read_output: bad session");
+    const Session& se = s->sessions[id];
+    const size_t bytes = (size_t)se.w * se.h * sizeof(float);
+    DHR_CUDA_TRY(cudaMemcpyAsync(ao_host, se.fin_ao, bytes, cudaMemcpyDeviceToHost, s->mem_stream));
+    DHR_CUDA_TRY(cudaMemcpyAsync(shadow_host, se.fin_sh, bytes, cudaMemcpyDeviceToHost, s->mem_stream));
+    DHR_CUDA_TRY(cudaStreamSynchronize(s->mem_stream));
+    return DHR_OK;
+}
+
 extern "C" dhr_status dhr_server_get_stats(dhr_server* s, dhr_server_stats* out) {
     clear_error();
     DHR_CHECK_ARG(s && out, "server_get_stats: null pointer");
@@ -743,5 +1503,155 @@ extern "C" dhr_status dhr_server_get_stats(dhr_server* s, dhr_server_stats* out)
     out->batches = s->n_batches;
     out->frames = s->n_frames;
     out->dropped = s->n_dropped;
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_server_loop_start(dhr_server* s, uint32_t idle_ms, uint32_t max_run_ms) {
+    clear_error();
+    DHR_CHECK_ARG(s, "server_loop_start: null server");
+    DHR_CHECK_ARG(!s->loop.active, "server_loop_start: the loop is already running");
+    DHR_CHECK_ARG(idle_ms >= 1 && idle_ms <= 600000, "server_loop_start: idle_ms not in 1..600000");
+    DHR_CHECK_ARG(max_run_ms >= 1 && max_run_ms <= 3600000, "server_loop_start: max_run_ms not in 1..3600000");
+    LoopHost& L = s->loop;
+    // batches the host launched finish first; the loop continues every
+    // session's history from where they left it
+    for (auto& sl : s->slots)
+        if (sl.in_flight) {
+            DHR_CUDA_TRY(cudaEventSynchronize(sl.done));
+            DHR_TRY(complete_slot(s, sl));
+        }
+    for (size_t i = 0; i < s->sessions.size(); ++i)
+        if (s->sessions[i].closing) release_session(s, (int)i);
+    std::vector<DevSession> ds(kLoopMaxSessions);
+    for (size_t i = 0; i < s->sessions.size() && i < (size_t)kLoopMaxSessions; ++i) {
+        const Session& se = s->sessions[i];
+        DevSession& d = ds[i];
+        d.generation = L.generation[i];
+        d.taken = L.published[i];
+        d.cur = se.cur;
+        d.has_prev = se.has_prev ? 1 : 0;
+        d.cam_prev = se.cam_prev;
+    }
+    DHR_CUDA_TRY(cudaMemcpy(L.d_sess, ds.data(), sizeof(DevSession) * kLoopMaxSessions, cudaMemcpyHostToDevice));
+    LoopMeta m;
+    memset(&m, 0, sizeof(m));
+    dhr_camera c0{};
+    c0.width = c0.height = 1;
+    m.tk_base = make_trace_consts(c0, s->tp);
+    m.sk_base = make_consts(1, 1, &s->sp);
+    m.levels = (int)s->sp.levels;
+    m.nsq = s->sp.sigma_n == 128.0f ? 7 : -1;
+    m.lim.idle_ns = (uint64_t)idle_ms * 1000000ull;
+    m.lim.max_run_ns = (uint64_t)max_run_ms * 1000000ull;
+    m.lim.poll_ns = 50000;                  // 50 us of waiting per scheduling pass
+    m.lim.max_iters = (uint64_t)max_run_ms * 200ull + 1000ull;
+    for (int li = 0; li < kLoops; ++li)
+        DHR_CUDA_TRY(cudaMemcpy(L.d_meta[li], &m, sizeof(m), cudaMemcpyHostToDevice));
+    DHR_CUDA_TRY(cudaMemset(L.d_shared, 0, sizeof(LoopShared)));
+    memset(L.ring, 0, sizeof(LoopRecord) * kRingRecords);
+    L.ctl->stop = 0;
+    L.ctl->ring_tail = 0;
+    L.ctl->max_batch_px = s->max_batch_px;
+    L.ctl->n_slots = (uint32_t)std::min<size_t>(s->sessions.size(), (size_t)kLoopMaxSessions);
+    for (int li = 0; li < kLoops; ++li) {
+        L.ctl->epoch[li] = 0;
+        L.ctl->status[li] = (uint32_t)DHR_OK;
+        __atomic_store_n(&L.ctl->running[li], 1u, __ATOMIC_RELEASE);
+    }
+    // the newest queued request of each session moves into its mailbox
+    for (size_t i = 0; i < s->sessions.size(); ++i) {
+        Session& se = s->sessions[i];
+        if (se.open && se.pending) {
+            se.pending = false;
+            publish_request(s, (int)i, se.req);
+        }
+    }
+    s->order.clear();
+    // device clock against the host clock
+    uint64_t* clock_d = nullptr;
+    DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&clock_d, L.clock, 0));
+    const uint64_t h0 = now_ns();
+    clock_kernel<<<1, 1, 0, L.stream[0]>>>(clock_d);
+    DHR_CUDA_TRY(cudaGetLastError());
+    DHR_CUDA_TRY(cudaStreamSynchronize(L.stream[0]));
+    const uint64_t h1 = now_ns();
+    L.clock_offset = (int64_t)((h0 + h1) / 2) - (int64_t)*(volatile uint64_t*)L.clock;
+    for (int li = 0; li < kLoops; ++li) DHR_CUDA_TRY(cudaGraphLaunch(L.exec[li], L.stream[li]));
+    L.active = true;
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_server_loop_stop(dhr_server* s) {
+    clear_error();
+    DHR_CHECK_ARG(s, "server_loop_stop: null server");
+    LoopHost& L = s->loop;
+    if (!L.active) return DHR_OK;
+    __atomic_store_n(&L.ctl->stop, 1u, __ATOMIC_RELEASE);
+    cudaError_t e = cudaSuccess;
+    for (int li = 0; li < kLoops; ++li) {
+        const cudaError_t ei = cudaStreamSynchronize(L.stream[li]);
+        if (e == cudaSuccess) e = ei;
+    }
+    L.active = false;
+    if (e != cudaSuccess) return set_error(DHR_ERR_CUDA, "server_loop_stop: %s", cudaGetErrorString(e));
+    // records, then the loop's per-session state back to the host
+    s->loop.active = true;
+    loop_collect(s);
+    s->loop.active = false;
+    std::vector<DevSession> ds(kLoopMaxSessions);
+    DHR_CUDA_TRY(cudaMemcpy(ds.data(), L.d_sess, sizeof(DevSession) * kLoopMaxSessions, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < s->sessions.size() && i < (size_t)kLoopMaxSessions; ++i) {
+        Session& se = s->sessions[i];
+        if (!se.open || ds[i].generation != L.generation[i]) continue;
+        se.cur = ds[i].cur;
+        se.has_prev = ds[i].has_prev != 0;
+        se.cam_prev = ds[i].cam_prev;
+        // requests the loop did not take: the newest is queued for the host's
+        // batches, older ones were replaced (dropped)
+        auto& out = L.outstanding[i];
+        while (!out.empty() && out.begin()->first <= ds[i].taken) out.erase(out.begin());
+        while (out.size() > 1) {
+            dhr_completion c{};
+            c.request_id = out.begin()->second.id;
+            c.session = (int)i;
+            c.frame = out.begin()->second.frame;
+            c.t_arrival_ns = out.begin()->second.t_arrival;
+            c.t_done_ns = now_ns();
+            c.dropped = 1;
+            s->done.push_back(c);
+            ++s->n_dropped;
+            out.erase(out.begin());
+        }
+        if (!out.empty()) {
+            se.pending = true;
+            se.req = out.begin()->second;
+            s->order.push_back((int)i);
+            L.published[i] = ds[i].taken;       // the mailbox request is withdrawn
+            __atomic_store_n(&L.mb[i].seq, 2u * ds[i].taken, __ATOMIC_RELEASE);
+            out.clear();
+        }
+    }
+    for (auto& v : L.to_release) release_session(s, v.first);
+    L.to_release.clear();
+    bool timed_out = false;
+    for (int li = 0; li < kLoops; ++li)
+        timed_out = timed_out || __atomic_load_n(&L.ctl->status[li], __ATOMIC_ACQUIRE) == (uint32_t)DHR_ERR_TIMEOUT;
+    if (timed_out)
+        return set_error(DHR_ERR_TIMEOUT, "server_loop_stop: the device loop had ended at its idle or run-time limit");
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_server_loop_status(dhr_server* s, int32_t* running, uint64_t* batches) {
+    clear_error();
+    DHR_CHECK_ARG(s && running, "server_loop_status: null pointer");
+    // from the flags the loop writes (no CUDA call)
+    int r = 0;
+    uint64_t b = 0;
+    for (int li = 0; li < kLoops; ++li) {
+        r |= (s->loop.active && __atomic_load_n(&s->loop.ctl->running[li], __ATOMIC_ACQUIRE) != 0u) ? 1 : 0;
+        b += __atomic_load_n(&s->loop.ctl->epoch[li], __ATOMIC_ACQUIRE);
+    }
+    *running = r;
+    if (batches) *batches = b;
     return DHR_OK;
 }
