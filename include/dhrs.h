@@ -370,7 +370,11 @@ dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur,
 typedef struct dhr_svgf_tape dhr_svgf_tape;
 
 /* Recording space for F frames of W x H (FP32): per frame the temporal
- * output, moments and history lengths (33 B/px), plus work buffers. */
+ * output, moments and history lengths (33 B/px), plus work buffers
+ * (208 B/px).  The first forward with L > 1 levels adds the inputs of
+ * levels 1..L-1 of every frame, 16 (L - 1) B/px per frame (kept with the
+ * tape until it is destroyed).  Errors: DHR_ERR_INVALID (size outside
+ * 1..2^27 pixels, frames outside 1..1024), DHR_ERR_OOM. */
 dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_t frames, dhr_svgf_tape** out);
 void dhr_svgf_tape_destroy(dhr_svgf_tape* tape);
 
@@ -379,7 +383,9 @@ void dhr_svgf_tape_destroy(dhr_svgf_tape* tape);
  * cameras (the G-buffers are device memory and must stay unchanged until
  * the backward call).  sig (device, float [F][2][H][W]): noisy AO and
  * shadow signals in [0, 1] (planes).  out (device, float [F][2][H][W]):
- * filtered AO and shadow. */
+ * filtered AO and shadow.  Records every a-trous level's input for the
+ * backward.  Errors: DHR_ERR_INVALID (mismatched G-buffers or cameras,
+ * a 3x3 kernel, FP16 G-buffers), DHR_ERR_OOM (level records). */
 dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, const dhr_camera* cams,
                                 const float* sig, const dhr_svgf_params* params, float* out,
                                 void* stream);
@@ -387,10 +393,13 @@ dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, c
 /* Backward of the last dhr_svgf_seq_forward on `tape` (same arguments):
  * g_out (device, [F][2][H][W]) = dL/d out.  Writes g_sig (device,
  * [F][2][H][W]) = dL/d sig and g_sigma (device, float [3]) = dL/d
- * (sigma_z, sigma_n, sigma_l).  The a-trous levels are recomputed from the
- * recorded temporal outputs; history scatter and the short-history
- * variance estimate accumulate with atomics (summation order may vary).
- * Errors: DHR_ERR_STATE without a preceding forward. */
+ * (sigma_z, sigma_n, sigma_l).  It reads the forward's records (temporal
+ * outputs and level inputs), so sig and params must be the forward's.  The
+ * history scatter and the short-history variance estimate accumulate with
+ * atomics (summation order may vary); dL/d sigma is summed per pixel in
+ * binary32 over levels and frames, then over pixels in double in a fixed
+ * order.  Errors: DHR_ERR_STATE without a preceding forward or with
+ * another level count than the forward's. */
 dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, const dhr_camera* cams,
                                  const float* sig, const dhr_svgf_params* params, const float* g_out,
                                  float* g_sig, float* g_sigma, void* stream);

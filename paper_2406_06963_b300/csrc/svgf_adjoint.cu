@@ -7,15 +7,18 @@
 // estimate, the moving averages and the reprojected history of earlier
 // frames (the temporal recursion is not cut).
 //
-// Forward (dhr_svgf_seq_forward) records per frame only the temporal output
-// (colour, variance), the moments and the history lengths; the a-trous
-// levels are recomputed during the backward pass.  Backward of one a-trous
-// level is a two-pass gather:
-//   pass A (per output pixel p): re-evaluate the level at p and form the
-//     per-pixel factors of dL/dw_pq = a1 c_q - a2 + a3 w_pq v_q, the
-//     gradient through p's own colour and p's luminance scale;
-//   pass B (per input pixel q): gather from the 25 pixels whose footprint
-//     contains q (and the 9 whose variance Gaussian does).
+// Forward (dhr_svgf_seq_forward) records per frame the temporal output
+// (colour, variance), the moments, the history lengths and the input of
+// every a-trous level after the first.  Backward of one a-trous level is a
+// two-pass gather:
+//   pass A (per output pixel p): one pass over p's taps re-evaluates the
+//     level at p, forms the per-pixel factors of dL/dw_pq = a1 c_q - a2 +
+//     a3 w_pq v_q, the gradient through p's own colour and p's luminance
+//     scale and the sigma derivatives (as sums factored by a1, a2, a3), and
+//     stores the colour-free part of each tap's log-weight;
+//   pass B (per input pixel q): gather from the 24 pixels whose footprint
+//     contains q (weights rebuilt from the stored log-weights and the
+//     colours) and from the 9 whose variance Gaussian does.
 // The reprojection taps and history lengths depend only on G-buffers and
 // cameras and are constants of the adjoint.  Conventions as in the CPU
 // reference: sign(0) = 0, d max(0, x) = [x > 0], d sqrt(g)/dg = 0 for g < 1e-12,
@@ -31,166 +34,306 @@ constexpr int kBX = 32, kBY = 8, kThreadsA = kBX * kBY;
 
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-// block sum of three values into out[blockIdx linear][3]
-__device__ __forceinline__ void block_sum3(float a, float b, float c, float* out) {
-    __shared__ float sh[3][kThreadsA / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(kFull, a, o);
-        b += __shfl_xor_sync(kFull, b, o);
-        c += __shfl_xor_sync(kFull, c, o);
-    }
-    const int t = threadIdx.y * blockDim.x + threadIdx.x, w = t >> 5;
-    if ((t & 31) == 0) {
-        sh[0][w] = a;
-        sh[1][w] = b;
-        sh[2][w] = c;
-    }
-    __syncthreads();
-    if (t == 0) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int i = 0; i < kThreadsA / 32; ++i) {
-            s0 += sh[0][i];
-            s1 += sh[1][i];
-            s2 += sh[2][i];
-        }
-        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        out[3 * blk + 0] = s0;
-        out[3 * blk + 1] = s1;
-        out[3 * blk + 2] = s2;
-    }
+constexpr float kLn2 = 0.69314718055994531f;
+
+// Index of the tap at offset (i, j), i, j in -2..2, among the 24 taps
+// around the centre (row-major, centre left out).
+__device__ __forceinline__ int tap_index(int i, int j) {
+    const int t = (j + 2) * 5 + (i + 2);
+    return t < 12 ? t : t - 1;
 }
 
-// Weight of tap q for output pixel p at offset (i, j) * step, per channel,
-// with the factors needed by the derivatives.
-struct TapW {
-    float w0, w1;     // full weights
-    float a_off;      // |grad z_p . (p - q)|
-    float D;          // sigma_z a_off + eps_z
-    float dz;         // |z_p - z_q|
-    float nd;         // n_p . n_q
+// Sums over the taps q != p that the derivatives of the level need, both
+// channels at once (lane 0: AO, lane 1: shadow; packed binary32 pairs, each
+// lane rounded as the scalar operation).  With w = w_pq, delta = c_q - c_p,
+// a = |delta|, s = sgn(delta) and v = the variance of q:
+//   S0[f] = sum w f,  S1[f] = sum w f delta,  S2[f] = sum w^2 v f
+// for the factors f = 1, s, a, Z (= d w / d sigma_z / w) and L (= ln n.n_q).
+// Since dL/dw_pq = a1 c_q - a2 + a3 w_pq v_q with per-pixel a1, a2, a3
+// (known only once the level's totals are), every sum over the taps of
+// dL/dw_pq w_pq f_q is  (a1 c_p - a2) S0[f] + a1 S1[f] + a3 S2[f]:  one pass
+// over the taps is enough.  (S1[s] = S0[a].)  The differences are taken
+// from c_p so that the cancellation in a1 c_q - a2 happens at the scale of
+// the local colour differences, not of the colours.
+using u64 = unsigned long long;
+
+struct ChanSums {
+    u64 S0_1 = 0, S1_1 = 0, S2_1 = 0;
+    u64 S0_s = 0, S2_s = 0;
+    u64 S0_a = 0, S1_a = 0, S2_a = 0;
+    u64 S0_Z = 0, S1_Z = 0, S2_Z = 0;
+    u64 S0_L = 0, S1_L = 0, S2_L = 0;
+
+    template <bool kLum>
+    __device__ __forceinline__ void add(float w0, float w1, float2 d, float2 ad, u64 v, float Z, float L) {
+        const u64 w = pack2(w0, w1), delta = pack2(d.x, d.y);
+        const u64 wv = mul2(w, v), w2v = mul2(w, wv);
+        S0_1 = add2(S0_1, w);
+        S1_1 = fma2(w, delta, S1_1);
+        S2_1 = add2(S2_1, w2v);
+        if (kLum) {
+            const u64 ws = pack2(d.x == 0.f ? 0.f : copysignf(w0, d.x), d.y == 0.f ? 0.f : copysignf(w1, d.y));
+            const u64 wa = mul2(w, pack2(ad.x, ad.y));
+            S0_s = add2(S0_s, ws);
+            S2_s = fma2(ws, wv, S2_s);
+            S0_a = add2(S0_a, wa);
+            S1_a = fma2(wa, delta, S1_a);
+            S2_a = fma2(w2v, pack2(ad.x, ad.y), S2_a);
+        }
+        const u64 ZZ = pack2(Z, Z), LL = pack2(L, L);
+        const u64 wZ = mul2(w, ZZ), wL = mul2(w, LL);
+        S0_Z = add2(S0_Z, wZ);
+        S1_Z = fma2(wZ, delta, S1_Z);
+        S2_Z = fma2(w2v, ZZ, S2_Z);
+        S0_L = add2(S0_L, wL);
+        S1_L = fma2(wL, delta, S1_L);
+        S2_L = fma2(w2v, LL, S2_L);
+    }
 };
 
-// The weight is evaluated as one power of two, as in the forward kernel:
-// 2^(log2(h_i h_j) + sigma_n log2(n.n_q) - log2(e) (|dz| / D + |dc| il)).
-template <int kNsq>
-__device__ __forceinline__ TapW tap_weight(const SvgfConsts& k, int step, int i, int j, float4 zp, float2 gz,
-                                           float cp0, float cp1, float il0, float il1, float4 zq, float cq0,
-                                           float cq1) {
+__device__ __forceinline__ float lane(u64 v, int c) {
+    const float2 f = unpack2(v);
+    return c ? f.y : f.x;
+}
+
+// records of pass A, three planes of one float4 per pixel (rec[r * N + p],
+// so that a warp's loads of one plane are contiguous), channel pairs adjacent:
+//   r0 = (a1[0], a1[1], -a2[0], -a2[1]), r1 = (a3[0], a3[1], il[0], il[1]),
+//   r2 = (Gg[0], Gg[1], self[0], self[1])
+// (Gg already divided by the pixel's Gaussian normaliser; zero records on
+// background pixels).  E[t][p] (t = tap_index) is the part of log2 w_pq
+// that does not depend on the colour,
+//   log2(h_i h_j) + sigma_n log2(n_p . n_q) - log2(e) |z_p - z_q| / D,
+// so that pass B rebuilds w_pq = 2^(E - log2(e) il_p |c_p - c_q|) without
+// the G-buffers.  gs[p] += this level's (dL/d sigma_z, dL/d sigma_n,
+// dL/d sigma_l) terms of pixel p.
+template <int kNsq, bool kLum, bool kCheck>
+__device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const float4* g, const float4* x,
+                                            float2 Gc, float2 Gv, float4* rec, float* E, float4* gs, size_t N, int px,
+                                            int py, int p, float4 cp) {
+    using S = Store<DHR_FP32>;
     const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
-    TapW t;
-    t.a_off = (float)step * fabsf(fmaf(gz.x, (float)i, gz.y * (float)j));
-    t.D = fmaf(k.sigma_z, t.a_off, k.eps_z);
-    t.dz = fabsf(zp.x - zq.x);
-    t.nd = zp.y * zq.y + zp.z * zq.z + zp.w * zq.w;
-    const float e = fmaf(-kLog2e, t.dz * rcp_approx(t.D), l5[i + 2] + l5[j + 2]) + log2_normal<kNsq>(t.nd, k.sigma_n);
-    t.w0 = ex2_approx(fmaf(-kLog2e * il0, fabsf(cp0 - cq0), e));
-    t.w1 = ex2_approx(fmaf(-kLog2e * il1, fabsf(cp1 - cq1), e));
-    return t;
-}
-
-// records of pass A, 4 x float4 per pixel:
-//   r0 = (a1, a2, a3, il) of channel 0, r1 = same for channel 1,
-//   r2 = (Gg0, Gg1, self0, self1), r3 = (gz.x, gz.y, -, -)
-// Gg already divided by the pixel's Gaussian normaliser.
-template <int kNsq>
-__global__ void __launch_bounds__(kThreadsA) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
-                                                          const float2* gc, const float2* gv, float4* rec,
-                                                          float* partial) {
-    using S = Store<DHR_FP32>;
-    const int px = blockIdx.x * kBX + threadIdx.x, py = blockIdx.y * kBY + threadIdx.y;
-    float gsz = 0.f, gsn = 0.f, gsl = 0.f;
-    const bool inside = px < k.W && py < k.H;
-    const int p = inside ? py * k.W + px : 0;
-    float4 cp = make_float4(0.f, 0.f, -1.f, -1.f);
-    if (inside) cp = __ldg(x + p);
-    if (inside && fg_var(cp.z)) {
-        const float4 zp = S::g(g, p);
-        float gv0 = 0.f, gv1 = 0.f, gw = 0.f;
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int qx = px + dx, qy = py + dy;
-                if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                const float4 v = __ldg(x + qy * k.W + qx);
-                if (!fg_var(v.z)) continue;
-                const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
-                gw += kk;
-                gv0 = fmaf(kk, v.z, gv0);
-                gv1 = fmaf(kk, v.w, gv1);
-            }
-        const float root0 = sqrtf(fmaxf(0.f, gv0 / gw)), root1 = sqrtf(fmaxf(0.f, gv1 / gw));
-        const float il0 = k.wl_in_atrous ? 1.0f / (k.sigma_l * root0 + k.eps_l) : 0.f;
-        const float il1 = k.wl_in_atrous ? 1.0f / (k.sigma_l * root1 + k.eps_l) : 0.f;
-        const float2 gz = depth_grad<S>(g, k.W, k.H, px, py, zp.x);
-        const float kc = 0.375f * 0.375f;
-        // pass 1: W, A, B per channel
-        float W0 = kc, W1 = kc, A0 = kc * cp.x, A1 = kc * cp.y, B0 = kc * kc * cp.z, B1 = kc * kc * cp.w;
-        for (int j = -2; j <= 2; ++j)
-            for (int i = -2; i <= 2; ++i) {
-                if (!i && !j) continue;
-                const int qx = px + i * step, qy = py + j * step;
-                if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                const int q = qy * k.W + qx;
-                const float4 cq = __ldg(x + q);
-                if (!fg_var(cq.z)) continue;
-                const TapW t = tap_weight<kNsq>(k, step, i, j, zp, gz, cp.x, cp.y, il0, il1, S::g(g, q), cq.x, cq.y);
-                W0 += t.w0;
-                W1 += t.w1;
-                A0 = fmaf(t.w0, cq.x, A0);
-                A1 = fmaf(t.w1, cq.y, A1);
-                B0 = fmaf(t.w0 * t.w0, cq.z, B0);
-                B1 = fmaf(t.w1 * t.w1, cq.w, B1);
-            }
-        const float c0 = A0 / W0, c1 = A1 / W1, v0 = B0 / (W0 * W0), v1 = B1 / (W1 * W1);
-        const float2 Gc = gc[p], Gv = gv[p];
-        const float a10 = Gc.x / W0, a11 = Gc.y / W1;
-        const float a20 = (Gc.x * c0 + 2.f * Gv.x * v0) / W0, a21 = (Gc.y * c1 + 2.f * Gv.y * v1) / W1;
-        const float a30 = 2.f * Gv.x / (W0 * W0), a31 = 2.f * Gv.y / (W1 * W1);
-        // pass 2: gradient of the loss with respect to each weight
-        float self0 = 0.f, self1 = 0.f, Gil0 = 0.f, Gil1 = 0.f;
-        for (int j = -2; j <= 2; ++j)
-            for (int i = -2; i <= 2; ++i) {
-                if (!i && !j) continue;
-                const int qx = px + i * step, qy = py + j * step;
-                if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                const int q = qy * k.W + qx;
-                const float4 cq = __ldg(x + q);
-                if (!fg_var(cq.z)) continue;
-                const TapW t = tap_weight<kNsq>(k, step, i, j, zp, gz, cp.x, cp.y, il0, il1, S::g(g, q), cq.x, cq.y);
-                const float Gw0 = a10 * cq.x - a20 + a30 * t.w0 * cq.z;
-                const float Gw1 = a11 * cq.y - a21 + a31 * t.w1 * cq.w;
-                const float d0 = cp.x - cq.x, d1 = cp.y - cq.y;
-                if (k.wl_in_atrous) {
-                    self0 -= Gw0 * t.w0 * il0 * sgnf(d0);
-                    self1 -= Gw1 * t.w1 * il1 * sgnf(d1);
-                    Gil0 -= Gw0 * t.w0 * fabsf(d0);
-                    Gil1 -= Gw1 * t.w1 * fabsf(d1);
-                }
-                const float gw01 = Gw0 * t.w0 + Gw1 * t.w1;
-                gsz += gw01 * t.dz * t.a_off * rcp_approx(t.D * t.D);
-                if (t.nd > 0.f) gsn += gw01 * __logf(t.nd);
-            }
-        float Gg0 = 0.f, Gg1 = 0.f;
-        if (k.wl_in_atrous) {
-            gsl += Gil0 * (-il0 * il0 * root0) + Gil1 * (-il1 * il1 * root1);
-            // d sqrt(g)/dg is taken as 0 below g = 1e-12 (it grows without bound
-            // toward g = 0, where the weight is already insensitive)
-            if (root0 > 1e-6f) Gg0 = Gil0 * (-il0 * il0 * k.sigma_l * 0.5f / root0) / gw;
-            if (root1 > 1e-6f) Gg1 = Gil1 * (-il1 * il1 * k.sigma_l * 0.5f / root1) / gw;
+    const float4 zp = S::g(g, p);
+    float gv0 = 0.f, gv1 = 0.f, gw = 0.f;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int qx = px + dx, qy = py + dy;
+            if (kCheck && (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H)) continue;
+            const float4 v = __ldg(x + qy * k.W + qx);
+            if (!fg_var(v.z)) continue;
+            const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
+            gw += kk;
+            gv0 = fmaf(kk, v.z, gv0);
+            gv1 = fmaf(kk, v.w, gv1);
         }
-        rec[4 * p + 0] = make_float4(a10, a20, a30, il0);
-        rec[4 * p + 1] = make_float4(a11, a21, a31, il1);
-        rec[4 * p + 2] = make_float4(Gg0, Gg1, self0, self1);
-        rec[4 * p + 3] = make_float4(gz.x, gz.y, 0.f, 0.f);
+    const float root0 = sqrtf(fmaxf(0.f, gv0 / gw)), root1 = sqrtf(fmaxf(0.f, gv1 / gw));
+    const float il0 = kLum ? 1.0f / (k.sigma_l * root0 + k.eps_l) : 0.f;
+    const float il1 = kLum ? 1.0f / (k.sigma_l * root1 + k.eps_l) : 0.f;
+    const float nil0 = -kLog2e * il0, nil1 = -kLog2e * il1;
+    const float2 gz = depth_grad<S>(g, k.W, k.H, px, py, zp.x);
+    const float kc = 0.375f * 0.375f;
+    float* Ep = E + p;
+    ChanSums c;
+#pragma unroll
+    for (int j = -2; j <= 2; ++j)
+#pragma unroll
+        for (int i = -2; i <= 2; ++i) {
+            if (!i && !j) continue;
+            const int qx = px + i * step, qy = py + j * step;
+            if (kCheck && (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H)) continue;
+            const int q = qy * k.W + qx;
+            const float4 cq = __ldg(x + q);
+            if (!fg_var(cq.z)) continue;
+            const float4 zq = S::g(g, q);
+            const float a_off = (float)step * fabsf(fmaf(gz.x, (float)i, gz.y * (float)j));
+            const float rD = rcp_approx(fmaf(k.sigma_z, a_off, k.eps_z));
+            const float dz = fabsf(zp.x - zq.x);
+            const float nd = zp.y * zq.y + zp.z * zq.z + zp.w * zq.w;
+            const float l2n = lg2_approx(fmaxf(nd, 0.0f));
+            float en;
+            if constexpr (kNsq >= 0) en = (float)(1 << kNsq) * l2n;
+            else en = k.sigma_n == 0.0f ? 0.0f : k.sigma_n * l2n;
+            const float e = fmaf(-kLog2e, dz * rD, l5[i + 2] + l5[j + 2]) + en;
+            Ep[(size_t)tap_index(i, j) * N] = e;
+            const float Z = dz * a_off * rD * rD;
+            const float L = nd > 0.f ? l2n * kLn2 : 0.f;
+            const float2 d = make_float2(cq.x - cp.x, cq.y - cp.y), ad = make_float2(fabsf(d.x), fabsf(d.y));
+            c.add<kLum>(ex2_approx(fmaf(nil0, ad.x, e)), ex2_approx(fmaf(nil1, ad.y, e)), d, ad, pack2(cq.z, cq.w), Z,
+                        L);
+        }
+    const float W0 = kc + lane(c.S0_1, 0), W1 = kc + lane(c.S0_1, 1);
+    const float rW0 = 1.0f / W0, rW1 = 1.0f / W1;
+    const float v0 = (kc * kc * cp.z + lane(c.S2_1, 0)) * rW0 * rW0, v1 = (kc * kc * cp.w + lane(c.S2_1, 1)) * rW1 * rW1;
+    // filtered colour minus the centre's: (sum w c_q + kc c_p) / W - c_p
+    const float dc0 = lane(c.S1_1, 0) * rW0, dc1 = lane(c.S1_1, 1) * rW1;
+    const float a10 = Gc.x * rW0, a11 = Gc.y * rW1;
+    const float a20 = (Gc.x * (cp.x + dc0) + 2.f * Gv.x * v0) * rW0, a21 = (Gc.y * (cp.y + dc1) + 2.f * Gv.y * v1) * rW1;
+    const float a30 = 2.f * Gv.x * rW0 * rW0, a31 = 2.f * Gv.y * rW1 * rW1;
+    // a1 c_p - a2, formed without the colours' own scale
+    const float k00 = -(Gc.x * dc0 + 2.f * Gv.x * v0) * rW0, k01 = -(Gc.y * dc1 + 2.f * Gv.y * v1) * rW1;
+    float4 acc = gs[p];
+    acc.x += k00 * lane(c.S0_Z, 0) + a10 * lane(c.S1_Z, 0) + a30 * lane(c.S2_Z, 0) + k01 * lane(c.S0_Z, 1) +
+             a11 * lane(c.S1_Z, 1) + a31 * lane(c.S2_Z, 1);
+    acc.y += k00 * lane(c.S0_L, 0) + a10 * lane(c.S1_L, 0) + a30 * lane(c.S2_L, 0) + k01 * lane(c.S0_L, 1) +
+             a11 * lane(c.S1_L, 1) + a31 * lane(c.S2_L, 1);
+    float Gg0 = 0.f, Gg1 = 0.f, self0 = 0.f, self1 = 0.f;
+    if (kLum) {
+        // sum dL/dw w sgn(c_q - c_p) and sum dL/dw w |c_q - c_p|
+        const float Ts0 = k00 * lane(c.S0_s, 0) + a10 * lane(c.S0_a, 0) + a30 * lane(c.S2_s, 0);
+        const float Ts1 = k01 * lane(c.S0_s, 1) + a11 * lane(c.S0_a, 1) + a31 * lane(c.S2_s, 1);
+        const float Ta0 = k00 * lane(c.S0_a, 0) + a10 * lane(c.S1_a, 0) + a30 * lane(c.S2_a, 0);
+        const float Ta1 = k01 * lane(c.S0_a, 1) + a11 * lane(c.S1_a, 1) + a31 * lane(c.S2_a, 1);
+        // d w / d c_p = -w il sgn(c_p - c_q) = w il sgn(c_q - c_p)
+        self0 = il0 * Ts0;
+        self1 = il1 * Ts1;
+        // d w / d il = -w |c_p - c_q|
+        const float Gil0 = -Ta0, Gil1 = -Ta1;
+        acc.z += Gil0 * (-il0 * il0 * root0) + Gil1 * (-il1 * il1 * root1);
+        // d sqrt(g)/dg is taken as 0 below g = 1e-12 (it grows without bound
+        // toward g = 0, where the weight is already insensitive)
+        if (root0 > 1e-6f) Gg0 = Gil0 * (-il0 * il0 * k.sigma_l * 0.5f / root0) / gw;
+        if (root1 > 1e-6f) Gg1 = Gil1 * (-il1 * il1 * k.sigma_l * 0.5f / root1) / gw;
     }
-    block_sum3(gsz, gsn, gsl, partial);
+    gs[p] = acc;
+    rec[p] = make_float4(a10, a11, -a20, -a21);
+    rec[N + p] = make_float4(a30, a31, il0, il1);
+    rec[2 * N + p] = make_float4(Gg0, Gg1, self0, self1);
 }
 
-// pass B: gradient with respect to the level's input colour and variance
-template <int kNsq>
-__global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step, const float4* g, const float4* x,
-                                                          const float4* rec, float2* gc_in, float2* gv_in) {
-    using S = Store<DHR_FP32>;
-    const int qx = blockIdx.x * kBX + threadIdx.x, qy = blockIdx.y * kBY + threadIdx.y;
+// 32x8 pixel tiles; a tile whose taps (reach 2 step) and 3x3 variance
+// neighbourhoods all lie inside the image skips the bounds tests
+__device__ __forceinline__ bool tile_interior(const SvgfConsts& k, int step, int bx, int by) {
+    const int reach = 2 * step, bx0 = bx * kBX, by0 = by * kBY;
+    return bx0 - reach >= 0 && by0 - reach >= 0 && bx0 + kBX - 1 + reach < k.W && by0 + kBY - 1 + reach < k.H;
+}
+
+// pass B: gradient with respect to the level's input colour and variance.
+// The taps are evaluated without branches (a tap outside the image reads the
+// centre's own records, and a select drops every tap outside the image or
+// on background) so that the loads of all taps can be issued together.
+// Returns (dL/d c_q, dL/d v_q) per channel.
+template <bool kCheck>
+__device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, const float4* x, const float4* rec,
+                                              const float* E, size_t N, int qx, int qy, int q, float4 cq) {
+    const float kc = 0.375f * 0.375f;
+    const float4 r0 = rec[q], r1 = rec[N + q], r2 = rec[2 * N + q];
+    // own colour through the weights of q's own footprint, and the centre tap
+    u64 gcs = pack2(r2.z + r0.x * kc, r2.w + r0.y * kc);
+    u64 gvs = pack2(0.5f * r1.x * kc * kc, 0.5f * r1.y * kc * kc);
+    // variance Gaussians that read q (background pixels hold zero records)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int px = qx + dx, py = qy + dy;
+            if (kCheck && (px < 0 || py < 0 || px >= k.W || py >= k.H)) continue;
+            const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
+            const float4 rp = rec[2 * N + py * k.W + px];
+            gvs = fma2(pack2(rp.x, rp.y), pack2(kk, kk), gvs);
+        }
+    const u64 cqc = pack2(cq.x, cq.y), cqv = pack2(cq.z, cq.w), half = pack2(0.5f, 0.5f);
+    const u64 ncq = pack2(-cq.x, -cq.y);
+    // the log-weights stream from memory once each: issue all 24 loads first
+    float ev[24];
+#pragma unroll
+    for (int j = -2; j <= 2; ++j)
+#pragma unroll
+        for (int i = -2; i <= 2; ++i) {
+            if (!i && !j) continue;
+            const int px = qx - i * step, py = qy - j * step;
+            const bool in = !kCheck || (px >= 0 && py >= 0 && px < k.W && py < k.H);
+            ev[tap_index(i, j)] = __ldg(E + (size_t)tap_index(i, j) * N + (in ? py * k.W + px : q));
+        }
+    // footprints of the 24 pixels p = q - (i, j) step that tap q at (i, j)
+#pragma unroll
+    for (int j = -2; j <= 2; ++j)
+#pragma unroll
+        for (int i = -2; i <= 2; ++i) {
+            if (!i && !j) continue;
+            const int px = qx - i * step, py = qy - j * step;
+            const bool in = !kCheck || (px >= 0 && py >= 0 && px < k.W && py < k.H);
+            const int p = in ? py * k.W + px : q;
+            const float4 cp = __ldg(x + p);
+            const float4 p0 = rec[p], p1 = rec[N + p];
+            const float e = ev[tap_index(i, j)];
+            const bool use = in && fg_var(cp.z);
+            const float2 d = unpack2(add2(pack2(cp.x, cp.y), ncq));   // c_p - c_q
+            const float w0 = ex2_approx(fmaf(-kLog2e * p1.z, fabsf(d.x), e));
+            const float w1 = ex2_approx(fmaf(-kLog2e * p1.w, fabsf(d.y), e));
+            const u64 w = pack2(w0, w1);
+            const u64 a3w = mul2(pack2(p1.x, p1.y), w);
+            // dL/dw_pq = a1 c_q - a2 + a3 w v_q
+            const u64 Gw = fma2(a3w, cqv, fma2(pack2(p0.x, p0.y), cqc, pack2(p0.z, p0.w)));
+            const u64 sil = pack2(p1.z * sgnf(d.x), p1.w * sgnf(d.y));
+            const float2 dc = unpack2(fma2(mul2(Gw, w), sil, mul2(pack2(p0.x, p0.y), w)));
+            const float2 dv = unpack2(mul2(mul2(a3w, w), half));
+            gcs = add2(gcs, pack2(use ? dc.x : 0.f, use ? dc.y : 0.f));
+            gvs = add2(gvs, pack2(use ? dv.x : 0.f, use ? dv.y : 0.f));
+        }
+    const float2 gc = unpack2(gcs), gv = unpack2(gvs);
+    return make_float4(gc.x, gc.y, gv.x, gv.y);
+}
+
+// Upstream gradient (dL/d colour, dL/d variance) of pixel q at the output
+// of a level (or at the temporal output): from the loss gradient planes
+// g_out [2][N] (the last level; no variance gradient) or from the buffers
+// gc, gv that pass B of the level above wrote.  gcol (or null) adds the
+// gradient that reaches level 0's output through the colour history of the
+// next frame.
+struct Upstream {
+    const float* g_out;
+    const float2* gc;
+    const float2* gv;
+    const float2* gcol;
+};
+
+__device__ __forceinline__ float4 upstream(const Upstream& up, size_t N, int q) {
+    float4 G;
+    if (up.g_out) {
+        G = make_float4(up.g_out[q], up.g_out[N + q], 0.f, 0.f);
+    } else {
+        const float2 c = up.gc[q], v = up.gv[q];
+        G = make_float4(c.x, c.y, v.x, v.y);
+    }
+    if (up.gcol) {
+        const float2 a = up.gcol[q];
+        G.x += a.x;
+        G.y += a.y;
+    }
+    return G;
+}
+
+template <int kNsq, bool kLum>
+__global__ void __launch_bounds__(kThreadsA, 4) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
+                                                             Upstream up, float4* rec, float* E, float4* gs) {
+    const int px = blockIdx.x * kBX + threadIdx.x, py = blockIdx.y * kBY + threadIdx.y;
+    if (px >= k.W || py >= k.H) return;
+    const int p = py * k.W + px;
+    const size_t N = (size_t)k.W * k.H;
+    const float4 cp = __ldg(x + p);
+    if (!fg_var(cp.z)) {
+        rec[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rec[N + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rec[2 * N + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float4 G = upstream(up, N, p);
+    if (tile_interior(k, step, blockIdx.x, blockIdx.y))
+        bwd_a_pixel<kNsq, kLum, false>(k, step, g, x, make_float2(G.x, G.y), make_float2(G.z, G.w), rec, E, gs, N,
+                                       px, py, p, cp);
+    else
+        bwd_a_pixel<kNsq, kLum, true>(k, step, g, x, make_float2(G.x, G.y), make_float2(G.z, G.w), rec, E, gs, N,
+                                      px, py, p, cp);
+}
+
+// Pass B runs its tiles in the reverse of pass A's order: the log-weights and
+// records pass A wrote last are the ones still in L2 when pass B starts.
+__global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step, const float4* x, const float4* rec,
+                                                          const float* E, float2* gc_in, float2* gv_in) {
+    const int bx = gridDim.x - 1 - blockIdx.x, by = gridDim.y - 1 - blockIdx.y;
+    const int qx = bx * kBX + threadIdx.x, qy = by * kBY + threadIdx.y;
     if (qx >= k.W || qy >= k.H) return;
     const int q = qy * k.W + qx;
     const float4 cq = __ldg(x + q);
@@ -199,75 +342,58 @@ __global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step
         gv_in[q] = make_float2(0.f, 0.f);
         return;
     }
-    const float4 zq = S::g(g, q);
-    const float kc = 0.375f * 0.375f;
-    const float4 r0 = rec[4 * q + 0], r1 = rec[4 * q + 1], r2 = rec[4 * q + 2];
-    // own colour through the weights of q's own footprint, and the centre tap
-    float gcx = r2.z + r0.x * kc, gcy = r2.w + r1.x * kc;
-    float gvx = 0.5f * r0.z * kc * kc, gvy = 0.5f * r1.z * kc * kc;
-    // variance Gaussians that read q
-    for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-            const int px = qx + dx, py = qy + dy;
-            if (px < 0 || py < 0 || px >= k.W || py >= k.H) continue;
-            const int p = py * k.W + px;
-            if (!fg_var(__ldg(x + p).z)) continue;
-            const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
-            const float4 rp = rec[4 * p + 2];
-            gvx = fmaf(rp.x, kk, gvx);
-            gvy = fmaf(rp.y, kk, gvy);
-        }
-    // footprints of the 24 pixels p = q - (i, j) step that tap q at (i, j)
-    for (int j = -2; j <= 2; ++j)
-        for (int i = -2; i <= 2; ++i) {
-            if (!i && !j) continue;
-            const int px = qx - i * step, py = qy - j * step;
-            if (px < 0 || py < 0 || px >= k.W || py >= k.H) continue;
-            const int p = py * k.W + px;
-            const float4 cp = __ldg(x + p);
-            if (!fg_var(cp.z)) continue;
-            const float4 p0 = rec[4 * p + 0], p1 = rec[4 * p + 1], p3 = rec[4 * p + 3];
-            const TapW t = tap_weight<kNsq>(k, step, i, j, S::g(g, p), make_float2(p3.x, p3.y), cp.x, cp.y, p0.w,
-                                            p1.w, zq, cq.x, cq.y);
-            const float Gw0 = p0.x * cq.x - p0.y + p0.z * t.w0 * cq.z;
-            const float Gw1 = p1.x * cq.y - p1.y + p1.z * t.w1 * cq.w;
-            gcx += p0.x * t.w0 + Gw0 * t.w0 * p0.w * sgnf(cp.x - cq.x);
-            gcy += p1.x * t.w1 + Gw1 * t.w1 * p1.w * sgnf(cp.y - cq.y);
-            gvx = fmaf(0.5f * p0.z, t.w0 * t.w0, gvx);
-            gvy = fmaf(0.5f * p1.z, t.w1 * t.w1, gvy);
-        }
-    gc_in[q] = make_float2(gcx, gcy);
-    gv_in[q] = make_float2(gvx, gvy);
-}
-
-// upstream gradient of the last level: planes [2][N] -> float2 (+ history term)
-__global__ void gather_planes_kernel(int n, const float* g_out, const float2* add, float2* gc, float2* gv) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float2 v = make_float2(g_out[i], g_out[n + i]);
-    if (add) {
-        const float2 a = add[i];
-        v.x += a.x;
-        v.y += a.y;
-    }
-    gc[i] = v;
-    gv[i] = make_float2(0.f, 0.f);
-}
-
-__global__ void add2_kernel(int n, float2* a, const float2* b) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float2 u = a[i], v = b[i];
-    a[i] = make_float2(u.x + v.x, u.y + v.y);
+    const size_t N = (size_t)k.W * k.H;
+    const float4 G = tile_interior(k, step, bx, by) ? bwd_b_pixel<false>(k, step, x, rec, E, N, qx, qy, q, cq)
+                                                    : bwd_b_pixel<true>(k, step, x, rec, E, N, qx, qy, q, cq);
+    gc_in[q] = make_float2(G.x, G.y);
+    gv_in[q] = make_float2(G.z, G.w);
 }
 
 // Backward of the temporal step of one frame (FP32 storage).
+//
+// dL/d sig lands on the pixel itself (moving averages) and, for pixels with
+// fewer than 4 frames of history, on the 7x7 neighbourhood of the spatial
+// moment estimate.  The block accumulates both in a shared tile of its
+// 32x8 pixels plus a 3-pixel apron and adds the tile to g_sig once, so the
+// atomics to device memory are one per nonzero tile entry.  The history
+// gradients scatter to the 4 reprojection taps of the previous frame with
+// vector atomics (one float2 and one float4 per tap).
+constexpr int kTR = 3, kTW = kBX + 2 * kTR, kTH = kBY + 2 * kTR;
+
+// Weight of the 7x7 short-history estimate (the forward's w_spatial) with
+// the intermediates its derivatives reuse: w = 2^(sigma_n log2(n.n_q) -
+// log2(e) |dz| rD), rD = 1 / (sigma_z a_off + eps_z); the centre has w = 1.
+struct W7 {
+    float w, dz, a_off, rD, nd, l2n;
+};
+
+__device__ __forceinline__ W7 w7(const SvgfConsts& k, float4 zn, float2 gz, int dx, int dy, float4 zq) {
+    W7 t;
+    if (!(dx || dy)) {
+        t.w = 1.0f;
+        t.dz = t.a_off = t.l2n = 0.f;
+        t.rD = t.nd = 1.f;
+        return t;
+    }
+    t.a_off = fabsf(fmaf(gz.x, (float)-dx, gz.y * (float)-dy));
+    t.rD = rcp_approx(fmaf(k.sigma_z, t.a_off, k.eps_z));
+    t.dz = fabsf(zn.x - zq.x);
+    t.nd = zn.y * zq.y + zn.z * zq.z + zn.w * zq.w;
+    t.l2n = lg2_approx(fmaxf(t.nd, 0.0f));
+    t.w = ex2_approx(fmaf(-t.dz, kLog2e * t.rD, k.sigma_n == 0.0f ? 0.0f : k.sigma_n * t.l2n));
+    return t;
+}
+
 __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
     SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const float4* g_cur, const uint32_t* mesh_cur,
     const float4* g_prev, const uint32_t* mesh_prev, const float* sig, const float4* mom, const uint8_t* hist,
-    const float2* gc, const float2* gv, const float4* gmom, float* g_sig, float2* gcol_prev, float4* gmom_prev,
-    float* partial) {
+    Upstream up, const float4* gmom, float* g_sig, float2* gcol_prev, float4* gmom_prev, float4* gs) {
     using S = Store<DHR_FP32>;
+    __shared__ float tile[2][kTH][kTW];
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    for (int e = tid; e < 2 * kTH * kTW; e += kThreadsA) (&tile[0][0][0])[e] = 0.f;
+    __syncthreads();
+    const int bx0 = blockIdx.x * kBX - kTR, by0 = blockIdx.y * kBY - kTR;
     const int x = blockIdx.x * kBX + threadIdx.x, y = blockIdx.y * kBY + threadIdx.y;
     const int N = k.W * k.H;
     float gsz = 0.f, gsn = 0.f;
@@ -287,7 +413,8 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
         const float2 s = make_float2(sig[p], sig[N + p]);
         float2 Gce = make_float2(0.f, 0.f);
         float4 Gm = gmom[p];
-        const float2 Gc = gc[p], Gv = gv[p];
+        const float4 G = upstream(up, N, p);   // at the temporal output (level 0's input)
+        const float2 Gc = make_float2(G.x, G.y), Gv = make_float2(G.z, G.w);
         if (n >= 4) {
             Gce = Gc;
             const float4 m = mom[p];
@@ -300,8 +427,13 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                 Gm.y -= 2.f * m.y * Gv.y;
             }
         } else {
-            // 7x7 estimate: colour = m1, var = max(0, m2 - m1^2), m_k = sum w s^k / sum w
+            // 7x7 estimate: colour = m1, var = max(0, m2 - m1^2), m_k = sum w s^k / sum w.
+            // With Gw_q = (G1 (s_q - m1) + G2 (s_q^2 - m2)) / sw summed over both
+            // channels, the sigma derivatives need sum_q Gw_q w_q f_q for
+            // f = Z (d w / d sigma_z / w) and L (ln n.n_q): the first pass keeps
+            // sum w f, sum w f s and sum w f s^2 per channel.
             float sw = 0.f, s1x = 0.f, s1y = 0.f, s2x = 0.f, s2y = 0.f;
+            float fZ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, fL[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             for (int dy = -3; dy <= 3; ++dy)
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx, qy = y + dy;
@@ -309,18 +441,34 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                     const int q = qy * k.W + qx;
                     const float4 zq = S::g(g_cur, q);
                     if (!is_fg(zq.x)) continue;
-                    const float w = w_spatial(k, zn.x, make_float3(zn.y, zn.z, zn.w), gz, dx, dy, zq);
+                    const W7 t = w7(k, zn, gz, dx, dy, zq);
                     const float sx = sig[q], sy = sig[N + q];
-                    sw += w;
-                    s1x = fmaf(w, sx, s1x);
-                    s1y = fmaf(w, sy, s1y);
-                    s2x = fmaf(w, sx * sx, s2x);
-                    s2y = fmaf(w, sy * sy, s2y);
+                    sw += t.w;
+                    s1x = fmaf(t.w, sx, s1x);
+                    s1y = fmaf(t.w, sy, s1y);
+                    s2x = fmaf(t.w, sx * sx, s2x);
+                    s2y = fmaf(t.w, sy * sy, s2y);
+                    if (dx || dy) {
+                        const float wZ = t.w * t.dz * t.a_off * t.rD * t.rD;
+                        const float wL = t.nd > 0.f ? t.w * t.l2n * kLn2 : 0.f;
+                        const float f[5] = {1.f, sx, sx * sx, sy, sy * sy};
+#pragma unroll
+                        for (int u = 0; u < 5; ++u) {
+                            fZ[u] = fmaf(wZ, f[u], fZ[u]);
+                            fL[u] = fmaf(wL, f[u], fL[u]);
+                        }
+                    }
                 }
             const float m1x = s1x / sw, m1y = s1y / sw, m2x = s2x / sw, m2y = s2y / sw;
             const bool vx = m2x - m1x * m1x > 0.f, vy = m2y - m1y * m1y > 0.f;
             const float G1x = Gc.x - (vx ? 2.f * m1x * Gv.x : 0.f), G1y = Gc.y - (vy ? 2.f * m1y * Gv.y : 0.f);
             const float G2x = vx ? Gv.x : 0.f, G2y = vy ? Gv.y : 0.f;
+            const float isw = 1.f / sw;
+            gsz += (G1x * (fZ[1] - m1x * fZ[0]) + G2x * (fZ[2] - m2x * fZ[0]) + G1y * (fZ[3] - m1y * fZ[0]) +
+                    G2y * (fZ[4] - m2y * fZ[0])) * isw;
+            gsn += (G1x * (fL[1] - m1x * fL[0]) + G2x * (fL[2] - m2x * fL[0]) + G1y * (fL[3] - m1y * fL[0]) +
+                    G2y * (fL[4] - m2y * fL[0])) * isw;
+            // dL/d s_q = (G1 + 2 G2 s_q) w_q / sw, into the shared tile
             for (int dy = -3; dy <= 3; ++dy)
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx, qy = y + dy;
@@ -328,43 +476,68 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                     const int q = qy * k.W + qx;
                     const float4 zq = S::g(g_cur, q);
                     if (!is_fg(zq.x)) continue;
-                    float a_off = 0.f, D = 1.f, nd = 1.f;
-                    if (dx || dy) {
-                        a_off = fabsf(fmaf(gz.x, (float)-dx, gz.y * (float)-dy));
-                        D = fmaf(k.sigma_z, a_off, k.eps_z);
-                        nd = zn.y * zq.y + zn.z * zq.z + zn.w * zq.w;
-                    }
-                    const float w = w_spatial(k, zn.x, make_float3(zn.y, zn.z, zn.w), gz, dx, dy, zq);
+                    const float w = w7(k, zn, gz, dx, dy, zq).w * isw;
                     const float sx = sig[q], sy = sig[N + q];
-                    atomicAdd(g_sig + q, (G1x + G2x * 2.f * sx) * w / sw);
-                    atomicAdd(g_sig + N + q, (G1y + G2y * 2.f * sy) * w / sw);
-                    if (dx || dy) {
-                        const float Gw = (G1x * (sx - m1x) + G2x * (sx * sx - m2x) + G1y * (sy - m1y) +
-                                          G2y * (sy * sy - m2y)) / sw;
-                        gsz += Gw * w * fabsf(zn.x - zq.x) * a_off * rcp_approx(D * D);
-                        if (nd > 0.f) gsn += Gw * w * __logf(nd);
-                    }
+                    atomicAdd(&tile[0][qy - by0][qx - bx0], (G1x + G2x * 2.f * sx) * w);
+                    atomicAdd(&tile[1][qy - by0][qx - bx0], (G1y + G2y * 2.f * sy) * w);
                 }
         }
         // moving averages
-        atomicAdd(g_sig + p, a * Gce.x + a * Gm.x + 2.f * a * s.x * Gm.z);
-        atomicAdd(g_sig + N + p, a * Gce.y + a * Gm.y + 2.f * a * s.y * Gm.w);
+        atomicAdd(&tile[0][y - by0][x - bx0], a * Gce.x + a * Gm.x + 2.f * a * s.x * Gm.z);
+        atomicAdd(&tile[1][y - by0][x - bx0], a * Gce.y + a * Gm.y + 2.f * a * s.y * Gm.w);
         if (valid) {
             const float b = 1.f - a;
             for (int t = 0; t < 4; ++t) {
                 if (!(r.ok & (1 << t))) continue;
                 const int q = (r.y0 + (t >> 1)) * k.W + (r.x0 + (t & 1));
-                const float beta = r.w[t] / r.sumw;
-                atomicAdd(&gcol_prev[q].x, beta * b * Gce.x);
-                atomicAdd(&gcol_prev[q].y, beta * b * Gce.y);
-                atomicAdd(&gmom_prev[q].x, beta * b * Gm.x);
-                atomicAdd(&gmom_prev[q].y, beta * b * Gm.y);
-                atomicAdd(&gmom_prev[q].z, beta * b * Gm.z);
-                atomicAdd(&gmom_prev[q].w, beta * b * Gm.w);
+                const float bb = r.w[t] / r.sumw * b;
+                atomicAdd(gcol_prev + q, make_float2(bb * Gce.x, bb * Gce.y));
+                atomicAdd(gmom_prev + q, make_float4(bb * Gm.x, bb * Gm.y, bb * Gm.z, bb * Gm.w));
             }
         }
     }
-    block_sum3(gsz, gsn, 0.f, partial);
+    __syncthreads();
+    for (int e = tid; e < 2 * kTH * kTW; e += kThreadsA) {
+        const int c = e / (kTH * kTW), r = e % (kTH * kTW);
+        const int qx = bx0 + r % kTW, qy = by0 + r / kTW;
+        const float v = tile[c][r / kTW][r % kTW];
+        if (v != 0.f && qx >= 0 && qy >= 0 && qx < k.W && qy < k.H) atomicAdd(g_sig + (size_t)c * N + qy * k.W + qx, v);
+    }
+    if (inside && (gsz != 0.f || gsn != 0.f)) {
+        float4 acc = gs[p];
+        acc.x += gsz;
+        acc.y += gsn;
+        gs[p] = acc;
+    }
+}
+
+// per-block sums (double, then rounded to float) of the per-pixel sigma
+// terms: block b sums a fixed contiguous range of pixels in a fixed order
+constexpr int kPixReduceBlocks = 296, kPixReduceThreads = 256;
+__global__ void __launch_bounds__(kPixReduceThreads) reduce_pixels_kernel(int n, const float4* gs, float* partial) {
+    __shared__ double sh[3][kPixReduceThreads];
+    const int t = threadIdx.x;
+    const int per = (n + gridDim.x - 1) / gridDim.x, b0 = blockIdx.x * per, b1 = min(n, b0 + per);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int i = b0 + t; i < b1; i += kPixReduceThreads) {
+        const float4 v = gs[i];
+        s0 += (double)v.x;
+        s1 += (double)v.y;
+        s2 += (double)v.z;
+    }
+    sh[0][t] = s0;
+    sh[1][t] = s1;
+    sh[2][t] = s2;
+    __syncthreads();
+    for (int o = kPixReduceThreads / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            sh[0][t] += sh[0][t + o];
+            sh[1][t] += sh[1][t + o];
+            sh[2][t] += sh[2][t + o];
+        }
+        __syncthreads();
+    }
+    if (t < 3) partial[3 * blockIdx.x + t] = (float)sh[t][0];
 }
 
 // sum the per-block partials into acc[3] (double) with one block of
@@ -407,22 +580,28 @@ __global__ void finish_sigma_kernel(const double* acc, float* out) {
 struct dhr_svgf_tape {
     int W = 0, H = 0, F = 0;
     int frames_recorded = 0;
+    int levels_recorded = 0;
     float4* illum = nullptr;   // [F][N] temporal outputs
     float4* mom = nullptr;     // [F][N] moments
     uint8_t* hist = nullptr;   // [F][N] history lengths
     float2* col = nullptr;     // [N] colour history (forward)
     float4* lev[2] = {nullptr, nullptr};
-    float4* lvin = nullptr;    // [levels - 1][N] inputs of levels 1.. (backward scratch)
-    int lvin_levels = 0;
-    float2* gc[2] = {nullptr, nullptr};
-    float2* gv[2] = {nullptr, nullptr};
+    float4* lvs = nullptr;     // [F][levels - 1][N] inputs of levels 1.. (recorded by the forward)
+    int lvs_levels = 0;
     float2* gcol[2] = {nullptr, nullptr};
     float4* gmom[2] = {nullptr, nullptr};
-    float4* rec = nullptr;     // [N][4]
-    float* partial = nullptr;  // [blocks][3]
+    float2* gc = nullptr;      // [N] dL/d colour at the input of the level just processed
+    float2* gv = nullptr;      // [N] dL/d variance, same
+    float4* rec = nullptr;     // [3][N] pass-A records
+    float* E = nullptr;        // [24][N] colour-free part of log2 w per tap
+    float4* gs = nullptr;      // [N] per-pixel (dL/d sigma_z, dL/d sigma_n, dL/d sigma_l, -)
+    float* partial = nullptr;  // [kPixReduceBlocks][3]
     double* acc = nullptr;     // [3]
     int nblocks = 0;
 };
+
+// levels the differentiable form accepts (check_svgf_params enforces it)
+constexpr int kMaxLevels = 8;
 
 using namespace dhr;
 
@@ -434,13 +613,15 @@ static void tape_free(dhr_svgf_tape* t) {
     cudaFree(t->col);
     for (int i = 0; i < 2; ++i) {
         cudaFree(t->lev[i]);
-        cudaFree(t->gc[i]);
-        cudaFree(t->gv[i]);
         cudaFree(t->gcol[i]);
         cudaFree(t->gmom[i]);
     }
+    cudaFree(t->gc);
+    cudaFree(t->gv);
     cudaFree(t->rec);
-    cudaFree(t->lvin);
+    cudaFree(t->E);
+    cudaFree(t->gs);
+    cudaFree(t->lvs);
     cudaFree(t->partial);
     cudaFree(t->acc);
     delete t;
@@ -466,13 +647,15 @@ extern "C" dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_
     if (!e) e = cudaMalloc((void**)&t->col, n * 8);
     for (int i = 0; i < 2 && !e; ++i) {
         e = cudaMalloc((void**)&t->lev[i], n * 16);
-        if (!e) e = cudaMalloc((void**)&t->gc[i], n * 8);
-        if (!e) e = cudaMalloc((void**)&t->gv[i], n * 8);
         if (!e) e = cudaMalloc((void**)&t->gcol[i], n * 8);
         if (!e) e = cudaMalloc((void**)&t->gmom[i], n * 16);
     }
-    if (!e) e = cudaMalloc((void**)&t->rec, n * 64);
-    if (!e) e = cudaMalloc((void**)&t->partial, (size_t)t->nblocks * 3 * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&t->gc, n * 8);
+    if (!e) e = cudaMalloc((void**)&t->gv, n * 8);
+    if (!e) e = cudaMalloc((void**)&t->rec, n * 48);
+    if (!e) e = cudaMalloc((void**)&t->E, n * 24 * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&t->gs, n * 16);
+    if (!e) e = cudaMalloc((void**)&t->partial, (size_t)kPixReduceBlocks * 3 * sizeof(float));
     if (!e) e = cudaMalloc((void**)&t->acc, 3 * sizeof(double));
     if (e) {
         cudaGetLastError();
@@ -511,6 +694,20 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
     const size_t N = (size_t)t->W * t->H;
     const dim3 blk(32, 8), grid((t->W + 31) / 32, (t->H + 7) / 8);
     const int L = (int)params->levels;
+    DHR_CHECK_ARG(L <= kMaxLevels, "svgf_seq_forward: levels %d > %d", L, kMaxLevels);
+    if (L > 1 && t->lvs_levels < L - 1) {   // inputs of levels 1..L-1 of every frame, allocated on first use
+        cudaFree(t->lvs);
+        t->lvs = nullptr;
+        t->lvs_levels = 0;
+        const cudaError_t e = cudaMalloc((void**)&t->lvs, (size_t)t->F * (L - 1) * N * 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
+                             "svgf_seq_forward: level records: %s", cudaGetErrorString(e));
+        }
+        t->lvs_levels = L - 1;
+    }
+    t->frames_recorded = 0;
     for (int f = 0; f < t->F; ++f) {
         const bool hp = f > 0;
         const auto* gc = static_cast<const S::G*>(gbufs[f].depth_normal);
@@ -530,7 +727,7 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
         }
         const float4* in = illum;
         for (int l = 0; l < L; ++l) {
-            float4* o = t->lev[l & 1];
+            float4* o = l + 1 < L ? t->lvs + ((size_t)f * (L - 1) + l) * N : t->lev[l & 1];
             const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
             DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, 2, st, k, 1 << l, gc, in, o, t->col, ao, sh));
             if (L == 1) {
@@ -541,6 +738,7 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
         }
     }
     t->frames_recorded = t->F;
+    t->levels_recorded = L;
     return DHR_OK;
 }
 
@@ -552,6 +750,9 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
     DHR_CHECK_ARG(sig && g_out && g_sig && g_sigma, "svgf_seq_backward: null pointer");
     if (t->frames_recorded != t->F)
         return set_error(DHR_ERR_STATE, "svgf_seq_backward: run dhr_svgf_seq_forward on this tape first");
+    if (t->levels_recorded != (int)params->levels)
+        return set_error(DHR_ERR_STATE, "svgf_seq_backward: the forward ran %d levels, not %d", t->levels_recorded,
+                         (int)params->levels);
     cudaStream_t st = as_stream(stream);
     using S = Store<DHR_FP32>;
     const SvgfConsts k = make_consts(t->W, t->H, params);
@@ -559,21 +760,9 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
     const size_t N = (size_t)t->W * t->H;
     const int n = (int)N;
     const dim3 blk(32, 8), grid((t->W + 31) / 32, (t->H + 7) / 8);
-    const int eb = (n + 255) / 256;
     const int L = (int)params->levels;
-    if (L > 1 && t->lvin_levels < L - 1) {   // inputs of levels 1..L-1, allocated on first use
-        cudaFree(t->lvin);
-        t->lvin = nullptr;
-        t->lvin_levels = 0;
-        const cudaError_t e = cudaMalloc((void**)&t->lvin, (size_t)(L - 1) * N * 16);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
-                             "svgf_seq_backward: level scratch: %s", cudaGetErrorString(e));
-        }
-        t->lvin_levels = L - 1;
-    }
     DHR_CUDA_TRY(cudaMemsetAsync(g_sig, 0, (size_t)t->F * 2 * N * sizeof(float), st));
+    DHR_CUDA_TRY(cudaMemsetAsync(t->gs, 0, N * 16, st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->acc, 0, 3 * sizeof(double), st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[0], 0, N * 8, st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[0], 0, N * 16, st));
@@ -581,47 +770,45 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
     for (int f = t->F - 1; f >= 0; --f) {
         const auto* gcur = static_cast<const S::G*>(gbufs[f].depth_normal);
         const float4* illum = t->illum + (size_t)f * N;
-        int cur = 0;
-        gather_planes_kernel<<<eb, 256, 0, st>>>(n, g_out + (size_t)f * 2 * N, L == 0 ? t->gcol[nx] : nullptr,
-                                                t->gc[0], t->gv[0]);
-        DHR_CUDA_TRY(cudaGetLastError());
-        // recompute the inputs of levels 1..L-1 from the recorded temporal output
-        for (int i = 0; i + 1 < L; ++i)
-            DHR_TRY(launch_atrous<DHR_FP32>(0, nsq, 2, st, k, 1 << i, gcur, i == 0 ? illum : t->lvin + (size_t)(i - 1) * N,
-                                            t->lvin + (size_t)i * N, nullptr, nullptr, nullptr));
+        // the gradient at the output of the level being processed comes from
+        // the loss (last level) or from pass B of the level above
+        Upstream up{g_out + (size_t)f * 2 * N, nullptr, nullptr, L <= 1 ? t->gcol[nx] : nullptr};
         for (int l = L - 1; l >= 0; --l) {
-            const float4* xin = l == 0 ? illum : t->lvin + (size_t)(l - 1) * N;
-            if (l == 0) {   // level-0 colour is also next frame's colour history
-                add2_kernel<<<eb, 256, 0, st>>>(n, t->gc[cur], t->gcol[nx]);
-                DHR_CUDA_TRY(cudaGetLastError());
-            }
-            if (nsq == 7)
-                atrous_bwd_a<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->gc[cur], t->gv[cur], t->rec, t->partial);
+            const float4* xin = l == 0 ? illum : t->lvs + ((size_t)f * (L - 1) + (l - 1)) * N;
+            if (nsq == 7 && k.wl_in_atrous)
+                atrous_bwd_a<7, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
+            else if (nsq == 7)
+                atrous_bwd_a<7, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
+            else if (k.wl_in_atrous)
+                atrous_bwd_a<-1, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
             else
-                atrous_bwd_a<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->gc[cur], t->gv[cur], t->rec,
-                                                       t->partial);
+                atrous_bwd_a<-1, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
             DHR_CUDA_TRY(cudaGetLastError());
-            reduce_partials_kernel<<<1, kReduceThreads, 0, st>>>(t->nblocks, t->partial, t->acc);
-            if (nsq == 7)
-                atrous_bwd_b<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc[cur ^ 1], t->gv[cur ^ 1]);
-            else
-                atrous_bwd_b<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc[cur ^ 1], t->gv[cur ^ 1]);
+            atrous_bwd_b<<<grid, blk, 0, st>>>(k, 1 << l, xin, t->rec, t->E, t->gc, t->gv);
             DHR_CUDA_TRY(cudaGetLastError());
-            cur ^= 1;
+            // level l - 1's output gradient (plus, for level 0's output, the
+            // next frame's colour-history gradient)
+            up = Upstream{nullptr, t->gc, t->gv, l == 1 ? t->gcol[nx] : nullptr};
         }
         const int pv = nx ^ 1;
         DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[pv], 0, N * 8, st));
         DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[pv], 0, N * 16, st));
         const bool hp = f > 0;
+        // at the temporal output: pass B of level 0, or the loss gradient plus
+        // the colour-history gradient when there are no levels
+        up.gcol = L == 0 ? t->gcol[nx] : nullptr;
         temporal_bwd_kernel<<<grid, blk, 0, st>>>(
             k, cams[f], hp ? cams[f - 1] : cams[f], gcur, gbufs[f].mesh_id,
             hp ? static_cast<const S::G*>(gbufs[f - 1].depth_normal) : nullptr, hp ? gbufs[f - 1].mesh_id : nullptr,
-            sig + (size_t)f * 2 * N, t->mom + (size_t)f * N, t->hist + (size_t)f * N, t->gc[cur], t->gv[cur],
-            t->gmom[nx], g_sig + (size_t)f * 2 * N, t->gcol[pv], t->gmom[pv], t->partial);
+            sig + (size_t)f * 2 * N, t->mom + (size_t)f * N, t->hist + (size_t)f * N, up, t->gmom[nx],
+            g_sig + (size_t)f * 2 * N, t->gcol[pv], t->gmom[pv], t->gs);
         DHR_CUDA_TRY(cudaGetLastError());
-        reduce_partials_kernel<<<1, kReduceThreads, 0, st>>>(t->nblocks, t->partial, t->acc);
         nx = pv;
     }
+    reduce_pixels_kernel<<<kPixReduceBlocks, kPixReduceThreads, 0, st>>>(n, t->gs, t->partial);
+    DHR_CUDA_TRY(cudaGetLastError());
+    reduce_partials_kernel<<<1, kReduceThreads, 0, st>>>(kPixReduceBlocks, t->partial, t->acc);
+    DHR_CUDA_TRY(cudaGetLastError());
     finish_sigma_kernel<<<1, 32, 0, st>>>(t->acc, g_sigma);
     DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
