@@ -148,8 +148,8 @@ typedef struct {
     float sigma_z;        /* depth edge stopping */
     float sigma_n;        /* normal edge stopping exponent (>= 0) */
     float sigma_l;        /* luminance edge stopping */
-    float eps_z;
-    float eps_l;
+    float eps_z;          /* > 0: keeps the depth weight's denominator away from 0 */
+    float eps_l;          /* > 0: same for the luminance weight */
     uint32_t ao_spp;      /* N used to turn the AO count into [0, 1] */
     uint32_t levels;      /* a-trous iterations, 0..8 (step 2^i) */
     uint32_t fixed_alpha; /* 1: effective alpha = alpha once history exists */
@@ -371,10 +371,11 @@ typedef struct dhr_svgf_tape dhr_svgf_tape;
 
 /* Recording space for F frames of W x H (FP32): per frame the temporal
  * output, moments and history lengths (33 B/px), plus work buffers
- * (208 B/px).  The first forward with L > 1 levels adds the inputs of
- * levels 1..L-1 of every frame, 16 (L - 1) B/px per frame (kept with the
- * tape until it is destroyed).  Errors: DHR_ERR_INVALID (size outside
- * 1..2^27 pixels, frames outside 1..1024), DHR_ERR_OOM. */
+ * (264 B/px).  The first forward with L >= 1 levels (or more levels than
+ * before) adds per frame the inputs of levels 1..L-1, the weight sums of
+ * every level and the last level's output, 24 L + 16 B/px per frame (kept
+ * with the tape until it is destroyed).  Errors: DHR_ERR_INVALID (size
+ * outside 1..2^27 pixels, frames outside 1..1024), DHR_ERR_OOM. */
 dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_t frames, dhr_svgf_tape** out);
 void dhr_svgf_tape_destroy(dhr_svgf_tape* tape);
 

@@ -82,6 +82,8 @@ dhr_status check_svgf_params(const dhr_svgf_params* p) {
     DHR_CHECK_ARG(p->ao_spp >= 1 && p->ao_spp <= 255, "svgf: ao_spp %u not in 1..255", p->ao_spp);
     DHR_CHECK_ARG(p->alpha > 0.0f && p->alpha <= 1.0f, "svgf: alpha not in (0, 1]");
     DHR_CHECK_ARG(p->sigma_n >= 0.0f && p->sigma_z >= 0.0f && p->sigma_l >= 0.0f, "svgf: negative sigma");
+    DHR_CHECK_ARG(p->eps_z > 0.0f && p->eps_l > 0.0f && p->eps_z < INFINITY && p->eps_l < INFINITY,
+                  "svgf: eps_z and eps_l must be positive and finite");
     DHR_CHECK_ARG(p->shadow_light < DHR_MAX_LIGHTS, "svgf: shadow_light %u not in 0..%d", p->shadow_light,
                   DHR_MAX_LIGHTS - 1);
     DHR_CHECK_ARG(p->kernel_width == 0 || p->kernel_width == 3 || p->kernel_width == 5,

@@ -8,17 +8,17 @@
 // frames (the temporal recursion is not cut).
 //
 // Forward (dhr_svgf_seq_forward) records per frame the temporal output
-// (colour, variance), the moments, the history lengths and the input of
-// every a-trous level after the first.  Backward of one a-trous level is a
-// two-pass gather:
-//   pass A (per output pixel p): one pass over p's taps re-evaluates the
-//     level at p, forms the per-pixel factors of dL/dw_pq = a1 c_q - a2 +
-//     a3 w_pq v_q, the gradient through p's own colour and p's luminance
-//     scale and the sigma derivatives (as sums factored by a1, a2, a3), and
-//     stores the colour-free part of each tap's log-weight;
+// (colour, variance), the moments, the history lengths, the input of every
+// a-trous level after the first, every level's weight sums and the last
+// level's output.  Backward of one a-trous level is a two-pass gather:
+//   pass A (per output pixel p): with the level's weight sum, filtered
+//     colour and variance at p from the forward, dL/dw_pq = a1 c_q - a2 +
+//     a3 w_pq v_q is known tap by tap, so one pass over p's taps forms the
+//     gradient through p's own colour and p's luminance scale and the sigma
+//     derivatives;
 //   pass B (per input pixel q): gather from the 24 pixels whose footprint
-//     contains q (weights rebuilt from the stored log-weights and the
-//     colours) and from the 9 whose variance Gaussian does.
+//     contains q (weights rebuilt from the G-buffer and the records) and
+//     from the 9 whose variance Gaussian does.
 // The reprojection taps and history lengths depend only on G-buffers and
 // cameras and are constants of the adjoint.  Conventions as in the CPU
 // reference: sign(0) = 0, d max(0, x) = [x > 0], d sqrt(g)/dg = 0 for g < 1e-12,
@@ -36,83 +36,53 @@ __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f
 
 constexpr float kLn2 = 0.69314718055994531f;
 
-// Index of the tap at offset (i, j), i, j in -2..2, among the 24 taps
-// around the centre (row-major, centre left out).
-__device__ __forceinline__ int tap_index(int i, int j) {
-    const int t = (j + 2) * 5 + (i + 2);
-    return t < 12 ? t : t - 1;
-}
-
-// Sums over the taps q != p that the derivatives of the level need, both
-// channels at once (lane 0: AO, lane 1: shadow; packed binary32 pairs, each
-// lane rounded as the scalar operation).  With w = w_pq, delta = c_q - c_p,
-// a = |delta|, s = sgn(delta) and v = the variance of q:
-//   S0[f] = sum w f,  S1[f] = sum w f delta,  S2[f] = sum w^2 v f
-// for the factors f = 1, s, a, Z (= d w / d sigma_z / w) and L (= ln n.n_q).
-// Since dL/dw_pq = a1 c_q - a2 + a3 w_pq v_q with per-pixel a1, a2, a3
-// (known only once the level's totals are), every sum over the taps of
-// dL/dw_pq w_pq f_q is  (a1 c_p - a2) S0[f] + a1 S1[f] + a3 S2[f]:  one pass
-// over the taps is enough.  (S1[s] = S0[a].)  The differences are taken
-// from c_p so that the cancellation in a1 c_q - a2 happens at the scale of
-// the local colour differences, not of the colours.
 using u64 = unsigned long long;
 
-struct ChanSums {
-    u64 S0_1 = 0, S1_1 = 0, S2_1 = 0;
-    u64 S0_s = 0, S2_s = 0;
-    u64 S0_a = 0, S1_a = 0, S2_a = 0;
-    u64 S0_Z = 0, S1_Z = 0, S2_Z = 0;
-    u64 S0_L = 0, S1_L = 0, S2_L = 0;
-
-    template <bool kLum>
-    __device__ __forceinline__ void add(float w0, float w1, float2 d, float2 ad, u64 v, float Z, float L) {
-        const u64 w = pack2(w0, w1), delta = pack2(d.x, d.y);
-        const u64 wv = mul2(w, v), w2v = mul2(w, wv);
-        S0_1 = add2(S0_1, w);
-        S1_1 = fma2(w, delta, S1_1);
-        S2_1 = add2(S2_1, w2v);
-        if (kLum) {
-            const u64 ws = pack2(d.x == 0.f ? 0.f : copysignf(w0, d.x), d.y == 0.f ? 0.f : copysignf(w1, d.y));
-            const u64 wa = mul2(w, pack2(ad.x, ad.y));
-            S0_s = add2(S0_s, ws);
-            S2_s = fma2(ws, wv, S2_s);
-            S0_a = add2(S0_a, wa);
-            S1_a = fma2(wa, delta, S1_a);
-            S2_a = fma2(w2v, pack2(ad.x, ad.y), S2_a);
-        }
-        const u64 ZZ = pack2(Z, Z), LL = pack2(L, L);
-        const u64 wZ = mul2(w, ZZ), wL = mul2(w, LL);
-        S0_Z = add2(S0_Z, wZ);
-        S1_Z = fma2(wZ, delta, S1_Z);
-        S2_Z = fma2(w2v, ZZ, S2_Z);
-        S0_L = add2(S0_L, wL);
-        S1_L = fma2(wL, delta, S1_L);
-        S2_L = fma2(w2v, LL, S2_L);
-    }
-};
-
-__device__ __forceinline__ float lane(u64 v, int c) {
-    const float2 f = unpack2(v);
-    return c ? f.y : f.x;
-}
-
-// records of pass A, three planes of one float4 per pixel (rec[r * N + p],
+// records of pass A, four planes of one float4 per pixel (rec[r * N + p],
 // so that a warp's loads of one plane are contiguous), channel pairs adjacent:
 //   r0 = (a1[0], a1[1], -a2[0], -a2[1]), r1 = (a3[0], a3[1], il[0], il[1]),
-//   r2 = (Gg[0], Gg[1], self[0], self[1])
+//   r2 = (Gg[0], Gg[1], self[0], self[1]), r3 = (grad z, c[0], c[1])
 // (Gg already divided by the pixel's Gaussian normaliser; zero records on
-// background pixels).  E[t][p] (t = tap_index) is the part of log2 w_pq
-// that does not depend on the colour,
-//   log2(h_i h_j) + sigma_n log2(n_p . n_q) - log2(e) |z_p - z_q| / D,
-// so that pass B rebuilds w_pq = 2^(E - log2(e) il_p |c_p - c_q|) without
-// the G-buffers.  gs[p] += this level's (dL/d sigma_z, dL/d sigma_n,
+// background pixels, whose infinite depth gives every tap of theirs weight
+// 0 in pass B).  gs[p] += this level's (dL/d sigma_z, dL/d sigma_n,
 // dL/d sigma_l) terms of pixel p.
+//
+// dL/dw_pq = a1 c_q - a2 + a3 w_pq v_q with a1 = G_c / W, a2 = (G_c c +
+// 2 G_v v) / W, a3 = 2 G_v / W^2, where W, c and v are the level's weight
+// sum, filtered colour and filtered variance at p (the forward's records),
+// so one pass over the taps forms every derivative.  Both channels at once
+// as packed binary32 pairs (lane 0: AO, lane 1: shadow; each lane rounded
+// as the scalar operation).
+// The colour-free part of log2 w_pq for tap (i, j) of p (q = p + (i, j) step):
+//   log2(h_i h_j) + sigma_n log2(n_p . n_q) - log2(e) |z_p - z_q| / D,
+// D = sigma_z step |grad z_p . (i, j)| + eps_z; with the factors the sigma
+// derivatives reuse (u = |z_p - z_q| / D, a_off, rD = 1 / D, nd, log2 nd).
+struct TapLog {
+    float e, u, a_off, rD, nd, l2n;
+};
+
+template <int kNsq>
+__device__ __forceinline__ TapLog tap_log(const SvgfConsts& k, int step, int i, int j, float4 zp, float2 gz,
+                                          float4 zq) {
+    const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
+    TapLog t;
+    t.a_off = (float)step * fabsf(fmaf(gz.x, (float)i, gz.y * (float)j));
+    t.rD = rcp_approx(fmaf(k.sigma_z, t.a_off, k.eps_z));
+    t.u = fabsf(zp.x - zq.x) * t.rD;
+    t.nd = zp.y * zq.y + zp.z * zq.z + zp.w * zq.w;
+    t.l2n = lg2_approx(fmaxf(t.nd, 0.0f));
+    float en;
+    if constexpr (kNsq >= 0) en = (float)(1 << kNsq) * t.l2n;
+    else en = k.sigma_n == 0.0f ? 0.0f : k.sigma_n * t.l2n;
+    t.e = fmaf(-kLog2e, t.u, l5[i + 2] + l5[j + 2]) + en;
+    return t;
+}
+
 template <int kNsq, bool kLum, bool kCheck>
 __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const float4* g, const float4* x,
-                                            float2 Gc, float2 Gv, float4* rec, float* E, float4* gs, size_t N, int px,
-                                            int py, int p, float4 cp) {
+                                            float2 Gc, float2 Gv, float2 W, float4 out, float4* rec, float4* gs,
+                                            size_t N, int px, int py, int p, float4 cp) {
     using S = Store<DHR_FP32>;
-    const float l5[5] = {-4.f, -2.f, -1.41503750f, -2.f, -4.f};
     const float4 zp = S::g(g, p);
     float gv0 = 0.f, gv1 = 0.f, gw = 0.f;
 #pragma unroll
@@ -133,9 +103,13 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
     const float il1 = kLum ? 1.0f / (k.sigma_l * root1 + k.eps_l) : 0.f;
     const float nil0 = -kLog2e * il0, nil1 = -kLog2e * il1;
     const float2 gz = depth_grad<S>(g, k.W, k.H, px, py, zp.x);
-    const float kc = 0.375f * 0.375f;
-    float* Ep = E + p;
-    ChanSums c;
+    const float rW0 = 1.0f / W.x, rW1 = 1.0f / W.y;
+    const float a10 = Gc.x * rW0, a11 = Gc.y * rW1;
+    const float a20 = (Gc.x * out.x + 2.f * Gv.x * out.z) * rW0, a21 = (Gc.y * out.y + 2.f * Gv.y * out.w) * rW1;
+    const float a30 = 2.f * Gv.x * rW0 * rW0, a31 = 2.f * Gv.y * rW1 * rW1;
+    const u64 A1 = pack2(a10, a11), NA2 = pack2(-a20, -a21), A3 = pack2(a30, a31);
+    u64 self_s = 0, gil_s = 0;   // sum dL/dw w sgn(c_q - c_p), sum dL/dw w |c_q - c_p|
+    float gsz = 0.f, gsn = 0.f;
 #pragma unroll
     for (int j = -2; j <= 2; ++j)
 #pragma unroll
@@ -146,50 +120,32 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
             const int q = qy * k.W + qx;
             const float4 cq = __ldg(x + q);
             if (!fg_var(cq.z)) continue;
-            const float4 zq = S::g(g, q);
-            const float a_off = (float)step * fabsf(fmaf(gz.x, (float)i, gz.y * (float)j));
-            const float rD = rcp_approx(fmaf(k.sigma_z, a_off, k.eps_z));
-            const float dz = fabsf(zp.x - zq.x);
-            const float nd = zp.y * zq.y + zp.z * zq.z + zp.w * zq.w;
-            const float l2n = lg2_approx(fmaxf(nd, 0.0f));
-            float en;
-            if constexpr (kNsq >= 0) en = (float)(1 << kNsq) * l2n;
-            else en = k.sigma_n == 0.0f ? 0.0f : k.sigma_n * l2n;
-            const float e = fmaf(-kLog2e, dz * rD, l5[i + 2] + l5[j + 2]) + en;
-            Ep[(size_t)tap_index(i, j) * N] = e;
-            const float Z = dz * a_off * rD * rD;
-            const float L = nd > 0.f ? l2n * kLn2 : 0.f;
-            const float2 d = make_float2(cq.x - cp.x, cq.y - cp.y), ad = make_float2(fabsf(d.x), fabsf(d.y));
-            c.add<kLum>(ex2_approx(fmaf(nil0, ad.x, e)), ex2_approx(fmaf(nil1, ad.y, e)), d, ad, pack2(cq.z, cq.w), Z,
-                        L);
+            const TapLog t = tap_log<kNsq>(k, step, i, j, zp, gz, S::g(g, q));
+            const float d0 = cq.x - cp.x, d1 = cq.y - cp.y;
+            const u64 w = pack2(ex2_approx(fmaf(nil0, fabsf(d0), t.e)), ex2_approx(fmaf(nil1, fabsf(d1), t.e)));
+            const u64 Gw = fma2(mul2(A3, w), pack2(cq.z, cq.w), fma2(A1, pack2(cq.x, cq.y), NA2));
+            const u64 gww = mul2(Gw, w);
+            if (kLum) {
+                self_s = fma2(gww, pack2(sgnf(d0), sgnf(d1)), self_s);
+                gil_s = fma2(gww, pack2(fabsf(d0), fabsf(d1)), gil_s);
+            }
+            const float2 gf = unpack2(gww);
+            const float gsum = gf.x + gf.y;
+            // d w / d sigma_z = w |dz| a_off / D^2;  d w / d sigma_n = w ln(n . n_q)
+            gsz = fmaf(gsum, t.u * t.a_off * t.rD, gsz);
+            if (t.nd > 0.f) gsn = fmaf(gsum, t.l2n, gsn);
         }
-    const float W0 = kc + lane(c.S0_1, 0), W1 = kc + lane(c.S0_1, 1);
-    const float rW0 = 1.0f / W0, rW1 = 1.0f / W1;
-    const float v0 = (kc * kc * cp.z + lane(c.S2_1, 0)) * rW0 * rW0, v1 = (kc * kc * cp.w + lane(c.S2_1, 1)) * rW1 * rW1;
-    // filtered colour minus the centre's: (sum w c_q + kc c_p) / W - c_p
-    const float dc0 = lane(c.S1_1, 0) * rW0, dc1 = lane(c.S1_1, 1) * rW1;
-    const float a10 = Gc.x * rW0, a11 = Gc.y * rW1;
-    const float a20 = (Gc.x * (cp.x + dc0) + 2.f * Gv.x * v0) * rW0, a21 = (Gc.y * (cp.y + dc1) + 2.f * Gv.y * v1) * rW1;
-    const float a30 = 2.f * Gv.x * rW0 * rW0, a31 = 2.f * Gv.y * rW1 * rW1;
-    // a1 c_p - a2, formed without the colours' own scale
-    const float k00 = -(Gc.x * dc0 + 2.f * Gv.x * v0) * rW0, k01 = -(Gc.y * dc1 + 2.f * Gv.y * v1) * rW1;
     float4 acc = gs[p];
-    acc.x += k00 * lane(c.S0_Z, 0) + a10 * lane(c.S1_Z, 0) + a30 * lane(c.S2_Z, 0) + k01 * lane(c.S0_Z, 1) +
-             a11 * lane(c.S1_Z, 1) + a31 * lane(c.S2_Z, 1);
-    acc.y += k00 * lane(c.S0_L, 0) + a10 * lane(c.S1_L, 0) + a30 * lane(c.S2_L, 0) + k01 * lane(c.S0_L, 1) +
-             a11 * lane(c.S1_L, 1) + a31 * lane(c.S2_L, 1);
+    acc.x += gsz;
+    acc.y += gsn * kLn2;
     float Gg0 = 0.f, Gg1 = 0.f, self0 = 0.f, self1 = 0.f;
     if (kLum) {
-        // sum dL/dw w sgn(c_q - c_p) and sum dL/dw w |c_q - c_p|
-        const float Ts0 = k00 * lane(c.S0_s, 0) + a10 * lane(c.S0_a, 0) + a30 * lane(c.S2_s, 0);
-        const float Ts1 = k01 * lane(c.S0_s, 1) + a11 * lane(c.S0_a, 1) + a31 * lane(c.S2_s, 1);
-        const float Ta0 = k00 * lane(c.S0_a, 0) + a10 * lane(c.S1_a, 0) + a30 * lane(c.S2_a, 0);
-        const float Ta1 = k01 * lane(c.S0_a, 1) + a11 * lane(c.S1_a, 1) + a31 * lane(c.S2_a, 1);
+        const float2 ss = unpack2(self_s), ga = unpack2(gil_s);
         // d w / d c_p = -w il sgn(c_p - c_q) = w il sgn(c_q - c_p)
-        self0 = il0 * Ts0;
-        self1 = il1 * Ts1;
+        self0 = il0 * ss.x;
+        self1 = il1 * ss.y;
         // d w / d il = -w |c_p - c_q|
-        const float Gil0 = -Ta0, Gil1 = -Ta1;
+        const float Gil0 = -ga.x, Gil1 = -ga.y;
         acc.z += Gil0 * (-il0 * il0 * root0) + Gil1 * (-il1 * il1 * root1);
         // d sqrt(g)/dg is taken as 0 below g = 1e-12 (it grows without bound
         // toward g = 0, where the weight is already insensitive)
@@ -200,6 +156,7 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
     rec[p] = make_float4(a10, a11, -a20, -a21);
     rec[N + p] = make_float4(a30, a31, il0, il1);
     rec[2 * N + p] = make_float4(Gg0, Gg1, self0, self1);
+    rec[3 * N + p] = make_float4(gz.x, gz.y, cp.x, cp.y);
 }
 
 // 32x8 pixel tiles; a tile whose taps (reach 2 step) and 3x3 variance
@@ -211,12 +168,15 @@ __device__ __forceinline__ bool tile_interior(const SvgfConsts& k, int step, int
 
 // pass B: gradient with respect to the level's input colour and variance.
 // The taps are evaluated without branches (a tap outside the image reads the
-// centre's own records, and a select drops every tap outside the image or
-// on background) so that the loads of all taps can be issued together.
+// centre's own records, and a select drops it; a background tap has zero
+// records and weight 0) so that the loads of all taps can be issued
+// together.  The colour-free log-weight of each tap is recomputed from the
+// G-buffer and the tapping pixel's recorded depth gradient.
 // Returns (dL/d c_q, dL/d v_q) per channel.
-template <bool kCheck>
-__device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, const float4* x, const float4* rec,
-                                              const float* E, size_t N, int qx, int qy, int q, float4 cq) {
+template <int kNsq, bool kCheck>
+__device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, const float4* g, const float4* rec,
+                                              size_t N, int qx, int qy, int q, float4 cq) {
+    using S = Store<DHR_FP32>;
     const float kc = 0.375f * 0.375f;
     const float4 r0 = rec[q], r1 = rec[N + q], r2 = rec[2 * N + q];
     // own colour through the weights of q's own footprint, and the centre tap
@@ -233,19 +193,9 @@ __device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, con
             const float4 rp = rec[2 * N + py * k.W + px];
             gvs = fma2(pack2(rp.x, rp.y), pack2(kk, kk), gvs);
         }
+    const float4 zq = S::g(g, q);
     const u64 cqc = pack2(cq.x, cq.y), cqv = pack2(cq.z, cq.w), half = pack2(0.5f, 0.5f);
     const u64 ncq = pack2(-cq.x, -cq.y);
-    // the log-weights stream from memory once each: issue all 24 loads first
-    float ev[24];
-#pragma unroll
-    for (int j = -2; j <= 2; ++j)
-#pragma unroll
-        for (int i = -2; i <= 2; ++i) {
-            if (!i && !j) continue;
-            const int px = qx - i * step, py = qy - j * step;
-            const bool in = !kCheck || (px >= 0 && py >= 0 && px < k.W && py < k.H);
-            ev[tap_index(i, j)] = __ldg(E + (size_t)tap_index(i, j) * N + (in ? py * k.W + px : q));
-        }
     // footprints of the 24 pixels p = q - (i, j) step that tap q at (i, j)
 #pragma unroll
     for (int j = -2; j <= 2; ++j)
@@ -255,13 +205,11 @@ __device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, con
             const int px = qx - i * step, py = qy - j * step;
             const bool in = !kCheck || (px >= 0 && py >= 0 && px < k.W && py < k.H);
             const int p = in ? py * k.W + px : q;
-            const float4 cp = __ldg(x + p);
-            const float4 p0 = rec[p], p1 = rec[N + p];
-            const float e = ev[tap_index(i, j)];
-            const bool use = in && fg_var(cp.z);
-            const float2 d = unpack2(add2(pack2(cp.x, cp.y), ncq));   // c_p - c_q
-            const float w0 = ex2_approx(fmaf(-kLog2e * p1.z, fabsf(d.x), e));
-            const float w1 = ex2_approx(fmaf(-kLog2e * p1.w, fabsf(d.y), e));
+            const float4 p0 = rec[p], p1 = rec[N + p], p3 = rec[3 * N + p];
+            const TapLog t = tap_log<kNsq>(k, step, i, j, S::g(g, p), make_float2(p3.x, p3.y), zq);
+            const float2 d = unpack2(add2(pack2(p3.z, p3.w), ncq));   // c_p - c_q
+            const float w0 = ex2_approx(fmaf(-kLog2e * p1.z, fabsf(d.x), t.e));
+            const float w1 = ex2_approx(fmaf(-kLog2e * p1.w, fabsf(d.y), t.e));
             const u64 w = pack2(w0, w1);
             const u64 a3w = mul2(pack2(p1.x, p1.y), w);
             // dL/dw_pq = a1 c_q - a2 + a3 w v_q
@@ -269,8 +217,8 @@ __device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, con
             const u64 sil = pack2(p1.z * sgnf(d.x), p1.w * sgnf(d.y));
             const float2 dc = unpack2(fma2(mul2(Gw, w), sil, mul2(pack2(p0.x, p0.y), w)));
             const float2 dv = unpack2(mul2(mul2(a3w, w), half));
-            gcs = add2(gcs, pack2(use ? dc.x : 0.f, use ? dc.y : 0.f));
-            gvs = add2(gvs, pack2(use ? dv.x : 0.f, use ? dv.y : 0.f));
+            gcs = add2(gcs, pack2(in ? dc.x : 0.f, in ? dc.y : 0.f));
+            gvs = add2(gvs, pack2(in ? dv.x : 0.f, in ? dv.y : 0.f));
         }
     const float2 gc = unpack2(gcs), gv = unpack2(gvs);
     return make_float4(gc.x, gc.y, gv.x, gv.y);
@@ -305,9 +253,11 @@ __device__ __forceinline__ float4 upstream(const Upstream& up, size_t N, int q) 
     return G;
 }
 
+// wsum: the level's weight sums [N]; xout: its filtered colour and variance [N]
 template <int kNsq, bool kLum>
 __global__ void __launch_bounds__(kThreadsA, 4) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
-                                                             Upstream up, float4* rec, float* E, float4* gs) {
+                                                             const float2* wsum, const float4* xout, Upstream up,
+                                                             float4* rec, float4* gs) {
     const int px = blockIdx.x * kBX + threadIdx.x, py = blockIdx.y * kBY + threadIdx.y;
     if (px >= k.W || py >= k.H) return;
     const int p = py * k.W + px;
@@ -317,21 +267,25 @@ __global__ void __launch_bounds__(kThreadsA, 4) atrous_bwd_a(SvgfConsts k, int s
         rec[p] = make_float4(0.f, 0.f, 0.f, 0.f);
         rec[N + p] = make_float4(0.f, 0.f, 0.f, 0.f);
         rec[2 * N + p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rec[3 * N + p] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     const float4 G = upstream(up, N, p);
+    const float2 W = wsum[p];
+    const float4 o = __ldg(xout + p);
     if (tile_interior(k, step, blockIdx.x, blockIdx.y))
-        bwd_a_pixel<kNsq, kLum, false>(k, step, g, x, make_float2(G.x, G.y), make_float2(G.z, G.w), rec, E, gs, N,
+        bwd_a_pixel<kNsq, kLum, false>(k, step, g, x, make_float2(G.x, G.y), make_float2(G.z, G.w), W, o, rec, gs, N,
                                        px, py, p, cp);
     else
-        bwd_a_pixel<kNsq, kLum, true>(k, step, g, x, make_float2(G.x, G.y), make_float2(G.z, G.w), rec, E, gs, N,
+        bwd_a_pixel<kNsq, kLum, true>(k, step, g, x, make_float2(G.x, G.y), make_float2(G.z, G.w), W, o, rec, gs, N,
                                       px, py, p, cp);
 }
 
-// Pass B runs its tiles in the reverse of pass A's order: the log-weights and
-// records pass A wrote last are the ones still in L2 when pass B starts.
-__global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step, const float4* x, const float4* rec,
-                                                          const float* E, float2* gc_in, float2* gv_in) {
+// Pass B runs its tiles in the reverse of pass A's order: the records pass
+// A wrote last are the ones still in L2 when pass B starts.
+template <int kNsq>
+__global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step, const float4* g, const float4* x,
+                                                          const float4* rec, float2* gc_in, float2* gv_in) {
     const int bx = gridDim.x - 1 - blockIdx.x, by = gridDim.y - 1 - blockIdx.y;
     const int qx = bx * kBX + threadIdx.x, qy = by * kBY + threadIdx.y;
     if (qx >= k.W || qy >= k.H) return;
@@ -343,8 +297,8 @@ __global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step
         return;
     }
     const size_t N = (size_t)k.W * k.H;
-    const float4 G = tile_interior(k, step, bx, by) ? bwd_b_pixel<false>(k, step, x, rec, E, N, qx, qy, q, cq)
-                                                    : bwd_b_pixel<true>(k, step, x, rec, E, N, qx, qy, q, cq);
+    const float4 G = tile_interior(k, step, bx, by) ? bwd_b_pixel<kNsq, false>(k, step, g, rec, N, qx, qy, q, cq)
+                                                    : bwd_b_pixel<kNsq, true>(k, step, g, rec, N, qx, qy, q, cq);
     gc_in[q] = make_float2(G.x, G.y);
     gv_in[q] = make_float2(G.z, G.w);
 }
@@ -586,14 +540,16 @@ struct dhr_svgf_tape {
     uint8_t* hist = nullptr;   // [F][N] history lengths
     float2* col = nullptr;     // [N] colour history (forward)
     float4* lev[2] = {nullptr, nullptr};
-    float4* lvs = nullptr;     // [F][levels - 1][N] inputs of levels 1.. (recorded by the forward)
-    int lvs_levels = 0;
+    // recorded by the forward, allocated for `rec_levels` levels on first use:
+    float4* lvs = nullptr;     // [F][levels - 1][N] inputs of levels 1..
+    float2* wsum = nullptr;    // [F][levels][N] weight sums of every level
+    float4* last = nullptr;    // [F][N] filtered colour and variance of the last level
+    int rec_levels = 0;
     float2* gcol[2] = {nullptr, nullptr};
     float4* gmom[2] = {nullptr, nullptr};
     float2* gc = nullptr;      // [N] dL/d colour at the input of the level just processed
     float2* gv = nullptr;      // [N] dL/d variance, same
-    float4* rec = nullptr;     // [3][N] pass-A records
-    float* E = nullptr;        // [24][N] colour-free part of log2 w per tap
+    float4* rec = nullptr;     // [4][N] pass-A records
     float4* gs = nullptr;      // [N] per-pixel (dL/d sigma_z, dL/d sigma_n, dL/d sigma_l, -)
     float* partial = nullptr;  // [kPixReduceBlocks][3]
     double* acc = nullptr;     // [3]
@@ -619,9 +575,10 @@ static void tape_free(dhr_svgf_tape* t) {
     cudaFree(t->gc);
     cudaFree(t->gv);
     cudaFree(t->rec);
-    cudaFree(t->E);
     cudaFree(t->gs);
     cudaFree(t->lvs);
+    cudaFree(t->wsum);
+    cudaFree(t->last);
     cudaFree(t->partial);
     cudaFree(t->acc);
     delete t;
@@ -652,8 +609,7 @@ extern "C" dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_
     }
     if (!e) e = cudaMalloc((void**)&t->gc, n * 8);
     if (!e) e = cudaMalloc((void**)&t->gv, n * 8);
-    if (!e) e = cudaMalloc((void**)&t->rec, n * 48);
-    if (!e) e = cudaMalloc((void**)&t->E, n * 24 * sizeof(float));
+    if (!e) e = cudaMalloc((void**)&t->rec, n * 64);
     if (!e) e = cudaMalloc((void**)&t->gs, n * 16);
     if (!e) e = cudaMalloc((void**)&t->partial, (size_t)kPixReduceBlocks * 3 * sizeof(float));
     if (!e) e = cudaMalloc((void**)&t->acc, 3 * sizeof(double));
@@ -695,17 +651,24 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
     const dim3 blk(32, 8), grid((t->W + 31) / 32, (t->H + 7) / 8);
     const int L = (int)params->levels;
     DHR_CHECK_ARG(L <= kMaxLevels, "svgf_seq_forward: levels %d > %d", L, kMaxLevels);
-    if (L > 1 && t->lvs_levels < L - 1) {   // inputs of levels 1..L-1 of every frame, allocated on first use
+    if (L > t->rec_levels) {   // level records of every frame, allocated on first use
         cudaFree(t->lvs);
+        cudaFree(t->wsum);
+        cudaFree(t->last);
         t->lvs = nullptr;
-        t->lvs_levels = 0;
-        const cudaError_t e = cudaMalloc((void**)&t->lvs, (size_t)t->F * (L - 1) * N * 16);
+        t->wsum = nullptr;
+        t->last = nullptr;
+        t->rec_levels = 0;
+        cudaError_t e = cudaSuccess;
+        if (L > 1) e = cudaMalloc((void**)&t->lvs, (size_t)t->F * (L - 1) * N * 16);
+        if (!e) e = cudaMalloc((void**)&t->wsum, (size_t)t->F * L * N * 8);
+        if (!e) e = cudaMalloc((void**)&t->last, (size_t)t->F * N * 16);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
                              "svgf_seq_forward: level records: %s", cudaGetErrorString(e));
         }
-        t->lvs_levels = L - 1;
+        t->rec_levels = L;
     }
     t->frames_recorded = 0;
     for (int f = 0; f < t->F; ++f) {
@@ -729,7 +692,8 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
         for (int l = 0; l < L; ++l) {
             float4* o = l + 1 < L ? t->lvs + ((size_t)f * (L - 1) + l) * N : t->lev[l & 1];
             const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-            DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, 2, st, k, 1 << l, gc, in, o, t->col, ao, sh));
+            const AtrousRec rec{t->wsum + ((size_t)f * L + l) * N, t->last + (size_t)f * N};
+            DHR_TRY(launch_atrous_recorded(mode, nsq, st, k, 1 << l, gc, in, o, t->col, ao, sh, rec));
             if (L == 1) {
                 passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, o, t->col, ao, sh);
                 DHR_CUDA_TRY(cudaGetLastError());
@@ -775,16 +739,21 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
         Upstream up{g_out + (size_t)f * 2 * N, nullptr, nullptr, L <= 1 ? t->gcol[nx] : nullptr};
         for (int l = L - 1; l >= 0; --l) {
             const float4* xin = l == 0 ? illum : t->lvs + ((size_t)f * (L - 1) + (l - 1)) * N;
+            const float4* xout = l + 1 < L ? t->lvs + ((size_t)f * (L - 1) + l) * N : t->last + (size_t)f * N;
+            const float2* ws = t->wsum + ((size_t)f * L + l) * N;
             if (nsq == 7 && k.wl_in_atrous)
-                atrous_bwd_a<7, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
+                atrous_bwd_a<7, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
             else if (nsq == 7)
-                atrous_bwd_a<7, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
+                atrous_bwd_a<7, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
             else if (k.wl_in_atrous)
-                atrous_bwd_a<-1, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
+                atrous_bwd_a<-1, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
             else
-                atrous_bwd_a<-1, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, up, t->rec, t->E, t->gs);
+                atrous_bwd_a<-1, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
             DHR_CUDA_TRY(cudaGetLastError());
-            atrous_bwd_b<<<grid, blk, 0, st>>>(k, 1 << l, xin, t->rec, t->E, t->gc, t->gv);
+            if (nsq == 7)
+                atrous_bwd_b<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
+            else
+                atrous_bwd_b<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
             DHR_CUDA_TRY(cudaGetLastError());
             // level l - 1's output gradient (plus, for level 0's output, the
             // next frame's colour-history gradient)

@@ -633,15 +633,29 @@ __device__ __forceinline__ void var_gauss(const float4 (&v)[3][3], float& gv0, f
         }
 }
 
-template <dhr_precision P, int kMode>
+// Records of one level for the differentiable form (both null outside it):
+// the weight sums (sum w per channel, centre included) and, for the last
+// level, its filtered colour and variance, which no later level keeps.
+struct AtrousRec {
+    float2* wsum;
+    float4* last;
+};
+
+template <dhr_precision P, int kMode, bool kRec = false>
 __device__ __forceinline__ void atrous_store(const AtrousSums& a, int p, float4* out,
-                                             typename Store<P>::Col* col_hist, float* ao_out, float* sh_out) {
+                                             typename Store<P>::Col* col_hist, float* ao_out, float* sh_out,
+                                             AtrousRec rec = AtrousRec{nullptr, nullptr}) {
     // (sum w c) / (sum w) correctly rounded: a constant neighbourhood stays
     // exactly constant; the variance (sum w^2 v) / (sum w)^2 needs no such care
     const float c0 = a.sc0 / a.sw0, c1 = a.sc1 / a.sw1;
+    if (kRec) rec.wsum[p] = make_float2(a.sw0, a.sw1);
     if (kMode == 2) {
         ao_out[p] = c0;
         sh_out[p] = c1;
+        if (kRec) {
+            const float r0 = rcp_approx(a.sw0), r1 = rcp_approx(a.sw1);
+            rec.last[p] = make_float4(c0, c1, a.sv0 * r0 * r0, a.sv1 * r1 * r1);
+        }
     } else {
         const float r0 = rcp_approx(a.sw0), r1 = rcp_approx(a.sw1);
         out[p] = make_float4(c0, c1, a.sv0 * r0 * r0, a.sv1 * r1 * r1);
@@ -666,10 +680,11 @@ __device__ __forceinline__ void atrous_background(int p, float4* out, typename S
 // planes only.  kNsq >= 0: sigma_n is 2^kNsq.  kR: footprint radius (2:
 // 5x5, 1: 3x3).  Every thread of the block must call it (block barriers at
 // step 1).
-template <dhr_precision P, int kMode, int kNsq, int kR = 2>
+template <dhr_precision P, int kMode, int kNsq, int kR = 2, bool kRec = false>
 __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t, const typename Store<P>::G* g,
                                             const float4* in, float4* out, typename Store<P>::Col* col_hist,
-                                            float* ao_out, float* sh_out, AtrousSmem& sm) {
+                                            float* ao_out, float* sh_out, AtrousSmem& sm,
+                                            AtrousRec rec = AtrousRec{nullptr, nullptr}) {
     using S = Store<P>;
     const int ntx = atrous_tiles_x(k.W);
     const int bx0 = (t % ntx) * kAtW, by0 = (t / ntx) * kAtH;
@@ -707,7 +722,7 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
                 const float2 gz = grad_from(zn.x, sm.g[ty][tx + 1].x, sm.g[ty][tx - 1].x, sm.g[ty + 1][tx].x,
                                             sm.g[ty - 1][tx].x);
                 const AtrousSums a = atrous_sums<kNsq, kR>(k, 1, cp, zn, gv0, gv1, gw, gz, TapsSmem{sm, tx, ty});
-                atrous_store<P, kMode>(a, p, out, col_hist, ao_out, sh_out);
+                atrous_store<P, kMode, kRec>(a, p, out, col_hist, ao_out, sh_out, rec);
             }
         }
         __syncthreads();    // the staging area is reused by the block's next tile
@@ -744,16 +759,16 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
     else
         a = atrous_sums<kNsq, kR>(k, step, cp, zn, gv0, gv1, gw, gz,
                                   TapsGlobal<S, true>{g, in, k.W, k.H, x, y, step});
-    atrous_store<P, kMode>(a, p, out, col_hist, ao_out, sh_out);
+    atrous_store<P, kMode, kRec>(a, p, out, col_hist, ao_out, sh_out, rec);
 }
 
-template <dhr_precision P, int kMode, int kNsq, int kR>
+template <dhr_precision P, int kMode, int kNsq, int kR, bool kRec = false>
 __global__ void __launch_bounds__(256, 4) atrous_kernel(SvgfConsts k, int step, const typename Store<P>::G* g,
                                                      const float4* in, float4* out,
                                                      typename Store<P>::Col* col_hist, float* ao_out,
-                                                     float* sh_out) {
+                                                     float* sh_out, AtrousRec rec) {
     __shared__ AtrousSmem sm;
-    atrous_tile<P, kMode, kNsq, kR>(k, step, blockIdx.x, g, in, out, col_hist, ao_out, sh_out, sm);
+    atrous_tile<P, kMode, kNsq, kR, kRec>(k, step, blockIdx.x, g, in, out, col_hist, ao_out, sh_out, sm, rec);
 }
 
 // levels == 0: the temporal colour is the output and the colour history
@@ -796,10 +811,11 @@ inline void launch_atrous_mode(int nsq, cudaStream_t st, const SvgfConsts& k, in
                                const typename Store<P>::G* g, const float4* in, float4* out,
                                typename Store<P>::Col* col, float* ao_out, float* sh_out) {
     const dim3 grid(atrous_tiles(k.W, k.H)), blk(kAtW, kAtH);
+    const AtrousRec none{nullptr, nullptr};
     if (nsq == 7)
-        atrous_kernel<P, kMode, 7, kR><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
+        atrous_kernel<P, kMode, 7, kR><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out, none);
     else
-        atrous_kernel<P, kMode, -1, kR><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out);
+        atrous_kernel<P, kMode, -1, kR><<<grid, blk, 0, st>>>(k, step, g, in, out, col, ao_out, sh_out, none);
 }
 
 template <dhr_precision P, int kR>
@@ -824,6 +840,30 @@ inline dhr_status launch_atrous(int mode, int nsq, int R, cudaStream_t st, const
         launch_atrous_r<P, 1>(mode, nsq, st, k, step, g, in, out, col, ao_out, sh_out);
     else
         launch_atrous_r<P, 2>(mode, nsq, st, k, step, g, in, out, col, ao_out, sh_out);
+    DHR_CUDA_TRY(cudaGetLastError());
+    return DHR_OK;
+}
+
+// The differentiable form's forward level (binary32, 5x5): as launch_atrous,
+// plus the level's records `rec` (wsum always; last on mode 2).
+inline dhr_status launch_atrous_recorded(int mode, int nsq, cudaStream_t st, const SvgfConsts& k, int step,
+                                         const float4* g, const float4* in, float4* out, float2* col, float* ao_out,
+                                         float* sh_out, AtrousRec rec) {
+    const dim3 grid(atrous_tiles(k.W, k.H)), blk(kAtW, kAtH);
+    constexpr dhr_precision P = DHR_FP32;
+#define DHR_ATROUS_REC(M, NSQ, OUT, COL, AO, SH) \
+    atrous_kernel<P, M, NSQ, 2, true><<<grid, blk, 0, st>>>(k, step, g, in, OUT, COL, AO, SH, rec)
+    if (mode == 2) {
+        if (nsq == 7) DHR_ATROUS_REC(2, 7, nullptr, nullptr, ao_out, sh_out);
+        else DHR_ATROUS_REC(2, -1, nullptr, nullptr, ao_out, sh_out);
+    } else if (mode == 1) {
+        if (nsq == 7) DHR_ATROUS_REC(1, 7, out, col, nullptr, nullptr);
+        else DHR_ATROUS_REC(1, -1, out, col, nullptr, nullptr);
+    } else {
+        if (nsq == 7) DHR_ATROUS_REC(0, 7, out, nullptr, nullptr, nullptr);
+        else DHR_ATROUS_REC(0, -1, out, nullptr, nullptr, nullptr);
+    }
+#undef DHR_ATROUS_REC
     DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
 }
