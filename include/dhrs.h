@@ -364,6 +364,29 @@ dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur,
                                 float* ao_out, float* shadow_out, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Debug build (libdhrs_debug.so, compiled with DHR_DEBUG)                 */
+/* ---------------------------------------------------------------------- */
+/* In the debug build every gather index of the a-trous taps and variance
+ * Gaussian, the depth slope, the reprojection taps, the short-history
+ * estimate, BVH node and triangle fetches, the rasterised tile lists and
+ * the adjoint's gathers and scatters is checked against its buffer; an
+ * index outside the buffer is recorded and replaced by 0 (the kernel runs
+ * on, nothing is read or written outside a buffer).
+ * dhr_debug_status waits for the device (cudaDeviceSynchronize), returns
+ * the first recorded event since the last call (0: none) and clears the
+ * record: bit 63 set, bits 40..47 the site (1 a-trous tap, 2 a-trous
+ * variance, 3 depth slope, 4 reprojection, 5 short-history estimate, 6 BVH
+ * node, 7 triangle, 8 tile list, 10 adjoint, 11 self test), bits 0..39 the
+ * offending index.  debug_build: 1 in the debug build (first_error is
+ * always 0 in the release build).  Errors: DHR_ERR_INVALID (null),
+ * DHR_ERR_CUDA. */
+dhr_status dhr_debug_status(uint64_t* first_error, int32_t* debug_build);
+/* Debug build only: one checked read at index 5 of a one-element buffer on
+ * `stream` (synchronised), which the check records (site 11) and redirects.
+ * Errors: DHR_ERR_STATE in the release build, DHR_ERR_CUDA. */
+dhr_status dhr_debug_selftest(void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Differentiable form of the modified SVGF (no counterpart in the paper,  */
 /* which only runs the filter forward; this is its adjoint, Section 3.3)   */
 /* ---------------------------------------------------------------------- */

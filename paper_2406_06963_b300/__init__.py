@@ -16,7 +16,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdhrs.so")
+# DHRS_DEBUG=1 in the environment selects the bounds-checked debug build
+LIB_PATH = os.path.join(HERE, "libdhrs_debug.so" if os.environ.get("DHRS_DEBUG") == "1" else "libdhrs.so")
 
 DHR_FP32, DHR_FP16 = 0, 1
 BACKGROUND = 0xFFFFFFFF
@@ -85,6 +86,8 @@ _SIGNATURES = {
     "dhr_cast_rays": ([_P, _P, _P, _P, _P, C.c_int32, C.c_int64, _P, _P, _P], C.c_int),
     "dhr_trace_stats": ([_P, _P, _P, _P, _P], C.c_int),
     "dhr_l2_read_bandwidth": ([C.c_int64, C.c_int32, _P, _P], C.c_int),
+    "dhr_debug_status": ([_P, _P], C.c_int),
+    "dhr_debug_selftest": ([_P], C.c_int),
     "dhr_trace_timed": ([_P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_gbuffer_convert": ([_P, _P, _P], C.c_int),
     "dhr_sample_directions": ([_P, _P, C.c_int64, C.c_uint32, C.c_uint32, C.c_uint32, _P, _P,
@@ -407,6 +410,19 @@ def l2_read_bandwidth(nbytes: int = 48 << 20, passes: int = 40, stream=None) -> 
     out = C.c_float()
     _check(lib().dhr_l2_read_bandwidth(int(nbytes), int(passes), C.byref(out), _stream(stream)))
     return float(out.value)
+
+
+def debug_status():
+    """(first recorded out-of-bounds event or 0, is_debug_build); the event
+    word: bit 63 set, bits 40..47 the site, bits 0..39 the index."""
+    err, dbg = C.c_uint64(), C.c_int32()
+    _check(lib().dhr_debug_status(C.byref(err), C.byref(dbg)))
+    return int(err.value), bool(dbg.value)
+
+
+def debug_selftest(stream=None):
+    """Debug build: one checked out-of-range read that the check records."""
+    _check(lib().dhr_debug_selftest(_stream(stream)))
 
 
 def cast_rays(scene: Scene, origins, dirs, tmin, tmax, any_hit=False, stream=None):

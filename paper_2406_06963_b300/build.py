@@ -1,6 +1,7 @@
-"""Build libdhrs.so (all CUDA sources, sm_103a) in-tree with nvcc.
+"""Build libdhrs.so (all CUDA sources, sm_103a) in-tree with nvcc, and the
+bounds-checked debug build libdhrs_debug.so (DHR_DEBUG).
 
-    python -m paper_2406_06963_b300.build [--force]
+    python -m paper_2406_06963_b300.build [--force] [--debug | --all]
 """
 from __future__ import annotations
 
@@ -13,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdhrs.so")
+LIB_DEBUG = os.path.join(HERE, "libdhrs_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -28,17 +30,25 @@ def _inputs():
     return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "dhrs.h"), __file__]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Build the release library (or, with debug, the DHR_DEBUG one) unless it
+    is newer than every source."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(f) <= t for f in _inputs()):
-            return LIB
-    cmd = ["nvcc", *ARCH, *FLAGS, *sources(), "-o", LIB]
+            return lib
+    cmd = ["nvcc", *ARCH, *FLAGS, *(["-DDHR_DEBUG"] if debug else []), *sources(), "-o", lib]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.run(cmd, check=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    force, verbose = "--force" in sys.argv, "-v" in sys.argv
+    if "--all" in sys.argv:
+        print(build(force, verbose))
+        print(build(force, verbose, debug=True))
+    else:
+        print(build(force, verbose, debug="--debug" in sys.argv))

@@ -21,6 +21,18 @@ dhr_status set_error(dhr_status s, const char* fmt, ...) {
 
 void clear_error() { g_error.clear(); }
 
+static std::vector<DebugReader>& debug_readers() {
+    static std::vector<DebugReader> v;
+    return v;
+}
+void debug_register(DebugReader f) { debug_readers().push_back(f); }
+
+#ifdef DHR_DEBUG
+// reads element 5 of a one-element buffer through the bounds check, which
+// records the event and reads element 0 instead
+__global__ void debug_selftest_kernel(const int* buf, int* out) { out[0] = buf[dbg_index(5, 1, kSiteSelfTest)]; }
+#endif
+
 dhr_status svgf_create(int32_t w, int32_t h, dhr_precision prec, dhr_svgf_state** out);
 void svgf_free(dhr_svgf_state* s);
 dhr_status svgf_run(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev, const dhr_camera* cam,
@@ -50,6 +62,45 @@ static dhr_status check_gbuffer(const dhr_gbuffer* g, int w, int h) {
 using namespace dhr;
 
 extern "C" const char* dhr_last_error(void) { return g_error.c_str(); }
+
+// ------------------------------------------------------------ debug build
+extern "C" dhr_status dhr_debug_status(uint64_t* first_error, int32_t* debug_build) {
+    clear_error();
+    DHR_CHECK_ARG(first_error && debug_build, "debug_status: null pointer");
+    *first_error = 0;
+#ifdef DHR_DEBUG
+    *debug_build = 1;
+    DHR_CUDA_TRY(cudaDeviceSynchronize());   // the kernels whose checks are read have finished
+    for (DebugReader f : debug_readers()) {
+        const unsigned long long v = f();
+        if (v && !*first_error) *first_error = v;
+    }
+#else
+    *debug_build = 0;
+#endif
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_debug_selftest(void* stream) {
+    clear_error();
+#ifdef DHR_DEBUG
+    int* buf = nullptr;
+    DHR_CUDA_TRY(cudaMalloc((void**)&buf, 2 * sizeof(int)));
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) {
+        debug_selftest_kernel<<<1, 1, 0, st>>>(buf, buf + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return set_error(DHR_ERR_CUDA, "debug_selftest: %s", cudaGetErrorString(e));
+    return DHR_OK;
+#else
+    (void)stream;
+    return set_error(DHR_ERR_STATE, "debug_selftest: not a DHR_DEBUG build");
+#endif
+}
 
 // ------------------------------------------------------------------ scene
 extern "C" dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream, dhr_scene** out) {

@@ -40,6 +40,70 @@ void clear_error();
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// ------------------------------------------------------------ debug build
+// Built with DHR_DEBUG (libdhrs_debug.so), every gather index at the checked
+// sites is tested against its buffer's extent n.  An index outside [0, n)
+// records the first such event of the translation unit in its error word
+// (bit 63 set, the site in bits 40..47, the index's low 40 bits) and is
+// replaced by 0, so the access stays inside the buffer (every checked buffer
+// has n >= 1) and the kernel runs on.  dhr_debug_status collects and clears
+// the words of all translation units.  Without DHR_DEBUG the check is the
+// identity and costs nothing.
+enum DebugSite : uint32_t {
+    kSiteAtrousTap = 1,     // a-trous tap (colour and G-buffer)
+    kSiteAtrousVar = 2,     // a-trous variance Gaussian
+    kSiteDepthGrad = 3,     // depth slope neighbours
+    kSiteReproject = 4,     // reprojection taps of the previous frame
+    kSiteShortHist = 5,     // 7x7 short-history estimate
+    kSiteNode = 6,          // BVH node fetch
+    kSiteTriangle = 7,      // triangle fetch
+    kSiteRasterList = 8,    // rasterised tile list words
+    kSiteRasterBin = 9,     // binning writes
+    kSiteAdjoint = 10,      // adjoint gathers and scatters
+    kSiteSelfTest = 11,     // dhr_debug_selftest
+};
+
+#ifdef DHR_DEBUG
+static __device__ unsigned long long g_debug_err = 0;
+#endif
+
+__device__ __forceinline__ long long dbg_index(long long i, long long n, uint32_t site) {
+#ifdef DHR_DEBUG
+    if (i < 0 || i >= n) {
+        atomicCAS(&g_debug_err, 0ull,
+                  (1ull << 63) | ((unsigned long long)(site & 0xFFu) << 40) |
+                      ((unsigned long long)i & 0xFFFFFFFFFFull));
+        return 0;
+    }
+#else
+    (void)n;
+    (void)site;
+#endif
+    return i;
+}
+
+// host side: each translation unit registers a reader of its error word
+using DebugReader = unsigned long long (*)();
+void debug_register(DebugReader f);
+#ifdef DHR_DEBUG
+static unsigned long long debug_take_this_unit() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_debug_err, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (v) {
+        const unsigned long long z = 0;
+        cudaMemcpyToSymbol(g_debug_err, &z, sizeof(z));
+    }
+    return v;
+}
+struct DebugRegistration {
+    DebugRegistration() { debug_register(&debug_take_this_unit); }
+};
+static DebugRegistration g_debug_registration;
+#endif
+
 // ---------------------------------------------------------------- scene
 // BVH node, 64 bytes: the boxes of both children plus their references,
 // paired by plane so that one f32x2 fma gives both children's distances:
@@ -54,6 +118,7 @@ struct SceneView {
     const float4* tris;
     int32_t n_tris;
     const uint32_t* leaf_of;   // original triangle index -> leaf (sorted) index
+    int32_t n_nodes;           // internal nodes
 };
 
 constexpr int kStackSize = 64;
@@ -145,7 +210,9 @@ struct dhr_scene {
     uint32_t height = 0;
     uint64_t bytes = 0;
     float build_ms = 0.f;
-    dhr::SceneView view() const { return dhr::SceneView{nodes, tris, (int32_t)n_tris, leaf_of}; }
+    dhr::SceneView view() const {
+        return dhr::SceneView{nodes, tris, (int32_t)n_tris, leaf_of, (int32_t)n_nodes};
+    }
 };
 
 namespace dhr {

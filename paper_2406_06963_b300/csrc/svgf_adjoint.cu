@@ -91,7 +91,7 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
         for (int dx = -1; dx <= 1; ++dx) {
             const int qx = px + dx, qy = py + dy;
             if (kCheck && (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H)) continue;
-            const float4 v = __ldg(x + qy * k.W + qx);
+            const float4 v = __ldg(x + dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint));
             if (!fg_var(v.z)) continue;
             const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
             gw += kk;
@@ -117,7 +117,7 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
             if (!i && !j) continue;
             const int qx = px + i * step, qy = py + j * step;
             if (kCheck && (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H)) continue;
-            const int q = qy * k.W + qx;
+            const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
             const float4 cq = __ldg(x + q);
             if (!fg_var(cq.z)) continue;
             const TapLog t = tap_log<kNsq>(k, step, i, j, zp, gz, S::g(g, q));
@@ -190,7 +190,7 @@ __device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, con
             const int px = qx + dx, py = qy + dy;
             if (kCheck && (px < 0 || py < 0 || px >= k.W || py >= k.H)) continue;
             const float kk = (dx == 0 ? 0.5f : 0.25f) * (dy == 0 ? 0.5f : 0.25f);
-            const float4 rp = rec[2 * N + py * k.W + px];
+            const float4 rp = rec[2 * N + dbg_index((long long)py * k.W + px, (long long)N, kSiteAdjoint)];
             gvs = fma2(pack2(rp.x, rp.y), pack2(kk, kk), gvs);
         }
     const float4 zq = S::g(g, q);
@@ -204,7 +204,7 @@ __device__ __forceinline__ float4 bwd_b_pixel(const SvgfConsts& k, int step, con
             if (!i && !j) continue;
             const int px = qx - i * step, py = qy - j * step;
             const bool in = !kCheck || (px >= 0 && py >= 0 && px < k.W && py < k.H);
-            const int p = in ? py * k.W + px : q;
+            const int p = (int)dbg_index(in ? (long long)py * k.W + px : q, (long long)N, kSiteAdjoint);
             const float4 p0 = rec[p], p1 = rec[N + p], p3 = rec[3 * N + p];
             const TapLog t = tap_log<kNsq>(k, step, i, j, S::g(g, p), make_float2(p3.x, p3.y), zq);
             const float2 d = unpack2(add2(pack2(p3.z, p3.w), ncq));   // c_p - c_q
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx, qy = y + dy;
                     if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                    const int q = qy * k.W + qx;
+                    const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
                     const float4 zq = S::g(g_cur, q);
                     if (!is_fg(zq.x)) continue;
                     const W7 t = w7(k, zn, gz, dx, dy, zq);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx, qy = y + dy;
                     if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                    const int q = qy * k.W + qx;
+                    const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
                     const float4 zq = S::g(g_cur, q);
                     if (!is_fg(zq.x)) continue;
                     const float w = w7(k, zn, gz, dx, dy, zq).w * isw;
@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
             const float b = 1.f - a;
             for (int t = 0; t < 4; ++t) {
                 if (!(r.ok & (1 << t))) continue;
-                const int q = (r.y0 + (t >> 1)) * k.W + (r.x0 + (t & 1));
+                const int q = (int)dbg_index((long long)(r.y0 + (t >> 1)) * k.W + (r.x0 + (t & 1)), (long long)N,
+                                             kSiteAdjoint);
                 const float bb = r.w[t] / r.sumw * b;
                 atomicAdd(gcol_prev + q, make_float2(bb * Gce.x, bb * Gce.y));
                 atomicAdd(gmom_prev + q, make_float4(bb * Gm.x, bb * Gm.y, bb * Gm.z, bb * Gm.w));

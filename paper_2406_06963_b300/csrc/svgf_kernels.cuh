@@ -130,11 +130,11 @@ __device__ __forceinline__ float2 depth_grad(const typename S::G* g, int W, int 
         bool hp = false, hm = false;
         float dp = 0.f, dm = 0.f;
         if (xp < W && yp < H) {
-            const float z = S::g(g, (size_t)yp * W + xp).x;
+            const float z = S::g(g, dbg_index((long long)yp * W + xp, (long long)W * H, kSiteDepthGrad)).x;
             if (is_fg(z)) { dp = z - zp; hp = true; }
         }
         if (xm >= 0 && ym >= 0) {
-            const float z = S::g(g, (size_t)ym * W + xm).x;
+            const float z = S::g(g, dbg_index((long long)ym * W + xm, (long long)W * H, kSiteDepthGrad)).x;
             if (is_fg(z)) { dm = zp - z; hm = true; }
         }
         r[ax] = minmod_slope(hp, dp, hm, dm);
@@ -232,7 +232,8 @@ __device__ __forceinline__ bool reproject(const dhr_camera& c, const dhr_camera&
     for (int k = 0; k < 4; ++k) {
         const int qx2 = r.x0 + (k & 1), qy2 = r.y0 + (k >> 1);
         inb[k] = qx2 >= 0 && qy2 >= 0 && qx2 < W && qy2 < H;
-        r.q[k] = min(max(qy2, 0), H - 1) * W + min(max(qx2, 0), W - 1);
+        r.q[k] = (int)dbg_index((long long)min(max(qy2, 0), H - 1) * W + min(max(qx2, 0), W - 1), (long long)W * H,
+                                kSiteReproject);
         mq[k] = __ldg(mesh_prev + r.q[k]);
         gq[k] = S::g(g_prev, r.q[k]);
     }
@@ -400,7 +401,7 @@ __device__ __forceinline__ void temporal_tile(
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx;
                     if (qx < 0 || qx >= k.W) continue;
-                    const int q = qy * k.W + qx;
+                    const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)k.W * k.H, kSiteShortHist);
                     const float4 zq = S::g(g_cur, q);
                     const float2 sq = sig(q);
                     if (!is_fg(zq.x)) continue;
@@ -432,7 +433,7 @@ __device__ __forceinline__ void temporal_tile(
             const int dx = t % 7 - 3, dy = t / 7 - 3;
             const int qx = px + dx, qy = py + dy;
             if (t >= 49 || qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-            const int q = qy * k.W + qx;
+            const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)k.W * k.H, kSiteShortHist);
             const float4 zq = S::g(g_cur, q);
             const float2 sq = sig(q);
             if (!is_fg(zq.x)) continue;
@@ -541,7 +542,7 @@ struct TapsGlobal {
             z = make_float4(INFINITY, 0.f, 0.f, 0.f);
             return;
         }
-        const int q = qy * W + qx;
+        const int q = (int)dbg_index((long long)qy * W + qx, (long long)W * H, kSiteAtrousTap);
         c = __ldg(in + q);
         z = S::g(g, q);
     }
@@ -697,7 +698,7 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
             const int qx = bx0 - kAtHalo + sx, qy = by0 - kAtHalo + sy;
             float4 c = make_float4(1.f, 1.f, -1.f, -1.f), z = make_float4(INFINITY, 0.f, 0.f, 0.f);
             if (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H) {
-                const int q = qy * k.W + qx;
+                const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)k.W * k.H, kSiteAtrousTap);
                 c = __ldg(in + q);
                 z = S::g(g, q);
             }
@@ -741,8 +742,10 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
 #pragma unroll
         for (int dx = -1; dx <= 1; ++dx) {
             const int qx = x + dx, qy = y + dy;
-            v[dy + 1][dx + 1] = (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) ? make_float4(1.f, 1.f, -1.f, -1.f)
-                                                                              : __ldg(in + (qy * k.W + qx));
+            v[dy + 1][dx + 1] =
+                (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H)
+                    ? make_float4(1.f, 1.f, -1.f, -1.f)
+                    : __ldg(in + dbg_index((long long)qy * k.W + qx, (long long)k.W * k.H, kSiteAtrousVar));
         }
     float gv0, gv1, gw;
     var_gauss(v, gv0, gv1, gw);

@@ -159,6 +159,7 @@ __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tm
     for (uint32_t guard = 0; guard < kMaxSteps; ++guard) {
         if (node >= 0) {
             if (kStats) ++work->visits;
+            node = (int)dbg_index(node, sc.n_nodes, kSiteNode);
             const ulonglong2* nd = reinterpret_cast<const ulonglong2*>(sc.nodes + 4 * node);
             const ulonglong2 ax = __ldg(nd), ay = __ldg(nd + 1), az = __ldg(nd + 2);
             const float4 d = __ldg(sc.nodes + 4 * node + 3);
@@ -179,7 +180,7 @@ __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tm
             if (h0) { node = c0; continue; }
             if (h1) { node = c1; continue; }
         } else {
-            const int leaf = ~node;
+            const int leaf = (int)dbg_index(~node, sc.n_tris, kSiteTriangle);
             if (leaf == skip_leaf) goto pop;
             if (kStats) ++work->tests;
             const float4* tr = sc.tris + 3 * leaf;
@@ -426,7 +427,8 @@ __device__ __forceinline__ int tile_capacity(const TileStore& s, int tx, int ty)
 // word k of the tile (the tile's origin must lie inside the image)
 __device__ __forceinline__ uint32_t* tile_word(const TileStore& s, int tx, int ty, int k) {
     const int wpr = tile_row_words(s, tx);
-    return s.base + ((size_t)(kRasterTileH * ty + k / wpr) * s.W + kRasterTileW * tx) * s.ew + k % wpr;
+    const long long i = ((long long)(kRasterTileH * ty + k / wpr) * s.W + kRasterTileW * tx) * s.ew + k % wpr;
+    return s.base + dbg_index(i, (long long)s.W * s.H * s.ew, kSiteRasterList);
 }
 
 // Pixel of a thread: each warp covers an 8x4 tile; a 128-thread block

@@ -29,6 +29,26 @@ def test_library_exports_every_declared_symbol():
     assert names <= set(dhrs._SIGNATURES), sorted(names - set(dhrs._SIGNATURES))
 
 
+def test_debug_library_exports_every_declared_symbol():
+    """The bounds-checked build (DHR_DEBUG) has the same ABI."""
+    from paper_2406_06963_b300 import build
+    L = ctypes.CDLL(build.build(debug=True))
+    missing = [n for n in sorted(_declared_symbols()) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_release_build_reports_itself():
+    """The release library says it is not the debug build and refuses the
+    self test, without touching a device."""
+    from paper_2406_06963_b300 import build
+    L = ctypes.CDLL(build.build())
+    err, dbg = ctypes.c_uint64(7), ctypes.c_int32(7)
+    assert L.dhr_debug_status(ctypes.byref(err), ctypes.byref(dbg)) == 0
+    assert (err.value, dbg.value) == (0, 0)
+    assert L.dhr_debug_selftest(None) == 6   # DHR_ERR_STATE
+    assert L.dhr_debug_status(ctypes.byref(err), ctypes.byref(dbg)) == 0   # clears the error text
+
+
 def test_binding_loads_without_gpu():
     import paper_2406_06963_b300 as dhrs
     L = dhrs.lib()

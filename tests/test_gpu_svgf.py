@@ -129,7 +129,8 @@ def test_svgf_rejects_bad_arguments():
     cam = wl.boxes_camera(16, 16)
     m = torch.zeros((16, 16), dtype=torch.uint8, device="cuda")
     o = torch.empty((16, 16), device="cuda")
-    for bad in (dict(levels=9), dict(ao_spp=0), dict(alpha=0.0), dict(shadow_light=8), dict(kernel_width=4)):
+    for bad in (dict(levels=9), dict(ao_spp=0), dict(alpha=0.0), dict(shadow_light=8), dict(kernel_width=4),
+                dict(eps_z=0.0), dict(eps_l=0.0), dict(eps_z=float("inf"))):
         with pytest.raises(dhrs.DhrError):
             st.reconstruct(g, None, cam, None, m, m, dhrs.SvgfParams(**bad), o, o)
     g16 = dhrs.GBuffer(16, 16, dhrs.DHR_FP16)
