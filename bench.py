@@ -50,6 +50,9 @@ KERNEL_SOURCES = {
     "trace_kernel_raster_form": ["trace.cu", "trace_device.cuh", "sampling.cuh", "common.cuh"],
     "atrous_kernel": ["svgf.cu", "svgf_kernels.cuh", "common.cuh"],
     "temporal_kernel": ["svgf.cu", "svgf_kernels.cuh", "common.cuh"],
+    "atrous_bwd_a": ["svgf_adjoint.cu", "svgf_kernels.cuh", "common.cuh"],
+    "atrous_bwd_b": ["svgf_adjoint.cu", "svgf_kernels.cuh", "common.cuh"],
+    "temporal_bwd_kernel": ["svgf_adjoint.cu", "svgf_kernels.cuh", "common.cuh"],
 }
 
 
@@ -597,9 +600,15 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
     e[2].record()
     torch.cuda.synchronize()
     fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
-    # algorithmic bytes per pixel and frame: forward 340; backward: 4 level
-    # recomputations x 48, 5 x (pass A 112 + pass B 112), temporal 100
-    bytes_fb = frames * W * H * (340 + 4 * 48 + 5 * 224 + 100)
+    # algorithmic bytes per pixel and frame (each buffer read or written once
+    # per kernel): forward 340 as the SVGF frame + the records (weight sums
+    # 8 per level, last output 16); backward per level pass A 176 (input 16,
+    # G-buffer 16, weight sums 8, output 16, upstream gradient 16, sigma
+    # terms 32 read + written, records 64 written) and pass B 112 (records
+    # 64, input 16, G-buffer 16, gradient 16 written), temporal backward 180
+    bytes_fwd = frames * W * H * (340 + 5 * 8 + 16)
+    bytes_bwd = frames * W * H * (5 * (176 + 112) + 180)
+    bytes_fb = bytes_fwd + bytes_bwd
     log_s = torch.tensor([0.0, 4.852, 1.386], device="cuda").requires_grad_(True)  # log(1, 128, 4)
     opt = torch.optim.Adam([log_s], lr=0.05)
     losses = []
@@ -610,8 +619,15 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
         loss.backward()
         opt.step()
         losses.append(round(float(loss.detach()), 6))
+    peak = _peaks()[0].get("hbm_gbs")
+    gbs_b = bytes_bwd / (bwd * 1e-3) / 1e9
+    traffic = {k: _traffic(k) for k in ("atrous_bwd_a", "atrous_bwd_b", "temporal_bwd_kernel")}
     return {"workload": f"{frames} frames x {W}x{H}, terrain776k", "forward_ms": round(fwd, 3),
             "backward_ms": round(bwd, 3), "algorithmic_gb_per_s": round(bytes_fb / ((fwd + bwd) * 1e-3) / 1e9, 1),
+            "backward_algorithmic_gb_per_s": round(gbs_b, 1),
+            "backward_frac_hbm": round(gbs_b / peak, 4) if peak else None,
+            "backward_bytes_per_px_frame": 5 * (176 + 112) + 180,
+            "ncu_dram_bytes_per_launch": traffic,
             "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.detach().exp()]}
 
 
@@ -821,6 +837,8 @@ def main():
                          "traversal (same outputs)")
     ap.add_argument("--selective-only", action="store_true",
                     help="print only the selective shadow ray measurement (profiling aid)")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="print only the adjoint measurement (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -830,6 +848,12 @@ def main():
         scene_d = wl.scene_terrain()
         print(json.dumps({"selective_shadows": run_selective(dhrs.Scene(scene_d), scene_d,
                                                              frames=args.steps + args.warmup)}), flush=True)
+        return
+    if args.adjoint_only:
+        import paper_2406_06963_b300 as dhrs
+        import workloads as wl
+        scene_d = wl.scene_terrain()
+        print(json.dumps({"adjoint": run_adjoint(dhrs.Scene(scene_d), scene_d)}), flush=True)
         return
     res = run_reference(args) if args.impl == "reference" else run_ours(args)
     if res is not None:
