@@ -129,7 +129,7 @@ extern "C" dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream,
             s = set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA, "create_scene: %s",
                           cudaGetErrorString(e));
         if (s == DHR_OK) s = build_lbvh(v, idx, mesh, desc->n_vertices, desc->n_triangles, st, sc, desc->builder);
-        if (s == DHR_OK) s = build_leaf_map(sc, st);
+        if (s == DHR_OK) s = build_chunk_boxes(sc, st);
         cudaStreamSynchronize(st);
     }
     cudaFree(v);
@@ -147,7 +147,7 @@ extern "C" void dhr_destroy_scene(dhr_scene* sc) {
     if (!sc) return;
     cudaFree(sc->nodes);
     cudaFree(sc->tris);
-    cudaFree(sc->leaf_of);
+    cudaFree(sc->chunk_box);
     delete sc;
 }
 

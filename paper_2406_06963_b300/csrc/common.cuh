@@ -117,9 +117,12 @@ struct SceneView {
     const float4* nodes;
     const float4* tris;
     int32_t n_tris;
-    const uint32_t* leaf_of;   // original triangle index -> leaf (sorted) index
+    const float4* chunk_box;   // per kChunk consecutive leaves: (lo, -), (hi, -) of their vertices
     int32_t n_nodes;           // internal nodes
 };
+
+// leaves per chunk of the rasteriser's frustum test (one binning block)
+constexpr int kChunk = 128;
 
 constexpr int kStackSize = 64;
 
@@ -204,14 +207,14 @@ __device__ __forceinline__ float4 unpack_gbuf16(uint2 u) {
 struct dhr_scene {
     float4* nodes = nullptr;
     float4* tris = nullptr;
-    uint32_t* leaf_of = nullptr;
+    float4* chunk_box = nullptr;
     uint32_t n_tris = 0;
     uint32_t n_nodes = 0;
     uint32_t height = 0;
     uint64_t bytes = 0;
     float build_ms = 0.f;
     dhr::SceneView view() const {
-        return dhr::SceneView{nodes, tris, (int32_t)n_tris, leaf_of, (int32_t)n_nodes};
+        return dhr::SceneView{nodes, tris, (int32_t)n_tris, chunk_box, (int32_t)n_nodes};
     }
 };
 
@@ -241,7 +244,7 @@ dhr_status launch_trace_selective(const dhr_scene* sc, const dhr_camera* cam, co
 // hit of the pixel-centre ray, or ~0 where there is none.  Returns false (and
 // launches nothing) when the camera basis is singular; the caller then traces
 // primary rays instead.
-dhr_status build_leaf_map(dhr_scene* sc, cudaStream_t st);
+dhr_status build_chunk_boxes(dhr_scene* sc, cudaStream_t st);
 dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer* g, cudaStream_t st,
                          bool* launched);
 

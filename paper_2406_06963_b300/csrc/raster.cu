@@ -31,6 +31,7 @@ struct RasterConsts {
     float kx, ky;               // tan(half fov) * aspect, tan(half fov)
     float inv_kx, inv_ky;
     float sx_lo, sx_hi, sy_lo, sy_hi;   // pixel-centre range widened by one pixel
+    float3 pn[4];               // plane_dist's four planes as world-space normals: d_k = pn[k] . (P - eye)
 };
 
 __device__ __forceinline__ float3 cam_coords(const RasterConsts& rc, float3 p) {
@@ -190,7 +191,29 @@ __device__ __forceinline__ void bin_tiles(const BinLayout& b, int tx0, int ty0, 
     }
 }
 
-__global__ void __launch_bounds__(128) bin_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
+// A chunk of kChunk leaves whose vertex box lies wholly outside one of the
+// side planes (with a margin far above the rounding of plane_dist) holds
+// only triangles that tri_bounds rejects as outside that plane: its block
+// bins nothing.
+__device__ __forceinline__ bool chunk_outside(const SceneView& sc, const RasterConsts& rc, int chunk) {
+    const float4 lo = __ldg(sc.chunk_box + 2 * chunk), hi = __ldg(sc.chunk_box + 2 * chunk + 1);
+    const float3 c = make_float3(0.5f * (lo.x + hi.x) - rc.eye.x, 0.5f * (lo.y + hi.y) - rc.eye.y,
+                                 0.5f * (lo.z + hi.z) - rc.eye.z);
+    const float3 h = make_float3(0.5f * (hi.x - lo.x), 0.5f * (hi.y - lo.y), 0.5f * (hi.z - lo.z));
+    const float scale = fabsf(c.x) + fabsf(c.y) + fabsf(c.z) + h.x + h.y + h.z;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float3 n = rc.pn[k];
+        // largest d_k over the box, against a margin of 1e-4 of the box's extent from the eye
+        const float dmax = dot(n, c) + fabsf(n.x) * h.x + fabsf(n.y) * h.y + fabsf(n.z) * h.z;
+        const float nn = fabsf(n.x) + fabsf(n.y) + fabsf(n.z);
+        if (dmax < -1e-4f * nn * scale) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kChunk) bin_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
+    if (chunk_outside(sc, rc, blockIdx.x)) return;   // uniform over the block
     const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
@@ -251,20 +274,50 @@ __global__ void bin_clear_kernel(BinLayout b) {
     if (t == 0) b.big[0] = 0u;
 }
 
-__global__ void leaf_map_kernel(const float4* tris, int n, uint32_t* leaf_of) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    leaf_of[__float_as_uint(__ldg(tris + 3 * i).w)] = (uint32_t)i;
+// box of the vertices of kChunk consecutive leaves, one block per chunk
+__global__ void __launch_bounds__(kChunk) chunk_box_kernel(const float4* tris, int n, float4* box) {
+    const int i = blockIdx.x * kChunk + threadIdx.x;
+    float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+    if (i < n) {
+        for (int v = 0; v < 3; ++v) {
+            const float4 p = __ldg(tris + 3 * i + v);
+            lo = make_float3(fminf(lo.x, p.x), fminf(lo.y, p.y), fminf(lo.z, p.z));
+            hi = make_float3(fmaxf(hi.x, p.x), fmaxf(hi.y, p.y), fmaxf(hi.z, p.z));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+    __shared__ float3 s_lo[kChunk / 32], s_hi[kChunk / 32];
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kChunk / 32; ++w) {
+            lo = make_float3(fminf(lo.x, s_lo[w].x), fminf(lo.y, s_lo[w].y), fminf(lo.z, s_lo[w].z));
+            hi = make_float3(fmaxf(hi.x, s_hi[w].x), fmaxf(hi.y, s_hi[w].y), fmaxf(hi.z, s_hi[w].z));
+        }
+        box[2 * blockIdx.x] = make_float4(lo.x, lo.y, lo.z, 0.f);
+        box[2 * blockIdx.x + 1] = make_float4(hi.x, hi.y, hi.z, 0.f);
+    }
 }
 
 }  // namespace
 
-dhr_status build_leaf_map(dhr_scene* sc, cudaStream_t st) {
+dhr_status build_chunk_boxes(dhr_scene* sc, cudaStream_t st) {
     if (sc->n_tris == 0) return DHR_OK;
-    DHR_CUDA_TRY(cudaMalloc((void**)&sc->leaf_of, (size_t)sc->n_tris * 4));
-    leaf_map_kernel<<<(sc->n_tris + 255) / 256, 256, 0, st>>>(sc->tris, (int)sc->n_tris, sc->leaf_of);
+    const uint32_t chunks = (sc->n_tris + kChunk - 1) / kChunk;
+    DHR_CUDA_TRY(cudaMalloc((void**)&sc->chunk_box, (size_t)chunks * 32));
+    chunk_box_kernel<<<chunks, kChunk, 0, st>>>(sc->tris, (int)sc->n_tris, sc->chunk_box);
     DHR_CUDA_TRY(cudaGetLastError());
-    sc->bytes += (uint64_t)sc->n_tris * 4;
+    sc->bytes += (uint64_t)chunks * 32;
     return DHR_OK;
 }
 
@@ -310,10 +363,23 @@ dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer
     rc.sx_lo = -rc.sx_hi;
     rc.sy_hi = (float)((1.0 + 1.0 / H) * ky * 1.001);
     rc.sy_lo = -rc.sy_hi;
+    // d_k of plane_dist as world-space normals: a = (mf, mr, mu) . (P - eye), so
+    // d_0 = (mr - sx_lo mf) . (P - eye) and so on (double, then rounded)
+    {
+        const double sx_lo = rc.sx_lo, sx_hi = rc.sx_hi, sy_lo = rc.sy_lo, sy_hi = rc.sy_hi;
+        double n[4][3];
+        for (int c = 0; c < 3; ++c) {
+            n[0][c] = inv[1][c] - sx_lo * inv[0][c];
+            n[1][c] = sx_hi * inv[0][c] - inv[1][c];
+            n[2][c] = inv[2][c] - sy_lo * inv[0][c];
+            n[3][c] = sy_hi * inv[0][c] - inv[2][c];
+        }
+        for (int k = 0; k < 4; ++k) rc.pn[k] = make_float3((float)n[k][0], (float)n[k][1], (float)n[k][2]);
+    }
     b.ts = TileStore{reinterpret_cast<uint32_t*>(g->depth_normal), W, H, g->precision == DHR_FP16 ? 2 : 4};
     b.big = g->mesh_id;
     bin_clear_kernel<<<(unsigned)((n_tiles + 255) / 256), 256, 0, st>>>(b);
-    bin_kernel<<<(sc->n_tris + 127) / 128, 128, 0, st>>>(sc->view(), rc, b);
+    bin_kernel<<<(sc->n_tris + kChunk - 1) / kChunk, kChunk, 0, st>>>(sc->view(), rc, b);
     bin_big_kernel<<<kBigGrid, 128, 0, st>>>(sc->view(), rc, b);
     DHR_CUDA_TRY(cudaGetLastError());
     *launched = true;
