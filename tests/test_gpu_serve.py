@@ -5,6 +5,8 @@ delay reprojection (dhr_delay_warp, Section 4.1 / Fig. 5).
 - A session served by the batching server gives exactly what dhr_step_frame
   gives, alone and in a mix of sessions of other resolutions (same kernels,
   same per-pixel arithmetic: bit-identical, well inside 1e-3).
+- Sessions of two sizes batched together equal the oracle's trace-then-filter
+  frame by frame (no GPU path in between).
 - Admission by device-memory budget, latest-wins request replacement.
 """
 import numpy as np
@@ -76,6 +78,52 @@ def test_server_equals_step_frame_alone_and_in_mix():
         ref = (a.cpu().numpy(), b.cpu().numpy())
         for got in (alone[0][f], mix[1][f]):
             assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), f
+
+
+def test_server_sessions_match_oracle():
+    """Two sessions of different sizes batched together by the server, frame
+    by frame against the oracle tracing the same poses itself and filtering
+    them with orc_svgf_frame (Sections 3.1-3.3 and the serving form end to
+    end, without the server-equals-session step in between).  The raw
+    visibility of each pose (dhr_trace_visibility, the server's trace
+    function) may differ from the oracle's only on rays the oracle flags as
+    grazing; the filtered AO and shadow the server returns must be within
+    1e-3 of the oracle's on every pixel whose filter footprint, over all
+    frames so far, saw no such difference (a flipped bit spreads up to 62
+    pixels through the levels and through the history)."""
+    s = wl.scene_boxes()
+    sc, S = dhrs.Scene(s), orc.Scene(s)
+    sizes = [(256, 192, wl.orbit_path(5, 256, 192, degrees=10.0)),
+             (160, 96, wl.orbit_path(5, 160, 96, degrees=8.0, start_deg=35))]
+    outs, _ = _run_server(sc, sizes, 5)
+    checked, total = 0, 0
+    for k, (W, H, path) in enumerate(sizes):
+        ost = orc.SvgfState(W, H)
+        tainted = np.zeros((H, W), bool)
+        for f, cam in enumerate(path):
+            tr = orc.trace(S, cam, orc.TraceParams(frame=f))
+            zn, mesh = orc.gbuffer_f32(tr, W, H)
+            ref = ost.frame(zn, mesh, cam, tr["shadow_mask"].reshape(H, W), tr["ao_count"].reshape(H, W),
+                            orc.SvgfParams())
+            flagged = (tr["amb_primary"] | tr["amb_shadow"] | tr["amb_ao"]).reshape(H, W) > 0
+            g = dhrs.GBuffer(W, H)
+            m = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+            a = torch.empty_like(m)
+            dhrs.trace_visibility(sc, cam, dhrs.TraceParams(frame=f), g, m, a)
+            differ = (m.cpu().numpy() != tr["shadow_mask"].reshape(H, W)) | \
+                     (a.cpu().numpy() != tr["ao_count"].reshape(H, W))
+            assert not (differ & ~flagged).any(), (k, f)
+            for y, x in zip(*np.nonzero(differ)):
+                tainted[max(0, y - 72):y + 73, max(0, x - 72):x + 73] = True
+            ok = ~tainted
+            got_ao, got_sh = outs[k][f]
+            e = np.maximum(np.abs(got_ao - ref["ao"]), np.abs(got_sh - ref["shadow"]))
+            if ok.any():
+                assert e[ok].max() <= 1e-3, (k, f, float(e[ok].max()))
+            checked += int(ok.sum())
+            total += W * H
+    print(f"server vs oracle: {checked} of {total} pixel-frames checked")
+    assert checked >= 0.8 * total
 
 
 def test_server_admission_by_memory_budget():
