@@ -110,6 +110,7 @@ _SIGNATURES = {
     "dhr_server_close": ([_P, C.c_int32], C.c_int),
     "dhr_server_submit": ([_P, C.c_int32, _P, _P, C.c_uint32, C.c_uint64, C.c_uint64], C.c_int),
     "dhr_server_set_max_batch_pixels": ([_P, C.c_uint64], C.c_int),
+    "dhr_server_set_raster_min_pixels": ([_P, C.c_uint64], C.c_int),
     "dhr_visibility_pack_bound": ([C.c_int32, C.c_int32, C.c_uint32, C.c_uint32], C.c_uint64),
     "dhr_visibility_pack_work": ([C.c_int32, C.c_int32, C.c_uint32, C.c_uint32], C.c_uint64),
     "dhr_visibility_pack": ([_P, _P, C.c_int32, C.c_int32, C.c_uint32, C.c_uint32, _P, _P, _P], C.c_int),
@@ -745,6 +746,11 @@ class Server:
     def set_max_batch_pixels(self, max_pixels: int):
         """Pixel cap of one batch (0: none)."""
         _check(lib().dhr_server_set_max_batch_pixels(self.h, C.c_uint64(max_pixels)))
+
+    def set_raster_min_pixels(self, min_pixels: int):
+        """Sessions of at least min_pixels rasterise their primary visibility
+        (0: all, 2**64 - 1: none); the G-buffers are the same either way."""
+        _check(lib().dhr_server_set_raster_min_pixels(self.h, C.c_uint64(int(min_pixels))))
 
     def pump(self) -> int:
         n = C.c_int32()

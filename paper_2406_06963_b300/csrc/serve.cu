@@ -23,8 +23,8 @@
 #include <thread>
 #include <vector>
 
+#include "raster_device.cuh"
 #include "svgf_kernels.cuh"
-#include "trace_device.cuh"
 
 namespace dhr {
 namespace {
@@ -36,6 +36,10 @@ constexpr int kMaxItems = 64;
 // 37 ms at the same pixel throughput)
 constexpr uint64_t kDefaultBatchPx = 2u << 20;
 constexpr int kTileW = 32, kTileH = 8;
+// sessions of at least this many pixels rasterise their primary visibility
+// (the binning pass costs about the same at every resolution, the traversal
+// it replaces grows with the pixels: measured break-even near 1.1 Mpx)
+constexpr uint64_t kDefaultRasterMinPx = 3u << 19;
 
 struct ServeItem {
     TraceConsts tk;          // traced pose and trace parameters
@@ -63,6 +67,9 @@ struct ServeItem {
     uint32_t* m_tgt;
     float* fin_ao;
     float* fin_sh;
+    int raster;              // primary visibility rasterised (tile lists in g_cur, big list in m_cur)
+    RasterConsts rc;
+    BinLayout bl;
 };
 
 struct BatchTable {
@@ -94,17 +101,51 @@ __device__ __forceinline__ int2 trace_thread_pixel(int2 o) {
     return make_int2(o.x + (warp & 3) * 8 + (lane & 7), o.y + (warp >> 2) * 4 + (lane >> 3));
 }
 
-__global__ void __launch_bounds__(256) serve_trace_kernel(SceneView sc, const BatchTable* tb, int primary_target) {
+__global__ void __launch_bounds__(256, 4) serve_trace_kernel(SceneView sc, const BatchTable* tb, int primary_target) {
     const BatchTable& b = *tb;
     for (int t = blockIdx.x; t < b.n_tiles; t += gridDim.x) {
         const ServeItem& it = b.items[find_item(b, t)];
         const int2 px = trace_thread_pixel(tile_origin(it, t));
         if (primary_target) {
             if (it.warp)
-                trace_pixel<false, false, true>(sc, it.tk_target, px, it.g_tgt, it.m_tgt, nullptr, nullptr, nullptr);
+                trace_pixel<false, false, true, false, false, 8>(sc, it.tk_target, px, it.g_tgt, it.m_tgt, nullptr,
+                                                                 nullptr, nullptr);
+        } else if (it.raster) {
+            trace_pixel<false, false, false, false, true, 8>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask, it.ao, nullptr);
         } else {
-            trace_pixel<false, false, false>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask, it.ao, nullptr);
+            trace_pixel<false, false, false, false, false, 8>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask, it.ao,
+                                                              nullptr);
         }
+    }
+}
+
+// rasterised primary visibility of the batch's items with raster set: clear
+// their tile counts, bin every chunk of the scene, bin the big triangles
+__global__ void __launch_bounds__(256) serve_bin_clear_kernel(const BatchTable* tb) {
+    const BatchTable& b = *tb;
+    for (int i = 0; i < b.n_items; ++i) {
+        const ServeItem& it = b.items[i];
+        if (!it.raster) continue;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < it.bl.n_tiles; t += gridDim.x * blockDim.x)
+            bin_clear(it.bl, t);
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) serve_bin_kernel(SceneView sc, const BatchTable* tb) {
+    const BatchTable& b = *tb;
+    const int chunks = (sc.n_tris + kChunk - 1) / kChunk;
+    for (int i = 0; i < b.n_items; ++i) {
+        const ServeItem& it = b.items[i];
+        if (!it.raster) continue;
+        for (int c = blockIdx.x; c < chunks; c += gridDim.x) bin_chunk(sc, it.rc, it.bl, c);
+    }
+}
+
+__global__ void __launch_bounds__(128) serve_bin_big_kernel(SceneView sc, const BatchTable* tb) {
+    const BatchTable& b = *tb;
+    for (int i = 0; i < b.n_items; ++i) {
+        const ServeItem& it = b.items[i];
+        if (it.raster) bin_big(sc, it.rc, it.bl, blockIdx.x, gridDim.x);
     }
 }
 
@@ -334,6 +375,7 @@ struct LoopMeta {
     TraceConsts tk_base;      // lights, cones, AO parameters; camera and frame per request
     SvgfConsts sk_base;
     int32_t levels, nsq;
+    uint64_t raster_min_px;   // sessions of at least this many pixels rasterise (~0: none)
     int32_t n_items;
     uint64_t t_batch;
     int32_t item_session[kMaxItems];
@@ -531,6 +573,8 @@ __global__ void __launch_bounds__(1024) loop_schedule_kernel(int li, LoopCtl* ct
         it.m_tgt = sl.m_tgt;
         it.fin_ao = sl.fin_ao;
         it.fin_sh = sl.fin_sh;
+        it.raster = (uint64_t)sl.w * sl.h >= meta->raster_min_px &&
+                    make_raster(cam, it.g_cur, it.m_cur, 4, it.rc, it.bl);
         __threadfence_system();
         valid = valid && ld_acquire_sys(&m.seq) == sreq[id] && ld_acquire_sys(&sl.generation) == sgen[id];
         if (valid) {
@@ -763,6 +807,7 @@ struct dhr_server {
     std::vector<dhr_completion> done;  // finished or dropped, not yet polled
     uint64_t n_dropped = 0, n_batches = 0, n_frames = 0;
     uint64_t max_batch_px = kDefaultBatchPx;   // pixel cap of one batch (0: none)
+    uint64_t raster_min_px = kDefaultRasterMinPx;   // sessions from this size rasterise primaries
     cudaStream_t mem_stream = nullptr;  // session allocations (stream ordered)
     LoopHost loop;
 };
@@ -771,6 +816,9 @@ struct dhr_server {
 // trace, temporal, a-trous levels, target G-buffer, delay warp
 static void launch_stages(const dhr_server* s, cudaStream_t st, const BatchTable* tb) {
     const SceneView sv = s->scene->view();
+    serve_bin_clear_kernel<<<148 * 2, 256, 0, st>>>(tb);
+    serve_bin_kernel<<<148 * 8, kChunk, 0, st>>>(sv, tb);
+    serve_bin_big_kernel<<<kBigGrid, 128, 0, st>>>(sv, tb);
     serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, tb, 0);
     serve_temporal_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
     const int L = (int)s->sp.levels;
@@ -1346,6 +1394,13 @@ extern "C" dhr_status dhr_server_set_max_batch_pixels(dhr_server* s, uint64_t ma
     return DHR_OK;
 }
 
+extern "C" dhr_status dhr_server_set_raster_min_pixels(dhr_server* s, uint64_t min_pixels) {
+    clear_error();
+    DHR_CHECK_ARG(s, "server_set_raster_min_pixels: null server");
+    s->raster_min_px = min_pixels;
+    return DHR_OK;
+}
+
 extern "C" dhr_status dhr_server_pump(dhr_server* s, int32_t* launched) {
     clear_error();
     DHR_CHECK_ARG(s, "server_pump: null server");
@@ -1421,6 +1476,8 @@ extern "C" dhr_status dhr_server_pump(dhr_server* s, int32_t* launched) {
         it.m_tgt = se.m_tgt;
         it.fin_ao = se.fin_ao;
         it.fin_sh = se.fin_sh;
+        it.raster = s->tp.primary == DHR_PRIMARY_RASTER && px >= s->raster_min_px && s->scene->n_tris > 0 &&
+                    make_raster(r.cam, it.g_cur, it.m_cur, 4, it.rc, it.bl);
         ++b.n_items;
         se.cur = cur;
         se.cam_prev = r.cam;
@@ -1541,6 +1598,7 @@ extern "C" dhr_status dhr_server_loop_start(dhr_server* s, uint32_t idle_ms, uin
     m.sk_base = make_consts(1, 1, &s->sp);
     m.levels = (int)s->sp.levels;
     m.nsq = s->sp.sigma_n == 128.0f ? 7 : -1;
+    m.raster_min_px = (s->tp.primary == DHR_PRIMARY_RASTER && s->scene->n_tris > 0) ? s->raster_min_px : ~0ull;
     m.lim.idle_ns = (uint64_t)idle_ms * 1000000ull;
     m.lim.max_run_ns = (uint64_t)max_run_ms * 1000000ull;
     m.lim.poll_ns = 50000;                  // 50 us of waiting per scheduling pass

@@ -447,10 +447,11 @@ __device__ __forceinline__ int2 thread_pixel() {
 // decide (smap_classify); ray_mask (optional) receives bit l = light l's
 // ray was called for.
 // kRaster: the primary hit is the closest among the triangles binned to the
-// warp's tile (launch_raster), read from the tile's G-buffer storage before
-// the warp overwrites it; a tile whose list is too long or did not fit is
-// traversed.
-template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false, bool kRaster = false>
+// warp's tile (raster_device.cuh), read from the tile's G-buffer storage
+// before the warp overwrites it; a tile whose list is too long or did not fit
+// is traversed.  kWarps: warps per block (the warp's 32 lanes must cover one
+// 8 x 4-pixel tile).
+template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false, bool kRaster = false, int kWarps = 4>
 __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceConsts& k, int2 px, void* gbuf_dn,
                                             uint32_t* gbuf_mesh, uint8_t* mask_out, uint8_t* ao_out,
                                             unsigned long long* stats, const SmapSet* sel = nullptr,
@@ -461,7 +462,7 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
     if constexpr (kRaster) {
         // the whole warp copies its tile's list to shared memory before any
         // lane writes its pixel (which holds part of the list)
-        __shared__ uint32_t s_list[4][kMaxBin];   // 128-thread blocks: 4 warps
+        __shared__ uint32_t s_list[kWarps][kMaxBin];   // kWarps warps per block
         const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
         list = s_list[wib];
         const int tx = px.x / kRasterTileW, ty = px.y / kRasterTileH;

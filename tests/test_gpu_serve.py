@@ -42,9 +42,14 @@ def test_delay_warp_matches_oracle():
     assert np.array_equal(ob.cpu().numpy(), rb.astype(np.float32))
 
 
-def _run_server(sc, sessions, frames, budget=8 << 30):
-    """sessions: list of (W, H, path); returns outputs[session][frame]."""
+def _run_server(sc, sessions, frames, budget=8 << 30, raster_min=None):
+    """sessions: list of (W, H, path); returns outputs[session][frame].
+    raster_min: sessions of at least this many pixels rasterise their primary
+    visibility (None: the library's default, which these small sessions stay
+    below, so they trace primary rays)."""
     srv = dhrs.Server(sc, budget)
+    if raster_min is not None:
+        srv.set_raster_min_pixels(raster_min)
     ids = [srv.open(w, h) for (w, h, _) in sessions]
     outs = {i: [] for i in range(len(sessions))}
     for f in range(frames):
@@ -60,15 +65,18 @@ def _run_server(sc, sessions, frames, budget=8 << 30):
     return outs, srv
 
 
-def test_server_equals_step_frame_alone_and_in_mix():
+@pytest.mark.parametrize("raster_min", [None, 0, 20000])
+def test_server_equals_step_frame_alone_and_in_mix(raster_min):
+    """raster_min None: every session traces primary rays; 0: every session
+    rasterises; 20000: a mix of both in one batch."""
     s = wl.scene_boxes()
     sc = dhrs.Scene(s)
     A = (200, 120, wl.orbit_path(4, 200, 120, degrees=6.0))
     others = [(96, 64, wl.orbit_path(4, 96, 64, degrees=9.0, start_deg=40)),
               (333, 77, wl.orbit_path(4, 333, 77, degrees=3.0, start_deg=-30)),
               (64, 200, wl.orbit_path(4, 64, 200, degrees=5.0, start_deg=90))]
-    alone, _ = _run_server(sc, [A], 4)
-    mix, _ = _run_server(sc, others[:1] + [A] + others[1:], 4)
+    alone, _ = _run_server(sc, [A], 4, raster_min=raster_min)
+    mix, _ = _run_server(sc, others[:1] + [A] + others[1:], 4, raster_min=raster_min)
     sess = dhrs.Session(sc, 200, 120)
     a = torch.empty((120, 200), device="cuda")
     b = torch.empty_like(a)
@@ -80,7 +88,8 @@ def test_server_equals_step_frame_alone_and_in_mix():
             assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), f
 
 
-def test_server_sessions_match_oracle():
+@pytest.mark.parametrize("raster_min", [None, 0])
+def test_server_sessions_match_oracle(raster_min):
     """Two sessions of different sizes batched together by the server, frame
     by frame against the oracle tracing the same poses itself and filtering
     them with orc_svgf_frame (Sections 3.1-3.3 and the serving form end to
@@ -95,7 +104,7 @@ def test_server_sessions_match_oracle():
     sc, S = dhrs.Scene(s), orc.Scene(s)
     sizes = [(256, 192, wl.orbit_path(5, 256, 192, degrees=10.0)),
              (160, 96, wl.orbit_path(5, 160, 96, degrees=8.0, start_deg=35))]
-    outs, _ = _run_server(sc, sizes, 5)
+    outs, _ = _run_server(sc, sizes, 5, raster_min=raster_min)
     checked, total = 0, 0
     for k, (W, H, path) in enumerate(sizes):
         ost = orc.SvgfState(W, H)
@@ -244,10 +253,13 @@ def _collect(srv, want, limit_s=30.0):
     return got
 
 
-def test_device_loop_equals_host_batches(no_gc):
+@pytest.mark.parametrize("raster_min", [None, 20000])
+def test_device_loop_equals_host_batches(no_gc, raster_min):
     """The same per-session request sequences through the device loop and
     through host-formed batches give bit-identical outputs (same kernels,
-    same inputs, whatever the batching)."""
+    same inputs, whatever the batching; raster_min 20000: the two larger
+    sessions rasterise, with raster constants formed on the device by the
+    loop and on the host for the host batches)."""
     s = wl.scene_boxes()
     sc = dhrs.Scene(s)
     sessions = [(200, 120, wl.orbit_path(4, 200, 120, degrees=6.0)),
@@ -255,8 +267,10 @@ def test_device_loop_equals_host_batches(no_gc):
                 (333, 77, wl.orbit_path(4, 333, 77, degrees=3.0, start_deg=-30))]
     # the host-batched server stays referenced: destroying it frees pinned
     # memory, a device-wide synchronisation that would wait for the loop
-    host, host_srv = _run_server(sc, sessions, 4)
+    host, host_srv = _run_server(sc, sessions, 4, raster_min=raster_min)
     srv = dhrs.Server(sc, 8 << 30)
+    if raster_min is not None:
+        srv.set_raster_min_pixels(raster_min)
     ids = [srv.open(w, h) for (w, h, _p) in sessions]
     srv.loop_start(idle_ms=5000, max_run_ms=60000)
     for f in range(4):
