@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) serve_bin_clear_kernel(const BatchTable* 
     const BatchTable& b = *tb;
     for (int i = 0; i < b.n_items; ++i) {
         const ServeItem& it = b.items[i];
-        if (!it.raster) continue;
+        if (!it.raster || it.tiles_x == 0) continue;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < it.bl.n_tiles; t += gridDim.x * blockDim.x)
             bin_clear(it.bl, t);
     }
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kChunk) serve_bin_kernel(SceneView sc, const B
     const int chunks = (sc.n_tris + kChunk - 1) / kChunk;
     for (int i = 0; i < b.n_items; ++i) {
         const ServeItem& it = b.items[i];
-        if (!it.raster) continue;
+        if (!it.raster || it.tiles_x == 0) continue;
         for (int c = blockIdx.x; c < chunks; c += gridDim.x) bin_chunk(sc, it.rc, it.bl, c);
     }
 }
@@ -145,11 +145,11 @@ __global__ void __launch_bounds__(128) serve_bin_big_kernel(SceneView sc, const 
     const BatchTable& b = *tb;
     for (int i = 0; i < b.n_items; ++i) {
         const ServeItem& it = b.items[i];
-        if (it.raster) bin_big(sc, it.rc, it.bl, blockIdx.x, gridDim.x);
+        if (it.raster && it.tiles_x > 0) bin_big(sc, it.rc, it.bl, blockIdx.x, gridDim.x);
     }
 }
 
-__global__ void __launch_bounds__(256) serve_temporal_kernel(const BatchTable* tb) {
+__global__ void __launch_bounds__(256, 5) serve_temporal_kernel(const BatchTable* tb) {
     const BatchTable& b = *tb;
     for (int t = blockIdx.x; t < b.n_tiles; t += gridDim.x) {
         const ServeItem& it = b.items[find_item(b, t)];
@@ -172,7 +172,7 @@ __device__ __forceinline__ void serve_atrous_tile(const ServeItem& it, int l, in
 // level l of every session; mode: 1 writes the colour history, 2 the outputs.
 // The session's a-trous tiles are its 32x8 pixel tiles.
 template <int kNsq, int kR>
-__global__ void __launch_bounds__(256) serve_atrous_kernel(const BatchTable* tb, int l, int mode) {
+__global__ void __launch_bounds__(256, 4) serve_atrous_kernel(const BatchTable* tb, int l, int mode) {
     __shared__ AtrousSmem sm;
     const BatchTable& b = *tb;
     for (int t = blockIdx.x; t < b.n_tiles; t += gridDim.x) {
@@ -583,7 +583,10 @@ __global__ void __launch_bounds__(1024) loop_schedule_kernel(int li, LoopCtl* ct
             d.has_prev = 1;
             d.taken = sreq[id] >> 1;
         } else {
+            // not this loop's to serve: no tile and no binning pass may touch
+            // the session's buffers (the loop that claimed it is using them)
             it.tiles_x = 0;
+            it.raster = 0;
             if (claimed) {
                 __threadfence();
                 atomicExch(&d.busy, 0u);
