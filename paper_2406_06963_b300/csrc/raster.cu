@@ -8,7 +8,7 @@
 namespace dhr {
 namespace {
 
-__global__ void __launch_bounds__(kChunk) bin_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
+__global__ void __launch_bounds__(kChunk, 8) bin_kernel(SceneView sc, RasterConsts rc, BinLayout b) {
     bin_chunk(sc, rc, b, blockIdx.x);
 }
 
