@@ -394,7 +394,7 @@ typedef struct dhr_svgf_tape dhr_svgf_tape;
 
 /* Recording space for F frames of W x H (FP32): per frame the temporal
  * output, moments and history lengths (33 B/px), plus work buffers
- * (264 B/px).  The first forward with L >= 1 levels (or more levels than
+ * (184 B/px).  The first forward with L >= 1 levels (or more levels than
  * before) adds per frame the inputs of levels 1..L-1, the weight sums of
  * every level and the last level's output, 24 L + 16 B/px per frame (kept
  * with the tape until it is destroyed).  Errors: DHR_ERR_INVALID (size
