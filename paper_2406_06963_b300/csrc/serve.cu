@@ -573,7 +573,8 @@ __global__ void __launch_bounds__(1024) loop_schedule_kernel(int li, LoopCtl* ct
         it.m_tgt = sl.m_tgt;
         it.fin_ao = sl.fin_ao;
         it.fin_sh = sl.fin_sh;
-        it.raster = (uint64_t)sl.w * sl.h >= meta->raster_min_px &&
+        // (the tile layout follows the camera's size, which must be the session's)
+        it.raster = (uint64_t)sl.w * sl.h >= meta->raster_min_px && cam.width == sl.w && cam.height == sl.h &&
                     make_raster(cam, it.g_cur, it.m_cur, 4, it.rc, it.bl);
         __threadfence_system();
         valid = valid && ld_acquire_sys(&m.seq) == sreq[id] && ld_acquire_sys(&sl.generation) == sgen[id];
