@@ -47,11 +47,14 @@ def _planes(a):          # [F, H, W, 2] -> [F, 2, H, W]
     return np.ascontiguousarray(np.moveaxis(a, -1, 1))
 
 
-@pytest.mark.parametrize("levels,wl_in", [(5, True), (2, True), (3, False), (0, True)])
-def test_adjoint_matches_oracle(levels, wl_in):
+@pytest.mark.parametrize("levels,wl_in,sigma_n", [(5, True, 128.0), (2, True, 128.0), (3, False, 128.0),
+                                                   (0, True, 128.0), (3, True, 32.0), (2, False, 0.0)])
+def test_adjoint_matches_oracle(levels, wl_in, sigma_n):
+    """sigma_n 128 takes the kernels' power-of-two normal weight; 32 and 0
+    (no normal term) the general one."""
     W, H, F = 64, 40, 6
     zn, mesh, cams, sig, g_out = _inputs(W, H, F)
-    op = orc.SvgfParams(levels=levels, wl_in_atrous=wl_in)
+    op = orc.SvgfParams(levels=levels, wl_in_atrous=wl_in, sigma_n=sigma_n)
     out_o, gsig_o, gsigma_o = orc.svgf_seq_grad(zn, mesh, cams, sig, op, g_out)
     gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
     gp = dhrs.SvgfParams(**op.__dict__)
