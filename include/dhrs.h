@@ -542,6 +542,25 @@ dhr_status dhr_session_get_frame(dhr_session* session, dhr_gbuffer* gbuf,
 /* Drops the SVGF history: the next frame starts without history. */
 dhr_status dhr_session_reset(dhr_session* session);
 
+/* Checkpoint / resume of a session's history (the state a next frame
+ * reads: the current G-buffer and mesh ids, the SVGF colour history, the
+ * moments and history lengths written last, the previous camera).  The
+ * checkpoint is a host byte image: a header (format tag, version, size,
+ * precision, camera) then those buffers, (20 + 25) B/px in FP32 and
+ * (12 + 21) B/px in the 16-bit form, plus the header.
+ * dhr_session_checkpoint_bytes: its size (0 for a null session).
+ * dhr_session_export: copies it into dst (host memory, `size` bytes at
+ * least) after the session's last frame, using `stream`; returns when the
+ * copy is complete.  dhr_session_import: restores a checkpoint into a
+ * session of the same size and precision (waiting for the session's own
+ * work first); the next dhr_step_frame then continues exactly as the
+ * exported session would have, given the same parameters and cameras.
+ * Errors: DHR_ERR_INVALID (null pointer, buffer too small, not a checkpoint
+ * of this format, another size or precision), DHR_ERR_CUDA. */
+uint64_t dhr_session_checkpoint_bytes(const dhr_session* session);
+dhr_status dhr_session_export(dhr_session* session, void* dst, uint64_t size, void* stream);
+dhr_status dhr_session_import(dhr_session* session, const void* src, uint64_t size, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Serving: many thin-client sessions with continuous batching             */
 /* (Section 1 and Section 4.1 describe one remote server per client and    */

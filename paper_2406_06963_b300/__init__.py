@@ -130,6 +130,9 @@ _SIGNATURES = {
     "dhr_session_wait": ([_P, C.c_uint64], C.c_int),
     "dhr_session_get_frame": ([_P, _P, _P, _P], C.c_int),
     "dhr_session_reset": ([_P], C.c_int),
+    "dhr_session_checkpoint_bytes": ([_P], C.c_uint64),
+    "dhr_session_export": ([_P, _P, C.c_uint64, _P], C.c_int),
+    "dhr_session_import": ([_P, _P, C.c_uint64, _P], C.c_int),
     "dhr_shadow_map_create": ([_P, _P, C.c_int32, _P, _P], C.c_int),
     "dhr_shadow_map_destroy": ([_P], None),
     "dhr_shadow_map_get_info": ([_P, _P], C.c_int),
@@ -582,6 +585,19 @@ class Session:
         m, a = C.c_void_p(), C.c_void_p()
         _check(lib().dhr_session_get_frame(self.h, C.byref(g), C.byref(m), C.byref(a)))
         return dict(depth_normal=g.depth_normal, mesh=g.mesh_id, mask=m.value, ao=a.value)
+
+    def checkpoint(self, stream=None) -> np.ndarray:
+        """The session's history as a host byte image (dhr_session_export)."""
+        n = int(lib().dhr_session_checkpoint_bytes(self.h))
+        buf = np.empty(n, np.uint8)
+        _check(lib().dhr_session_export(self.h, buf.ctypes.data_as(C.c_void_p), n, _stream(stream)))
+        return buf
+
+    def restore(self, image: np.ndarray, stream=None):
+        """Continue from a checkpoint of a session of the same size and
+        precision (dhr_session_import)."""
+        image = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(lib().dhr_session_import(self.h, image.ctypes.data_as(C.c_void_p), int(image.size), _stream(stream)))
 
     def reset(self):
         _check(lib().dhr_session_reset(self.h))

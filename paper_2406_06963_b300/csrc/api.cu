@@ -35,6 +35,8 @@ __global__ void debug_selftest_kernel(const int* buf, int* out) { out[0] = buf[d
 
 dhr_status svgf_create(int32_t w, int32_t h, dhr_precision prec, dhr_svgf_state** out);
 void svgf_free(dhr_svgf_state* s);
+uint64_t svgf_history_bytes(const dhr_svgf_state* s);
+dhr_status svgf_history_copy(dhr_svgf_state* s, void* h, bool to_host, cudaStream_t st);
 dhr_status svgf_run(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev, const dhr_camera* cam,
                     const dhr_camera* cam_prev, const uint8_t* mask, const uint8_t* ao,
                     const dhr_svgf_params* prm, float* ao_out, float* sh_out, cudaStream_t st);
@@ -412,6 +414,88 @@ extern "C" dhr_status dhr_session_get_frame(dhr_session* s, dhr_gbuffer* gbuf, u
     if (gbuf) *gbuf = session_gbuf(s, s->cur);
     if (shadow_mask) *shadow_mask = s->mask[s->cur];
     if (ao_count) *ao_count = s->ao[s->cur];
+    return DHR_OK;
+}
+
+// ------------------------------------------------------- checkpoint / resume
+// Header of a session checkpoint; the buffers follow it: the current
+// G-buffer (depth_normal, then mesh ids) and the SVGF history (colour
+// history, moments, history lengths).
+struct CheckpointHeader {
+    uint32_t magic, version;
+    int32_t width, height;
+    int32_t precision, has_prev;
+    dhr_camera cam_prev;
+    uint64_t bytes;          // the whole checkpoint, header included
+};
+constexpr uint32_t kCheckpointMagic = 0x43524844u;   // "DHRC"
+
+static uint64_t checkpoint_bytes(const dhr_session* s) {
+    const uint64_t n = (uint64_t)s->w * s->h;
+    return sizeof(CheckpointHeader) + n * ((s->prec == DHR_FP16 ? 8 : 16) + 4) + svgf_history_bytes(s->svgf);
+}
+
+extern "C" uint64_t dhr_session_checkpoint_bytes(const dhr_session* s) { return s ? checkpoint_bytes(s) : 0; }
+
+extern "C" dhr_status dhr_session_export(dhr_session* s, void* dst, uint64_t size, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(s && dst, "session_export: null pointer");
+    const uint64_t need = checkpoint_bytes(s);
+    DHR_CHECK_ARG(size >= need, "session_export: %llu bytes given, %llu needed", (unsigned long long)size,
+                  (unsigned long long)need);
+    cudaStream_t st = as_stream(stream);
+    // the last frame's filter (which follows its trace) has written the history
+    DHR_CUDA_TRY(cudaStreamWaitEvent(st, s->filtered[s->cur], 0));
+    CheckpointHeader hd{};
+    hd.magic = kCheckpointMagic;
+    hd.version = 1;
+    hd.width = s->w;
+    hd.height = s->h;
+    hd.precision = (int32_t)s->prec;
+    hd.has_prev = s->has_prev ? 1 : 0;
+    hd.cam_prev = s->cam_prev;
+    hd.bytes = need;
+    memcpy(dst, &hd, sizeof(hd));
+    char* p = static_cast<char*>(dst) + sizeof(hd);
+    const size_t n = (size_t)s->w * s->h, gb = s->prec == DHR_FP16 ? 8 : 16;
+    DHR_CUDA_TRY(cudaMemcpyAsync(p, s->gdn[s->cur], n * gb, cudaMemcpyDeviceToHost, st));
+    p += n * gb;
+    DHR_CUDA_TRY(cudaMemcpyAsync(p, s->gmesh[s->cur], n * 4, cudaMemcpyDeviceToHost, st));
+    p += n * 4;
+    DHR_TRY(svgf_history_copy(s->svgf, p, true, st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_session_import(dhr_session* s, const void* src, uint64_t size, void* stream) {
+    clear_error();
+    DHR_CHECK_ARG(s && src, "session_import: null pointer");
+    DHR_CHECK_ARG(size >= sizeof(CheckpointHeader), "session_import: %llu bytes is no checkpoint",
+                  (unsigned long long)size);
+    CheckpointHeader hd;
+    memcpy(&hd, src, sizeof(hd));
+    DHR_CHECK_ARG(hd.magic == kCheckpointMagic && hd.version == 1, "session_import: not a session checkpoint");
+    DHR_CHECK_ARG(hd.width == s->w && hd.height == s->h && hd.precision == (int32_t)s->prec,
+                  "session_import: checkpoint of a %dx%d session (precision %d), this one is %dx%d (%d)",
+                  hd.width, hd.height, hd.precision, s->w, s->h, (int)s->prec);
+    const uint64_t need = checkpoint_bytes(s);
+    DHR_CHECK_ARG(hd.bytes == need && size >= need, "session_import: checkpoint of %llu bytes, %llu expected",
+                  (unsigned long long)hd.bytes, (unsigned long long)need);
+    cudaStream_t st = as_stream(stream);
+    // nothing of the session may still read or write the buffers
+    DHR_CUDA_TRY(cudaStreamSynchronize(s->trace_st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(s->svgf_st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(s->copy_st));
+    const char* p = static_cast<const char*>(src) + sizeof(hd);
+    const size_t n = (size_t)s->w * s->h, gb = s->prec == DHR_FP16 ? 8 : 16;
+    DHR_CUDA_TRY(cudaMemcpyAsync(s->gdn[s->cur], p, n * gb, cudaMemcpyHostToDevice, st));
+    p += n * gb;
+    DHR_CUDA_TRY(cudaMemcpyAsync(s->gmesh[s->cur], p, n * 4, cudaMemcpyHostToDevice, st));
+    p += n * 4;
+    DHR_TRY(svgf_history_copy(s->svgf, const_cast<char*>(p), false, st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    s->cam_prev = hd.cam_prev;
+    s->has_prev = hd.has_prev != 0;
     return DHR_OK;
 }
 

@@ -144,6 +144,27 @@ static dhr_status run_svgf(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_
     return DHR_OK;
 }
 
+// The history a next frame reads: colour history, the moments and history
+// lengths written last.  Bytes per pixel, and a copy to (to_host) or from
+// host memory `h` laid out in that order, enqueued on st.
+uint64_t svgf_history_bytes(const dhr_svgf_state* s) {
+    const uint64_t n = (uint64_t)s->w * s->h;
+    return n * (8 + (s->prec == DHR_FP16 ? sizeof(Mom16) : 16) + 1);
+}
+
+dhr_status svgf_history_copy(dhr_svgf_state* s, void* h, bool to_host, cudaStream_t st) {
+    const size_t n = (size_t)s->w * s->h;
+    const size_t sizes[3] = {n * 8, n * (s->prec == DHR_FP16 ? sizeof(Mom16) : 16), n};
+    void* dev[3] = {s->col, s->mom[s->cur], s->hist[s->cur]};
+    char* hp = static_cast<char*>(h);
+    for (int i = 0; i < 3; ++i) {
+        if (to_host) DHR_CUDA_TRY(cudaMemcpyAsync(hp, dev[i], sizes[i], cudaMemcpyDeviceToHost, st));
+        else DHR_CUDA_TRY(cudaMemcpyAsync(dev[i], hp, sizes[i], cudaMemcpyHostToDevice, st));
+        hp += sizes[i];
+    }
+    return DHR_OK;
+}
+
 dhr_status svgf_run(dhr_svgf_state* s, const dhr_gbuffer* cur, const dhr_gbuffer* prev, const dhr_camera* cam,
                     const dhr_camera* cam_prev, const uint8_t* mask, const uint8_t* ao,
                     const dhr_svgf_params* prm, float* ao_out, float* sh_out, cudaStream_t st) {

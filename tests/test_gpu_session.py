@@ -138,3 +138,41 @@ def test_step_frame_sequence_matches_oracle():
         assert e[ok].max() <= 1e-3, (f, float(e[ok].max()))
         checked += int(ok.sum())
     assert checked >= 0.9 * W * H * len(cams)
+
+
+@pytest.mark.parametrize("precision", [dhrs.DHR_FP32, dhrs.DHR_FP16])
+def test_checkpoint_resume_continues_exactly(precision):
+    """A session exported after three frames and imported into a fresh
+    session continues bit for bit as the original does (same cameras and
+    parameters); a checkpoint of another size or a damaged one is refused."""
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    W, H = 160, 96
+    cams = wl.orbit_path(6, W, H, degrees=8.0)
+    a = dhrs.Session(sc, W, H, precision)
+    o = [torch.empty((H, W), device="cuda") for _ in range(4)]
+    for f in range(3):
+        a.step(cams[f], f, o[0], o[1])
+    image = a.checkpoint()
+    assert image.size == dhrs.lib().dhr_session_checkpoint_bytes(a.h)
+    b = dhrs.Session(sc, W, H, precision)
+    b.restore(image)
+    for f in range(3, 6):
+        a.step(cams[f], f, o[0], o[1])
+        b.step(cams[f], f, o[2], o[3])
+        torch.cuda.synchronize()
+        assert torch.equal(o[0], o[2]) and torch.equal(o[1], o[3]), f
+    # a fresh session without the checkpoint differs (the history matters)
+    c = dhrs.Session(sc, W, H, precision)
+    c.step(cams[5], 5, o[2], o[3])
+    torch.cuda.synchronize()
+    assert not torch.equal(o[0], o[2])
+    other = dhrs.Session(sc, W + 8, H, precision)
+    with pytest.raises(dhrs.DhrError):
+        other.restore(image)
+    bad = image.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(dhrs.DhrError):
+        b.restore(bad)
+    with pytest.raises(dhrs.DhrError):
+        b.restore(image[:100])
