@@ -153,6 +153,42 @@ def test_server_admission_by_memory_budget():
     srv.close_session(small)
 
 
+def test_server_session_closed_mid_flight():
+    """A client that disconnects while its frame is in flight: the batch
+    completes, the session's memory is released after it (not before), the
+    request that was still queued for it is reported as dropped, and the
+    other session of the batch is served as if alone."""
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    A = (128, 96, wl.orbit_path(3, 128, 96, degrees=6.0))
+    B = (96, 64, wl.orbit_path(3, 96, 64, degrees=9.0, start_deg=40))
+    alone, _ = _run_server(sc, [B], 2)
+    srv = dhrs.Server(sc, 1 << 30)
+    a, b = srv.open(A[0], A[1]), srv.open(B[0], B[1])
+    used_two = srv.stats()["used_bytes"]
+    srv.submit(a, A[2][0], 0, dhrs.now_ns(), 10)
+    srv.submit(b, B[2][0], 0, dhrs.now_ns(), 20)
+    assert srv.pump() == 2
+    srv.submit(a, A[2][1], 1, dhrs.now_ns(), 11)      # queued behind the frame in flight
+    srv.close_session(a)                              # disconnects mid-flight
+    done = []
+    while len(done) < 3:
+        done += srv.poll(wait=True)
+    by_id = {d["request_id"]: d for d in done}
+    assert by_id[11]["dropped"] and not by_id[20]["dropped"]
+    st = srv.stats()
+    assert st["open_sessions"] == 1 and st["used_bytes"] < used_two
+    got = srv.output(b, B[0], B[1])
+    assert np.array_equal(got[0], alone[0][0][0]) and np.array_equal(got[1], alone[0][0][1])
+    srv.submit(b, B[2][1], 1, dhrs.now_ns(), 21)      # the server goes on
+    assert srv.pump() == 1
+    done = srv.poll(wait=True)
+    while not any(d["request_id"] == 21 for d in done):
+        done += srv.poll(wait=True)
+    got = srv.output(b, B[0], B[1])
+    assert np.array_equal(got[0], alone[0][1][0]) and np.array_equal(got[1], alone[0][1][1])
+
+
 def test_server_latest_request_wins():
     s = wl.scene_boxes()
     sc = dhrs.Scene(s)
