@@ -18,8 +18,9 @@ LIB_DEBUG = os.path.join(HERE, "libdhrs_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xptxas", "-warn-spills", "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+OBJ_DIR = os.path.join(HERE, "_build")   # per-source objects (git-ignored)
 
 
 def sources():
@@ -38,10 +39,26 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
         t = os.path.getmtime(lib)
         if all(os.path.getmtime(f) <= t for f in _inputs()):
             return lib
-    cmd = ["nvcc", *ARCH, *FLAGS, *(["-DDHR_DEBUG"] if debug else []), *sources(), "-o", lib]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+    # every source compiles to its own object in parallel (each translation
+    # unit carries its own device code), then one link
+    from concurrent.futures import ThreadPoolExecutor
+    tag = "debug" if debug else "release"
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    extra = (["-DDHR_DEBUG"] if debug else []) + (["-Xptxas=-v"] if verbose else [])
+    objs = [os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + "." + tag + ".o") for src in sources()]
+
+    def compile_one(src_obj):
+        src, obj = src_obj
+        return subprocess.run(["nvcc", *ARCH, *FLAGS, *extra, "-c", src, "-o", obj], capture_output=True, text=True)
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(objs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, zip(sources(), objs)))
+    for src, r in zip(sources(), results):
+        if r.stdout or r.stderr:
+            sys.stderr.write(r.stdout + r.stderr)
+        if r.returncode != 0:
+            raise subprocess.CalledProcessError(r.returncode, "nvcc " + src)
+    subprocess.run(["nvcc", *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", lib], check=True)
     return lib
 
 
