@@ -584,30 +584,51 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
         ref.append(a2.float() / 255.0)
     sig = torch.stack(sig).contiguous()
     ref = torch.stack(ref)
-    tape = dhrs.SvgfTape(W, H, frames)
     p = dhrs.SvgfParams()
-    out = tape.forward(gbufs, cams, sig, p)
-    g_out = torch.zeros_like(out)
-    g_out[:, 0] = 2 * (out[:, 0] - ref)
-    tape.backward(gbufs, cams, sig, p, g_out)
-    torch.cuda.synchronize()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    e[0].record()
-    out = tape.forward(gbufs, cams, sig, p)
-    e[1].record()
-    g_out[:, 0] = 2 * (out[:, 0] - ref)
-    tape.backward(gbufs, cams, sig, p, g_out)
-    e[2].record()
-    torch.cuda.synchronize()
-    fwd, bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    g_out = torch.zeros_like(sig)
+
+    def time_fb(tape, reps=3):
+        """median forward and backward times (ms) of `reps` runs after one warm-up"""
+        out = tape.forward(gbufs, cams, sig, p)
+        g_out[:, 0] = 2 * (out[:, 0] - ref)
+        tape.backward(gbufs, cams, sig, p, g_out)
+        torch.cuda.synchronize()
+        fw, bw = [], []
+        for _ in range(reps):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            out = tape.forward(gbufs, cams, sig, p)
+            e[1].record()
+            g_out[:, 0] = 2 * (out[:, 0] - ref)
+            tape.backward(gbufs, cams, sig, p, g_out)
+            e[2].record()
+            torch.cuda.synchronize()
+            fw.append(e[0].elapsed_time(e[1]))
+            bw.append(e[1].elapsed_time(e[2]))
+        return statistics.median(fw), statistics.median(bw)
+
+    # the stored schedule first, then the default (levels recomputed by the
+    # backward), whose tape the fit below uses
+    tape_s = dhrs.SvgfTape(W, H, frames, dhrs.TAPE_STORE)
+    fwd_s, bwd_s = time_fb(tape_s)
+    rec_bytes_s = tape_s.level_bytes(p.levels)
+    tape_s.close()
+    tape = dhrs.SvgfTape(W, H, frames, dhrs.TAPE_RECOMPUTE)
+    fwd, bwd = time_fb(tape)
     # algorithmic bytes per pixel and frame (each buffer read or written once
     # per kernel): forward 340 as the SVGF frame + the records (weight sums
     # 8 per level, last output 16); backward per level pass A 176 (input 16,
     # G-buffer 16, weight sums 8, output 16, upstream gradient 16, sigma
     # terms 32 read + written, records 64 written) and pass B 112 (records
-    # 64, input 16, G-buffer 16, gradient 16 written), temporal backward 180
-    bytes_fwd = frames * W * H * (340 + 5 * 8 + 16)
-    bytes_bwd = frames * W * H * (5 * (176 + 112) + 180)
+    # 64, input 16, G-buffer 16, gradient 16 written), temporal backward 180;
+    # recomputing the levels of every frame but the last: the forward's five
+    # levels (56 + 3 x 48 + 40) + their records (5 x 8 + 16) = 296
+    L = p.levels
+    px = W * H
+    bwd_px = L * (176 + 112) + 180
+    bytes_fwd = frames * px * (340 + L * 8 + 16)
+    bytes_bwd = frames * px * bwd_px + (frames - 1) * px * 296
+    bytes_bwd_s = frames * px * bwd_px
     bytes_fb = bytes_fwd + bytes_bwd
     log_s = torch.tensor([0.0, 4.852, 1.386], device="cuda").requires_grad_(True)  # log(1, 128, 4)
     opt = torch.optim.Adam([log_s], lr=0.05)
@@ -621,12 +642,18 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
         losses.append(round(float(loss.detach()), 6))
     peak = _peaks()[0].get("hbm_gbs")
     gbs_b = bytes_bwd / (bwd * 1e-3) / 1e9
+    gbs_bs = bytes_bwd_s / (bwd_s * 1e-3) / 1e9
     traffic = {k: _traffic(k) for k in ("atrous_bwd_a", "atrous_bwd_b", "temporal_bwd_kernel")}
-    return {"workload": f"{frames} frames x {W}x{H}, terrain776k", "forward_ms": round(fwd, 3),
-            "backward_ms": round(bwd, 3), "algorithmic_gb_per_s": round(bytes_fb / ((fwd + bwd) * 1e-3) / 1e9, 1),
+    return {"workload": f"{frames} frames x {W}x{H}, terrain776k", "schedule": "levels recomputed",
+            "forward_ms": round(fwd, 3), "backward_ms": round(bwd, 3),
+            "level_record_bytes": tape.level_bytes(L),
+            "algorithmic_gb_per_s": round(bytes_fb / ((fwd + bwd) * 1e-3) / 1e9, 1),
             "backward_algorithmic_gb_per_s": round(gbs_b, 1),
             "backward_frac_hbm": round(gbs_b / peak, 4) if peak else None,
-            "backward_bytes_per_px_frame": 5 * (176 + 112) + 180,
+            "backward_bytes_per_px_frame": bwd_px, "recompute_bytes_per_px_frame": 296,
+            "stored_levels": {"forward_ms": round(fwd_s, 3), "backward_ms": round(bwd_s, 3),
+                              "level_record_bytes": rec_bytes_s,
+                              "backward_frac_hbm": round(gbs_bs / peak, 4) if peak else None},
             "ncu_dram_bytes_per_launch": traffic,
             "l2_vs_255spp_fit": losses, "sigmas_after_fit": [round(float(v), 4) for v in log_s.detach().exp()]}
 

@@ -392,24 +392,49 @@ dhr_status dhr_debug_selftest(void* stream);
 /* ---------------------------------------------------------------------- */
 typedef struct dhr_svgf_tape dhr_svgf_tape;
 
+/* Schedules of the a-trous level records (dhr_svgf_tape_set_schedule).
+ * RECOMPUTE (the default): the records of two frames are kept (frame f in
+ * slot f mod 2); the forward leaves the last two frames' there and the
+ * backward recomputes each earlier frame's L levels from that frame's
+ * stored temporal output, on a stream of the tape's own, while the adjoint
+ * of the frame after it runs (L more a-trous launches per earlier frame;
+ * the call orders the tape's stream after `stream` on entry and `stream`
+ * after it on return).
+ * STORE: the forward keeps the records of every frame and the backward
+ * recomputes nothing.  The a-trous levels are deterministic, so the
+ * recomputed records equal the stored ones bit for bit. */
+#define DHR_TAPE_RECOMPUTE 0
+#define DHR_TAPE_STORE 1
+
 /* Recording space for F frames of W x H (FP32): per frame the temporal
  * output, moments and history lengths (33 B/px), plus work buffers
  * (184 B/px).  The first forward with L >= 1 levels (or more levels than
- * before) adds per frame the inputs of levels 1..L-1, the weight sums of
- * every level and the last level's output, 24 L + 16 B/px per frame (kept
- * with the tape until it is destroyed).  Errors: DHR_ERR_INVALID (size
- * outside 1..2^27 pixels, frames outside 1..1024), DHR_ERR_OOM. */
+ * before, or after a schedule change) adds the level records: the inputs of
+ * levels 1..L-1, the weight sums of every level and the last level's
+ * output, 24 L + 16 B/px for each of two frames (RECOMPUTE; one if F = 1)
+ * or of the F frames (STORE), kept with the tape until it is destroyed.
+ * Errors: DHR_ERR_INVALID (size outside 1..2^27 pixels, frames outside
+ * 1..1024), DHR_ERR_OOM. */
 dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_t frames, dhr_svgf_tape** out);
 void dhr_svgf_tape_destroy(dhr_svgf_tape* tape);
+/* Selects the record schedule (DHR_TAPE_RECOMPUTE or DHR_TAPE_STORE).  A
+ * change discards the last forward's records (the next backward needs a new
+ * forward).  Errors: DHR_ERR_INVALID (null tape, unknown schedule). */
+dhr_status dhr_svgf_tape_set_schedule(dhr_svgf_tape* tape, int32_t schedule);
+/* Bytes of level records a forward with `levels` levels holds under the
+ * tape's current schedule (0 for levels == 0).  Errors: DHR_ERR_INVALID
+ * (null pointer, levels outside 0..8). */
+dhr_status dhr_svgf_tape_level_bytes(const dhr_svgf_tape* tape, int32_t levels, int64_t* bytes);
 
 /* Forward over F consecutive frames starting without history, recording
  * into `tape`.  gbufs, cams: host arrays of F FP32 G-buffer descriptors and
  * cameras (the G-buffers are device memory and must stay unchanged until
  * the backward call).  sig (device, float [F][2][H][W]): noisy AO and
  * shadow signals in [0, 1] (planes).  out (device, float [F][2][H][W]):
- * filtered AO and shadow.  Records every a-trous level's input for the
- * backward.  Errors: DHR_ERR_INVALID (mismatched G-buffers or cameras,
- * a 3x3 kernel, FP16 G-buffers), DHR_ERR_OOM (level records). */
+ * filtered AO and shadow.  Keeps every frame's temporal output and the
+ * level records its schedule asks for.  Errors: DHR_ERR_INVALID
+ * (mismatched G-buffers or cameras, a 3x3 kernel, FP16 G-buffers, levels
+ * above 8), DHR_ERR_OOM (level records). */
 dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, const dhr_camera* cams,
                                 const float* sig, const dhr_svgf_params* params, float* out,
                                 void* stream);
@@ -418,7 +443,9 @@ dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* tape, const dhr_gbuffer* gbufs, c
  * g_out (device, [F][2][H][W]) = dL/d out.  Writes g_sig (device,
  * [F][2][H][W]) = dL/d sig and g_sigma (device, float [3]) = dL/d
  * (sigma_z, sigma_n, sigma_l).  It reads the forward's records (temporal
- * outputs and level inputs), so sig and params must be the forward's.  The
+ * outputs, and level records, recomputed from the temporal outputs under
+ * DHR_TAPE_RECOMPUTE), so gbufs, cams, sig and params must be the
+ * forward's; it may run more than once after one forward.  The
  * history scatter and the short-history variance estimate accumulate with
  * atomics (summation order may vary); dL/d sigma is summed per pixel in
  * binary32 over levels and frames, then over pixels in double in a fixed

@@ -23,6 +23,7 @@ DHR_FP32, DHR_FP16 = 0, 1
 BACKGROUND = 0xFFFFFFFF
 MAX_LIGHTS = 8
 PRIMARY_RASTER, PRIMARY_TRAVERSE = 0, 1
+TAPE_RECOMPUTE, TAPE_STORE = 0, 1
 STATUS = {0: "DHR_OK", 1: "DHR_ERR_INVALID", 2: "DHR_ERR_OOM", 3: "DHR_ERR_CUDA",
           4: "DHR_ERR_TIMEOUT", 5: "DHR_ERR_ADMISSION", 6: "DHR_ERR_STATE"}
 
@@ -99,6 +100,8 @@ _SIGNATURES = {
     "dhr_svgf_atrous_noalloc": ([_P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_svgf_tape_create": ([C.c_int32, C.c_int32, C.c_int32, _P], C.c_int),
     "dhr_svgf_tape_destroy": ([_P], None),
+    "dhr_svgf_tape_set_schedule": ([_P, C.c_int32], C.c_int),
+    "dhr_svgf_tape_level_bytes": ([_P, C.c_int32, _P], C.c_int),
     "dhr_svgf_seq_forward": ([_P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_svgf_seq_backward": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "dhr_delay_warp": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], C.c_int),
@@ -616,12 +619,27 @@ class Session:
 
 # --------------------------------------------------------------- adjoint
 class SvgfTape:
-    """Recording of the differentiable SVGF over F frames (FP32)."""
+    """Recording of the differentiable SVGF over F frames (FP32).
 
-    def __init__(self, width, height, frames):
+    schedule TAPE_RECOMPUTE (default): one frame of a-trous level records,
+    earlier frames' levels recomputed by the backward; TAPE_STORE: every
+    frame's level records kept by the forward."""
+
+    def __init__(self, width, height, frames, schedule=None):
         h = C.c_void_p()
         _check(lib().dhr_svgf_tape_create(width, height, frames, C.byref(h)))
         self.h, self.width, self.height, self.frames = h, width, height, frames
+        if schedule is not None:
+            self.set_schedule(schedule)
+
+    def set_schedule(self, schedule):
+        _check(lib().dhr_svgf_tape_set_schedule(self.h, int(schedule)))
+
+    def level_bytes(self, levels):
+        """Bytes of level records a forward with `levels` levels keeps."""
+        b = C.c_int64()
+        _check(lib().dhr_svgf_tape_level_bytes(self.h, int(levels), C.byref(b)))
+        return b.value
 
     @staticmethod
     def _arrays(gbufs, cams):

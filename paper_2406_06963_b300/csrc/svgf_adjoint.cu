@@ -8,9 +8,13 @@
 // frames (the temporal recursion is not cut).
 //
 // Forward (dhr_svgf_seq_forward) records per frame the temporal output
-// (colour, variance), the moments, the history lengths, the input of every
-// a-trous level after the first, every level's weight sums and the last
-// level's output.  Backward of one a-trous level is a two-pass gather:
+// (colour, variance), the moments and the history lengths.  The level
+// records a frame's adjoint reads -- the input of every a-trous level after
+// the first, every level's weight sums and the last level's output -- are
+// recomputed from the temporal output by the backward, one frame ahead on a
+// second stream (the forward leaves the last two frames' in place), or kept
+// for every frame by the forward (DHR_TAPE_STORE).  Backward of one a-trous
+// level is a two-pass gather:
 //   pass A (per output pixel p): with the level's weight sum, filtered
 //     colour and variance at p from the forward, dL/dw_pq = a1 c_q - a2 +
 //     a3 w_pq v_q is known tap by tap, so one pass over p's taps forms the
@@ -255,7 +259,7 @@ __device__ __forceinline__ float4 upstream(const Upstream& up, size_t N, int q) 
 
 // wsum: the level's weight sums [N]; xout: its filtered colour and variance [N]
 template <int kNsq, bool kLum>
-__global__ void __launch_bounds__(kThreadsA, 4) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
+__global__ void __launch_bounds__(kThreadsA, 5) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
                                                              const float2* wsum, const float4* xout, Upstream up,
                                                              float4* rec, float4* gs) {
     const int px = blockIdx.x * kBX + threadIdx.x, py = blockIdx.y * kBY + threadIdx.y;
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kThreadsA, 4) atrous_bwd_a(SvgfConsts k, int s
 // Pass B runs its tiles in the reverse of pass A's order: the records pass
 // A wrote last are the ones still in L2 when pass B starts.
 template <int kNsq>
-__global__ void __launch_bounds__(kThreadsA) atrous_bwd_b(SvgfConsts k, int step, const float4* g, const float4* x,
+__global__ void __launch_bounds__(kThreadsA, 5) atrous_bwd_b(SvgfConsts k, int step, const float4* g, const float4* x,
                                                           const float4* rec, float2* gc_in, float2* gv_in) {
     const int bx = gridDim.x - 1 - blockIdx.x, by = gridDim.y - 1 - blockIdx.y;
     const int qx = bx * kBX + threadIdx.x, qy = by * kBY + threadIdx.y;
@@ -541,11 +545,22 @@ struct dhr_svgf_tape {
     uint8_t* hist = nullptr;   // [F][N] history lengths
     float2* col = nullptr;     // [N] colour history (forward)
     float4* lev[2] = {nullptr, nullptr};
-    // recorded by the forward, allocated for `rec_levels` levels on first use:
-    float4* lvs = nullptr;     // [F][levels - 1][N] inputs of levels 1..
-    float2* wsum = nullptr;    // [F][levels][N] weight sums of every level
-    float4* last = nullptr;    // [F][N] filtered colour and variance of the last level
+    // level records, allocated for `rec_levels` levels and `rec_slots` frames
+    // on first use: one slot per frame when the forward stores every frame's
+    // levels (DHR_TAPE_STORE); otherwise (DHR_TAPE_RECOMPUTE) two slots, frame
+    // f in slot f & 1: the forward leaves the last two frames' records there
+    // and the backward recomputes frame f - 1's levels on `side` while frame
+    // f's adjoint runs
+    float4* lvs = nullptr;     // [slots][levels - 1][N] inputs of levels 1..
+    float2* wsum = nullptr;    // [slots][levels][N] weight sums of every level
+    float4* last = nullptr;    // [slots][N] filtered colour and variance of the last level
     int rec_levels = 0;
+    int rec_slots = 0;
+    int schedule = DHR_TAPE_RECOMPUTE;
+    int slot_frame[2] = {-1, -1};   // DHR_TAPE_RECOMPUTE: the frame whose records a slot holds
+    cudaStream_t side = nullptr;    // recompute stream
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ready[2] = {nullptr, nullptr},
+                ev_free[2] = {nullptr, nullptr};
     float2* gcol[2] = {nullptr, nullptr};
     float4* gmom[2] = {nullptr, nullptr};
     float2* gc = nullptr;      // [N] dL/d colour at the input of the level just processed
@@ -582,6 +597,9 @@ static void tape_free(dhr_svgf_tape* t) {
     cudaFree(t->last);
     cudaFree(t->partial);
     cudaFree(t->acc);
+    for (cudaEvent_t e : {t->ev_fork, t->ev_join, t->ev_ready[0], t->ev_ready[1], t->ev_free[0], t->ev_free[1]})
+        if (e) cudaEventDestroy(e);
+    if (t->side) cudaStreamDestroy(t->side);
     delete t;
 }
 
@@ -614,6 +632,10 @@ extern "C" dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_
     if (!e) e = cudaMalloc((void**)&t->gs, n * 16);
     if (!e) e = cudaMalloc((void**)&t->partial, (size_t)kPixReduceBlocks * 3 * sizeof(float));
     if (!e) e = cudaMalloc((void**)&t->acc, 3 * sizeof(double));
+    if (!e) e = cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&t->ev_fork, &t->ev_join, &t->ev_ready[0], &t->ev_ready[1], &t->ev_free[0],
+                            &t->ev_free[1]})
+        if (!e) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e) {
         cudaGetLastError();
         tape_free(t);
@@ -638,6 +660,88 @@ static dhr_status check_seq(const dhr_svgf_tape* t, const dhr_gbuffer* g, const 
     return DHR_OK;
 }
 
+// Level records of one frame in slot `slot`: input of level l (l >= 1),
+// output of level l, weight sums of level l.
+struct LevelSlot {
+    const dhr_svgf_tape* t;
+    size_t N;
+    int L, slot;
+    float4* in(int l, const float4* illum) const {
+        return l == 0 ? const_cast<float4*>(illum) : t->lvs + ((size_t)slot * (L - 1) + (l - 1)) * N;
+    }
+    float4* out(int l) const {
+        return l + 1 < L ? t->lvs + ((size_t)slot * (L - 1) + l) * N : t->last + (size_t)slot * N;
+    }
+    float2* wsum(int l) const { return t->wsum + ((size_t)slot * L + l) * N; }
+};
+
+static int level_slots(const dhr_svgf_tape* t) {
+    return t->schedule == DHR_TAPE_STORE ? t->F : (t->F < 2 ? t->F : 2);
+}
+
+static dhr_status alloc_level_records(dhr_svgf_tape* t, int L, size_t N) {
+    const int slots = level_slots(t);
+    if (L <= t->rec_levels && slots == t->rec_slots) return DHR_OK;
+    cudaFree(t->lvs);
+    cudaFree(t->wsum);
+    cudaFree(t->last);
+    t->lvs = nullptr;
+    t->wsum = nullptr;
+    t->last = nullptr;
+    t->rec_levels = 0;
+    t->rec_slots = 0;
+    t->slot_frame[0] = t->slot_frame[1] = -1;
+    cudaError_t e = cudaSuccess;
+    if (L > 1) e = cudaMalloc((void**)&t->lvs, (size_t)slots * (L - 1) * N * 16);
+    if (!e) e = cudaMalloc((void**)&t->wsum, (size_t)slots * L * N * 8);
+    if (!e) e = cudaMalloc((void**)&t->last, (size_t)slots * N * 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
+                         "svgf_seq_forward: level records: %s", cudaGetErrorString(e));
+    }
+    t->rec_levels = L;
+    t->rec_slots = slots;
+    return DHR_OK;
+}
+
+// The L recorded a-trous levels of one frame (Section 3.3's filter with the
+// weight sums kept): level 0 writes the colour history `col`, the last level
+// (L >= 2) the planes ao / sh; with L == 1 the single level's output is the
+// slot's last-level record.  col == nullptr: the records only (a recompute).
+static dhr_status run_levels(const SvgfConsts& k, int nsq, cudaStream_t st, const float4* g, const float4* illum,
+                             const LevelSlot& s, float2* col, float* ao, float* sh) {
+    for (int l = 0; l < s.L; ++l) {
+        const int mode = (l == s.L - 1 && s.L > 1) ? 2 : (l == 0 && col ? 1 : 0);
+        DHR_TRY(launch_atrous_recorded(mode, nsq, st, k, 1 << l, g, s.in(l, illum), s.out(l), col, ao, sh,
+                                       AtrousRec{s.wsum(l), s.t->last + (size_t)s.slot * s.N}));
+    }
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_svgf_tape_set_schedule(dhr_svgf_tape* t, int32_t schedule) {
+    clear_error();
+    DHR_CHECK_ARG(t, "svgf_tape_set_schedule: null tape");
+    DHR_CHECK_ARG(schedule == DHR_TAPE_RECOMPUTE || schedule == DHR_TAPE_STORE,
+                  "svgf_tape_set_schedule: unknown schedule %d", schedule);
+    if (schedule != t->schedule) {
+        t->schedule = schedule;
+        t->frames_recorded = 0;   // the records of the last forward no longer fit the schedule
+        t->slot_frame[0] = t->slot_frame[1] = -1;
+    }
+    return DHR_OK;
+}
+
+extern "C" dhr_status dhr_svgf_tape_level_bytes(const dhr_svgf_tape* t, int32_t levels, int64_t* bytes) {
+    clear_error();
+    DHR_CHECK_ARG(t && bytes, "svgf_tape_level_bytes: null pointer");
+    DHR_CHECK_ARG(levels >= 0 && levels <= kMaxLevels, "svgf_tape_level_bytes: levels %d outside 0..%d", levels,
+                  kMaxLevels);
+    const int64_t N = (int64_t)t->W * t->H, slots = level_slots(t);
+    *bytes = levels == 0 ? 0 : slots * N * (16 * (levels - 1) + 8 * levels + 16);
+    return DHR_OK;
+}
+
 extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* gbufs, const dhr_camera* cams,
                                            const float* sig, const dhr_svgf_params* params, float* out,
                                            void* stream) {
@@ -652,26 +756,10 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
     const dim3 blk(32, 8), grid((t->W + 31) / 32, (t->H + 7) / 8);
     const int L = (int)params->levels;
     DHR_CHECK_ARG(L <= kMaxLevels, "svgf_seq_forward: levels %d > %d", L, kMaxLevels);
-    if (L > t->rec_levels) {   // level records of every frame, allocated on first use
-        cudaFree(t->lvs);
-        cudaFree(t->wsum);
-        cudaFree(t->last);
-        t->lvs = nullptr;
-        t->wsum = nullptr;
-        t->last = nullptr;
-        t->rec_levels = 0;
-        cudaError_t e = cudaSuccess;
-        if (L > 1) e = cudaMalloc((void**)&t->lvs, (size_t)t->F * (L - 1) * N * 16);
-        if (!e) e = cudaMalloc((void**)&t->wsum, (size_t)t->F * L * N * 8);
-        if (!e) e = cudaMalloc((void**)&t->last, (size_t)t->F * N * 16);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(e == cudaErrorMemoryAllocation ? DHR_ERR_OOM : DHR_ERR_CUDA,
-                             "svgf_seq_forward: level records: %s", cudaGetErrorString(e));
-        }
-        t->rec_levels = L;
-    }
     t->frames_recorded = 0;
+    t->slot_frame[0] = t->slot_frame[1] = -1;
+    if (L > 0) DHR_TRY(alloc_level_records(t, L, N));
+    const bool store = t->schedule == DHR_TAPE_STORE;
     for (int f = 0; f < t->F; ++f) {
         const bool hp = f > 0;
         const auto* gc = static_cast<const S::G*>(gbufs[f].depth_normal);
@@ -689,21 +777,17 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
             DHR_CUDA_TRY(cudaGetLastError());
             continue;
         }
-        const float4* in = illum;
-        for (int l = 0; l < L; ++l) {
-            float4* o = l + 1 < L ? t->lvs + ((size_t)f * (L - 1) + l) * N : t->lev[l & 1];
-            const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
-            const AtrousRec rec{t->wsum + ((size_t)f * L + l) * N, t->last + (size_t)f * N};
-            DHR_TRY(launch_atrous_recorded(mode, nsq, st, k, 1 << l, gc, in, o, t->col, ao, sh, rec));
-            if (L == 1) {
-                passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, o, t->col, ao, sh);
-                DHR_CUDA_TRY(cudaGetLastError());
-            }
-            in = o;
+        const LevelSlot s{t, N, L, store ? f : (f & 1)};
+        DHR_TRY(run_levels(k, nsq, st, gc, illum, s, t->col, ao, sh));
+        if (L == 1) {
+            passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, s.out(0), t->col, ao, sh);
+            DHR_CUDA_TRY(cudaGetLastError());
         }
     }
     t->frames_recorded = t->F;
     t->levels_recorded = L;
+    if (!store && L > 0)
+        for (int f = t->F - 1; f >= 0 && f >= t->F - 2; --f) t->slot_frame[f & 1] = f;
     return DHR_OK;
 }
 
@@ -726,55 +810,99 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
     const int n = (int)N;
     const dim3 blk(32, 8), grid((t->W + 31) / 32, (t->H + 7) / 8);
     const int L = (int)params->levels;
+    const bool store = t->schedule == DHR_TAPE_STORE;
     DHR_CUDA_TRY(cudaMemsetAsync(g_sig, 0, (size_t)t->F * 2 * N * sizeof(float), st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->gs, 0, N * 16, st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->acc, 0, 3 * sizeof(double), st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[0], 0, N * 8, st));
     DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[0], 0, N * 16, st));
-    int nx = 0;   // index of the "from the next frame" gradient buffers
-    for (int f = t->F - 1; f >= 0; --f) {
-        const auto* gcur = static_cast<const S::G*>(gbufs[f].depth_normal);
-        const float4* illum = t->illum + (size_t)f * N;
-        // the gradient at the output of the level being processed comes from
-        // the loss (last level) or from pass B of the level above
-        Upstream up{g_out + (size_t)f * 2 * N, nullptr, nullptr, L <= 1 ? t->gcol[nx] : nullptr};
-        for (int l = L - 1; l >= 0; --l) {
-            const float4* xin = l == 0 ? illum : t->lvs + ((size_t)f * (L - 1) + (l - 1)) * N;
-            const float4* xout = l + 1 < L ? t->lvs + ((size_t)f * (L - 1) + l) * N : t->last + (size_t)f * N;
-            const float2* ws = t->wsum + ((size_t)f * L + l) * N;
-            if (nsq == 7 && k.wl_in_atrous)
-                atrous_bwd_a<7, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
-            else if (nsq == 7)
-                atrous_bwd_a<7, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
-            else if (k.wl_in_atrous)
-                atrous_bwd_a<-1, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
-            else
-                atrous_bwd_a<-1, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+    // DHR_TAPE_RECOMPUTE: frame f's records are in slot f & 1; a frame the
+    // slots do not hold is recomputed on the side stream one frame ahead,
+    // into the slot frame f + 1's adjoint has finished with
+    const bool side = L > 0 && !store;
+    bool pending[2] = {false, false};
+    auto prefetch = [&](int f) -> dhr_status {
+        const int sl = f & 1;
+        if (t->slot_frame[sl] == f) return DHR_OK;
+        t->slot_frame[sl] = -1;
+        if (f + 2 < t->F) DHR_CUDA_TRY(cudaStreamWaitEvent(t->side, t->ev_free[sl], 0));
+        DHR_TRY(run_levels(k, nsq, t->side, static_cast<const S::G*>(gbufs[f].depth_normal), t->illum + (size_t)f * N,
+                           LevelSlot{t, N, L, sl}, nullptr, nullptr, nullptr));
+        DHR_CUDA_TRY(cudaEventRecord(t->ev_ready[sl], t->side));
+        pending[sl] = true;
+        t->slot_frame[sl] = f;
+        return DHR_OK;
+    };
+    auto frames = [&]() -> dhr_status {
+        if (side) DHR_TRY(prefetch(t->F - 1));
+        int nx = 0;   // index of the "from the next frame" gradient buffers
+        for (int f = t->F - 1; f >= 0; --f) {
+            const auto* gcur = static_cast<const S::G*>(gbufs[f].depth_normal);
+            const float4* illum = t->illum + (size_t)f * N;
+            const LevelSlot s{t, N, L, store ? f : (f & 1)};
+            if (side && f > 0) DHR_TRY(prefetch(f - 1));
+            if (side && pending[f & 1]) {
+                DHR_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_ready[f & 1], 0));
+                pending[f & 1] = false;
+            }
+            // the gradient at the output of the level being processed comes
+            // from the loss (last level) or from pass B of the level above
+            Upstream up{g_out + (size_t)f * 2 * N, nullptr, nullptr, L <= 1 ? t->gcol[nx] : nullptr};
+            for (int l = L - 1; l >= 0; --l) {
+                const float4* xin = s.in(l, illum);
+                const float4* xout = s.out(l);
+                const float2* ws = s.wsum(l);
+                if (nsq == 7 && k.wl_in_atrous)
+                    atrous_bwd_a<7, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+                else if (nsq == 7)
+                    atrous_bwd_a<7, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+                else if (k.wl_in_atrous)
+                    atrous_bwd_a<-1, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+                else
+                    atrous_bwd_a<-1, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec,
+                                                                  t->gs);
+                DHR_CUDA_TRY(cudaGetLastError());
+                if (nsq == 7)
+                    atrous_bwd_b<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
+                else
+                    atrous_bwd_b<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
+                DHR_CUDA_TRY(cudaGetLastError());
+                // level l - 1's output gradient (plus, for level 0's output,
+                // the next frame's colour-history gradient)
+                up = Upstream{nullptr, t->gc, t->gv, l == 1 ? t->gcol[nx] : nullptr};
+            }
+            if (side) DHR_CUDA_TRY(cudaEventRecord(t->ev_free[f & 1], st));   // slot f & 1 read for the last time
+            const int pv = nx ^ 1;
+            DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[pv], 0, N * 8, st));
+            DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[pv], 0, N * 16, st));
+            const bool hp = f > 0;
+            // at the temporal output: pass B of level 0, or the loss gradient
+            // plus the colour-history gradient when there are no levels
+            up.gcol = L == 0 ? t->gcol[nx] : nullptr;
+            temporal_bwd_kernel<<<grid, blk, 0, st>>>(
+                k, cams[f], hp ? cams[f - 1] : cams[f], gcur, gbufs[f].mesh_id,
+                hp ? static_cast<const S::G*>(gbufs[f - 1].depth_normal) : nullptr,
+                hp ? gbufs[f - 1].mesh_id : nullptr, sig + (size_t)f * 2 * N, t->mom + (size_t)f * N,
+                t->hist + (size_t)f * N, up, t->gmom[nx], g_sig + (size_t)f * 2 * N, t->gcol[pv], t->gmom[pv],
+                t->gs);
             DHR_CUDA_TRY(cudaGetLastError());
-            if (nsq == 7)
-                atrous_bwd_b<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
-            else
-                atrous_bwd_b<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
-            DHR_CUDA_TRY(cudaGetLastError());
-            // level l - 1's output gradient (plus, for level 0's output, the
-            // next frame's colour-history gradient)
-            up = Upstream{nullptr, t->gc, t->gv, l == 1 ? t->gcol[nx] : nullptr};
+            nx = pv;
         }
-        const int pv = nx ^ 1;
-        DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[pv], 0, N * 8, st));
-        DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[pv], 0, N * 16, st));
-        const bool hp = f > 0;
-        // at the temporal output: pass B of level 0, or the loss gradient plus
-        // the colour-history gradient when there are no levels
-        up.gcol = L == 0 ? t->gcol[nx] : nullptr;
-        temporal_bwd_kernel<<<grid, blk, 0, st>>>(
-            k, cams[f], hp ? cams[f - 1] : cams[f], gcur, gbufs[f].mesh_id,
-            hp ? static_cast<const S::G*>(gbufs[f - 1].depth_normal) : nullptr, hp ? gbufs[f - 1].mesh_id : nullptr,
-            sig + (size_t)f * 2 * N, t->mom + (size_t)f * N, t->hist + (size_t)f * N, up, t->gmom[nx],
-            g_sig + (size_t)f * 2 * N, t->gcol[pv], t->gmom[pv], t->gs);
-        DHR_CUDA_TRY(cudaGetLastError());
-        nx = pv;
+        return DHR_OK;
+    };
+    if (side) {   // the side stream starts after everything before this call on `st`
+        DHR_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+        DHR_CUDA_TRY(cudaStreamWaitEvent(t->side, t->ev_fork, 0));
     }
+    const dhr_status r = frames();
+    if (side) {   // and `st` continues after all of the side stream's work, also on an error
+        const cudaError_t e1 = cudaEventRecord(t->ev_join, t->side);
+        const cudaError_t e2 = e1 ? e1 : cudaStreamWaitEvent(st, t->ev_join, 0);
+        if (r != DHR_OK || e2) t->slot_frame[0] = t->slot_frame[1] = -1;
+        if (r != DHR_OK) return r;
+        DHR_CUDA_TRY(e2);
+    }
+    if (r != DHR_OK) return r;
     reduce_pixels_kernel<<<kPixReduceBlocks, kPixReduceThreads, 0, st>>>(n, t->gs, t->partial);
     DHR_CUDA_TRY(cudaGetLastError());
     reduce_partials_kernel<<<1, kReduceThreads, 0, st>>>(kPixReduceBlocks, t->partial, t->acc);

@@ -651,8 +651,10 @@ __device__ __forceinline__ void atrous_store(const AtrousSums& a, int p, float4*
     const float c0 = a.sc0 / a.sw0, c1 = a.sc1 / a.sw1;
     if (kRec) rec.wsum[p] = make_float2(a.sw0, a.sw1);
     if (kMode == 2) {
-        ao_out[p] = c0;
-        sh_out[p] = c1;
+        if (!kRec || ao_out) {   // a recording pass may only want the records
+            ao_out[p] = c0;
+            sh_out[p] = c1;
+        }
         if (kRec) {
             const float r0 = rcp_approx(a.sw0), r1 = rcp_approx(a.sw1);
             rec.last[p] = make_float4(c0, c1, a.sv0 * r0 * r0, a.sv1 * r1 * r1);
@@ -664,12 +666,14 @@ __device__ __forceinline__ void atrous_store(const AtrousSums& a, int p, float4*
     }
 }
 
-template <dhr_precision P, int kMode>
+template <dhr_precision P, int kMode, bool kRec = false>
 __device__ __forceinline__ void atrous_background(int p, float4* out, typename Store<P>::Col* col_hist,
                                                   float* ao_out, float* sh_out) {
     if (kMode == 2) {
-        ao_out[p] = 1.f;
-        sh_out[p] = 1.f;
+        if (!kRec || ao_out) {
+            ao_out[p] = 1.f;
+            sh_out[p] = 1.f;
+        }
     } else {
         out[p] = make_float4(1.f, 1.f, -1.f, -1.f);
         if (kMode == 1) Store<P>::put_col(col_hist, p, make_float2(1.f, 1.f));
@@ -710,7 +714,7 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
         const float4 cp = sm.c[ty][tx];
         if (inside) {
             if (!fg_var(cp.z)) {
-                atrous_background<P, kMode>(p, out, col_hist, ao_out, sh_out);
+                atrous_background<P, kMode, kRec>(p, out, col_hist, ao_out, sh_out);
             } else {
                 const float4 zn = sm.g[ty][tx];
                 float4 v[3][3];
@@ -732,7 +736,7 @@ __device__ __forceinline__ void atrous_tile(const SvgfConsts& k, int step, int t
     if (!inside) return;
     const float4 cp = __ldg(in + p);
     if (!fg_var(cp.z)) {
-        atrous_background<P, kMode>(p, out, col_hist, ao_out, sh_out);
+        atrous_background<P, kMode, kRec>(p, out, col_hist, ao_out, sh_out);
         return;
     }
     const float4 zn = S::g(g, p);
@@ -848,7 +852,8 @@ inline dhr_status launch_atrous(int mode, int nsq, int R, cudaStream_t st, const
 }
 
 // The differentiable form's forward level (binary32, 5x5): as launch_atrous,
-// plus the level's records `rec` (wsum always; last on mode 2).
+// plus the level's records `rec` (wsum always; last on mode 2).  Mode 2
+// with null ao_out / sh_out writes the records only.
 inline dhr_status launch_atrous_recorded(int mode, int nsq, cudaStream_t st, const SvgfConsts& k, int step,
                                          const float4* g, const float4* in, float4* out, float2* col, float* ao_out,
                                          float* sh_out, AtrousRec rec) {

@@ -49,6 +49,20 @@ def test_release_build_reports_itself():
     assert L.dhr_debug_status(ctypes.byref(err), ctypes.byref(dbg)) == 0   # clears the error text
 
 
+def test_binding_constants_match_header():
+    """The binding's integer constants are the header's #defines."""
+    import paper_2406_06963_b300 as dhrs
+    text = open(os.path.join(ROOT, "include", "dhrs.h")).read()
+    defs = dict(re.findall(r"#define\s+DHR_([A-Z0-9_]+)\s+(\w+)", text))
+    as_int = lambda v: int(v.rstrip("uU"), 0)
+    assert as_int(defs["PRIMARY_RASTER"]) == dhrs.PRIMARY_RASTER
+    assert as_int(defs["PRIMARY_TRAVERSE"]) == dhrs.PRIMARY_TRAVERSE
+    assert as_int(defs["TAPE_RECOMPUTE"]) == dhrs.TAPE_RECOMPUTE
+    assert as_int(defs["TAPE_STORE"]) == dhrs.TAPE_STORE
+    assert as_int(defs["MAX_LIGHTS"]) == dhrs.MAX_LIGHTS
+    assert as_int(defs["BACKGROUND"]) == dhrs.BACKGROUND
+
+
 def test_binding_loads_without_gpu():
     import paper_2406_06963_b300 as dhrs
     L = dhrs.lib()

@@ -47,18 +47,23 @@ def _planes(a):          # [F, H, W, 2] -> [F, 2, H, W]
     return np.ascontiguousarray(np.moveaxis(a, -1, 1))
 
 
-@pytest.mark.parametrize("levels,wl_in,sigma_n", [(5, True, 128.0), (2, True, 128.0), (3, False, 128.0),
-                                                   (0, True, 128.0), (3, True, 32.0), (2, False, 0.0)])
-def test_adjoint_matches_oracle(levels, wl_in, sigma_n):
+@pytest.mark.parametrize("levels,wl_in,sigma_n,schedule", [
+    (5, True, 128.0, dhrs.TAPE_RECOMPUTE), (5, True, 128.0, dhrs.TAPE_STORE),
+    (2, True, 128.0, dhrs.TAPE_RECOMPUTE), (3, False, 128.0, dhrs.TAPE_STORE),
+    (1, True, 128.0, dhrs.TAPE_RECOMPUTE), (1, False, 128.0, dhrs.TAPE_STORE),
+    (0, True, 128.0, dhrs.TAPE_RECOMPUTE), (3, True, 32.0, dhrs.TAPE_RECOMPUTE),
+    (2, False, 0.0, dhrs.TAPE_STORE)])
+def test_adjoint_matches_oracle(levels, wl_in, sigma_n, schedule):
     """sigma_n 128 takes the kernels' power-of-two normal weight; 32 and 0
-    (no normal term) the general one."""
+    (no normal term) the general one.  Both record schedules: levels
+    recomputed by the backward, and stored by the forward."""
     W, H, F = 64, 40, 6
     zn, mesh, cams, sig, g_out = _inputs(W, H, F)
     op = orc.SvgfParams(levels=levels, wl_in_atrous=wl_in, sigma_n=sigma_n)
     out_o, gsig_o, gsigma_o = orc.svgf_seq_grad(zn, mesh, cams, sig, op, g_out)
     gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
     gp = dhrs.SvgfParams(**op.__dict__)
-    tape = dhrs.SvgfTape(W, H, F)
+    tape = dhrs.SvgfTape(W, H, F, schedule)
     sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
     gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
     out = tape.forward(gbufs, cams, sig_t, gp)
@@ -107,3 +112,55 @@ def test_autograd_function_and_fit():
         losses.append(float(l.detach()))
     print("fit losses", losses)
     assert losses[-1] < losses[0]
+
+
+def test_recompute_schedule_equals_store():
+    """The recomputed level records are the stored ones: the same filtered
+    output bit for bit, the same gradients up to the atomics' summation
+    order; a second backward after one forward gives the first's; the
+    recomputing tape keeps two frames of level records, the storing one F."""
+    W, H, F, L = 96, 56, 5, 5
+    zn, mesh, cams, sig, g_out = _inputs(W, H, F, seed=4)
+    gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
+    gp = dhrs.SvgfParams(levels=L, sigma_n=32.0)
+    sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
+    gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
+    res = {}
+    for sched in (dhrs.TAPE_RECOMPUTE, dhrs.TAPE_STORE):
+        tape = dhrs.SvgfTape(W, H, F, sched)
+        out = tape.forward(gbufs, cams, sig_t, gp)
+        g1 = tape.backward(gbufs, cams, sig_t, gp, gout_t)
+        g2 = tape.backward(gbufs, cams, sig_t, gp, gout_t)
+        torch.cuda.synchronize()
+        res[sched] = (out, g1, g2, tape.level_bytes(L))
+    N = W * H
+    per_frame = N * (16 * (L - 1) + 8 * L + 16)
+    assert res[dhrs.TAPE_RECOMPUTE][3] == 2 * per_frame
+    assert res[dhrs.TAPE_STORE][3] == F * per_frame
+    out_r, out_s = res[dhrs.TAPE_RECOMPUTE][0], res[dhrs.TAPE_STORE][0]
+    assert torch.equal(out_r, out_s)
+    ref_sig, ref_sigma = res[dhrs.TAPE_STORE][1]
+    scale = float(ref_sig.abs().max())
+    for sched in res:
+        for g_sig, g_sigma in res[sched][1:3]:
+            assert float((g_sig - ref_sig).abs().max()) <= 1e-6 * scale
+            assert torch.allclose(g_sigma, ref_sigma, rtol=1e-5, atol=1e-7), (g_sigma, ref_sigma)
+
+
+def test_schedule_change_needs_a_new_forward():
+    W, H, F = 32, 16, 2
+    zn, mesh, cams, sig, g_out = _inputs(W, H, F, seed=5)
+    gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
+    gp = dhrs.SvgfParams(levels=2)
+    sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
+    gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
+    tape = dhrs.SvgfTape(W, H, F)
+    tape.forward(gbufs, cams, sig_t, gp)
+    tape.set_schedule(dhrs.TAPE_STORE)
+    with pytest.raises(dhrs.DhrError):
+        tape.backward(gbufs, cams, sig_t, gp, gout_t)
+    with pytest.raises(dhrs.DhrError):
+        tape.set_schedule(7)
+    tape.forward(gbufs, cams, sig_t, gp)
+    tape.backward(gbufs, cams, sig_t, gp, gout_t)
+    torch.cuda.synchronize()

@@ -64,7 +64,6 @@ for f, cam in enumerate(cams):
 res["session"] = dhrs.debug_status()[0]
 
 F = 3
-tape = dhrs.SvgfTape(W, H, F)
 gbs = []
 for f in range(F):
     gg = dhrs.GBuffer(W, H)
@@ -73,10 +72,13 @@ for f in range(F):
 r = np.random.default_rng(0)
 sig = torch.from_numpy(r.uniform(0.05, 0.95, (F, 2, H, W)).astype(np.float32)).cuda()
 gout = torch.from_numpy(r.normal(size=(F, 2, H, W)).astype(np.float32)).cuda()
-for levels in (5, 2, 0):
-    p = dhrs.SvgfParams(levels=levels)
-    tape.forward(gbs, cams[:F], sig, p)
-    tape.backward(gbs, cams[:F], sig, p, gout)
+for sched in (dhrs.TAPE_RECOMPUTE, dhrs.TAPE_STORE):
+    tape = dhrs.SvgfTape(W, H, F, sched)
+    for levels in (5, 2, 1, 0):
+        p = dhrs.SvgfParams(levels=levels)
+        tape.forward(gbs, cams[:F], sig, p)
+        tape.backward(gbs, cams[:F], sig, p, gout)
+        tape.backward(gbs, cams[:F], sig, p, gout)
 res["adjoint"] = dhrs.debug_status()[0]
 
 srv = dhrs.Server(sc, 4 << 30)
