@@ -621,13 +621,14 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
     # G-buffer 16, weight sums 8, output 16, upstream gradient 16, sigma
     # terms 32 read + written, records 64 written) and pass B 112 (records
     # 64, input 16, G-buffer 16, gradient 16 written), temporal backward 180;
-    # recomputing the levels of every frame but the last: the forward's five
-    # levels (56 + 3 x 48 + 40) + their records (5 x 8 + 16) = 296
+    # recomputing the levels of every frame but the last two (whose records
+    # the forward leaves in place): the forward's five levels (56 + 3 x 48 +
+    # 40) + their records (5 x 8 + 16) = 296
     L = p.levels
     px = W * H
     bwd_px = L * (176 + 112) + 180
     bytes_fwd = frames * px * (340 + L * 8 + 16)
-    bytes_bwd = frames * px * bwd_px + (frames - 1) * px * 296
+    bytes_bwd = frames * px * bwd_px + max(frames - 2, 0) * px * 296
     bytes_bwd_s = frames * px * bwd_px
     bytes_fb = bytes_fwd + bytes_bwd
     log_s = torch.tensor([0.0, 4.852, 1.386], device="cuda").requires_grad_(True)  # log(1, 128, 4)
