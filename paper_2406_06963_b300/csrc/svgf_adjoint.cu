@@ -123,8 +123,13 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
             if (kCheck && (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H)) continue;
             const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
             const float4 cq = __ldg(x + q);
-            if (!fg_var(cq.z)) continue;
-            const TapLog t = tap_log<kNsq>(k, step, i, j, zp, gz, S::g(g, q));
+            // interior tiles issue both loads before testing the tap: a
+            // background tap (depth +inf, finite colour sentinel) gets weight
+            // exactly 0, and its sigma_z term is selected away
+            const float4 zq = S::g(g, q);
+            const bool fg = fg_var(cq.z);
+            if (kCheck && !fg) continue;
+            const TapLog t = tap_log<kNsq>(k, step, i, j, zp, gz, zq);
             const float d0 = cq.x - cp.x, d1 = cq.y - cp.y;
             const u64 w = pack2(ex2_approx(fmaf(nil0, fabsf(d0), t.e)), ex2_approx(fmaf(nil1, fabsf(d1), t.e)));
             const u64 Gw = fma2(mul2(A3, w), pack2(cq.z, cq.w), fma2(A1, pack2(cq.x, cq.y), NA2));
@@ -136,7 +141,7 @@ __device__ __forceinline__ void bwd_a_pixel(const SvgfConsts& k, int step, const
             const float2 gf = unpack2(gww);
             const float gsum = gf.x + gf.y;
             // d w / d sigma_z = w |dz| a_off / D^2;  d w / d sigma_n = w ln(n . n_q)
-            gsz = fmaf(gsum, t.u * t.a_off * t.rD, gsz);
+            gsz = fmaf(gsum, fg ? t.u * t.a_off * t.rD : 0.f, gsz);
             if (t.nd > 0.f) gsn = fmaf(gsum, t.l2n, gsn);
         }
     float4 acc = gs[p];
@@ -259,7 +264,7 @@ __device__ __forceinline__ float4 upstream(const Upstream& up, size_t N, int q) 
 
 // wsum: the level's weight sums [N]; xout: its filtered colour and variance [N]
 template <int kNsq, bool kLum>
-__global__ void __launch_bounds__(kThreadsA, 5) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
+__global__ void __launch_bounds__(kThreadsA, 4) atrous_bwd_a(SvgfConsts k, int step, const float4* g, const float4* x,
                                                              const float2* wsum, const float4* xout, Upstream up,
                                                              float4* rec, float4* gs) {
     const int px = blockIdx.x * kBX + threadIdx.x, py = blockIdx.y * kBY + threadIdx.y;
@@ -342,7 +347,7 @@ __device__ __forceinline__ W7 w7(const SvgfConsts& k, float4 zn, float2 gz, int 
     return t;
 }
 
-__global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
+__global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
     SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const float4* g_cur, const uint32_t* mesh_cur,
     const float4* g_prev, const uint32_t* mesh_prev, const float* sig, const float4* mom, const uint8_t* hist,
     Upstream up, const float4* gmom, float* g_sig, float2* gcol_prev, float4* gmom_prev, float4* gs) {
@@ -392,23 +397,28 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
             // sum w f, sum w f s and sum w f s^2 per channel.
             float sw = 0.f, s1x = 0.f, s1y = 0.f, s2x = 0.f, s2y = 0.f;
             float fZ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, fL[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            // every tap's loads are issued before it is tested: a tap outside
+            // the image reads the clamped pixel and is masked, a background
+            // tap (depth +inf) has weight exactly 0 and is masked likewise
             for (int dy = -3; dy <= 3; ++dy)
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx, qy = y + dy;
-                    if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                    const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
+                    const bool in = qx >= 0 && qy >= 0 && qx < k.W && qy < k.H;
+                    const int q = (int)dbg_index((long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1),
+                                                 (long long)N, kSiteAdjoint);
                     const float4 zq = S::g(g_cur, q);
-                    if (!is_fg(zq.x)) continue;
-                    const W7 t = w7(k, zn, gz, dx, dy, zq);
                     const float sx = sig[q], sy = sig[N + q];
-                    sw += t.w;
-                    s1x = fmaf(t.w, sx, s1x);
-                    s1y = fmaf(t.w, sy, s1y);
-                    s2x = fmaf(t.w, sx * sx, s2x);
-                    s2y = fmaf(t.w, sy * sy, s2y);
+                    const bool use = in && is_fg(zq.x);
+                    const W7 t = w7(k, zn, gz, dx, dy, zq);
+                    const float w = use ? t.w : 0.f;
+                    sw += w;
+                    s1x = fmaf(w, sx, s1x);
+                    s1y = fmaf(w, sy, s1y);
+                    s2x = fmaf(w, sx * sx, s2x);
+                    s2y = fmaf(w, sy * sy, s2y);
                     if (dx || dy) {
-                        const float wZ = t.w * t.dz * t.a_off * t.rD * t.rD;
-                        const float wL = t.nd > 0.f ? t.w * t.l2n * kLn2 : 0.f;
+                        const float wZ = use ? w * t.dz * t.a_off * t.rD * t.rD : 0.f;
+                        const float wL = use && t.nd > 0.f ? w * t.l2n * kLn2 : 0.f;
                         const float f[5] = {1.f, sx, sx * sx, sy, sy * sy};
 #pragma unroll
                         for (int u = 0; u < 5; ++u) {
@@ -430,12 +440,13 @@ __global__ void __launch_bounds__(kThreadsA) temporal_bwd_kernel(
             for (int dy = -3; dy <= 3; ++dy)
                 for (int dx = -3; dx <= 3; ++dx) {
                     const int qx = x + dx, qy = y + dy;
-                    if (qx < 0 || qy < 0 || qx >= k.W || qy >= k.H) continue;
-                    const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
+                    const bool in = qx >= 0 && qy >= 0 && qx < k.W && qy < k.H;
+                    const int q = (int)dbg_index((long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1),
+                                                 (long long)N, kSiteAdjoint);
                     const float4 zq = S::g(g_cur, q);
-                    if (!is_fg(zq.x)) continue;
-                    const float w = w7(k, zn, gz, dx, dy, zq).w * isw;
                     const float sx = sig[q], sy = sig[N + q];
+                    if (!in || !is_fg(zq.x)) continue;
+                    const float w = w7(k, zn, gz, dx, dy, zq).w * isw;
                     atomicAdd(&tile[0][qy - by0][qx - bx0], (G1x + G2x * 2.f * sx) * w);
                     atomicAdd(&tile[1][qy - by0][qx - bx0], (G1y + G2y * 2.f * sy) * w);
                 }
