@@ -164,3 +164,55 @@ def test_schedule_change_needs_a_new_forward():
     tape.forward(gbufs, cams, sig_t, gp)
     tape.backward(gbufs, cams, sig_t, gp, gout_t)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("F", [1, 2, 3])
+def test_short_sequences_both_schedules(F):
+    """One to three frames: the recomputing tape holds min(F, 2) slots and,
+    for F <= 2, recomputes nothing; outputs bit-identical, gradients equal up
+    to the atomics' order, and both match the oracle."""
+    W, H = 40, 24
+    zn, mesh, cams, sig, g_out = _inputs(W, H, F, seed=6)
+    op = orc.SvgfParams(levels=3)
+    out_o, gsig_o, gsigma_o = orc.svgf_seq_grad(zn, mesh, cams, sig, op, g_out)
+    gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
+    gp = dhrs.SvgfParams(**op.__dict__)
+    sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
+    gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
+    res = []
+    for sched in (dhrs.TAPE_RECOMPUTE, dhrs.TAPE_STORE):
+        tape = dhrs.SvgfTape(W, H, F, sched)
+        out = tape.forward(gbufs, cams, sig_t, gp)
+        g_sig, g_sigma = tape.backward(gbufs, cams, sig_t, gp, gout_t)
+        torch.cuda.synchronize()
+        res.append((out, g_sig, g_sigma))
+        per_frame = W * H * (16 * 2 + 8 * 3 + 16)
+        assert tape.level_bytes(3) == per_frame * (min(F, 2) if sched == dhrs.TAPE_RECOMPUTE else F)
+    assert torch.equal(res[0][0], res[1][0])
+    assert float((res[0][1] - res[1][1]).abs().max()) <= 1e-6 * float(res[1][1].abs().max())
+    g_sig = np.moveaxis(res[0][1].cpu().numpy(), 1, -1)
+    assert np.abs(g_sig - gsig_o).max() <= 1e-3 * np.abs(gsig_o).max()
+    assert np.abs(np.moveaxis(res[0][0].cpu().numpy(), 1, -1) - out_o).max() <= 1e-3
+
+
+def test_level_records_grow_with_the_level_count():
+    """A forward with more levels than the tape's records hold reallocates
+    them; the backward then matches a fresh tape's."""
+    W, H, F = 48, 32, 4
+    zn, mesh, cams, sig, g_out = _inputs(W, H, F, seed=7)
+    gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
+    sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
+    gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
+    tape = dhrs.SvgfTape(W, H, F)
+    p2, p5 = dhrs.SvgfParams(levels=2), dhrs.SvgfParams(levels=5)
+    tape.forward(gbufs, cams, sig_t, p2)
+    tape.backward(gbufs, cams, sig_t, p2, gout_t)
+    out = tape.forward(gbufs, cams, sig_t, p5)
+    g_sig, g_sigma = tape.backward(gbufs, cams, sig_t, p5, gout_t)
+    fresh = dhrs.SvgfTape(W, H, F)
+    out_f = fresh.forward(gbufs, cams, sig_t, p5)
+    g_sig_f, g_sigma_f = fresh.backward(gbufs, cams, sig_t, p5, gout_t)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out_f)
+    assert float((g_sig - g_sig_f).abs().max()) <= 1e-6 * float(g_sig_f.abs().max())
+    assert torch.allclose(g_sigma, g_sigma_f, rtol=1e-5, atol=1e-7)
