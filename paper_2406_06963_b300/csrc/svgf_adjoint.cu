@@ -347,13 +347,111 @@ __device__ __forceinline__ W7 w7(const SvgfConsts& k, float4 zn, float2 gz, int 
     return t;
 }
 
+// Sums of the 7x7 estimate of one pixel: the weighted sums of w, s and s^2
+// per channel (the forward's means).
+struct Short7 {
+    float sw, s1x, s1y, s2x, s2y;
+};
+
+// Adds tap (dx, dy) of pixel (x, y).  The tap's loads are issued before it
+// is tested: with kCheck a tap outside the image reads the clamped pixel and
+// is masked; a background tap (depth +inf) has weight exactly 0 and is
+// masked likewise.
+template <bool kCheck>
+__device__ __forceinline__ void short7_tap(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
+                                           float4 zn, float2 gz, int x, int y, int dx, int dy, Short7& a) {
+    using S = Store<DHR_FP32>;
+    const int qx = x + dx, qy = y + dy;
+    const bool in = !kCheck || (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H);
+    const long long qi = kCheck ? (long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1)
+                                : (long long)qy * k.W + qx;
+    const int q = (int)dbg_index(qi, (long long)N, kSiteAdjoint);
+    const float4 zq = S::g(g_cur, q);
+    const float sx = sig[q], sy = sig[N + q];
+    const bool use = in && is_fg(zq.x);
+    const float w = use ? w7(k, zn, gz, dx, dy, zq).w : 0.f;
+    a.sw += w;
+    a.s1x = fmaf(w, sx, a.s1x);
+    a.s1y = fmaf(w, sy, a.s1y);
+    a.s2x = fmaf(w, sx * sx, a.s2x);
+    a.s2y = fmaf(w, sy * sy, a.s2y);
+}
+
+// Coefficients of the gradient with respect to tap q's signal and weight,
+// from the sums and the gradient (Gc, Gv) at the estimate's colour and
+// variance (colour = m1, var = max(0, m2 - m1^2), m_k = sum w s^k / sum w):
+//   dL/d s_q = (G1 + 2 G2 s_q) w_q / sw per channel,
+//   dL/d w_q = (G1 (s_q - m1) + G2 (s_q^2 - m2)) / sw summed over channels
+//            = (c0 + sum_ch s_q (G1 + G2 s_q)) / sw.
+struct ShortG {
+    float G1x, G1y, G2x, G2y, c0, isw;
+};
+
+__device__ __forceinline__ ShortG short7_finish(const Short7& a, float2 Gc, float2 Gv) {
+    const float m1x = a.s1x / a.sw, m1y = a.s1y / a.sw, m2x = a.s2x / a.sw, m2y = a.s2y / a.sw;
+    const bool vx = m2x - m1x * m1x > 0.f, vy = m2y - m1y * m1y > 0.f;
+    ShortG G;
+    G.G1x = Gc.x - (vx ? 2.f * m1x * Gv.x : 0.f);
+    G.G1y = Gc.y - (vy ? 2.f * m1y * Gv.y : 0.f);
+    G.G2x = vx ? Gv.x : 0.f;
+    G.G2y = vy ? Gv.y : 0.f;
+    G.c0 = -(G.G1x * m1x + G.G2x * m2x + G.G1y * m1y + G.G2y * m2y);
+    G.isw = 1.f / a.sw;
+    return G;
+}
+
+// dL/d s of tap (dx, dy) of pixel (x, y) into the block's shared tile
+// (origin bx0, by0: the block's first pixel minus the apron), and the tap's
+// sigma terms dL/d w_q d w_q / d sigma into gsz, gsn (d w / d sigma_z = w
+// |dz| a_off / D^2, d w / d sigma_n = w ln(n . n_q))
+template <bool kCheck>
+__device__ __forceinline__ void short7_scatter(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
+                                               float4 zn, float2 gz, int x, int y, int dx, int dy, const ShortG& G,
+                                               float (*tile)[kTH][kTW], int bx0, int by0, float& gsz,
+                                               float& gsn) {
+    using S = Store<DHR_FP32>;
+    const int qx = x + dx, qy = y + dy;
+    const bool in = !kCheck || (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H);
+    const long long qi = kCheck ? (long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1)
+                                : (long long)qy * k.W + qx;
+    const int q = (int)dbg_index(qi, (long long)N, kSiteAdjoint);
+    const float4 zq = S::g(g_cur, q);
+    const float sx = sig[q], sy = sig[N + q];
+    if (!in || !is_fg(zq.x)) return;
+    const W7 t = w7(k, zn, gz, dx, dy, zq);
+    const float w = t.w * G.isw;
+    atomicAdd(&tile[0][qy - by0][qx - bx0], (G.G1x + G.G2x * 2.f * sx) * w);
+    atomicAdd(&tile[1][qy - by0][qx - bx0], (G.G1y + G.G2y * 2.f * sy) * w);
+    if (dx || dy) {
+        const float gw = fmaf(sx, fmaf(G.G2x, sx, G.G1x), fmaf(sy, fmaf(G.G2y, sy, G.G1y), G.c0)) * w;
+        gsz = fmaf(gw, t.dz * t.a_off * t.rD * t.rD, gsz);
+        if (t.nd > 0.f) gsn = fmaf(gw, t.l2n * kLn2, gsn);
+    }
+}
+
+// the whole 7x7 estimate of one lane's own pixel
+template <bool kCheck>
+__device__ __forceinline__ void short7_lane(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
+                                            float4 zn, float2 gz, int x, int y, float2 Gc, float2 Gv,
+                                            float (*tile)[kTH][kTW], int bx0, int by0, float& gsz, float& gsn) {
+    Short7 a = {};
+    for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx) short7_tap<kCheck>(k, g_cur, sig, N, zn, gz, x, y, dx, dy, a);
+    const ShortG G = short7_finish(a, Gc, Gv);
+    for (int dy = -3; dy <= 3; ++dy)
+#pragma unroll
+        for (int dx = -3; dx <= 3; ++dx)
+            short7_scatter<kCheck>(k, g_cur, sig, N, zn, gz, x, y, dx, dy, G, tile, bx0, by0, gsz, gsn);
+}
+
 __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
     SvgfConsts k, dhr_camera cam, dhr_camera cam_prev, const float4* g_cur, const uint32_t* mesh_cur,
     const float4* g_prev, const uint32_t* mesh_prev, const float* sig, const float4* mom, const uint8_t* hist,
     Upstream up, const float4* gmom, float* g_sig, float2* gcol_prev, float4* gmom_prev, float4* gs) {
     using S = Store<DHR_FP32>;
     __shared__ float tile[2][kTH][kTW];
-    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const int tid = threadIdx.y * kBX + threadIdx.x, lane = threadIdx.x & 31;
     for (int e = tid; e < 2 * kTH * kTW; e += kThreadsA) (&tile[0][0][0])[e] = 0.f;
     __syncthreads();
     const int bx0 = blockIdx.x * kBX - kTR, by0 = blockIdx.y * kBY - kTR;
@@ -363,21 +461,27 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
     const bool inside = x < k.W && y < k.H;
     const int p = inside ? y * k.W + x : 0;
     const float4 zn = inside ? S::g(g_cur, p) : make_float4(INFINITY, 0.f, 0.f, 0.f);
-    if (inside && is_fg(zn.x)) {
-        const int n = hist[p];
-        const float2 gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
-        Reproj r;
-        bool valid = false;
+    const bool fg = inside && is_fg(zn.x);
+    int n = 0;
+    float2 gz = make_float2(0.f, 0.f), Gc = make_float2(0.f, 0.f), Gv = make_float2(0.f, 0.f);
+    float2 Gce = make_float2(0.f, 0.f), s = make_float2(0.f, 0.f);
+    float4 Gm = make_float4(0.f, 0.f, 0.f, 0.f);
+    float a = 1.0f;
+    Reproj r;
+    bool valid = false;
+    if (fg) {
+        n = hist[p];
+        gz = depth_grad<S>(g_cur, k.W, k.H, x, y, zn.x);
         if (g_prev && n >= 2) {
             const float slope = fmaxf(fabsf(gz.x), fabsf(gz.y));
             valid = reproject<S>(cam, cam_prev, k.W, k.H, x, y, zn, __ldg(mesh_cur + p), slope, g_prev, mesh_prev, r);
         }
-        const float a = valid ? (k.fixed_alpha ? k.alpha : fmaxf(k.alpha, 1.0f / (float)n)) : 1.0f;
-        const float2 s = make_float2(sig[p], sig[N + p]);
-        float2 Gce = make_float2(0.f, 0.f);
-        float4 Gm = gmom[p];
+        a = valid ? (k.fixed_alpha ? k.alpha : fmaxf(k.alpha, 1.0f / (float)n)) : 1.0f;
+        s = make_float2(sig[p], sig[N + p]);
+        Gm = gmom[p];
         const float4 G = upstream(up, N, p);   // at the temporal output (level 0's input)
-        const float2 Gc = make_float2(G.x, G.y), Gv = make_float2(G.z, G.w);
+        Gc = make_float2(G.x, G.y);
+        Gv = make_float2(G.z, G.w);
         if (n >= 4) {
             Gce = Gc;
             const float4 m = mom[p];
@@ -389,68 +493,67 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
                 Gm.w += Gv.y;
                 Gm.y -= 2.f * m.y * Gv.y;
             }
-        } else {
-            // 7x7 estimate: colour = m1, var = max(0, m2 - m1^2), m_k = sum w s^k / sum w.
-            // With Gw_q = (G1 (s_q - m1) + G2 (s_q^2 - m2)) / sw summed over both
-            // channels, the sigma derivatives need sum_q Gw_q w_q f_q for
-            // f = Z (d w / d sigma_z / w) and L (ln n.n_q): the first pass keeps
-            // sum w f, sum w f s and sum w f s^2 per channel.
-            float sw = 0.f, s1x = 0.f, s1y = 0.f, s2x = 0.f, s2y = 0.f;
-            float fZ[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, fL[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-            // every tap's loads are issued before it is tested: a tap outside
-            // the image reads the clamped pixel and is masked, a background
-            // tap (depth +inf) has weight exactly 0 and is masked likewise
-            for (int dy = -3; dy <= 3; ++dy)
-                for (int dx = -3; dx <= 3; ++dx) {
-                    const int qx = x + dx, qy = y + dy;
-                    const bool in = qx >= 0 && qy >= 0 && qx < k.W && qy < k.H;
-                    const int q = (int)dbg_index((long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1),
-                                                 (long long)N, kSiteAdjoint);
-                    const float4 zq = S::g(g_cur, q);
-                    const float sx = sig[q], sy = sig[N + q];
-                    const bool use = in && is_fg(zq.x);
-                    const W7 t = w7(k, zn, gz, dx, dy, zq);
-                    const float w = use ? t.w : 0.f;
-                    sw += w;
-                    s1x = fmaf(w, sx, s1x);
-                    s1y = fmaf(w, sy, s1y);
-                    s2x = fmaf(w, sx * sx, s2x);
-                    s2y = fmaf(w, sy * sy, s2y);
-                    if (dx || dy) {
-                        const float wZ = use ? w * t.dz * t.a_off * t.rD * t.rD : 0.f;
-                        const float wL = use && t.nd > 0.f ? w * t.l2n * kLn2 : 0.f;
-                        const float f[5] = {1.f, sx, sx * sx, sy, sy * sy};
-#pragma unroll
-                        for (int u = 0; u < 5; ++u) {
-                            fZ[u] = fmaf(wZ, f[u], fZ[u]);
-                            fL[u] = fmaf(wL, f[u], fL[u]);
-                        }
-                    }
-                }
-            const float m1x = s1x / sw, m1y = s1y / sw, m2x = s2x / sw, m2y = s2y / sw;
-            const bool vx = m2x - m1x * m1x > 0.f, vy = m2y - m1y * m1y > 0.f;
-            const float G1x = Gc.x - (vx ? 2.f * m1x * Gv.x : 0.f), G1y = Gc.y - (vy ? 2.f * m1y * Gv.y : 0.f);
-            const float G2x = vx ? Gv.x : 0.f, G2y = vy ? Gv.y : 0.f;
-            const float isw = 1.f / sw;
-            gsz += (G1x * (fZ[1] - m1x * fZ[0]) + G2x * (fZ[2] - m2x * fZ[0]) + G1y * (fZ[3] - m1y * fZ[0]) +
-                    G2y * (fZ[4] - m2y * fZ[0])) * isw;
-            gsn += (G1x * (fL[1] - m1x * fL[0]) + G2x * (fL[2] - m2x * fL[0]) + G1y * (fL[3] - m1y * fL[0]) +
-                    G2y * (fL[4] - m2y * fL[0])) * isw;
-            // dL/d s_q = (G1 + 2 G2 s_q) w_q / sw, into the shared tile
-            for (int dy = -3; dy <= 3; ++dy)
-                for (int dx = -3; dx <= 3; ++dx) {
-                    const int qx = x + dx, qy = y + dy;
-                    const bool in = qx >= 0 && qy >= 0 && qx < k.W && qy < k.H;
-                    const int q = (int)dbg_index((long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1),
-                                                 (long long)N, kSiteAdjoint);
-                    const float4 zq = S::g(g_cur, q);
-                    const float sx = sig[q], sy = sig[N + q];
-                    if (!in || !is_fg(zq.x)) continue;
-                    const float w = w7(k, zn, gz, dx, dy, zq).w * isw;
-                    atomicAdd(&tile[0][qy - by0][qx - bx0], (G1x + G2x * 2.f * sx) * w);
-                    atomicAdd(&tile[1][qy - by0][qx - bx0], (G1y + G2y * 2.f * sy) * w);
-                }
         }
+    }
+    // short history (n < 4): backward of the 7x7 spatial estimate.  A warp
+    // with many such lanes lets each do its own 49 taps twice (sums, then
+    // scatter); with few, the warp serves them one after another, lane l
+    // taking taps l and l + 32, the sums reduced across the warp.
+    const bool need = fg && n < 4;
+    unsigned todo = __ballot_sync(kFull, need);
+    if (__popc(todo) >= kShortPerLane) {
+        if (need) {
+            const bool interior = bx0 >= 0 && by0 >= 0 && bx0 + kTW <= k.W && by0 + kTH <= k.H;
+            if (interior)
+                short7_lane<false>(k, g_cur, sig, N, zn, gz, x, y, Gc, Gv, tile, bx0, by0, gsz, gsn);
+            else
+                short7_lane<true>(k, g_cur, sig, N, zn, gz, x, y, Gc, Gv, tile, bx0, by0, gsz, gsn);
+        }
+    } else {
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int px = __shfl_sync(kFull, x, src), py = __shfl_sync(kFull, y, src);
+            const float4 pz = make_float4(__shfl_sync(kFull, zn.x, src), __shfl_sync(kFull, zn.y, src),
+                                          __shfl_sync(kFull, zn.z, src), __shfl_sync(kFull, zn.w, src));
+            const float2 pg = make_float2(__shfl_sync(kFull, gz.x, src), __shfl_sync(kFull, gz.y, src));
+            const float2 pc = make_float2(__shfl_sync(kFull, Gc.x, src), __shfl_sync(kFull, Gc.y, src));
+            const float2 pv = make_float2(__shfl_sync(kFull, Gv.x, src), __shfl_sync(kFull, Gv.y, src));
+            Short7 acc = {};
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int t = lane + 32 * it;
+                if (t < 49) short7_tap<true>(k, g_cur, sig, N, pz, pg, px, py, t % 7 - 3, t / 7 - 3, acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.sw += __shfl_xor_sync(kFull, acc.sw, o);
+                acc.s1x += __shfl_xor_sync(kFull, acc.s1x, o);
+                acc.s1y += __shfl_xor_sync(kFull, acc.s1y, o);
+                acc.s2x += __shfl_xor_sync(kFull, acc.s2x, o);
+                acc.s2y += __shfl_xor_sync(kFull, acc.s2y, o);
+            }
+            const ShortG G = short7_finish(acc, pc, pv);
+            float dz_s = 0.f, dn_s = 0.f;
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int t = lane + 32 * it;
+                if (t < 49)
+                    short7_scatter<true>(k, g_cur, sig, N, pz, pg, px, py, t % 7 - 3, t / 7 - 3, G, tile, bx0, by0,
+                                         dz_s, dn_s);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dz_s += __shfl_xor_sync(kFull, dz_s, o);
+                dn_s += __shfl_xor_sync(kFull, dn_s, o);
+            }
+            if (lane == src) {
+                gsz += dz_s;
+                gsn += dn_s;
+            }
+        }
+    }
+    if (fg) {
         // moving averages
         atomicAdd(&tile[0][y - by0][x - bx0], a * Gce.x + a * Gm.x + 2.f * a * s.x * Gm.z);
         atomicAdd(&tile[1][y - by0][x - bx0], a * Gce.y + a * Gm.y + 2.f * a * s.y * Gm.w);
@@ -468,9 +571,9 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
     }
     __syncthreads();
     for (int e = tid; e < 2 * kTH * kTW; e += kThreadsA) {
-        const int c = e / (kTH * kTW), r = e % (kTH * kTW);
-        const int qx = bx0 + r % kTW, qy = by0 + r / kTW;
-        const float v = tile[c][r / kTW][r % kTW];
+        const int c = e / (kTH * kTW), rr = e % (kTH * kTW);
+        const int qx = bx0 + rr % kTW, qy = by0 + rr / kTW;
+        const float v = tile[c][rr / kTW][rr % kTW];
         if (v != 0.f && qx >= 0 && qy >= 0 && qx < k.W && qy < k.H) atomicAdd(g_sig + (size_t)c * N + qy * k.W + qx, v);
     }
     if (inside && (gsz != 0.f || gsn != 0.f)) {
