@@ -396,10 +396,12 @@ typedef struct dhr_svgf_tape dhr_svgf_tape;
  * RECOMPUTE (the default): the records of two frames are kept (frame f in
  * slot f mod 2); the forward leaves the last two frames' there and the
  * backward recomputes each earlier frame's L levels from that frame's
- * stored temporal output, on a stream of the tape's own, while the adjoint
- * of the frame after it runs (L more a-trous launches per earlier frame;
- * the call orders the tape's stream after `stream` on entry and `stream`
- * after it on return).
+ * stored temporal output while the adjoint of the frame after it runs (L
+ * more a-trous launches per earlier frame).  The tape owns two streams for
+ * this: the passes run on one of the device's highest priority, the
+ * recomputation on one of its lowest, so that recompute blocks take the SM
+ * slots the passes leave free; the call orders both after `stream` on
+ * entry and `stream` after both on return.
  * STORE: the forward keeps the records of every frame and the backward
  * recomputes nothing.  The a-trous levels are deterministic, so the
  * recomputed records equal the stored ones bit for bit. */

@@ -12,8 +12,9 @@
 // records a frame's adjoint reads -- the input of every a-trous level after
 // the first, every level's weight sums and the last level's output -- are
 // recomputed from the temporal output by the backward, one frame ahead on a
-// second stream (the forward leaves the last two frames' in place), or kept
-// for every frame by the forward (DHR_TAPE_STORE).  Backward of one a-trous
+// low-priority stream while the passes run on a high-priority one (the
+// forward leaves the last two frames' in place), or kept for every frame by
+// the forward (DHR_TAPE_STORE).  Backward of one a-trous
 // level is a two-pass gather:
 //   pass A (per output pixel p): with the level's weight sum, filtered
 //     colour and variance at p from the forward, dL/dw_pq = a1 c_q - a2 +
@@ -672,8 +673,11 @@ struct dhr_svgf_tape {
     int rec_slots = 0;
     int schedule = DHR_TAPE_RECOMPUTE;
     int slot_frame[2] = {-1, -1};   // DHR_TAPE_RECOMPUTE: the frame whose records a slot holds
-    cudaStream_t side = nullptr;    // recompute stream
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ready[2] = {nullptr, nullptr},
+    // DHR_TAPE_RECOMPUTE: the backward's passes run on `mainq` (highest
+    // priority), the recomputation on `side` (lowest), so that recompute blocks
+    // take only the SM slots the passes leave free
+    cudaStream_t side = nullptr, mainq = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_main = nullptr, ev_ready[2] = {nullptr, nullptr},
                 ev_free[2] = {nullptr, nullptr};
     float2* gcol[2] = {nullptr, nullptr};
     float4* gmom[2] = {nullptr, nullptr};
@@ -711,9 +715,11 @@ static void tape_free(dhr_svgf_tape* t) {
     cudaFree(t->last);
     cudaFree(t->partial);
     cudaFree(t->acc);
-    for (cudaEvent_t e : {t->ev_fork, t->ev_join, t->ev_ready[0], t->ev_ready[1], t->ev_free[0], t->ev_free[1]})
+    for (cudaEvent_t e : {t->ev_fork, t->ev_join, t->ev_main, t->ev_ready[0], t->ev_ready[1], t->ev_free[0],
+                          t->ev_free[1]})
         if (e) cudaEventDestroy(e);
     if (t->side) cudaStreamDestroy(t->side);
+    if (t->mainq) cudaStreamDestroy(t->mainq);
     delete t;
 }
 
@@ -746,9 +752,12 @@ extern "C" dhr_status dhr_svgf_tape_create(int32_t width, int32_t height, int32_
     if (!e) e = cudaMalloc((void**)&t->gs, n * 16);
     if (!e) e = cudaMalloc((void**)&t->partial, (size_t)kPixReduceBlocks * 3 * sizeof(float));
     if (!e) e = cudaMalloc((void**)&t->acc, 3 * sizeof(double));
-    if (!e) e = cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&t->ev_fork, &t->ev_join, &t->ev_ready[0], &t->ev_ready[1], &t->ev_free[0],
-                            &t->ev_free[1]})
+    int least = 0, greatest = 0;
+    if (!e) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (!e) e = cudaStreamCreateWithPriority(&t->side, cudaStreamNonBlocking, least);
+    if (!e) e = cudaStreamCreateWithPriority(&t->mainq, cudaStreamNonBlocking, greatest);
+    for (cudaEvent_t* ev : {&t->ev_fork, &t->ev_join, &t->ev_main, &t->ev_ready[0], &t->ev_ready[1],
+                            &t->ev_free[0], &t->ev_free[1]})
         if (!e) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e) {
         cudaGetLastError();
@@ -934,6 +943,7 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
     // slots do not hold is recomputed on the side stream one frame ahead,
     // into the slot frame f + 1's adjoint has finished with
     const bool side = L > 0 && !store;
+    cudaStream_t ms = side ? t->mainq : st;   // the passes' stream
     bool pending[2] = {false, false};
     auto prefetch = [&](int f) -> dhr_status {
         const int sl = f & 1;
@@ -956,7 +966,7 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
             const LevelSlot s{t, N, L, store ? f : (f & 1)};
             if (side && f > 0) DHR_TRY(prefetch(f - 1));
             if (side && pending[f & 1]) {
-                DHR_CUDA_TRY(cudaStreamWaitEvent(st, t->ev_ready[f & 1], 0));
+                DHR_CUDA_TRY(cudaStreamWaitEvent(ms, t->ev_ready[f & 1], 0));
                 pending[f & 1] = false;
             }
             // the gradient at the output of the level being processed comes
@@ -967,33 +977,33 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
                 const float4* xout = s.out(l);
                 const float2* ws = s.wsum(l);
                 if (nsq == 7 && k.wl_in_atrous)
-                    atrous_bwd_a<7, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+                    atrous_bwd_a<7, true><<<grid, blk, 0, ms>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
                 else if (nsq == 7)
-                    atrous_bwd_a<7, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+                    atrous_bwd_a<7, false><<<grid, blk, 0, ms>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
                 else if (k.wl_in_atrous)
-                    atrous_bwd_a<-1, true><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
+                    atrous_bwd_a<-1, true><<<grid, blk, 0, ms>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec, t->gs);
                 else
-                    atrous_bwd_a<-1, false><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec,
+                    atrous_bwd_a<-1, false><<<grid, blk, 0, ms>>>(k, 1 << l, gcur, xin, ws, xout, up, t->rec,
                                                                   t->gs);
                 DHR_CUDA_TRY(cudaGetLastError());
                 if (nsq == 7)
-                    atrous_bwd_b<7><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
+                    atrous_bwd_b<7><<<grid, blk, 0, ms>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
                 else
-                    atrous_bwd_b<-1><<<grid, blk, 0, st>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
+                    atrous_bwd_b<-1><<<grid, blk, 0, ms>>>(k, 1 << l, gcur, xin, t->rec, t->gc, t->gv);
                 DHR_CUDA_TRY(cudaGetLastError());
                 // level l - 1's output gradient (plus, for level 0's output,
                 // the next frame's colour-history gradient)
                 up = Upstream{nullptr, t->gc, t->gv, l == 1 ? t->gcol[nx] : nullptr};
             }
-            if (side) DHR_CUDA_TRY(cudaEventRecord(t->ev_free[f & 1], st));   // slot f & 1 read for the last time
+            if (side) DHR_CUDA_TRY(cudaEventRecord(t->ev_free[f & 1], ms));   // slot f & 1 read for the last time
             const int pv = nx ^ 1;
-            DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[pv], 0, N * 8, st));
-            DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[pv], 0, N * 16, st));
+            DHR_CUDA_TRY(cudaMemsetAsync(t->gcol[pv], 0, N * 8, ms));
+            DHR_CUDA_TRY(cudaMemsetAsync(t->gmom[pv], 0, N * 16, ms));
             const bool hp = f > 0;
             // at the temporal output: pass B of level 0, or the loss gradient
             // plus the colour-history gradient when there are no levels
             up.gcol = L == 0 ? t->gcol[nx] : nullptr;
-            temporal_bwd_kernel<<<grid, blk, 0, st>>>(
+            temporal_bwd_kernel<<<grid, blk, 0, ms>>>(
                 k, cams[f], hp ? cams[f - 1] : cams[f], gcur, gbufs[f].mesh_id,
                 hp ? static_cast<const S::G*>(gbufs[f - 1].depth_normal) : nullptr,
                 hp ? gbufs[f - 1].mesh_id : nullptr, sig + (size_t)f * 2 * N, t->mom + (size_t)f * N,
@@ -1004,14 +1014,17 @@ extern "C" dhr_status dhr_svgf_seq_backward(dhr_svgf_tape* t, const dhr_gbuffer*
         }
         return DHR_OK;
     };
-    if (side) {   // the side stream starts after everything before this call on `st`
+    if (side) {   // both tape streams start after everything before this call on `st`
         DHR_CUDA_TRY(cudaEventRecord(t->ev_fork, st));
         DHR_CUDA_TRY(cudaStreamWaitEvent(t->side, t->ev_fork, 0));
+        DHR_CUDA_TRY(cudaStreamWaitEvent(t->mainq, t->ev_fork, 0));
     }
     const dhr_status r = frames();
-    if (side) {   // and `st` continues after all of the side stream's work, also on an error
-        const cudaError_t e1 = cudaEventRecord(t->ev_join, t->side);
-        const cudaError_t e2 = e1 ? e1 : cudaStreamWaitEvent(st, t->ev_join, 0);
+    if (side) {   // and `st` continues after all of their work, also on an error
+        cudaError_t e2 = cudaEventRecord(t->ev_join, t->side);
+        if (!e2) e2 = cudaEventRecord(t->ev_main, t->mainq);
+        if (!e2) e2 = cudaStreamWaitEvent(st, t->ev_join, 0);
+        if (!e2) e2 = cudaStreamWaitEvent(st, t->ev_main, 0);
         if (r != DHR_OK || e2) t->slot_frame[0] = t->slot_frame[1] = -1;
         if (r != DHR_OK) return r;
         DHR_CUDA_TRY(e2);
