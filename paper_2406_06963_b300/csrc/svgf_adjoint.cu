@@ -354,10 +354,10 @@ struct Short7 {
     float sw, s1x, s1y, s2x, s2y;
 };
 
-// Adds tap (dx, dy) of pixel (x, y).  The tap's loads are issued before it
-// is tested: with kCheck a tap outside the image reads the clamped pixel and
-// is masked; a background tap (depth +inf) has weight exactly 0 and is
-// masked likewise.
+// Adds tap (dx, dy) of pixel (x, y), read from the buffers (the warp-
+// cooperative path).  The tap's loads are issued before it is tested: with
+// kCheck a tap outside the image reads the clamped pixel and is masked; a
+// background tap (depth +inf) has weight exactly 0 and is masked likewise.
 template <bool kCheck>
 __device__ __forceinline__ void short7_tap(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
                                            float4 zn, float2 gz, int x, int y, int dx, int dy, Short7& a) {
@@ -430,20 +430,49 @@ __device__ __forceinline__ void short7_scatter(const SvgfConsts& k, const float4
     }
 }
 
-// the whole 7x7 estimate of one lane's own pixel
-template <bool kCheck>
-__device__ __forceinline__ void short7_lane(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
-                                            float4 zn, float2 gz, int x, int y, float2 Gc, float2 Gv,
-                                            float (*tile)[kTH][kTW], int bx0, int by0, float& gsz, float& gsn) {
+// A block's 7x7 neighbourhoods staged in shared memory: the G-buffer and
+// both signal planes of the kTW x kTH pixels around its tile (outside the
+// image: depth +inf, which gives weight exactly 0, and signals 0).
+struct ShortStage {
+    float4 z[kTH][kTW];
+    float2 s[kTH][kTW];
+};
+
+// the whole 7x7 estimate of one lane's own pixel (tile position tx, ty),
+// its taps read from the staged neighbourhood
+__device__ __forceinline__ void short7_lane(const SvgfConsts& k, const ShortStage& st, float4 zn, float2 gz,
+                                            int tx, int ty, float2 Gc, float2 Gv, float (*tile)[kTH][kTW],
+                                            float& gsz, float& gsn) {
     Short7 a = {};
     for (int dy = -3; dy <= 3; ++dy)
 #pragma unroll
-        for (int dx = -3; dx <= 3; ++dx) short7_tap<kCheck>(k, g_cur, sig, N, zn, gz, x, y, dx, dy, a);
+        for (int dx = -3; dx <= 3; ++dx) {
+            const float4 zq = st.z[ty + kTR + dy][tx + kTR + dx];
+            const float2 sq = st.s[ty + kTR + dy][tx + kTR + dx];
+            const float w = is_fg(zq.x) ? w7(k, zn, gz, dx, dy, zq).w : 0.f;
+            a.sw += w;
+            a.s1x = fmaf(w, sq.x, a.s1x);
+            a.s1y = fmaf(w, sq.y, a.s1y);
+            a.s2x = fmaf(w, sq.x * sq.x, a.s2x);
+            a.s2y = fmaf(w, sq.y * sq.y, a.s2y);
+        }
     const ShortG G = short7_finish(a, Gc, Gv);
     for (int dy = -3; dy <= 3; ++dy)
 #pragma unroll
-        for (int dx = -3; dx <= 3; ++dx)
-            short7_scatter<kCheck>(k, g_cur, sig, N, zn, gz, x, y, dx, dy, G, tile, bx0, by0, gsz, gsn);
+        for (int dx = -3; dx <= 3; ++dx) {
+            const float4 zq = st.z[ty + kTR + dy][tx + kTR + dx];
+            const float2 sq = st.s[ty + kTR + dy][tx + kTR + dx];
+            if (!is_fg(zq.x)) continue;
+            const W7 t = w7(k, zn, gz, dx, dy, zq);
+            const float w = t.w * G.isw;
+            atomicAdd(&tile[0][ty + kTR + dy][tx + kTR + dx], (G.G1x + G.G2x * 2.f * sq.x) * w);
+            atomicAdd(&tile[1][ty + kTR + dy][tx + kTR + dx], (G.G1y + G.G2y * 2.f * sq.y) * w);
+            if (dx || dy) {
+                const float gw = fmaf(sq.x, fmaf(G.G2x, sq.x, G.G1x), fmaf(sq.y, fmaf(G.G2y, sq.y, G.G1y), G.c0)) * w;
+                gsz = fmaf(gw, t.dz * t.a_off * t.rD * t.rD, gsz);
+                if (t.nd > 0.f) gsn = fmaf(gw, t.l2n * kLn2, gsn);
+            }
+        }
 }
 
 __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
@@ -452,6 +481,7 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
     Upstream up, const float4* gmom, float* g_sig, float2* gcol_prev, float4* gmom_prev, float4* gs) {
     using S = Store<DHR_FP32>;
     __shared__ float tile[2][kTH][kTW];
+    __shared__ ShortStage stage;
     const int tid = threadIdx.y * kBX + threadIdx.x, lane = threadIdx.x & 31;
     for (int e = tid; e < 2 * kTH * kTW; e += kThreadsA) (&tile[0][0][0])[e] = 0.f;
     __syncthreads();
@@ -498,18 +528,30 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
     }
     // short history (n < 4): backward of the 7x7 spatial estimate.  A warp
     // with many such lanes lets each do its own 49 taps twice (sums, then
-    // scatter); with few, the warp serves them one after another, lane l
-    // taking taps l and l + 32, the sums reduced across the warp.
+    // scatter) on the block's staged neighbourhood; with few, the warp serves
+    // them one after another, lane l taking taps l and l + 32, the sums
+    // reduced across the warp.
     const bool need = fg && n < 4;
     unsigned todo = __ballot_sync(kFull, need);
-    if (__popc(todo) >= kShortPerLane) {
-        if (need) {
-            const bool interior = bx0 >= 0 && by0 >= 0 && bx0 + kTW <= k.W && by0 + kTH <= k.H;
-            if (interior)
-                short7_lane<false>(k, g_cur, sig, N, zn, gz, x, y, Gc, Gv, tile, bx0, by0, gsz, gsn);
-            else
-                short7_lane<true>(k, g_cur, sig, N, zn, gz, x, y, Gc, Gv, tile, bx0, by0, gsz, gsn);
+    const bool many = __popc(todo) >= kShortPerLane;
+    if (__syncthreads_or(many && need)) {   // some warp of the block works per lane: stage
+        for (int e = tid; e < kTH * kTW; e += kThreadsA) {
+            const int sy = e / kTW, sx = e - sy * kTW;
+            const int qx = bx0 + sx, qy = by0 + sy;
+            float4 z = make_float4(INFINITY, 0.f, 0.f, 0.f);
+            float2 v = make_float2(0.f, 0.f);
+            if (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H) {
+                const int q = (int)dbg_index((long long)qy * k.W + qx, (long long)N, kSiteAdjoint);
+                z = S::g(g_cur, q);
+                v = make_float2(sig[q], sig[N + q]);
+            }
+            stage.z[sy][sx] = z;
+            stage.s[sy][sx] = v;
         }
+        __syncthreads();
+    }
+    if (many) {
+        if (need) short7_lane(k, stage, zn, gz, threadIdx.x, threadIdx.y, Gc, Gv, tile, gsz, gsn);
     } else {
         while (todo) {
             const int src = __ffs(todo) - 1;

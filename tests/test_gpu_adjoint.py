@@ -216,3 +216,30 @@ def test_level_records_grow_with_the_level_count():
     assert torch.equal(out, out_f)
     assert float((g_sig - g_sig_f).abs().max()) <= 1e-6 * float(g_sig_f.abs().max())
     assert torch.allclose(g_sigma, g_sigma_f, rtol=1e-5, atol=1e-7)
+
+
+def test_backward_on_a_caller_stream():
+    """Forward and backward issued on a side stream of the caller's: after
+    synchronising only that stream the gradients are complete (the tape's own
+    streams join it before the call returns) and equal the default stream's."""
+    W, H, F = 64, 40, 5
+    zn, mesh, cams, sig, g_out = _inputs(W, H, F, seed=8)
+    gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
+    gp = dhrs.SvgfParams()
+    sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
+    gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
+    ref = dhrs.SvgfTape(W, H, F)
+    ref.forward(gbufs, cams, sig_t, gp)
+    g_ref, s_ref = ref.backward(gbufs, cams, sig_t, gp, gout_t)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    tape = dhrs.SvgfTape(W, H, F)
+    with torch.cuda.stream(side):
+        tape.forward(gbufs, cams, sig_t, gp, stream=side)
+        g_sig, g_sigma = tape.backward(gbufs, cams, sig_t, gp, gout_t, stream=side)
+        host = (g_sig.to("cpu", non_blocking=False), g_sigma.to("cpu", non_blocking=False))
+    side.synchronize()
+    scale = float(g_ref.abs().max())
+    assert float((host[0] - g_ref.cpu()).abs().max()) <= 1e-6 * scale
+    assert torch.allclose(host[1], s_ref.cpu(), rtol=1e-5, atol=1e-7)
