@@ -438,7 +438,7 @@ def run_ours(args):
 SERVE_BATCH_PX = int(os.environ.get("DHR_SERVE_BATCH_PX", str(2 << 20)))
 
 
-def run_serving(sc, scene_d, seconds=2.0, n_sessions=32, budget=64 << 30, max_batch_px=SERVE_BATCH_PX,
+def run_serving(sc, scene_d, seconds=10.0, n_sessions=32, budget=64 << 30, max_batch_px=SERVE_BATCH_PX,
                 mode="host"):
     """32 thin-client sessions, resolutions drawn from {640x360, 1280x720,
     1920x1080, 2560x1440}, each sending camera poses as a 60 Hz Poisson
@@ -857,7 +857,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the serving, FP16 and adjoint measurements")
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-pixels", type=int, default=4096)
     ap.add_argument("--ref-pixels", type=int, default=24)
     ap.add_argument("--primary", default="raster", choices=["raster", "traverse"],
