@@ -616,8 +616,8 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
     tape = dhrs.SvgfTape(W, H, frames, dhrs.TAPE_RECOMPUTE)
     fwd, bwd = time_fb(tape)
     # algorithmic bytes per pixel and frame (each buffer read or written once
-    # per kernel): forward 340 as the SVGF frame + the records (weight sums
-    # 8 per level, last output 16); backward per level pass A 176 (input 16,
+    # per kernel): forward 340 as the SVGF frame + the records of a recorded
+    # frame (weight sums 8 per level, last output 16); backward per level pass A 176 (input 16,
     # G-buffer 16, weight sums 8, output 16, upstream gradient 16, sigma
     # terms 32 read + written, records 64 written) and pass B 112 (records
     # 64, input 16, G-buffer 16, gradient 16 written), temporal backward 180;
@@ -627,7 +627,8 @@ def run_adjoint(sc, scene_d, frames=8, W=1280, H=720, fit_steps=4):
     L = p.levels
     px = W * H
     bwd_px = L * (176 + 112) + 180
-    bytes_fwd = frames * px * (340 + L * 8 + 16)
+    # (the recomputing tape's forward records only the last two frames)
+    bytes_fwd = frames * px * 340 + min(frames, 2) * px * (L * 8 + 16)
     bytes_bwd = frames * px * bwd_px + max(frames - 2, 0) * px * 296
     bytes_bwd_s = frames * px * bwd_px
     bytes_fb = bytes_fwd + bytes_bwd

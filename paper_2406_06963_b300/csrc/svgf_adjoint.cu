@@ -942,10 +942,22 @@ extern "C" dhr_status dhr_svgf_seq_forward(dhr_svgf_tape* t, const dhr_gbuffer* 
             DHR_CUDA_TRY(cudaGetLastError());
             continue;
         }
-        const LevelSlot s{t, N, L, store ? f : (f & 1)};
-        DHR_TRY(run_levels(k, nsq, st, gc, illum, s, t->col, ao, sh));
+        const float4* last_out;
+        if (store || f + 2 >= t->F) {   // records kept: every frame, or the last two
+            const LevelSlot s{t, N, L, store ? f : (f & 1)};
+            DHR_TRY(run_levels(k, nsq, st, gc, illum, s, t->col, ao, sh));
+            last_out = s.out(0);
+        } else {   // the backward recomputes this frame's records: plain levels
+            const float4* in = illum;
+            for (int l = 0; l < L; ++l) {
+                const int mode = (l == L - 1 && L > 1) ? 2 : (l == 0 ? 1 : 0);
+                DHR_TRY(launch_atrous<DHR_FP32>(mode, nsq, 2, st, k, 1 << l, gc, in, t->lev[l & 1], t->col, ao, sh));
+                in = t->lev[l & 1];
+            }
+            last_out = t->lev[0];
+        }
         if (L == 1) {
-            passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, s.out(0), t->col, ao, sh);
+            passthrough_kernel<DHR_FP32><<<(int)((N + 255) / 256), 256, 0, st>>>((int)N, last_out, t->col, ao, sh);
             DHR_CUDA_TRY(cudaGetLastError());
         }
     }
