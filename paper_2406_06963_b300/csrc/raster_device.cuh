@@ -153,13 +153,21 @@ __device__ __forceinline__ void tri_bounds(const RasterConsts& rc, float3 v0, fl
 }
 
 // ---------------------------------------------------------------- binning
-constexpr int kBigTiles = 256;          // more tiles: binned by a whole block
+// A triangle over at most kLaneTiles tiles is binned by its own thread; one
+// over more, up to kBigTiles, is listed and later binned by a warp; one over
+// more than kBigTiles is listed and binned by a whole block.  The lists let
+// the triangles of a chunk near the camera spread over the whole GPU instead
+// of running one after another on the chunk's block.
+constexpr int kLaneTiles = 32;
+constexpr int kBigTiles = 256;
 constexpr int kBigGrid = 148 * 4;
 
 struct BinLayout {
     TileStore ts;        // the tiles' lists (G-buffer depth storage)
     uint32_t* big;       // [1 + big_cap]: number of big triangles, then their leaves
     uint32_t big_cap;
+    uint32_t* med;       // [1 + med_cap]: number of medium triangles, then their leaves
+    uint32_t med_cap;
     int tiles_x, n_tiles;
 };
 
@@ -217,7 +225,6 @@ __device__ __forceinline__ bool chunk_outside(const SceneView& sc, const RasterC
 __device__ __forceinline__ void bin_chunk(const SceneView& sc, const RasterConsts& rc, const BinLayout& b, int chunk) {
     if (chunk_outside(sc, rc, chunk)) return;   // uniform over the block
     const int leaf = chunk * kChunk + (int)threadIdx.x;
-    const int lane = threadIdx.x & 31;
     int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
     uint32_t entry = (uint32_t)leaf;
     if (leaf < sc.n_tris) {
@@ -230,52 +237,56 @@ __device__ __forceinline__ void bin_chunk(const SceneView& sc, const RasterConst
     const int tx0 = x0 / kRasterTileW, tx1 = x1 / kRasterTileW, ty0 = y0 / kRasterTileH, ty1 = y1 / kRasterTileH;
     const int ntx = any ? tx1 - tx0 + 1 : 0, nty = any ? ty1 - ty0 + 1 : 0;
     const int nt = ntx * nty;
-    if (nt > 0 && nt <= 32) bin_tiles(b, tx0, ty0, ntx, 0, 1, nt, entry);
-    if (nt > kBigTiles) {
-        const uint32_t slot = atomicAdd(b.big, 1u);
-        if (slot < b.big_cap) b.big[1 + slot] = (uint32_t)leaf;   // else: bin_big marks every tile
-    }
-    unsigned big = __ballot_sync(0xffffffffu, nt > 32 && nt <= kBigTiles);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const int s_tx0 = __shfl_sync(0xffffffffu, tx0, src), s_ty0 = __shfl_sync(0xffffffffu, ty0, src);
-        const int s_ntx = __shfl_sync(0xffffffffu, ntx, src), s_nt = __shfl_sync(0xffffffffu, nt, src);
-        const uint32_t s_entry = __shfl_sync(0xffffffffu, entry, src);
-        bin_tiles(b, s_tx0, s_ty0, s_ntx, lane, 32, s_nt, s_entry);
+    if (nt > 0 && nt <= kLaneTiles) bin_tiles(b, tx0, ty0, ntx, 0, 1, nt, entry);
+    if (nt > kLaneTiles) {   // listed; on overflow bin_big marks every tile
+        uint32_t* list = nt > kBigTiles ? b.big : b.med;
+        const uint32_t cap = nt > kBigTiles ? b.big_cap : b.med_cap;
+        const uint32_t slot = atomicAdd(list, 1u);
+        if (slot < cap) list[1 + slot] = (uint32_t)leaf;
     }
 }
 
-// The listed big triangles, one block each (threads stride over its tiles);
-// if the list overflowed, the bins are incomplete and every tile is marked
-// to be traversed instead.  Block `blk` of `nblk` (every thread of the block
-// calls it).
+// Bins listed triangle `leaf` with `n` threads of which this is number
+// `first` (its bounds as when it was listed).
+__device__ __forceinline__ void bin_listed(const SceneView& sc, const RasterConsts& rc, const BinLayout& b,
+                                           uint32_t leaf, int first, int n) {
+    const float4* tr = sc.tris + 3 * (size_t)leaf;
+    const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
+    int x0, x1, y0, y1;
+    tri_bounds(rc, v0, v1, v2, x0, x1, y0, y1);
+    if (x0 > x1 || y0 > y1) return;   // not for a listed triangle
+    const uint32_t entry = leaf | (sliver(v0, v1, v2) ? kThinBit : 0u);
+    const int tx0 = x0 / kRasterTileW, ty0 = y0 / kRasterTileH;
+    const int ntx = x1 / kRasterTileW - tx0 + 1, nt = ntx * (y1 / kRasterTileH - ty0 + 1);
+    bin_tiles(b, tx0, ty0, ntx, first, n, nt, entry);
+}
+
+// The listed triangles: the big ones one block each (threads stride over
+// its tiles), the medium ones one warp each; if a list overflowed, the bins
+// are incomplete and every tile is marked to be traversed instead.  Block
+// `blk` of `nblk` (every thread of the block calls it).
 __device__ __forceinline__ void bin_big(const SceneView& sc, const RasterConsts& rc, const BinLayout& b, int blk,
                                         int nblk) {
-    const uint32_t nb = b.big[0];
-    if (nb > b.big_cap) {
+    const uint32_t nb = b.big[0], nm = b.med[0];
+    if (nb > b.big_cap || nm > b.med_cap) {
         for (int t = blk * (int)blockDim.x + (int)threadIdx.x; t < b.n_tiles; t += nblk * (int)blockDim.x)
             *tile_word(b.ts, t % b.tiles_x, t / b.tiles_x, 0) = 0xFFFFFFFFu;
         return;
     }
-    for (uint32_t k = (uint32_t)blk; k < nb; k += (uint32_t)nblk) {
-        const uint32_t leaf = b.big[1 + k];
-        const float4* tr = sc.tris + 3 * (size_t)leaf;
-        const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
-        int x0, x1, y0, y1;
-        tri_bounds(rc, v0, v1, v2, x0, x1, y0, y1);
-        if (x0 > x1 || y0 > y1) continue;   // not for a listed triangle (same bounds as when listed)
-        const uint32_t entry = leaf | (sliver(v0, v1, v2) ? kThinBit : 0u);
-        const int tx0 = x0 / kRasterTileW, ty0 = y0 / kRasterTileH;
-        const int ntx = x1 / kRasterTileW - tx0 + 1, nt = ntx * (y1 / kRasterTileH - ty0 + 1);
-        bin_tiles(b, tx0, ty0, ntx, threadIdx.x, blockDim.x, nt, entry);
-    }
+    const int lane = threadIdx.x & 31, wpb = (int)blockDim.x >> 5;
+    for (uint32_t k = (uint32_t)(blk * wpb + ((int)threadIdx.x >> 5)); k < nm; k += (uint32_t)(nblk * wpb))
+        bin_listed(sc, rc, b, b.med[1 + k], lane, 32);
+    for (uint32_t k = (uint32_t)blk; k < nb; k += (uint32_t)nblk)
+        bin_listed(sc, rc, b, b.big[1 + k], threadIdx.x, blockDim.x);
 }
 
-// clears entry t of the tile counts (t == 0 also the big list's count)
+// clears entry t of the tile counts (t == 0 also the lists' counts)
 __device__ __forceinline__ void bin_clear(const BinLayout& b, int t) {
     if (t < b.n_tiles) *tile_word(b.ts, t % b.tiles_x, t / b.tiles_x, 0) = 0u;
-    if (t == 0) b.big[0] = 0u;
+    if (t == 0) {
+        b.big[0] = 0u;
+        b.med[0] = 0u;
+    }
 }
 
 
@@ -294,9 +305,12 @@ __host__ __device__ inline bool make_raster(const dhr_camera& cam, void* depth_n
     const int W = cam.width, H = cam.height;
     b.tiles_x = (W + kRasterTileW - 1) / kRasterTileW;
     const long long n_tiles = (long long)b.tiles_x * ((H + kRasterTileH - 1) / kRasterTileH);
-    const unsigned long long words = (unsigned long long)W * H;   // the mesh-id buffer holds the big list
+    // the mesh-id buffer (W H words) holds the big list, then the medium list
+    const unsigned long long words = (unsigned long long)W * H;
     b.big_cap = (uint32_t)(words / 64 < 4096 ? words / 64 : 4096);
     if (b.big_cap < 16 || n_tiles >= (1ll << 31)) return false;
+    const unsigned long long med_words = words - 2 - b.big_cap;
+    b.med_cap = (uint32_t)(med_words < (1ull << 24) ? med_words : (1ull << 24));
     b.n_tiles = (int)n_tiles;
     double inv[3][3];
     for (int r = 0; r < 3; ++r)
@@ -332,6 +346,7 @@ __host__ __device__ inline bool make_raster(const dhr_camera& cam, void* depth_n
     for (int k = 0; k < 4; ++k) rc.pn[k] = make_float3((float)n[k][0], (float)n[k][1], (float)n[k][2]);
     b.ts = TileStore{reinterpret_cast<uint32_t*>(depth_normal), W, H, ew};
     b.big = mesh_id;
+    b.med = mesh_id + 1 + b.big_cap;
     return true;
 }
 

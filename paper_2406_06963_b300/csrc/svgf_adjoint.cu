@@ -355,17 +355,15 @@ struct Short7 {
 };
 
 // Adds tap (dx, dy) of pixel (x, y), read from the buffers (the warp-
-// cooperative path).  The tap's loads are issued before it is tested: with
-// kCheck a tap outside the image reads the clamped pixel and is masked; a
-// background tap (depth +inf) has weight exactly 0 and is masked likewise.
-template <bool kCheck>
+// cooperative path).  The tap's loads are issued before it is tested: a tap
+// outside the image reads the clamped pixel and is masked; a background tap
+// (depth +inf) has weight exactly 0 and is masked likewise.
 __device__ __forceinline__ void short7_tap(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
                                            float4 zn, float2 gz, int x, int y, int dx, int dy, Short7& a) {
     using S = Store<DHR_FP32>;
     const int qx = x + dx, qy = y + dy;
-    const bool in = !kCheck || (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H);
-    const long long qi = kCheck ? (long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1)
-                                : (long long)qy * k.W + qx;
+    const bool in = qx >= 0 && qy >= 0 && qx < k.W && qy < k.H;
+    const long long qi = (long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1);
     const int q = (int)dbg_index(qi, (long long)N, kSiteAdjoint);
     const float4 zq = S::g(g_cur, q);
     const float sx = sig[q], sy = sig[N + q];
@@ -405,16 +403,14 @@ __device__ __forceinline__ ShortG short7_finish(const Short7& a, float2 Gc, floa
 // (origin bx0, by0: the block's first pixel minus the apron), and the tap's
 // sigma terms dL/d w_q d w_q / d sigma into gsz, gsn (d w / d sigma_z = w
 // |dz| a_off / D^2, d w / d sigma_n = w ln(n . n_q))
-template <bool kCheck>
 __device__ __forceinline__ void short7_scatter(const SvgfConsts& k, const float4* g_cur, const float* sig, int N,
                                                float4 zn, float2 gz, int x, int y, int dx, int dy, const ShortG& G,
                                                float (*tile)[kTH][kTW], int bx0, int by0, float& gsz,
                                                float& gsn) {
     using S = Store<DHR_FP32>;
     const int qx = x + dx, qy = y + dy;
-    const bool in = !kCheck || (qx >= 0 && qy >= 0 && qx < k.W && qy < k.H);
-    const long long qi = kCheck ? (long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1)
-                                : (long long)qy * k.W + qx;
+    const bool in = qx >= 0 && qy >= 0 && qx < k.W && qy < k.H;
+    const long long qi = (long long)min(max(qy, 0), k.H - 1) * k.W + min(max(qx, 0), k.W - 1);
     const int q = (int)dbg_index(qi, (long long)N, kSiteAdjoint);
     const float4 zq = S::g(g_cur, q);
     const float sx = sig[q], sy = sig[N + q];
@@ -566,7 +562,7 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
 #pragma unroll
             for (int it = 0; it < 2; ++it) {
                 const int t = lane + 32 * it;
-                if (t < 49) short7_tap<true>(k, g_cur, sig, N, pz, pg, px, py, t % 7 - 3, t / 7 - 3, acc);
+                if (t < 49) short7_tap(k, g_cur, sig, N, pz, pg, px, py, t % 7 - 3, t / 7 - 3, acc);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -582,7 +578,7 @@ __global__ void __launch_bounds__(kThreadsA, 4) temporal_bwd_kernel(
             for (int it = 0; it < 2; ++it) {
                 const int t = lane + 32 * it;
                 if (t < 49)
-                    short7_scatter<true>(k, g_cur, sig, N, pz, pg, px, py, t % 7 - 3, t / 7 - 3, G, tile, bx0, by0,
+                    short7_scatter(k, g_cur, sig, N, pz, pg, px, py, t % 7 - 3, t / 7 - 3, G, tile, bx0, by0,
                                          dz_s, dn_s);
             }
 #pragma unroll
