@@ -155,16 +155,17 @@ __device__ __forceinline__ void tri_bounds(const RasterConsts& rc, float3 v0, fl
 // ---------------------------------------------------------------- binning
 // A triangle over at most kLaneTiles tiles is binned by its own thread; one
 // over more, up to kBigTiles, is listed and later binned by a warp; one over
-// more than kBigTiles is listed and binned by a whole block.  The lists let
-// the triangles of a chunk near the camera spread over the whole GPU instead
-// of running one after another on the chunk's block.
+// more than kBigTiles is listed in pieces of kBigPiece tiles, each binned by a
+// whole block.  The lists let the triangles of a chunk near the camera, and
+// the tiles of a triangle that fills the screen, spread over the whole GPU.
 constexpr int kLaneTiles = 32;
 constexpr int kBigTiles = 256;
+constexpr int kBigPiece = 1024;   // 128 threads x kBatch atomics in flight
 constexpr int kBigGrid = 148 * 4;
 
 struct BinLayout {
     TileStore ts;        // the tiles' lists (G-buffer depth storage)
-    uint32_t* big;       // [1 + big_cap]: number of big triangles, then their leaves
+    uint32_t* big;       // [1 + 2 big_cap]: number of big pieces, then (leaf, piece) pairs
     uint32_t big_cap;
     uint32_t* med;       // [1 + med_cap]: number of medium triangles, then their leaves
     uint32_t med_cap;
@@ -238,18 +239,25 @@ __device__ __forceinline__ void bin_chunk(const SceneView& sc, const RasterConst
     const int ntx = any ? tx1 - tx0 + 1 : 0, nty = any ? ty1 - ty0 + 1 : 0;
     const int nt = ntx * nty;
     if (nt > 0 && nt <= kLaneTiles) bin_tiles(b, tx0, ty0, ntx, 0, 1, nt, entry);
-    if (nt > kLaneTiles) {   // listed; on overflow bin_big marks every tile
-        uint32_t* list = nt > kBigTiles ? b.big : b.med;
-        const uint32_t cap = nt > kBigTiles ? b.big_cap : b.med_cap;
-        const uint32_t slot = atomicAdd(list, 1u);
-        if (slot < cap) list[1 + slot] = (uint32_t)leaf;
+    // listed (on overflow bin_big marks every tile)
+    if (nt > kBigTiles) {
+        const uint32_t np = (uint32_t)((nt + kBigPiece - 1) / kBigPiece);
+        const uint32_t slot = atomicAdd(b.big, np);
+        if (slot + np <= b.big_cap)
+            for (uint32_t c = 0; c < np; ++c) {
+                b.big[1 + 2 * (slot + c)] = (uint32_t)leaf;
+                b.big[2 + 2 * (slot + c)] = c;
+            }
+    } else if (nt > kLaneTiles) {
+        const uint32_t slot = atomicAdd(b.med, 1u);
+        if (slot < b.med_cap) b.med[1 + slot] = (uint32_t)leaf;
     }
 }
 
-// Bins listed triangle `leaf` with `n` threads of which this is number
-// `first` (its bounds as when it was listed).
+// Bins tiles first, first + n, ... below `limit` of listed triangle `leaf`
+// (its bounds as when it was listed).
 __device__ __forceinline__ void bin_listed(const SceneView& sc, const RasterConsts& rc, const BinLayout& b,
-                                           uint32_t leaf, int first, int n) {
+                                           uint32_t leaf, int first, int n, int limit) {
     const float4* tr = sc.tris + 3 * (size_t)leaf;
     const float3 v0 = f3(__ldg(tr)), v1 = f3(__ldg(tr + 1)), v2 = f3(__ldg(tr + 2));
     int x0, x1, y0, y1;
@@ -258,13 +266,14 @@ __device__ __forceinline__ void bin_listed(const SceneView& sc, const RasterCons
     const uint32_t entry = leaf | (sliver(v0, v1, v2) ? kThinBit : 0u);
     const int tx0 = x0 / kRasterTileW, ty0 = y0 / kRasterTileH;
     const int ntx = x1 / kRasterTileW - tx0 + 1, nt = ntx * (y1 / kRasterTileH - ty0 + 1);
-    bin_tiles(b, tx0, ty0, ntx, first, n, nt, entry);
+    bin_tiles(b, tx0, ty0, ntx, first, n, min(nt, limit), entry);
 }
 
-// The listed triangles: the big ones one block each (threads stride over
-// its tiles), the medium ones one warp each; if a list overflowed, the bins
-// are incomplete and every tile is marked to be traversed instead.  Block
-// `blk` of `nblk` (every thread of the block calls it).
+// The listed triangles: each piece of a big one by one block (threads
+// stride over its kBigPiece tiles), each medium one by one warp; if a list
+// overflowed, the bins are incomplete and every tile is marked to be
+// traversed instead.  Block `blk` of `nblk` (every thread of the block calls
+// it).
 __device__ __forceinline__ void bin_big(const SceneView& sc, const RasterConsts& rc, const BinLayout& b, int blk,
                                         int nblk) {
     const uint32_t nb = b.big[0], nm = b.med[0];
@@ -275,9 +284,12 @@ __device__ __forceinline__ void bin_big(const SceneView& sc, const RasterConsts&
     }
     const int lane = threadIdx.x & 31, wpb = (int)blockDim.x >> 5;
     for (uint32_t k = (uint32_t)(blk * wpb + ((int)threadIdx.x >> 5)); k < nm; k += (uint32_t)(nblk * wpb))
-        bin_listed(sc, rc, b, b.med[1 + k], lane, 32);
-    for (uint32_t k = (uint32_t)blk; k < nb; k += (uint32_t)nblk)
-        bin_listed(sc, rc, b, b.big[1 + k], threadIdx.x, blockDim.x);
+        bin_listed(sc, rc, b, b.med[1 + k], lane, 32, kBigTiles);
+    for (uint32_t k = (uint32_t)blk; k < nb; k += (uint32_t)nblk) {
+        const int piece = (int)b.big[2 + 2 * k];
+        bin_listed(sc, rc, b, b.big[1 + 2 * k], piece * kBigPiece + (int)threadIdx.x, blockDim.x,
+                   (piece + 1) * kBigPiece);
+    }
 }
 
 // clears entry t of the tile counts (t == 0 also the lists' counts)
@@ -307,9 +319,9 @@ __host__ __device__ inline bool make_raster(const dhr_camera& cam, void* depth_n
     const long long n_tiles = (long long)b.tiles_x * ((H + kRasterTileH - 1) / kRasterTileH);
     // the mesh-id buffer (W H words) holds the big list, then the medium list
     const unsigned long long words = (unsigned long long)W * H;
-    b.big_cap = (uint32_t)(words / 64 < 4096 ? words / 64 : 4096);
+    b.big_cap = (uint32_t)(words / 16 < 65536 ? words / 16 : 65536);
     if (b.big_cap < 16 || n_tiles >= (1ll << 31)) return false;
-    const unsigned long long med_words = words - 2 - b.big_cap;
+    const unsigned long long med_words = words - 2 - 2ull * b.big_cap;
     b.med_cap = (uint32_t)(med_words < (1ull << 24) ? med_words : (1ull << 24));
     b.n_tiles = (int)n_tiles;
     double inv[3][3];
@@ -346,7 +358,7 @@ __host__ __device__ inline bool make_raster(const dhr_camera& cam, void* depth_n
     for (int k = 0; k < 4; ++k) rc.pn[k] = make_float3((float)n[k][0], (float)n[k][1], (float)n[k][2]);
     b.ts = TileStore{reinterpret_cast<uint32_t*>(depth_normal), W, H, ew};
     b.big = mesh_id;
-    b.med = mesh_id + 1 + b.big_cap;
+    b.med = mesh_id + 1 + 2 * b.big_cap;
     return true;
 }
 

@@ -67,14 +67,23 @@ def test_ragged_sizes(boxes, w, h):
 
 
 def test_small_images_and_list_overflow(boxes):
-    """Close-ups at 16 x 16 (no room for the bins: traversed), 24 x 20 and
-    40 x 32 (the bins fit); terrain776k at 64 x 36: about 10^5 (tile,
-    triangle) pairs for about 2,100 list slots, so the tiles whose lists do
-    not fit are traversed."""
-    for w, h in ((16, 16), (24, 20), (40, 32)):
+    """Close-ups at 15 x 15 (no room for the lists in the mesh-id buffer:
+    traversed), 16 x 16, 24 x 20 and 40 x 32; terrain776k at 64 x 36: about
+    10^5 (tile, triangle) pairs for about 2,100 list slots, so the tiles whose
+    lists do not fit are traversed."""
+    for w, h in ((15, 15), (16, 16), (24, 20), (40, 32)):
         _same(boxes, wl.look_at((0.5, 1.0, 2.5), (0.0, 0.5, 0.0), w, h, fov_y_deg=100.0), frame=2)
     s = wl.scene_terrain()
     _same(dhrs.Scene(s), wl.spline_path(s["terrain"], 60, 64, 36)[10], frame=10)
+
+
+def test_screen_filling_triangles(boxes):
+    """A close-up at 512 x 256 (4,096 tiles): the ground's two triangles each
+    cover more than one 1,024-tile piece of the big list, the boxes' faces
+    fall in the medium list (33-256 tiles) and in the threads' own range."""
+    cam = wl.look_at((0.5, 1.0, 2.5), (0.0, 0.5, 0.0), 512, 256, fov_y_deg=100.0)
+    out = _same(boxes, cam, frame=2)
+    assert (out["mesh"].view(np.uint32) != 0xFFFFFFFF).mean() > 0.5
 
 
 def test_camera_inside_closed_sphere():
