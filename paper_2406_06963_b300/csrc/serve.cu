@@ -70,6 +70,9 @@ struct ServeItem {
     int raster;              // primary visibility rasterised (tile lists in g_cur, big list in m_cur)
     RasterConsts rc;
     BinLayout bl;
+    int raster_tgt;          // the warp target's primary visibility rasterised (lists in g_tgt, m_tgt)
+    RasterConsts rc_tgt;
+    BinLayout bl_tgt;
 };
 
 struct BatchTable {
@@ -107,7 +110,10 @@ __global__ void __launch_bounds__(256, 4) serve_trace_kernel(SceneView sc, const
         const ServeItem& it = b.items[find_item(b, t)];
         const int2 px = trace_thread_pixel(tile_origin(it, t));
         if (primary_target) {
-            if (it.warp)
+            if (it.warp && it.raster_tgt)
+                trace_pixel<false, false, true, false, true, 8>(sc, it.tk_target, px, it.g_tgt, it.m_tgt, nullptr,
+                                                                nullptr, nullptr);
+            else if (it.warp)
                 trace_pixel<false, false, true, false, false, 8>(sc, it.tk_target, px, it.g_tgt, it.m_tgt, nullptr,
                                                                  nullptr, nullptr);
         } else if (it.raster) {
@@ -119,33 +125,46 @@ __global__ void __launch_bounds__(256, 4) serve_trace_kernel(SceneView sc, const
     }
 }
 
-// rasterised primary visibility of the batch's items with raster set: clear
-// their tile counts, bin every chunk of the scene, bin the big triangles
+// rasterised primary visibility of the batch's items with raster (the
+// traced pose) or raster_tgt (the warp's target pose) set: clear their tile
+// counts, bin every chunk of the scene, bin the listed triangles.  Layout 0
+// of an item is its traced pose's, layout 1 its target's.
+__device__ __forceinline__ bool bin_layout(const ServeItem& it, int l, const RasterConsts*& rc,
+                                           const BinLayout*& bl) {
+    if (it.tiles_x == 0 || !(l == 0 ? it.raster : it.raster_tgt)) return false;
+    rc = l == 0 ? &it.rc : &it.rc_tgt;
+    bl = l == 0 ? &it.bl : &it.bl_tgt;
+    return true;
+}
+
 __global__ void __launch_bounds__(256) serve_bin_clear_kernel(const BatchTable* tb) {
     const BatchTable& b = *tb;
-    for (int i = 0; i < b.n_items; ++i) {
-        const ServeItem& it = b.items[i];
-        if (!it.raster || it.tiles_x == 0) continue;
-        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < it.bl.n_tiles; t += gridDim.x * blockDim.x)
-            bin_clear(it.bl, t);
+    for (int i = 0; i < 2 * b.n_items; ++i) {
+        const RasterConsts* rc;
+        const BinLayout* bl;
+        if (!bin_layout(b.items[i >> 1], i & 1, rc, bl)) continue;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < bl->n_tiles; t += gridDim.x * blockDim.x)
+            bin_clear(*bl, t);
     }
 }
 
 __global__ void __launch_bounds__(kChunk) serve_bin_kernel(SceneView sc, const BatchTable* tb) {
     const BatchTable& b = *tb;
     const int chunks = (sc.n_tris + kChunk - 1) / kChunk;
-    for (int i = 0; i < b.n_items; ++i) {
-        const ServeItem& it = b.items[i];
-        if (!it.raster || it.tiles_x == 0) continue;
-        for (int c = blockIdx.x; c < chunks; c += gridDim.x) bin_chunk(sc, it.rc, it.bl, c);
+    for (int i = 0; i < 2 * b.n_items; ++i) {
+        const RasterConsts* rc;
+        const BinLayout* bl;
+        if (!bin_layout(b.items[i >> 1], i & 1, rc, bl)) continue;
+        for (int c = blockIdx.x; c < chunks; c += gridDim.x) bin_chunk(sc, *rc, *bl, c);
     }
 }
 
 __global__ void __launch_bounds__(128) serve_bin_big_kernel(SceneView sc, const BatchTable* tb) {
     const BatchTable& b = *tb;
-    for (int i = 0; i < b.n_items; ++i) {
-        const ServeItem& it = b.items[i];
-        if (it.raster && it.tiles_x > 0) bin_big(sc, it.rc, it.bl, blockIdx.x, gridDim.x);
+    for (int i = 0; i < 2 * b.n_items; ++i) {
+        const RasterConsts* rc;
+        const BinLayout* bl;
+        if (bin_layout(b.items[i >> 1], i & 1, rc, bl)) bin_big(sc, *rc, *bl, blockIdx.x, gridDim.x);
     }
 }
 
@@ -576,6 +595,8 @@ __global__ void __launch_bounds__(1024) loop_schedule_kernel(int li, LoopCtl* ct
         // (the tile layout follows the camera's size, which must be the session's)
         it.raster = (uint64_t)sl.w * sl.h >= meta->raster_min_px && cam.width == sl.w && cam.height == sl.h &&
                     make_raster(cam, it.g_cur, it.m_cur, 4, it.rc, it.bl);
+        it.raster_tgt = warp && (uint64_t)sl.w * sl.h >= meta->raster_min_px && cam_t.width == sl.w &&
+                        cam_t.height == sl.h && make_raster(cam_t, it.g_tgt, it.m_tgt, 4, it.rc_tgt, it.bl_tgt);
         __threadfence_system();
         valid = valid && ld_acquire_sys(&m.seq) == sreq[id] && ld_acquire_sys(&sl.generation) == sgen[id];
         if (valid) {
@@ -588,6 +609,7 @@ __global__ void __launch_bounds__(1024) loop_schedule_kernel(int li, LoopCtl* ct
             // the session's buffers (the loop that claimed it is using them)
             it.tiles_x = 0;
             it.raster = 0;
+            it.raster_tgt = 0;
             if (claimed) {
                 __threadfence();
                 atomicExch(&d.busy, 0u);
@@ -1482,6 +1504,8 @@ extern "C" dhr_status dhr_server_pump(dhr_server* s, int32_t* launched) {
         it.fin_sh = se.fin_sh;
         it.raster = s->tp.primary == DHR_PRIMARY_RASTER && px >= s->raster_min_px && s->scene->n_tris > 0 &&
                     make_raster(r.cam, it.g_cur, it.m_cur, 4, it.rc, it.bl);
+        it.raster_tgt = it.warp && s->tp.primary == DHR_PRIMARY_RASTER && px >= s->raster_min_px &&
+                        s->scene->n_tris > 0 && make_raster(r.cam_target, it.g_tgt, it.m_tgt, 4, it.rc_tgt, it.bl_tgt);
         ++b.n_items;
         se.cur = cur;
         se.cam_prev = r.cam;
