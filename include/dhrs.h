@@ -674,8 +674,8 @@ dhr_status dhr_server_set_max_batch_pixels(dhr_server* server, uint64_t max_pixe
  * (when the server's trace params ask for DHR_PRIMARY_RASTER, the default);
  * smaller ones trace primary rays.  Both give the same G-buffer bit for bit:
  * the choice is speed only (the binning pass costs about the same at every
- * resolution).  Default 1,572,864 pixels; 0 = every session, UINT64_MAX =
- * none.  Takes effect for batches formed afterwards (a running device loop
+ * resolution; at and above 640 x 360 it is faster than primary rays).
+ * Default 131,072 pixels; 0 = every session, UINT64_MAX = none.  Takes effect for batches formed afterwards (a running device loop
  * keeps the value it started with).  Errors: DHR_ERR_INVALID for a null
  * server. */
 dhr_status dhr_server_set_raster_min_pixels(dhr_server* server, uint64_t min_pixels);

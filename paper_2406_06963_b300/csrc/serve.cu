@@ -39,7 +39,7 @@ constexpr int kTileW = 32, kTileH = 8;
 // sessions of at least this many pixels rasterise their primary visibility
 // (the binning pass costs about the same at every resolution, the traversal
 // it replaces grows with the pixels: measured break-even near 1.1 Mpx)
-constexpr uint64_t kDefaultRasterMinPx = 3u << 19;
+constexpr uint64_t kDefaultRasterMinPx = 1u << 17;
 
 struct ServeItem {
     TraceConsts tk;          // traced pose and trace parameters

@@ -206,14 +206,19 @@ def test_server_latest_request_wins():
     assert srv.stats()["dropped"] == 1
 
 
-def test_server_delay_warp_equals_components():
+@pytest.mark.parametrize("raster_min", [None, 0])
+def test_server_delay_warp_equals_components(raster_min):
     """A request with a target pose = trace + SVGF at the sent pose, then
-    dhr_delay_warp onto a G-buffer of the target pose."""
+    dhr_delay_warp onto a G-buffer of the target pose.  raster_min 0: the
+    server rasterises both the traced pose's and the target pose's primary
+    visibility (binned into the session's and the target's buffers)."""
     s = wl.scene_boxes()
     sc = dhrs.Scene(s)
     W, H = 128, 96
     path = wl.orbit_path(8, W, H, degrees=14.0)
     srv = dhrs.Server(sc, 1 << 30)
+    if raster_min is not None:
+        srv.set_raster_min_pixels(raster_min)
     sid = srv.open(W, H)
     sess = dhrs.Session(sc, W, H)
     a = torch.empty((H, W), device="cuda")
@@ -323,6 +328,45 @@ def test_device_loop_equals_host_batches(no_gc, raster_min):
     assert running and passes > 0
     srv.loop_stop()
     assert not srv.loop_status()[0]
+
+
+def test_device_loop_delay_warp_equals_host_batches(no_gc):
+    """Requests with target poses, every session rasterising both poses:
+    the device loop (raster constants of both poses formed on the device)
+    and host-formed batches give bit-identical warped outputs."""
+    s = wl.scene_boxes()
+    sc = dhrs.Scene(s)
+    sessions = [(200, 120, wl.orbit_path(7, 200, 120, degrees=6.0)),
+                (96, 64, wl.orbit_path(7, 96, 64, degrees=9.0, start_deg=40))]
+    outs = {}
+    keep = []
+    for mode in ("host", "loop"):
+        srv = dhrs.Server(sc, 4 << 30)
+        keep.append(srv)   # destroying a server synchronises the device: not while a loop runs
+        srv.set_raster_min_pixels(0)
+        ids = [srv.open(w, h) for (w, h, _p) in sessions]
+        if mode == "loop":
+            srv.loop_start(idle_ms=5000, max_run_ms=60000)
+        res = []
+        for f in range(4):
+            for k, (w, h, path) in enumerate(sessions):
+                srv.submit(ids[k], path[f], f, dhrs.now_ns(), 1000 * k + f, cam_target=path[f + 3])
+            if mode == "host":
+                srv.pump()
+                done = srv.poll(wait=True)
+                while len([d for d in done if not d["dropped"]]) < len(sessions):
+                    done += srv.poll(wait=True)
+            else:
+                _collect(srv, len(sessions))
+            res.append([srv.output(ids[k], w, h) for k, (w, h, _p) in enumerate(sessions)])
+        if mode == "loop":
+            srv.loop_stop()
+        outs[mode] = res
+    for f in range(4):
+        for k in range(len(sessions)):
+            for c in range(2):
+                assert np.array_equal(outs["host"][f][k][c], outs["loop"][f][k][c]), (f, k, c)
+        assert float((outs["host"][f][0][0] == 1).mean()) < 0.9
 
 
 def test_device_loop_times_out_when_work_is_withheld(no_gc):
