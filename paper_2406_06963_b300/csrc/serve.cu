@@ -835,16 +835,26 @@ struct dhr_server {
     uint64_t max_batch_px = kDefaultBatchPx;   // pixel cap of one batch (0: none)
     uint64_t raster_min_px = kDefaultRasterMinPx;   // sessions from this size rasterise primaries
     cudaStream_t mem_stream = nullptr;  // session allocations (stream ordered)
+    // a batch graph's branch for the warp target's primary visibility (only
+    // used while graphs are captured; lowest priority)
+    cudaStream_t fork_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     LoopHost loop;
 };
 
 // the stages of one batch on `st`, all reading the batch table `tb`:
-// trace, temporal, a-trous levels, target G-buffer, delay warp
+// binning, trace, temporal, a-trous levels, delay warp; the warp target's
+// primary visibility needs only the bins, so it runs on a branch of its own
+// (fork_st) that joins before the warp
 static void launch_stages(const dhr_server* s, cudaStream_t st, const BatchTable* tb) {
     const SceneView sv = s->scene->view();
     serve_bin_clear_kernel<<<148 * 2, 256, 0, st>>>(tb);
     serve_bin_kernel<<<148 * 8, kChunk, 0, st>>>(sv, tb);
     serve_bin_big_kernel<<<kBigGrid, 128, 0, st>>>(sv, tb);
+    cudaEventRecord(s->ev_fork, st);
+    cudaStreamWaitEvent(s->fork_st, s->ev_fork, 0);
+    serve_trace_kernel<<<s->grid_trace, 256, 0, s->fork_st>>>(sv, tb, 1);
+    cudaEventRecord(s->ev_join, s->fork_st);
     serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, tb, 0);
     serve_temporal_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
     const int L = (int)s->sp.levels;
@@ -858,7 +868,7 @@ static void launch_stages(const dhr_server* s, cudaStream_t st, const BatchTable
         else serve_atrous_kernel<-1, 1><<<s->grid_px, dim3(32, 8), 0, st>>>(tb, l, mode);
     }
     if (L <= 1) serve_copy_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
-    serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, tb, 1);
+    cudaStreamWaitEvent(st, s->ev_join, 0);
     serve_warp_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
 }
 
@@ -875,7 +885,7 @@ static dhr_status capture_slot(dhr_server* s, Slot& sl) {
         return set_error(DHR_ERR_CUDA, "server: graph capture failed: %s",
                          cudaGetErrorString(e_launch != cudaSuccess ? e_launch : e_end));
     }
-    const cudaError_t e = cudaGraphInstantiate(&sl.graph, g, 0);
+    const cudaError_t e = cudaGraphInstantiate(&sl.graph, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     DHR_CUDA_TRY(e);
     return DHR_OK;
@@ -961,7 +971,9 @@ static dhr_status loop_create(dhr_server* s) {
     DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&slots_d, L.slots, 0));
     DHR_CUDA_TRY(cudaHostGetDevicePointer((void**)&ring_d, L.ring, 0));
     for (int li = 0; li < kLoops; ++li) {
-        DHR_CUDA_TRY(cudaStreamCreateWithFlags(&L.stream[li], cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        DHR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        DHR_CUDA_TRY(cudaStreamCreateWithPriority(&L.stream[li], cudaStreamNonBlocking, greatest));
         DHR_CUDA_TRY(cudaMalloc((void**)&L.d_meta[li], sizeof(LoopMeta)));
         DHR_CUDA_TRY(cudaMalloc((void**)&L.d_table[li], sizeof(BatchTable)));
         DHR_CUDA_TRY(cudaMemset(L.d_table[li], 0, sizeof(BatchTable)));
@@ -1011,7 +1023,7 @@ static dhr_status loop_create(dhr_server* s) {
                 if (!e) e = e2;
             }
         }
-        if (!e) e = cudaGraphInstantiate(&L.exec[li], g, 0);
+        if (!e) e = cudaGraphInstantiate(&L.exec[li], g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e) return set_error(DHR_ERR_CUDA, "server: device loop graph: %s", cudaGetErrorString(e));
     }
@@ -1161,6 +1173,9 @@ extern "C" void dhr_server_destroy(dhr_server* s) {
         cudaStreamDestroy(s->mem_stream);
     }
     if (s->ref) cudaEventDestroy(s->ref);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->fork_st) cudaStreamDestroy(s->fork_st);
     delete s;
 }
 
@@ -1182,11 +1197,18 @@ extern "C" dhr_status dhr_server_create(const dhr_scene* scene, uint64_t budget_
     s->grid_trace = sms * 4;
     s->grid_px = sms * 8;
     dhr_status st = DHR_OK;
-    if (cudaStreamCreateWithFlags(&s->mem_stream, cudaStreamNonBlocking) != cudaSuccess)
+    int least = 0, greatest = 0;
+    if (cudaStreamCreateWithFlags(&s->mem_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->fork_st, cudaStreamNonBlocking, least) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
         st = set_error(DHR_ERR_CUDA, "server_create: cannot create a stream");
     for (auto& sl : s->slots) {
         if (st != DHR_OK) break;
-        cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        int least = 0, greatest = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (!e) e = cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, greatest);
         if (!e) e = cudaEventCreateWithFlags(&sl.done, cudaEventDefault);
         if (!e) e = cudaMallocHost((void**)&sl.h_table, sizeof(BatchTable));
         if (!e) e = cudaMalloc((void**)&sl.d_table, sizeof(BatchTable));
