@@ -137,34 +137,34 @@ __device__ __forceinline__ bool bin_layout(const ServeItem& it, int l, const Ras
     return true;
 }
 
-__global__ void __launch_bounds__(256) serve_bin_clear_kernel(const BatchTable* tb) {
+__global__ void __launch_bounds__(256) serve_bin_clear_kernel(const BatchTable* tb, int layout) {
     const BatchTable& b = *tb;
-    for (int i = 0; i < 2 * b.n_items; ++i) {
+    for (int i = 0; i < b.n_items; ++i) {
         const RasterConsts* rc;
         const BinLayout* bl;
-        if (!bin_layout(b.items[i >> 1], i & 1, rc, bl)) continue;
+        if (!bin_layout(b.items[i], layout, rc, bl)) continue;
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < bl->n_tiles; t += gridDim.x * blockDim.x)
             bin_clear(*bl, t);
     }
 }
 
-__global__ void __launch_bounds__(kChunk) serve_bin_kernel(SceneView sc, const BatchTable* tb) {
+__global__ void __launch_bounds__(kChunk) serve_bin_kernel(SceneView sc, const BatchTable* tb, int layout) {
     const BatchTable& b = *tb;
     const int chunks = (sc.n_tris + kChunk - 1) / kChunk;
-    for (int i = 0; i < 2 * b.n_items; ++i) {
+    for (int i = 0; i < b.n_items; ++i) {
         const RasterConsts* rc;
         const BinLayout* bl;
-        if (!bin_layout(b.items[i >> 1], i & 1, rc, bl)) continue;
+        if (!bin_layout(b.items[i], layout, rc, bl)) continue;
         for (int c = blockIdx.x; c < chunks; c += gridDim.x) bin_chunk(sc, *rc, *bl, c);
     }
 }
 
-__global__ void __launch_bounds__(128) serve_bin_big_kernel(SceneView sc, const BatchTable* tb) {
+__global__ void __launch_bounds__(128) serve_bin_big_kernel(SceneView sc, const BatchTable* tb, int layout) {
     const BatchTable& b = *tb;
-    for (int i = 0; i < 2 * b.n_items; ++i) {
+    for (int i = 0; i < b.n_items; ++i) {
         const RasterConsts* rc;
         const BinLayout* bl;
-        if (bin_layout(b.items[i >> 1], i & 1, rc, bl)) bin_big(sc, *rc, *bl, blockIdx.x, gridDim.x);
+        if (bin_layout(b.items[i], layout, rc, bl)) bin_big(sc, *rc, *bl, blockIdx.x, gridDim.x);
     }
 }
 
@@ -842,19 +842,25 @@ struct dhr_server {
     LoopHost loop;
 };
 
+// binning of the batch's layout 0 (traced poses) or 1 (warp targets) on `st`
+static void launch_bins(const SceneView& sv, cudaStream_t st, const BatchTable* tb, int layout) {
+    serve_bin_clear_kernel<<<148 * 2, 256, 0, st>>>(tb, layout);
+    serve_bin_kernel<<<148 * 8, kChunk, 0, st>>>(sv, tb, layout);
+    serve_bin_big_kernel<<<kBigGrid, 128, 0, st>>>(sv, tb, layout);
+}
+
 // the stages of one batch on `st`, all reading the batch table `tb`:
 // binning, trace, temporal, a-trous levels, delay warp; the warp target's
-// primary visibility needs only the bins, so it runs on a branch of its own
-// (fork_st) that joins before the warp
+// binning and primary visibility form a branch of their own (fork_st) that
+// joins before the warp
 static void launch_stages(const dhr_server* s, cudaStream_t st, const BatchTable* tb) {
     const SceneView sv = s->scene->view();
-    serve_bin_clear_kernel<<<148 * 2, 256, 0, st>>>(tb);
-    serve_bin_kernel<<<148 * 8, kChunk, 0, st>>>(sv, tb);
-    serve_bin_big_kernel<<<kBigGrid, 128, 0, st>>>(sv, tb);
     cudaEventRecord(s->ev_fork, st);
     cudaStreamWaitEvent(s->fork_st, s->ev_fork, 0);
+    launch_bins(sv, s->fork_st, tb, 1);
     serve_trace_kernel<<<s->grid_trace, 256, 0, s->fork_st>>>(sv, tb, 1);
     cudaEventRecord(s->ev_join, s->fork_st);
+    launch_bins(sv, st, tb, 0);
     serve_trace_kernel<<<s->grid_trace, 256, 0, st>>>(sv, tb, 0);
     serve_temporal_kernel<<<s->grid_px, dim3(32, 8), 0, st>>>(tb);
     const int L = (int)s->sp.levels;
