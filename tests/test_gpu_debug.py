@@ -4,7 +4,8 @@ Every path runs on ragged image sizes (tiles cut by the image border) in a
 child process that loads libdhrs_debug.so (DHRS_DEBUG=1): tracing with
 traversed and rasterised primaries, selective shadow rays, the SVGF in both
 storage forms and both kernel widths, the pipelined session, the adjoint,
-the batched server and the packer.  No gather index may leave its buffer
+the batched server (with warp targets, traced and rasterised) and the
+packer.  No gather index may leave its buffer
 (dhr_debug_status reports no event).  The self test then makes one checked
 out-of-range read, which must be reported with its site and index; the
 check redirects the read, so nothing outside a buffer is touched.
@@ -81,16 +82,20 @@ for sched in (dhrs.TAPE_RECOMPUTE, dhrs.TAPE_STORE):
         tape.backward(gbs, cams[:F], sig, p, gout)
 res["adjoint"] = dhrs.debug_status()[0]
 
-srv = dhrs.Server(sc, 4 << 30)
-ids = [srv.open(W, H), srv.open(96, 50)]
 paths = [cams, wl.orbit_path(4, 96, 50, degrees=9.0, start_deg=40)]
-for f in range(3):
-    for k, sid in enumerate(ids):
-        srv.submit(sid, paths[k][f], f, dhrs.now_ns(), 10 * k + f)
-    srv.pump()
-    done = srv.poll(wait=True)
-    while len([d for d in done if not d["dropped"]]) < len(ids):
-        done += srv.poll(wait=True)
+for raster_min in (None, 0):   # primary rays; every session and warp target rasterised
+    srv = dhrs.Server(sc, 4 << 30)
+    if raster_min is not None:
+        srv.set_raster_min_pixels(raster_min)
+    ids = [srv.open(W, H), srv.open(96, 50)]
+    for f in range(3):
+        for k, sid in enumerate(ids):
+            srv.submit(sid, paths[k][f], f, dhrs.now_ns(), 10 * k + f, cam_target=paths[k][f + 1])
+        srv.pump()
+        done = srv.poll(wait=True)
+        while len([d for d in done if not d["dropped"]]) < len(ids):
+            done += srv.poll(wait=True)
+    srv.close()
 res["server"] = dhrs.debug_status()[0]
 
 dhrs.pack_visibility(mask, ao, 1, 1)
