@@ -835,8 +835,9 @@ struct dhr_server {
     uint64_t max_batch_px = kDefaultBatchPx;   // pixel cap of one batch (0: none)
     uint64_t raster_min_px = kDefaultRasterMinPx;   // sessions from this size rasterise primaries
     cudaStream_t mem_stream = nullptr;  // session allocations (stream ordered)
-    // a batch graph's branch for the warp target's primary visibility (only
-    // used while graphs are captured; lowest priority)
+    // a batch graph's branch for the warp targets' binning and primary
+    // visibility (only used while graphs are captured; lowest priority, the
+    // slots' and loops' capture streams highest)
     cudaStream_t fork_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     LoopHost loop;
