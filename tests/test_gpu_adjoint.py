@@ -243,3 +243,29 @@ def test_backward_on_a_caller_stream():
     scale = float(g_ref.abs().max())
     assert float((host[0] - g_ref.cpu()).abs().max()) <= 1e-6 * scale
     assert torch.allclose(host[1], s_ref.cpu(), rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("W,H,F,levels", [(37, 23, 3, 5), (50, 31, 4, 8)])
+def test_ragged_sizes_and_most_levels(W, H, F, levels):
+    """Image sizes that cut the 32 x 8 tiles, and the largest level count
+    (8: steps up to 128, beyond the image), under both record schedules,
+    against the oracle's adjoint."""
+    zn, mesh, cams, sig, g_out = _inputs(W, H, F, seed=9)
+    op = orc.SvgfParams(levels=levels)
+    out_o, gsig_o, gsigma_o = orc.svgf_seq_grad(zn, mesh, cams, sig, op, g_out)
+    gbufs = [dhrs.GBuffer.from_arrays(zn[f], mesh[f]) for f in range(F)]
+    gp = dhrs.SvgfParams(**op.__dict__)
+    sig_t = torch.from_numpy(_planes(sig).astype(np.float32)).cuda()
+    gout_t = torch.from_numpy(_planes(g_out).astype(np.float32)).cuda()
+    for sched in (dhrs.TAPE_RECOMPUTE, dhrs.TAPE_STORE):
+        tape = dhrs.SvgfTape(W, H, F, sched)
+        out = tape.forward(gbufs, cams, sig_t, gp)
+        g_sig, g_sigma = tape.backward(gbufs, cams, sig_t, gp, gout_t)
+        torch.cuda.synchronize()
+        out = np.moveaxis(out.cpu().numpy(), 1, -1)
+        g_sig = np.moveaxis(g_sig.cpu().numpy(), 1, -1)
+        g_sigma = g_sigma.cpu().numpy()
+        assert np.abs(out - out_o).max() <= 1e-3
+        assert np.abs(g_sig - gsig_o).max() <= 1e-3 * np.abs(gsig_o).max()
+        for c in range(3):
+            assert abs(g_sigma[c] - gsigma_o[c]) <= 1e-2 * abs(gsigma_o[c]) + 1e-4, (sched, c, g_sigma, gsigma_o)
