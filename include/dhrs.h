@@ -192,6 +192,13 @@ const char* dhr_last_error(void);
 /* triangle centroids on the device.                                        */
 /* ---------------------------------------------------------------------- */
 /* Copies the soup to the device, builds the BVH on `stream`, synchronises.
+ * It also builds the start cells of bounded rays: loose grids over the
+ * scene box, 128 cells along its longest axis at the finest level and
+ * sqrt(2) times wider cells at each coarser one.  Each cell holds up to four
+ * BVH nodes under which lies every triangle that overlaps the cell.  An AO
+ * ray (length r) and a shadow ray (clipped to the scene box) start their
+ * traversal at those nodes of the finest cell that holds their segment's
+ * box (16 bytes per cell, in the scene's device memory).
  * Errors: DHR_ERR_INVALID (null desc, index out of range, more than 2^31
  * triangles), DHR_ERR_OOM, DHR_ERR_CUDA. */
 dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream, dhr_scene** out);
@@ -376,9 +383,9 @@ dhr_status dhr_svgf_reconstruct(dhr_svgf_state* state, const dhr_gbuffer* cur,
  * the first recorded event since the last call (0: none) and clears the
  * record: bit 63 set, bits 40..47 the site (1 a-trous tap, 2 a-trous
  * variance, 3 depth slope, 4 reprojection, 5 short-history estimate, 6 BVH
- * node, 7 triangle, 8 tile list, 10 adjoint, 11 self test), bits 0..39 the
- * offending index.  debug_build: 1 in the debug build (first_error is
- * always 0 in the release build).  Errors: DHR_ERR_INVALID (null),
+ * node, 7 triangle, 8 tile list, 10 adjoint, 11 self test, 12 start cell
+ * of an AO ray), bits 0..39 the offending index.  debug_build: 1 in the
+ * debug build (first_error is always 0 in the release build).  Errors: DHR_ERR_INVALID (null),
  * DHR_ERR_CUDA. */
 dhr_status dhr_debug_status(uint64_t* first_error, int32_t* debug_build);
 /* Debug build only: one checked read at index 5 of a one-element buffer on

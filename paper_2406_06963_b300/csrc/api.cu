@@ -132,6 +132,7 @@ extern "C" dhr_status dhr_create_scene(const dhr_scene_desc* desc, void* stream,
                           cudaGetErrorString(e));
         if (s == DHR_OK) s = build_lbvh(v, idx, mesh, desc->n_vertices, desc->n_triangles, st, sc, desc->builder);
         if (s == DHR_OK) s = build_chunk_boxes(sc, st);
+        if (s == DHR_OK) s = build_seed_grid(sc, st);
         cudaStreamSynchronize(st);
     }
     cudaFree(v);
@@ -150,6 +151,7 @@ extern "C" void dhr_destroy_scene(dhr_scene* sc) {
     cudaFree(sc->nodes);
     cudaFree(sc->tris);
     cudaFree(sc->chunk_box);
+    cudaFree(const_cast<int4*>(sc->seeds.cells));
     delete sc;
 }
 

@@ -7,6 +7,9 @@
 // tree construction of Karras ("Maximizing Parallelism in the Construction
 // of BVHs, Octrees, and k-d Trees", HPG 2012), and a bottom-up box refit in
 // which the second thread to reach a node computes its box.
+#include <algorithm>
+#include <cmath>
+
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
@@ -522,6 +525,132 @@ dhr_status build_lbvh(const float* v, const uint32_t* idx, const uint32_t* mesh,
         return set_error(DHR_ERR_INVALID,
                          "create_scene: BVH height %u exceeds the traversal stack (%d)", sc->height,
                          kStackSize);
+    return DHR_OK;
+}
+
+// ------------------------------------------------ start cells of bounded rays
+namespace {
+
+// Nodes under which lies every triangle whose box overlaps [lo, hi]: from
+// the root, each of kSeedSlots slots follows one subtree; a child whose box
+// misses [lo, hi] is dropped, a node whose two child boxes both overlap it
+// takes a second slot while one is free, and a slot with no free slot to
+// split into keeps its node.  Returns the occupied slots.
+__device__ uint32_t seed_frontier(const SceneView& sc, float3 lo, float3 hi, int (&node)[kSeedSlots]) {
+    constexpr uint32_t kAll = (1u << kSeedSlots) - 1u;
+#pragma unroll
+    for (int s = 0; s < kSeedSlots; ++s) node[s] = kSeedEmpty;
+    if (sc.n_tris == 0) return 0u;
+    node[0] = 0;
+    uint32_t used = 1u, done = 0u;   // slots occupied / not to be split further
+    // every round moves each open slot one level down: a tree of height
+    // < kStackSize (checked at build) ends within kStackSize rounds
+    for (int round = 0; round < kStackSize && (used & ~done); ++round) {
+#pragma unroll
+        for (int s = 0; s < kSeedSlots; ++s) {
+            if (!(((used & ~done) >> s) & 1u)) continue;
+            const int n = node[s];
+            if (n < 0) {   // a leaf: its triangle is the slot's only one
+                done |= 1u << s;
+                continue;
+            }
+            const float4* nd = sc.nodes + 4 * (int)dbg_index(n, sc.n_nodes, kSiteNode);
+            const float4 a = nd[0], b = nd[1], c = nd[2], d = nd[3];
+            const bool o0 = a.x <= hi.x && a.z >= lo.x && b.x <= hi.y && b.z >= lo.y && c.x <= hi.z && c.z >= lo.z;
+            const bool o1 = a.y <= hi.x && a.w >= lo.x && b.y <= hi.y && b.w >= lo.y && c.y <= hi.z && c.w >= lo.z;
+            const int c0 = __float_as_int(d.x), c1 = __float_as_int(d.y);
+            if (o0 != o1) {
+                node[s] = o0 ? c0 : c1;
+            } else if (!o0) {
+                node[s] = kSeedEmpty;
+                used &= ~(1u << s);
+                done = 0u;   // a slot came free: stopped slots may split again
+            } else {
+                const uint32_t fre = ~used & kAll;
+                if (!fre) {
+                    done |= 1u << s;
+                } else {
+                    const int t = __ffs(fre) - 1;
+                    node[s] = c0;
+#pragma unroll
+                    for (int u = 0; u < kSeedSlots; ++u)
+                        if (u == t) node[u] = c1;
+                    used |= 1u << t;
+                }
+            }
+        }
+    }
+    return used;
+}
+
+// one thread per cell of every level
+__global__ void seed_grid_kernel(SceneView sc, int4* cells) {
+    const SeedGrid& g = sc.seeds;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.n_cells) return;
+    int l = 0;
+    while (l + 1 < g.levels && c >= g.off[l + 1]) ++l;
+    const int r = c - g.off[l], dx = g.dim[l][0], dy = g.dim[l][1];
+    const int i[3] = {r % dx, (r / dx) % dy, r / (dx * dy)};
+    const float s = g.side[l];
+    // the loose box, padded far beyond the rounding of its corners and of
+    // the lookup's cell index
+    const float pad = s * (1.0f / 1024.0f);
+    float lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = g.org[k] + ((float)i[k] - 0.5f) * s - pad;
+        hi[k] = g.org[k] + ((float)i[k] + 1.5f) * s + pad;
+    }
+    int node[kSeedSlots];
+    seed_frontier(sc, make_float3(lo[0], lo[1], lo[2]), make_float3(hi[0], hi[1], hi[2]), node);
+    static_assert(kSeedSlots == 4, "a cell is one int4");
+    cells[c] = make_int4(node[0], node[1], node[2], node[3]);
+}
+
+}  // namespace
+
+dhr_status build_seed_grid(dhr_scene* sc, cudaStream_t st) {
+    SeedGrid& g = sc->seeds;
+    g = SeedGrid{};
+    if (sc->n_tris == 0) return DHR_OK;
+    // the scene box: the root's two child boxes
+    float4 root[4];
+    DHR_CUDA_TRY(cudaMemcpyAsync(root, sc->nodes, sizeof(root), cudaMemcpyDeviceToHost, st));
+    DHR_CUDA_TRY(cudaStreamSynchronize(st));
+    const float lo[3] = {fminf(root[0].x, root[0].y), fminf(root[1].x, root[1].y), fminf(root[2].x, root[2].y)};
+    const float hi[3] = {fmaxf(root[0].z, root[0].w), fmaxf(root[1].z, root[1].w), fmaxf(root[2].z, root[2].w)};
+    float ext = 0.f;
+    for (int k = 0; k < 3; ++k) ext = fmaxf(ext, hi[k] - lo[k]);
+    if (!(ext > 0.f) || !std::isfinite(ext)) return DHR_OK;   // no grid: rays start at the root
+    // level 0: 128 cells along the longest axis; each level's cells are
+    // sqrt(2) times wider than the previous level's
+    for (int k = 0; k < 3; ++k) {
+        g.org[k] = lo[k];
+        g.top[k] = hi[k];
+    }
+    long long total = 0;
+    for (int l = 0; l < kSeedLevels; ++l) {
+        const double s = (double)ext / 128.0 * std::pow(std::sqrt(2.0), (double)l);
+        g.side[l] = (float)s;
+        g.inv[l] = (float)(1.0 / s);
+        bool one = true;
+        for (int k = 0; k < 3; ++k) {
+            g.dim[l][k] = std::max(1, (int)std::ceil((double)(hi[k] - lo[k]) / s));
+            one = one && g.dim[l][k] == 1;
+        }
+        g.off[l] = (int)total;
+        total += (long long)g.dim[l][0] * g.dim[l][1] * g.dim[l][2];
+        g.levels = l + 1;
+        if (one) break;
+    }
+    g.n_cells = (int)total;
+    int4* cells = nullptr;
+    DHR_TRY(dmalloc(&cells, (size_t)total, "seed grid"));
+    g.cells = cells;
+    sc->bytes += (uint64_t)total * sizeof(int4);
+    seed_grid_kernel<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(sc->view(), cells);
+    DHR_CUDA_TRY(cudaGetLastError());
     return DHR_OK;
 }
 

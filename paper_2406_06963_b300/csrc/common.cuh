@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
@@ -61,6 +62,7 @@ enum DebugSite : uint32_t {
     kSiteRasterBin = 9,     // binning writes
     kSiteAdjoint = 10,      // adjoint gathers and scatters
     kSiteSelfTest = 11,     // dhr_debug_selftest
+    kSiteSeedCell = 12,     // start cell of a bounded ray
 };
 
 #ifdef DHR_DEBUG
@@ -113,12 +115,34 @@ static DebugRegistration g_debug_registration;
 //   d = (child0, child1, -, -) as int bits; >= 0 internal node, < 0 leaf ~i
 // Leaf i holds sorted triangle i: 3 float4 (v0, orig index bits),
 // (v1, mesh id bits), (v2, 0).
+//
+// Start cells of bounded rays: a hierarchy of loose grids over the scene
+// box.  Level l has cells of side s_l = s_0 sqrt(2)^l; cell i of an axis covers
+// [org + (i - 1/2) s_l, org + (i + 3/2) s_l] (its own extent and half a side
+// beyond each face), so a box of side <= s_l whose centre lies in cell i
+// lies inside it.  A cell holds up to kSeedSlots nodes (kSeedEmpty: unused)
+// under which lies every triangle whose box overlaps the cell's.
+constexpr int kSeedSlots = 4, kSeedLevels = 16;
+constexpr int kSeedEmpty = INT_MIN;
+struct SeedGrid {
+    const int4* cells;   // all levels' cells, level by level, x fastest, then y, then z
+    float org[3];        // scene box minimum
+    float top[3];        // scene box maximum
+    float side[kSeedLevels];   // s_l
+    float inv[kSeedLevels];    // 1 / s_l
+    int levels;          // 0: no grid (every ray starts at the root)
+    int n_cells;
+    int dim[kSeedLevels][3];
+    int off[kSeedLevels];
+};
+
 struct SceneView {
     const float4* nodes;
     const float4* tris;
     int32_t n_tris;
     const float4* chunk_box;   // per kChunk consecutive leaves: (lo, -), (hi, -) of their vertices
     int32_t n_nodes;           // internal nodes
+    SeedGrid seeds;
 };
 
 // leaves per chunk of the rasteriser's frustum test (one binning block)
@@ -208,13 +232,14 @@ struct dhr_scene {
     float4* nodes = nullptr;
     float4* tris = nullptr;
     float4* chunk_box = nullptr;
+    dhr::SeedGrid seeds{};      // seeds.cells: device memory owned by the scene
     uint32_t n_tris = 0;
     uint32_t n_nodes = 0;
     uint32_t height = 0;
     uint64_t bytes = 0;
     float build_ms = 0.f;
     dhr::SceneView view() const {
-        return dhr::SceneView{nodes, tris, (int32_t)n_tris, chunk_box, (int32_t)n_nodes};
+        return dhr::SceneView{nodes, tris, (int32_t)n_tris, chunk_box, (int32_t)n_nodes, seeds};
     }
 };
 
@@ -245,6 +270,8 @@ dhr_status launch_trace_selective(const dhr_scene* sc, const dhr_camera* cam, co
 // launches nothing) when the camera basis is singular; the caller then traces
 // primary rays instead.
 dhr_status build_chunk_boxes(dhr_scene* sc, cudaStream_t st);
+// the start cells of bounded rays (SeedGrid), after the BVH
+dhr_status build_seed_grid(dhr_scene* sc, cudaStream_t st);
 dhr_status launch_raster(const dhr_scene* sc, const dhr_camera* cam, dhr_gbuffer* g, cudaStream_t st,
                          bool* launched);
 

@@ -7,6 +7,8 @@
 // Traversal: depth-first over the 2-wide BVH with a per-thread stack, near
 // child first; any-hit rays stop at the first accepted hit, and AO rays
 // carry tmax = r so that short rays prune most of the tree (Section 3.2).
+// AO and shadow rays start below the root: at the nodes of a precomputed
+// start cell that holds every triangle their segment can reach.
 // Triangle test: the watertight ray/triangle intersection of Woop, Benthin
 // and Wald (JCGT 2013) in binary32, with its double-precision fallback for
 // edge functions that are exactly zero.  Ray/box test: slabs with the
@@ -16,6 +18,7 @@
 
 #include <cuda_fp16.h>
 
+#include <climits>
 #include <cmath>
 
 #include "common.cuh"
@@ -145,13 +148,30 @@ struct Work {
     uint32_t tests = 0;    // triangles tested
 };
 
-template <bool kAnyHit, bool kStats = false>
+// The traversal starts at the root, or (kF > 0) at the nodes seed[s] of the
+// slots s set in `seeds`, under which lies every triangle the ray can reach
+// (seed_start).
+template <bool kAnyHit, bool kStats = false, int kF = 0>
 __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tmax, float3& bary,
-                        int skip_leaf = -1, Work* work = nullptr) {
+                        int skip_leaf = -1, Work* work = nullptr, const int* seed = nullptr,
+                        uint32_t seeds = 0) {
     if (sc.n_tris == 0) return -1;
-    int stack[kStackSize];
+    // a start from kF seeds holds up to kF - 1 of them on the stack beside
+    // the at most height - 1 entries of a depth-first walk below depth 1
+    int stack[kStackSize + kF];
     int sp = 0;
     int node = 0;
+    if constexpr (kF > 0) {
+        if (seeds == 0) return -1;
+        bool first = true;
+#pragma unroll
+        for (int s = 0; s < kF; ++s) {
+            if (!((seeds >> s) & 1u)) continue;
+            if (first) node = seed[s];
+            else stack[sp++] = seed[s];
+            first = false;
+        }
+    }
     int best = -1;
     uint32_t best_orig = 0xFFFFFFFFu;
     // a valid tree visits each node at most once per ray; the cap only
@@ -173,7 +193,7 @@ __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tm
                     c0 = c1;
                     c1 = t;
                 }
-                if (sp < kStackSize) stack[sp++] = c1;   // height < kStackSize is checked at build
+                if (sp < kStackSize + kF) stack[sp++] = c1;   // height < kStackSize is checked at build
                 node = c0;
                 continue;
             }
@@ -209,6 +229,62 @@ __device__ int traverse(const SceneView& sc, const Ray& r, float tmin, float& tm
         node = stack[--sp];
     }
     return best;
+}
+
+// Start of a bounded ray: the nodes of the start cell (SeedGrid) whose
+// loose box contains the box [c - h, c + h] that the ray cannot leave.  The
+// level is the finest whose cells are at least 2h wide (with a margin for
+// the rounding of the cell index); a centre outside the grid takes the
+// nearest cell, which still holds the part of the box inside the scene.
+// Returns the occupied slots of seed; a box wider than every level (or not
+// finite) starts at the root.
+__device__ __forceinline__ uint32_t seed_start(const SceneView& sc, float3 c, float h, int (&seed)[kSeedSlots]) {
+    const SeedGrid& g = sc.seeds;
+    seed[0] = 0;
+    const float w = 2.0f * h * 1.002f;
+    int l = 0;
+    while (l < g.levels && !(w <= g.side[l])) ++l;
+    if (l == g.levels) return 1u;
+    const float inv = g.inv[l];
+    const int ix = min(max(__float2int_rd((c.x - g.org[0]) * inv), 0), g.dim[l][0] - 1);
+    const int iy = min(max(__float2int_rd((c.y - g.org[1]) * inv), 0), g.dim[l][1] - 1);
+    const int iz = min(max(__float2int_rd((c.z - g.org[2]) * inv), 0), g.dim[l][2] - 1);
+    const long long cell = g.off[l] + ((long long)iz * g.dim[l][1] + iy) * g.dim[l][0] + ix;
+    const int4 v = __ldg(g.cells + dbg_index(cell, g.n_cells, kSiteSeedCell));
+    seed[0] = v.x;
+    seed[1] = v.y;
+    seed[2] = v.z;
+    seed[3] = v.w;
+    return (v.x != kSeedEmpty ? 1u : 0u) | (v.y != kSeedEmpty ? 2u : 0u) | (v.z != kSeedEmpty ? 4u : 0u) |
+           (v.w != kSeedEmpty ? 8u : 0u);
+}
+
+// Start of an unbounded ray (a shadow ray): every triangle lies in the
+// scene box, so the ray can reach only the part of it inside that box, up to
+// its exit distance; the start cell is the one of that segment's box.
+__device__ __forceinline__ uint32_t segment_start(const SceneView& sc, const Ray& r, int (&seed)[kSeedSlots]) {
+    const SeedGrid& g = sc.seeds;
+    seed[0] = 0;
+    if (g.levels == 0) return 1u;
+    const float o[3] = {r.o.x, r.o.y, r.o.z}, d[3] = {r.d.x, r.d.y, r.d.z};
+    float t1 = INFINITY;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float id = unpack2(r.idir2[k]).x;   // 1 / d (tiny d clamped)
+        t1 = fminf(t1, ((d[k] >= 0.0f ? g.top[k] : g.org[k]) - o[k]) * id);
+    }
+    t1 = fmaxf(t1, 0.0f);   // an origin outside the box, heading away: nothing to reach
+    float c[3], h = 0.0f, m = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float e = fmaf(t1, d[k], o[k]);
+        c[k] = 0.5f * (o[k] + e);
+        h = fmaxf(h, fabsf(e - o[k]));
+        m = fmaxf(m, fabsf(o[k]));
+    }
+    // half the widest side, padded far beyond the rounding of t1 and of e
+    h = 0.5f * h + 1e-5f * (m + h);
+    return seed_start(sc, make_float3(c[0], c[1], c[2]), h, seed);
 }
 
 // Unit normal of a triangle with a written binary32 operation order, each
@@ -571,21 +647,33 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
         float tm = INFINITY;
         float3 b;
         ++n_sh;
-        if (traverse<true, kStats>(sc, make_ray(o, d), 0.0f, tm, b, leaf, &ws) < 0) mask |= 1u << l;
+        const Ray ray = make_ray(o, d);
+        int sd[kSeedSlots];
+        const uint32_t sds = segment_start(sc, ray, sd);
+        if (traverse<true, kStats, kSeedSlots>(sc, ray, 0.0f, tm, b, leaf, &ws, sd, sds) < 0) mask |= 1u << l;
     }
     mask_out[pix] = (uint8_t)mask;
     if constexpr (kSel) {
         if (ray_mask) ray_mask[pix] = (uint8_t)called;
     }
-    // AO rays: cosine-weighted, a hit closer than r occludes (Eq. 2-3)
+    // AO rays: cosine-weighted, a hit closer than r occludes (Eq. 2-3).  They
+    // stay inside the ball of radius r around o; its box, padded far beyond
+    // the rounding of the hit distance and of the hit point, bounds them.
     uint32_t unocc = 0;
+    int seed[kSeedSlots];
+    const float pad = 1e-5f * (k.ao_radius + fmaxf(fabsf(o.x), fmaxf(fabsf(o.y), fabsf(o.z))));
+    const uint32_t seeds = k.ao_spp > 0 ? seed_start(sc, o, k.ao_radius + pad, seed) : 0u;
     for (uint32_t j = 0; j < k.ao_spp; ++j) {
+        ++n_ao;
+        if (seeds == 0) {   // no triangle near o
+            ++unocc;
+            continue;
+        }
         const float2 xy = disk_point(px.x, px.y, k.frame, k.seed, kAoRay, j);
         const float3 d = ao_direction(n, xy);
         float tm = k.ao_radius;
         float3 b;
-        ++n_ao;
-        if (traverse<true, kStats>(sc, make_ray(o, d), 0.0f, tm, b, leaf, &wa) < 0) ++unocc;
+        if (traverse<true, kStats, kSeedSlots>(sc, make_ray(o, d), 0.0f, tm, b, leaf, &wa, seed, seeds) < 0) ++unocc;
     }
     ao_out[pix] = (uint8_t)unocc;
     if (kStats) {

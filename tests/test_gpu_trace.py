@@ -90,6 +90,38 @@ def test_trace_ragged_sizes(boxes, w, h):
     _check(compare_trace(gpu, ref, np.arange(w * h), 1, 4), max_frac=1.0)
 
 
+@pytest.fixture(scope="module")
+def soup():
+    """A floor quad (the bottom face of the scene box) with 3,000 small
+    random triangles scattered above it."""
+    r = np.random.default_rng(11)
+    floor = np.array([[-4, 0, -4], [4, 0, -4], [4, 0, 4], [-4, 0, 4]], np.float64)
+    c = r.uniform([-4, 0.05, -4], [4, 1.5, 4], (3000, 3))
+    sz = r.uniform(0.02, 0.4, (3000, 1, 1))
+    tri = c[:, None, :] + r.normal(size=(3000, 3, 3)) * sz
+    verts = np.concatenate([floor, tri.reshape(-1, 3)]).astype(np.float32)
+    idx = np.concatenate([[[0, 2, 1], [0, 3, 2]], 4 + np.arange(9000).reshape(-1, 3)]).astype(np.uint32)
+    mesh = np.concatenate([[0, 0], 1 + np.arange(3000)]).astype(np.uint32)
+    s = dict(vertices=verts, indices=idx, mesh_ids=mesh)
+    return s, dhrs.Scene(s), orc.Scene(s)
+
+
+@pytest.mark.parametrize("radius", [0.01, 0.07, 0.3, 1.0, 5.0, 100.0])
+def test_ao_start_cells(soup, radius):
+    """AO rays start their traversal at the nodes of the start cell that
+    holds their ball of radius r (levels of cells 1/16 to 8 units wide over
+    this 8-unit scene; origins on the scene box's bottom face take the
+    nearest cell; r = 5 and 100 are wider than every cell and start at the
+    root).  Every pixel and ray against the oracle, 4 AO rays per pixel."""
+    s, g_scene, o_scene = soup
+    cam = wl.look_at((5.0, 3.0, 6.0), (0.0, 0.3, 0.0), 96, 96)
+    tp = orc.TraceParams(ao_spp=4, ao_radius=radius, frame=2)
+    ref = orc.trace(o_scene, cam, tp)
+    gpu = trace_gpu(g_scene, cam, gpu_params(tp))
+    res = compare_trace(gpu, ref, np.arange(96 * 96), 1, 4)
+    _check(res, max_frac=2e-3)
+
+
 def test_trace_terrain_1080p_sampled(terrain):
     """1920x1080, 776,050 triangles, the configuration bench.py times
     (rasterised primary visibility, as in its session frames): the full GPU
