@@ -104,6 +104,9 @@ __device__ __forceinline__ int2 trace_thread_pixel(int2 o) {
     return make_int2(o.x + (warp & 3) * 8 + (lane & 7), o.y + (warp >> 2) * 4 + (lane >> 3));
 }
 
+// The batch's trace: AO rays start at their start cells; shadow rays start
+// at the root (their start cells, at 64 registers per thread here, spilled
+// the kernel's traversal state and served fewer pixels per second).
 __global__ void __launch_bounds__(256, 4) serve_trace_kernel(SceneView sc, const BatchTable* tb, int primary_target) {
     const BatchTable& b = *tb;
     for (int t = blockIdx.x; t < b.n_tiles; t += gridDim.x) {
@@ -117,10 +120,11 @@ __global__ void __launch_bounds__(256, 4) serve_trace_kernel(SceneView sc, const
                 trace_pixel<false, false, true, false, false, 8>(sc, it.tk_target, px, it.g_tgt, it.m_tgt, nullptr,
                                                                  nullptr, nullptr);
         } else if (it.raster) {
-            trace_pixel<false, false, false, false, true, 8>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask, it.ao, nullptr);
+            trace_pixel<false, false, false, false, true, 8, false>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask, it.ao,
+                                                                    nullptr);
         } else {
-            trace_pixel<false, false, false, false, false, 8>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask, it.ao,
-                                                              nullptr);
+            trace_pixel<false, false, false, false, false, 8, false>(sc, it.tk, px, it.g_cur, it.m_cur, it.mask,
+                                                                     it.ao, nullptr);
         }
     }
 }

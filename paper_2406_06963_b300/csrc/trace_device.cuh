@@ -526,8 +526,10 @@ __device__ __forceinline__ int2 thread_pixel() {
 // warp's tile (raster_device.cuh), read from the tile's G-buffer storage
 // before the warp overwrites it; a tile whose list is too long or did not fit
 // is traversed.  kWarps: warps per block (the warp's 32 lanes must cover one
-// 8 x 4-pixel tile).
-template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false, bool kRaster = false, int kWarps = 4>
+// 8 x 4-pixel tile).  kShadowStart: shadow rays start at their segment's
+// start cell (else at the root).
+template <bool kHalf, bool kStats, bool kPrimaryOnly, bool kSel = false, bool kRaster = false, int kWarps = 4,
+          bool kShadowStart = true>
 __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceConsts& k, int2 px, void* gbuf_dn,
                                             uint32_t* gbuf_mesh, uint8_t* mask_out, uint8_t* ao_out,
                                             unsigned long long* stats, const SmapSet* sel = nullptr,
@@ -648,9 +650,13 @@ __device__ __forceinline__ void trace_pixel(const SceneView& sc, const TraceCons
         float3 b;
         ++n_sh;
         const Ray ray = make_ray(o, d);
-        int sd[kSeedSlots];
-        const uint32_t sds = segment_start(sc, ray, sd);
-        if (traverse<true, kStats, kSeedSlots>(sc, ray, 0.0f, tm, b, leaf, &ws, sd, sds) < 0) mask |= 1u << l;
+        if constexpr (kShadowStart) {
+            int sd[kSeedSlots];
+            const uint32_t sds = segment_start(sc, ray, sd);
+            if (traverse<true, kStats, kSeedSlots>(sc, ray, 0.0f, tm, b, leaf, &ws, sd, sds) < 0) mask |= 1u << l;
+        } else {
+            if (traverse<true, kStats>(sc, ray, 0.0f, tm, b, leaf, &ws) < 0) mask |= 1u << l;
+        }
     }
     mask_out[pix] = (uint8_t)mask;
     if constexpr (kSel) {
