@@ -531,11 +531,15 @@ dhr_status build_lbvh(const float* v, const uint32_t* idx, const uint32_t* mesh,
 // ------------------------------------------------ start cells of bounded rays
 namespace {
 
-// Nodes under which lies every triangle whose box overlaps [lo, hi]: from
-// the root, each of kSeedSlots slots follows one subtree; a child whose box
-// misses [lo, hi] is dropped, a node whose two child boxes both overlap it
-// takes a second slot while one is free, and a slot with no free slot to
-// split into keeps its node.  Returns the occupied slots.
+// Internal nodes under which lies every triangle whose box overlaps
+// [lo, hi]: from the root, each of kSeedSlots slots follows one subtree; a
+// child whose box misses [lo, hi] is dropped, a node whose two child boxes
+// both overlap it takes a second slot while one is free, and a slot with no
+// free slot to split into keeps its node.  A slot never steps onto a leaf
+// (it keeps the leaf's parent), so a ray reaches every leaf through the slab
+// test of the leaf's box, as from the root: a triangle whose box the ray
+// misses is never tested (the watertight test alone can accept a ray that
+// grazes a zero-area triangle).  Returns the occupied slots.
 __device__ uint32_t seed_frontier(const SceneView& sc, float3 lo, float3 hi, int (&node)[kSeedSlots]) {
     constexpr uint32_t kAll = (1u << kSeedSlots) - 1u;
 #pragma unroll
@@ -550,24 +554,22 @@ __device__ uint32_t seed_frontier(const SceneView& sc, float3 lo, float3 hi, int
         for (int s = 0; s < kSeedSlots; ++s) {
             if (!(((used & ~done) >> s) & 1u)) continue;
             const int n = node[s];
-            if (n < 0) {   // a leaf: its triangle is the slot's only one
-                done |= 1u << s;
-                continue;
-            }
             const float4* nd = sc.nodes + 4 * (int)dbg_index(n, sc.n_nodes, kSiteNode);
             const float4 a = nd[0], b = nd[1], c = nd[2], d = nd[3];
             const bool o0 = a.x <= hi.x && a.z >= lo.x && b.x <= hi.y && b.z >= lo.y && c.x <= hi.z && c.z >= lo.z;
             const bool o1 = a.y <= hi.x && a.w >= lo.x && b.y <= hi.y && b.w >= lo.y && c.y <= hi.z && c.w >= lo.z;
             const int c0 = __float_as_int(d.x), c1 = __float_as_int(d.y);
             if (o0 != o1) {
-                node[s] = o0 ? c0 : c1;
+                const int c = o0 ? c0 : c1;
+                if (c >= 0) node[s] = c;
+                else done |= 1u << s;   // the one overlapping child is a leaf
             } else if (!o0) {
                 node[s] = kSeedEmpty;
                 used &= ~(1u << s);
                 done = 0u;   // a slot came free: stopped slots may split again
             } else {
                 const uint32_t fre = ~used & kAll;
-                if (!fre) {
+                if (!fre || c0 < 0 || c1 < 0) {
                     done |= 1u << s;
                 } else {
                     const int t = __ffs(fre) - 1;
