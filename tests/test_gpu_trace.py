@@ -93,15 +93,24 @@ def test_trace_ragged_sizes(boxes, w, h):
 @pytest.fixture(scope="module")
 def soup():
     """A floor quad (the bottom face of the scene box) with 3,000 small
-    random triangles scattered above it."""
+    random triangles scattered above it, and 300 zero-area ones (three
+    collinear vertices, or one vertex three times), which no ray hits.
+    Small start cells often hold one of them alone."""
     r = np.random.default_rng(11)
     floor = np.array([[-4, 0, -4], [4, 0, -4], [4, 0, 4], [-4, 0, 4]], np.float64)
     c = r.uniform([-4, 0.05, -4], [4, 1.5, 4], (3000, 3))
     sz = r.uniform(0.02, 0.4, (3000, 1, 1))
     tri = c[:, None, :] + r.normal(size=(3000, 3, 3)) * sz
+    # on a 1/64 grid, so that binary32 holds the vertices exactly and the
+    # collinear ones stay collinear
+    a = np.round(r.uniform([-4, 0.05, -4], [4, 1.5, 4], (300, 1, 3)) * 64) / 64
+    step = np.round(r.normal(size=(300, 1, 3)) * 6.4) / 64
+    step[::2] = 0.0   # even ones: one vertex three times
+    line = a + np.array([0.0, 1.0, 2.0])[None, :, None] * step
+    tri = np.concatenate([tri, line])
     verts = np.concatenate([floor, tri.reshape(-1, 3)]).astype(np.float32)
-    idx = np.concatenate([[[0, 2, 1], [0, 3, 2]], 4 + np.arange(9000).reshape(-1, 3)]).astype(np.uint32)
-    mesh = np.concatenate([[0, 0], 1 + np.arange(3000)]).astype(np.uint32)
+    idx = np.concatenate([[[0, 2, 1], [0, 3, 2]], 4 + np.arange(9900).reshape(-1, 3)]).astype(np.uint32)
+    mesh = np.concatenate([[0, 0], 1 + np.arange(3300)]).astype(np.uint32)
     s = dict(vertices=verts, indices=idx, mesh_ids=mesh)
     return s, dhrs.Scene(s), orc.Scene(s)
 
@@ -112,12 +121,14 @@ def test_ao_start_cells(soup, radius):
     holds their ball of radius r (levels of cells 1/16 to 8 units wide over
     this 8-unit scene; origins on the scene box's bottom face take the
     nearest cell; r = 5 and 100 are wider than every cell and start at the
-    root).  Every pixel and ray against the oracle, 4 AO rays per pixel."""
+    root).  Every pixel and ray against the oracle, 4 AO rays per pixel;
+    no primary ray hits a zero-area triangle."""
     s, g_scene, o_scene = soup
     cam = wl.look_at((5.0, 3.0, 6.0), (0.0, 0.3, 0.0), 96, 96)
     tp = orc.TraceParams(ao_spp=4, ao_radius=radius, frame=2)
     ref = orc.trace(o_scene, cam, tp)
     gpu = trace_gpu(g_scene, cam, gpu_params(tp))
+    assert not ((gpu["mesh"] > 3000) & (gpu["mesh"] <= 3300)).any()   # the zero-area triangles' ids
     res = compare_trace(gpu, ref, np.arange(96 * 96), 1, 4)
     _check(res, max_frac=2e-3)
 
